@@ -1,0 +1,271 @@
+"""Strip solve: GMRES with the combination-technique preconditioner (Sect. 4.3).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+* ``fgmres``: right-preconditioned flexible GMRES(m) with modified Gram-Schmidt
+  and Givens rotations, in FP64; stops on the true relative residual
+  ||b - A x|| / ||b||.
+* ``ComponentSolver``: solves A_{l,l} du = r on one anisotropic full grid
+  (Eq. 22) by GMRES, preconditioned by the inverse of
+  (T_t + d C_t + G_t) (x) M^(1)_{l1} (x) M^(2)_{l2} (Sect. 4.3), each factor
+  inverted exactly (2x2 inverse; sparse LU of the mass matrices).
+* ``ct_precondition``: Algorithm 1's preconditioner step with 0-based levels:
+  solves on the grids (l, L-l), l = 0..L and (l, L-1-l), l = 0..L-1 (residual
+  restricted in dim 1 from grid (l+1, L-1-l)), then the combination
+  du_l = dhat_l - (E^(1) (x) Id) dhat_(l-1, L-l).
+* ``richardson``: Algorithm 1 itself (u <- u - P(A u - b)), stop on the
+  Euclidean norm of the correction.
+* ``StripSolver``: the implicit strip-by-strip scheme (Sect. 2): the right-hand
+  side (U^-_{j-1}, w^+_{j-1}) = eta(t_{j-1}^+) (x) M_sg U^-_{j-1} (Eq. 5), with
+  (u0, w^+) from load vectors for the first strip; the end value
+  U^-_j = sum_s eta_s(t_j) u_s.
+* ``nodal_values``: the unique representation of a sparse-grid function: its
+  values at the nodes of every component grid (prolongation from coarser
+  levels, injection from finer ones).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .assembly import Factor, assemble_load
+from .operator import SparseGridOperator, eta_at, time_matrices
+
+
+def fgmres(A, b, M=None, x0=None, tol=1e-10, restart=30, maxiter=1000):
+    """Returns (x, iterations, relative true residual, history)."""
+    M = M if M is not None else (lambda v: v)
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return np.zeros_like(b), 0, 0.0, [0.0]
+    r = b - A(x)
+    beta = np.linalg.norm(r)
+    hist = [beta / bnorm]
+    it = 0
+    while beta > tol * bnorm and it < maxiter:
+        m = restart
+        V = [r / beta]
+        Z = []
+        H = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        k = 0
+        for j in range(m):
+            z = M(V[j])
+            Z.append(z)
+            w = A(z)
+            for i in range(j + 1):
+                H[i, j] = np.dot(w, V[i])
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            rho = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / rho, H[j + 1, j] / rho
+            H[j, j] = rho
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            k = j + 1
+            it += 1
+            hist.append(abs(g[j + 1]) / bnorm)
+            if abs(g[j + 1]) <= tol * bnorm or it >= maxiter:
+                break
+            nw = np.linalg.norm(w)
+            if nw == 0.0:
+                break
+            V.append(w / nw)
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+        for i in range(k):
+            x = x + y[i] * Z[i]
+        r = b - A(x)
+        beta = np.linalg.norm(r)
+        hist.append(beta / bnorm)
+    return x, it, beta / bnorm, hist
+
+
+class ComponentSolver:
+    """GMRES on A_{l,l} with the (T_t + d C_t + G_t) (x) M (x) M preconditioner."""
+
+    def __init__(self, op: SparseGridOperator, tol=1e-12, restart=60, maxiter=5000):
+        self.op = op
+        self.tol, self.restart, self.maxiter = tol, restart, maxiter
+        Mt, Tt, Ct, Gt = time_matrices(op.prob.dt, op.prob.r)
+        self.Pt_inv = np.linalg.inv(Tt + op.prob.delta * Ct + Gt)
+        self._lu = {}
+        self.iterations = []
+
+    def _mass_lu(self, store, l):
+        key = (id(store), l)
+        if key not in self._lu:
+            self._lu[key] = spla.splu(store.proj(Factor("vol"), l, l).tocsc())
+        return self._lu[key]
+
+    def precond(self, l1, l2, v):
+        n1, n2 = self.op.grid_shape(l1, l2)
+        R = self.op.R
+        u = v.reshape(n1, n2, R)
+        u = np.einsum("st,abt->abs", self.Pt_inv, u)
+        lu1 = self._mass_lu(self.op.fx, l1)
+        lu2 = self._mass_lu(self.op.fv, l2)
+        u = lu1.solve(u.reshape(n1, n2 * R)).reshape(n1, n2, R)
+        t = np.ascontiguousarray(u.transpose(1, 0, 2)).reshape(n2, n1 * R)
+        u = lu2.solve(t).reshape(n2, n1, R).transpose(1, 0, 2)
+        return np.ascontiguousarray(u).ravel()
+
+    def solve(self, l1, l2, r):
+        n1, n2 = self.op.grid_shape(l1, l2)
+        R = self.op.R
+        A = lambda x: self.op.apply_diag(l1, l2, x.reshape(n1, n2, R)).ravel()
+        x, it, res, _ = fgmres(A, r.ravel(), lambda v: self.precond(l1, l2, v),
+                               tol=self.tol, restart=self.restart, maxiter=self.maxiter)
+        self.iterations.append(it)
+        return x.reshape(n1, n2, R)
+
+
+def ct_precondition(op: SparseGridOperator, comp: ComponentSolver, r: np.ndarray) -> np.ndarray:
+    """Algorithm 1 (0-based levels): the preconditioned residual du = P(r)."""
+    L = op.L
+    up = [comp.solve(l, L - l, op.block(r, l)) for l in range(L + 1)]
+    lo = []
+    for l in range(L):
+        r_hi = op.block(r, l + 1)                       # grid (l+1, L-1-l)
+        E = op.hx.E[l]                                  # E_{l+1 <- l}
+        r_lo = op.left(E.T.tocsr(), r_hi)               # restriction in dim 1
+        lo.append(comp.solve(l, L - 1 - l, r_lo))
+    out = np.zeros(op.size)
+    for l in range(L + 1):
+        du = up[l]
+        if l >= 1:
+            du = du - op.left(op.hx.E[l - 1], lo[l - 1])   # (l-1, L-l) -> (l, L-l)
+        out[op.offsets[l]:op.offsets[l + 1]] = du.ravel()
+    return out
+
+
+def richardson(op, comp, b, tol=1e-10, maxiter=200):
+    """Algorithm 1: u <- u - P(A u - b) until ||du||_2 < tol * ||b||_2."""
+    u = np.zeros_like(b)
+    bn = np.linalg.norm(b)
+    for k in range(maxiter):
+        du = ct_precondition(op, comp, op.apply(u) - b)
+        u = u - du
+        if np.linalg.norm(du) < tol * bn:
+            return u, k + 1
+    return u, maxiter
+
+
+class StripSolver:
+    """Implicit time stepping over strips (Sect. 2) with FGMRES + CT."""
+
+    def __init__(self, prob, tol=1e-10, inner_tol=1e-12, restart=30, maxiter=500):
+        self.prob = prob
+        self.op = SparseGridOperator(prob)
+        self.comp = ComponentSolver(self.op, tol=inner_tol)
+        self.tol, self.restart, self.maxiter = tol, restart, maxiter
+        R = self.op.R
+        self.e_start = eta_at(prob.r, 0.0)             # eta_s(t_{j-1}^+)
+        self.e_end = eta_at(prob.r, 1.0)               # eta_s(t_j^-)
+        self.outer_its = []
+
+    def initial_mass_u0(self) -> np.ndarray:
+        """(u0, phi_{l,k}) on every grid: sum of products of load vectors."""
+        op = self.op
+        out = np.zeros(op.size // op.R)
+        off = 0
+        for (l1, l2) in op.grids:
+            n1, n2 = op.grid_shape(l1, l2)
+            blk = np.zeros((n1, n2))
+            for pr in self.prob.u0:
+                fx = op.fx.embed(l1).T @ assemble_load(op.hx.levels[op.L], pr.fx)
+                fv = op.fv.embed(l2).T @ assemble_load(op.hv.levels[op.L], pr.fv)
+                blk += pr.coef * np.outer(fx, fv)
+            out[off:off + n1 * n2] = blk.ravel()
+            off += n1 * n2
+        return out
+
+    def mass_spatial(self, U: np.ndarray) -> np.ndarray:
+        """M_sg U for a spatial sparse-grid vector (no time index)."""
+        op = self.op
+        u = np.zeros((U.size, op.R))
+        u[:, 0] = U
+        return op.apply_mass(u.ravel()).reshape(-1, op.R)[:, 0]
+
+    def rhs(self, MU: np.ndarray) -> np.ndarray:
+        return np.outer(MU, self.e_start).ravel()
+
+    def endpoint(self, u: np.ndarray) -> np.ndarray:
+        return u.reshape(-1, self.op.R) @ self.e_end
+
+    def solve_strip(self, b: np.ndarray, x0=None):
+        op = self.op
+        P = lambda v: ct_precondition(op, self.comp, v)
+        x, it, res, hist = fgmres(op.apply, b, P, x0=x0, tol=self.tol,
+                                  restart=self.restart, maxiter=self.maxiter)
+        self.outer_its.append(it)
+        return x, it, res
+
+    def run(self, n_strips=None):
+        """Returns the list of end values U^-_j (spatial sparse-grid vectors)."""
+        n = self.prob.n_strips if n_strips is None else n_strips
+        MU = self.initial_mass_u0()
+        ends = []
+        for j in range(n):
+            u, it, res = self.solve_strip(self.rhs(MU))
+            U = self.endpoint(u)
+            ends.append(U)
+            MU = self.mass_spatial(U)
+        return ends
+
+
+# ----------------------------------------------------------------------------
+# unique representation and errors
+# ----------------------------------------------------------------------------
+
+def injection(hier, lc: int, lf: int) -> sp.csr_matrix:
+    """Rows: level-lc vertices; picks the coinciding level-lf vertex (lf >= lc)."""
+    cf = hier.levels[lf].coords
+    cc = hier.levels[lc].coords
+    idx = {tuple(x.tolist()): i for i, x in enumerate(cf)}
+    cols = np.array([idx[tuple(x.tolist())] for x in cc])
+    return sp.csr_matrix((np.ones(cc.shape[0]), (np.arange(cc.shape[0]), cols)),
+                         shape=(cc.shape[0], cf.shape[0]))
+
+
+def _transfer(hier, l_to: int, l_from: int) -> sp.csr_matrix:
+    if l_from <= l_to:
+        return hier.embed(l_to, l_from)
+    return injection(hier, l_to, l_from)
+
+
+def nodal_values(op: SparseGridOperator, U: np.ndarray, R: int = 1) -> np.ndarray:
+    """Values of the sparse-grid function at the nodes of every component grid."""
+    out = np.zeros(U.size)
+    off = [0]
+    for (a, b) in op.shape:
+        off.append(off[-1] + a * b * R)
+    for i, (l1, l2) in enumerate(op.grids):
+        n1, n2 = op.shape[i]
+        acc = np.zeros((n1, n2, R))
+        for j, (m1, m2) in enumerate(op.grids):
+            u = U[off[j]:off[j + 1]].reshape(op.shape[j] + (R,))
+            acc += op.right(_transfer(op.hv, l2, m2), op.left(_transfer(op.hx, l1, m1), u))
+        out[off[i]:off[i + 1]] = acc.ravel()
+    return out
+
+
+def full_grid_values(op: SparseGridOperator, U: np.ndarray) -> np.ndarray:
+    """The sparse-grid function (spatial) on the finest full grid (L, L)."""
+    L = op.L
+    acc = np.zeros((op.hx.levels[L].n, op.hv.levels[L].n, 1))
+    off = 0
+    for i, (l1, l2) in enumerate(op.grids):
+        n1, n2 = op.shape[i]
+        u = U[off:off + n1 * n2].reshape(n1, n2, 1)
+        off += n1 * n2
+        acc += op.right(op.hv.embed(L, l2), op.left(op.hx.embed(L, l1), u))
+    return acc[:, :, 0]

@@ -1,0 +1,189 @@
+"""Seeded synthetic workloads shared by the oracle, the tests and the benchmark.
+
+This module holds only *inputs*: coarse simplicial meshes, the coefficient
+functions of the transport problem (beta, sigma, u0) and seeded random
+coefficient vectors.  It contains none of the method's arithmetic (no
+refinement, no assembly, no operator, no solver); the oracle and the CUDA
+library each implement those on their own.
+
+Problem statement (Sect. 1, Eqs. 1-2): d_t u + beta . grad u + sigma u = f on
+(0,T) x Omega_x x Omega_v with inflow data g and initial data u0.  Coefficients
+are given in the tensor-product form of Sect. 4.2: every one of the 2d
+components of beta is a single product coef * fx(x) * fv(v); sigma likewise.
+A ``None`` factor means the constant 1.
+
+All callables take an array of points of shape (npts, d) and return (npts,).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+Fn = Optional[Callable[[np.ndarray], np.ndarray]]
+
+
+@dataclass
+class CoarseMesh:
+    """A coarse simplicial mesh on a box domain.
+
+    coords: (nv, d) float64; cells: (nc, d+1) int32, vertex indices.
+    lo/hi: box bounds per axis.  periodic: per-axis periodicity flag.
+    """
+    coords: np.ndarray
+    cells: np.ndarray
+    lo: Tuple[float, ...]
+    hi: Tuple[float, ...]
+    periodic: Tuple[bool, ...]
+
+    @property
+    def dim(self) -> int:
+        return self.coords.shape[1]
+
+
+@dataclass
+class Product:
+    """coef * fx(x) * fv(v); ``None`` factors are the constant 1."""
+    coef: float
+    fx: Fn = None
+    fv: Fn = None
+
+
+@dataclass
+class Problem:
+    """One transport problem on a product phase space (Sect. 1-2)."""
+    name: str
+    d: int
+    mesh_x: CoarseMesh
+    mesh_v: CoarseMesh
+    L: int                      # sparse level, 0-based: grids (l, L-l), l = 0..L
+    r: int                      # time-DG degree (1)
+    dt: float
+    delta: float                # streamline-diffusion parameter
+    n_strips: int
+    beta: List[Product]         # 2d components: x-components then v-components
+    sigma: Product
+    u0: List[Product]           # sum of separable products
+    exact: Optional[Callable[[float, np.ndarray, np.ndarray], np.ndarray]] = None
+
+
+# ----------------------------------------------------------------------------
+# coarse meshes (input data: the vertex/cell lists a user would hand over)
+# ----------------------------------------------------------------------------
+
+def interval_mesh(a: float, b: float, n_cells: int = 4, periodic: bool = False) -> CoarseMesh:
+    x = np.linspace(a, b, n_cells + 1)
+    cells = np.array([[i, i + 1] for i in range(n_cells)], dtype=np.int32)
+    return CoarseMesh(x[:, None].copy(), cells, (a,), (b,), (periodic,))
+
+
+def square_mesh(a: float, b: float, n_sq: int = 2, periodic: bool = False) -> CoarseMesh:
+    """n_sq x n_sq squares, each cut along the same diagonal (lower-left to
+    upper-right); 2 n_sq^2 triangles.  n_sq = 2 gives the 8-triangle mesh."""
+    t = np.linspace(a, b, n_sq + 1)
+    X, Y = np.meshgrid(t, t, indexing="xy")
+    coords = np.stack([X.ravel(), Y.ravel()], axis=1)
+    vid = lambda i, j: j * (n_sq + 1) + i
+    cells = []
+    for j in range(n_sq):
+        for i in range(n_sq):
+            p00, p10, p01, p11 = vid(i, j), vid(i + 1, j), vid(i, j + 1), vid(i + 1, j + 1)
+            cells.append([p00, p10, p11])
+            cells.append([p00, p11, p01])
+    return CoarseMesh(coords, np.array(cells, dtype=np.int32), (a, a), (b, b), (periodic, periodic))
+
+
+# ----------------------------------------------------------------------------
+# problems
+# ----------------------------------------------------------------------------
+
+def _gauss(c: float, var2: float):
+    # exp(-(s - c)^2 / var2) along axis 0
+    return lambda p: np.exp(-((p[:, 0] - c) ** 2) / var2)
+
+
+def free_streaming_1d(L: int = 6, n_strips: int = 16, dt: float = 1.0 / 32.0) -> Problem:
+    """d=1 free streaming: x in [0,1], v in [-1,1], beta = (v, 0), sigma = 0,
+    f = 0, g = 0, u0 = exp(-(x-0.5)^2/0.01) exp(-v^2/0.1).  delta = finest
+    edge length of the two meshes (the smaller one).  Exact solution
+    u0(x - v t, v) where x - v t stays in [0,1] (inflow g = 0), else 0."""
+    mx = interval_mesh(0.0, 1.0, 4)
+    mv = interval_mesh(-1.0, 1.0, 4)
+    hx = 1.0 / (4 * 2 ** L)
+    hv = 2.0 / (4 * 2 ** L)
+    ux = _gauss(0.5, 0.01)
+    uv = lambda p: np.exp(-(p[:, 0] ** 2) / 0.1)
+
+    def exact(t, x, v):
+        xs = x - v * t
+        inside = (xs >= 0.0) & (xs <= 1.0)
+        return np.where(inside, np.exp(-((xs - 0.5) ** 2) / 0.01) * np.exp(-(v ** 2) / 0.1), 0.0)
+
+    return Problem(
+        name=f"free_streaming_1d_L{L}", d=1, mesh_x=mx, mesh_v=mv, L=L, r=1, dt=dt,
+        delta=min(hx, hv), n_strips=n_strips,
+        beta=[Product(1.0, None, lambda p: p[:, 0]), Product(0.0)],
+        sigma=Product(0.0), u0=[Product(1.0, ux, uv)], exact=exact)
+
+
+def transport_2d(L: int = 9, sigma: float = 0.1, dt: float = 1.0 / 64.0, n_strips: int = 16) -> Problem:
+    """d=2: Omega_x = [0,1]^2, Omega_v = [-1,1]^2, 8-triangle coarse meshes,
+    beta = (v1, v2, E1(x), E2(x)) with E = 0.5 (sin 2 pi x2, cos 2 pi x1),
+    constant sigma, Gaussian u0, f = 0, g = 0.  delta = finest edge leg."""
+    mx = square_mesh(0.0, 1.0, 2)
+    mv = square_mesh(-1.0, 1.0, 2)
+    hx = 1.0 / 2 ** (L + 1)
+    hv = 2.0 / 2 ** (L + 1)
+    beta = [
+        Product(1.0, None, lambda p: p[:, 0]),
+        Product(1.0, None, lambda p: p[:, 1]),
+        Product(0.5, lambda p: np.sin(2 * np.pi * p[:, 1]), None),
+        Product(0.5, lambda p: np.cos(2 * np.pi * p[:, 0]), None),
+    ]
+    ux = lambda p: np.exp(-((p[:, 0] - 0.5) ** 2 + (p[:, 1] - 0.5) ** 2) / 0.01)
+    uv = lambda p: np.exp(-(p[:, 0] ** 2 + p[:, 1] ** 2) / 0.1)
+    return Problem(
+        name=f"transport_2d_L{L}", d=2, mesh_x=mx, mesh_v=mv, L=L, r=1, dt=dt,
+        delta=min(hx, hv), n_strips=n_strips, beta=beta,
+        sigma=Product(sigma) if sigma != 0.0 else Product(0.0),
+        u0=[Product(1.0, ux, uv)])
+
+
+def periodic_advection_1d(L: int, r: int = 1) -> Problem:
+    """Sect. 5.1 (Eq. 25) with d = 1: beta = (1, 1) on the periodic unit
+    square, u0 = sin(2 pi (x + v)); coarse meshes of 4 cells; 2^(L_paper+1)
+    strips over one period T = 1/2; delta = finest edge length.  Here L is
+    0-based (L_paper = L + 1)."""
+    mx = interval_mesh(0.0, 1.0, 4, periodic=True)
+    mv = interval_mesh(0.0, 1.0, 4, periodic=True)
+    Lp = L + 1
+    n_strips = 2 ** (Lp + 1)
+    T = 0.5
+    h = 1.0 / (4 * 2 ** L)
+    # sin(2 pi (x + v)) = sin(2 pi x) cos(2 pi v) + cos(2 pi x) sin(2 pi v)
+    u0 = [Product(1.0, lambda p: np.sin(2 * np.pi * p[:, 0]), lambda p: np.cos(2 * np.pi * p[:, 0])),
+          Product(1.0, lambda p: np.cos(2 * np.pi * p[:, 0]), lambda p: np.sin(2 * np.pi * p[:, 0]))]
+
+    def exact(t, x, v):
+        return np.sin(2 * np.pi * (x + v - 2 * t))
+
+    return Problem(name=f"periodic_advection_1d_L{L}", d=1, mesh_x=mx, mesh_v=mv, L=L, r=r,
+                   dt=T / n_strips, delta=h, n_strips=n_strips,
+                   beta=[Product(1.0), Product(1.0)], sigma=Product(0.0), u0=u0, exact=exact)
+
+
+# ----------------------------------------------------------------------------
+# seeded random inputs
+# ----------------------------------------------------------------------------
+
+def uniform_vector(n: int, seed: int) -> np.ndarray:
+    """U[-1, 1] float64 values, seeded (PCG64)."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, size=n)
+
+
+def sample_indices(n: int, k: int, seed: int) -> np.ndarray:
+    """k distinct sorted indices in [0, n), seeded."""
+    rng = np.random.default_rng(seed)
+    k = min(k, n)
+    return np.sort(rng.choice(n, size=k, replace=False))
