@@ -1,0 +1,296 @@
+"""Benchmark: sparse-grid SD-Galerkin operator apply (GDoF/s) and strip solves.
+
+Workload (default): the 4D transport problem, d = 2, Omega_x = [0,1]^2,
+Omega_v = [-1,1]^2, 8-triangle coarse meshes, sparse level L = 9 (grids
+(l, 9-l)), time-DG degree 1, beta = (v, E(x)), sigma = 0.1: 61,590,186 spatial
+coefficients, 123,180,372 DoF per strip vector (FP32: 493 MB, FP64: 985 MB,
+both larger than L2).  A step is one application of the strip operator
+A^(delta) to a seeded U[-1,1] vector, resident in HBM.
+
+Reported: value = GDoF/s of the mixed-precision (FP32) apply; the FP64 apply,
+the end-to-end apply through the C ABI with host buffers, per-kernel roofline,
+strip solves at 1e-8 (mixed vs FP64), the oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import sgdg_workloads as W  # noqa: E402
+
+METRIC = "operator-apply GDoF/s; s/time-strip at 1e-8 rel. residual, mixed vs FP64"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(steps: int = 4, L: int = 5):
+    """The oracle's blockwise apply (Sect. 4.2) on the host cores, as it stands,
+    on a bounded sample of the same workload family (d = 2, level L)."""
+    from oracle.operator import SparseGridOperator
+    prob = W.transport_2d(L=L, sigma=0.1)
+    op = SparseGridOperator(prob)
+    u = W.uniform_vector(op.size, seed=7)
+    op.apply(u)                                     # warm-up: builds the projected factors
+    t = time.perf_counter()
+    for _ in range(steps):
+        op.apply(u)
+    dt = (time.perf_counter() - t) / steps
+    return {"value": op.size / dt / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"blockwise FP64 apply, d=2 L={L} ({op.size} DoF), {steps} applies after 1 warm-up; "
+                      f"numpy/scipy single thread"}, dt, op.size
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    W_, K = args.warmup, args.steps
+    from oracle.operator import SparseGridOperator
+    L = args.ref_L
+    prob = W.transport_2d(L=L, sigma=0.1)
+    op = SparseGridOperator(prob)
+    u = W.uniform_vector(op.size, seed=7)
+    for _ in range(max(1, W_)):
+        op.apply(u)
+    t = time.perf_counter()
+    for _ in range(K):
+        op.apply(u)
+    dt = (time.perf_counter() - t) / K
+    val = op.size / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GDoF/s", "n_gpus": world,
+            "steps": K, "warmup": W_, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"transport_2d d=2 L={L} sigma=0.1 operator apply (oracle sample)",
+                       "dof_per_step": op.size},
+            "cpu_baseline": {"value": val, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                             "sample": f"blockwise FP64 apply, d=2 L={L} ({op.size} DoF) per step"},
+            "e2e": {"value": val, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=9)
+    ap.add_argument("--ref-L", type=int, default=5)
+    ap.add_argument("--strip-L", type=int, default=7, help="level of the strip-solve timing (-1: skip)")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2204_05988_gb300 as P
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    prob = W.transport_2d(L=args.L, sigma=0.1)
+    t0 = time.perf_counter()
+    s = P.Solver(prob, device=local)
+    setup_s = time.perf_counter() - t0
+    n = s.n_coeffs
+    u64 = torch.tensor(W.uniform_vector(n, seed=1 + rank), dtype=torch.float64, device="cuda")
+    u32 = u64.float()
+    y32 = torch.empty_like(u32)
+    y64 = torch.empty_like(u64)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, K, Wm):
+        for _ in range(Wm):
+            fn()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            fn()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / K
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # ---- FP32 apply (headline), clocks sampled during the timed region
+    for _ in range(args.warmup):
+        s.apply_operator(u32, y32, P.SGDG_MIXED_FP32, stream)
+    barrier()
+    l0 = s.launch_count()
+    with Clocks(local) as clk:
+        ms32 = timed(lambda: s.apply_operator(u32, y32, P.SGDG_MIXED_FP32, stream), args.steps, 0)
+    launches = (s.launch_count() - l0) // 1
+    clocks = clk.summary()
+    value = world * n / (ms32 * 1e-3) / 1e9
+
+    # ---- FP64 apply
+    ms64 = timed(lambda: s.apply_operator(u64, y64, P.SGDG_FP64, stream), max(2, args.steps // 2), 1)
+
+    # ---- per-kernel roofline (one profiled apply per precision)
+    peak, peak_kind = _peaks()
+    roof = {}
+    for name, (u_, y_, pr) in {"f32": (u32, y32, P.SGDG_MIXED_FP32), "f64": (u64, y64, P.SGDG_FP64)}.items():
+        s.profile(True)
+        s.apply_operator(u_, y_, pr, stream)
+        st = s.kernel_stats()
+        s.profile(False)
+        roof[name] = st
+    st = roof["f32"]
+    dom = max(st, key=lambda k: st[k]["ms"])
+    ach = st[dom]["bytes"] / (st[dom]["ms"] * 1e-3) / 1e9
+    tot_ms = sum(v["ms"] for v in st.values())
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+                "share_of_apply": st[dom]["ms"] / tot_ms,
+                "per_kind": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                                 "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                             for k, v in st.items()},
+                "f64_per_kind": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                                     "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                                 for k, v in roof["f64"].items()}}
+
+    # ---- end to end through the C ABI with pinned host buffers (FP64 in/out, FP32 apply)
+    hu = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hu.copy_(u64.cpu())
+    hy = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    for _ in range(1):
+        s.apply_operator_host(hu, hy, P.SGDG_MIXED_FP32)
+    barrier()
+    te = time.perf_counter()
+    ke = max(2, args.steps // 2)
+    for _ in range(ke):
+        s.apply_operator_host(hu, hy, P.SGDG_MIXED_FP32)
+    barrier()
+    e2e_s = (time.perf_counter() - te) / ke
+    e2e = {"value": world * n / e2e_s / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * n,
+           "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_s * 1e3}
+    s.close()
+    del u64, u32, y32, y64
+    torch.cuda.empty_cache()
+
+    # ---- strip solves at 1e-8 (mixed vs FP64)
+    strip = None
+    if args.strip_L >= 0:
+        strip = {"workload": f"transport_2d d=2 L={args.strip_L} sigma=0.1 dt=1/64, strips 1-2, rtol 1e-8"}
+        for nm, pr in (("mixed", P.SGDG_MIXED_FP32), ("fp64", P.SGDG_FP64)):
+            ps = W.transport_2d(L=args.strip_L, sigma=0.1)
+            sv = P.Solver(ps, precision=pr, rtol=1e-8, restart=30, inner_its=12, inner_rtol=1e-2, device=local)
+            sv.set_initial()
+            sts = []
+            for _ in range(2):
+                r = sv.advance_strip(check=False)
+                sts.append({"s": round(r.seconds, 4), "outer": r.outer_its, "inner": r.inner_its_total,
+                            "applies": r.applies, "rel_res": r.rel_residual, "status": r.status})
+            strip[nm] = {"s_per_strip": sts[-1]["s"], "strips": sts, "dof": sv.n_coeffs}
+            sv.close()
+        strip["speedup_mixed_vs_fp64"] = strip["fp64"]["s_per_strip"] / strip["mixed"]["s_per_strip"]
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu:
+            cpu, _, _ = cpu_baseline()
+        line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"transport_2d d=2 L={args.L} sigma=0.1 operator apply A^(delta) u",
+                           "dof_per_step": n, "terms": s.info.n_terms, "l2": "inputs larger than L2 (493 MB f32)",
+                           "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2)},
+                "fp64_apply": {"value": world * n / (ms64 * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms64},
+                "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
+                "strip": strip, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * sgdg.h - C ABI of the GB300 sparse-grid time-DG streamline-diffusion
+ * transport library (sm_103a CUDA + C++).
+ *
+ * Problem (Sect. 1, Eqs. 1-2): d_t u + beta . grad u + sigma u = f on
+ * (0,T) x Omega, Omega = Omega_x x Omega_v (both d-dimensional, d = 1, 2),
+ * u(0) = u0, inflow u = g on Gamma^- = {beta . n < 0}.  This library solves
+ * f = 0, g = 0.
+ *
+ * Discretisation (Sect. 2): sparse grid V_L = sum_{l=0..L} V^(1)_l (x) V^(2)_{L-l}
+ * of nested P1 spaces (levels 0-based: the paper's level is L+1), time-DG of
+ * degree r = 1 on strips, streamline diffusion with parameter delta; the strip
+ * problem a_j(U_j, w) = b_j(w) of Eq. 5 is solved strip by strip.
+ *
+ * Storage (Sect. 4.1): a sparse-grid coefficient vector is the concatenation
+ * over grids l = 0..L of arrays u_l[k1][k2][s] (row-major, s fastest), k1 over
+ * the vertices of level l of Omega_x, k2 over level L-l of Omega_v, s = 0, 1
+ * the Legendre time basis eta_s(t) = P_s(2 (t - t_{j-1}) / dt - 1).  Vertices
+ * of every level are ordered lexicographically by coordinates (last axis
+ * slowest).  A spatial vector (no time index) has the same layout without s.
+ * These coefficients belong to a spanning set: they are not unique
+ * (Sect. 4.1); operator outputs are unique (rows are test functions).
+ *
+ * Conventions:
+ *  - Every call returns an sgdg_status; on error, outputs are untouched and
+ *    sgdg_last_error() describes the failure.
+ *  - The caller owns every array it passes.  Mesh arrays and callbacks are
+ *    read during sgdg_create only.  The library owns all memory it allocates
+ *    (device and host) and frees it in sgdg_destroy.
+ *  - Device pointers passed in (u, y, r, z) must be allocations on the
+ *    handle's device, 16-byte aligned, and are not retained after the call.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream); calls taking a
+ *    stream enqueue work on it and may synchronise it to read Krylov scalars.
+ *  - A handle is thread-compatible, not thread-safe.
+ */
+#ifndef SGDG_H
+#define SGDG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SGDG_OK = 0,
+  SGDG_EINVAL = 1,     /* bad argument or unsupported configuration */
+  SGDG_ENOMEM = 2,     /* device or host allocation failed / over budget */
+  SGDG_ECUDA = 3,      /* a CUDA call failed */
+  SGDG_ENOCONV = 4,    /* Krylov solve hit its iteration cap (stats filled) */
+  SGDG_ENAN = 5,       /* NaN or Inf met in a residual */
+  SGDG_ETIMEOUT = 6,   /* a bounded device wait gave up */
+  SGDG_EIO = 7
+} sgdg_status;
+
+typedef enum {
+  SGDG_FP64 = 0,        /* every apply, transfer and Krylov vector in FP64 */
+  SGDG_MIXED_FP32 = 1   /* FP32 apply / transfers / component solves, FP64
+                           Krylov scalars and FP64 outer residual
+                           (iterative refinement) */
+} sgdg_precision;
+
+/* A coarse simplicial mesh of an axis-aligned box (one of Omega_x, Omega_v).
+ * coords: [n_vertices][dim]; cells: [n_cells][dim+1] vertex indices.
+ * lo/hi: box bounds per axis; periodic: per-axis flag (0/1).  Uniform
+ * refinement (1D bisection, 2D red refinement) builds the levels. */
+typedef struct {
+  int dim;
+  int n_vertices;
+  const double* coords;
+  int n_cells;
+  const int* cells;
+  const double* lo;
+  const double* hi;
+  const int* periodic;
+} sgdg_mesh;
+
+/* Batched coefficient callback: out[i] = f(pts[i*dim .. i*dim+dim-1]),
+ * i < npts.  Called on the host during sgdg_create / sgdg_set_initial. */
+typedef void (*sgdg_fn)(int npts, const double* pts, double* out, void* user);
+
+/* coef * fx(x) * fv(v); a NULL function is the constant 1 (Sect. 4.2). */
+typedef struct {
+  double coef;
+  sgdg_fn fx;
+  void* ux;
+  sgdg_fn fv;
+  void* uv;
+} sgdg_product;
+
+/* beta_p = beta[p] for p < 2d (x-components first), sigma, and
+ * u0 = sum_k u0[k].  Every component of beta is ONE product (the tensor
+ * structure of Sect. 4.2); inflow splitting (Sect. 5.2) assumes the sign of
+ * each factor changes only on mesh lines. */
+typedef struct {
+  sgdg_product beta[4];
+  sgdg_product sigma;
+  int n_u0;
+  const sgdg_product* u0;
+} sgdg_coeffs;
+
+typedef struct {
+  sgdg_mesh mesh_x, mesh_v;
+  int level_L;          /* sparse level, 0-based, 0..11 */
+  int time_degree;      /* r; must be 1 */
+  double dt;            /* strip length */
+  double delta;         /* streamline-diffusion parameter (> 0) */
+  sgdg_precision precision;
+  double rtol;          /* outer stop: ||b - A u||_2 <= rtol ||b||_2 */
+  int max_outer;        /* outer FGMRES iteration cap */
+  int restart;          /* outer FGMRES restart length (<= 64) */
+  int inner_its;        /* GMRES iterations per component solve (<= 64) */
+  double inner_rtol;    /* early stop of a component solve */
+  int cheb_steps;       /* Chebyshev-Jacobi steps per mass inverse */
+  int device;           /* CUDA device ordinal */
+} sgdg_config;
+
+typedef struct {
+  int L, d, R;                 /* R = r + 1 time coefficients */
+  int n_grids;                 /* L + 1 */
+  long long n_spatial;         /* sum_l n1(l) n2(L-l) */
+  long long n_coeffs;          /* R * n_spatial: length of a strip vector */
+  int n_terms;                 /* Kronecker terms after merging */
+  int n_x_factors, n_v_factors;
+  double device_bytes;         /* device memory held by the handle */
+} sgdg_info;
+
+typedef struct {
+  int outer_its;
+  int inner_its_total;
+  int applies;                 /* full sparse-grid operator applies */
+  double rel_residual;         /* true ||b - A u|| / ||b|| (FP64) */
+  double seconds;
+  int status;
+} sgdg_strip_stats;
+
+/* Build the level hierarchies, assemble the finest-level factor matrices in
+ * FP64 (Sect. 4.2), project them to every level with the embeddings
+ * (X_l = E^T X_{l+1} E), compile the Kronecker term table of the block
+ * formula (Sect. 4.2; delta on K~ per the weak form of Sect. 2), upload
+ * everything to the device.  EINVAL for unsupported input, ENOMEM, ECUDA. */
+sgdg_status sgdg_create(const sgdg_config* cfg, const sgdg_coeffs* coeffs, void** out_handle);
+void sgdg_destroy(void* h);
+const char* sgdg_last_error(const void* h);
+sgdg_status sgdg_get_info(const void* h, sgdg_info* out);
+/* Shape and element offset (in doubles/floats of a strip vector, i.e. with
+ * the time index) of grid l = (l, L-l). */
+sgdg_status sgdg_grid_shape(const void* h, int l, int* n1, int* n2, long long* offset);
+
+/* y = A^(delta) u: the strip operator of Eq. 5 on the sparse grid,
+ * [A u]_l = sum_l' A_{l,l'} u_l' (Sect. 4.2), evaluated by a linear-cost
+ * sweep over the grids.  u, y: device arrays of n_coeffs elements of type
+ * double (SGDG_FP64) or float (SGDG_MIXED_FP32); y is overwritten; u and y
+ * must not overlap. */
+sgdg_status sgdg_apply_operator(void* h, const void* u, void* y, int precision, void* stream);
+/* Same operator with host arrays (double): copies u to the device, applies
+ * in the given precision, copies y back.  Synchronous. */
+sgdg_status sgdg_apply_operator_host(void* h, const double* u, double* y, int precision);
+/* y = (Id_t (x) M_sg) u, the sparse-grid mass matrix on both time slots. */
+sgdg_status sgdg_apply_mass(void* h, const void* u, void* y, int precision, void* stream);
+/* y = A_{l,l} u on one anisotropic full grid (l1, l2) with l1 + l2 in {L-1, L}
+ * (the component systems of Eq. 22); arrays [n1][n2][2] on the device. */
+sgdg_status sgdg_apply_diag(void* h, int l1, int l2, const void* u, void* y, int precision, void* stream);
+/* z = P_CT(r): Algorithm 1's preconditioner step (component solves with the
+ * configured inner iterations, restriction of the residual, combination).
+ * r, z: device arrays of n_coeffs doubles. */
+sgdg_status sgdg_ct_precondition(void* h, const double* r, double* z, void* stream);
+
+/* U^-_0 := u0 (the first right-hand side uses (u0, w^+) directly). */
+sgdg_status sgdg_set_initial(void* h);
+/* Solve one strip (Eq. 5) with right-preconditioned FGMRES + CT (Algorithm 1
+ * as preconditioner), starting from u = 0; advance U^-_j.  ENOCONV when
+ * max_outer is reached (stats still filled). */
+sgdg_status sgdg_advance_strip(void* h, void* stream, sgdg_strip_stats* stats);
+/* Copy out the last strip solution u (n_coeffs doubles) or the end value
+ * U^-_j (n_spatial doubles); dst is device (on_device=1) or host memory. */
+sgdg_status sgdg_get_solution(const void* h, double* dst, int on_device);
+sgdg_status sgdg_get_end_value(const void* h, double* dst, int on_device);
+/* Unique representation of a spatial sparse-grid function: its values at the
+ * nodes of every component grid (prolongation from coarser grids, injection
+ * from finer ones).  u, out: device arrays of n_spatial doubles. */
+sgdg_status sgdg_eval_nodal(void* h, const double* u, double* out, void* stream);
+
+/* Kernel accounting (measurement; no counterpart in the paper).  Kinds:
+ * 0 = factor SpMM along dim 1 ("left"), 1 = factor SpMM along dim 2
+ * ("right"), 2 / 3 = transfers (prolongation / restriction) along dim 1 / 2. */
+typedef struct {
+  long long launches;
+  double ms;        /* summed CUDA-event duration of the launches */
+  double bytes;     /* summed algorithmic bytes: inputs + outputs (read and
+                       written when accumulating) + CSR pattern and values */
+} sgdg_kernel_stat;
+/* enable != 0: bracket every subsequent SpMM launch with CUDA events and
+ * record its algorithmic bytes (clears earlier records); 0: stop. */
+sgdg_status sgdg_profile(void* h, int enable);
+/* Synchronise the device, fill out[0..3] (one per kind) and clear the records. */
+sgdg_status sgdg_kernel_stats(void* h, sgdg_kernel_stat* out, int n_kinds);
+/* Number of SpMM kernels this handle has launched so far. */
+long long sgdg_launch_count(const void* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGDG_H */

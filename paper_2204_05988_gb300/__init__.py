@@ -1,0 +1,289 @@
+"""Python binding of libsgdg: the GB300 sparse-grid time-DG streamline-diffusion
+transport library (C ABI in include/sgdg.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams.  The library must
+have been built (``paper_2204_05988_gb300.build.build()``); importing the
+binding without it raises - there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional
+
+from . import build  # noqa: F401  (in-tree build step)
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsgdg.so")
+
+SGDG_FP64 = 0
+SGDG_MIXED_FP32 = 1
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENAN", 6: "ETIMEOUT", 7: "EIO"}
+
+FN = C.CFUNCTYPE(None, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
+
+
+class Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_vertices", C.c_int), ("coords", C.POINTER(C.c_double)),
+                ("n_cells", C.c_int), ("cells", C.POINTER(C.c_int)), ("lo", C.POINTER(C.c_double)),
+                ("hi", C.POINTER(C.c_double)), ("periodic", C.POINTER(C.c_int))]
+
+
+class Product(C.Structure):
+    _fields_ = [("coef", C.c_double), ("fx", FN), ("ux", C.c_void_p), ("fv", FN), ("uv", C.c_void_p)]
+
+
+class Coeffs(C.Structure):
+    _fields_ = [("beta", Product * 4), ("sigma", Product), ("n_u0", C.c_int), ("u0", C.POINTER(Product))]
+
+
+class Config(C.Structure):
+    _fields_ = [("mesh_x", Mesh), ("mesh_v", Mesh), ("level_L", C.c_int), ("time_degree", C.c_int),
+                ("dt", C.c_double), ("delta", C.c_double), ("precision", C.c_int), ("rtol", C.c_double),
+                ("max_outer", C.c_int), ("restart", C.c_int), ("inner_its", C.c_int),
+                ("inner_rtol", C.c_double), ("cheb_steps", C.c_int), ("device", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("L", C.c_int), ("d", C.c_int), ("R", C.c_int), ("n_grids", C.c_int),
+                ("n_spatial", C.c_longlong), ("n_coeffs", C.c_longlong), ("n_terms", C.c_int),
+                ("n_x_factors", C.c_int), ("n_v_factors", C.c_int), ("device_bytes", C.c_double)]
+
+
+class StripStats(C.Structure):
+    _fields_ = [("outer_its", C.c_int), ("inner_its_total", C.c_int), ("applies", C.c_int),
+                ("rel_residual", C.c_double), ("seconds", C.c_double), ("status", C.c_int)]
+
+
+EXPORTS = {
+    "sgdg_create": (C.c_int, [C.POINTER(Config), C.POINTER(Coeffs), C.POINTER(C.c_void_p)]),
+    "sgdg_destroy": (None, [C.c_void_p]),
+    "sgdg_last_error": (C.c_char_p, [C.c_void_p]),
+    "sgdg_get_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
+    "sgdg_grid_shape": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_longlong)]),
+    "sgdg_apply_operator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "sgdg_apply_operator_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "sgdg_apply_mass": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "sgdg_apply_diag": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "sgdg_ct_precondition": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sgdg_set_initial": (C.c_int, [C.c_void_p]),
+    "sgdg_advance_strip": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(StripStats)]),
+    "sgdg_get_solution": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "sgdg_get_end_value": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "sgdg_eval_nodal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sgdg_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "sgdg_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "sgdg_launch_count": (C.c_longlong, [C.c_void_p]),
+}
+
+KERNEL_KINDS = ("spmm_left", "spmm_right", "transfer_left", "transfer_right")
+
+
+class KernelStat(C.Structure):
+    _fields_ = [("launches", C.c_longlong), ("ms", C.c_double), ("bytes", C.c_double)]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load libsgdg.so and declare its entry points; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsgdg.so not built ({path}); run paper_2204_05988_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class SgdgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sgdg {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return int(t)
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Solver:
+    """One transport problem on the GPU (a handle of the C library).
+
+    ``problem`` is an ``sgdg_workloads.Problem`` (coarse meshes, beta, sigma,
+    u0 as products of callables); callables are evaluated by the library
+    during construction only.
+    """
+
+    def __init__(self, problem, precision: int = SGDG_FP64, rtol: float = 1e-10, max_outer: int = 200,
+                 restart: int = 30, inner_its: int = 20, inner_rtol: float = 1e-3, cheb_steps: int = 6,
+                 device: int = 0):
+        self.lib = load_library()
+        self.problem = problem
+        self._keep: List = []
+        self._cb_error: List[str] = []
+        cfg = Config()
+        cfg.mesh_x = self._mesh(problem.mesh_x)
+        cfg.mesh_v = self._mesh(problem.mesh_v)
+        cfg.level_L = problem.L
+        cfg.time_degree = problem.r
+        cfg.dt = problem.dt
+        cfg.delta = problem.delta
+        cfg.precision = precision
+        cfg.rtol = rtol
+        cfg.max_outer = max_outer
+        cfg.restart = restart
+        cfg.inner_its = inner_its
+        cfg.inner_rtol = inner_rtol
+        cfg.cheb_steps = cheb_steps
+        cfg.device = device
+        co = Coeffs()
+        d = problem.d
+        for p in range(4):
+            if p < 2 * d:
+                co.beta[p] = self._product(problem.beta[p], d)
+            else:
+                co.beta[p] = Product(0.0, FN(), None, FN(), None)
+        co.sigma = self._product(problem.sigma, d)
+        u0 = (Product * max(1, len(problem.u0)))()
+        for k, pr in enumerate(problem.u0):
+            u0[k] = self._product(pr, d)
+        co.n_u0 = len(problem.u0)
+        co.u0 = u0
+        self._keep += [cfg, co, u0]
+        h = C.c_void_p()
+        st = self.lib.sgdg_create(C.byref(cfg), C.byref(co), C.byref(h))
+        if self._cb_error:
+            if st == 0:
+                self.lib.sgdg_destroy(h)
+            raise RuntimeError("coefficient callback failed: " + self._cb_error[0])
+        if st != 0:
+            raise SgdgError(st, self.lib.sgdg_last_error(None).decode())
+        self.h = h
+        self.info = Info()
+        self._check(self.lib.sgdg_get_info(self.h, C.byref(self.info)))
+        self.shapes, self.offsets = [], []
+        for l in range(self.info.n_grids):
+            n1, n2, off = C.c_int(), C.c_int(), C.c_longlong()
+            self._check(self.lib.sgdg_grid_shape(self.h, l, C.byref(n1), C.byref(n2), C.byref(off)))
+            self.shapes.append((n1.value, n2.value))
+            self.offsets.append(off.value)
+        self.n_coeffs = self.info.n_coeffs
+        self.n_spatial = self.info.n_spatial
+
+    # -- marshalling helpers
+    def _mesh(self, m) -> Mesh:
+        coords = np.ascontiguousarray(m.coords, dtype=np.float64)
+        cells = np.ascontiguousarray(m.cells, dtype=np.int32)
+        lo = np.ascontiguousarray(m.lo, dtype=np.float64)
+        hi = np.ascontiguousarray(m.hi, dtype=np.float64)
+        per = np.ascontiguousarray([int(p) for p in m.periodic], dtype=np.int32)
+        self._keep += [coords, cells, lo, hi, per]
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int)
+        return Mesh(m.dim, coords.shape[0], coords.ctypes.data_as(dp), cells.shape[0], cells.ctypes.data_as(ip),
+                    lo.ctypes.data_as(dp), hi.ctypes.data_as(dp), per.ctypes.data_as(ip))
+
+    def _fn(self, f, d):
+        if f is None:
+            return FN()
+        errs = self._cb_error
+
+        def cb(n, pts, out, user):
+            try:
+                p = np.ctypeslib.as_array(pts, shape=(n * d,)).reshape(n, d)
+                o = np.ctypeslib.as_array(out, shape=(n,))
+                o[:] = np.asarray(f(p), dtype=np.float64)
+            except Exception as e:  # report after sgdg_create returns
+                errs.append(repr(e))
+                np.ctypeslib.as_array(out, shape=(n,))[:] = np.nan
+        c = FN(cb)
+        self._keep.append(c)
+        return c
+
+    def _product(self, pr, d) -> Product:
+        return Product(float(pr.coef), self._fn(pr.fx, d), None, self._fn(pr.fv, d), None)
+
+    def _check(self, st):
+        if st != 0:
+            raise SgdgError(st, self.lib.sgdg_last_error(self.h).decode())
+
+    # -- entry points (device arrays: torch CUDA tensors or raw pointers)
+    def apply_operator(self, u, y, precision: int = SGDG_FP64, stream=None):
+        self._check(self.lib.sgdg_apply_operator(self.h, _ptr(u), _ptr(y), precision, _stream(stream)))
+
+    def apply_operator_host(self, u: np.ndarray, y: np.ndarray, precision: int = SGDG_FP64):
+        self._check(self.lib.sgdg_apply_operator_host(self.h, _ptr(u), _ptr(y), precision))
+
+    def apply_mass(self, u, y, precision: int = SGDG_FP64, stream=None):
+        self._check(self.lib.sgdg_apply_mass(self.h, _ptr(u), _ptr(y), precision, _stream(stream)))
+
+    def apply_diag(self, l1: int, l2: int, u, y, precision: int = SGDG_FP64, stream=None):
+        self._check(self.lib.sgdg_apply_diag(self.h, l1, l2, _ptr(u), _ptr(y), precision, _stream(stream)))
+
+    def ct_precondition(self, r, z, stream=None):
+        self._check(self.lib.sgdg_ct_precondition(self.h, _ptr(r), _ptr(z), _stream(stream)))
+
+    def set_initial(self):
+        self._check(self.lib.sgdg_set_initial(self.h))
+
+    def advance_strip(self, stream=None, check: bool = True) -> StripStats:
+        st = StripStats()
+        code = self.lib.sgdg_advance_strip(self.h, _stream(stream), C.byref(st))
+        if check:
+            self._check(code)
+        return st
+
+    def get_solution(self, dst, on_device: bool = True):
+        self._check(self.lib.sgdg_get_solution(self.h, _ptr(dst), int(on_device)))
+
+    def get_end_value(self, dst, on_device: bool = True):
+        self._check(self.lib.sgdg_get_end_value(self.h, _ptr(dst), int(on_device)))
+
+    def eval_nodal(self, u, out, stream=None):
+        self._check(self.lib.sgdg_eval_nodal(self.h, _ptr(u), _ptr(out), _stream(stream)))
+
+    def profile(self, enable: bool):
+        self._check(self.lib.sgdg_profile(self.h, int(enable)))
+
+    def kernel_stats(self):
+        arr = (KernelStat * 4)()
+        self._check(self.lib.sgdg_kernel_stats(self.h, arr, 4))
+        return {KERNEL_KINDS[k]: {"launches": arr[k].launches, "ms": arr[k].ms, "bytes": arr[k].bytes}
+                for k in range(4)}
+
+    def launch_count(self) -> int:
+        return int(self.lib.sgdg_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sgdg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

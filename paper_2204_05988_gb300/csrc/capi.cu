@@ -1,0 +1,483 @@
+// C ABI of the sgdg library: set-up (hierarchies, FP64 assembly, term table,
+// device upload) and the entry points declared in include/sgdg.h.
+#include <cstdio>
+#include <cstring>
+#include <map>
+
+#include "handle.h"
+
+namespace sgdg {
+
+static std::vector<void*>& registry(Handle* h) {
+  static std::map<Handle*, std::vector<void*>> reg;
+  return reg[h];
+}
+
+// Every device allocation of a handle goes through here and is released in
+// sgdg_destroy.
+cudaError_t dev_alloc(Handle& h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) {
+    h.device_bytes += bytes;
+    registry(&h).push_back(*p);
+  }
+  return e;
+}
+
+namespace {
+
+#define SG_CU(x)                                                              \
+  do {                                                                        \
+    cudaError_t e_ = (x);                                                     \
+    if (e_ != cudaSuccess) return {SGDG_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+#define SG_ST(x)                   \
+  do {                             \
+    Status s_ = (x);               \
+    if (s_.code) return s_;        \
+  } while (0)
+
+template <typename T>
+Status upload(Handle& h, T** dst, const T* src, size_t n) {
+  if (dev_alloc(h, (void**)dst, sizeof(T) * n) != cudaSuccess) return {SGDG_ENOMEM, "device upload"};
+  SG_CU(cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice));
+  return {};
+}
+
+Status upload_vals(Handle& h, const std::vector<double>& v, double** d64, float** d32) {
+  SG_ST(upload(h, d64, v.data(), v.size()));
+  std::vector<float> f(v.begin(), v.end());
+  SG_ST(upload(h, d32, f.data(), f.size()));
+  return {};
+}
+
+Status upload_side(Handle& h, const Hierarchy& hi, SideDev& sd) {
+  const int L = hi.L;
+  sd.n.resize(L + 1);
+  sd.nnz.resize(L + 1);
+  sd.rowptr.resize(L + 1);
+  sd.col.resize(L + 1);
+  for (int l = 0; l <= L; ++l) {
+    const Csr& P = hi.lev[l].pattern;
+    sd.n[l] = P.nrows;
+    sd.nnz[l] = P.nnz();
+    SG_ST(upload(h, &sd.rowptr[l], P.rowptr.data(), P.rowptr.size()));
+    SG_ST(upload(h, &sd.col[l], P.col.data(), P.col.size()));
+  }
+  sd.E_rowptr.resize(L); sd.E_col.resize(L); sd.R_rowptr.resize(L); sd.R_col.resize(L); sd.inj.resize(L);
+  sd.E_nnz.resize(L); sd.R_nnz.resize(L);
+  sd.v64.E.resize(L); sd.v64.R.resize(L); sd.v32.E.resize(L); sd.v32.R.resize(L);
+  for (int l = 0; l < L; ++l) {
+    const Csr& E = hi.E[l];
+    const Csr& R = hi.Rt[l];
+    sd.E_nnz[l] = E.nnz();
+    sd.R_nnz[l] = R.nnz();
+    SG_ST(upload(h, &sd.E_rowptr[l], E.rowptr.data(), E.rowptr.size()));
+    SG_ST(upload(h, &sd.E_col[l], E.col.data(), E.col.size()));
+    SG_ST(upload_vals(h, E.val, &sd.v64.E[l], &sd.v32.E[l]));
+    SG_ST(upload(h, &sd.R_rowptr[l], R.rowptr.data(), R.rowptr.size()));
+    SG_ST(upload(h, &sd.R_col[l], R.col.data(), R.col.size()));
+    SG_ST(upload_vals(h, R.val, &sd.v64.R[l], &sd.v32.R[l]));
+    SG_ST(upload(h, &sd.inj[l], hi.inj[l].data(), hi.inj[l].size()));
+  }
+  return {};
+}
+
+std::vector<Chain> make_chains(const std::vector<Term>& terms, bool by_v) {
+  std::map<int, int> idx;
+  std::vector<Chain> out;
+  for (int t = 0; t < (int)terms.size(); ++t) {
+    int key = by_v ? terms[t].v : terms[t].x;
+    auto it = idx.find(key);
+    if (it == idx.end()) {
+      it = idx.emplace(key, (int)out.size()).first;
+      Chain c;
+      c.first = key;
+      c.by_v = by_v;
+      out.push_back(c);
+    }
+    out[it->second].terms.push_back(t);
+  }
+  return out;
+}
+
+void make_plan(Plan& p, const std::vector<Term>& terms) {
+  p.terms = terms;
+  std::vector<Chain> cv = make_chains(terms, true), cx = make_chains(terms, false);
+  p.A = cv.size() <= cx.size() ? cv : cx;
+  p.B = cx.size() <= cv.size() ? cx : cv;
+  p.D = p.A;
+}
+
+struct ErrStore {
+  std::string msg;
+};
+ErrStore& global_err() {
+  static ErrStore e;
+  return e;
+}
+
+sgdg_status fail(Handle* h, const Status& st) {
+  if (h) h->err = st.msg;
+  global_err().msg = st.msg;
+  return st.code;
+}
+
+Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
+  if (cfg.mesh_x.dim != cfg.mesh_v.dim) return {SGDG_EINVAL, "mesh_x and mesh_v must have the same dimension"};
+  if (cfg.mesh_x.dim < 1 || cfg.mesh_x.dim > 2) return {SGDG_EINVAL, "dimension must be 1 or 2"};
+  if (cfg.level_L < 0 || cfg.level_L >= kMaxLevels) return {SGDG_EINVAL, "level_L out of range 0..11"};
+  if (2 * cfg.level_L + 2 > kMaxGrids) return {SGDG_EINVAL, "too many grids"};
+  if (cfg.time_degree != 1) return {SGDG_EINVAL, "only time_degree 1 is supported"};
+  if (!(cfg.dt > 0.0) || !(cfg.delta >= 0.0)) return {SGDG_EINVAL, "dt must be > 0 and delta >= 0"};
+  if (cfg.precision != SGDG_FP64 && cfg.precision != SGDG_MIXED_FP32) return {SGDG_EINVAL, "unknown precision"};
+  if (cfg.restart < 1 || cfg.restart > 63 || cfg.inner_its < 1 || cfg.inner_its > 63)
+    return {SGDG_EINVAL, "restart and inner_its must be in 1..63"};
+  if (c.n_u0 < 0 || (c.n_u0 > 0 && !c.u0)) return {SGDG_EINVAL, "bad u0 list"};
+  h.cfg = cfg;
+  h.d = cfg.mesh_x.dim;
+  h.L = cfg.level_L;
+  SG_CU(cudaSetDevice(cfg.device));
+  Hierarchy hx, hv;
+  SG_ST(build_hierarchy(cfg.mesh_x, h.L, hx));
+  SG_ST(build_hierarchy(cfg.mesh_v, h.L, hv));
+  SG_ST(build_terms(c, h.d, cfg.mesh_x, cfg.mesh_v, cfg.dt, cfg.delta, h.tt));
+  // callback tables: ids 0..3 beta components, 4 sigma
+  SideFns fx, fv;
+  for (int p = 0; p < 4; ++p) {
+    fx.fn.push_back(p < 2 * h.d ? c.beta[p].fx : nullptr); fx.user.push_back(c.beta[p].ux);
+    fv.fn.push_back(p < 2 * h.d ? c.beta[p].fv : nullptr); fv.user.push_back(c.beta[p].uv);
+  }
+  fx.fn.push_back(c.sigma.fx); fx.user.push_back(c.sigma.ux);
+  fv.fn.push_back(c.sigma.fv); fv.user.push_back(c.sigma.uv);
+  // make sure the plain mass factor exists on both sides
+  FactorSpec mass;
+  auto find_or_add = [&](std::vector<FactorSpec>& fs) {
+    for (size_t i = 0; i < fs.size(); ++i)
+      if (fs[i] == mass) return (int)i;
+    fs.push_back(mass);
+    return (int)fs.size() - 1;
+  };
+  h.X.mass = find_or_add(h.tt.xf);
+  h.V.mass = find_or_add(h.tt.vf);
+  SG_ST(upload_side(h, hx, h.X));
+  SG_ST(upload_side(h, hv, h.V));
+  for (int side = 0; side < 2; ++side) {
+    SideDev& sd = side == 0 ? h.X : h.V;
+    const Hierarchy& hi = side == 0 ? hx : hv;
+    const std::vector<FactorSpec>& fs = side == 0 ? h.tt.xf : h.tt.vf;
+    const SideFns& fns = side == 0 ? fx : fv;
+    sd.v64.fac.assign(fs.size(), std::vector<double*>(h.L + 1, nullptr));
+    sd.v32.fac.assign(fs.size(), std::vector<float*>(h.L + 1, nullptr));
+    for (size_t f = 0; f < fs.size(); ++f) {
+      for (int id : fs[f].wfn)
+        if (!fns.fn[id]) return {SGDG_EINVAL, "factor references a missing coefficient function"};
+      std::vector<Csr> X;
+      SG_ST(assemble_factor(hi, fns, fs[f], X));
+      for (int l = 0; l <= h.L; ++l) SG_ST(upload_vals(h, X[l].val, &sd.v64.fac[f][l], &sd.v32.fac[f][l]));
+      if ((int)f == sd.mass) {
+        sd.v64.dinv.resize(h.L + 1);
+        sd.v32.dinv.resize(h.L + 1);
+        for (int l = 0; l <= h.L; ++l) {
+          std::vector<double> di(X[l].nrows);
+          for (int i = 0; i < X[l].nrows; ++i) {
+            double dd = 0.0;
+            for (int p = X[l].rowptr[i]; p < X[l].rowptr[i + 1]; ++p)
+              if (X[l].col[p] == i) dd = X[l].val[p];
+            if (!(dd > 0.0)) return {SGDG_EINVAL, "mass matrix with a non-positive diagonal"};
+            di[i] = 1.0 / dd;
+          }
+          SG_ST(upload_vals(h, di, &sd.v64.dinv[l], &sd.v32.dinv[l]));
+        }
+      }
+    }
+  }
+  // grids, offsets
+  const int L = h.L;
+  h.n1.resize(L + 1);
+  h.n2.resize(L + 1);
+  h.off.assign(L + 2, 0);
+  h.soff.assign(L + 2, 0);
+  for (int l = 0; l <= L; ++l) {
+    h.n1[l] = h.X.n[l];
+    h.n2[l] = h.V.n[L - l];
+    h.soff[l + 1] = h.soff[l] + (long long)h.n1[l] * h.n2[l];
+    h.off[l + 1] = 2 * h.soff[l + 1];
+  }
+  h.n_spatial = h.soff[L + 1];
+  h.n_coeffs = h.off[L + 1];
+  long long tmp = 2;
+  for (int i = 1; i <= L; ++i) tmp = std::max(tmp, 2LL * h.X.n[i - 1] * h.V.n[L - i]);
+  for (int i = 0; i < L; ++i) tmp = std::max(tmp, 2LL * h.X.n[i + 1] * h.V.n[L - i]);
+  h.tmp_elems = tmp;
+  make_plan(h.op, h.tt.terms);
+  Term mt;
+  mt.tau[0][0] = 1.0; mt.tau[0][1] = 0.0; mt.tau[1][0] = 0.0; mt.tau[1][1] = 1.0;
+  mt.x = h.X.mass;
+  mt.v = h.V.mass;
+  make_plan(h.mass, std::vector<Term>{mt});
+  // u0 load vectors
+  for (int k = 0; k < c.n_u0; ++k) {
+    std::vector<std::vector<double>> lx, lv;
+    SG_ST(load_vectors(hx, c.u0[k].fx, c.u0[k].ux, lx));
+    SG_ST(load_vectors(hv, c.u0[k].fv, c.u0[k].uv, lv));
+    h.u0x.push_back(lx);
+    h.u0v.push_back(lv);
+    h.u0coef.push_back(c.u0[k].coef);
+  }
+  if (dev_alloc(h, (void**)&h.U_end, sizeof(double) * h.n_spatial) != cudaSuccess ||
+      dev_alloc(h, (void**)&h.u_sol, sizeof(double) * h.n_coeffs) != cudaSuccess ||
+      dev_alloc(h, (void**)&h.rhs, sizeof(double) * h.n_coeffs) != cudaSuccess)
+    return {SGDG_ENOMEM, "state vectors"};
+  SG_CU(cudaMemset(h.u_sol, 0, sizeof(double) * h.n_coeffs));
+  SG_CU(cudaMemset(h.U_end, 0, sizeof(double) * h.n_spatial));
+  SG_CU(cudaDeviceSynchronize());
+  return {};
+}
+
+}  // namespace
+}  // namespace sgdg
+
+using namespace sgdg;
+
+extern "C" {
+
+sgdg_status sgdg_create(const sgdg_config* cfg, const sgdg_coeffs* coeffs, void** out) {
+  if (!cfg || !coeffs || !out) return fail(nullptr, {SGDG_EINVAL, "null argument"});
+  Handle* h = new Handle();
+  Status st = create(*cfg, *coeffs, *h);
+  if (st.code) {
+    global_err().msg = st.msg;
+    sgdg_destroy(h);
+    return st.code;
+  }
+  *out = h;
+  return SGDG_OK;
+}
+
+void sgdg_destroy(void* hp) {
+  if (!hp) return;
+  Handle* h = (Handle*)hp;
+  cudaSetDevice(h->cfg.device);
+  cudaDeviceSynchronize();
+  solver_free(*h);
+  for (void* p : registry(h)) cudaFree(p);
+  registry(h).clear();
+  delete h;
+}
+
+const char* sgdg_last_error(const void* hp) {
+  if (!hp) return global_err().msg.c_str();
+  return ((const Handle*)hp)->err.c_str();
+}
+
+sgdg_status sgdg_get_info(const void* hp, sgdg_info* o) {
+  if (!hp || !o) return SGDG_EINVAL;
+  const Handle* h = (const Handle*)hp;
+  o->L = h->L;
+  o->d = h->d;
+  o->R = 2;
+  o->n_grids = h->L + 1;
+  o->n_spatial = h->n_spatial;
+  o->n_coeffs = h->n_coeffs;
+  o->n_terms = (int)h->op.terms.size();
+  o->n_x_factors = (int)h->tt.xf.size();
+  o->n_v_factors = (int)h->tt.vf.size();
+  o->device_bytes = (double)h->device_bytes;
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_grid_shape(const void* hp, int l, int* n1, int* n2, long long* offset) {
+  if (!hp) return SGDG_EINVAL;
+  const Handle* h = (const Handle*)hp;
+  if (l < 0 || l > h->L) return SGDG_EINVAL;
+  if (n1) *n1 = h->n1[l];
+  if (n2) *n2 = h->n2[l];
+  if (offset) *offset = h->off[l];
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_apply_operator(void* hp, const void* u, void* y, int prec, void* stream) {
+  if (!hp || !u || !y) return fail((Handle*)hp, {SGDG_EINVAL, "null argument"});
+  Handle* h = (Handle*)hp;
+  cudaStream_t s = (cudaStream_t)stream;
+  Status st;
+  if (prec == SGDG_FP64) st = apply_plan<double>(*h, h->op, (const double*)u, (double*)y, s);
+  else if (prec == SGDG_MIXED_FP32) st = apply_plan<float>(*h, h->op, (const float*)u, (float*)y, s);
+  else st = {SGDG_EINVAL, "unknown precision"};
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+sgdg_status sgdg_apply_mass(void* hp, const void* u, void* y, int prec, void* stream) {
+  if (!hp || !u || !y) return fail((Handle*)hp, {SGDG_EINVAL, "null argument"});
+  Handle* h = (Handle*)hp;
+  cudaStream_t s = (cudaStream_t)stream;
+  Status st;
+  if (prec == SGDG_FP64) st = apply_plan<double>(*h, h->mass, (const double*)u, (double*)y, s);
+  else if (prec == SGDG_MIXED_FP32) st = apply_plan<float>(*h, h->mass, (const float*)u, (float*)y, s);
+  else st = {SGDG_EINVAL, "unknown precision"};
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+sgdg_status sgdg_apply_operator_host(void* hp, const double* u, double* y, int prec) {
+  if (!hp || !u || !y) return fail((Handle*)hp, {SGDG_EINVAL, "null argument"});
+  Handle* h = (Handle*)hp;
+  Handle::Bufs& b = h->b64;
+  size_t n = (size_t)h->n_coeffs;
+  if (!b.cvt_in) {
+    if (dev_alloc(*h, &b.cvt_in, 8 * n) != cudaSuccess || dev_alloc(*h, &b.cvt_out, 8 * n) != cudaSuccess)
+      return fail(h, {SGDG_ENOMEM, "host-apply buffers"});
+  }
+  if (prec == SGDG_MIXED_FP32 && !h->b32.cvt_in) {
+    if (dev_alloc(*h, &h->b32.cvt_in, 4 * n) != cudaSuccess || dev_alloc(*h, &h->b32.cvt_out, 4 * n) != cudaSuccess)
+      return fail(h, {SGDG_ENOMEM, "host-apply buffers"});
+  }
+  cudaStream_t s = nullptr;
+  if (cudaMemcpyAsync(b.cvt_in, u, 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(h, {SGDG_ECUDA, "host-to-device copy"});
+  Status st;
+  if (prec == SGDG_FP64) {
+    st = apply_plan<double>(*h, h->op, (const double*)b.cvt_in, (double*)b.cvt_out, s);
+  } else if (prec == SGDG_MIXED_FP32) {
+    vec_convert<double, float>((const double*)b.cvt_in, (float*)h->b32.cvt_in, n, s);
+    st = apply_plan<float>(*h, h->op, (const float*)h->b32.cvt_in, (float*)h->b32.cvt_out, s);
+    vec_convert<float, double>((const float*)h->b32.cvt_out, (double*)b.cvt_out, n, s);
+  } else {
+    st = {SGDG_EINVAL, "unknown precision"};
+  }
+  if (st.code) return fail(h, st);
+  if (cudaMemcpyAsync(y, b.cvt_out, 8 * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(h, {SGDG_ECUDA, "device-to-host copy"});
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_apply_diag(void* hp, int l1, int l2, const void* u, void* y, int prec, void* stream) {
+  if (!hp || !u || !y) return fail((Handle*)hp, {SGDG_EINVAL, "null argument"});
+  Handle* h = (Handle*)hp;
+  if (l1 < 0 || l2 < 0 || l1 > h->L || l2 > h->L || (l1 + l2 != h->L && l1 + l2 != h->L - 1))
+    return fail(h, {SGDG_EINVAL, "grid levels must satisfy l1 + l2 in {L-1, L}"});
+  cudaStream_t s = (cudaStream_t)stream;
+  Status st;
+  if (prec == SGDG_FP64) {
+    const double* ui[1] = {(const double*)u};
+    double* yo[1] = {(double*)y};
+    st = apply_diag_grids<double>(*h, 1, &l1, &l2, ui, yo, s);
+  } else if (prec == SGDG_MIXED_FP32) {
+    const float* ui[1] = {(const float*)u};
+    float* yo[1] = {(float*)y};
+    st = apply_diag_grids<float>(*h, 1, &l1, &l2, ui, yo, s);
+  } else {
+    st = {SGDG_EINVAL, "unknown precision"};
+  }
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+sgdg_status sgdg_ct_precondition(void* hp, const double* r, double* z, void* stream) {
+  if (!hp || !r || !z) return fail((Handle*)hp, {SGDG_EINVAL, "null argument"});
+  Handle* h = (Handle*)hp;
+  int its = 0;
+  Status st = ct_precondition(*h, r, z, (cudaStream_t)stream, &its);
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+sgdg_status sgdg_set_initial(void* hp) {
+  if (!hp) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  // b_1 = eta(t_0^+) (x) (u0, phi_{l,k}) = (1, -1) (x) sum_p fx_p (x) fv_p per grid
+  const int np = (int)h->u0x.size();
+  if (np == 0) {
+    cudaMemset(h->rhs, 0, sizeof(double) * h->n_coeffs);
+  } else {
+    for (int l = 0; l <= h->L; ++l) {
+      const int n1 = h->n1[l], n2 = h->n2[l];
+      std::vector<double> fx((size_t)np * n1), fv((size_t)np * n2);
+      for (int p = 0; p < np; ++p) {
+        for (int i = 0; i < n1; ++i) fx[(size_t)p * n1 + i] = h->u0coef[p] * h->u0x[p][l][i];
+        for (int i = 0; i < n2; ++i) fv[(size_t)p * n2 + i] = h->u0v[p][h->L - l][i];
+      }
+      double *dfx, *dfv;
+      if (cudaMalloc(&dfx, 8 * fx.size()) != cudaSuccess || cudaMalloc(&dfv, 8 * fv.size()) != cudaSuccess)
+        return fail(h, {SGDG_ENOMEM, "initial load vectors"});
+      cudaMemcpy(dfx, fx.data(), 8 * fx.size(), cudaMemcpyHostToDevice);
+      cudaMemcpy(dfv, fv.data(), 8 * fv.size(), cudaMemcpyHostToDevice);
+      outer_init(h->rhs + h->off[l], n1, n2, np, dfx, dfv, 1.0, -1.0, nullptr);
+      cudaDeviceSynchronize();
+      cudaFree(dfx);
+      cudaFree(dfv);
+    }
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(h, {SGDG_ECUDA, "set_initial"});
+  h->have_initial = true;
+  h->first_strip = true;
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_advance_strip(void* hp, void* stream, sgdg_strip_stats* stats) {
+  if (!hp) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  Status st = advance_strip(*h, (cudaStream_t)stream, stats);
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+sgdg_status sgdg_get_solution(const void* hp, double* dst, int on_device) {
+  if (!hp || !dst) return SGDG_EINVAL;
+  const Handle* h = (const Handle*)hp;
+  cudaError_t e = cudaMemcpy(dst, h->u_sol, sizeof(double) * h->n_coeffs,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? SGDG_OK : SGDG_ECUDA;
+}
+
+sgdg_status sgdg_get_end_value(const void* hp, double* dst, int on_device) {
+  if (!hp || !dst) return SGDG_EINVAL;
+  const Handle* h = (const Handle*)hp;
+  cudaError_t e = cudaMemcpy(dst, h->U_end, sizeof(double) * h->n_spatial,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? SGDG_OK : SGDG_ECUDA;
+}
+
+static void drop_events(Handle* h) {
+  for (auto& k : h->kev) {
+    cudaEventDestroy(k.e0);
+    cudaEventDestroy(k.e1);
+  }
+  h->kev.clear();
+}
+
+sgdg_status sgdg_profile(void* hp, int enable) {
+  if (!hp) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  cudaDeviceSynchronize();
+  drop_events(h);
+  h->prof = enable != 0;
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_kernel_stats(void* hp, sgdg_kernel_stat* out, int n_kinds) {
+  if (!hp || !out || n_kinds < KIND_COUNT) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(h, {SGDG_ECUDA, "synchronize"});
+  for (int k = 0; k < n_kinds; ++k) out[k] = sgdg_kernel_stat{0, 0.0, 0.0};
+  for (auto& k : h->kev) {
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, k.e0, k.e1);
+    out[k.kind].launches++;
+    out[k.kind].ms += ms;
+    out[k.kind].bytes += k.bytes;
+  }
+  drop_events(h);
+  return SGDG_OK;
+}
+
+long long sgdg_launch_count(const void* hp) { return hp ? ((const Handle*)hp)->launches : 0; }
+
+sgdg_status sgdg_eval_nodal(void* hp, const double* u, double* out, void* stream) {
+  if (!hp || !u || !out) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  Status st = nodal_eval(*h, u, out, (cudaStream_t)stream);
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// The library handle: host description + device-resident data of one problem.
+#pragma once
+
+#include <memory>
+
+#include "device.h"
+
+namespace sgdg {
+
+// Device copies of one side's (Omega_x or Omega_v) level data.
+template <typename T>
+struct SideValues {
+  std::vector<std::vector<T*>> fac;   // [factor][level] values on the level pattern
+  std::vector<T*> E, R;               // E[l]: level l -> l+1 values;  R[l] = E[l]^T values
+  std::vector<T*> dinv;               // inverse diagonal of the mass matrix per level
+};
+
+struct SideDev {
+  std::vector<int> n, nnz, E_nnz, R_nnz;
+  std::vector<int*> rowptr, col;                  // P1 pattern per level
+  std::vector<int*> E_rowptr, E_col, R_rowptr, R_col;
+  std::vector<int*> inj;                          // level l vertex -> index on level l+1
+  int mass = -1;                                  // factor id of the plain mass matrix
+  SideValues<double> v64;
+  SideValues<float> v32;
+  template <typename T> SideValues<T>& vals();
+};
+template <> inline SideValues<double>& SideDev::vals<double>() { return v64; }
+template <> inline SideValues<float>& SideDev::vals<float>() { return v32; }
+
+// A grouping of terms that share the factor applied first in a sweep branch.
+struct Chain {
+  int first;               // factor id applied first (V for by_v, X otherwise)
+  bool by_v;               // first factor is on the v side
+  std::vector<int> terms;  // term indices
+};
+
+struct Plan {
+  std::vector<Term> terms;
+  std::vector<Chain> A, B;  // branch A: sources l1' <= l1; branch B: l1' > l1
+  std::vector<Chain> D;     // diagonal-block apply grouping
+};
+
+struct Workspace;  // solver buffers (solve.cu)
+
+struct Handle {
+  sgdg_config cfg{};
+  int d = 0, L = 0;
+  std::string err;
+  TermTable tt;
+  SideDev X, V;
+  std::vector<int> n1, n2;           // grid l: (n1[l], n2[l]) = (nx[l], nv[L-l])
+  std::vector<long long> off;        // element offsets (with the time index)
+  std::vector<long long> soff;       // spatial offsets
+  long long n_coeffs = 0, n_spatial = 0;
+  Plan op, mass;
+  // sweep buffers (both precisions allocated lazily)
+  struct Bufs {
+    void* S = nullptr; void* Z = nullptr; void* TP = nullptr; void* tmp = nullptr; void* W = nullptr;
+    void* cvt_in = nullptr; void* cvt_out = nullptr;
+  } b64, b32;
+  long long tmp_elems = 0;
+  // host copies of the u0 load vectors per level (for set_initial)
+  std::vector<std::vector<std::vector<double>>> u0x, u0v;   // [product][level][n]
+  std::vector<double> u0coef;
+  // strip state
+  double* U_end = nullptr;   // spatial, n_spatial
+  double* u_sol = nullptr;   // last strip solution, n_coeffs
+  double* rhs = nullptr;     // n_coeffs
+  bool have_initial = false, first_strip = true;
+  size_t device_bytes = 0;
+  Workspace* ws = nullptr;      // owned; released by solver_free
+  cudaStream_t cur = nullptr;
+  // launch accounting: every SpMM launch is counted; with profiling on, each
+  // one is bracketed by CUDA events and its algorithmic bytes recorded
+  long long launches = 0;
+  bool prof = false;
+  struct KEvent { int kind; double bytes; cudaEvent_t e0, e1; };
+  std::vector<KEvent> kev;
+  ~Handle();
+};
+
+// kinds of SpMM launches for the per-kernel statistics
+enum { KIND_LEFT = 0, KIND_RIGHT = 1, KIND_XFER_LEFT = 2, KIND_XFER_RIGHT = 3, KIND_COUNT = 4 };
+
+// Launch a grouped SpMM (left or right) with accounting.  mat_bytes: bytes of
+// the CSR pattern and value arrays the launch reads.
+template <typename T>
+cudaError_t run_spmm(Handle& h, bool left, SpmmLaunch<T>& a, cudaStream_t s, int kind, double mat_bytes);
+
+// allocation helper that records bytes and reports ENOMEM
+cudaError_t dev_alloc(Handle& h, void** p, size_t bytes);
+
+template <typename T>
+Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s);
+template <typename T>
+Status apply_diag_grids(Handle& h, int ng, const int* l1, const int* l2, const T* const* u, T* const* y,
+                        cudaStream_t s);
+Status nodal_eval(Handle& h, const double* u, double* out, cudaStream_t s);
+
+Status solver_init(Handle& h);
+Status ct_precondition(Handle& h, const double* r, double* z, cudaStream_t s, int* inner_its);
+Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st);
+void solver_free(Handle& h);
+
+}  // namespace sgdg

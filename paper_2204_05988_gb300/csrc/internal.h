@@ -1,0 +1,94 @@
+// Internal data structures of the sgdg library (host side).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sgdg.h"
+
+namespace sgdg {
+
+constexpr int kMaxLevels = 12;   // 0..11
+constexpr int kR = 2;            // time-DG degree 1: two Legendre coefficients
+
+struct Status {
+  sgdg_status code = SGDG_OK;
+  std::string msg;
+};
+
+// Host CSR (rows sorted, columns sorted within a row).
+struct Csr {
+  int nrows = 0, ncols = 0;
+  std::vector<int> rowptr, col;
+  std::vector<double> val;
+  int nnz() const { return (int)col.size(); }
+};
+
+// One refinement level of a mesh, canonical (lexicographic) vertex order.
+struct MeshLevel {
+  int n = 0;                          // vertices (periodic masters only)
+  std::vector<double> coords;         // n * d
+  std::vector<int> cells;             // nc * (d+1), canonical vertex ids
+  std::vector<double> cell_coords;    // nc * (d+1) * d, geometric coords
+  std::vector<int> bfaces;            // nf * d, canonical vertex ids
+  std::vector<double> bface_coords;   // nf * d * d
+  std::vector<int> bface_axis, bface_side;
+  Csr pattern;                        // P1 adjacency (vertices sharing a cell)
+  int ncells(int d) const { return (int)cells.size() / (d + 1); }
+  int nbfaces(int d) const { return (int)bfaces.size() / d; }
+};
+
+struct Hierarchy {
+  int d = 0, L = 0;
+  std::vector<MeshLevel> lev;         // 0..L
+  std::vector<Csr> E;                 // E[l]: prolongation level l -> l+1 (n_{l+1} x n_l)
+  std::vector<Csr> Rt;                // Rt[l] = E[l]^T (n_l x n_{l+1})
+  std::vector<std::vector<int>> inj;  // inj[l][k]: level-(l+1) index of level-l vertex k
+};
+
+Status build_hierarchy(const sgdg_mesh& m, int L, Hierarchy& h);
+
+// ---------------------------------------------------------------------------
+// Factors of the Kronecker terms (Sect. 4.2)
+// ---------------------------------------------------------------------------
+
+// Coefficient functions on one side: ids into a table of callbacks.
+struct SideFns {
+  std::vector<sgdg_fn> fn;
+  std::vector<void*> user;
+};
+
+// X[i,j] = int w (D_trial phi_j)(D_test phi_i), w = product of fns (no
+// scalar); over the domain (kind 0) or the boundary faces of one box side
+// (kind 1); restricted to cells whose centroid has sign(fn) == sign.
+struct FactorSpec {
+  int kind = 0;
+  std::vector<int> wfn;                         // sorted function ids
+  int test = 0, trial = 0;                      // 0 value, p >= 1: d/dy_p
+  std::vector<std::pair<int, int>> restrict_;   // (fn id, sign), sorted
+  int face_axis = -1, face_side = 0;
+  bool operator<(const FactorSpec& o) const;
+  bool operator==(const FactorSpec& o) const;
+};
+
+Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec& f,
+                       std::vector<Csr>& per_level);   // per_level[l] on lev[l].pattern
+
+struct Term {
+  double tau[kR][kR];  // time coupling [s][s']
+  int x, v;            // factor ids
+};
+
+struct TermTable {
+  std::vector<FactorSpec> xf, vf;
+  std::vector<Term> terms;
+};
+
+Status build_terms(const sgdg_coeffs& c, int d, const sgdg_mesh& mx, const sgdg_mesh& mv,
+                   double dt, double delta, TermTable& out);
+
+// Load vector F[i] = int fn phi_i on the finest level, restricted to all levels.
+Status load_vectors(const Hierarchy& h, sgdg_fn fn, void* user, std::vector<std::vector<double>>& per_level);
+
+}  // namespace sgdg

@@ -1,0 +1,49 @@
+"""The C-ABI library loads and exports every entry point include/sgdg.h declares
+(CPU only: no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "sgdg.h")) as f:
+        src = f.read()
+    return sorted(set(re.findall(r"^\s*(?:sgdg_status|void|const char\*|long long)\s+(sgdg_\w+)\s*\(", src, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2204_05988_gb300 import LIB_PATH, build
+    if not os.path.exists(LIB_PATH):
+        build.build()
+    return ctypes.CDLL(LIB_PATH)
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    assert "sgdg_create" in names and "sgdg_apply_operator" in names and len(names) >= 15
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_declares_exactly_the_header(lib):
+    from paper_2204_05988_gb300 import EXPORTS
+    assert sorted(EXPORTS) == _declared()
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    import paper_2204_05988_gb300 as P
+    saved = P._lib
+    P._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            P.load_library(str(tmp_path / "missing.so"))
+    finally:
+        P._lib = saved
