@@ -152,6 +152,8 @@ def main():
     ap.add_argument("--ref-L", type=int, default=5)
     ap.add_argument("--strip-L", type=int, default=7, help="level of the strip-solve timing (-1: skip)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch", type=int, default=8, help="instances in the batch measurement (0: skip)")
+    ap.add_argument("--batch-levels", type=int, nargs="+", default=[5, 6, 7])
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -183,6 +185,11 @@ def main():
     y32 = torch.empty_like(u32)
     y64 = torch.empty_like(u64)
     stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    s.autotune(u32, y32, P.SGDG_MIXED_FP32, stream)
+    s.autotune(u64, y64, P.SGDG_FP64, stream)
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
 
     def timed(fn, K, Wm):
         for _ in range(Wm):
@@ -274,6 +281,41 @@ def main():
             sv.close()
         strip["speedup_mixed_vs_fp64"] = strip["fp64"]["s_per_strip"] / strip["mixed"]["s_per_strip"]
 
+    # ---- batch of independent instances of uneven L: one CUDA graph per apply,
+    # concurrent strip solves
+    batch = None
+    if args.batch > 0:
+        probs = W.batched_4d(n=args.batch, seed=0, levels=tuple(args.batch_levels))
+        tb = time.perf_counter()
+        solvers = [P.Solver(pr, precision=P.SGDG_MIXED_FP32, rtol=1e-8, restart=30, inner_its=12,
+                            inner_rtol=1e-2, device=local) for pr in probs]
+        bsetup = time.perf_counter() - tb
+        bus = [torch.tensor(W.uniform_vector(sv.n_coeffs, seed=100 + k), dtype=torch.float32, device="cuda")
+               for k, sv in enumerate(solvers)]
+        bys = [torch.empty_like(x) for x in bus]
+        for sv, x, y in zip(solvers, bus, bys):
+            sv.autotune(x, y, P.SGDG_MIXED_FP32, stream)
+        B = P.Batch(solvers)
+        B.apply(bus, bys, P.SGDG_MIXED_FP32, stream)          # capture
+        bms = timed(lambda: B.apply(bus, bys, P.SGDG_MIXED_FP32, stream), args.steps, 1)
+        dof = sum(sv.n_coeffs for sv in solvers)
+        for sv in solvers:
+            sv.set_initial()
+        tstr = []
+        for _ in range(2):
+            t1 = time.perf_counter()
+            st = B.advance()
+            tstr.append(time.perf_counter() - t1)
+        batch = {"workload": f"{args.batch} x transport_4d free streaming, L from {sorted(set(p.L for p in probs))}",
+                 "levels": [p.L for p in probs], "dof_total": dof, "setup_s": round(bsetup, 2),
+                 "apply_graph_ms": bms, "apply_GDoFps": dof / (bms * 1e-3) / 1e9,
+                 "s_per_batched_strip": round(tstr[-1], 4),
+                 "max_rel_residual": max(x.rel_residual for x in st),
+                 "outer_its": [x.outer_its for x in st]}
+        B.close()
+        for sv in solvers:
+            sv.close()
+
     if rank == 0:
         cpu = None
         if not args.no_cpu:
@@ -283,10 +325,11 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"transport_2d d=2 L={args.L} sigma=0.1 operator apply A^(delta) u",
                            "dof_per_step": n, "terms": s.info.n_terms, "l2": "inputs larger than L2 (493 MB f32)",
-                           "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2)},
+                           "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
+                           "autotune_s": round(tune_s, 2)},
                 "fp64_apply": {"value": world * n / (ms64 * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms64},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
-                "strip": strip, "cpu_baseline": cpu}
+                "strip": strip, "batch": batch, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

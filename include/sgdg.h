@@ -181,9 +181,32 @@ sgdg_status sgdg_get_end_value(const void* h, double* dst, int on_device);
  * from finer ones).  u, out: device arrays of n_spatial doubles. */
 sgdg_status sgdg_eval_nodal(void* h, const double* u, double* out, void* stream);
 
+/* Autotuner (no counterpart in the paper): times candidate rows-per-thread
+ * settings of every sweep launch site on live applies y = A u (device
+ * arrays as for sgdg_apply_operator, overwritten) and keeps the fastest per
+ * site for all later applies of this handle. */
+sgdg_status sgdg_autotune(void* h, const void* u, void* y, int precision, void* stream);
+
+/* Batches of independent problems (many instances of uneven L, Sect. 5's
+ * experiments run one after another; here they share the GPU).  A batch
+ * references n >= 1 member handles (not owned; they must outlive it). */
+sgdg_status sgdg_batch_create(int n, void* const* members, void** out_batch);
+void sgdg_batch_destroy(void* batch);
+/* y_k = A_k u_k for every member k (u, y: arrays of n device pointers, the
+ * precision's element type).  The whole batch is one CUDA graph: captured on
+ * the first call for a given pointer set and precision, replayed on `stream`
+ * afterwards.  The first call also runs one eager apply per member. */
+sgdg_status sgdg_batch_apply(void* batch, const void* const* u, void* const* y, int precision, void* stream);
+/* Advance every member by one strip, members concurrently (one stream and one
+ * host thread each).  per_member: n stats (may be NULL).  Returns the first
+ * non-OK member status. */
+sgdg_status sgdg_batch_advance(void* batch, sgdg_strip_stats* per_member);
+
 /* Kernel accounting (measurement; no counterpart in the paper).  Kinds:
- * 0 = factor SpMM along dim 1 ("left"), 1 = factor SpMM along dim 2
- * ("right"), 2 / 3 = transfers (prolongation / restriction) along dim 1 / 2. */
+ * 0 / 1 = factor SpMM along dim 1 / dim 2 (diagonal blocks, CT transfers),
+ * 2 / 3 = transfers along dim 1 / dim 2, 4 / 5 = sweep chain steps of
+ * branch A / B, 6 / 7 = sweep final updates along dim 1 / dim 2.
+ * n_kinds must be >= 8. */
 typedef struct {
   long long launches;
   double ms;        /* summed CUDA-event duration of the launches */

@@ -78,9 +78,15 @@ EXPORTS = {
     "sgdg_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "sgdg_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "sgdg_launch_count": (C.c_longlong, [C.c_void_p]),
+    "sgdg_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "sgdg_batch_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+    "sgdg_batch_destroy": (None, [C.c_void_p]),
+    "sgdg_batch_apply": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
+                                   C.c_void_p]),
+    "sgdg_batch_advance": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
 
-KERNEL_KINDS = ("spmm_left", "spmm_right", "transfer_left", "transfer_right")
+KERNEL_KINDS = ("spmm_left", "spmm_right", "transfer_left", "transfer_right", "chain_a", "chain_b", "final_left", "final_right")
 
 
 class KernelStat(C.Structure):
@@ -269,10 +275,13 @@ class Solver:
         self._check(self.lib.sgdg_profile(self.h, int(enable)))
 
     def kernel_stats(self):
-        arr = (KernelStat * 4)()
-        self._check(self.lib.sgdg_kernel_stats(self.h, arr, 4))
+        arr = (KernelStat * len(KERNEL_KINDS))()
+        self._check(self.lib.sgdg_kernel_stats(self.h, arr, len(KERNEL_KINDS)))
         return {KERNEL_KINDS[k]: {"launches": arr[k].launches, "ms": arr[k].ms, "bytes": arr[k].bytes}
-                for k in range(4)}
+                for k in range(len(KERNEL_KINDS))}
+
+    def autotune(self, u, y, precision: int = SGDG_MIXED_FP32, stream=None):
+        self._check(self.lib.sgdg_autotune(self.h, _ptr(u), _ptr(y), precision, _stream(stream)))
 
     def launch_count(self) -> int:
         return int(self.lib.sgdg_launch_count(self.h))
@@ -281,6 +290,48 @@ class Solver:
         if getattr(self, "h", None):
             self.lib.sgdg_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent problems advanced together (sgdg_batch_*): one CUDA graph per
+    batch apply, concurrent strip solves."""
+
+    def __init__(self, solvers):
+        self.lib = load_library()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s.h for s in self.solvers])
+        b = C.c_void_p()
+        st = self.lib.sgdg_batch_create(len(self.solvers), arr, C.byref(b))
+        if st != 0:
+            raise SgdgError(st, self.lib.sgdg_last_error(None).decode())
+        self.b = b
+
+    def apply(self, us, ys, precision: int = SGDG_MIXED_FP32, stream=None):
+        n = len(self.solvers)
+        ua = (C.c_void_p * n)(*[_ptr(u) for u in us])
+        ya = (C.c_void_p * n)(*[_ptr(y) for y in ys])
+        st = self.lib.sgdg_batch_apply(self.b, ua, ya, precision, _stream(stream))
+        if st != 0:
+            raise SgdgError(st, self.lib.sgdg_last_error(None).decode())
+
+    def advance(self):
+        n = len(self.solvers)
+        stats = (StripStats * n)()
+        st = self.lib.sgdg_batch_advance(self.b, stats)
+        if st != 0:
+            raise SgdgError(st, self.lib.sgdg_last_error(None).decode())
+        return list(stats)
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.sgdg_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "handle.h"
+#include "sweep.h"
 
 namespace sgdg {
 
@@ -44,7 +45,7 @@ cudaError_t run_spmm(Handle& h, bool left, SpmmLaunch<T>& a, cudaStream_t s, int
       double out = 2.0 * sizeof(T) * (double)a.g[g].n1_out * a.g[g].n2_out;
       bytes += in * (a.g[g].in2 ? 2 : 1) + out * (a.accumulate ? 2 : 1);
     }
-    h.kev.push_back({kind, bytes, e0, e1});
+    h.kev.push_back({kind, bytes, e0, e1, -1});
   }
   return e;
 }
@@ -95,70 +96,6 @@ void set_single(Handle& h, SpmmLaunch<T>& a, int factor, bool x_side, int level_
   }
 }
 
-// Launch "first" (chain-defining) or "last" (fused multi-term) stage of a chain
-// over grids [g0, g1) of the sparse grid; in/out are full sparse-grid vectors.
-template <typename T>
-Status stage(Handle& h, const std::vector<Term>& terms, const Chain& c, bool first, bool left, const T* in, T* out,
-             int g0, int g1, bool accumulate, cudaStream_t s) {
-  const bool x_side = left;
-  int lev[kMaxGrids];
-  SpmmLaunch<T> a;
-  a.ngrids = g1 - g0;
-  if (a.ngrids <= 0) return {};
-  for (int g = g0; g < g1; ++g) {
-    SpmmGrid<T>& G = a.g[g - g0];
-    G.in = in + h.off[g];
-    G.in2 = nullptr;
-    G.out = out + h.off[g];
-    G.n1_in = G.n1_out = h.n1[g];
-    G.n2_in = G.n2_out = h.n2[g];
-    lev[g - g0] = x_side ? g : h.L - g;
-  }
-  // the single-factor stage applies c.first with tau = I; the other stage
-  // applies every term's own factor with its tau
-  const bool single = (first == true);
-  const SideDev& sd = x_side ? h.X : h.V;
-  const int kind = left ? KIND_LEFT : KIND_RIGHT;
-  if (single) {
-    set_single(h, a, c.first, x_side, lev);
-    a.accumulate = accumulate;
-    double mb = 0.0;
-    for (int g = 0; g < a.ngrids; ++g) mb += pattern_bytes<T>(sd, lev[g], 1);
-    SG_CU(run_spmm(h, left, a, s, kind, mb));
-    return {};
-  }
-  const int nt = (int)c.terms.size();
-  for (int t0 = 0; t0 < nt; t0 += kMaxTerms) {
-    int t1 = std::min(nt, t0 + kMaxTerms);
-    set_terms(h, a, terms, c.terms, t0, t1, x_side, lev, a.ngrids);
-    a.accumulate = (t0 > 0) ? 1 : accumulate;
-    double mb = 0.0;
-    for (int g = 0; g < a.ngrids; ++g) mb += pattern_bytes<T>(sd, lev[g], t1 - t0);
-    SG_CU(run_spmm(h, left, a, s, kind, mb));
-  }
-  return {};
-}
-
-// One transfer: out = Op(in [+ in2]) on a single (n1 x n2) array.
-template <typename T>
-Status transfer(Handle& h, bool left, const int* rowptr, const int* col, const T* val, int nrows, int nnz,
-                const T* in, const T* in2, T* out, int n1_in, int n2_in, int n1_out, int n2_out, bool accumulate,
-                T scale, cudaStream_t s) {
-  SpmmLaunch<T> a;
-  a.ngrids = 1;
-  a.nterms = 1;
-  a.identity = scale == (T)1 ? 1 : 0;
-  a.tau[0][0] = scale; a.tau[0][1] = 0; a.tau[0][2] = 0; a.tau[0][3] = scale;
-  a.accumulate = accumulate;
-  SpmmGrid<T>& G = a.g[0];
-  G.in = in; G.in2 = in2; G.out = out;
-  G.n1_in = n1_in; G.n2_in = n2_in; G.n1_out = n1_out; G.n2_out = n2_out;
-  G.rowptr = rowptr; G.col = col; G.val[0] = val;
-  const double mb = 4.0 * (nrows + 1) + (4.0 + sizeof(T)) * (double)nnz;
-  SG_CU(run_spmm(h, left, a, s, left ? KIND_XFER_LEFT : KIND_XFER_RIGHT, mb));
-  return {};
-}
-
 template <typename T>
 Handle::Bufs& bufs(Handle& h);
 template <> Handle::Bufs& bufs<double>(Handle& h) { return h.b64; }
@@ -177,65 +114,229 @@ Status ensure_bufs(Handle& h) {
   return {};
 }
 
+// Chain-state pool of the sweep: 2 ring slots per branch-A chain, 2 ring
+// slots + 1 strict slot per branch-B chain, each slot one largest grid.
+template <typename T>
+Status ensure_pool(Handle& h, const Plan& p, T** pool, long long* slot) {
+  long long M = 2;
+  for (int l = 0; l <= h.L; ++l) M = std::max(M, 2LL * h.n1[l] * h.n2[l]);
+  // sized once for the largest plan of the handle (the operator's)
+  const Plan& big = h.op.A.size() + h.op.B.size() >= p.A.size() + p.B.size() ? h.op : p;
+  const long long need = M * std::max<long long>(2LL * (long long)big.A.size(), 3LL * (long long)big.B.size());
+  Handle::Bufs& b = bufs<T>(h);
+  if (!b.pool) {
+    if (dev_alloc(h, &b.pool, sizeof(T) * (size_t)need) != cudaSuccess) return {SGDG_ENOMEM, "sweep chain pool"};
+    b.pool_elems = need;
+  }
+  if (b.pool_elems < M * std::max<long long>(2LL * (long long)p.A.size(), 3LL * (long long)p.B.size()))
+    return {SGDG_EINVAL, "sweep chain pool too small for this plan"};
+  *pool = (T*)b.pool;
+  *slot = M;
+  return {};
+}
+
+template <typename T>
+double csr_bytes(int rows, int nnz, int nvals) {
+  return 4.0 * (rows + 1) + (4.0 + (double)nvals * sizeof(T)) * nnz;
+}
+
+// launch site: kind (< 16), chains or terms (< 64), element size, grid shape (< 2^24 each)
+inline long long site_key(int kind, int n1, int n2, int count, int elem) {
+  const long long head = ((long long)kind * 64 + count) * 16 + elem;
+  return (((head << 24) | (long long)n1) << 24) | (long long)n2;
+}
+
+template <typename T>
+int pick_ch(Handle& h, long long site) {
+  if (h.force_ch > 0) return h.force_ch;
+  auto it = h.tuned_ch.find(site);
+  return it == h.tuned_ch.end() ? 0 : it->second;
+}
+
+template <typename T>
+Status run_chain(Handle& h, ChainArgs<T>& a, bool mode_a, cudaStream_t s, double mat_bytes) {
+  const long long site = site_key(mode_a ? KIND_CHAIN_A : KIND_CHAIN_B, a.n1, a.n2, a.nchains, sizeof(T));
+  a.ch = std::min(pick_ch<T>(h, site), a.n1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h.prof) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+  }
+  SG_CU(launch_chain(a, mode_a, s));
+  h.launches++;
+  if (h.prof) {
+    cudaEventRecord(e1, s);
+    const double g = 2.0 * sizeof(T) * (double)a.n1 * a.n2;
+    const double gp = 2.0 * sizeof(T) * (double)a.n1_prev * a.n2_prev;
+    double bytes = mat_bytes + g + a.nchains * g * (mode_a ? 1.0 : 2.0) + (a.has_prev ? a.nchains * gp : 0.0);
+    h.kev.push_back({mode_a ? KIND_CHAIN_A : KIND_CHAIN_B, bytes, e0, e1, site});
+  }
+  return {};
+}
+
+template <typename T>
+Status run_final(Handle& h, FinalArgs<T>& f, bool left, int lev_rows, int lev_nnz, cudaStream_t s) {
+  const long long site = site_key(left ? KIND_FINAL_LEFT : KIND_FINAL_RIGHT, f.n1, f.n2, f.nterms, sizeof(T));
+  f.ch = std::min(pick_ch<T>(h, site), f.n1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h.prof) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+  }
+  SG_CU(launch_final(f, left, s));
+  h.launches++;
+  if (h.prof) {
+    cudaEventRecord(e1, s);
+    const double g = 2.0 * sizeof(T) * (double)f.n1 * f.n2;
+    double bytes = csr_bytes<T>(lev_rows, lev_nnz, f.nterms) + f.nin * g + g * (f.accumulate ? 2.0 : 1.0);
+    h.kev.push_back({left ? KIND_FINAL_LEFT : KIND_FINAL_RIGHT, bytes, e0, e1, site});
+  }
+  return {};
+}
+
+// y_i (+)= sum over the chains' terms of tau_a F_a in_c on grid i (F on the
+// x pattern at level i when left, on the v pattern at level L-i otherwise).
+template <typename T, typename InOf>
+Status finals_on(Handle& h, const Plan& p, const std::vector<Chain>& chains, bool left, int n1, int n2, int lev,
+                 InOf in_of, bool accumulate_first, T* ygrid, cudaStream_t s) {
+  const SideDev& sd = left ? h.X : h.V;
+  FinalArgs<T> f;
+  f.n1 = n1;
+  f.n2 = n2;
+  f.rowptr = sd.rowptr[lev];
+  f.col = sd.col[lev];
+  f.y = ygrid;
+  bool first = true;
+  auto flush = [&]() -> Status {
+    if (f.nterms == 0) return {};
+    f.accumulate = first ? (accumulate_first ? 1 : 0) : 1;
+    Status st = run_final(h, f, left, sd.n[lev], sd.nnz[lev], s);
+    first = false;
+    f.nin = 0;
+    f.nterms = 0;
+    return st;
+  };
+  for (size_t c = 0; c < chains.size(); ++c) {
+    const Chain& ch = chains[c];
+    if (f.nin == kFinalIn || f.nterms + (int)ch.terms.size() > kFinalTerms) {
+      Status st = flush();
+      if (st.code) return st;
+    }
+    int slot = f.nin++;
+    f.in[slot] = in_of((int)c);
+    for (int t : ch.terms) {
+      if (f.nterms == kFinalTerms) {
+        Status st = flush();
+        if (st.code) return st;
+        slot = f.nin++;
+        f.in[slot] = in_of((int)c);
+      }
+      const Term& tm = p.terms[t];
+      f.tin[f.nterms] = slot;
+      f.val[f.nterms] = sd.vals<T>().fac[left ? tm.x : tm.v][lev];
+      for (int a = 0; a < 2; ++a)
+        for (int q = 0; q < 2; ++q) f.tau[f.nterms][a * 2 + q] = (T)tm.tau[a][q];
+      f.nterms++;
+    }
+  }
+  return flush();
+}
+
+template <typename T, typename InOf>
+Status finals(Handle& h, const Plan& p, const std::vector<Chain>& chains, bool left, int i, InOf in_of,
+              bool accumulate_first, T* y, cudaStream_t s) {
+  return finals_on<T>(h, p, chains, left, h.n1[i], h.n2[i], left ? i : h.L - i, in_of, accumulate_first,
+                      y + h.off[i], s);
+}
+
 }  // namespace
 
 template <typename T>
 Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s) {
-  Status st = ensure_bufs<T>(h);
+  T* pool;
+  long long M;
+  Status st = ensure_pool<T>(h, p, &pool, &M);
   if (st.code) return st;
-  Handle::Bufs& b = bufs<T>(h);
-  T* S = (T*)b.S;
-  T* Z = (T*)b.Z;
-  T* TP = (T*)b.TP;
-  T* tmp = (T*)b.tmp;
   const int L = h.L;
-  SG_CU(vec_fill<T>(y, h.n_coeffs, (T)0, s));
-  // ---- branch A: sources with l1' <= l1 (diagonal included)
-  for (const Chain& c : p.A) {
-    // first factor: right (V) if by_v, else the fused multi-term right stage
-    if (c.by_v) st = stage<T>(h, p.terms, c, true, false, u, S, 0, L + 1, false, s);
-    else st = stage<T>(h, p.terms, c, false, false, u, S, 0, L + 1, false, s);
-    if (st.code) return st;
-    for (int i = 1; i <= L; ++i) {
-      // tmp = R2(S_{i-1}): restrict dim 2 from v-level L-i+1 to L-i
-      const int lv = L - i;
-      st = transfer<T>(h, false, h.V.R_rowptr[lv], h.V.R_col[lv], h.V.vals<T>().R[lv], h.V.n[lv], h.V.R_nnz[lv],
-                       S + h.off[i - 1], nullptr, tmp,
-                       h.n1[i - 1], h.n2[i - 1], h.n1[i - 1], h.V.n[lv], false, (T)1, s);
-      if (st.code) return st;
-      // S_i += P1(tmp): prolong dim 1 from x-level i-1 to i
-      st = transfer<T>(h, true, h.X.E_rowptr[i - 1], h.X.E_col[i - 1], h.X.vals<T>().E[i - 1], h.X.n[i],
-                       h.X.E_nnz[i - 1], tmp, nullptr,
-                       S + h.off[i], h.n1[i - 1], h.V.n[lv], h.n1[i], h.n2[i], true, (T)1, s);
+  const int G = kChainMax<T>();
+  const int nA = (int)p.A.size(), nB = (int)p.B.size();
+  auto slotA = [&](int c, int par) { return pool + (size_t)(2 * c + par) * M; };
+  auto slotT = [&](int c, int par) { return pool + (size_t)(3 * c + par) * M; };
+  auto slotTP = [&](int c) { return pool + (size_t)(3 * c + 2) * M; };
+  // ---- branch A (sources l1' <= l1): chains by the v factor
+  for (int i = 0; i <= L; ++i) {
+    const int lv = L - i;
+    for (int c0 = 0; c0 < nA; c0 += G) {
+      ChainArgs<T> a;
+      a.n1 = h.n1[i];
+      a.n2 = h.n2[i];
+      a.nchains = std::min(G, nA - c0);
+      a.has_prev = i > 0;
+      a.U = u + h.off[i];
+      a.f_rowptr = h.V.rowptr[lv];
+      a.f_col = h.V.col[lv];
+      double mb = csr_bytes<T>(h.V.n[lv], h.V.nnz[lv], a.nchains);
+      for (int g = 0; g < a.nchains; ++g) {
+        a.f_val[g] = h.V.vals<T>().fac[p.A[c0 + g].first][lv];
+        a.out[g] = slotA(c0 + g, i & 1);
+        a.prev[g] = i > 0 ? slotA(c0 + g, (i - 1) & 1) : nullptr;
+      }
+      if (i > 0) {
+        a.n1_prev = h.n1[i - 1];
+        a.n2_prev = h.n2[i - 1];
+        a.t1_rowptr = h.X.E_rowptr[i - 1];
+        a.t1_col = h.X.E_col[i - 1];
+        a.t1_val = h.X.vals<T>().E[i - 1];
+        a.t2_rowptr = h.V.R_rowptr[lv];
+        a.t2_col = h.V.R_col[lv];
+        a.t2_val = h.V.vals<T>().R[lv];
+        mb += csr_bytes<T>(h.X.n[i], h.X.E_nnz[i - 1], 1) + csr_bytes<T>(h.V.n[lv], h.V.R_nnz[lv], 1);
+      }
+      st = run_chain(h, a, true, s, mb);
       if (st.code) return st;
     }
-    if (c.by_v) st = stage<T>(h, p.terms, c, false, true, S, y, 0, L + 1, true, s);
-    else st = stage<T>(h, p.terms, c, true, true, S, y, 0, L + 1, true, s);
+    st = finals<T>(h, p, p.A, true, i, [&](int c) { return (const T*)slotA(c, i & 1); }, false, y, s);
     if (st.code) return st;
   }
-  // ---- branch B: sources with l1' > l1
+  // ---- branch B (sources l1' > l1): chains by the x factor
   if (L >= 1) {
-    for (const Chain& c : p.B) {
-      if (c.by_v) st = stage<T>(h, p.terms, c, false, true, u, Z, 1, L + 1, false, s);
-      else st = stage<T>(h, p.terms, c, true, true, u, Z, 1, L + 1, false, s);
-      if (st.code) return st;
-      for (int i = L - 1; i >= 0; --i) {
-        // tmp = P2(Z_{i+1} + T'_{i+1}): prolong dim 2 from v-level L-i-1 to L-i
-        const int lvc = L - i - 1;
-        st = transfer<T>(h, false, h.V.E_rowptr[lvc], h.V.E_col[lvc], h.V.vals<T>().E[lvc], h.V.n[lvc + 1],
-                         h.V.E_nnz[lvc], Z + h.off[i + 1],
-                         (i + 1 < L) ? TP + h.off[i + 1] : nullptr, tmp, h.n1[i + 1], h.n2[i + 1], h.n1[i + 1],
-                         h.V.n[L - i], false, (T)1, s);
-        if (st.code) return st;
-        // T'_i = R1(tmp): restrict dim 1 from x-level i+1 to i
-        st = transfer<T>(h, true, h.X.R_rowptr[i], h.X.R_col[i], h.X.vals<T>().R[i], h.X.n[i], h.X.R_nnz[i], tmp,
-                         nullptr, TP + h.off[i],
-                         h.n1[i + 1], h.V.n[L - i], h.n1[i], h.n2[i], false, (T)1, s);
+    for (int i = L; i >= 0; --i) {
+      for (int c0 = 0; c0 < nB; c0 += G) {
+        ChainArgs<T> a;
+        a.n1 = h.n1[i];
+        a.n2 = h.n2[i];
+        a.nchains = std::min(G, nB - c0);
+        a.has_prev = i < L;
+        a.U = u + h.off[i];
+        a.f_rowptr = h.X.rowptr[i];
+        a.f_col = h.X.col[i];
+        double mb = csr_bytes<T>(h.X.n[i], h.X.nnz[i], a.nchains);
+        for (int g = 0; g < a.nchains; ++g) {
+          a.f_val[g] = h.X.vals<T>().fac[p.B[c0 + g].first][i];
+          a.out[g] = slotT(c0 + g, i & 1);
+          a.prev[g] = i < L ? slotT(c0 + g, (i + 1) & 1) : nullptr;
+          a.strict[g] = i < L ? slotTP(c0 + g) : nullptr;
+        }
+        if (i < L) {
+          a.n1_prev = h.n1[i + 1];
+          a.n2_prev = h.n2[i + 1];
+          a.t1_rowptr = h.X.R_rowptr[i];
+          a.t1_col = h.X.R_col[i];
+          a.t1_val = h.X.vals<T>().R[i];
+          a.t2_rowptr = h.V.E_rowptr[L - i - 1];
+          a.t2_col = h.V.E_col[L - i - 1];
+          a.t2_val = h.V.vals<T>().E[L - i - 1];
+          mb += csr_bytes<T>(h.X.n[i], h.X.R_nnz[i], 1) + csr_bytes<T>(h.V.n[L - i], h.V.E_nnz[L - i - 1], 1);
+        }
+        st = run_chain(h, a, false, s, mb);
         if (st.code) return st;
       }
-      if (c.by_v) st = stage<T>(h, p.terms, c, true, false, TP, y, 0, L, true, s);
-      else st = stage<T>(h, p.terms, c, false, false, TP, y, 0, L, true, s);
-      if (st.code) return st;
+      if (i < L) {
+        st = finals<T>(h, p, p.B, false, i, [&](int c) { return (const T*)slotTP(c); }, true, y, s);
+        if (st.code) return st;
+      }
     }
   }
   return {};
@@ -244,56 +345,41 @@ Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s) {
 template Status apply_plan<double>(Handle&, const Plan&, const double*, double*, cudaStream_t);
 template Status apply_plan<float>(Handle&, const Plan&, const float*, float*, cudaStream_t);
 
-// Diagonal blocks A_{l,l} on a list of grids (l1[g], l2[g]) at once: the
-// component systems of the combination-technique preconditioner.
+// Diagonal blocks A_{l,l} on a list of grids (l1[g], l2[g]): the component
+// systems of the combination-technique preconditioner.  Per grid: one launch
+// forms W_b = u V_b^T for every distinct v factor (the chain-step kernel
+// without a transfer), then fused final launches fold all terms into y.
 template <typename T>
 Status apply_diag_grids(Handle& h, int ng, const int* l1, const int* l2, const T* const* u, T* const* y,
                         cudaStream_t s) {
-  Status st = ensure_bufs<T>(h);
+  T* pool;
+  long long M;
+  Status st = ensure_pool<T>(h, h.op, &pool, &M);
   if (st.code) return st;
-  if (ng > kMaxGrids) return {SGDG_EINVAL, "too many grids in one diagonal apply"};
-  T* W = (T*)bufs<T>(h).W;
-  std::vector<long long> woff(ng + 1, 0);
-  for (int g = 0; g < ng; ++g) woff[g + 1] = woff[g] + 2LL * h.X.n[l1[g]] * h.V.n[l2[g]];
-  if (woff[ng] > h.n_coeffs) return {SGDG_EINVAL, "diagonal apply workspace too small"};
-  for (size_t ci = 0; ci < h.op.D.size(); ++ci) {
-    const Chain& c = h.op.D[ci];
-    // stage 1 into W (right, V side), stage 2 into y (left, X side)
-    for (int pass = 0; pass < 2; ++pass) {
-      const bool left = (pass == 1);
-      const bool single = c.by_v ? (pass == 0) : (pass == 1);
-      int lev[kMaxGrids];
-      SpmmLaunch<T> a;
-      a.ngrids = ng;
-      for (int g = 0; g < ng; ++g) {
-        SpmmGrid<T>& G = a.g[g];
-        G.in = pass == 0 ? u[g] : W + woff[g];
-        G.in2 = nullptr;
-        G.out = pass == 0 ? W + woff[g] : y[g];
-        G.n1_in = G.n1_out = h.X.n[l1[g]];
-        G.n2_in = G.n2_out = h.V.n[l2[g]];
-        lev[g] = left ? l1[g] : l2[g];
+  const std::vector<Chain>& chains = h.op.A;   // by v factor
+  const int nc = (int)chains.size();
+  for (int g = 0; g < ng; ++g) {
+    const int n1 = h.X.n[l1[g]], n2 = h.V.n[l2[g]];
+    if (2LL * n1 * n2 > M) return {SGDG_EINVAL, "diagonal apply grid larger than the sweep slots"};
+    for (int c0 = 0; c0 < nc; c0 += kChainSlots) {
+      ChainArgs<T> a;
+      a.n1 = n1;
+      a.n2 = n2;
+      a.nchains = std::min(kChainSlots, nc - c0);
+      a.has_prev = 0;
+      a.U = u[g];
+      a.f_rowptr = h.V.rowptr[l2[g]];
+      a.f_col = h.V.col[l2[g]];
+      for (int c = 0; c < a.nchains; ++c) {
+        a.f_val[c] = h.V.vals<T>().fac[chains[c0 + c].first][l2[g]];
+        a.out[c] = pool + (size_t)(c0 + c) * M;
       }
-      const SideDev& sd = left ? h.X : h.V;
-      const int kind = left ? KIND_LEFT : KIND_RIGHT;
-      if (single) {
-        set_single(h, a, c.first, left, lev);
-        a.accumulate = pass == 1 ? (ci > 0) : 0;
-        double mb = 0.0;
-        for (int g = 0; g < ng; ++g) mb += pattern_bytes<T>(sd, lev[g], 1);
-        SG_CU(run_spmm(h, left, a, s, kind, mb));
-      } else {
-        const int nt = (int)c.terms.size();
-        for (int t0 = 0; t0 < nt; t0 += kMaxTerms) {
-          int t1 = std::min(nt, t0 + kMaxTerms);
-          set_terms(h, a, h.op.terms, c.terms, t0, t1, left, lev, ng);
-          a.accumulate = (t0 > 0) ? 1 : (pass == 1 ? (ci > 0) : 0);
-          double mb = 0.0;
-          for (int g = 0; g < ng; ++g) mb += pattern_bytes<T>(sd, lev[g], t1 - t0);
-          SG_CU(run_spmm(h, left, a, s, kind, mb));
-        }
-      }
+      st = run_chain(h, a, true, s, csr_bytes<T>(n2, h.V.nnz[l2[g]], a.nchains));
+      if (st.code) return st;
     }
+    st = finals_on<T>(h, h.op, chains, true, n1, n2, l1[g], [&](int c) { return (const T*)(pool + (size_t)c * M); },
+                      false, y[g], s);
+    if (st.code) return st;
   }
   return {};
 }
@@ -336,5 +422,42 @@ Status nodal_eval(Handle& h, const double* u, double* out, cudaStream_t s) {
   }
   return {};
 }
+
+template <typename T>
+Status autotune(Handle& h, const T* u, T* y, cudaStream_t s) {
+  const int cand[] = {1, 2, 4, 8};
+  std::map<long long, std::pair<float, int>> best;
+  const bool prof_was = h.prof;
+  for (int c : cand) {
+    h.force_ch = c;
+    for (auto& k : h.kev) { cudaEventDestroy(k.e0); cudaEventDestroy(k.e1); }
+    h.kev.clear();
+    h.prof = true;
+    Status st = apply_plan<T>(h, h.op, u, y, s);
+    h.prof = false;
+    if (st.code) { h.force_ch = 0; h.prof = prof_was; return st; }
+    SG_CU(cudaStreamSynchronize(s));
+    std::map<long long, float> tot;
+    for (auto& k : h.kev) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, k.e0, k.e1);
+      if (k.site >= 0) tot[k.site] += ms;
+      cudaEventDestroy(k.e0);
+      cudaEventDestroy(k.e1);
+    }
+    h.kev.clear();
+    for (auto& kv : tot) {
+      auto it = best.find(kv.first);
+      if (it == best.end() || kv.second < it->second.first) best[kv.first] = {kv.second, c};
+    }
+  }
+  h.force_ch = 0;
+  h.prof = prof_was;
+  for (auto& kv : best) h.tuned_ch[kv.first] = kv.second.second;
+  return {};
+}
+
+template Status autotune<double>(Handle&, const double*, double*, cudaStream_t);
+template Status autotune<float>(Handle&, const float*, float*, cudaStream_t);
 
 }  // namespace sgdg

@@ -163,6 +163,9 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
       eval_fn(fns, id, pts, d, tmp);
       for (size_t i = 0; i < wprod.size(); ++i) wprod[i] *= tmp[i];
     }
+    // element matrices in parallel, then one ordered scatter: the assembled
+    // values do not depend on the thread count (bit-reproducible set-up)
+    std::vector<double> Kall((size_t)nc * d1 * d1, 0.0);
 #pragma omp parallel for schedule(static)
     for (int e = 0; e < nc; ++e) {
       if (!keep[e]) continue;
@@ -201,13 +204,14 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
           }
         }
       }
+      for (int i = 0; i < d1; ++i)
+        for (int j = 0; j < d1; ++j) Kall[((size_t)e * d1 + i) * d1 + j] = Ke[i][j];
+    }
+    for (int e = 0; e < nc; ++e) {
+      if (!keep[e]) continue;
       const int* cv = &lv.cells[(size_t)e * d1];
       for (int i = 0; i < d1; ++i)
-        for (int j = 0; j < d1; ++j) {
-          int pos = find_pos(P, cv[i], cv[j]);
-#pragma omp atomic
-          A.val[pos] += Ke[i][j];
-        }
+        for (int j = 0; j < d1; ++j) A.val[find_pos(P, cv[i], cv[j])] += Kall[((size_t)e * d1 + i) * d1 + j];
     }
   } else {
     // boundary faces on one side

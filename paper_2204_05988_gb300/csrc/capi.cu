@@ -3,23 +3,32 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <thread>
 
 #include "handle.h"
 
 namespace sgdg {
 
+static std::mutex& registry_mutex() {
+  static std::mutex m;
+  return m;
+}
+
+// callers hold registry_mutex()
 static std::vector<void*>& registry(Handle* h) {
   static std::map<Handle*, std::vector<void*>> reg;
   return reg[h];
 }
 
 // Every device allocation of a handle goes through here and is released in
-// sgdg_destroy.
+// sgdg_destroy.  Batch members allocate lazily from their own host threads.
 cudaError_t dev_alloc(Handle& h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMalloc(p, bytes);
   if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(registry_mutex());
     h.device_bytes += bytes;
     registry(&h).push_back(*p);
   }
@@ -106,9 +115,10 @@ std::vector<Chain> make_chains(const std::vector<Term>& terms, bool by_v) {
 void make_plan(Plan& p, const std::vector<Term>& terms) {
   p.terms = terms;
   std::vector<Chain> cv = make_chains(terms, true), cx = make_chains(terms, false);
-  p.A = cv.size() <= cx.size() ? cv : cx;
-  p.B = cx.size() <= cv.size() ? cx : cv;
-  p.D = p.A;
+  // the sweep applies V first in branch A and X first in branch B
+  p.A = cv;
+  p.B = cx;
+  p.D = cv.size() <= cx.size() ? cv : cx;
 }
 
 struct ErrStore {
@@ -162,6 +172,18 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   };
   h.X.mass = find_or_add(h.tt.xf);
   h.V.mass = find_or_add(h.tt.vf);
+  // the sweep kernels keep one matrix row of at most 8 entries in registers
+  for (const Hierarchy* hi : {&hx, &hv}) {
+    auto maxrow = [](const Csr& A) {
+      int m = 0;
+      for (int i = 0; i < A.nrows; ++i) m = std::max(m, A.rowptr[i + 1] - A.rowptr[i]);
+      return m;
+    };
+    for (const MeshLevel& lv : hi->lev)
+      if (maxrow(lv.pattern) > 8) return {SGDG_EINVAL, "P1 pattern rows longer than 8 entries"};
+    for (const Csr& R : hi->Rt)
+      if (maxrow(R) > 8) return {SGDG_EINVAL, "restriction rows longer than 8 entries"};
+  }
   SG_ST(upload_side(h, hx, h.X));
   SG_ST(upload_side(h, hv, h.V));
   for (int side = 0; side < 2; ++side) {
@@ -263,8 +285,11 @@ void sgdg_destroy(void* hp) {
   cudaSetDevice(h->cfg.device);
   cudaDeviceSynchronize();
   solver_free(*h);
-  for (void* p : registry(h)) cudaFree(p);
-  registry(h).clear();
+  {
+    std::lock_guard<std::mutex> lk(registry_mutex());
+    for (void* p : registry(h)) cudaFree(p);
+    registry(h).clear();
+  }
   delete h;
 }
 
@@ -436,6 +461,141 @@ sgdg_status sgdg_get_end_value(const void* hp, double* dst, int on_device) {
   cudaError_t e = cudaMemcpy(dst, h->U_end, sizeof(double) * h->n_spatial,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
   return e == cudaSuccess ? SGDG_OK : SGDG_ECUDA;
+}
+
+sgdg_status sgdg_autotune(void* hp, const void* u, void* y, int prec, void* stream) {
+  if (!hp || !u || !y) return fail((Handle*)hp, {SGDG_EINVAL, "null argument"});
+  Handle* h = (Handle*)hp;
+  Status st;
+  if (prec == SGDG_FP64) st = autotune<double>(*h, (const double*)u, (double*)y, (cudaStream_t)stream);
+  else if (prec == SGDG_MIXED_FP32) st = autotune<float>(*h, (const float*)u, (float*)y, (cudaStream_t)stream);
+  else st = {SGDG_EINVAL, "unknown precision"};
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+namespace {
+struct Batch {
+  std::vector<Handle*> m;
+  struct Graph {
+    std::vector<const void*> u;
+    std::vector<void*> y;
+    int prec;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t cap = nullptr;
+};
+}  // namespace
+
+sgdg_status sgdg_batch_create(int n, void* const* members, void** out) {
+  if (n < 1 || !members || !out) return fail(nullptr, {SGDG_EINVAL, "bad batch arguments"});
+  Batch* b = new Batch();
+  for (int k = 0; k < n; ++k) {
+    if (!members[k]) {
+      delete b;
+      return fail(nullptr, {SGDG_EINVAL, "null batch member"});
+    }
+    b->m.push_back((Handle*)members[k]);
+  }
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return fail(nullptr, {SGDG_ECUDA, "batch stream"});
+  }
+  *out = b;
+  return SGDG_OK;
+}
+
+void sgdg_batch_destroy(void* bp) {
+  if (!bp) return;
+  Batch* b = (Batch*)bp;
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+sgdg_status sgdg_batch_apply(void* bp, const void* const* u, void* const* y, int prec, void* stream) {
+  if (!bp || !u || !y) return fail(nullptr, {SGDG_EINVAL, "null argument"});
+  if (prec != SGDG_FP64 && prec != SGDG_MIXED_FP32) return fail(nullptr, {SGDG_EINVAL, "unknown precision"});
+  Batch* b = (Batch*)bp;
+  const size_t n = b->m.size();
+  for (auto& g : b->graphs) {
+    bool same = g.prec == prec;
+    for (size_t k = 0; same && k < n; ++k) same = g.u[k] == u[k] && g.y[k] == y[k];
+    if (same) {
+      if (cudaGraphLaunch(g.exec, (cudaStream_t)stream) != cudaSuccess)
+        return fail(nullptr, {SGDG_ECUDA, "batch graph launch"});
+      return SGDG_OK;
+    }
+  }
+  // eager pass: allocates every lazily created buffer before the capture
+  auto run_all = [&](cudaStream_t s) -> Status {
+    for (size_t k = 0; k < n; ++k) {
+      Status st = prec == SGDG_FP64
+                      ? apply_plan<double>(*b->m[k], b->m[k]->op, (const double*)u[k], (double*)y[k], s)
+                      : apply_plan<float>(*b->m[k], b->m[k]->op, (const float*)u[k], (float*)y[k], s);
+      if (st.code) return st;
+    }
+    return {};
+  };
+  Status st = run_all(b->cap);
+  if (st.code) return fail(nullptr, st);
+  if (cudaStreamSynchronize(b->cap) != cudaSuccess) return fail(nullptr, {SGDG_ECUDA, "batch eager apply"});
+  bool prof[64] = {};
+  for (size_t k = 0; k < n && k < 64; ++k) { prof[k] = b->m[k]->prof; b->m[k]->prof = false; }
+  if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return fail(nullptr, {SGDG_ECUDA, "begin capture"});
+  st = run_all(b->cap);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(b->cap, &graph);
+  for (size_t k = 0; k < n && k < 64; ++k) b->m[k]->prof = prof[k];
+  if (st.code || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(nullptr, st.code ? st : Status{SGDG_ECUDA, "end capture"});
+  }
+  Batch::Graph g;
+  g.u.assign(u, u + n);
+  g.y.assign(y, y + n);
+  g.prec = prec;
+  ce = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return fail(nullptr, {SGDG_ECUDA, "graph instantiate"});
+  b->graphs.push_back(g);
+  if (cudaGraphLaunch(g.exec, (cudaStream_t)stream) != cudaSuccess)
+    return fail(nullptr, {SGDG_ECUDA, "batch graph launch"});
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_batch_advance(void* bp, sgdg_strip_stats* per_member) {
+  if (!bp) return fail(nullptr, {SGDG_EINVAL, "null batch"});
+  Batch* b = (Batch*)bp;
+  const size_t n = b->m.size();
+  std::vector<Status> res(n);
+  std::vector<sgdg_strip_stats> st(n);
+  std::vector<std::thread> th;
+  for (size_t k = 0; k < n; ++k) {
+    th.emplace_back([&, k]() {
+      Handle& h = *b->m[k];
+      cudaSetDevice(h.cfg.device);
+      cudaStream_t s;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        res[k] = {SGDG_ECUDA, "member stream"};
+        return;
+      }
+      res[k] = advance_strip(h, s, &st[k]);
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    });
+  }
+  for (auto& t : th) t.join();
+  sgdg_status first = SGDG_OK;
+  for (size_t k = 0; k < n; ++k) {
+    if (per_member) per_member[k] = st[k];
+    if (res[k].code && first == SGDG_OK) {
+      first = res[k].code;
+      fail(b->m[k], res[k]);
+    }
+  }
+  return first;
 }
 
 static void drop_events(Handle* h) {

@@ -25,7 +25,8 @@ struct SpmmGrid {
   const int* rowptr;
   const int* col;
   const T* val[kMaxTerms];
-  int block0;          // first block of this grid
+  int block0;          // first block of this grid (set by the launcher)
+  int ch;              // rows of k1 per thread (set by the launcher)
 };
 
 template <typename T>

@@ -1,6 +1,7 @@
 // The library handle: host description + device-resident data of one problem.
 #pragma once
 
+#include <map>
 #include <memory>
 
 #include "device.h"
@@ -24,9 +25,12 @@ struct SideDev {
   SideValues<double> v64;
   SideValues<float> v32;
   template <typename T> SideValues<T>& vals();
+  template <typename T> const SideValues<T>& vals() const;
 };
 template <> inline SideValues<double>& SideDev::vals<double>() { return v64; }
 template <> inline SideValues<float>& SideDev::vals<float>() { return v32; }
+template <> inline const SideValues<double>& SideDev::vals<double>() const { return v64; }
+template <> inline const SideValues<float>& SideDev::vals<float>() const { return v32; }
 
 // A grouping of terms that share the factor applied first in a sweep branch.
 struct Chain {
@@ -58,6 +62,7 @@ struct Handle {
   struct Bufs {
     void* S = nullptr; void* Z = nullptr; void* TP = nullptr; void* tmp = nullptr; void* W = nullptr;
     void* cvt_in = nullptr; void* cvt_out = nullptr;
+    void* pool = nullptr; long long pool_elems = 0;   // sweep chain states
   } b64, b32;
   long long tmp_elems = 0;
   // host copies of the u0 load vectors per level (for set_initial)
@@ -75,13 +80,20 @@ struct Handle {
   // one is bracketed by CUDA events and its algorithmic bytes recorded
   long long launches = 0;
   bool prof = false;
-  struct KEvent { int kind; double bytes; cudaEvent_t e0, e1; };
+  struct KEvent { int kind; double bytes; cudaEvent_t e0, e1; long long site; };
   std::vector<KEvent> kev;
+  // autotuner: rows-per-thread choice per launch site (kind and grid shape);
+  // force_ch > 0 overrides every site while tuning
+  std::map<long long, int> tuned_ch;
+  int force_ch = 0;
   ~Handle();
 };
 
 // kinds of SpMM launches for the per-kernel statistics
-enum { KIND_LEFT = 0, KIND_RIGHT = 1, KIND_XFER_LEFT = 2, KIND_XFER_RIGHT = 3, KIND_COUNT = 4 };
+enum {
+  KIND_LEFT = 0, KIND_RIGHT = 1, KIND_XFER_LEFT = 2, KIND_XFER_RIGHT = 3,
+  KIND_CHAIN_A = 4, KIND_CHAIN_B = 5, KIND_FINAL_LEFT = 6, KIND_FINAL_RIGHT = 7, KIND_COUNT = 8
+};
 
 // Launch a grouped SpMM (left or right) with accounting.  mat_bytes: bytes of
 // the CSR pattern and value arrays the launch reads.
@@ -97,6 +109,11 @@ template <typename T>
 Status apply_diag_grids(Handle& h, int ng, const int* l1, const int* l2, const T* const* u, T* const* y,
                         cudaStream_t s);
 Status nodal_eval(Handle& h, const double* u, double* out, cudaStream_t s);
+
+// Time candidate rows-per-thread settings of every sweep launch site on live
+// applies of u and keep the fastest per site.
+template <typename T>
+Status autotune(Handle& h, const T* u, T* y, cudaStream_t s);
 
 Status solver_init(Handle& h);
 Status ct_precondition(Handle& h, const double* r, double* z, cudaStream_t s, int* inner_its);

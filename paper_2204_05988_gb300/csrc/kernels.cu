@@ -63,82 +63,137 @@ __device__ __forceinline__ void store_terms(const SpmmLaunch<T>& a, T* out, cons
   }
 }
 
+// Thread mapping (both kernels): virtual thread v over [0, nchunk * n2), with
+// k2 = v % n2 (consecutive threads -> consecutive k2: coalesced 8/16 B loads
+// and stores) and rows k1 in [c * ch, c * ch + ch), c = v / n2.  One 32-bit
+// division per thread; the loop over ch rows reuses the matrix row (right) or
+// the neighbouring input rows through L1 (left).
 template <typename T, int NT>
 __global__ void __launch_bounds__(kThreads) k_left(const __grid_constant__ SpmmLaunch<T> a) {
   using T2 = typename V2<T>::type;
   const int gi = find_grid(a);
   const SpmmGrid<T>& g = a.g[gi];
-  const long long e = (long long)(blockIdx.x - g.block0) * kThreads + threadIdx.x;
-  const long long total = (long long)g.n1_out * g.n2_out;
-  if (e >= total) return;
-  const int n2 = g.n2_out;
-  const int k1 = (int)(e / n2);
-  const int k2 = (int)(e - (long long)k1 * n2);
-  T acc[kMaxTerms][2];
+  const unsigned v = (unsigned)(blockIdx.x - g.block0) * kThreads + threadIdx.x;
+  const unsigned n2 = (unsigned)g.n2_out;
+  const unsigned c = v / n2;
+  const unsigned k2 = v - c * n2;
+  const int r0 = (int)c * g.ch;
+  if (r0 >= g.n1_out) return;
+  const int r1 = min(r0 + g.ch, g.n1_out);
+  const T2* in = reinterpret_cast<const T2*>(g.in) + k2;
+  const T2* in2 = g.in2 ? reinterpret_cast<const T2*>(g.in2) + k2 : nullptr;
+  for (int k1 = r0; k1 < r1; ++k1) {
+    T acc[kMaxTerms][2];
 #pragma unroll
-  for (int t = 0; t < kMaxTerms; ++t) acc[t][0] = acc[t][1] = 0;
-  const int p0 = g.rowptr[k1], p1 = g.rowptr[k1 + 1];
-  const T2* in = reinterpret_cast<const T2*>(g.in);
-  const T2* in2 = reinterpret_cast<const T2*>(g.in2);
-  for (int p = p0; p < p1; ++p) {
-    const long long j = g.col[p];
-    T2 u = in[j * n2 + k2];
-    if (in2) {
-      T2 w = in2[j * n2 + k2];
-      u.x += w.x;
-      u.y += w.y;
-    }
+    for (int t = 0; t < kMaxTerms; ++t) acc[t][0] = acc[t][1] = 0;
+    const int p0 = __ldg(g.rowptr + k1), p1 = __ldg(g.rowptr + k1 + 1);
+    for (int p = p0; p < p1; ++p) {
+      const size_t j = (size_t)__ldg(g.col + p) * n2;
+      T2 u = in[j];
+      if (in2) {
+        const T2 w = in2[j];
+        u.x += w.x;
+        u.y += w.y;
+      }
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const T v = g.val[t][p];
-      acc[t][0] += v * u.x;
-      acc[t][1] += v * u.y;
+      for (int t = 0; t < NT; ++t) {
+        const T vv = __ldg(g.val[t] + p);
+        acc[t][0] += vv * u.x;
+        acc[t][1] += vv * u.y;
+      }
     }
+    store_terms(a, g.out + 2 * ((size_t)k1 * n2 + k2), acc);
   }
-  store_terms(a, g.out + 2 * e, acc);
 }
+
+constexpr int kRowCache = 8;   // matrix entries per row held in registers
 
 template <typename T, int NT>
 __global__ void __launch_bounds__(kThreads) k_right(const __grid_constant__ SpmmLaunch<T> a) {
   using T2 = typename V2<T>::type;
+  constexpr int NC = (NT <= 4) ? NT : 0;   // terms whose row values stay in registers
   const int gi = find_grid(a);
   const SpmmGrid<T>& g = a.g[gi];
-  const long long e = (long long)(blockIdx.x - g.block0) * kThreads + threadIdx.x;
-  const long long total = (long long)g.n1_out * g.n2_out;
-  if (e >= total) return;
-  const int n2 = g.n2_out;
-  const int k1 = (int)(e / n2);
-  const int k2 = (int)(e - (long long)k1 * n2);
-  T acc[kMaxTerms][2];
+  const unsigned v = (unsigned)(blockIdx.x - g.block0) * kThreads + threadIdx.x;
+  const unsigned n2 = (unsigned)g.n2_out;
+  const unsigned c = v / n2;
+  const unsigned k2 = v - c * n2;
+  const int r0 = (int)c * g.ch;
+  if (r0 >= g.n1_out) return;
+  const int r1 = min(r0 + g.ch, g.n1_out);
+  const int p0 = __ldg(g.rowptr + k2), p1 = __ldg(g.rowptr + k2 + 1);
+  const int nz = p1 - p0;
+  int cols[kRowCache];
+  T vals[NC > 0 ? NC : 1][kRowCache];
 #pragma unroll
-  for (int t = 0; t < kMaxTerms; ++t) acc[t][0] = acc[t][1] = 0;
-  const int p0 = g.rowptr[k2], p1 = g.rowptr[k2 + 1];
-  const T2* in = reinterpret_cast<const T2*>(g.in) + (long long)k1 * g.n2_in;
-  const T2* in2 = g.in2 ? reinterpret_cast<const T2*>(g.in2) + (long long)k1 * g.n2_in : nullptr;
-  for (int p = p0; p < p1; ++p) {
-    const int j = g.col[p];
-    T2 u = in[j];
-    if (in2) {
-      T2 w = in2[j];
-      u.x += w.x;
-      u.y += w.y;
-    }
+  for (int q = 0; q < kRowCache; ++q) {
+    cols[q] = (q < nz) ? __ldg(g.col + p0 + q) : 0;
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const T v = g.val[t][p];
-      acc[t][0] += v * u.x;
-      acc[t][1] += v * u.y;
-    }
+    for (int t = 0; t < NC; ++t) vals[t][q] = (q < nz) ? __ldg(g.val[t] + p0 + q) : (T)0;
   }
-  store_terms(a, g.out + 2 * e, acc);
+  const size_t n2i = (size_t)g.n2_in;
+  for (int k1 = r0; k1 < r1; ++k1) {
+    const T2* in = reinterpret_cast<const T2*>(g.in) + (size_t)k1 * n2i;
+    const T2* in2 = g.in2 ? reinterpret_cast<const T2*>(g.in2) + (size_t)k1 * n2i : nullptr;
+    T acc[kMaxTerms][2];
+#pragma unroll
+    for (int t = 0; t < kMaxTerms; ++t) acc[t][0] = acc[t][1] = 0;
+#pragma unroll
+    for (int q = 0; q < kRowCache; ++q) {
+      if (q < nz) {
+        T2 u = in[cols[q]];
+        if (in2) {
+          const T2 w = in2[cols[q]];
+          u.x += w.x;
+          u.y += w.y;
+        }
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          const T vv = (t < NC) ? vals[t < NC ? t : 0][q] : __ldg(g.val[t] + p0 + q);
+          acc[t][0] += vv * u.x;
+          acc[t][1] += vv * u.y;
+        }
+      }
+    }
+    for (int p = p0 + kRowCache; p < p1; ++p) {   // rows longer than the register cache
+      const int j = __ldg(g.col + p);
+      T2 u = in[j];
+      if (in2) {
+        const T2 w = in2[j];
+        u.x += w.x;
+        u.y += w.y;
+      }
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const T vv = __ldg(g.val[t] + p);
+        acc[t][0] += vv * u.x;
+        acc[t][1] += vv * u.y;
+      }
+    }
+    store_terms(a, g.out + 2 * ((size_t)k1 * n2 + k2), acc);
+  }
+}
+
+// rows per thread: enough threads to fill the GPU several times over, at most
+// 8 rows per thread
+inline int rows_per_thread(long long n1, long long n2) {
+  const long long want_threads = 152LL * 2048 * 4;
+  long long ch = (n1 * n2 + want_threads - 1) / want_threads;
+  if (ch < 1) ch = 1;
+  if (ch > 8) ch = 8;
+  if (ch > n1) ch = n1;
+  return (int)ch;
 }
 
 template <typename T>
 int assign_blocks(SpmmLaunch<T>& a) {
   int b = 0;
   for (int i = 0; i < a.ngrids; ++i) {
-    a.g[i].block0 = b;
-    long long tot = (long long)a.g[i].n1_out * a.g[i].n2_out;
+    SpmmGrid<T>& g = a.g[i];
+    g.block0 = b;
+    g.ch = rows_per_thread(g.n1_out, g.n2_out);
+    const long long nchunk = (g.n1_out + g.ch - 1) / g.ch;
+    const long long tot = nchunk * g.n2_out;
     b += (int)((tot + kThreads - 1) / kThreads);
   }
   return b;

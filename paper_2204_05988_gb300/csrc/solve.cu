@@ -427,9 +427,15 @@ Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st) {
   double hcol[kMaxKrylov + 1], y[kMaxKrylov];
   int total = 0;
   Status res{};
+  // mixed mode: one restart cycle is one refinement step; it stops once its
+  // FP32-level Krylov estimate has gained kRefineGain (the FP32 apply bounds
+  // what one cycle can resolve), then the FP64 residual restarts it
+  const bool mixed = h.cfg.precision == SGDG_MIXED_FP32;
+  const double kRefineGain = 1e-4;
   while (beta > tol && total < h.cfg.max_outer && bnorm > 0.0) {
     G.start(beta);
     SG_CU(vec_axpby<double>(n, 1.0 / beta, r, 0.0, O.V, s));
+    const double cycle_tol = mixed ? std::max(tol, kRefineGain * beta) : tol;
     int k = 0;
     for (int j = 0; j < O.m && total < h.cfg.max_outer; ++j) {
       double* Vj = O.V + (long long)j * n;
@@ -442,7 +448,7 @@ Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st) {
       double est = G.add(j, hcol);
       k = j + 1;
       total++;
-      if (est <= tol || hcol[j + 1] == 0.0) break;
+      if (est <= cycle_tol || hcol[j + 1] == 0.0) break;
     }
     G.solve(k, y);
     SG_CU(cudaMemcpyAsync(ws.dev_dots, y, sizeof(double) * k, cudaMemcpyHostToDevice, s));

@@ -173,6 +173,31 @@ def periodic_advection_1d(L: int, r: int = 1) -> Problem:
                    beta=[Product(1.0), Product(1.0)], sigma=Product(0.0), u0=u0, exact=exact)
 
 
+def batched_4d(n: int = 48, seed: int = 0, levels=(6, 7, 8, 9), dt: float = 1.0 / 32.0,
+               n_strips: int = 16) -> List[Problem]:
+    """Many independent 4D instances with the d=1 free-streaming physics on the
+    d=2 geometry: beta = (v1, v2, 0, 0), sigma = f = g = 0, 8-triangle coarse
+    meshes, L drawn uniformly from ``levels``, u0 = exp(-|x-c|^2/(2 s))
+    exp(-|v|^2/0.1) with c ~ U[0.3, 0.7]^2 and s ~ U[0.005, 0.02] (seeded)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        L = int(rng.choice(levels))
+        c = rng.uniform(0.3, 0.7, size=2)
+        s = float(rng.uniform(0.005, 0.02))
+        ux = (lambda c0, c1, s2: (lambda p: np.exp(-((p[:, 0] - c0) ** 2 + (p[:, 1] - c1) ** 2) / s2)))(
+            float(c[0]), float(c[1]), 2.0 * s)
+        uv = lambda p: np.exp(-(p[:, 0] ** 2 + p[:, 1] ** 2) / 0.1)
+        hx = 1.0 / 2 ** (L + 1)
+        out.append(Problem(
+            name=f"batched_4d_{k}_L{L}", d=2, mesh_x=square_mesh(0.0, 1.0, 2), mesh_v=square_mesh(-1.0, 1.0, 2),
+            L=L, r=1, dt=dt, delta=hx, n_strips=n_strips,
+            beta=[Product(1.0, None, lambda p: p[:, 0]), Product(1.0, None, lambda p: p[:, 1]),
+                  Product(0.0), Product(0.0)],
+            sigma=Product(0.0), u0=[Product(1.0, ux, uv)]))
+    return out
+
+
 # ----------------------------------------------------------------------------
 # seeded random inputs
 # ----------------------------------------------------------------------------

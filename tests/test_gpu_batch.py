@@ -1,0 +1,94 @@
+"""Batching, CUDA-graph replay and the autotuner (GPU).
+
+* a batch of instances of uneven L applied through one captured CUDA graph
+  gives exactly the per-instance applies (same kernels, same order), on the
+  first (capture) call and on replays;
+* the batched concurrent strip advance reaches the same strip solutions as
+  advancing each instance alone;
+* autotuning changes only the thread mapping, never the arithmetic: applies
+  before and after are identical, and still match the oracle.
+"""
+import numpy as np
+import pytest
+
+import sgdg_workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2204_05988_gb300 as P
+    P.load_library()
+    return P
+
+
+def _batch_problems():
+    return [W.transport_2d(L=3, sigma=0.1), W.transport_2d(L=4, sigma=0.0), W.free_streaming_1d(L=5)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_graph_apply_equals_single(P, prec):
+    solvers = [P.Solver(pr) for pr in _batch_problems()]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    pc = P.SGDG_FP64 if prec == "fp64" else P.SGDG_MIXED_FP32
+    us = [torch.tensor(W.uniform_vector(s.n_coeffs, seed=40 + k), dtype=dt, device="cuda")
+          for k, s in enumerate(solvers)]
+    refs = []
+    for s, u in zip(solvers, us):
+        y = torch.empty_like(u)
+        s.apply_operator(u, y, pc)
+        refs.append(y.clone())
+    b = P.Batch(solvers)
+    ys = [torch.full_like(u, float("nan")) for u in us]
+    for rep in range(3):          # capture, then replays
+        for y in ys:
+            y.fill_(float("nan"))
+        b.apply(us, ys, pc)
+        torch.cuda.synchronize()
+        for y, r in zip(ys, refs):
+            assert torch.equal(y, r), rep
+    b.close()
+
+
+def test_batch_advance_equals_single(P):
+    probs = [W.free_streaming_1d(L=4, n_strips=1), W.transport_2d(L=3, sigma=0.1, n_strips=1)]
+    alone = []
+    for pr in probs:
+        s = P.Solver(pr, rtol=1e-10)
+        s.set_initial()
+        s.advance_strip()
+        U = np.empty(s.n_spatial)
+        s.get_end_value(U, on_device=False)
+        alone.append(U)
+    solvers = [P.Solver(pr, rtol=1e-10) for pr in probs]
+    for s in solvers:
+        s.set_initial()
+    b = P.Batch(solvers)
+    stats = b.advance()
+    for s, st, U0 in zip(solvers, stats, alone):
+        assert st.rel_residual <= 1e-10
+        U = np.empty(s.n_spatial)
+        s.get_end_value(U, on_device=False)
+        assert np.array_equal(U, U0)
+    b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_autotune_keeps_results(P, prec):
+    from oracle.operator import SparseGridOperator
+    prob = W.transport_2d(L=4, sigma=0.1)
+    s = P.Solver(prob)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    pc = P.SGDG_FP64 if prec == "fp64" else P.SGDG_MIXED_FP32
+    u = torch.tensor(W.uniform_vector(s.n_coeffs, seed=5), dtype=dt, device="cuda")
+    y0, y1, tmp = torch.empty_like(u), torch.empty_like(u), torch.empty_like(u)
+    s.apply_operator(u, y0, pc)
+    s.autotune(u, tmp, pc)
+    s.apply_operator(u, y1, pc)
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y1)
+    ref = SparseGridOperator(prob).apply(u.double().cpu().numpy())
+    err = np.linalg.norm(y1.double().cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err < (1e-12 if prec == "fp64" else 1e-5)
