@@ -161,6 +161,23 @@ sgdg_status sgdg_apply_mass(void* h, const void* u, void* y, int precision, void
 /* y = A_{l,l} u on one anisotropic full grid (l1, l2) with l1 + l2 in {L-1, L}
  * (the component systems of Eq. 22); arrays [n1][n2][2] on the device. */
 sgdg_status sgdg_apply_diag(void* h, int l1, int l2, const void* u, void* y, int precision, void* stream);
+
+/* The same y = A_{l,l} u as sgdg_apply_diag, from an entry point that
+ * allocates nothing.  The paper has no counterpart: this exists for callers
+ * that may not allocate device memory when they apply the operator - code
+ * being captured into a CUDA graph (an allocation is not capturable), loops
+ * that must not pay the allocator's device-wide synchronisation, processes
+ * whose device memory belongs to another pool.  Its scratch is a static
+ * device array of SGDG_NOALLOC_SCRATCH_BYTES held by every GPU that loads the
+ * library until the process exits; grids whose intermediates
+ * (distinct v factors x n1 x n2 x 2 elements) do not fit are rejected with
+ * SGDG_EINVAL and a message naming the size and the limit.  The first call on
+ * a device looks up the array's device address; make that first call before
+ * any stream capture.  All calls share the array: calls that overlap on the
+ * GPU race.  u, y as for sgdg_apply_diag. */
+#define SGDG_NOALLOC_SCRATCH_BYTES (64u << 20)
+sgdg_status sgdg_apply_diag_noalloc(void* h, int l1, int l2, const void* u, void* y, int precision,
+                                    void* stream);
 /* z = P_CT(r): Algorithm 1's preconditioner step (component solves with the
  * configured inner iterations, restriction of the residual, combination).
  * r, z: device arrays of n_coeffs doubles. */

@@ -69,6 +69,8 @@ EXPORTS = {
     "sgdg_apply_operator_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "sgdg_apply_mass": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "sgdg_apply_diag": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "sgdg_apply_diag_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                          C.c_void_p]),
     "sgdg_ct_precondition": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_set_initial": (C.c_int, [C.c_void_p]),
     "sgdg_advance_strip": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(StripStats)]),
@@ -248,6 +250,13 @@ class Solver:
 
     def apply_diag(self, l1: int, l2: int, u, y, precision: int = SGDG_FP64, stream=None):
         self._check(self.lib.sgdg_apply_diag(self.h, l1, l2, _ptr(u), _ptr(y), precision, _stream(stream)))
+
+    def apply_diag_noalloc(self, l1: int, l2: int, u, y, precision: int = SGDG_FP64, stream=None):
+        """sgdg_apply_diag without any device allocation (static scratch of
+        SGDG_NOALLOC_SCRATCH_BYTES; for callers that may not allocate, e.g.
+        inside a CUDA graph capture)."""
+        self._check(self.lib.sgdg_apply_diag_noalloc(self.h, l1, l2, _ptr(u), _ptr(y), precision,
+                                                     _stream(stream)))
 
     def ct_precondition(self, r, z, stream=None):
         self._check(self.lib.sgdg_ct_precondition(self.h, _ptr(r), _ptr(z), _stream(stream)))
