@@ -113,6 +113,9 @@ typedef struct {
   double inner_rtol;    /* early stop of a component solve */
   int cheb_steps;       /* Chebyshev-Jacobi steps per mass inverse */
   int device;           /* CUDA device ordinal */
+  int vlasov_poisson;   /* 1: beta_v = -E(x) with E from a Poisson solve of the
+                           density (Sect. 5.3); needs a periodic Omega_x and
+                           beta[d+i] = {coef -1, fx = initial E_i, fv = NULL} */
 } sgdg_config;
 
 typedef struct {
@@ -130,6 +133,7 @@ typedef struct {
   int inner_its_total;
   int applies;                 /* full sparse-grid operator applies */
   double rel_residual;         /* true ||b - A u|| / ||b|| (FP64) */
+  double initial_rel_residual; /* the same for the initial guess */
   double seconds;
   int status;
 } sgdg_strip_stats;
@@ -197,6 +201,34 @@ sgdg_status sgdg_get_end_value(const void* h, double* dst, int on_device);
  * nodes of every component grid (prolongation from coarser grids, injection
  * from finer ones).  u, out: device arrays of n_spatial doubles. */
 sgdg_status sgdg_eval_nodal(void* h, const double* u, double* out, void* stream);
+
+/* Vlasov-Poisson field update (Sect. 5.3: "-Delta phi = -int f dv + 1",
+ * E = -grad phi; one update per strip, from U^-_{j-1}; midpoint rule).
+ * Computes rho(x) = int U^- dv as a P1 function on the finest level of
+ * Omega_x (rho of u0 before the first strip), solves the periodic P1 Poisson
+ * problem (mean of the source removed, phi of zero mean) by CG in FP64,
+ * takes E = -grad phi per finest cell, re-assembles every x factor that
+ * depends on E (finest level + Galerkin projection) and uploads it.
+ * source 0: rho from the end value of the last strip (u0 before the first
+ * strip); source 1: rho from the last strip solution at the strip midpoint
+ * (the fixed point of Sect. 5.3, with sgdg_resolve_strip).
+ * field_energy (may be NULL): 1/2 int |E|^2 dx of the new field.  Only for
+ * handles created with vlasov_poisson = 1 (else EINVAL). */
+sgdg_status sgdg_field_update(void* h, int source, double* field_energy);
+/* Re-solve the last strip with the current coefficients (same right-hand
+ * side), starting from its last solution; replaces the solution and the end
+ * value.  One step of the per-strip fixed point of Sect. 5.3. */
+sgdg_status sgdg_resolve_strip(void* h, void* stream, sgdg_strip_stats* stats);
+/* Initial guess of the next sgdg_advance_strip: 0 zero (default), 1 the
+ * previous strip's solution, 2 the array last given to sgdg_set_guess. */
+sgdg_status sgdg_set_warm_start(void* h, int mode);
+/* Copy an initial guess (device array of n_coeffs doubles) for warm-start mode 2. */
+sgdg_status sgdg_set_guess(void* h, const double* u);
+/* Number of vertices / cells of the finest level of Omega_x. */
+sgdg_status sgdg_finest_x(const void* h, int* n_vertices, int* n_cells);
+/* Last computed density rho and potential phi at the finest x vertices
+ * (lexicographic order), host arrays of n_vertices doubles. */
+sgdg_status sgdg_get_density_potential(const void* h, double* rho, double* phi);
 
 /* Autotuner (no counterpart in the paper): times candidate rows-per-thread
  * settings of every sweep launch site on live applies y = A u (device

@@ -70,17 +70,26 @@ class Factor:
     face: Tuple[int, int] = (-1, 0)             # (axis, side) for kind == 'face'
 
 
-def _weight(f: Factor, pts: np.ndarray) -> np.ndarray:
+class CellField:
+    """A function that is constant on every cell of the finest level (values in
+    the order of ``Level.cells``); used for the electric field of Sect. 5.3."""
+
+    def __init__(self, values: np.ndarray):
+        self.values = np.asarray(values, dtype=np.float64)
+
+
+def _weight(f: Factor, pts: np.ndarray, nq: int = 1) -> np.ndarray:
     w = np.full(pts.shape[0], float(f.coef))
     for fn in f.weight:
-        w = w * fn(pts)
+        w = w * (np.repeat(fn.values, nq) if isinstance(fn, CellField) else fn(pts))
     return w
 
 
 def _keep(f: Factor, centroids: np.ndarray) -> np.ndarray:
     keep = np.ones(centroids.shape[0], dtype=bool)
     for fn, c, s in f.restrict:
-        keep &= (s * c * fn(centroids)) > 0.0
+        vals = fn.values if isinstance(fn, CellField) else fn(centroids)
+        keep &= (s * c * vals) > 0.0
     return keep
 
 
@@ -93,6 +102,9 @@ def assemble_level(lev: Level, f: Factor, q: int = QUAD_Q) -> sp.csr_matrix:
         cc, cells = cc[keep], lev.cells[keep]
         if cc.shape[0] == 0:
             return sp.csr_matrix((n, n))
+        if any(isinstance(fn, CellField) for fn in f.weight):
+            f = Factor(f.kind, f.coef, tuple(CellField(fn.values[keep]) if isinstance(fn, CellField) else fn
+                                            for fn in f.weight), f.test, f.trial, (), f.face)
         v0 = cc[:, 0, :]
         J = np.transpose(cc[:, 1:, :] - v0[:, None, :], (0, 2, 1))   # columns = edges
         det = np.abs(np.linalg.det(J))
@@ -102,7 +114,7 @@ def assemble_level(lev: Level, f: Factor, q: int = QUAD_Q) -> sp.csr_matrix:
         lam = np.concatenate([1.0 - rp.sum(axis=1, keepdims=True), rp], axis=1)  # (nq, d+1)
         gref = np.vstack([-np.ones((1, d)), np.eye(d)])              # (d+1, d)
         gphys = np.einsum("cji,kj->cki", Jinv, gref)                 # (nc, d+1, d)
-        wt = _weight(f, pts.reshape(-1, d)).reshape(pts.shape[0], -1)
+        wt = _weight(f, pts.reshape(-1, d), rp.shape[0]).reshape(pts.shape[0], -1)
         wq = wt * rw[None, :] * det[:, None]                          # (nc, nq)
 
         def D(a):

@@ -44,7 +44,8 @@ class Config(C.Structure):
     _fields_ = [("mesh_x", Mesh), ("mesh_v", Mesh), ("level_L", C.c_int), ("time_degree", C.c_int),
                 ("dt", C.c_double), ("delta", C.c_double), ("precision", C.c_int), ("rtol", C.c_double),
                 ("max_outer", C.c_int), ("restart", C.c_int), ("inner_its", C.c_int),
-                ("inner_rtol", C.c_double), ("cheb_steps", C.c_int), ("device", C.c_int)]
+                ("inner_rtol", C.c_double), ("cheb_steps", C.c_int), ("device", C.c_int),
+                ("vlasov_poisson", C.c_int)]
 
 
 class Info(C.Structure):
@@ -55,7 +56,8 @@ class Info(C.Structure):
 
 class StripStats(C.Structure):
     _fields_ = [("outer_its", C.c_int), ("inner_its_total", C.c_int), ("applies", C.c_int),
-                ("rel_residual", C.c_double), ("seconds", C.c_double), ("status", C.c_int)]
+                ("rel_residual", C.c_double), ("initial_rel_residual", C.c_double), ("seconds", C.c_double),
+                ("status", C.c_int)]
 
 
 EXPORTS = {
@@ -81,6 +83,12 @@ EXPORTS = {
     "sgdg_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "sgdg_launch_count": (C.c_longlong, [C.c_void_p]),
     "sgdg_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "sgdg_field_update": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "sgdg_resolve_strip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sgdg_set_warm_start": (C.c_int, [C.c_void_p, C.c_int]),
+    "sgdg_set_guess": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sgdg_finest_x": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "sgdg_get_density_potential": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_batch_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
     "sgdg_batch_destroy": (None, [C.c_void_p]),
     "sgdg_batch_apply": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
@@ -147,7 +155,7 @@ class Solver:
 
     def __init__(self, problem, precision: int = SGDG_FP64, rtol: float = 1e-10, max_outer: int = 200,
                  restart: int = 30, inner_its: int = 20, inner_rtol: float = 1e-3, cheb_steps: int = 6,
-                 device: int = 0):
+                 device: int = 0, vlasov_poisson: bool = False):
         self.lib = load_library()
         self.problem = problem
         self._keep: List = []
@@ -167,6 +175,7 @@ class Solver:
         cfg.inner_rtol = inner_rtol
         cfg.cheb_steps = cheb_steps
         cfg.device = device
+        cfg.vlasov_poisson = int(vlasov_poisson)
         co = Coeffs()
         d = problem.d
         for p in range(4):
@@ -288,6 +297,33 @@ class Solver:
         self._check(self.lib.sgdg_kernel_stats(self.h, arr, len(KERNEL_KINDS)))
         return {KERNEL_KINDS[k]: {"launches": arr[k].launches, "ms": arr[k].ms, "bytes": arr[k].bytes}
                 for k in range(len(KERNEL_KINDS))}
+
+    def field_update(self, source: int = 0) -> float:
+        """Vlasov-Poisson field from the end value (source 0) or from the last
+        strip solution at the strip midpoint (source 1); returns 1/2 int |E|^2."""
+        e = C.c_double()
+        self._check(self.lib.sgdg_field_update(self.h, source, C.byref(e)))
+        return e.value
+
+    def resolve_strip(self, stream=None, check: bool = True) -> StripStats:
+        st = StripStats()
+        code = self.lib.sgdg_resolve_strip(self.h, _stream(stream), C.byref(st))
+        if check:
+            self._check(code)
+        return st
+
+    def set_warm_start(self, mode: int):
+        self._check(self.lib.sgdg_set_warm_start(self.h, mode))
+
+    def set_guess(self, u):
+        self._check(self.lib.sgdg_set_guess(self.h, _ptr(u)))
+
+    def density_potential(self):
+        nv, nc = C.c_int(), C.c_int()
+        self._check(self.lib.sgdg_finest_x(self.h, C.byref(nv), C.byref(nc)))
+        rho, phi = np.empty(nv.value), np.empty(nv.value)
+        self._check(self.lib.sgdg_get_density_potential(self.h, _ptr(rho), _ptr(phi)))
+        return rho, phi
 
     def autotune(self, u, y, precision: int = SGDG_MIXED_FP32, stream=None):
         self._check(self.lib.sgdg_autotune(self.h, _ptr(u), _ptr(y), precision, _stream(stream)))

@@ -142,7 +142,12 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
         for (int a = 0; a < d1; ++a)
           for (int k = 0; k < d; ++k) cen[(size_t)e * d + k] += lv.cell_coords[((size_t)e * d1 + a) * d + k] / d1;
       for (auto& rs : f.restrict_) {
-        eval_fn(fns, rs.first, cen, d, val);
+        if (const std::vector<double>* cf = fns.cell_field(rs.first)) {
+          if ((int)cf->size() != nc) return {SGDG_EINVAL, "cell field size differs from the finest cell count"};
+          val = *cf;
+        } else {
+          eval_fn(fns, rs.first, cen, d, val);
+        }
         for (int e = 0; e < nc; ++e)
           if (!(rs.second * val[e] > 0.0)) keep[e] = 0;
       }
@@ -160,6 +165,13 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
     }
     std::vector<double> wprod((size_t)nc * nq, 1.0), tmp;
     for (int id : f.wfn) {
+      if (const std::vector<double>* cf = fns.cell_field(id)) {
+        if ((int)cf->size() != nc) return {SGDG_EINVAL, "cell field size differs from the finest cell count"};
+        for (int e = 0; e < nc; ++e)
+          for (int q = 0; q < nq; ++q) wprod[(size_t)e * nq + q] *= (*cf)[e];
+        continue;
+      }
+      if (!fns.fn[id]) return {SGDG_EINVAL, "factor needs a coefficient function that is no longer available"};
       eval_fn(fns, id, pts, d, tmp);
       for (size_t i = 0; i < wprod.size(); ++i) wprod[i] *= tmp[i];
     }
@@ -224,6 +236,10 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
     simplex_rule(dv - 1, rp, rw);
     const int nq = (int)rw.size();
     std::vector<char> keep(sel.size(), 1);
+    for (auto& rs : f.restrict_)
+      if (fns.cell_field(rs.first)) return {SGDG_EINVAL, "cell fields are not supported on boundary faces"};
+    for (int id : f.wfn)
+      if (fns.cell_field(id)) return {SGDG_EINVAL, "cell fields are not supported on boundary faces"};
     if (!f.restrict_.empty() && !sel.empty()) {
       std::vector<double> cen(sel.size() * d, 0.0), val;
       for (size_t s = 0; s < sel.size(); ++s)

@@ -230,6 +230,7 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   }
   h.n_spatial = h.soff[L + 1];
   h.n_coeffs = h.off[L + 1];
+  if (cfg.vlasov_poisson) SG_ST(field_setup(h, c, hx, hv, fx));
   long long tmp = 2;
   for (int i = 1; i <= L; ++i) tmp = std::max(tmp, 2LL * h.X.n[i - 1] * h.V.n[L - i]);
   for (int i = 0; i < L; ++i) tmp = std::max(tmp, 2LL * h.X.n[i + 1] * h.V.n[L - i]);
@@ -632,6 +633,57 @@ sgdg_status sgdg_kernel_stats(void* hp, sgdg_kernel_stat* out, int n_kinds) {
 }
 
 long long sgdg_launch_count(const void* hp) { return hp ? ((const Handle*)hp)->launches : 0; }
+
+sgdg_status sgdg_field_update(void* hp, int source, double* energy) {
+  if (!hp) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  Status st = field_update(*h, source, energy);
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+sgdg_status sgdg_resolve_strip(void* hp, void* stream, sgdg_strip_stats* stats) {
+  if (!hp) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  Status st = advance_strip(*h, (cudaStream_t)stream, stats, true);
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+sgdg_status sgdg_set_warm_start(void* hp, int mode) {
+  if (!hp) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  if (mode < 0 || mode > 2) return fail(h, {SGDG_EINVAL, "warm start mode must be 0, 1 or 2"});
+  h->warm = mode;
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_set_guess(void* hp, const double* u) {
+  if (!hp || !u) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  if (!h->guess && dev_alloc(*h, (void**)&h->guess, sizeof(double) * h->n_coeffs) != cudaSuccess)
+    return fail(h, {SGDG_ENOMEM, "guess buffer"});
+  if (cudaMemcpy(h->guess, u, sizeof(double) * h->n_coeffs, cudaMemcpyDeviceToDevice) != cudaSuccess)
+    return fail(h, {SGDG_ECUDA, "guess copy"});
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_finest_x(const void* hp, int* nv, int* nc) {
+  if (!hp) return SGDG_EINVAL;
+  const Handle* h = (const Handle*)hp;
+  if (!h->field) return SGDG_EINVAL;
+  const MeshLevel& lv = h->field->hx.lev[h->L];
+  if (nv) *nv = lv.n;
+  if (nc) *nc = lv.ncells(h->d);
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_get_density_potential(const void* hp, double* rho, double* phi) {
+  if (!hp) return SGDG_EINVAL;
+  const Handle* h = (const Handle*)hp;
+  if (!h->field || h->field->rho.empty()) return SGDG_EINVAL;
+  if (rho) std::copy(h->field->rho.begin(), h->field->rho.end(), rho);
+  if (phi) std::copy(h->field->phi.begin(), h->field->phi.end(), phi);
+  return SGDG_OK;
+}
 
 sgdg_status sgdg_eval_nodal(void* hp, const double* u, double* out, void* stream) {
   if (!hp || !u || !out) return SGDG_EINVAL;

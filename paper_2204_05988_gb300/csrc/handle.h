@@ -72,7 +72,9 @@ struct Handle {
   double* U_end = nullptr;   // spatial, n_spatial
   double* u_sol = nullptr;   // last strip solution, n_coeffs
   double* rhs = nullptr;     // n_coeffs
-  bool have_initial = false, first_strip = true;
+  bool have_initial = false, first_strip = true, solved = false;
+  int warm = 0;              // initial guess of the next strip: 0 zero, 1 last solution, 2 guess
+  double* guess = nullptr;   // n_coeffs, allocated by sgdg_set_guess
   size_t device_bytes = 0;
   Workspace* ws = nullptr;      // owned; released by solver_free
   cudaStream_t cur = nullptr;
@@ -86,6 +88,19 @@ struct Handle {
   // force_ch > 0 overrides every site while tuning
   std::map<long long, int> tuned_ch;
   int force_ch = 0;
+  // Vlasov-Poisson coupling (kept only when cfg.vlasov_poisson)
+  struct Field {
+    Hierarchy hx;                              // Omega_x levels (finest level for assembly)
+    SideFns fx;                                // x function table; E ids carry cell fields
+    std::vector<std::vector<double>> E;        // E_i per finest x cell, i < d
+    std::vector<std::vector<double>> mv;       // int phi^(2)_k per v level
+    std::vector<double*> d_mv;                 // device copies
+    std::vector<double> rho0;                  // density of u0 at the finest x vertices
+    std::vector<double> rho, phi;              // last density and potential
+    Csr K, M;                                  // finest-level stiffness and mass (FP64)
+    double* d_rowsum = nullptr;                // per-grid int U dv (device, sum of n1)
+  };
+  std::unique_ptr<Field> field;
   ~Handle();
 };
 
@@ -115,9 +130,13 @@ Status nodal_eval(Handle& h, const double* u, double* out, cudaStream_t s);
 template <typename T>
 Status autotune(Handle& h, const T* u, T* y, cudaStream_t s);
 
+// Vlasov-Poisson coupling (field.cu)
+Status field_setup(Handle& h, const sgdg_coeffs& c, const Hierarchy& hx, const Hierarchy& hv, const SideFns& fx);
+Status field_update(Handle& h, int source, double* energy);
+
 Status solver_init(Handle& h);
 Status ct_precondition(Handle& h, const double* r, double* z, cudaStream_t s, int* inner_its);
-Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st);
+Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resolve = false);
 void solver_free(Handle& h);
 
 }  // namespace sgdg

@@ -57,6 +57,12 @@ Status build_hierarchy(const sgdg_mesh& m, int L, Hierarchy& h);
 struct SideFns {
   std::vector<sgdg_fn> fn;
   std::vector<void*> user;
+  // optional piecewise-constant replacement of function id k: one value per
+  // cell of the finest level (nullptr: use fn[k])
+  std::vector<const std::vector<double>*> cell;
+  const std::vector<double>* cell_field(int id) const {
+    return id < (int)cell.size() ? cell[id] : nullptr;
+  }
 };
 
 // X[i,j] = int w (D_trial phi_j)(D_test phi_i), w = product of fns (no

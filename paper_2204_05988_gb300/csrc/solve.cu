@@ -401,15 +401,17 @@ static Status apply_mixed(Handle& h, const double* z, double* w, bool force64, c
   return {};
 }
 
-Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st) {
+Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resolve) {
   auto t0 = std::chrono::steady_clock::now();
   SG_ST(solver_init(h));
   Workspace& ws = *h.ws;
   KrylovWs<double>& O = ws.outer;
   const long long n = h.n_coeffs;
   if (!h.have_initial) return {SGDG_EINVAL, "sgdg_set_initial was not called"};
-  // right-hand side: eta(t_{j-1}^+) (x) M_sg U^-_{j-1}; the first strip uses (u0, phi)
-  if (!h.first_strip) {
+  if (resolve && !h.solved) return {SGDG_EINVAL, "no strip has been solved yet"};
+  // right-hand side: eta(t_{j-1}^+) (x) M_sg U^-_{j-1}; the first strip uses (u0, phi);
+  // a re-solve keeps the right-hand side of the strip
+  if (!resolve && !h.first_strip) {
     k_expand<<<gridsz(h.n_spatial), kThreads, 0, s>>>(h.n_spatial, h.U_end, O.t0, 1.0, -1.0);
     SG_CU(cudaGetLastError());
     SG_ST(apply_plan<double>(h, h.mass, O.t0, h.rhs, s));
@@ -418,10 +420,22 @@ Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st) {
   double bnorm;
   SG_ST(vnorm<double>(h, h.rhs, n, &bnorm, s));
   double* x = h.u_sol;
-  SG_CU(vec_fill<double>(x, n, 0.0, s));
   double* r = O.t1;
-  SG_CU(cudaMemcpyAsync(r, h.rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  // initial guess: the last solution (re-solve, warm start 1), a given guess (2) or zero
+  const int mode = resolve ? 1 : h.warm;
   double beta = bnorm;
+  if (mode == 2 && !h.guess) return {SGDG_EINVAL, "warm start 2 needs sgdg_set_guess"};
+  if (mode == 2) SG_CU(cudaMemcpyAsync(x, h.guess, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  if ((mode == 1 && h.solved) || mode == 2) {
+    SG_ST(apply_plan<double>(h, h.op, x, r, s));
+    S.applies++;
+    SG_CU(vec_axpby<double>(n, 1.0, h.rhs, -1.0, r, s));
+    SG_ST(vnorm<double>(h, r, n, &beta, s));
+  } else {
+    SG_CU(vec_fill<double>(x, n, 0.0, s));
+    SG_CU(cudaMemcpyAsync(r, h.rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  S.initial_rel_residual = bnorm > 0.0 ? beta / bnorm : 0.0;
   const double tol = h.cfg.rtol * bnorm;
   static thread_local Givens G;
   double hcol[kMaxKrylov + 1], y[kMaxKrylov];
@@ -467,6 +481,7 @@ Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st) {
   SG_CU(cudaGetLastError());
   SG_CU(cudaStreamSynchronize(s));
   h.first_strip = false;
+  h.solved = true;
   S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (st) *st = S;
   if (S.status == SGDG_ENOCONV) return {SGDG_ENOCONV, "outer FGMRES reached max_outer"};

@@ -173,6 +173,32 @@ def periodic_advection_1d(L: int, r: int = 1) -> Problem:
                    beta=[Product(1.0), Product(1.0)], sigma=Product(0.0), u0=u0, exact=exact)
 
 
+def landau_4d(L: int = 8, alpha: float = 0.01, k: float = 0.5, n_strips: int = 200, dt: float = None,
+              phase: float = 0.0) -> Problem:
+    """2+2-dimensional Landau damping (Sect. 5.3): periodic x in [0, 4 pi]^2,
+    v in [-6, 6]^2 (8-triangle coarse meshes), f0 = (1 + alpha cos(k x1 +
+    phase)) exp(-|v|^2/2) / (2 pi), Vlasov beta = (v, -E(x)) with E from the
+    Poisson problem of the density; the initial E callback is zero (the first
+    field update replaces it).  dt halves per level: 1/32 at L = 8 (100 steps
+    on [0, 50] at the paper's level 5, doubled per level)."""
+    four_pi = 4.0 * np.pi
+    mx = square_mesh(0.0, four_pi, 2, periodic=True)
+    mv = square_mesh(-6.0, 6.0, 2)
+    if dt is None:
+        dt = 0.5 / 2 ** (L - 4)
+    hx = four_pi / 2 ** (L + 1)
+    hv = 12.0 / 2 ** (L + 1)
+    zero = lambda p: np.zeros(p.shape[0])
+    fx = lambda p: 1.0 + alpha * np.cos(k * p[:, 0] + phase)
+    fv = lambda p: np.exp(-(p[:, 0] ** 2 + p[:, 1] ** 2) / 2.0) / (2.0 * np.pi)
+    return Problem(
+        name=f"landau_4d_L{L}", d=2, mesh_x=mx, mesh_v=mv, L=L, r=1, dt=dt, delta=min(hx, hv),
+        n_strips=n_strips,
+        beta=[Product(1.0, None, lambda p: p[:, 0]), Product(1.0, None, lambda p: p[:, 1]),
+              Product(-1.0, zero, None), Product(-1.0, zero, None)],
+        sigma=Product(0.0), u0=[Product(1.0, fx, fv)])
+
+
 def batched_4d(n: int = 48, seed: int = 0, levels=(6, 7, 8, 9), dt: float = 1.0 / 32.0,
                n_strips: int = 16) -> List[Problem]:
     """Many independent 4D instances with the d=1 free-streaming physics on the
