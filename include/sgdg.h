@@ -220,8 +220,12 @@ sgdg_status sgdg_field_update(void* h, int source, double* field_energy);
  * value.  One step of the per-strip fixed point of Sect. 5.3. */
 sgdg_status sgdg_resolve_strip(void* h, void* stream, sgdg_strip_stats* stats);
 /* Initial guess of the next sgdg_advance_strip: 0 zero (default), 1 the
- * previous strip's solution, 2 the array last given to sgdg_set_guess. */
+ * previous strip's solution, 2 the array last given to sgdg_set_guess, 3 the
+ * linear extrapolation 2 u_{j-1} - u_{j-2} of the last two strip solutions
+ * (the previous solution while fewer than two strips are solved). */
 sgdg_status sgdg_set_warm_start(void* h, int mode);
+/* dst (device, n_coeffs doubles) = the mode-3 guess for the next strip. */
+sgdg_status sgdg_extrapolated_guess(const void* h, double* dst);
 /* Copy an initial guess (device array of n_coeffs doubles) for warm-start mode 2. */
 sgdg_status sgdg_set_guess(void* h, const double* u);
 /* Number of vertices / cells of the finest level of Omega_x. */
@@ -229,6 +233,36 @@ sgdg_status sgdg_finest_x(const void* h, int* n_vertices, int* n_cells);
 /* Last computed density rho and potential phi at the finest x vertices
  * (lexicographic order), host arrays of n_vertices doubles. */
 sgdg_status sgdg_get_density_potential(const void* h, double* rho, double* phi);
+
+/* Learned warm start (no counterpart in the paper; the task's extension).
+ *
+ * sgdg_coarse_values: the values of a sparse-grid function at the nodes of
+ * the full grid (lx, lv): u is a strip vector (R = 2) or a spatial vector
+ * (R = 1); out [n_x(lx)][n_v(lv)][R] on the device.  Finer component grids are
+ * injected, coarser ones prolonged (unique, unlike the coefficients).
+ * sgdg_add_coarse: adds the P1 function c ([n_x(lx)][n_v(lv)][2], device) to
+ * the strip vector u, represented on component grid (lx, L-lx) by
+ * prolongation in v; needs lv <= L - lx. */
+sgdg_status sgdg_coarse_values(void* h, const double* u, int R, int lx, int lv, double* out, void* stream);
+sgdg_status sgdg_add_coarse(void* h, const double* c, int lx, int lv, double* u, void* stream);
+
+/* A 3-layer MLP y = W3^T relu(W2^T relu(W1^T x + b1) + b2) + b3 trained and
+ * evaluated by the library's own BF16 tensor-core GEMMs (FP32 accumulation,
+ * FP32 master weights, Adam).  Sizes must be multiples of 16; batches are
+ * row-major [batch][n] FP64 device arrays (scaled by in_scale / out_scale
+ * inside); at most max_batch rows.  Loss: 1/(2 batch) sum (y - t)^2. */
+sgdg_status sgdg_mlp_create(int n_in, int width, int n_out, int max_batch, unsigned long long seed, void** mlp);
+void sgdg_mlp_destroy(void* mlp);
+sgdg_status sgdg_mlp_set_scaling(void* mlp, double in_scale, double out_scale);
+sgdg_status sgdg_mlp_forward(void* mlp, const double* x, int batch, double* y, void* stream);
+sgdg_status sgdg_mlp_train_step(void* mlp, const double* x, const double* t, int batch, double lr, double* loss,
+                                void* stream);
+/* Gradients of the loss (host, layout W1, b1, W2, b2, W3, b3 with W_k
+ * [fan_in][fan_out]) without an update; loss to *loss. */
+sgdg_status sgdg_mlp_gradients(void* mlp, const double* x, const double* t, int batch, float* grads, double* loss);
+long long sgdg_mlp_num_params(const void* mlp);
+sgdg_status sgdg_mlp_get_params(const void* mlp, float* params);
+sgdg_status sgdg_mlp_set_params(void* mlp, const float* params);
 
 /* Autotuner (no counterpart in the paper): times candidate rows-per-thread
  * settings of every sweep launch site on live applies y = A u (device

@@ -269,3 +269,18 @@ def full_grid_values(op: SparseGridOperator, U: np.ndarray) -> np.ndarray:
         off += n1 * n2
         acc += op.right(op.hv.embed(L, l2), op.left(op.hx.embed(L, l1), u))
     return acc[:, :, 0]
+
+
+def coarse_values(op: SparseGridOperator, U: np.ndarray, R: int, lx: int, lv: int) -> np.ndarray:
+    """Values at the nodes of the full grid (lx, lv) of a sparse-grid function
+    (strip vector R = 2, spatial R = 1): injection from finer grids,
+    prolongation from coarser ones; layout [kx][kv][s]."""
+    nx, nv = op.hx.levels[lx].n, op.hv.levels[lv].n
+    out = np.zeros((nx, nv, R))
+    off = 0
+    for (l1, l2) in op.grids:
+        n1, n2 = op.grid_shape(l1, l2)
+        u = U[off:off + n1 * n2 * R].reshape(n1, n2, R)
+        off += n1 * n2 * R
+        out += op.right(_transfer(op.hv, lv, l2), op.left(_transfer(op.hx, lx, l1), u))
+    return out.ravel()

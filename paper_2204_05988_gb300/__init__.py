@@ -87,8 +87,22 @@ EXPORTS = {
     "sgdg_resolve_strip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_set_warm_start": (C.c_int, [C.c_void_p, C.c_int]),
     "sgdg_set_guess": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sgdg_extrapolated_guess": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sgdg_finest_x": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "sgdg_get_density_potential": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sgdg_coarse_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "sgdg_add_coarse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "sgdg_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_ulonglong, C.POINTER(C.c_void_p)]),
+    "sgdg_mlp_destroy": (None, [C.c_void_p]),
+    "sgdg_mlp_set_scaling": (C.c_int, [C.c_void_p, C.c_double, C.c_double]),
+    "sgdg_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "sgdg_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                      C.POINTER(C.c_double), C.c_void_p]),
+    "sgdg_mlp_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                     C.POINTER(C.c_double)]),
+    "sgdg_mlp_num_params": (C.c_longlong, [C.c_void_p]),
+    "sgdg_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sgdg_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sgdg_batch_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
     "sgdg_batch_destroy": (None, [C.c_void_p]),
     "sgdg_batch_apply": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
@@ -312,8 +326,17 @@ class Solver:
             self._check(code)
         return st
 
+    def coarse_values(self, u, R: int, lx: int, lv: int, out, stream=None):
+        self._check(self.lib.sgdg_coarse_values(self.h, _ptr(u), R, lx, lv, _ptr(out), _stream(stream)))
+
+    def add_coarse(self, c, lx: int, lv: int, u, stream=None):
+        self._check(self.lib.sgdg_add_coarse(self.h, _ptr(c), lx, lv, _ptr(u), _stream(stream)))
+
     def set_warm_start(self, mode: int):
         self._check(self.lib.sgdg_set_warm_start(self.h, mode))
+
+    def extrapolated_guess(self, dst):
+        self._check(self.lib.sgdg_extrapolated_guess(self.h, _ptr(dst)))
 
     def set_guess(self, u):
         self._check(self.lib.sgdg_set_guess(self.h, _ptr(u)))
@@ -377,6 +400,65 @@ class Batch:
         if getattr(self, "b", None):
             self.lib.sgdg_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mlp:
+    """The library's BF16 MLP (sgdg_mlp_*): 3 layers, FP64 batches on the device."""
+
+    def __init__(self, n_in: int, width: int, n_out: int, max_batch: int, seed: int = 0):
+        self.lib = load_library()
+        m = C.c_void_p()
+        st = self.lib.sgdg_mlp_create(n_in, width, n_out, max_batch, seed, C.byref(m))
+        if st != 0:
+            raise SgdgError(st, "mlp create")
+        self.m = m
+        self.n_in, self.width, self.n_out = n_in, width, n_out
+
+    def _chk(self, st, what):
+        if st != 0:
+            raise SgdgError(st, what)
+
+    def set_scaling(self, in_scale: float, out_scale: float):
+        self._chk(self.lib.sgdg_mlp_set_scaling(self.m, in_scale, out_scale), "mlp scaling")
+
+    def forward(self, x, batch: int, y, stream=None):
+        self._chk(self.lib.sgdg_mlp_forward(self.m, _ptr(x), batch, _ptr(y), _stream(stream)), "mlp forward")
+
+    def train_step(self, x, t, batch: int, lr: float, stream=None) -> float:
+        loss = C.c_double()
+        self._chk(self.lib.sgdg_mlp_train_step(self.m, _ptr(x), _ptr(t), batch, lr, C.byref(loss),
+                                               _stream(stream)), "mlp train step")
+        return loss.value
+
+    def num_params(self) -> int:
+        return int(self.lib.sgdg_mlp_num_params(self.m))
+
+    def gradients(self, x, t, batch: int):
+        g = np.empty(self.num_params(), dtype=np.float32)
+        loss = C.c_double()
+        self._chk(self.lib.sgdg_mlp_gradients(self.m, _ptr(x), _ptr(t), batch, _ptr(g), C.byref(loss)),
+                  "mlp gradients")
+        return g, loss.value
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.num_params(), dtype=np.float32)
+        self._chk(self.lib.sgdg_mlp_get_params(self.m, _ptr(p)), "mlp params")
+        return p
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._chk(self.lib.sgdg_mlp_set_params(self.m, _ptr(p)), "mlp params")
+
+    def close(self):
+        if getattr(self, "m", None):
+            self.lib.sgdg_mlp_destroy(self.m)
+            self.m = None
 
     def __del__(self):
         try:

@@ -438,6 +438,8 @@ sgdg_status sgdg_set_initial(void* hp) {
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(h, {SGDG_ECUDA, "set_initial"});
   h->have_initial = true;
   h->first_strip = true;
+  h->solved = false;
+  h->nsolved = 0;
   return SGDG_OK;
 }
 
@@ -641,6 +643,20 @@ sgdg_status sgdg_field_update(void* hp, int source, double* energy) {
   return st.code ? fail(h, st) : SGDG_OK;
 }
 
+sgdg_status sgdg_coarse_values(void* hp, const double* u, int R, int lx, int lv, double* out, void* stream) {
+  if (!hp || !u || !out) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  Status st = coarse_values(*h, u, R, lx, lv, out, (cudaStream_t)stream);
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+sgdg_status sgdg_add_coarse(void* hp, const double* c, int lx, int lv, double* u, void* stream) {
+  if (!hp || !c || !u) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  Status st = add_coarse(*h, c, lx, lv, u, (cudaStream_t)stream);
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
 sgdg_status sgdg_resolve_strip(void* hp, void* stream, sgdg_strip_stats* stats) {
   if (!hp) return SGDG_EINVAL;
   Handle* h = (Handle*)hp;
@@ -651,8 +667,21 @@ sgdg_status sgdg_resolve_strip(void* hp, void* stream, sgdg_strip_stats* stats) 
 sgdg_status sgdg_set_warm_start(void* hp, int mode) {
   if (!hp) return SGDG_EINVAL;
   Handle* h = (Handle*)hp;
-  if (mode < 0 || mode > 2) return fail(h, {SGDG_EINVAL, "warm start mode must be 0, 1 or 2"});
+  if (mode < 0 || mode > 3) return fail(h, {SGDG_EINVAL, "warm start mode must be 0, 1, 2 or 3"});
   h->warm = mode;
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_extrapolated_guess(const void* hp, double* dst) {
+  if (!hp || !dst) return SGDG_EINVAL;
+  const Handle* h = (const Handle*)hp;
+  if (!h->solved) return SGDG_EINVAL;
+  const size_t bytes = sizeof(double) * h->n_coeffs;
+  if (cudaMemcpy(dst, h->u_sol, bytes, cudaMemcpyDeviceToDevice) != cudaSuccess) return SGDG_ECUDA;
+  if (h->nsolved >= 2 && h->u_prev2) {
+    if (vec_axpby<double>(h->n_coeffs, -1.0, h->u_prev2, 2.0, dst, nullptr) != cudaSuccess) return SGDG_ECUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return SGDG_ECUDA;
+  }
   return SGDG_OK;
 }
 

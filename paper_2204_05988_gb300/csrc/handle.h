@@ -73,8 +73,11 @@ struct Handle {
   double* u_sol = nullptr;   // last strip solution, n_coeffs
   double* rhs = nullptr;     // n_coeffs
   bool have_initial = false, first_strip = true, solved = false;
-  int warm = 0;              // initial guess of the next strip: 0 zero, 1 last solution, 2 guess
+  int warm = 0;              // initial guess of the next strip: 0 zero, 1 last solution, 2 guess,
+                             // 3 extrapolation of the last two solutions
   double* guess = nullptr;   // n_coeffs, allocated by sgdg_set_guess
+  double* u_prev2 = nullptr; // the solution before the last one (for mode 3)
+  int nsolved = 0;           // strips solved since set_initial
   size_t device_bytes = 0;
   Workspace* ws = nullptr;      // owned; released by solver_free
   cudaStream_t cur = nullptr;
@@ -133,6 +136,10 @@ Status autotune(Handle& h, const T* u, T* y, cudaStream_t s);
 // Vlasov-Poisson coupling (field.cu)
 Status field_setup(Handle& h, const sgdg_coeffs& c, const Hierarchy& hx, const Hierarchy& hv, const SideFns& fx);
 Status field_update(Handle& h, int source, double* energy);
+
+// coarse full-grid views (coarse.cu)
+Status coarse_values(Handle& h, const double* u, int R, int lx, int lv, double* out, cudaStream_t s);
+Status add_coarse(Handle& h, const double* c, int lx, int lv, double* u, cudaStream_t s);
 
 Status solver_init(Handle& h);
 Status ct_precondition(Handle& h, const double* r, double* z, cudaStream_t s, int* inner_its);

@@ -421,12 +421,21 @@ Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resol
   SG_ST(vnorm<double>(h, h.rhs, n, &bnorm, s));
   double* x = h.u_sol;
   double* r = O.t1;
-  // initial guess: the last solution (re-solve, warm start 1), a given guess (2) or zero
+  // initial guess: the last solution (re-solve, warm start 1), a given guess
+  // (2), the linear extrapolation 2 u_{j-1} - u_{j-2} of the last two strip
+  // solutions (3) or zero; u_prev2 keeps u_{j-1} for the next extrapolation
   const int mode = resolve ? 1 : h.warm;
   double beta = bnorm;
   if (mode == 2 && !h.guess) return {SGDG_EINVAL, "warm start 2 needs sgdg_set_guess"};
+  if (!resolve && h.solved) {
+    if (!h.u_prev2 && dev_alloc(h, (void**)&h.u_prev2, sizeof(double) * n) != cudaSuccess)
+      return {SGDG_ENOMEM, "previous solution buffer"};
+    SG_CU(cudaMemcpyAsync(O.t0, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (mode == 3 && h.nsolved >= 2) SG_CU(vec_axpby<double>(n, -1.0, h.u_prev2, 2.0, x, s));
+    SG_CU(cudaMemcpyAsync(h.u_prev2, O.t0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
   if (mode == 2) SG_CU(cudaMemcpyAsync(x, h.guess, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  if ((mode == 1 && h.solved) || mode == 2) {
+  if (((mode == 1 || mode == 3) && h.solved) || mode == 2) {
     SG_ST(apply_plan<double>(h, h.op, x, r, s));
     S.applies++;
     SG_CU(vec_axpby<double>(n, 1.0, h.rhs, -1.0, r, s));
@@ -482,6 +491,7 @@ Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resol
   SG_CU(cudaStreamSynchronize(s));
   h.first_strip = false;
   h.solved = true;
+  if (!resolve) h.nsolved++;
   S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (st) *st = S;
   if (S.status == SGDG_ENOCONV) return {SGDG_ENOCONV, "outer FGMRES reached max_outer"};
