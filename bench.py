@@ -235,9 +235,19 @@ def main():
     dom = max(st, key=lambda k: st[k]["ms"])
     ach = st[dom]["bytes"] / (st[dom]["ms"] * 1e-3) / 1e9
     tot_ms = sum(v["ms"] for v in st.values())
+    # whole-apply effective bandwidth: the bytes the method must move per apply
+    # (read u, write y, every pattern once, every factor value array once),
+    # independent of the sweep's intermediates
+    inf = s.info
+    b_alg = (n * (4 + 4) + 4 * (inf.rows_x + inf.rows_v + 2 * (inf.L + 1))
+             + 4 * inf.nnz_x * (1 + inf.n_x_factors) + 4 * inf.nnz_v * (1 + inf.n_v_factors))
     roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
                 "share_of_apply": st[dom]["ms"] / tot_ms,
+                "apply_effective": {"b_alg_bytes": b_alg, "GBps": b_alg / (ms32 * 1e-3) / 1e9,
+                                    "frac": b_alg / (ms32 * 1e-3) / 1e9 / peak,
+                                    "sweep_bytes": sum(v["bytes"] for v in st.values()),
+                                    "sweep_GBps": sum(v["bytes"] for v in st.values()) / (tot_ms * 1e-3) / 1e9},
                 "per_kind": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                                  "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                              for k, v in st.items()},

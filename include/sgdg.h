@@ -126,6 +126,8 @@ typedef struct {
   int n_terms;                 /* Kronecker terms after merging */
   int n_x_factors, n_v_factors;
   double device_bytes;         /* device memory held by the handle */
+  long long nnz_x, nnz_v;      /* P1 pattern entries summed over the levels of each side */
+  long long rows_x, rows_v;    /* pattern rows (vertices) summed over the levels of each side */
 } sgdg_info;
 
 typedef struct {
@@ -264,10 +266,11 @@ long long sgdg_mlp_num_params(const void* mlp);
 sgdg_status sgdg_mlp_get_params(const void* mlp, float* params);
 sgdg_status sgdg_mlp_set_params(void* mlp, const float* params);
 
-/* Autotuner (no counterpart in the paper): times candidate rows-per-thread
- * settings of every sweep launch site on live applies y = A u (device
- * arrays as for sgdg_apply_operator, overwritten) and keeps the fastest per
- * site for all later applies of this handle. */
+/* Autotuner (no counterpart in the paper): times candidate launch shapes
+ * (rows per thread in {1,2,4,8} x row-major or column-tiled block order) of
+ * every sweep launch site on live applies y = A u (device arrays as for
+ * sgdg_apply_operator, overwritten) and keeps the fastest per site for all
+ * later applies of this handle. */
 sgdg_status sgdg_autotune(void* h, const void* u, void* y, int precision, void* stream);
 
 /* Batches of independent problems (many instances of uneven L, Sect. 5's

@@ -51,7 +51,9 @@ class Config(C.Structure):
 class Info(C.Structure):
     _fields_ = [("L", C.c_int), ("d", C.c_int), ("R", C.c_int), ("n_grids", C.c_int),
                 ("n_spatial", C.c_longlong), ("n_coeffs", C.c_longlong), ("n_terms", C.c_int),
-                ("n_x_factors", C.c_int), ("n_v_factors", C.c_int), ("device_bytes", C.c_double)]
+                ("n_x_factors", C.c_int), ("n_v_factors", C.c_int), ("device_bytes", C.c_double),
+                ("nnz_x", C.c_longlong), ("nnz_v", C.c_longlong), ("rows_x", C.c_longlong),
+                ("rows_v", C.c_longlong)]
 
 
 class StripStats(C.Structure):

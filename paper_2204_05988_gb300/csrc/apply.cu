@@ -115,23 +115,28 @@ Status ensure_bufs(Handle& h) {
 }
 
 // Chain-state pool of the sweep: 2 ring slots per branch-A chain, 2 ring
-// slots + 1 strict slot per branch-B chain, each slot one largest grid.
+// slots + 1 strict slot per branch-B chain, then the restriction
+// intermediates Z of one launch group; each slot holds one largest grid.
+inline long long pool_slots(const Plan& q) {
+  const long long a = (long long)q.A.size(), b = (long long)q.B.size();
+  return std::max(2 * a, 3 * b) + std::min<long long>(kChainSlots, std::max(a, b));
+}
+
 template <typename T>
-Status ensure_pool(Handle& h, const Plan& p, T** pool, long long* slot) {
+Status ensure_pool(Handle& h, const Plan& p, T** pool, long long* slot, T** zbase) {
   long long M = 2;
   for (int l = 0; l <= h.L; ++l) M = std::max(M, 2LL * h.n1[l] * h.n2[l]);
   // sized once for the largest plan of the handle (the operator's)
-  const Plan& big = h.op.A.size() + h.op.B.size() >= p.A.size() + p.B.size() ? h.op : p;
-  const long long need = M * std::max<long long>(2LL * (long long)big.A.size(), 3LL * (long long)big.B.size());
+  const long long need = M * std::max(pool_slots(h.op), pool_slots(p));
   Handle::Bufs& b = bufs<T>(h);
   if (!b.pool) {
     if (dev_alloc(h, &b.pool, sizeof(T) * (size_t)need) != cudaSuccess) return {SGDG_ENOMEM, "sweep chain pool"};
     b.pool_elems = need;
   }
-  if (b.pool_elems < M * std::max<long long>(2LL * (long long)p.A.size(), 3LL * (long long)p.B.size()))
-    return {SGDG_EINVAL, "sweep chain pool too small for this plan"};
+  if (b.pool_elems < M * pool_slots(p)) return {SGDG_EINVAL, "sweep chain pool too small for this plan"};
   *pool = (T*)b.pool;
   *slot = M;
+  *zbase = (T*)b.pool + (size_t)M * std::max(2LL * (long long)p.A.size(), 3LL * (long long)p.B.size());
   return {};
 }
 
@@ -146,53 +151,94 @@ inline long long site_key(int kind, int n1, int n2, int count, int elem) {
   return (((head << 24) | (long long)n1) << 24) | (long long)n2;
 }
 
+// Launch shape of a site: rows per thread (ch, 0 = heuristic) and block order
+// (tiled).  Tuned choices are stored as ch | tiled << 4.  Untuned sites take
+// the column tiles when the launch's stencil runs along dim 1 and rows are
+// long enough to fill a tile.
+struct Shape {
+  int ch = 0, tiled = 0;
+};
+
 template <typename T>
-int pick_ch(Handle& h, long long site) {
-  if (h.force_ch > 0) return h.force_ch;
-  auto it = h.tuned_ch.find(site);
-  return it == h.tuned_ch.end() ? 0 : it->second;
+Shape pick_shape(Handle& h, long long site, bool dim1_stencil, int n1, int n2) {
+  int code = h.force_ch > 0 ? h.force_ch : 0;
+  if (!code) {
+    auto it = h.tuned_ch.find(site);
+    if (it != h.tuned_ch.end()) code = it->second;
+  }
+  Shape sh;
+  if (code) {
+    sh.ch = std::min(code & 15, n1);
+    sh.tiled = code >> 4;
+  } else {
+    sh.tiled = dim1_stencil && n2 >= kTileW ? 1 : 0;
+  }
+  return sh;
+}
+
+struct ProfScope {
+  Handle& h;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ProfScope(Handle& hh, cudaStream_t ss) : h(hh), s(ss) {
+    if (h.prof) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, s);
+    }
+  }
+  void done(int kind, double bytes, long long site) {
+    h.launches++;
+    if (!h.prof) return;
+    cudaEventRecord(e1, s);
+    h.kev.push_back({kind, bytes, e0, e1, site});
+  }
+};
+
+template <typename T>
+double grid_bytes(long long n1, long long n2) {
+  return 2.0 * sizeof(T) * (double)n1 * (double)n2;
 }
 
 template <typename T>
-Status run_chain(Handle& h, ChainArgs<T>& a, bool mode_a, cudaStream_t s, double mat_bytes) {
-  const long long site = site_key(mode_a ? KIND_CHAIN_A : KIND_CHAIN_B, a.n1, a.n2, a.nchains, sizeof(T));
-  a.ch = std::min(pick_ch<T>(h, site), a.n1);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (h.prof) {
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, s);
-  }
+Status run_restrict(Handle& h, RestrictArgs<T>& a, bool dim2, cudaStream_t s, double mat_bytes) {
+  const int kind = dim2 ? KIND_XFER_RIGHT : KIND_XFER_LEFT;
+  const long long site = site_key(kind, a.n1, a.n2, a.nchains, sizeof(T));
+  const Shape sh = pick_shape<T>(h, site, !dim2, a.n1, a.n2);
+  a.ch = sh.ch;
+  a.tiled = sh.tiled;
+  ProfScope ps(h, s);
+  SG_CU(launch_restrict(a, dim2, s));
+  ps.done(kind, mat_bytes + a.nchains * (grid_bytes<T>(a.n1_in, a.n2_in) + grid_bytes<T>(a.n1, a.n2)), site);
+  return {};
+}
+
+// extra_bytes: matrices and the restriction intermediates the launch reads
+template <typename T>
+Status run_chain(Handle& h, ChainArgs<T>& a, bool mode_a, cudaStream_t s, double extra_bytes) {
+  const int kind = mode_a ? KIND_CHAIN_A : KIND_CHAIN_B;
+  const long long site = site_key(kind, a.n1, a.n2, a.nchains, sizeof(T));
+  const Shape sh = pick_shape<T>(h, site, mode_a, a.n1, a.n2);
+  a.ch = sh.ch;
+  a.tiled = sh.tiled;
+  ProfScope ps(h, s);
   SG_CU(launch_chain(a, mode_a, s));
-  h.launches++;
-  if (h.prof) {
-    cudaEventRecord(e1, s);
-    const double g = 2.0 * sizeof(T) * (double)a.n1 * a.n2;
-    const double gp = 2.0 * sizeof(T) * (double)a.n1_prev * a.n2_prev;
-    double bytes = mat_bytes + g + a.nchains * g * (mode_a ? 1.0 : 2.0) + (a.has_prev ? a.nchains * gp : 0.0);
-    h.kev.push_back({mode_a ? KIND_CHAIN_A : KIND_CHAIN_B, bytes, e0, e1, site});
-  }
+  const double g = grid_bytes<T>(a.n1, a.n2);
+  ps.done(kind, extra_bytes + g + a.nchains * g * (!mode_a && a.has_prev ? 2.0 : 1.0), site);
   return {};
 }
 
 template <typename T>
 Status run_final(Handle& h, FinalArgs<T>& f, bool left, int lev_rows, int lev_nnz, cudaStream_t s) {
-  const long long site = site_key(left ? KIND_FINAL_LEFT : KIND_FINAL_RIGHT, f.n1, f.n2, f.nterms, sizeof(T));
-  f.ch = std::min(pick_ch<T>(h, site), f.n1);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (h.prof) {
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, s);
-  }
+  const int kind = left ? KIND_FINAL_LEFT : KIND_FINAL_RIGHT;
+  const long long site = site_key(kind, f.n1, f.n2, f.nin, sizeof(T));
+  const Shape sh = pick_shape<T>(h, site, left, f.n1, f.n2);
+  f.ch = sh.ch;
+  f.tiled = sh.tiled;
+  ProfScope ps(h, s);
   SG_CU(launch_final(f, left, s));
-  h.launches++;
-  if (h.prof) {
-    cudaEventRecord(e1, s);
-    const double g = 2.0 * sizeof(T) * (double)f.n1 * f.n2;
-    double bytes = csr_bytes<T>(lev_rows, lev_nnz, f.nterms) + f.nin * g + g * (f.accumulate ? 2.0 : 1.0);
-    h.kev.push_back({left ? KIND_FINAL_LEFT : KIND_FINAL_RIGHT, bytes, e0, e1, site});
-  }
+  const double g = grid_bytes<T>(f.n1, f.n2);
+  ps.done(kind, csr_bytes<T>(lev_rows, lev_nnz, f.nterms) + f.nin * g + g * (f.accumulate ? 2.0 : 1.0), site);
   return {};
 }
 
@@ -205,12 +251,13 @@ Status finals_on(Handle& h, const Plan& p, const std::vector<Chain>& chains, boo
   FinalArgs<T> f;
   f.n1 = n1;
   f.n2 = n2;
-  f.rowptr = sd.rowptr[lev];
-  f.col = sd.col[lev];
+  f.row = sd.row_regs();
+  f.col = sd.ell_col[lev];
   f.y = ygrid;
   bool first = true;
   auto flush = [&]() -> Status {
     if (f.nterms == 0) return {};
+    f.tbeg[f.nin] = f.nterms;
     f.accumulate = first ? (accumulate_first ? 1 : 0) : 1;
     Status st = run_final(h, f, left, sd.n[lev], sd.nnz[lev], s);
     first = false;
@@ -220,22 +267,19 @@ Status finals_on(Handle& h, const Plan& p, const std::vector<Chain>& chains, boo
   };
   for (size_t c = 0; c < chains.size(); ++c) {
     const Chain& ch = chains[c];
-    if (f.nin == kFinalIn || f.nterms + (int)ch.terms.size() > kFinalTerms) {
-      Status st = flush();
-      if (st.code) return st;
-    }
-    int slot = f.nin++;
-    f.in[slot] = in_of((int)c);
+    bool open = false;
     for (int t : ch.terms) {
-      if (f.nterms == kFinalTerms) {
-        Status st = flush();
-        if (st.code) return st;
-        slot = f.nin++;
-        f.in[slot] = in_of((int)c);
+      if (!open || f.nterms == kFinalTerms) {
+        if (f.nin == kFinalIn || f.nterms == kFinalTerms) {
+          Status st = flush();
+          if (st.code) return st;
+        }
+        f.tbeg[f.nin] = f.nterms;
+        f.in[f.nin++] = in_of((int)c);
+        open = true;
       }
       const Term& tm = p.terms[t];
-      f.tin[f.nterms] = slot;
-      f.val[f.nterms] = sd.vals<T>().fac[left ? tm.x : tm.v][lev];
+      f.val[f.nterms] = sd.vals<T>().ell_fac[left ? tm.x : tm.v][lev];
       for (int a = 0; a < 2; ++a)
         for (int q = 0; q < 2; ++q) f.tau[f.nterms][a * 2 + q] = (T)tm.tau[a][q];
       f.nterms++;
@@ -256,8 +300,9 @@ Status finals(Handle& h, const Plan& p, const std::vector<Chain>& chains, bool l
 template <typename T>
 Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s) {
   T* pool;
+  T* zb;
   long long M;
-  Status st = ensure_pool<T>(h, p, &pool, &M);
+  Status st = ensure_pool<T>(h, p, &pool, &M, &zb);
   if (st.code) return st;
   const int L = h.L;
   const int G = kChainMax<T>();
@@ -265,36 +310,51 @@ Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s) {
   auto slotA = [&](int c, int par) { return pool + (size_t)(2 * c + par) * M; };
   auto slotT = [&](int c, int par) { return pool + (size_t)(3 * c + par) * M; };
   auto slotTP = [&](int c) { return pool + (size_t)(3 * c + 2) * M; };
+  auto slotZ = [&](int g) { return zb + (size_t)g * M; };
   // ---- branch A (sources l1' <= l1): chains by the v factor
   for (int i = 0; i <= L; ++i) {
     const int lv = L - i;
     for (int c0 = 0; c0 < nA; c0 += G) {
+      const int nc = std::min(G, nA - c0);
+      double zbytes = 0.0;
+      if (i > 0) {
+        // Z_g = S_{g,i-1} R2^T  (n1[i-1] x n2[i])
+        RestrictArgs<T> r;
+        r.n1 = h.n1[i - 1];
+        r.n2 = h.n2[i];
+        r.n1_in = h.n1[i - 1];
+        r.n2_in = h.n2[i - 1];
+        r.nchains = nc;
+        r.row = h.V.row_regs();
+        r.col = h.V.R_ell_col[lv];
+        r.val = h.V.vals<T>().ell_R[lv];
+        for (int g = 0; g < nc; ++g) {
+          r.in[g] = slotA(c0 + g, (i - 1) & 1);
+          r.out[g] = slotZ(g);
+        }
+        st = run_restrict(h, r, true, s, csr_bytes<T>(h.V.n[lv], h.V.R_nnz[lv], 1));
+        if (st.code) return st;
+        zbytes = nc * grid_bytes<T>(r.n1, r.n2) + csr_bytes<T>(h.X.n[i], h.X.E_nnz[i - 1], 1);
+      }
       ChainArgs<T> a;
       a.n1 = h.n1[i];
       a.n2 = h.n2[i];
-      a.nchains = std::min(G, nA - c0);
+      a.nz2 = h.n2[i];
+      a.nchains = nc;
       a.has_prev = i > 0;
+      a.row = h.V.row_regs();
       a.U = u + h.off[i];
-      a.f_rowptr = h.V.rowptr[lv];
-      a.f_col = h.V.col[lv];
-      double mb = csr_bytes<T>(h.V.n[lv], h.V.nnz[lv], a.nchains);
-      for (int g = 0; g < a.nchains; ++g) {
-        a.f_val[g] = h.V.vals<T>().fac[p.A[c0 + g].first][lv];
+      a.f_col = h.V.ell_col[lv];
+      for (int g = 0; g < nc; ++g) {
+        a.f_val[g] = h.V.vals<T>().ell_fac[p.A[c0 + g].first][lv];
         a.out[g] = slotA(c0 + g, i & 1);
-        a.prev[g] = i > 0 ? slotA(c0 + g, (i - 1) & 1) : nullptr;
+        a.Z[g] = i > 0 ? slotZ(g) : nullptr;
       }
       if (i > 0) {
-        a.n1_prev = h.n1[i - 1];
-        a.n2_prev = h.n2[i - 1];
-        a.t1_rowptr = h.X.E_rowptr[i - 1];
-        a.t1_col = h.X.E_col[i - 1];
-        a.t1_val = h.X.vals<T>().E[i - 1];
-        a.t2_rowptr = h.V.R_rowptr[lv];
-        a.t2_col = h.V.R_col[lv];
-        a.t2_val = h.V.vals<T>().R[lv];
-        mb += csr_bytes<T>(h.X.n[i], h.X.E_nnz[i - 1], 1) + csr_bytes<T>(h.V.n[lv], h.V.R_nnz[lv], 1);
+        a.p_col = h.X.E_ell_col[i - 1];
+        a.p_val = h.X.vals<T>().ell_E[i - 1];
       }
-      st = run_chain(h, a, true, s, mb);
+      st = run_chain(h, a, true, s, csr_bytes<T>(h.V.n[lv], h.V.nnz[lv], nc) + zbytes);
       if (st.code) return st;
     }
     st = finals<T>(h, p, p.A, true, i, [&](int c) { return (const T*)slotA(c, i & 1); }, false, y, s);
@@ -304,33 +364,47 @@ Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s) {
   if (L >= 1) {
     for (int i = L; i >= 0; --i) {
       for (int c0 = 0; c0 < nB; c0 += G) {
+        const int nc = std::min(G, nB - c0);
+        double zbytes = 0.0;
+        if (i < L) {
+          // Z_g = R1 T_{g,i+1}  (n1[i] x n2[i+1])
+          RestrictArgs<T> r;
+          r.n1 = h.n1[i];
+          r.n2 = h.n2[i + 1];
+          r.n1_in = h.n1[i + 1];
+          r.n2_in = h.n2[i + 1];
+          r.nchains = nc;
+          r.row = h.X.row_regs();
+          r.col = h.X.R_ell_col[i];
+          r.val = h.X.vals<T>().ell_R[i];
+          for (int g = 0; g < nc; ++g) {
+            r.in[g] = slotT(c0 + g, (i + 1) & 1);
+            r.out[g] = slotZ(g);
+          }
+          st = run_restrict(h, r, false, s, csr_bytes<T>(h.X.n[i], h.X.R_nnz[i], 1));
+          if (st.code) return st;
+          zbytes = nc * grid_bytes<T>(r.n1, r.n2) + csr_bytes<T>(h.V.n[L - i], h.V.E_nnz[L - i - 1], 1);
+        }
         ChainArgs<T> a;
         a.n1 = h.n1[i];
         a.n2 = h.n2[i];
-        a.nchains = std::min(G, nB - c0);
+        a.nz2 = i < L ? h.n2[i + 1] : 0;
+        a.nchains = nc;
         a.has_prev = i < L;
+        a.row = h.X.row_regs();
         a.U = u + h.off[i];
-        a.f_rowptr = h.X.rowptr[i];
-        a.f_col = h.X.col[i];
-        double mb = csr_bytes<T>(h.X.n[i], h.X.nnz[i], a.nchains);
-        for (int g = 0; g < a.nchains; ++g) {
-          a.f_val[g] = h.X.vals<T>().fac[p.B[c0 + g].first][i];
+        a.f_col = h.X.ell_col[i];
+        for (int g = 0; g < nc; ++g) {
+          a.f_val[g] = h.X.vals<T>().ell_fac[p.B[c0 + g].first][i];
           a.out[g] = slotT(c0 + g, i & 1);
-          a.prev[g] = i < L ? slotT(c0 + g, (i + 1) & 1) : nullptr;
+          a.Z[g] = i < L ? slotZ(g) : nullptr;
           a.strict[g] = i < L ? slotTP(c0 + g) : nullptr;
         }
         if (i < L) {
-          a.n1_prev = h.n1[i + 1];
-          a.n2_prev = h.n2[i + 1];
-          a.t1_rowptr = h.X.R_rowptr[i];
-          a.t1_col = h.X.R_col[i];
-          a.t1_val = h.X.vals<T>().R[i];
-          a.t2_rowptr = h.V.E_rowptr[L - i - 1];
-          a.t2_col = h.V.E_col[L - i - 1];
-          a.t2_val = h.V.vals<T>().E[L - i - 1];
-          mb += csr_bytes<T>(h.X.n[i], h.X.R_nnz[i], 1) + csr_bytes<T>(h.V.n[L - i], h.V.E_nnz[L - i - 1], 1);
+          a.p_col = h.V.E_ell_col[L - i - 1];
+          a.p_val = h.V.vals<T>().ell_E[L - i - 1];
         }
-        st = run_chain(h, a, false, s, mb);
+        st = run_chain(h, a, false, s, csr_bytes<T>(h.X.n[i], h.X.nnz[i], nc) + zbytes);
         if (st.code) return st;
       }
       if (i < L) {
@@ -353,8 +427,9 @@ template <typename T>
 Status apply_diag_grids(Handle& h, int ng, const int* l1, const int* l2, const T* const* u, T* const* y,
                         cudaStream_t s) {
   T* pool;
+  T* zb;
   long long M;
-  Status st = ensure_pool<T>(h, h.op, &pool, &M);
+  Status st = ensure_pool<T>(h, h.op, &pool, &M, &zb);
   if (st.code) return st;
   const std::vector<Chain>& chains = h.op.A;   // by v factor
   const int nc = (int)chains.size();
@@ -367,11 +442,11 @@ Status apply_diag_grids(Handle& h, int ng, const int* l1, const int* l2, const T
       a.n2 = n2;
       a.nchains = std::min(kChainSlots, nc - c0);
       a.has_prev = 0;
+      a.row = h.V.row_regs();
       a.U = u[g];
-      a.f_rowptr = h.V.rowptr[l2[g]];
-      a.f_col = h.V.col[l2[g]];
+      a.f_col = h.V.ell_col[l2[g]];
       for (int c = 0; c < a.nchains; ++c) {
-        a.f_val[c] = h.V.vals<T>().fac[chains[c0 + c].first][l2[g]];
+        a.f_val[c] = h.V.vals<T>().ell_fac[chains[c0 + c].first][l2[g]];
         a.out[c] = pool + (size_t)(c0 + c) * M;
       }
       st = run_chain(h, a, true, s, csr_bytes<T>(n2, h.V.nnz[l2[g]], a.nchains));
@@ -425,7 +500,8 @@ Status nodal_eval(Handle& h, const double* u, double* out, cudaStream_t s) {
 
 template <typename T>
 Status autotune(Handle& h, const T* u, T* y, cudaStream_t s) {
-  const int cand[] = {1, 2, 4, 8};
+  // rows per thread x block order, encoded as ch | tiled << 4
+  const int cand[] = {1, 2, 4, 8, 1 | 16, 2 | 16, 4 | 16, 8 | 16};
   std::map<long long, std::pair<float, int>> best;
   const bool prof_was = h.prof;
   for (int c : cand) {

@@ -7,6 +7,7 @@
 #include <thread>
 
 #include "handle.h"
+#include "sweep.h"
 
 namespace sgdg {
 
@@ -62,22 +63,67 @@ Status upload_vals(Handle& h, const std::vector<double>& v, double** d64, float*
   return {};
 }
 
+}  // namespace
+
+std::vector<int> ell_columns(const std::vector<int>& rowptr, const std::vector<int>& col, int w) {
+  const int n = (int)rowptr.size() - 1;
+  std::vector<int> out((size_t)n * w, 0);
+  for (int r = 0; r < n; ++r) {
+    const int b = rowptr[r], len = rowptr[r + 1] - b;
+    for (int j = 0; j < w; ++j) out[(size_t)r * w + j] = len == 0 ? 0 : col[b + (j < len ? j : 0)];
+  }
+  return out;
+}
+
+std::vector<double> ell_values(const std::vector<int>& rowptr, const std::vector<double>& val, int w) {
+  const int n = (int)rowptr.size() - 1;
+  std::vector<double> out((size_t)n * w, 0.0);
+  for (int r = 0; r < n; ++r) {
+    const int b = rowptr[r], len = rowptr[r + 1] - b;
+    for (int j = 0; j < len && j < w; ++j) out[(size_t)r * w + j] = val[b + j];
+  }
+  return out;
+}
+
+Status upload_ell_vals(Handle& h, const std::vector<int>& rowptr, const std::vector<double>& val, int w,
+                       double** d64, float** d32) {
+  const std::vector<double> e = ell_values(rowptr, val, w);
+  const std::vector<float> f(e.begin(), e.end());
+  if (!*d64) {
+    SG_ST(upload(h, d64, e.data(), e.size()));
+    SG_ST(upload(h, d32, f.data(), f.size()));
+  } else {
+    SG_CU(cudaMemcpy(*d64, e.data(), sizeof(double) * e.size(), cudaMemcpyHostToDevice));
+    SG_CU(cudaMemcpy(*d32, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice));
+  }
+  return {};
+}
+
+namespace {
+
 Status upload_side(Handle& h, const Hierarchy& hi, SideDev& sd) {
   const int L = hi.L;
   sd.n.resize(L + 1);
   sd.nnz.resize(L + 1);
   sd.rowptr.resize(L + 1);
   sd.col.resize(L + 1);
+  const int w = sd.ell_w();
+  sd.ell_col.resize(L + 1);
   for (int l = 0; l <= L; ++l) {
     const Csr& P = hi.lev[l].pattern;
     sd.n[l] = P.nrows;
     sd.nnz[l] = P.nnz();
     SG_ST(upload(h, &sd.rowptr[l], P.rowptr.data(), P.rowptr.size()));
     SG_ST(upload(h, &sd.col[l], P.col.data(), P.col.size()));
+    const std::vector<int> ec = ell_columns(P.rowptr, P.col, w);
+    SG_ST(upload(h, &sd.ell_col[l], ec.data(), ec.size()));
   }
   sd.E_rowptr.resize(L); sd.E_col.resize(L); sd.R_rowptr.resize(L); sd.R_col.resize(L); sd.inj.resize(L);
   sd.E_nnz.resize(L); sd.R_nnz.resize(L);
   sd.v64.E.resize(L); sd.v64.R.resize(L); sd.v32.E.resize(L); sd.v32.R.resize(L);
+  sd.E_ell_col.resize(L); sd.R_ell_col.resize(L);
+  sd.v64.ell_E.assign(L, nullptr); sd.v64.ell_R.assign(L, nullptr);
+  sd.v32.ell_E.assign(L, nullptr); sd.v32.ell_R.assign(L, nullptr);
   for (int l = 0; l < L; ++l) {
     const Csr& E = hi.E[l];
     const Csr& R = hi.Rt[l];
@@ -89,6 +135,12 @@ Status upload_side(Handle& h, const Hierarchy& hi, SideDev& sd) {
     SG_ST(upload(h, &sd.R_rowptr[l], R.rowptr.data(), R.rowptr.size()));
     SG_ST(upload(h, &sd.R_col[l], R.col.data(), R.col.size()));
     SG_ST(upload_vals(h, R.val, &sd.v64.R[l], &sd.v32.R[l]));
+    const std::vector<int> eec = ell_columns(E.rowptr, E.col, kEllE);
+    SG_ST(upload(h, &sd.E_ell_col[l], eec.data(), eec.size()));
+    SG_ST(upload_ell_vals(h, E.rowptr, E.val, kEllE, &sd.v64.ell_E[l], &sd.v32.ell_E[l]));
+    const std::vector<int> erc = ell_columns(R.rowptr, R.col, w);
+    SG_ST(upload(h, &sd.R_ell_col[l], erc.data(), erc.size()));
+    SG_ST(upload_ell_vals(h, R.rowptr, R.val, w, &sd.v64.ell_R[l], &sd.v32.ell_R[l]));
     SG_ST(upload(h, &sd.inj[l], hi.inj[l].data(), hi.inj[l].size()));
   }
   return {};
@@ -172,18 +224,24 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   };
   h.X.mass = find_or_add(h.tt.xf);
   h.V.mass = find_or_add(h.tt.vf);
-  // the sweep kernels keep one matrix row of at most 8 entries in registers
-  for (const Hierarchy* hi : {&hx, &hv}) {
+  // the sweep kernels keep one matrix row of at most 8 entries (prolongation:
+  // kProlongRow) in registers
+  int side_maxrow[2] = {0, 0};
+  for (int side = 0; side < 2; ++side) {
+    const Hierarchy* hi = side == 0 ? &hx : &hv;
     auto maxrow = [](const Csr& A) {
       int m = 0;
       for (int i = 0; i < A.nrows; ++i) m = std::max(m, A.rowptr[i + 1] - A.rowptr[i]);
       return m;
     };
-    for (const MeshLevel& lv : hi->lev)
-      if (maxrow(lv.pattern) > 8) return {SGDG_EINVAL, "P1 pattern rows longer than 8 entries"};
-    for (const Csr& R : hi->Rt)
-      if (maxrow(R) > 8) return {SGDG_EINVAL, "restriction rows longer than 8 entries"};
+    for (const MeshLevel& lv : hi->lev) side_maxrow[side] = std::max(side_maxrow[side], maxrow(lv.pattern));
+    for (const Csr& R : hi->Rt) side_maxrow[side] = std::max(side_maxrow[side], maxrow(R));
+    if (side_maxrow[side] > 8) return {SGDG_EINVAL, "P1 pattern or restriction rows longer than 8 entries"};
+    for (const Csr& E : hi->E)
+      if (maxrow(E) > kProlongRow) return {SGDG_EINVAL, "prolongation rows with more than 2 entries"};
   }
+  h.X.maxrow = side_maxrow[0];
+  h.V.maxrow = side_maxrow[1];
   SG_ST(upload_side(h, hx, h.X));
   SG_ST(upload_side(h, hv, h.V));
   for (int side = 0; side < 2; ++side) {
@@ -193,12 +251,18 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
     const SideFns& fns = side == 0 ? fx : fv;
     sd.v64.fac.assign(fs.size(), std::vector<double*>(h.L + 1, nullptr));
     sd.v32.fac.assign(fs.size(), std::vector<float*>(h.L + 1, nullptr));
+    sd.v64.ell_fac.assign(fs.size(), std::vector<double*>(h.L + 1, nullptr));
+    sd.v32.ell_fac.assign(fs.size(), std::vector<float*>(h.L + 1, nullptr));
     for (size_t f = 0; f < fs.size(); ++f) {
       for (int id : fs[f].wfn)
         if (!fns.fn[id]) return {SGDG_EINVAL, "factor references a missing coefficient function"};
       std::vector<Csr> X;
       SG_ST(assemble_factor(hi, fns, fs[f], X));
-      for (int l = 0; l <= h.L; ++l) SG_ST(upload_vals(h, X[l].val, &sd.v64.fac[f][l], &sd.v32.fac[f][l]));
+      for (int l = 0; l <= h.L; ++l) {
+        SG_ST(upload_vals(h, X[l].val, &sd.v64.fac[f][l], &sd.v32.fac[f][l]));
+        SG_ST(upload_ell_vals(h, hi.lev[l].pattern.rowptr, X[l].val, sd.ell_w(), &sd.v64.ell_fac[f][l],
+                              &sd.v32.ell_fac[f][l]));
+      }
       if ((int)f == sd.mass) {
         sd.v64.dinv.resize(h.L + 1);
         sd.v32.dinv.resize(h.L + 1);
@@ -228,6 +292,8 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
     h.soff[l + 1] = h.soff[l] + (long long)h.n1[l] * h.n2[l];
     h.off[l + 1] = 2 * h.soff[l + 1];
   }
+  for (int l = 0; l <= L; ++l)
+    if ((long long)h.n1[l] * h.n2[l] >= (1LL << 31)) return {SGDG_EINVAL, "component grid with 2^31 or more nodes"};
   h.n_spatial = h.soff[L + 1];
   h.n_coeffs = h.off[L + 1];
   if (cfg.vlasov_poisson) SG_ST(field_setup(h, c, hx, hv, fx));
@@ -312,6 +378,13 @@ sgdg_status sgdg_get_info(const void* hp, sgdg_info* o) {
   o->n_x_factors = (int)h->tt.xf.size();
   o->n_v_factors = (int)h->tt.vf.size();
   o->device_bytes = (double)h->device_bytes;
+  o->nnz_x = o->nnz_v = o->rows_x = o->rows_v = 0;
+  for (int l = 0; l <= h->L; ++l) {
+    o->nnz_x += h->X.nnz[l];
+    o->nnz_v += h->V.nnz[l];
+    o->rows_x += h->X.n[l];
+    o->rows_v += h->V.n[l];
+  }
   return SGDG_OK;
 }
 

@@ -245,6 +245,9 @@ Status field_update(Handle& h, int source, double* energy) {
                        cudaMemcpyHostToDevice));
       std::vector<float> v32(X[l].val.begin(), X[l].val.end());
       SG_CU(cudaMemcpy(h.X.v32.fac[f][l], v32.data(), sizeof(float) * v32.size(), cudaMemcpyHostToDevice));
+      st = upload_ell_vals(h, F.hx.lev[l].pattern.rowptr, X[l].val, h.X.ell_w(), &h.X.v64.ell_fac[f][l],
+                           &h.X.v32.ell_fac[f][l]);
+      if (st.code) return st;
     }
   }
   return {};

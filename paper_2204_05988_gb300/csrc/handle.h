@@ -14,7 +14,13 @@ struct SideValues {
   std::vector<std::vector<T*>> fac;   // [factor][level] values on the level pattern
   std::vector<T*> E, R;               // E[l]: level l -> l+1 values;  R[l] = E[l]^T values
   std::vector<T*> dinv;               // inverse diagonal of the mass matrix per level
+  // ELL copies read by the sweep kernels: row r's entries at [r w, r w + len),
+  // zero padding (w = SideDev::ell_w(); E: kEllE)
+  std::vector<std::vector<T*>> ell_fac;   // [factor][level]
+  std::vector<T*> ell_E, ell_R;
 };
+
+constexpr int kEllE = 2;   // ELL width of the prolongation (rows of at most 2 entries)
 
 struct SideDev {
   std::vector<int> n, nnz, E_nnz, R_nnz;
@@ -22,6 +28,12 @@ struct SideDev {
   std::vector<int*> E_rowptr, E_col, R_rowptr, R_col;
   std::vector<int*> inj;                          // level l vertex -> index on level l+1
   int mass = -1;                                  // factor id of the plain mass matrix
+  int maxrow = 8;                                 // longest pattern or restriction row
+  // row length the sweep kernels keep in registers (3, 4, 7 or 8) and the ELL
+  // width of the patterns and restrictions (4 or 8, 16-byte rows for vector loads)
+  int row_regs() const { return maxrow <= 3 ? 3 : maxrow <= 4 ? 4 : maxrow <= 7 ? 7 : 8; }
+  int ell_w() const { return maxrow <= 4 ? 4 : 8; }
+  std::vector<int*> ell_col, R_ell_col, E_ell_col;   // ELL column indices (padding repeats the first column)
   SideValues<double> v64;
   SideValues<float> v32;
   template <typename T> SideValues<T>& vals();
@@ -87,8 +99,8 @@ struct Handle {
   bool prof = false;
   struct KEvent { int kind; double bytes; cudaEvent_t e0, e1; long long site; };
   std::vector<KEvent> kev;
-  // autotuner: rows-per-thread choice per launch site (kind and grid shape);
-  // force_ch > 0 overrides every site while tuning
+  // autotuner: launch shape per launch site (kind and grid shape), stored as
+  // rows per thread | block order << 4; force_ch > 0 overrides every site while tuning
   std::map<long long, int> tuned_ch;
   int force_ch = 0;
   // Vlasov-Poisson coupling (kept only when cfg.vlasov_poisson)
@@ -120,6 +132,14 @@ cudaError_t run_spmm(Handle& h, bool left, SpmmLaunch<T>& a, cudaStream_t s, int
 
 // allocation helper that records bytes and reports ENOMEM
 cudaError_t dev_alloc(Handle& h, void** p, size_t bytes);
+
+// ELL (width w) copies of a CSR matrix: row r's entries at [r w, r w + len);
+// padded columns repeat the row's first column, padded values are zero.
+std::vector<int> ell_columns(const std::vector<int>& rowptr, const std::vector<int>& col, int w);
+std::vector<double> ell_values(const std::vector<int>& rowptr, const std::vector<double>& val, int w);
+// Uploads the FP64 and FP32 ELL values; allocates when *d64 is null, else overwrites.
+Status upload_ell_vals(Handle& h, const std::vector<int>& rowptr, const std::vector<double>& val, int w,
+                       double** d64, float** d32);
 
 template <typename T>
 Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s);

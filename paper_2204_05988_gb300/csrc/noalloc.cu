@@ -70,26 +70,28 @@ Status diag_noalloc(Handle& h, int l1, int l2, const T* u, T* y, cudaStream_t s)
     a.n1 = n1;
     a.n2 = n2;
     a.nchains = std::min(kChainSlots, nc - c0);
+    a.row = h.V.row_regs();
     a.U = u;
-    a.f_rowptr = h.V.rowptr[l2];
-    a.f_col = h.V.col[l2];
+    a.f_col = h.V.ell_col[l2];
     for (int c = 0; c < a.nchains; ++c) {
-      a.f_val[c] = h.V.vals<T>().fac[chains[c0 + c].first][l2];
+      a.f_val[c] = h.V.vals<T>().ell_fac[chains[c0 + c].first][l2];
       a.out[c] = W + (size_t)(c0 + c) * M;
     }
     cudaError_t e = launch_chain(a, true, s);
     if (e != cudaSuccess) return {SGDG_ECUDA, std::string("no-alloc apply: ") + cudaGetErrorString(e)};
   }
-  // y = sum_a tau_a X_a W_{b(a)}, folded in launches of kFinalTerms terms
+  // y = sum_a tau_a X_a W_{b(a)}, folded in launches of up to kFinalIn inputs
+  // and kFinalTerms terms
   FinalArgs<T> f;
   f.n1 = n1;
   f.n2 = n2;
-  f.rowptr = h.X.rowptr[l1];
-  f.col = h.X.col[l1];
+  f.row = h.X.row_regs();
+  f.col = h.X.ell_col[l1];
   f.y = y;
   bool first = true;
   auto flush = [&]() -> Status {
     if (f.nterms == 0) return {};
+    f.tbeg[f.nin] = f.nterms;
     f.accumulate = first ? 0 : 1;
     f.ch = 0;
     cudaError_t e = launch_final(f, true, s);
@@ -100,22 +102,19 @@ Status diag_noalloc(Handle& h, int l1, int l2, const T* u, T* y, cudaStream_t s)
     return {};
   };
   for (int c = 0; c < nc; ++c) {
-    if (f.nin == kFinalIn || f.nterms + (int)chains[c].terms.size() > kFinalTerms) {
-      st = flush();
-      if (st.code) return st;
-    }
-    int slot = f.nin++;
-    f.in[slot] = W + (size_t)c * M;
+    bool open = false;
     for (int t : chains[c].terms) {
-      if (f.nterms == kFinalTerms) {
-        st = flush();
-        if (st.code) return st;
-        slot = f.nin++;
-        f.in[slot] = W + (size_t)c * M;
+      if (!open || f.nterms == kFinalTerms) {
+        if (f.nin == kFinalIn || f.nterms == kFinalTerms) {
+          st = flush();
+          if (st.code) return st;
+        }
+        f.tbeg[f.nin] = f.nterms;
+        f.in[f.nin++] = W + (size_t)c * M;
+        open = true;
       }
       const Term& tm = h.op.terms[t];
-      f.tin[f.nterms] = slot;
-      f.val[f.nterms] = h.X.vals<T>().fac[tm.x][l1];
+      f.val[f.nterms] = h.X.vals<T>().ell_fac[tm.x][l1];
       for (int a = 0; a < 2; ++a)
         for (int q = 0; q < 2; ++q) f.tau[f.nterms][a * 2 + q] = (T)tm.tau[a][q];
       f.nterms++;
