@@ -267,7 +267,8 @@ sgdg_status sgdg_mlp_get_params(const void* mlp, float* params);
 sgdg_status sgdg_mlp_set_params(void* mlp, const float* params);
 
 /* Autotuner (no counterpart in the paper): times candidate launch shapes
- * (rows per thread in {1,2,4,8} x row-major or column-tiled block order) of
+ * (rows per thread in {1,2,4,8} x row-major or column-tiled block order x one
+ * or two outputs per thread in the final kernels) of
  * every sweep launch site on live applies y = A u (device arrays as for
  * sgdg_apply_operator, overwritten) and keeps the fastest per site for all
  * later applies of this handle. */
@@ -289,9 +290,10 @@ sgdg_status sgdg_batch_apply(void* batch, const void* const* u, void* const* y, 
 sgdg_status sgdg_batch_advance(void* batch, sgdg_strip_stats* per_member);
 
 /* Kernel accounting (measurement; no counterpart in the paper).  Kinds:
- * 0 / 1 = factor SpMM along dim 1 / dim 2 (diagonal blocks, CT transfers),
- * 2 / 3 = transfers along dim 1 / dim 2, 4 / 5 = sweep chain steps of
- * branch A / B, 6 / 7 = sweep final updates along dim 1 / dim 2.
+ * 0 / 1 = diagonal blocks: W_b = u V_b^T / y (+)= tau X W_b,
+ * 2 / 3 = restriction of sweep chain states along dim 1 / dim 2,
+ * 4 / 5 = sweep chain steps of branch A / B,
+ * 6 / 7 = sweep final updates of branch A (dim 1) / branch B (dim 2).
  * n_kinds must be >= 8. */
 typedef struct {
   long long launches;
@@ -302,7 +304,7 @@ typedef struct {
 /* enable != 0: bracket every subsequent SpMM launch with CUDA events and
  * record its algorithmic bytes (clears earlier records); 0: stop. */
 sgdg_status sgdg_profile(void* h, int enable);
-/* Synchronise the device, fill out[0..3] (one per kind) and clear the records. */
+/* Synchronise the device, fill out[0..7] (one per kind) and clear the records. */
 sgdg_status sgdg_kernel_stats(void* h, sgdg_kernel_stat* out, int n_kinds);
 /* Number of SpMM kernels this handle has launched so far. */
 long long sgdg_launch_count(const void* h);

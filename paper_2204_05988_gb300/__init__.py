@@ -112,7 +112,8 @@ EXPORTS = {
     "sgdg_batch_advance": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
 
-KERNEL_KINDS = ("spmm_left", "spmm_right", "transfer_left", "transfer_right", "chain_a", "chain_b", "final_left", "final_right")
+KERNEL_KINDS = ("diag_chain", "diag_final", "restrict_dim1", "restrict_dim2", "chain_a", "chain_b", "final_left",
+                "final_right")
 
 
 class KernelStat(C.Structure):

@@ -6,14 +6,25 @@
 // factor and a chain of transfers:
 //   l1' <= l1:  X_{l1,l1'} = X_{l1} E_{l1<-l1'},   V_{l2,l2'} = E_{l2'<-l2}^T V_{l2'}
 //   l1' >  l1:  X_{l1,l1'} = E_{l1'<-l1}^T X_{l1'}, V_{l2,l2'} = V_{l2} E_{l2<-l2'}
-// so that, per term a = (tau, X, V) and grids i = 0..L (grid i = (i, L-i)):
-//   branch A:  S_0 = U_0 V_{L}^T,  S_i = P1(R2(S_{i-1})) + U_i V_{L-i}^T,   Y_i += tau X_i S_i
-//   branch B:  T'_L = 0, T'_i = R1(P2(T'_{i+1} + X_{i+1} U_{i+1})),        Y_i += tau T'_i V_{L-i}^T
-// (P = prolongation E, R = restriction E^T, subscript = the dimension).  This
-// reaches the blockwise sum of Sect. 4.2 exactly in exact arithmetic with
-// O(#terms * N) work; intermediates never exceed one component grid, like
-// the ordering rule of Sect. 4.2.  Terms sharing the factor applied first are
-// grouped into one chain; the others are fused in the multi-term kernels.
+// Per term a = (tau, X, V) and grids i = 0..L (grid i = (i, L-i)), summing
+// over the sources gives two recursions, each chain keyed by the factor
+// applied first (P = prolongation E, R = restriction E^T, subscript = the
+// dimension, U_i the input on grid i):
+//   branch A (sources l1' < l1), chains b by V:
+//     Z_{b,1} = U_0 (R2 V_b)^T,   Z_{b,i+1} = P1 (Z_{b,i} R2^T) + U_i (R2 V_b)^T
+//     Y_i += tau_a (X_a P1) Z_{b,i}
+//   branch B (sources l1' > l1), chains c by X:
+//     Z_{c,L-1} = (R1 X_c) U_L,   Z_{c,i} = (R1 Z_{c,i+1}) P2^T + (R1 X_c) U_{i+1}
+//     Y_i += tau_a Z_{c,i} (V_a P2)^T
+//   diagonal blocks: Y_i += tau_a X_a (U_i V_a^T)   (W_b = U_i V_b^T per chain b)
+// Z_{b,i} = S_{b,i-1} R2^T and Z_{c,i} = R1 T_{c,i+1} are the chain states of
+// the plain recursions S_i = P1 R2 S_{i-1} + U_i V^T and T'_i = R1 P2 (T'_{i+1}
+// + X U_{i+1}) taken one transfer early: they live on the coarse side of both
+// dimensions (a quarter of a grid for 2-D sides), and the products R2 V_b,
+// R1 X_c, X_a P1, V_a P2 are formed once per level on the host.  This reaches
+// the blockwise sum of Sect. 4.2 exactly in exact arithmetic with
+// O(#terms * N) work; no intermediate exceeds one component grid, like the
+// ordering rule of Sect. 4.2.
 #include <algorithm>
 
 #include "handle.h"
@@ -114,29 +125,53 @@ Status ensure_bufs(Handle& h) {
   return {};
 }
 
-// Chain-state pool of the sweep: 2 ring slots per branch-A chain, 2 ring
-// slots + 1 strict slot per branch-B chain, then the restriction
-// intermediates Z of one launch group; each slot holds one largest grid.
-inline long long pool_slots(const Plan& q) {
-  const long long a = (long long)q.A.size(), b = (long long)q.B.size();
-  return std::max(2 * a, 3 * b) + std::min<long long>(kChainSlots, std::max(a, b));
+// Sweep pool: the diagonal-block products W_b (one grid each, all A chains),
+// a ring of two chain states Z per chain of both branches, and the
+// restricted states Q of one launch group.
+struct PoolShape {
+  long long mg = 2, mz = 2, mq = 2;   // elements per W, Z and Q slot
+  long long elems(const Plan& p) const {
+    const long long a = (long long)p.A.size(), b = (long long)p.B.size();
+    return a * mg + 2 * (a + b) * mz + std::min<long long>(kChainSlots, std::max(a, b)) * mq;
+  }
+};
+
+inline PoolShape pool_shape(const Handle& h) {
+  PoolShape ps;
+  const int L = h.L;
+  for (int l = 0; l <= L; ++l) ps.mg = std::max(ps.mg, 2LL * h.n1[l] * h.n2[l]);
+  for (int i = 1; i <= L; ++i) ps.mz = std::max(ps.mz, 2LL * h.X.n[i - 1] * h.V.n[L - i]);
+  for (int i = 0; i < L; ++i) ps.mz = std::max(ps.mz, 2LL * h.X.n[i] * h.V.n[L - i - 1]);
+  for (int i = 1; i < L; ++i) ps.mq = std::max(ps.mq, 2LL * h.X.n[i - 1] * h.V.n[L - i - 1]);
+  for (int i = 0; i + 2 <= L; ++i) ps.mq = std::max(ps.mq, 2LL * h.X.n[i] * h.V.n[L - i - 2]);
+  return ps;
 }
 
 template <typename T>
-Status ensure_pool(Handle& h, const Plan& p, T** pool, long long* slot, T** zbase) {
-  long long M = 2;
-  for (int l = 0; l <= h.L; ++l) M = std::max(M, 2LL * h.n1[l] * h.n2[l]);
+struct Pool {
+  T* base = nullptr;
+  PoolShape ps;
+  size_t nA = 0, nB = 0;
+  T* W(int b) const { return base + (size_t)b * ps.mg; }
+  T* ZA(int b, int par) const { return base + nA * ps.mg + (size_t)(2 * b + par) * ps.mz; }
+  T* ZB(int c, int par) const { return base + nA * ps.mg + 2 * nA * ps.mz + (size_t)(2 * c + par) * ps.mz; }
+  T* Q(int g) const { return base + nA * ps.mg + 2 * (nA + nB) * ps.mz + (size_t)g * ps.mq; }
+};
+
+template <typename T>
+Status ensure_pool(Handle& h, const Plan& p, Pool<T>& pool) {
+  pool.ps = pool_shape(h);
+  pool.nA = p.A.size();
+  pool.nB = p.B.size();
   // sized once for the largest plan of the handle (the operator's)
-  const long long need = M * std::max(pool_slots(h.op), pool_slots(p));
+  const long long need = std::max(pool.ps.elems(h.op), pool.ps.elems(p));
   Handle::Bufs& b = bufs<T>(h);
   if (!b.pool) {
     if (dev_alloc(h, &b.pool, sizeof(T) * (size_t)need) != cudaSuccess) return {SGDG_ENOMEM, "sweep chain pool"};
     b.pool_elems = need;
   }
-  if (b.pool_elems < M * pool_slots(p)) return {SGDG_EINVAL, "sweep chain pool too small for this plan"};
-  *pool = (T*)b.pool;
-  *slot = M;
-  *zbase = (T*)b.pool + (size_t)M * std::max(2LL * (long long)p.A.size(), 3LL * (long long)p.B.size());
+  if (b.pool_elems < pool.ps.elems(p)) return {SGDG_EINVAL, "sweep chain pool too small for this plan"};
+  pool.base = (T*)b.pool;
   return {};
 }
 
@@ -151,12 +186,13 @@ inline long long site_key(int kind, int n1, int n2, int count, int elem) {
   return (((head << 24) | (long long)n1) << 24) | (long long)n2;
 }
 
-// Launch shape of a site: rows per thread (ch, 0 = heuristic) and block order
-// (tiled).  Tuned choices are stored as ch | tiled << 4.  Untuned sites take
-// the column tiles when the launch's stencil runs along dim 1 and rows are
-// long enough to fill a tile.
+// Launch shape of a site: rows per thread (ch, 0 = heuristic), block order
+// (tiled) and, for the final kernels, two outputs per thread (pair).  Tuned
+// choices are stored as ch | tiled << 4 | pair << 5.  Untuned sites take the
+// column tiles when the launch's stencil runs along dim 1 and rows are long
+// enough to fill a tile.
 struct Shape {
-  int ch = 0, tiled = 0;
+  int ch = 0, tiled = 0, pair = 0;
 };
 
 template <typename T>
@@ -169,7 +205,8 @@ Shape pick_shape(Handle& h, long long site, bool dim1_stencil, int n1, int n2) {
   Shape sh;
   if (code) {
     sh.ch = std::min(code & 15, n1);
-    sh.tiled = code >> 4;
+    sh.tiled = (code >> 4) & 1;
+    sh.pair = (code >> 5) & 1;
   } else {
     sh.tiled = dim1_stencil && n2 >= kTileW ? 1 : 0;
   }
@@ -213,53 +250,69 @@ Status run_restrict(Handle& h, RestrictArgs<T>& a, bool dim2, cudaStream_t s, do
   return {};
 }
 
-// extra_bytes: matrices and the restriction intermediates the launch reads
+// in_bytes: the matrices, U and the Q inputs the launch reads
 template <typename T>
-Status run_chain(Handle& h, ChainArgs<T>& a, bool mode_a, cudaStream_t s, double extra_bytes) {
-  const int kind = mode_a ? KIND_CHAIN_A : KIND_CHAIN_B;
+Status run_chain(Handle& h, ChainArgs<T>& a, bool mode_a, int kind, cudaStream_t s, double in_bytes) {
   const long long site = site_key(kind, a.n1, a.n2, a.nchains, sizeof(T));
-  const Shape sh = pick_shape<T>(h, site, mode_a, a.n1, a.n2);
+  const Shape sh = pick_shape<T>(h, site, !mode_a, a.n1, a.n2);
   a.ch = sh.ch;
   a.tiled = sh.tiled;
+  a.pair = sh.pair;
   ProfScope ps(h, s);
   SG_CU(launch_chain(a, mode_a, s));
-  const double g = grid_bytes<T>(a.n1, a.n2);
-  ps.done(kind, extra_bytes + g + a.nchains * g * (!mode_a && a.has_prev ? 2.0 : 1.0), site);
+  ps.done(kind, in_bytes + a.nchains * grid_bytes<T>(a.n1, a.n2), site);
   return {};
 }
 
+// mat_bytes: pattern and value rows the launch reads; in_bytes: one input
 template <typename T>
-Status run_final(Handle& h, FinalArgs<T>& f, bool left, int lev_rows, int lev_nnz, cudaStream_t s) {
-  const int kind = left ? KIND_FINAL_LEFT : KIND_FINAL_RIGHT;
+Status run_final(Handle& h, FinalArgs<T>& f, bool left, int kind, cudaStream_t s, double mat_bytes, double in_bytes) {
   const long long site = site_key(kind, f.n1, f.n2, f.nin, sizeof(T));
   const Shape sh = pick_shape<T>(h, site, left, f.n1, f.n2);
   f.ch = sh.ch;
   f.tiled = sh.tiled;
+  f.pair = sh.pair;
   ProfScope ps(h, s);
   SG_CU(launch_final(f, left, s));
   const double g = grid_bytes<T>(f.n1, f.n2);
-  ps.done(kind, csr_bytes<T>(lev_rows, lev_nnz, f.nterms) + f.nin * g + g * (f.accumulate ? 2.0 : 1.0), site);
+  ps.done(kind, mat_bytes + f.nin * in_bytes + g * (f.accumulate ? 2.0 : 1.0), site);
   return {};
 }
 
-// y_i (+)= sum over the chains' terms of tau_a F_a in_c on grid i (F on the
-// x pattern at level i when left, on the v pattern at level L-i otherwise).
-template <typename T, typename InOf>
-Status finals_on(Handle& h, const Plan& p, const std::vector<Chain>& chains, bool left, int n1, int n2, int lev,
-                 InOf in_of, bool accumulate_first, T* ygrid, cudaStream_t s) {
-  const SideDev& sd = left ? h.X : h.V;
+// ELL bytes of `rows` rows of width w: the columns plus nvals value arrays
+template <typename T>
+double ell_bytes(long long rows, int w, int nvals) {
+  return (double)rows * w * (4.0 + (double)nvals * sizeof(T));
+}
+
+// One final launch family: y (+)= sum over the chains' terms of tau_a F_a in_c
+// with F on one ELL pattern (rows: the pattern's rows, w its width).
+struct FinalSpec {
+  bool left = true;
+  int kind = KIND_DIAG_FINAL;
+  int n1 = 0, n2 = 0, nin2 = 0;      // output grid, input row length (right)
+  const int* col = nullptr;
+  int row = 8, w = 8;
+  long long mat_rows = 0;
+  double in_bytes = 0.0;
+};
+
+template <typename T, typename InOf, typename ValOf>
+Status finals_on(Handle& h, const Plan& p, const std::vector<Chain>& chains, const FinalSpec& fs, InOf in_of,
+                 ValOf val_of, bool accumulate_first, T* ygrid, cudaStream_t s) {
   FinalArgs<T> f;
-  f.n1 = n1;
-  f.n2 = n2;
-  f.row = sd.row_regs();
-  f.col = sd.ell_col[lev];
+  f.n1 = fs.n1;
+  f.n2 = fs.n2;
+  f.nin2 = fs.nin2 > 0 ? fs.nin2 : fs.n2;
+  f.row = fs.row;
+  f.col = fs.col;
   f.y = ygrid;
   bool first = true;
   auto flush = [&]() -> Status {
     if (f.nterms == 0) return {};
     f.tbeg[f.nin] = f.nterms;
     f.accumulate = first ? (accumulate_first ? 1 : 0) : 1;
-    Status st = run_final(h, f, left, sd.n[lev], sd.nnz[lev], s);
+    Status st = run_final(h, f, fs.left, fs.kind, s, ell_bytes<T>(fs.mat_rows, fs.w, f.nterms), fs.in_bytes);
     first = false;
     f.nin = 0;
     f.nterms = 0;
@@ -279,7 +332,7 @@ Status finals_on(Handle& h, const Plan& p, const std::vector<Chain>& chains, boo
         open = true;
       }
       const Term& tm = p.terms[t];
-      f.val[f.nterms] = sd.vals<T>().ell_fac[left ? tm.x : tm.v][lev];
+      f.val[f.nterms] = val_of(tm);
       for (int a = 0; a < 2; ++a)
         for (int q = 0; q < 2; ++q) f.tau[f.nterms][a * 2 + q] = (T)tm.tau[a][q];
       f.nterms++;
@@ -288,130 +341,190 @@ Status finals_on(Handle& h, const Plan& p, const std::vector<Chain>& chains, boo
   return flush();
 }
 
-template <typename T, typename InOf>
-Status finals(Handle& h, const Plan& p, const std::vector<Chain>& chains, bool left, int i, InOf in_of,
-              bool accumulate_first, T* y, cudaStream_t s) {
-  return finals_on<T>(h, p, chains, left, h.n1[i], h.n2[i], left ? i : h.L - i, in_of, accumulate_first,
-                      y + h.off[i], s);
+// Diagonal blocks on one grid (n1 x n2) = (x level lx, v level lv):
+//   W_b = u V_b^T for the chains b (by v factor), then y (+)= sum tau_a X_a W_b
+template <typename T>
+Status diag_block(Handle& h, const Plan& p, const Pool<T>& pool, int lx, int lv, const T* u, T* y,
+                  bool accumulate, cudaStream_t s) {
+  const int n1 = h.X.n[lx], n2 = h.V.n[lv];
+  const int nc = (int)p.A.size();
+  if (2LL * n1 * n2 > pool.ps.mg) return {SGDG_EINVAL, "diagonal block larger than the sweep slots"};
+  const double g = grid_bytes<T>(n1, n2);
+  for (int c0 = 0; c0 < nc; c0 += kChainSlots) {
+    ChainArgs<T> a;
+    a.n1 = n1;
+    a.n2 = n2;
+    a.nu2 = n2;
+    a.nchains = std::min(kChainSlots, nc - c0);
+    a.has_prev = 0;
+    a.row = h.V.row_regs();
+    a.U = u;
+    a.f_col = h.V.ell_col[lv];
+    for (int c = 0; c < a.nchains; ++c) {
+      a.f_val[c] = h.V.vals<T>().ell_fac[p.A[c0 + c].first][lv];
+      a.out[c] = pool.W(c0 + c);
+    }
+    Status st = run_chain(h, a, true, KIND_DIAG_CHAIN, s, g + ell_bytes<T>(n2, h.V.ell_w(), a.nchains));
+    if (st.code) return st;
+  }
+  FinalSpec fs;
+  fs.left = true;
+  fs.kind = KIND_DIAG_FINAL;
+  fs.n1 = n1;
+  fs.n2 = n2;
+  fs.col = h.X.ell_col[lx];
+  fs.row = h.X.row_regs();
+  fs.w = h.X.ell_w();
+  fs.mat_rows = n1;
+  fs.in_bytes = g;
+  return finals_on<T>(h, p, p.A, fs, [&](int c) { return (const T*)pool.W(c); },
+                      [&](const Term& tm) { return (const T*)h.X.vals<T>().ell_fac[tm.x][lx]; }, accumulate, y, s);
 }
 
 }  // namespace
 
 template <typename T>
 Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s) {
-  T* pool;
-  T* zb;
-  long long M;
-  Status st = ensure_pool<T>(h, p, &pool, &M, &zb);
+  Pool<T> pool;
+  Status st = ensure_pool<T>(h, p, pool);
   if (st.code) return st;
   const int L = h.L;
   const int G = kChainMax<T>();
   const int nA = (int)p.A.size(), nB = (int)p.B.size();
-  auto slotA = [&](int c, int par) { return pool + (size_t)(2 * c + par) * M; };
-  auto slotT = [&](int c, int par) { return pool + (size_t)(3 * c + par) * M; };
-  auto slotTP = [&](int c) { return pool + (size_t)(3 * c + 2) * M; };
-  auto slotZ = [&](int g) { return zb + (size_t)g * M; };
-  // ---- branch A (sources l1' <= l1): chains by the v factor
+  SideDev& X = h.X;
+  SideDev& V = h.V;
+  // ---- diagonal blocks and branch A (sources l1' < l1): chains by the v factor
   for (int i = 0; i <= L; ++i) {
     const int lv = L - i;
-    for (int c0 = 0; c0 < nA; c0 += G) {
-      const int nc = std::min(G, nA - c0);
-      double zbytes = 0.0;
-      if (i > 0) {
-        // Z_g = S_{g,i-1} R2^T  (n1[i-1] x n2[i])
-        RestrictArgs<T> r;
-        r.n1 = h.n1[i - 1];
-        r.n2 = h.n2[i];
-        r.n1_in = h.n1[i - 1];
-        r.n2_in = h.n2[i - 1];
-        r.nchains = nc;
-        r.row = h.V.row_regs();
-        r.col = h.V.R_ell_col[lv];
-        r.val = h.V.vals<T>().ell_R[lv];
-        for (int g = 0; g < nc; ++g) {
-          r.in[g] = slotA(c0 + g, (i - 1) & 1);
-          r.out[g] = slotZ(g);
-        }
-        st = run_restrict(h, r, true, s, csr_bytes<T>(h.V.n[lv], h.V.R_nnz[lv], 1));
-        if (st.code) return st;
-        zbytes = nc * grid_bytes<T>(r.n1, r.n2) + csr_bytes<T>(h.X.n[i], h.X.E_nnz[i - 1], 1);
-      }
-      ChainArgs<T> a;
-      a.n1 = h.n1[i];
-      a.n2 = h.n2[i];
-      a.nz2 = h.n2[i];
-      a.nchains = nc;
-      a.has_prev = i > 0;
-      a.row = h.V.row_regs();
-      a.U = u + h.off[i];
-      a.f_col = h.V.ell_col[lv];
-      for (int g = 0; g < nc; ++g) {
-        a.f_val[g] = h.V.vals<T>().ell_fac[p.A[c0 + g].first][lv];
-        a.out[g] = slotA(c0 + g, i & 1);
-        a.Z[g] = i > 0 ? slotZ(g) : nullptr;
-      }
-      if (i > 0) {
-        a.p_col = h.X.E_ell_col[i - 1];
-        a.p_val = h.X.vals<T>().ell_E[i - 1];
-      }
-      st = run_chain(h, a, true, s, csr_bytes<T>(h.V.n[lv], h.V.nnz[lv], nc) + zbytes);
+    T* yi = y + h.off[i];
+    st = diag_block<T>(h, p, pool, i, lv, u + h.off[i], yi, false, s);
+    if (st.code) return st;
+    if (i >= 1) {
+      // Y_i += sum_a tau_a (X_a P1) Z_{b,i},  Z_{b,i}: (nx[i-1] x nv[lv])
+      FinalSpec fs;
+      fs.left = true;
+      fs.kind = KIND_FINAL_LEFT;
+      fs.n1 = h.n1[i];
+      fs.n2 = h.n2[i];
+      fs.col = X.FP_ell_col[i];
+      fs.row = row_class(X.fp_row);
+      fs.w = X.fp_w();
+      fs.mat_rows = X.n[i];
+      fs.in_bytes = grid_bytes<T>(X.n[i - 1], V.n[lv]);
+      st = finals_on<T>(h, p, p.A, fs, [&](int c) { return (const T*)pool.ZA(c, i & 1); },
+                        [&](const Term& tm) { return (const T*)X.vals<T>().ell_FP[tm.x][i]; }, true, yi, s);
       if (st.code) return st;
     }
-    st = finals<T>(h, p, p.A, true, i, [&](int c) { return (const T*)slotA(c, i & 1); }, false, y, s);
-    if (st.code) return st;
+    if (i == L) break;
+    // Z_{b,i+1} = P1 (Z_{b,i} R2^T) + U_i (R2 V_b)^T:  (nx[i] x nv[lv-1])
+    for (int c0 = 0; c0 < nA; c0 += G) {
+      const int nc = std::min(G, nA - c0);
+      double qbytes = 0.0;
+      if (i >= 1) {
+        RestrictArgs<T> r;   // Q_g = Z_{b,i} R2^T: (nx[i-1] x nv[lv-1])
+        r.n1 = X.n[i - 1];
+        r.n2 = V.n[lv - 1];
+        r.n1_in = X.n[i - 1];
+        r.n2_in = V.n[lv];
+        r.nchains = nc;
+        r.row = V.row_regs();
+        r.col = V.R_ell_col[lv - 1];
+        r.val = V.vals<T>().ell_R[lv - 1];
+        for (int g = 0; g < nc; ++g) {
+          r.in[g] = pool.ZA(c0 + g, i & 1);
+          r.out[g] = pool.Q(g);
+        }
+        st = run_restrict(h, r, true, s, ell_bytes<T>(V.n[lv - 1], V.ell_w(), 1));
+        if (st.code) return st;
+        qbytes = nc * grid_bytes<T>(r.n1, r.n2) + ell_bytes<T>(X.n[i], kEllE, 1);
+      }
+      ChainArgs<T> a;
+      a.n1 = X.n[i];
+      a.n2 = V.n[lv - 1];
+      a.nu2 = V.n[lv];
+      a.nchains = nc;
+      a.has_prev = i >= 1;
+      a.row = row_class(V.rf_row);
+      a.U = u + h.off[i];
+      a.f_col = V.RF_ell_col[lv - 1];
+      for (int g = 0; g < nc; ++g) {
+        a.f_val[g] = V.vals<T>().ell_RF[p.A[c0 + g].first][lv - 1];
+        a.out[g] = pool.ZA(c0 + g, (i + 1) & 1);
+        a.Z[g] = i >= 1 ? pool.Q(g) : nullptr;
+      }
+      if (i >= 1) {
+        a.p_col = X.E_ell_col[i - 1];
+        a.p_val = X.vals<T>().ell_E[i - 1];
+      }
+      st = run_chain(h, a, true, KIND_CHAIN_A, s,
+                     qbytes + grid_bytes<T>(h.n1[i], h.n2[i]) + ell_bytes<T>(V.n[lv - 1], V.rf_w(), nc));
+      if (st.code) return st;
+    }
   }
   // ---- branch B (sources l1' > l1): chains by the x factor
-  if (L >= 1) {
-    for (int i = L; i >= 0; --i) {
-      for (int c0 = 0; c0 < nB; c0 += G) {
-        const int nc = std::min(G, nB - c0);
-        double zbytes = 0.0;
-        if (i < L) {
-          // Z_g = R1 T_{g,i+1}  (n1[i] x n2[i+1])
-          RestrictArgs<T> r;
-          r.n1 = h.n1[i];
-          r.n2 = h.n2[i + 1];
-          r.n1_in = h.n1[i + 1];
-          r.n2_in = h.n2[i + 1];
-          r.nchains = nc;
-          r.row = h.X.row_regs();
-          r.col = h.X.R_ell_col[i];
-          r.val = h.X.vals<T>().ell_R[i];
-          for (int g = 0; g < nc; ++g) {
-            r.in[g] = slotT(c0 + g, (i + 1) & 1);
-            r.out[g] = slotZ(g);
-          }
-          st = run_restrict(h, r, false, s, csr_bytes<T>(h.X.n[i], h.X.R_nnz[i], 1));
-          if (st.code) return st;
-          zbytes = nc * grid_bytes<T>(r.n1, r.n2) + csr_bytes<T>(h.V.n[L - i], h.V.E_nnz[L - i - 1], 1);
-        }
-        ChainArgs<T> a;
-        a.n1 = h.n1[i];
-        a.n2 = h.n2[i];
-        a.nz2 = i < L ? h.n2[i + 1] : 0;
-        a.nchains = nc;
-        a.has_prev = i < L;
-        a.row = h.X.row_regs();
-        a.U = u + h.off[i];
-        a.f_col = h.X.ell_col[i];
+  for (int i = L - 1; i >= 0; --i) {
+    const int lv = L - i;   // output v level; Z_{c,i}: (nx[i] x nv[lv-1])
+    for (int c0 = 0; c0 < nB; c0 += G) {
+      const int nc = std::min(G, nB - c0);
+      double qbytes = 0.0;
+      const bool prev = i < L - 1;
+      if (prev) {
+        RestrictArgs<T> r;   // Q_g = R1 Z_{c,i+1}: (nx[i] x nv[lv-2])
+        r.n1 = X.n[i];
+        r.n2 = V.n[lv - 2];
+        r.n1_in = X.n[i + 1];
+        r.n2_in = V.n[lv - 2];
+        r.nchains = nc;
+        r.row = X.row_regs();
+        r.col = X.R_ell_col[i];
+        r.val = X.vals<T>().ell_R[i];
         for (int g = 0; g < nc; ++g) {
-          a.f_val[g] = h.X.vals<T>().ell_fac[p.B[c0 + g].first][i];
-          a.out[g] = slotT(c0 + g, i & 1);
-          a.Z[g] = i < L ? slotZ(g) : nullptr;
-          a.strict[g] = i < L ? slotTP(c0 + g) : nullptr;
+          r.in[g] = pool.ZB(c0 + g, (i + 1) & 1);
+          r.out[g] = pool.Q(g);
         }
-        if (i < L) {
-          a.p_col = h.V.E_ell_col[L - i - 1];
-          a.p_val = h.V.vals<T>().ell_E[L - i - 1];
-        }
-        st = run_chain(h, a, false, s, csr_bytes<T>(h.X.n[i], h.X.nnz[i], nc) + zbytes);
+        st = run_restrict(h, r, false, s, ell_bytes<T>(X.n[i], X.ell_w(), 1));
         if (st.code) return st;
+        qbytes = nc * grid_bytes<T>(r.n1, r.n2) + ell_bytes<T>(V.n[lv - 1], kEllE, 1);
       }
-      if (i < L) {
-        st = finals<T>(h, p, p.B, false, i, [&](int c) { return (const T*)slotTP(c); }, true, y, s);
-        if (st.code) return st;
+      // Z_{c,i} = Q P2^T + (R1 X_c) U_{i+1}
+      ChainArgs<T> a;
+      a.n1 = X.n[i];
+      a.n2 = V.n[lv - 1];
+      a.nu2 = V.n[lv - 1];
+      a.nz2 = prev ? V.n[lv - 2] : 0;
+      a.nchains = nc;
+      a.has_prev = prev;
+      a.row = row_class(X.rf_row);
+      a.U = u + h.off[i + 1];
+      a.f_col = X.RF_ell_col[i];
+      for (int g = 0; g < nc; ++g) {
+        a.f_val[g] = X.vals<T>().ell_RF[p.B[c0 + g].first][i];
+        a.out[g] = pool.ZB(c0 + g, i & 1);
+        a.Z[g] = prev ? pool.Q(g) : nullptr;
       }
+      if (prev) {
+        a.p_col = V.E_ell_col[lv - 2];
+        a.p_val = V.vals<T>().ell_E[lv - 2];
+      }
+      st = run_chain(h, a, false, KIND_CHAIN_B, s,
+                     qbytes + grid_bytes<T>(h.n1[i + 1], h.n2[i + 1]) + ell_bytes<T>(X.n[i], X.rf_w(), nc));
+      if (st.code) return st;
     }
+    // Y_i += sum_a tau_a Z_{c,i} (V_a P2)^T
+    FinalSpec fs;
+    fs.left = false;
+    fs.kind = KIND_FINAL_RIGHT;
+    fs.n1 = h.n1[i];
+    fs.n2 = h.n2[i];
+    fs.nin2 = V.n[lv - 1];
+    fs.col = V.FP_ell_col[lv];
+    fs.row = row_class(V.fp_row);
+    fs.w = V.fp_w();
+    fs.mat_rows = V.n[lv];
+    fs.in_bytes = grid_bytes<T>(X.n[i], V.n[lv - 1]);
+    st = finals_on<T>(h, p, p.B, fs, [&](int c) { return (const T*)pool.ZB(c, i & 1); },
+                      [&](const Term& tm) { return (const T*)V.vals<T>().ell_FP[tm.v][lv]; }, true, y + h.off[i], s);
+    if (st.code) return st;
   }
   return {};
 }
@@ -426,34 +539,11 @@ template Status apply_plan<float>(Handle&, const Plan&, const float*, float*, cu
 template <typename T>
 Status apply_diag_grids(Handle& h, int ng, const int* l1, const int* l2, const T* const* u, T* const* y,
                         cudaStream_t s) {
-  T* pool;
-  T* zb;
-  long long M;
-  Status st = ensure_pool<T>(h, h.op, &pool, &M, &zb);
+  Pool<T> pool;
+  Status st = ensure_pool<T>(h, h.op, pool);
   if (st.code) return st;
-  const std::vector<Chain>& chains = h.op.A;   // by v factor
-  const int nc = (int)chains.size();
   for (int g = 0; g < ng; ++g) {
-    const int n1 = h.X.n[l1[g]], n2 = h.V.n[l2[g]];
-    if (2LL * n1 * n2 > M) return {SGDG_EINVAL, "diagonal apply grid larger than the sweep slots"};
-    for (int c0 = 0; c0 < nc; c0 += kChainSlots) {
-      ChainArgs<T> a;
-      a.n1 = n1;
-      a.n2 = n2;
-      a.nchains = std::min(kChainSlots, nc - c0);
-      a.has_prev = 0;
-      a.row = h.V.row_regs();
-      a.U = u[g];
-      a.f_col = h.V.ell_col[l2[g]];
-      for (int c = 0; c < a.nchains; ++c) {
-        a.f_val[c] = h.V.vals<T>().ell_fac[chains[c0 + c].first][l2[g]];
-        a.out[c] = pool + (size_t)(c0 + c) * M;
-      }
-      st = run_chain(h, a, true, s, csr_bytes<T>(n2, h.V.nnz[l2[g]], a.nchains));
-      if (st.code) return st;
-    }
-    st = finals_on<T>(h, h.op, chains, true, n1, n2, l1[g], [&](int c) { return (const T*)(pool + (size_t)c * M); },
-                      false, y[g], s);
+    st = diag_block<T>(h, h.op, pool, l1[g], l2[g], u[g], y[g], false, s);
     if (st.code) return st;
   }
   return {};
@@ -500,8 +590,11 @@ Status nodal_eval(Handle& h, const double* u, double* out, cudaStream_t s) {
 
 template <typename T>
 Status autotune(Handle& h, const T* u, T* y, cudaStream_t s) {
-  // rows per thread x block order, encoded as ch | tiled << 4
-  const int cand[] = {1, 2, 4, 8, 1 | 16, 2 | 16, 4 | 16, 8 | 16};
+  // rows per thread x block order x paired outputs, encoded as ch | tiled << 4 | pair << 5
+  std::vector<int> cand;
+  for (int pair = 0; pair < 2; ++pair)
+    for (int tiled = 0; tiled < 2; ++tiled)
+      for (int ch : {1, 2, 4, 8}) cand.push_back(ch | tiled << 4 | pair << 5);
   std::map<long long, std::pair<float, int>> best;
   const bool prof_was = h.prof;
   for (int c : cand) {

@@ -99,7 +99,55 @@ Status upload_ell_vals(Handle& h, const std::vector<int>& rowptr, const std::vec
   return {};
 }
 
+Status upload_factor_products(Handle& h, const Hierarchy& hi, SideDev& sd, int f, const std::vector<Csr>& X) {
+  const int L = hi.L;
+  std::vector<double> v;
+  for (int l = 0; l < L; ++l) {
+    product_values(hi.Rt[l], hi.Rt[l].val, X[l + 1], X[l + 1].val, sd.RF_pat[l], v);
+    SG_ST(upload_ell_vals(h, sd.RF_pat[l].rowptr, v, sd.rf_w(), &sd.v64.ell_RF[f][l], &sd.v32.ell_RF[f][l]));
+  }
+  for (int l = 1; l <= L; ++l) {
+    product_values(X[l], X[l].val, hi.E[l - 1], hi.E[l - 1].val, sd.FP_pat[l], v);
+    SG_ST(upload_ell_vals(h, sd.FP_pat[l].rowptr, v, sd.fp_w(), &sd.v64.ell_FP[f][l], &sd.v32.ell_FP[f][l]));
+  }
+  return {};
+}
+
 namespace {
+
+// Patterns of the factor-transfer products R_l F_{l+1} and F_l E_{l-1}
+// (shared by every factor of the side), uploaded in ELL form.
+Status setup_products(Handle& h, const Hierarchy& hi, SideDev& sd) {
+  const int L = hi.L;
+  sd.RF_pat.assign(L, Csr());
+  sd.FP_pat.assign(L + 1, Csr());
+  sd.rf_row = sd.fp_row = 0;
+  for (int l = 0; l < L; ++l) {
+    sd.RF_pat[l] = product_pattern(hi.Rt[l], hi.lev[l + 1].pattern);
+    for (int r = 0; r < sd.RF_pat[l].nrows; ++r)
+      sd.rf_row = std::max(sd.rf_row, sd.RF_pat[l].rowptr[r + 1] - sd.RF_pat[l].rowptr[r]);
+  }
+  for (int l = 1; l <= L; ++l) {
+    sd.FP_pat[l] = product_pattern(hi.lev[l].pattern, hi.E[l - 1]);
+    for (int r = 0; r < sd.FP_pat[l].nrows; ++r)
+      sd.fp_row = std::max(sd.fp_row, sd.FP_pat[l].rowptr[r + 1] - sd.FP_pat[l].rowptr[r]);
+  }
+  if (sd.rf_row > kMaxChainRow) return {SGDG_EINVAL, "restriction-factor product rows longer than 24 entries"};
+  if (sd.fp_row > kMaxFinalRow) return {SGDG_EINVAL, "factor-prolongation product rows longer than 16 entries"};
+  sd.rf_row = std::max(sd.rf_row, 1);
+  sd.fp_row = std::max(sd.fp_row, 1);
+  sd.RF_ell_col.assign(L, nullptr);
+  sd.FP_ell_col.assign(L + 1, nullptr);
+  for (int l = 0; l < L; ++l) {
+    const std::vector<int> c = ell_columns(sd.RF_pat[l].rowptr, sd.RF_pat[l].col, sd.rf_w());
+    SG_ST(upload(h, &sd.RF_ell_col[l], c.data(), c.size()));
+  }
+  for (int l = 1; l <= L; ++l) {
+    const std::vector<int> c = ell_columns(sd.FP_pat[l].rowptr, sd.FP_pat[l].col, sd.fp_w());
+    SG_ST(upload(h, &sd.FP_ell_col[l], c.data(), c.size()));
+  }
+  return {};
+}
 
 Status upload_side(Handle& h, const Hierarchy& hi, SideDev& sd) {
   const int L = hi.L;
@@ -244,6 +292,8 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   h.V.maxrow = side_maxrow[1];
   SG_ST(upload_side(h, hx, h.X));
   SG_ST(upload_side(h, hv, h.V));
+  SG_ST(setup_products(h, hx, h.X));
+  SG_ST(setup_products(h, hv, h.V));
   for (int side = 0; side < 2; ++side) {
     SideDev& sd = side == 0 ? h.X : h.V;
     const Hierarchy& hi = side == 0 ? hx : hv;
@@ -253,6 +303,10 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
     sd.v32.fac.assign(fs.size(), std::vector<float*>(h.L + 1, nullptr));
     sd.v64.ell_fac.assign(fs.size(), std::vector<double*>(h.L + 1, nullptr));
     sd.v32.ell_fac.assign(fs.size(), std::vector<float*>(h.L + 1, nullptr));
+    sd.v64.ell_RF.assign(fs.size(), std::vector<double*>(h.L + 1, nullptr));
+    sd.v32.ell_RF.assign(fs.size(), std::vector<float*>(h.L + 1, nullptr));
+    sd.v64.ell_FP.assign(fs.size(), std::vector<double*>(h.L + 1, nullptr));
+    sd.v32.ell_FP.assign(fs.size(), std::vector<float*>(h.L + 1, nullptr));
     for (size_t f = 0; f < fs.size(); ++f) {
       for (int id : fs[f].wfn)
         if (!fns.fn[id]) return {SGDG_EINVAL, "factor references a missing coefficient function"};
@@ -263,6 +317,7 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
         SG_ST(upload_ell_vals(h, hi.lev[l].pattern.rowptr, X[l].val, sd.ell_w(), &sd.v64.ell_fac[f][l],
                               &sd.v32.ell_fac[f][l]));
       }
+      SG_ST(upload_factor_products(h, hi, sd, (int)f, X));
       if ((int)f == sd.mass) {
         sd.v64.dinv.resize(h.L + 1);
         sd.v32.dinv.resize(h.L + 1);

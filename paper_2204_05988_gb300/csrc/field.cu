@@ -249,6 +249,8 @@ Status field_update(Handle& h, int source, double* energy) {
                            &h.X.v32.ell_fac[f][l]);
       if (st.code) return st;
     }
+    st = upload_factor_products(h, F.hx, h.X, (int)f, X);
+    if (st.code) return st;
   }
   return {};
 }

@@ -18,6 +18,9 @@ struct SideValues {
   // zero padding (w = SideDev::ell_w(); E: kEllE)
   std::vector<std::vector<T*>> ell_fac;   // [factor][level]
   std::vector<T*> ell_E, ell_R;
+  // products with the transfers, ELL: RF[f][l] = R_l F_{l+1} (l < L, width
+  // rf_w), FP[f][l] = F_l E_{l-1} (1 <= l <= L, width fp_w)
+  std::vector<std::vector<T*>> ell_RF, ell_FP;
 };
 
 constexpr int kEllE = 2;   // ELL width of the prolongation (rows of at most 2 entries)
@@ -34,6 +37,13 @@ struct SideDev {
   int row_regs() const { return maxrow <= 3 ? 3 : maxrow <= 4 ? 4 : maxrow <= 7 ? 7 : 8; }
   int ell_w() const { return maxrow <= 4 ? 4 : 8; }
   std::vector<int*> ell_col, R_ell_col, E_ell_col;   // ELL column indices (padding repeats the first column)
+  // patterns of the factor-transfer products (shared by all factors of the side)
+  std::vector<int*> RF_ell_col, FP_ell_col;          // [l] as SideValues::ell_RF / ell_FP
+  int rf_row = 0, fp_row = 0;                        // longest product rows
+  static int ell_width(int row) { return (row + 3) / 4 * 4; }
+  int rf_w() const { return ell_width(rf_row); }
+  int fp_w() const { return ell_width(fp_row); }
+  std::vector<Csr> RF_pat, FP_pat;                   // host patterns (FP_pat[0] empty)
   SideValues<double> v64;
   SideValues<float> v32;
   template <typename T> SideValues<T>& vals();
@@ -100,7 +110,8 @@ struct Handle {
   struct KEvent { int kind; double bytes; cudaEvent_t e0, e1; long long site; };
   std::vector<KEvent> kev;
   // autotuner: launch shape per launch site (kind and grid shape), stored as
-  // rows per thread | block order << 4; force_ch > 0 overrides every site while tuning
+  // rows per thread | block order << 4 | paired outputs << 5; force_ch > 0
+  // overrides every site while tuning
   std::map<long long, int> tuned_ch;
   int force_ch = 0;
   // Vlasov-Poisson coupling (kept only when cfg.vlasov_poisson)
@@ -121,7 +132,7 @@ struct Handle {
 
 // kinds of SpMM launches for the per-kernel statistics
 enum {
-  KIND_LEFT = 0, KIND_RIGHT = 1, KIND_XFER_LEFT = 2, KIND_XFER_RIGHT = 3,
+  KIND_DIAG_CHAIN = 0, KIND_DIAG_FINAL = 1, KIND_XFER_LEFT = 2, KIND_XFER_RIGHT = 3,
   KIND_CHAIN_A = 4, KIND_CHAIN_B = 5, KIND_FINAL_LEFT = 6, KIND_FINAL_RIGHT = 7, KIND_COUNT = 8
 };
 
@@ -137,6 +148,9 @@ cudaError_t dev_alloc(Handle& h, void** p, size_t bytes);
 // padded columns repeat the row's first column, padded values are zero.
 std::vector<int> ell_columns(const std::vector<int>& rowptr, const std::vector<int>& col, int w);
 std::vector<double> ell_values(const std::vector<int>& rowptr, const std::vector<double>& val, int w);
+// Values of factor f's products with the transfers (R_l F_{l+1}, F_l E_{l-1})
+// from its per-level matrices X, uploaded in ELL form (allocated on first use).
+Status upload_factor_products(Handle& h, const Hierarchy& hi, SideDev& sd, int f, const std::vector<Csr>& X);
 // Uploads the FP64 and FP32 ELL values; allocates when *d64 is null, else overwrites.
 Status upload_ell_vals(Handle& h, const std::vector<int>& rowptr, const std::vector<double>& val, int w,
                        double** d64, float** d32);

@@ -94,6 +94,12 @@ struct TermTable {
 Status build_terms(const sgdg_coeffs& c, int d, const sgdg_mesh& mx, const sgdg_mesh& mv,
                    double dt, double delta, TermTable& out);
 
+// C = A B: the structural pattern (sorted rows, no values) and the values of
+// A B on that pattern (aval, bval: values of A and B on their patterns).
+Csr product_pattern(const Csr& A, const Csr& B);
+void product_values(const Csr& A, const std::vector<double>& aval, const Csr& B, const std::vector<double>& bval,
+                    const Csr& C, std::vector<double>& cval);
+
 // Load vector F[i] = int fn phi_i on the finest level, restricted to all levels.
 Status load_vectors(const Hierarchy& h, sgdg_fn fn, void* user, std::vector<std::vector<double>>& per_level);
 

@@ -70,6 +70,7 @@ Status diag_noalloc(Handle& h, int l1, int l2, const T* u, T* y, cudaStream_t s)
     a.n1 = n1;
     a.n2 = n2;
     a.nchains = std::min(kChainSlots, nc - c0);
+    a.nu2 = n2;
     a.row = h.V.row_regs();
     a.U = u;
     a.f_col = h.V.ell_col[l2];

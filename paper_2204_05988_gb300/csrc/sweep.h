@@ -1,4 +1,5 @@
-// Arguments of the sweep kernels (sweep.cu).
+// Arguments of the sweep kernels (sweep_restrict.cu, sweep_chain.cu,
+// sweep_final.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,21 +24,35 @@ constexpr int kProlongRow = 2;    // entries of a prolongation row (nested P1 re
 constexpr int kTileW = 64;
 
 // Matrices reach the sweep kernels in ELL form: row r's entries at
-// [r w, r w + w) of a column and a value array, w = 4 for rows of at most 4
-// entries and 8 otherwise (prolongation: w = 2), zero values in the padding.
-// `row` (3, 4, 7 or 8) is the longest row; the kernels keep that many entries
-// in registers.
+// [r w, r w + w) of a column and a value array, w = the longest row rounded
+// up to a multiple of 4 (16-byte rows for vector loads; prolongation: w = 2),
+// zero values in the padding.  `row` is the register row length a launch is
+// compiled for: row_class(longest row), with ELL width (row + 3) / 4 * 4.
+inline int row_class(int r) {
+  if (r <= 3) return 3;
+  if (r <= 4) return 4;
+  if (r <= 5) return 5;
+  if (r <= 7) return 7;
+  if (r <= 8) return 8;
+  if (r <= 12) return 12;
+  if (r <= 16) return 16;
+  if (r <= 19) return 19;
+  if (r <= 20) return 20;
+  if (r <= 24) return 24;
+  return -1;
+}
+constexpr int kMaxRestrictRow = 8;   // restriction rows (P1 nested meshes)
+constexpr int kMaxFinalRow = 16;     // factor and factor-prolongation rows
+constexpr int kMaxChainRow = 24;     // restriction-factor product rows
 
-// Restriction of up to kChainSlots chain states of the previous grid, the
-// first half of a chain step's transfer (restriction before prolongation
-// keeps the intermediate on the coarser of the two grids):
-//   dim 1:  Z_g = R in_g          (R rows n1, cols n1_in; n2 == n2_in)
-//   dim 2:  Z_g = in_g R^T        (R rows n2, cols n2_in; n1 == n1_in)
+// Restriction of up to kChainSlots chain intermediates:
+//   dim 1:  Q_g = R in_g          (R rows n1, cols n1_in; n2 == n2_in)
+//   dim 2:  Q_g = in_g R^T        (R rows n2, cols n2_in; n1 == n1_in)
 // All arrays are (rows x cols) with the time index innermost ([..][2]).
 template <typename T>
 struct RestrictArgs {
   int n1 = 0, n2 = 0, n1_in = 0, n2_in = 0;
-  int nchains = 0, ch = 0, row = 8;   // ch: rows per thread (0: heuristic); row: longest R row
+  int nchains = 0, ch = 0, row = 8;   // ch: rows per thread (0: heuristic)
   int tiled = 0;                      // block order: 0 row-major, 1 column tiles (see kTileW)
   const int* col = nullptr;           // R, ELL
   const T* val = nullptr;
@@ -45,32 +60,37 @@ struct RestrictArgs {
   T* out[kChainSlots] = {};
 };
 
-// One chain step on grid i = (n1 x n2) for up to kChainSlots chains:
-//  mode A: out = P1 Z + U V_c^T               (Z = prev R2^T, n1_prev x n2)
-//  mode B: strict = Z P2^T, out = strict + X_c U   (Z = R1 prev, n1 x n2_prev)
-// f_*: the chains' first factor on one shared pattern (A: v level, rows n2;
-// B: x level, rows n1); p_*: the prolongation (A: P1 rows n1, B: P2 rows n2).
+// One chain step producing (n1 x n2) outputs for up to kChainSlots chains,
+// with the chains' first factors F_g on one shared pattern:
+//  mode A: out_g[k1][k2] = sum_j F_g[k2][j] U[k1][col_j]   (U rows of length nu2)
+//                        + sum_q P[k1][q] Q_g[col_q][k2]   (Q rows of length n2)
+//  mode B: out_g[k1][k2] = sum_j F_g[k1][j] U[col_j][k2]   (U rows of length n2)
+//                        + sum_q P[k2][q] Q_g[k1][col_q]   (Q rows of length nz2)
+// The Q part is present when has_prev; P is a prolongation (ELL width 2).
 template <typename T>
 struct ChainArgs {
-  int n1 = 0, n2 = 0, nz2 = 0;   // nz2: row length of Z (A: n2, B: n2_prev)
-  int nchains = 0, has_prev = 0, ch = 0, row = 8;   // row: longest first-factor row
+  int n1 = 0, n2 = 0, nu2 = 0, nz2 = 0;
+  int nchains = 0, has_prev = 0, ch = 0, row = 8;
   int tiled = 0;
+  int pair = 0;   // mode A without Q, rows of at most 8: two rows per thread
   const T* U = nullptr;
   const int* f_col = nullptr;    // ELL
   const T* f_val[kChainSlots] = {};
   const int* p_col = nullptr;    // ELL, width 2
   const T* p_val = nullptr;
-  const T* Z[kChainSlots] = {};
+  const T* Z[kChainSlots] = {};  // the Q inputs
   T* out[kChainSlots] = {};
-  T* strict[kChainSlots] = {};
 };
 
-// y (+)= sum_c sum_{t in c} tau_t (x) F_t in_c on one grid: F_t along dim 1
-// (left) or dim 2 (right), all F_t on one shared pattern.  The terms of input
-// c are tbeg[c] .. tbeg[c+1]-1.
+// y (+)= sum_c sum_{t in c} tau_t (x) F_t in_c on one (n1 x n2) grid, all F_t
+// on one shared pattern:
+//   left:  y[k1][k2] += sum_j F_t[k1][j] in_c[col_j][k2]   (in rows of length n2)
+//   right: y[k1][k2] += sum_j F_t[k2][j] in_c[k1][col_j]   (in rows of length nin2)
+// The terms of input c are tbeg[c] .. tbeg[c+1]-1.
 template <typename T>
 struct FinalArgs {
-  int n1 = 0, n2 = 0, ch = 0, row = 8, accumulate = 0, tiled = 0;
+  int n1 = 0, n2 = 0, nin2 = 0, ch = 0, row = 8, accumulate = 0, tiled = 0;
+  int pair = 0;   // two outputs per thread: left - columns k2, k2 + 32; right - rows k1, k1 + 1
   int nin = 0, nterms = 0;
   const T* in[kFinalIn] = {};
   int tbeg[kFinalIn + 1] = {};

@@ -1,0 +1,182 @@
+// Chain steps of the sparse-grid operator sweep (sm_103a), for up to
+// kChainSlots chains that share their first factor's pattern:
+//  mode A: out_g[k1][k2] = sum_j F_g[k2][j] U[k1][col_j] + sum_q P[k1][q] Q_g[col_q][k2]
+//  mode B: out_g[k1][k2] = sum_j F_g[k1][j] U[col_j][k2] + sum_q P[k2][q] Q_g[k1][col_q]
+// One thread per column k2 of a chunk of rows.  The shared operand - U
+// gathered along the pattern row - is loaded once per element into
+// registers and used by every chain; for rows of at most 8 entries the next
+// chain's factor row and Q values are loaded before the current chain is
+// combined and stored.
+#include "sweep_common.cuh"
+
+namespace sgdg {
+
+namespace {
+
+using namespace sweep;
+
+template <typename T, int ROW>
+struct ChainBounds {
+  static constexpr int blocks = ROW > 8 ? 2 : (sizeof(T) == 4 ? 4 : 2);
+};
+
+template <typename T, bool MODE_A, int ROW>
+__global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW>::blocks)) k_chain(const __grid_constant__ ChainArgs<T> a) {
+  using T2 = typename V2<T>::type;
+  constexpr int W = Ell<ROW>::W;
+  constexpr bool kPrefetch = ROW <= 8;
+  const unsigned n2 = (unsigned)a.n2;
+  unsigned k2;
+  int r0, r1;
+  if (!thread_rows(a.n1, a.n2, a.ch, a.tiled, k2, r0, r1)) return;
+  unsigned fc[ROW];
+  unsigned pc[kProlongRow] = {0, 0};
+  T pv[kProlongRow] = {0, 0};
+  if (MODE_A) ell_cols<ROW>(a.f_col + (size_t)k2 * W, fc);          // F row k2
+  else if (a.has_prev) prolong_row(a.p_col, a.p_val, k2, pc, pv);   // P row k2
+  const T2* U = reinterpret_cast<const T2*>(a.U);
+  for (int k1 = r0; k1 < r1; ++k1) {
+    // the shared operand of the chains: U gathered along the first factor's row
+    T2 u[ROW];
+    unsigned zo[kProlongRow];
+    if (MODE_A) {
+      unsigned off[ROW];
+#pragma unroll
+      for (int j = 0; j < ROW; ++j) off[j] = (unsigned)k1 * (unsigned)a.nu2 + fc[j];
+      gather(U, off, u);
+      if (a.has_prev) prolong_row(a.p_col, a.p_val, (unsigned)k1, pc, pv);   // P row k1
+#pragma unroll
+      for (int q = 0; q < kProlongRow; ++q) zo[q] = pc[q] * n2 + k2;
+    } else {
+      ell_cols<ROW>(a.f_col + (size_t)k1 * W, fc);   // F row k1 (uniform in a warp)
+      unsigned off[ROW];
+#pragma unroll
+      for (int j = 0; j < ROW; ++j) off[j] = fc[j] * n2 + k2;
+      gather(U, off, u);
+#pragma unroll
+      for (int q = 0; q < kProlongRow; ++q) zo[q] = (unsigned)k1 * (unsigned)a.nz2 + pc[q];
+    }
+    const size_t o = (size_t)k1 * n2 + k2;
+    const size_t frow = (size_t)(MODE_A ? k2 : (unsigned)k1) * W;
+    T fv[ROW];
+    T2 z[kProlongRow];
+#pragma unroll
+    for (int q = 0; q < kProlongRow; ++q) z[q].x = z[q].y = 0;
+    if (kPrefetch) ell_vals<ROW>(a.f_val[0] + frow, fv);
+    if (a.has_prev) gather(reinterpret_cast<const T2*>(a.Z[0]), zo, z);
+    for (int g = 0; g < a.nchains; ++g) {
+      T cv[ROW];
+      T2 cz[kProlongRow];
+      if (kPrefetch) {
+#pragma unroll
+        for (int j = 0; j < ROW; ++j) cv[j] = fv[j];
+      }
+#pragma unroll
+      for (int q = 0; q < kProlongRow; ++q) cz[q] = z[q];
+      if (g + 1 < a.nchains) {
+        if (kPrefetch) ell_vals<ROW>(a.f_val[g + 1] + frow, fv);
+        if (a.has_prev) gather(reinterpret_cast<const T2*>(a.Z[g + 1]), zo, z);
+      }
+      if (!kPrefetch) ell_vals<ROW>(a.f_val[g] + frow, cv);
+      T zx = 0, zy = 0;
+      if (a.has_prev) {
+#pragma unroll
+        for (int q = 0; q < kProlongRow; ++q) {
+          zx += pv[q] * cz[q].x;
+          zy += pv[q] * cz[q].y;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < ROW; ++j) {
+        zx += cv[j] * u[j].x;
+        zy += cv[j] * u[j].y;
+      }
+      T2 r;
+      r.x = zx;
+      r.y = zy;
+      reinterpret_cast<T2*>(a.out[g])[o] = r;
+    }
+  }
+}
+
+// Mode A without a prolongated part, two rows (k1, k1 + 1) per thread: the
+// factor row k2 is loaded once per chain for both rows (the diagonal-block
+// products W_b = U V_b^T).
+template <typename T, bool MODE_A, int ROW>
+__global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW>::blocks)) k_chain_pair(const __grid_constant__ ChainArgs<T> a) {
+  static_assert(MODE_A && ROW <= 8, "row pairs: mode A, short rows");
+  using T2 = typename V2<T>::type;
+  constexpr int W = Ell<ROW>::W;
+  const unsigned n2 = (unsigned)a.n2;
+  unsigned k2;
+  int r0, r1;
+  if (!thread_rows(a.n1, a.n2, a.ch, a.tiled, k2, r0, r1)) return;
+  unsigned fc[ROW];
+  ell_cols<ROW>(a.f_col + (size_t)k2 * W, fc);
+  const T2* U = reinterpret_cast<const T2*>(a.U);
+  const size_t frow = (size_t)k2 * W;
+  for (int k1 = r0; k1 < r1; k1 += 2) {
+    const bool b_ok = k1 + 1 < r1;
+    T2 ua[ROW], ub[ROW];
+#pragma unroll
+    for (int j = 0; j < ROW; ++j) {
+      const unsigned off = (unsigned)k1 * (unsigned)a.nu2 + fc[j];
+      ua[j] = U[off];
+      if (b_ok) ub[j] = U[off + (unsigned)a.nu2];
+      else ub[j].x = ub[j].y = 0;
+    }
+    const size_t o = (size_t)k1 * n2 + k2;
+    T fv[ROW];
+    ell_vals<ROW>(a.f_val[0] + frow, fv);
+    for (int g = 0; g < a.nchains; ++g) {
+      T cv[ROW];
+#pragma unroll
+      for (int j = 0; j < ROW; ++j) cv[j] = fv[j];
+      if (g + 1 < a.nchains) ell_vals<ROW>(a.f_val[g + 1] + frow, fv);
+      T ax = 0, ay = 0, bx = 0, by = 0;
+#pragma unroll
+      for (int j = 0; j < ROW; ++j) {
+        ax += cv[j] * ua[j].x;
+        ay += cv[j] * ua[j].y;
+        bx += cv[j] * ub[j].x;
+        by += cv[j] * ub[j].y;
+      }
+      T2* out = reinterpret_cast<T2*>(a.out[g]) + o;
+      T2 r;
+      r.x = ax;
+      r.y = ay;
+      out[0] = r;
+      if (b_ok) {
+        r.x = bx;
+        r.y = by;
+        out[n2] = r;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_chain(ChainArgs<T>& a, bool mode_a, cudaStream_t s) {
+  if (a.nchains < 1 || a.nchains > kChainSlots || row_class(a.row) != a.row || a.row > kMaxChainRow)
+    return cudaErrorInvalidValue;
+  if (a.n1 <= 0 || a.n2 <= 0) return cudaSuccess;
+  if (a.nu2 <= 0) a.nu2 = a.n2;
+  unsigned b = 0;
+  if (a.pair && mode_a && !a.has_prev && a.row <= 8) {
+    if (a.ch <= 0 || a.ch % 2) a.ch = a.ch <= 0 ? 2 : a.ch + 1;
+    if (!launch_shape(a.n1, a.n2, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
+    SG_SWEEP_DISPATCH(k_chain_pair, T, true, a.row, 8, b, kThreads, 0, s)
+    return cudaGetLastError();
+  }
+  if (!launch_shape(a.n1, a.n2, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
+  if (mode_a) { SG_SWEEP_DISPATCH(k_chain, T, true, a.row, kMaxChainRow, b, kThreads, 0, s) }
+  else { SG_SWEEP_DISPATCH(k_chain, T, false, a.row, kMaxChainRow, b, kThreads, 0, s) }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_chain<double>(ChainArgs<double>&, bool, cudaStream_t);
+template cudaError_t launch_chain<float>(ChainArgs<float>&, bool, cudaStream_t);
+
+}  // namespace sgdg

@@ -1,0 +1,177 @@
+// Final updates of the sparse-grid operator sweep (sm_103a):
+//   y (+)= sum_c sum_{t in c} tau_t (x) F_t in_c
+// with F_t along dim 1 (left) or dim 2 (right) on one shared pattern.  One
+// thread per column k2 of a chunk of rows: the gather offsets of the
+// pattern row are computed once and serve every input; the next input's
+// values are loaded while the current one is combined with its terms.
+#include "sweep_common.cuh"
+
+namespace sgdg {
+
+namespace {
+
+using namespace sweep;
+
+template <typename T, bool LEFT, int ROW>
+__global__ void __launch_bounds__(kThreads) k_final(const __grid_constant__ FinalArgs<T> a) {
+  using T2 = typename V2<T>::type;
+  constexpr int W = Ell<ROW>::W;
+  const unsigned n2 = (unsigned)a.n2;
+  unsigned k2;
+  int r0, r1;
+  if (!thread_rows(a.n1, a.n2, a.ch, a.tiled, k2, r0, r1)) return;
+  unsigned fc[ROW];
+  if (!LEFT) ell_cols<ROW>(a.col + (size_t)k2 * W, fc);
+  for (int k1 = r0; k1 < r1; ++k1) {
+    if (LEFT) ell_cols<ROW>(a.col + (size_t)k1 * W, fc);
+    unsigned off[ROW];
+#pragma unroll
+    for (int j = 0; j < ROW; ++j) off[j] = LEFT ? fc[j] * n2 + k2 : (unsigned)k1 * (unsigned)a.nin2 + fc[j];
+    const size_t frow = (size_t)(LEFT ? (unsigned)k1 : k2) * W;
+    const size_t o = (size_t)k1 * n2 + k2;
+    T yx = 0, yy = 0;
+    T2 w[ROW];
+    gather(reinterpret_cast<const T2*>(a.in[0]), off, w);
+    for (int ci = 0; ci < a.nin; ++ci) {
+      T2 cw[ROW];
+#pragma unroll
+      for (int j = 0; j < ROW; ++j) cw[j] = w[j];
+      if (ci + 1 < a.nin) gather(reinterpret_cast<const T2*>(a.in[ci + 1]), off, w);
+      for (int t = a.tbeg[ci]; t < a.tbeg[ci + 1]; ++t) {
+        T ev[ROW];
+        ell_vals<ROW>(a.val[t] + frow, ev);
+        T sx = 0, sy = 0;
+#pragma unroll
+        for (int j = 0; j < ROW; ++j) {
+          sx += ev[j] * cw[j].x;
+          sy += ev[j] * cw[j].y;
+        }
+        yx += a.tau[t][0] * sx + a.tau[t][1] * sy;
+        yy += a.tau[t][2] * sx + a.tau[t][3] * sy;
+      }
+    }
+    T2* y = reinterpret_cast<T2*>(a.y) + o;
+    T2 r;
+    if (a.accumulate) {
+      r = *y;
+      r.x += yx;
+      r.y += yy;
+    } else {
+      r.x = yx;
+      r.y = yy;
+    }
+    *y = r;
+  }
+}
+
+// Two outputs per thread that share the pattern row, its values and the
+// time coupling: left - columns k2 and k2 + 32 of one row (the warp covers
+// 64 consecutive columns, both loads coalesced); right - rows k1 and k1 + 1
+// of one column.
+template <typename T, bool LEFT, int ROW>
+__global__ void __launch_bounds__(kThreads) k_final2(const __grid_constant__ FinalArgs<T> a) {
+  using T2 = typename V2<T>::type;
+  constexpr int W = Ell<ROW>::W;
+  const unsigned n2 = (unsigned)a.n2;
+  // left: the thread grid runs over column pairs, 32 pairs per 64 columns
+  const int ncol = LEFT ? (a.n2 + 63) / 64 * 32 : a.n2;
+  unsigned kc;
+  int r0, r1;
+  if (!thread_rows(a.n1, ncol, a.ch, a.tiled, kc, r0, r1)) return;
+  const unsigned k2 = LEFT ? (kc >> 5) * 64 + (kc & 31) : kc;
+  if (k2 >= n2) return;
+  const bool has_b = LEFT ? k2 + 32 < n2 : true;
+  unsigned fc[ROW];
+  if (!LEFT) ell_cols<ROW>(a.col + (size_t)k2 * W, fc);
+  for (int k1 = r0; k1 < r1; k1 += LEFT ? 1 : 2) {
+    const bool b_ok = LEFT ? has_b : k1 + 1 < r1;
+    if (LEFT) ell_cols<ROW>(a.col + (size_t)k1 * W, fc);
+    unsigned off[ROW];
+#pragma unroll
+    for (int j = 0; j < ROW; ++j) off[j] = LEFT ? fc[j] * n2 + k2 : (unsigned)k1 * (unsigned)a.nin2 + fc[j];
+    const unsigned step_b = LEFT ? 32u : (unsigned)a.nin2;   // second output's gather offset
+    const size_t frow = (size_t)(LEFT ? (unsigned)k1 : k2) * W;
+    T ax = 0, ay = 0, bx = 0, by = 0;
+    for (int ci = 0; ci < a.nin; ++ci) {
+      const T2* in = reinterpret_cast<const T2*>(a.in[ci]);
+      T2 wa[ROW], wb[ROW];
+#pragma unroll
+      for (int j = 0; j < ROW; ++j) {
+        wa[j] = in[off[j]];
+        if (b_ok) wb[j] = in[off[j] + step_b];
+        else wb[j].x = wb[j].y = 0;
+      }
+      for (int t = a.tbeg[ci]; t < a.tbeg[ci + 1]; ++t) {
+        T ev[ROW];
+        ell_vals<ROW>(a.val[t] + frow, ev);
+        T sax = 0, say = 0, sbx = 0, sby = 0;
+#pragma unroll
+        for (int j = 0; j < ROW; ++j) {
+          sax += ev[j] * wa[j].x;
+          say += ev[j] * wa[j].y;
+          sbx += ev[j] * wb[j].x;
+          sby += ev[j] * wb[j].y;
+        }
+        const T t0 = a.tau[t][0], t1 = a.tau[t][1], t2 = a.tau[t][2], t3 = a.tau[t][3];
+        ax += t0 * sax + t1 * say;
+        ay += t2 * sax + t3 * say;
+        bx += t0 * sbx + t1 * sby;
+        by += t2 * sbx + t3 * sby;
+      }
+    }
+    T2* ya = reinterpret_cast<T2*>(a.y) + (size_t)k1 * n2 + k2;
+    T2* yb = LEFT ? ya + 32 : ya + n2;
+    T2 r;
+    if (a.accumulate) {
+      r = *ya;
+      r.x += ax;
+      r.y += ay;
+    } else {
+      r.x = ax;
+      r.y = ay;
+    }
+    *ya = r;
+    if (b_ok) {
+      if (a.accumulate) {
+        r = *yb;
+        r.x += bx;
+        r.y += by;
+      } else {
+        r.x = bx;
+        r.y = by;
+      }
+      *yb = r;
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_final(FinalArgs<T>& a, bool left, cudaStream_t s) {
+  if (a.nterms < 1 || a.nterms > kFinalTerms || a.nin < 1 || a.nin > kFinalIn || row_class(a.row) != a.row ||
+      a.row > kMaxFinalRow)
+    return cudaErrorInvalidValue;
+  if (a.tbeg[0] != 0 || a.tbeg[a.nin] != a.nterms) return cudaErrorInvalidValue;
+  if (a.n1 <= 0 || a.n2 <= 0) return cudaSuccess;
+  if (a.nin2 <= 0) a.nin2 = a.n2;
+  unsigned b = 0;
+  if (a.pair) {
+    // left: column pairs (32 per 64 columns); right: row pairs (ch even)
+    if (!left && (a.ch <= 0 || a.ch % 2)) a.ch = a.ch <= 0 ? 2 : a.ch + 1;
+    const int ncol = left ? (a.n2 + 63) / 64 * 32 : a.n2;
+    if (!launch_shape(a.n1, ncol, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
+    if (left) { SG_SWEEP_DISPATCH(k_final2, T, true, a.row, kMaxFinalRow, b, kThreads, 0, s) }
+    else { SG_SWEEP_DISPATCH(k_final2, T, false, a.row, kMaxFinalRow, b, kThreads, 0, s) }
+    return cudaGetLastError();
+  }
+  if (!launch_shape(a.n1, a.n2, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
+  if (left) { SG_SWEEP_DISPATCH(k_final, T, true, a.row, kMaxFinalRow, b, kThreads, 0, s) }
+  else { SG_SWEEP_DISPATCH(k_final, T, false, a.row, kMaxFinalRow, b, kThreads, 0, s) }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_final<double>(FinalArgs<double>&, bool, cudaStream_t);
+template cudaError_t launch_final<float>(FinalArgs<float>&, bool, cudaStream_t);
+
+}  // namespace sgdg
