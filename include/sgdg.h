@@ -290,10 +290,11 @@ sgdg_status sgdg_batch_apply(void* batch, const void* const* u, void* const* y, 
 sgdg_status sgdg_batch_advance(void* batch, sgdg_strip_stats* per_member);
 
 /* Kernel accounting (measurement; no counterpart in the paper).  Kinds:
- * 0 / 1 = diagonal blocks: W_b = u V_b^T / y (+)= tau X W_b,
+ * 0 = per-grid states S_b = u V_b^T (+ P1 Z_b) of the sweep's branch A and of
+ *     the diagonal blocks, 1 = final updates y (+)= tau X S_b along dim 1,
  * 2 / 3 = restriction of sweep chain states along dim 1 / dim 2,
- * 4 / 5 = sweep chain steps of branch A / B,
- * 6 / 7 = sweep final updates of branch A (dim 1) / branch B (dim 2).
+ * 4 / 5 = sweep chain steps of branch A / B, 6 = reserved (no launches),
+ * 7 = final updates of branch B along dim 2.
  * n_kinds must be >= 8. */
 typedef struct {
   long long launches;

@@ -112,7 +112,7 @@ EXPORTS = {
     "sgdg_batch_advance": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
 
-KERNEL_KINDS = ("diag_chain", "diag_final", "restrict_dim1", "restrict_dim2", "chain_a", "chain_b", "final_left",
+KERNEL_KINDS = ("s_chain", "final_left", "restrict_dim1", "restrict_dim2", "chain_a", "chain_b", "reserved",
                 "final_right")
 
 

@@ -10,18 +10,19 @@
 // over the sources gives two recursions, each chain keyed by the factor
 // applied first (P = prolongation E, R = restriction E^T, subscript = the
 // dimension, U_i the input on grid i):
-//   branch A (sources l1' < l1), chains b by V:
+//   branch A (sources l1' <= l1), chains b by V:
 //     Z_{b,1} = U_0 (R2 V_b)^T,   Z_{b,i+1} = P1 (Z_{b,i} R2^T) + U_i (R2 V_b)^T
-//     Y_i += tau_a (X_a P1) Z_{b,i}
+//     S_{b,i} = U_i V_b^T + P1 Z_{b,i},   Y_i = sum_a tau_a X_a S_{b,i}
 //   branch B (sources l1' > l1), chains c by X:
 //     Z_{c,L-1} = (R1 X_c) U_L,   Z_{c,i} = (R1 Z_{c,i+1}) P2^T + (R1 X_c) U_{i+1}
 //     Y_i += tau_a Z_{c,i} (V_a P2)^T
-//   diagonal blocks: Y_i += tau_a X_a (U_i V_a^T)   (W_b = U_i V_b^T per chain b)
 // Z_{b,i} = S_{b,i-1} R2^T and Z_{c,i} = R1 T_{c,i+1} are the chain states of
 // the plain recursions S_i = P1 R2 S_{i-1} + U_i V^T and T'_i = R1 P2 (T'_{i+1}
 // + X U_{i+1}) taken one transfer early: they live on the coarse side of both
-// dimensions (a quarter of a grid for 2-D sides), and the products R2 V_b,
-// R1 X_c, X_a P1, V_a P2 are formed once per level on the host.  This reaches
+// dimensions (a quarter of a grid for 2-D sides) and are the only states
+// carried from grid to grid; S_{b,i} (which includes the diagonal blocks) is
+// formed on each grid only to feed its final update.  The products R2 V_b,
+// R1 X_c and V_a P2 are formed once per level on the host.  This reaches
 // the blockwise sum of Sect. 4.2 exactly in exact arithmetic with
 // O(#terms * N) work; no intermediate exceeds one component grid, like the
 // ordering rule of Sect. 4.2.
@@ -289,7 +290,7 @@ double ell_bytes(long long rows, int w, int nvals) {
 // with F on one ELL pattern (rows: the pattern's rows, w its width).
 struct FinalSpec {
   bool left = true;
-  int kind = KIND_DIAG_FINAL;
+  int kind = KIND_FINAL_LEFT;
   int n1 = 0, n2 = 0, nin2 = 0;      // output grid, input row length (right)
   const int* col = nullptr;
   int row = 8, w = 8;
@@ -342,34 +343,43 @@ Status finals_on(Handle& h, const Plan& p, const std::vector<Chain>& chains, con
 }
 
 // Diagonal blocks on one grid (n1 x n2) = (x level lx, v level lv):
-//   W_b = u V_b^T for the chains b (by v factor), then y (+)= sum tau_a X_a W_b
-template <typename T>
+//   S_b = u V_b^T (+ P1 Z_b when zin is given: the chain states of branch A)
+//   for the chains b (by v factor), then y (+)= sum tau_a X_a S_b
+template <typename T, typename ZOf>
 Status diag_block(Handle& h, const Plan& p, const Pool<T>& pool, int lx, int lv, const T* u, T* y,
-                  bool accumulate, cudaStream_t s) {
+                  bool accumulate, cudaStream_t s, ZOf zin) {
   const int n1 = h.X.n[lx], n2 = h.V.n[lv];
   const int nc = (int)p.A.size();
   if (2LL * n1 * n2 > pool.ps.mg) return {SGDG_EINVAL, "diagonal block larger than the sweep slots"};
   const double g = grid_bytes<T>(n1, n2);
+  const bool prev = zin(0) != nullptr;
   for (int c0 = 0; c0 < nc; c0 += kChainSlots) {
     ChainArgs<T> a;
     a.n1 = n1;
     a.n2 = n2;
     a.nu2 = n2;
     a.nchains = std::min(kChainSlots, nc - c0);
-    a.has_prev = 0;
+    a.has_prev = prev;
     a.row = h.V.row_regs();
     a.U = u;
     a.f_col = h.V.ell_col[lv];
     for (int c = 0; c < a.nchains; ++c) {
       a.f_val[c] = h.V.vals<T>().ell_fac[p.A[c0 + c].first][lv];
       a.out[c] = pool.W(c0 + c);
+      a.Z[c] = zin(c0 + c);
     }
-    Status st = run_chain(h, a, true, KIND_DIAG_CHAIN, s, g + ell_bytes<T>(n2, h.V.ell_w(), a.nchains));
+    double in = g + ell_bytes<T>(n2, h.V.ell_w(), a.nchains);
+    if (prev) {
+      a.p_col = h.X.E_ell_col[lx - 1];
+      a.p_val = h.X.vals<T>().ell_E[lx - 1];
+      in += a.nchains * grid_bytes<T>(h.X.n[lx - 1], n2) + ell_bytes<T>(n1, kEllE, 1);
+    }
+    Status st = run_chain(h, a, true, KIND_S_CHAIN, s, in);
     if (st.code) return st;
   }
   FinalSpec fs;
   fs.left = true;
-  fs.kind = KIND_DIAG_FINAL;
+  fs.kind = KIND_FINAL_LEFT;
   fs.n1 = n1;
   fs.n2 = n2;
   fs.col = h.X.ell_col[lx];
@@ -396,25 +406,11 @@ Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s) {
   // ---- diagonal blocks and branch A (sources l1' < l1): chains by the v factor
   for (int i = 0; i <= L; ++i) {
     const int lv = L - i;
+    // S_{b,i} = U_i V_b^T + P1 Z_{b,i};  Y_i = sum_a tau_a X_a S_{b,i}
     T* yi = y + h.off[i];
-    st = diag_block<T>(h, p, pool, i, lv, u + h.off[i], yi, false, s);
+    st = diag_block<T>(h, p, pool, i, lv, u + h.off[i], yi, false, s,
+                       [&](int c) { return i >= 1 ? (const T*)pool.ZA(c, i & 1) : (const T*)nullptr; });
     if (st.code) return st;
-    if (i >= 1) {
-      // Y_i += sum_a tau_a (X_a P1) Z_{b,i},  Z_{b,i}: (nx[i-1] x nv[lv])
-      FinalSpec fs;
-      fs.left = true;
-      fs.kind = KIND_FINAL_LEFT;
-      fs.n1 = h.n1[i];
-      fs.n2 = h.n2[i];
-      fs.col = X.FP_ell_col[i];
-      fs.row = row_class(X.fp_row);
-      fs.w = X.fp_w();
-      fs.mat_rows = X.n[i];
-      fs.in_bytes = grid_bytes<T>(X.n[i - 1], V.n[lv]);
-      st = finals_on<T>(h, p, p.A, fs, [&](int c) { return (const T*)pool.ZA(c, i & 1); },
-                        [&](const Term& tm) { return (const T*)X.vals<T>().ell_FP[tm.x][i]; }, true, yi, s);
-      if (st.code) return st;
-    }
     if (i == L) break;
     // Z_{b,i+1} = P1 (Z_{b,i} R2^T) + U_i (R2 V_b)^T:  (nx[i] x nv[lv-1])
     for (int c0 = 0; c0 < nA; c0 += G) {
@@ -543,7 +539,7 @@ Status apply_diag_grids(Handle& h, int ng, const int* l1, const int* l2, const T
   Status st = ensure_pool<T>(h, h.op, pool);
   if (st.code) return st;
   for (int g = 0; g < ng; ++g) {
-    st = diag_block<T>(h, h.op, pool, l1[g], l2[g], u[g], y[g], false, s);
+    st = diag_block<T>(h, h.op, pool, l1[g], l2[g], u[g], y[g], false, s, [](int) { return (const T*)nullptr; });
     if (st.code) return st;
   }
   return {};

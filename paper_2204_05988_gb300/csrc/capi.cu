@@ -106,6 +106,7 @@ Status upload_factor_products(Handle& h, const Hierarchy& hi, SideDev& sd, int f
     product_values(hi.Rt[l], hi.Rt[l].val, X[l + 1], X[l + 1].val, sd.RF_pat[l], v);
     SG_ST(upload_ell_vals(h, sd.RF_pat[l].rowptr, v, sd.rf_w(), &sd.v64.ell_RF[f][l], &sd.v32.ell_RF[f][l]));
   }
+  if (!sd.has_fp) return {};
   for (int l = 1; l <= L; ++l) {
     product_values(X[l], X[l].val, hi.E[l - 1], hi.E[l - 1].val, sd.FP_pat[l], v);
     SG_ST(upload_ell_vals(h, sd.FP_pat[l].rowptr, v, sd.fp_w(), &sd.v64.ell_FP[f][l], &sd.v32.ell_FP[f][l]));
@@ -115,10 +116,11 @@ Status upload_factor_products(Handle& h, const Hierarchy& hi, SideDev& sd, int f
 
 namespace {
 
-// Patterns of the factor-transfer products R_l F_{l+1} and F_l E_{l-1}
-// (shared by every factor of the side), uploaded in ELL form.
-Status setup_products(Handle& h, const Hierarchy& hi, SideDev& sd) {
+// Patterns of the factor-transfer products R_l F_{l+1} and (with_fp)
+// F_l E_{l-1}, shared by every factor of the side, uploaded in ELL form.
+Status setup_products(Handle& h, const Hierarchy& hi, SideDev& sd, bool with_fp) {
   const int L = hi.L;
+  sd.has_fp = with_fp;
   sd.RF_pat.assign(L, Csr());
   sd.FP_pat.assign(L + 1, Csr());
   sd.rf_row = sd.fp_row = 0;
@@ -127,7 +129,7 @@ Status setup_products(Handle& h, const Hierarchy& hi, SideDev& sd) {
     for (int r = 0; r < sd.RF_pat[l].nrows; ++r)
       sd.rf_row = std::max(sd.rf_row, sd.RF_pat[l].rowptr[r + 1] - sd.RF_pat[l].rowptr[r]);
   }
-  for (int l = 1; l <= L; ++l) {
+  for (int l = 1; l <= L && with_fp; ++l) {
     sd.FP_pat[l] = product_pattern(hi.lev[l].pattern, hi.E[l - 1]);
     for (int r = 0; r < sd.FP_pat[l].nrows; ++r)
       sd.fp_row = std::max(sd.fp_row, sd.FP_pat[l].rowptr[r + 1] - sd.FP_pat[l].rowptr[r]);
@@ -142,7 +144,7 @@ Status setup_products(Handle& h, const Hierarchy& hi, SideDev& sd) {
     const std::vector<int> c = ell_columns(sd.RF_pat[l].rowptr, sd.RF_pat[l].col, sd.rf_w());
     SG_ST(upload(h, &sd.RF_ell_col[l], c.data(), c.size()));
   }
-  for (int l = 1; l <= L; ++l) {
+  for (int l = 1; l <= L && with_fp; ++l) {
     const std::vector<int> c = ell_columns(sd.FP_pat[l].rowptr, sd.FP_pat[l].col, sd.fp_w());
     SG_ST(upload(h, &sd.FP_ell_col[l], c.data(), c.size()));
   }
@@ -292,8 +294,9 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   h.V.maxrow = side_maxrow[1];
   SG_ST(upload_side(h, hx, h.X));
   SG_ST(upload_side(h, hv, h.V));
-  SG_ST(setup_products(h, hx, h.X));
-  SG_ST(setup_products(h, hv, h.V));
+  // the sweep uses R X (branch B), R V (branch A) and V E (branch B's final)
+  SG_ST(setup_products(h, hx, h.X, false));
+  SG_ST(setup_products(h, hv, h.V, true));
   for (int side = 0; side < 2; ++side) {
     SideDev& sd = side == 0 ? h.X : h.V;
     const Hierarchy& hi = side == 0 ? hx : hv;

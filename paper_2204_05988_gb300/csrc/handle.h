@@ -19,7 +19,7 @@ struct SideValues {
   std::vector<std::vector<T*>> ell_fac;   // [factor][level]
   std::vector<T*> ell_E, ell_R;
   // products with the transfers, ELL: RF[f][l] = R_l F_{l+1} (l < L, width
-  // rf_w), FP[f][l] = F_l E_{l-1} (1 <= l <= L, width fp_w)
+  // rf_w), FP[f][l] = F_l E_{l-1} (1 <= l <= L, width fp_w; sides with has_fp)
   std::vector<std::vector<T*>> ell_RF, ell_FP;
 };
 
@@ -40,6 +40,7 @@ struct SideDev {
   // patterns of the factor-transfer products (shared by all factors of the side)
   std::vector<int*> RF_ell_col, FP_ell_col;          // [l] as SideValues::ell_RF / ell_FP
   int rf_row = 0, fp_row = 0;                        // longest product rows
+  bool has_fp = false;                               // F E products formed for this side
   static int ell_width(int row) { return (row + 3) / 4 * 4; }
   int rf_w() const { return ell_width(rf_row); }
   int fp_w() const { return ell_width(fp_row); }
@@ -132,8 +133,8 @@ struct Handle {
 
 // kinds of SpMM launches for the per-kernel statistics
 enum {
-  KIND_DIAG_CHAIN = 0, KIND_DIAG_FINAL = 1, KIND_XFER_LEFT = 2, KIND_XFER_RIGHT = 3,
-  KIND_CHAIN_A = 4, KIND_CHAIN_B = 5, KIND_FINAL_LEFT = 6, KIND_FINAL_RIGHT = 7, KIND_COUNT = 8
+  KIND_S_CHAIN = 0, KIND_FINAL_LEFT = 1, KIND_XFER_LEFT = 2, KIND_XFER_RIGHT = 3,
+  KIND_CHAIN_A = 4, KIND_CHAIN_B = 5, KIND_RESERVED = 6, KIND_FINAL_RIGHT = 7, KIND_COUNT = 8
 };
 
 // Launch a grouped SpMM (left or right) with accounting.  mat_bytes: bytes of

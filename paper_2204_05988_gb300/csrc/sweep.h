@@ -72,7 +72,7 @@ struct ChainArgs {
   int n1 = 0, n2 = 0, nu2 = 0, nz2 = 0;
   int nchains = 0, has_prev = 0, ch = 0, row = 8;
   int tiled = 0;
-  int pair = 0;   // mode A without Q, rows of at most 8: two rows per thread
+  int pair = 0;   // mode A, rows of at most 8: two rows per thread
   const T* U = nullptr;
   const int* f_col = nullptr;    // ELL
   const T* f_val[kChainSlots] = {};

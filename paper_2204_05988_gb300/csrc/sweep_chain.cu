@@ -99,11 +99,12 @@ __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW>::blocks)) k_cha
   }
 }
 
-// Mode A without a prolongated part, two rows (k1, k1 + 1) per thread: the
-// factor row k2 is loaded once per chain for both rows (the diagonal-block
-// products W_b = U V_b^T).
+// Mode A with rows of at most 8 entries, two rows (k1, k1 + 1) per thread:
+// the factor row k2 is loaded once per chain for both rows (the
+// diagonal-block products W_b = U V_b^T, and S_b = W_b + P1 Q_b); the next
+// chain's Q values are loaded before the current chain is combined.
 template <typename T, bool MODE_A, int ROW>
-__global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW>::blocks)) k_chain_pair(const __grid_constant__ ChainArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 ? 3 : 2)) k_chain_pair(const __grid_constant__ ChainArgs<T> a) {
   static_assert(MODE_A && ROW <= 8, "row pairs: mode A, short rows");
   using T2 = typename V2<T>::type;
   constexpr int W = Ell<ROW>::W;
@@ -125,15 +126,53 @@ __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW>::blocks)) k_cha
       if (b_ok) ub[j] = U[off + (unsigned)a.nu2];
       else ub[j].x = ub[j].y = 0;
     }
+    // prolongation rows k1, k1 + 1 and their Q offsets
+    unsigned pca[kProlongRow] = {0, 0}, pcb[kProlongRow] = {0, 0};
+    T pva[kProlongRow] = {0, 0}, pvb[kProlongRow] = {0, 0};
+    unsigned zoa[kProlongRow] = {0, 0}, zob[kProlongRow] = {0, 0};
+    if (a.has_prev) {
+      prolong_row(a.p_col, a.p_val, (unsigned)k1, pca, pva);
+      if (b_ok) prolong_row(a.p_col, a.p_val, (unsigned)k1 + 1, pcb, pvb);
+      else pcb[0] = pcb[1] = pca[0];
+#pragma unroll
+      for (int q = 0; q < kProlongRow; ++q) {
+        zoa[q] = pca[q] * n2 + k2;
+        zob[q] = pcb[q] * n2 + k2;
+      }
+    }
     const size_t o = (size_t)k1 * n2 + k2;
-    T fv[ROW];
-    ell_vals<ROW>(a.f_val[0] + frow, fv);
+    T2 za[kProlongRow], zb[kProlongRow];
+#pragma unroll
+    for (int q = 0; q < kProlongRow; ++q) za[q].x = za[q].y = zb[q].x = zb[q].y = 0;
+    if (a.has_prev) {
+      gather(reinterpret_cast<const T2*>(a.Z[0]), zoa, za);
+      gather(reinterpret_cast<const T2*>(a.Z[0]), zob, zb);
+    }
     for (int g = 0; g < a.nchains; ++g) {
       T cv[ROW];
+      T2 cza[kProlongRow], czb[kProlongRow];
+      ell_vals<ROW>(a.f_val[g] + frow, cv);
 #pragma unroll
-      for (int j = 0; j < ROW; ++j) cv[j] = fv[j];
-      if (g + 1 < a.nchains) ell_vals<ROW>(a.f_val[g + 1] + frow, fv);
+      for (int q = 0; q < kProlongRow; ++q) {
+        cza[q] = za[q];
+        czb[q] = zb[q];
+      }
+      if (g + 1 < a.nchains) {
+        if (a.has_prev) {
+          gather(reinterpret_cast<const T2*>(a.Z[g + 1]), zoa, za);
+          gather(reinterpret_cast<const T2*>(a.Z[g + 1]), zob, zb);
+        }
+      }
       T ax = 0, ay = 0, bx = 0, by = 0;
+      if (a.has_prev) {
+#pragma unroll
+        for (int q = 0; q < kProlongRow; ++q) {
+          ax += pva[q] * cza[q].x;
+          ay += pva[q] * cza[q].y;
+          bx += pvb[q] * czb[q].x;
+          by += pvb[q] * czb[q].y;
+        }
+      }
 #pragma unroll
       for (int j = 0; j < ROW; ++j) {
         ax += cv[j] * ua[j].x;
@@ -164,7 +203,7 @@ cudaError_t launch_chain(ChainArgs<T>& a, bool mode_a, cudaStream_t s) {
   if (a.n1 <= 0 || a.n2 <= 0) return cudaSuccess;
   if (a.nu2 <= 0) a.nu2 = a.n2;
   unsigned b = 0;
-  if (a.pair && mode_a && !a.has_prev && a.row <= 8) {
+  if (a.pair && mode_a && a.row <= 8) {
     if (a.ch <= 0 || a.ch % 2) a.ch = a.ch <= 0 ? 2 : a.ch + 1;
     if (!launch_shape(a.n1, a.n2, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
     SG_SWEEP_DISPATCH(k_chain_pair, T, true, a.row, 8, b, kThreads, 0, s)
