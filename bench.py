@@ -34,6 +34,32 @@ import sgdg_workloads as W  # noqa: E402
 METRIC = "operator-apply GDoF/s; s/time-strip at 1e-8 rel. residual, mixed vs FP64"
 
 
+# ALU peaks derived from the unit counts and the maximum SM clock (2,070 MHz):
+# FP32 - 152 SMs x 128 FP32 lanes x 2 flops per multiply-add; FP64 - the
+# nominal GB300 non-tensor FP64 rate (1.25 TFLOP/s), far below FP32.
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
+FP64_PEAK_GFLOPS = 1250.0
+
+
+def _traffic(kind: str, L: int):
+    """DRAM bytes per launch of a sweep kernel kind from the committed ncu
+    launch-list summary, when it was taken on this workload and on the kernel
+    sources as they are now (None otherwise)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "sweep_traffic_transport2d_L9.json")
+    if L != 9 or not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    h = hashlib.sha256()
+    for rel in d["kernel_sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != d["kernel_sources_sha256"]:
+        return None
+    return d["dram_bytes_per_launch"].get(kind)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -235,6 +261,16 @@ def main():
     dom = max(st, key=lambda k: st[k]["ms"])
     ach = st[dom]["bytes"] / (st[dom]["ms"] * 1e-3) / 1e9
     tot_ms = sum(v["ms"] for v in st.values())
+    st64 = roof["f64"]
+    dom64 = max(st64, key=lambda k: st64[k]["ms"])
+    tot64 = sum(v["ms"] for v in st64.values())
+    fl64 = sum(v["flops"] for v in st64.values())
+    fp64_roof = {"bound": "alu", "kernel": dom64,
+                 "achieved": st64[dom64]["flops"] / (st64[dom64]["ms"] * 1e-3) / 1e9, "peak": FP64_PEAK_GFLOPS,
+                 "unit": "GFLOP/s", "peak_source": "nominal GB300 FP64 rate",
+                 "frac": st64[dom64]["flops"] / (st64[dom64]["ms"] * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
+                 "apply_GFLOPs": fl64 / (tot64 * 1e-3) / 1e9, "apply_frac": fl64 / (tot64 * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
+                 "share_of_apply": st64[dom64]["ms"] / tot64}
     # whole-apply effective bandwidth: the bytes the method must move per apply
     # (read u, write y, every pattern once, every factor value array once),
     # independent of the sweep's intermediates
@@ -242,18 +278,24 @@ def main():
     b_alg = (n * (4 + 4) + 4 * (inf.rows_x + inf.rows_v + 2 * (inf.L + 1))
              + 4 * inf.nnz_x * (1 + inf.n_x_factors) + 4 * inf.nnz_v * (1 + inf.n_v_factors))
     roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+                "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs", "traffic": _traffic(dom, args.L),
+                "alg_bytes_per_launch": st[dom]["bytes"] / max(1, st[dom]["launches"]),
                 "share_of_apply": st[dom]["ms"] / tot_ms,
                 "apply_effective": {"b_alg_bytes": b_alg, "GBps": b_alg / (ms32 * 1e-3) / 1e9,
                                     "frac": b_alg / (ms32 * 1e-3) / 1e9 / peak,
                                     "sweep_bytes": sum(v["bytes"] for v in st.values()),
                                     "sweep_GBps": sum(v["bytes"] for v in st.values()) / (tot_ms * 1e-3) / 1e9},
+                "fp32_alu": {"achieved": st[dom]["flops"] / (st[dom]["ms"] * 1e-3) / 1e9, "peak": FP32_PEAK_GFLOPS,
+                             "unit": "GFLOP/s",
+                             "frac": st[dom]["flops"] / (st[dom]["ms"] * 1e-3) / 1e9 / FP32_PEAK_GFLOPS},
                 "per_kind": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
-                                 "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
-                             for k, v in st.items()},
+                                 "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None,
+                                 "GFLOPs": (v["flops"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                             for k, v in st.items() if v["launches"]},
                 "f64_per_kind": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
-                                     "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
-                                 for k, v in roof["f64"].items()}}
+                                     "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None,
+                                     "GFLOPs": (v["flops"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                                 for k, v in roof["f64"].items() if v["launches"]}}
 
     # ---- end to end through the C ABI with pinned host buffers (FP64 in/out, FP32 apply)
     hu = torch.empty(n, dtype=torch.float64, pin_memory=True)
@@ -334,10 +376,12 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"transport_2d d=2 L={args.L} sigma=0.1 operator apply A^(delta) u",
-                           "dof_per_step": n, "terms": s.info.n_terms, "l2": "inputs larger than L2 (493 MB f32)",
+                           "dof_per_step": n, "terms": s.info.n_terms, "x_factors": s.info.n_x_factors,
+                           "v_factors": s.info.n_v_factors, "l2": "inputs larger than L2 (493 MB f32)",
                            "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
                            "autotune_s": round(tune_s, 2)},
-                "fp64_apply": {"value": world * n / (ms64 * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms64},
+                "fp64_apply": {"value": world * n / (ms64 * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms64,
+                               "roofline": fp64_roof},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
                 "strip": strip, "batch": batch, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -300,7 +300,10 @@ typedef struct {
   long long launches;
   double ms;        /* summed CUDA-event duration of the launches */
   double bytes;     /* summed algorithmic bytes: inputs + outputs (read and
-                       written when accumulating) + CSR pattern and values */
+                       written when accumulating) + matrix rows (ELL columns
+                       and values) */
+  double flops;     /* summed floating-point operations executed: 2 per
+                       multiply-add, padded ELL entries included */
 } sgdg_kernel_stat;
 /* enable != 0: bracket every subsequent SpMM launch with CUDA events and
  * record its algorithmic bytes (clears earlier records); 0: stop. */

@@ -117,7 +117,7 @@ KERNEL_KINDS = ("s_chain", "final_left", "restrict_dim1", "restrict_dim2", "chai
 
 
 class KernelStat(C.Structure):
-    _fields_ = [("launches", C.c_longlong), ("ms", C.c_double), ("bytes", C.c_double)]
+    _fields_ = [("launches", C.c_longlong), ("ms", C.c_double), ("bytes", C.c_double), ("flops", C.c_double)]
 
 _lib = None
 
@@ -312,7 +312,8 @@ class Solver:
     def kernel_stats(self):
         arr = (KernelStat * len(KERNEL_KINDS))()
         self._check(self.lib.sgdg_kernel_stats(self.h, arr, len(KERNEL_KINDS)))
-        return {KERNEL_KINDS[k]: {"launches": arr[k].launches, "ms": arr[k].ms, "bytes": arr[k].bytes}
+        return {KERNEL_KINDS[k]: {"launches": arr[k].launches, "ms": arr[k].ms, "bytes": arr[k].bytes,
+                                  "flops": arr[k].flops}
                 for k in range(len(KERNEL_KINDS))}
 
     def field_update(self, source: int = 0) -> float:

@@ -57,7 +57,7 @@ cudaError_t run_spmm(Handle& h, bool left, SpmmLaunch<T>& a, cudaStream_t s, int
       double out = 2.0 * sizeof(T) * (double)a.g[g].n1_out * a.g[g].n2_out;
       bytes += in * (a.g[g].in2 ? 2 : 1) + out * (a.accumulate ? 2 : 1);
     }
-    h.kev.push_back({kind, bytes, e0, e1, -1});
+    h.kev.push_back({kind, bytes, e0, e1, -1, 0.0});
   }
   return e;
 }
@@ -225,11 +225,13 @@ struct ProfScope {
       cudaEventRecord(e0, s);
     }
   }
-  void done(int kind, double bytes, long long site) {
+  // bytes: algorithmic bytes; flops: 2 per multiply-add the launch executes
+  // (padded ELL entries included)
+  void done(int kind, double bytes, long long site, double flops) {
     h.launches++;
     if (!h.prof) return;
     cudaEventRecord(e1, s);
-    h.kev.push_back({kind, bytes, e0, e1, site});
+    h.kev.push_back({kind, bytes, e0, e1, site, flops});
   }
 };
 
@@ -247,7 +249,8 @@ Status run_restrict(Handle& h, RestrictArgs<T>& a, bool dim2, cudaStream_t s, do
   a.tiled = sh.tiled;
   ProfScope ps(h, s);
   SG_CU(launch_restrict(a, dim2, s));
-  ps.done(kind, mat_bytes + a.nchains * (grid_bytes<T>(a.n1_in, a.n2_in) + grid_bytes<T>(a.n1, a.n2)), site);
+  ps.done(kind, mat_bytes + a.nchains * (grid_bytes<T>(a.n1_in, a.n2_in) + grid_bytes<T>(a.n1, a.n2)), site,
+          4.0 * a.row * a.nchains * (double)a.n1 * a.n2);
   return {};
 }
 
@@ -261,7 +264,8 @@ Status run_chain(Handle& h, ChainArgs<T>& a, bool mode_a, int kind, cudaStream_t
   a.pair = sh.pair;
   ProfScope ps(h, s);
   SG_CU(launch_chain(a, mode_a, s));
-  ps.done(kind, in_bytes + a.nchains * grid_bytes<T>(a.n1, a.n2), site);
+  ps.done(kind, in_bytes + a.nchains * grid_bytes<T>(a.n1, a.n2), site,
+          4.0 * (a.row + (a.has_prev ? kProlongRow : 0)) * a.nchains * (double)a.n1 * a.n2);
   return {};
 }
 
@@ -276,7 +280,8 @@ Status run_final(Handle& h, FinalArgs<T>& f, bool left, int kind, cudaStream_t s
   ProfScope ps(h, s);
   SG_CU(launch_final(f, left, s));
   const double g = grid_bytes<T>(f.n1, f.n2);
-  ps.done(kind, mat_bytes + f.nin * in_bytes + g * (f.accumulate ? 2.0 : 1.0), site);
+  ps.done(kind, mat_bytes + f.nin * in_bytes + g * (f.accumulate ? 2.0 : 1.0), site,
+          2.0 * (2.0 * f.row + 4.0) * f.nterms * (double)f.n1 * f.n2);
   return {};
 }
 

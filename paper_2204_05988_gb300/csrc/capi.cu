@@ -753,13 +753,14 @@ sgdg_status sgdg_kernel_stats(void* hp, sgdg_kernel_stat* out, int n_kinds) {
   if (!hp || !out || n_kinds < KIND_COUNT) return SGDG_EINVAL;
   Handle* h = (Handle*)hp;
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(h, {SGDG_ECUDA, "synchronize"});
-  for (int k = 0; k < n_kinds; ++k) out[k] = sgdg_kernel_stat{0, 0.0, 0.0};
+  for (int k = 0; k < n_kinds; ++k) out[k] = sgdg_kernel_stat{0, 0.0, 0.0, 0.0};
   for (auto& k : h->kev) {
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, k.e0, k.e1);
     out[k.kind].launches++;
     out[k.kind].ms += ms;
     out[k.kind].bytes += k.bytes;
+    out[k.kind].flops += k.flops;
   }
   drop_events(h);
   return SGDG_OK;

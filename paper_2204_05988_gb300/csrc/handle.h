@@ -108,7 +108,7 @@ struct Handle {
   // one is bracketed by CUDA events and its algorithmic bytes recorded
   long long launches = 0;
   bool prof = false;
-  struct KEvent { int kind; double bytes; cudaEvent_t e0, e1; long long site; };
+  struct KEvent { int kind; double bytes; cudaEvent_t e0, e1; long long site; double flops = 0.0; };
   std::vector<KEvent> kev;
   // autotuner: launch shape per launch site (kind and grid shape), stored as
   // rows per thread | block order << 4 | paired outputs << 5; force_ch > 0
