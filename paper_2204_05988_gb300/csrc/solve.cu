@@ -96,14 +96,29 @@ struct KrylovWs {
   T* ch[4] = {nullptr, nullptr, nullptr, nullptr};   // Chebyshev x, r, d, Md
 };
 
+// Workspace of the lockstep component solves: per CT grid g a Krylov basis
+// (m+1 vectors), the preconditioner output t0, the combined correction t1
+// and four Chebyshev vectors, slices of one arena.
+template <typename T>
+struct CtBatch {
+  int m = 0;
+  T* arena = nullptr;
+  std::vector<T*> V, t0, t1, cx, cr, cd, cm;
+  double* part = nullptr;   // grouped partial sums: grid x (kMaxKrylov + 2) x nbg
+  double* dots = nullptr;   // grid x 3 x kMaxKrylov (device)
+  double* host = nullptr;   // pinned mirror of dots
+  double* y = nullptr;      // grid x kMaxKrylov (device), Givens solutions
+  double* yh = nullptr;     // pinned staging of y
+};
+
 struct Workspace {
   int nb = 0;                 // blocks of the multi-dot
   double* part = nullptr;     // kMaxKrylov+2 x nb
   double* dev_dots = nullptr; // 3 * (kMaxKrylov + 2)
   double* host = nullptr;     // pinned
   KrylovWs<double> outer;
-  KrylovWs<double> in64;
-  KrylovWs<float> in32;
+  CtBatch<double> ct64;       // batched component solves (the configured inner precision)
+  CtBatch<float> ct32;
   // CT buffers
   void* ct_x = nullptr;       // solutions of all CT grids (both precisions: max bytes)
   void* ct_b = nullptr;       // restricted rhs of a lower grid
@@ -117,9 +132,9 @@ struct Workspace {
 namespace {
 
 template <typename T>
-KrylovWs<T>& inner_ws(Workspace& w);
-template <> KrylovWs<double>& inner_ws<double>(Workspace& w) { return w.in64; }
-template <> KrylovWs<float>& inner_ws<float>(Workspace& w) { return w.in32; }
+CtBatch<T>& ct_ws(Workspace& w);
+template <> CtBatch<double>& ct_ws<double>(Workspace& w) { return w.ct64; }
+template <> CtBatch<float>& ct_ws<float>(Workspace& w) { return w.ct32; }
 
 // dots[0..k-1] = V_i . w (device), via deterministic block partials
 template <typename T>
@@ -196,126 +211,439 @@ struct Givens {
   }
 };
 
-// Chebyshev-Jacobi approximation of M^{-1} along one dimension, in place on x.
+// ---------------------------------------------------------------------------
+// Lockstep component solves (Algorithm 1): the 2L+1 CT systems are
+// independent, so their GMRES iterations advance together.  Every vector
+// operation of one inner step is one grouped launch over the active grids
+// (blockIdx.y = grid); the diagonal-block applies are queued grid by grid
+// without host synchronisation; the Hessenberg columns of all grids come
+// back in one copy per step.
+// ---------------------------------------------------------------------------
+
+constexpr int kGroupBlocks = 64;   // blocks per grid of the grouped reductions
+
+// Pointers and sizes of up to kMaxGrids grids for the grouped kernels.
 template <typename T>
-Status cheb_dim(Handle& h, int dim, int lev, int n1, int n2, const T* f, T* out, cudaStream_t s) {
-  KrylovWs<T>& W = inner_ws<T>(*h.ws);
-  const int K = std::max(1, h.cfg.cheb_steps);
-  const double a = 0.5, b = (h.d == 1) ? 1.5 : 2.0;
-  const double theta = 0.5 * (a + b), del = 0.5 * (b - a), sigma1 = theta / del;
-  SideDev& sd = dim == 1 ? h.X : h.V;
-  const T* dinv = sd.vals<T>().dinv[lev];
-  const long long npts = (long long)n1 * n2;
-  T *x = out, *r = W.ch[1], *d = W.ch[2], *Md = W.ch[3];
-  k_cheb_init<T><<<gridsz(npts), kThreads, 0, s>>>(npts, n2, dim, dinv, f, r, d, x, 1.0 / theta);
-  SG_CU(cudaGetLastError());
-  double rho = 1.0 / sigma1;
-  for (int k = 1; k < K; ++k) {
-    SpmmLaunch<T> A;
-    A.ngrids = 1;
-    A.nterms = 1;
-    A.identity = 1;
-    A.accumulate = 0;
-    SpmmGrid<T>& G = A.g[0];
-    G.in = d; G.in2 = nullptr; G.out = Md;
-    G.n1_in = G.n1_out = n1; G.n2_in = G.n2_out = n2;
-    G.rowptr = sd.rowptr[lev]; G.col = sd.col[lev]; G.val[0] = sd.vals<T>().fac[sd.mass][lev];
-    if (dim == 1) SG_CU(launch_left(A, s)); else SG_CU(launch_right(A, s));
-    double rhon = 1.0 / (2.0 * sigma1 - rho);
-    k_cheb_step<T><<<gridsz(npts), kThreads, 0, s>>>(npts, n2, dim, dinv, Md, r, d, x, rhon * rho, 2.0 * rhon / del);
-    SG_CU(cudaGetLastError());
-    rho = rhon;
+struct GVec {
+  int ng = 0;
+  long long n[kMaxGrids];        // scalars of grid g (time index included)
+  int n2[kMaxGrids];             // row length of grid g (pairs)
+  int slot[kMaxGrids];           // the grid's index in the per-grid scalar arrays
+  const T* a[kMaxGrids];
+  T* b[kMaxGrids];
+  T* c[kMaxGrids];
+  T* d[kMaxGrids];
+  T* e[kMaxGrids];
+  const T* dinv[kMaxGrids];      // Chebyshev: inverse mass diagonal along the smoothed dimension
+  long long ldv[kMaxGrids];      // stride of the Krylov basis
+};
+
+struct TimeInv {
+  double m[4];
+};
+
+template <typename T>
+__global__ void k_gtime2x2(const __grid_constant__ GVec<T> p, TimeInv M) {
+  const int g = blockIdx.y;
+  const long long npts = p.n[g] / 2;
+  const T* x = p.a[g];
+  T* y = p.b[g];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
+    const double x0 = (double)x[2 * i], x1 = (double)x[2 * i + 1];
+    y[2 * i] = (T)(M.m[0] * x0 + M.m[1] * x1);
+    y[2 * i + 1] = (T)(M.m[2] * x0 + M.m[3] * x1);
   }
-  return {};
 }
 
-// out = ((T_t + delta C_t + G_t)^{-1} (x) M1^{-1} (x) M2^{-1}) v on grid (l1, l2); v intact.
+// Chebyshev start on every grid: r = f, d = x = c D^{-1} f (a = f, b = r, c = d, d = x)
 template <typename T>
-Status precond_grid(Handle& h, int l1, int l2, const T* v, T* out, cudaStream_t s) {
-  KrylovWs<T>& W = inner_ws<T>(*h.ws);
-  const int n1 = h.X.n[l1], n2 = h.V.n[l2];
-  const long long npts = (long long)n1 * n2;
+__global__ void k_gcheb_init(const __grid_constant__ GVec<T> p, int dim, double c) {
+  const int g = blockIdx.y;
+  const long long npts = p.n[g] / 2;
+  const int n2 = p.n2[g];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
+    const long long k1 = i / n2, k2 = i - k1 * n2;
+    const double di = (double)p.dinv[g][dim == 1 ? k1 : k2];
+    for (int s = 0; s < 2; ++s) {
+      const double fr = (double)p.a[g][2 * i + s];
+      const double dd = c * di * fr;
+      p.b[g][2 * i + s] = (T)fr;
+      p.c[g][2 * i + s] = (T)dd;
+      p.d[g][2 * i + s] = (T)dd;
+    }
+  }
+}
+
+// Chebyshev step: r -= Md; d = c1 d + c2 D^{-1} r; x += d  (a = Md, b = r, c = d, d = x)
+template <typename T>
+__global__ void k_gcheb_step(const __grid_constant__ GVec<T> p, int dim, double c1, double c2) {
+  const int g = blockIdx.y;
+  const long long npts = p.n[g] / 2;
+  const int n2 = p.n2[g];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
+    const long long k1 = i / n2, k2 = i - k1 * n2;
+    const double di = (double)p.dinv[g][dim == 1 ? k1 : k2];
+    for (int s = 0; s < 2; ++s) {
+      const double rr = (double)p.b[g][2 * i + s] - (double)p.a[g][2 * i + s];
+      const double dd = c1 * (double)p.c[g][2 * i + s] + c2 * di * rr;
+      p.b[g][2 * i + s] = (T)rr;
+      p.c[g][2 * i + s] = (T)dd;
+      p.d[g][2 * i + s] = (T)((double)p.d[g][2 * i + s] + dd);
+    }
+  }
+}
+
+// part[(slot * (kMaxKrylov + 2) + i) * kGroupBlocks + block] = partial sum of
+// V_i . w over the block's share (a = V base, b = w), for i < k; fixed order.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_gmultidot(const __grid_constant__ GVec<T> p, int k, double* part) {
+  const int g = blockIdx.y;
+  const long long n = p.n[g];
+  const T* V = p.a[g];
+  const T* w = p.b[g];
+  __shared__ double red[kThreads / 32];
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long lo = blockIdx.x * per, hi = min(n, lo + per);
+  for (int i = 0; i < k; ++i) {
+    const T* Vi = V + (long long)i * p.ldv[g];
+    double acc = 0.0;
+    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) acc += (double)Vi[t] * (double)w[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int q = 0; q < kThreads / 32; ++q) sum += red[q];
+      part[((long long)p.slot[g] * (kMaxKrylov + 2) + i) * gridDim.x + blockIdx.x] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+// dots[slot * ld + off + i] = sum over blocks of part (fixed order), i < k
+__global__ void k_greduce2(const __grid_constant__ GVec<double> p, int k, const double* part, int nbg, double* dots,
+                           int ld, int off) {
+  const int g = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  const int slot = p.slot[g];
+  const double* src = part + ((long long)slot * (kMaxKrylov + 2) + i) * nbg;
+  double sum = 0.0;
+  for (int b = 0; b < nbg; ++b) sum += src[b];
+  dots[(long long)slot * ld + off + i] = sum;
+}
+
+// w -= sum_i h[slot * ld + off + i] V_i   (a = V base, b = w)
+template <typename T>
+__global__ void k_gmultiaxpy(const __grid_constant__ GVec<T> p, int k, const double* h, int ld, int off) {
+  const int g = blockIdx.y;
+  const long long n = p.n[g];
+  const double* hg = h + (long long)p.slot[g] * ld + off;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double acc = (double)p.b[g][t];
+    for (int i = 0; i < k; ++i) acc -= hg[i] * (double)p.a[g][(long long)i * p.ldv[g] + t];
+    p.b[g][t] = (T)acc;
+  }
+}
+
+// w *= 1 / sqrt(h[slot * ld + off]) when positive   (b = w)
+template <typename T>
+__global__ void k_gnormalize(const __grid_constant__ GVec<T> p, const double* h, int ld, int off) {
+  const int g = blockIdx.y;
+  const double nn = h[(long long)p.slot[g] * ld + off];
+  if (!(nn > 0.0)) return;
+  const double sc = 1.0 / sqrt(nn);
+  const long long n = p.n[g];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    p.b[g][t] = (T)((double)p.b[g][t] * sc);
+}
+
+// c = sum_i y[slot * ld + i] V_i   (a = V base, c = output), i < k[g] (in n2 of the descriptor)
+template <typename T>
+__global__ void k_gcombine(const __grid_constant__ GVec<T> p, const double* y, int ld) {
+  const int g = blockIdx.y;
+  const long long n = p.n[g];
+  const int k = p.n2[g];
+  const double* yg = y + (long long)p.slot[g] * ld;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc += yg[i] * (double)p.a[g][(long long)i * p.ldv[g] + t];
+    p.c[g][t] = (T)acc;
+  }
+}
+
+// grid of a grouped elementwise launch: enough blocks for the largest grid, capped
+inline dim3 ggrid(const long long* n, int ng) {
+  long long mx = 1;
+  for (int g = 0; g < ng; ++g) mx = std::max(mx, n[g]);
+  long long b = (mx + kThreads - 1) / kThreads;
+  const long long cap = std::max(1LL, (long long)num_sms() * 8 / std::max(1, ng) + 1);
+  return dim3((unsigned)std::max(1LL, std::min(b, cap)), (unsigned)ng);
+}
+
+// The active grids of one lockstep step.
+struct Active {
+  std::vector<int> g;   // CT grid indices
+};
+
+// out_g = ((T_t + delta C_t + G_t)^{-1} (x) M1^{-1} (x) M2^{-1}) in_g on every
+// active grid.  Uses cx, cr, cd, cm and t1 of each grid: in_g may be t1 (it is
+// consumed first), out_g must be none of them.
+template <typename T>
+Status precond_group(Handle& h, const Active& act, const std::vector<const T*>& in, const std::vector<T*>& out,
+                     cudaStream_t s) {
+  Workspace& ws = *h.ws;
+  CtBatch<T>& B = ct_ws<T>(ws);
+  const int ng = (int)act.g.size();
+  if (ng == 0) return {};
   const double dt = h.cfg.dt, dl = h.cfg.delta;
   // P_t = [[1, 1], [-1, 1 + 4 delta / dt]]
   const double p00 = 1.0, p01 = 1.0, p10 = -1.0, p11 = 1.0 + 4.0 * dl / dt;
   const double det = p00 * p11 - p01 * p10;
-  const double inv[4] = {p11 / det, -p01 / det, -p10 / det, p00 / det};
-  T* t = W.ch[0];
-  SG_CU(vec_time2x2<T>(npts, inv, v, out, s));
-  SG_ST(cheb_dim<T>(h, 1, l1, n1, n2, out, t, s));
-  SG_ST(cheb_dim<T>(h, 2, l2, n1, n2, t, out, s));
+  TimeInv Minv;
+  Minv.m[0] = p11 / det; Minv.m[1] = -p01 / det; Minv.m[2] = -p10 / det; Minv.m[3] = p00 / det;
+  GVec<T> t;
+  t.ng = ng;
+  for (int q = 0; q < ng; ++q) {
+    const int g = act.g[q];
+    t.n[q] = 2LL * h.X.n[ws.cl1[g]] * h.V.n[ws.cl2[g]];
+    t.a[q] = in[q];
+    t.b[q] = B.cx[g];   // time-inverted input, smoothed along dim 1 next
+  }
+  k_gtime2x2<T><<<ggrid(t.n, ng), kThreads, 0, s>>>(t, Minv);
+  SG_CU(cudaGetLastError());
+  // Chebyshev-Jacobi along dim 1 (f = cx -> x = t0), then along dim 2 (f = t0 -> x = out)
+  const int K = std::max(1, h.cfg.cheb_steps);
+  const double a = 0.5, b = (h.d == 1) ? 1.5 : 2.0;
+  const double theta = 0.5 * (a + b), del = 0.5 * (b - a), sigma1 = theta / del;
+  for (int dim = 1; dim <= 2; ++dim) {
+    GVec<T> c;
+    c.ng = ng;
+    SpmmLaunch<T> A;
+    A.ngrids = ng;
+    A.nterms = 1;
+    A.identity = 1;
+    A.accumulate = 0;
+    for (int q = 0; q < ng; ++q) {
+      const int g = act.g[q];
+      const int l1 = ws.cl1[g], l2 = ws.cl2[g];
+      const SideDev& sd = dim == 1 ? h.X : h.V;
+      const int lev = dim == 1 ? l1 : l2;
+      c.n[q] = 2LL * h.X.n[l1] * h.V.n[l2];
+      c.n2[q] = h.V.n[l2];
+      c.dinv[q] = sd.vals<T>().dinv[lev];
+      c.a[q] = dim == 1 ? B.cx[g] : B.t1[g];      // f
+      c.b[q] = B.cr[g];                            // r
+      c.c[q] = B.cd[g];                            // d
+      c.d[q] = dim == 1 ? B.t1[g] : out[q];        // x
+      SpmmGrid<T>& G = A.g[q];
+      G.in = B.cd[g];
+      G.in2 = nullptr;
+      G.out = B.cm[g];
+      G.n1_in = G.n1_out = h.X.n[l1];
+      G.n2_in = G.n2_out = h.V.n[l2];
+      G.rowptr = sd.rowptr[lev];
+      G.col = sd.col[lev];
+      G.val[0] = sd.vals<T>().fac[sd.mass][lev];
+    }
+    k_gcheb_init<T><<<ggrid(c.n, ng), kThreads, 0, s>>>(c, dim, 1.0 / theta);
+    SG_CU(cudaGetLastError());
+    double rho = 1.0 / sigma1;
+    GVec<T> st = c;
+    for (int q = 0; q < ng; ++q) st.a[q] = B.cm[act.g[q]];   // Md
+    for (int k = 1; k < K; ++k) {
+      if (dim == 1) SG_CU(launch_left(A, s)); else SG_CU(launch_right(A, s));
+      const double rhon = 1.0 / (2.0 * sigma1 - rho);
+      k_gcheb_step<T><<<ggrid(st.n, ng), kThreads, 0, s>>>(st, dim, rhon * rho, 2.0 * rhon / del);
+      SG_CU(cudaGetLastError());
+      rho = rhon;
+    }
+  }
   return {};
 }
 
-// GMRES(m) on A_{l,l} x = b (one restart cycle, x0 = 0), right preconditioned.
+// Grouped dots d[slot][off + i] = V_{g,i} . w_g (i < k) for the active grids.
 template <typename T>
-Status component_solve(Handle& h, int l1, int l2, const T* b, T* x, cudaStream_t s, int* its) {
-  KrylovWs<T>& W = inner_ws<T>(*h.ws);
-  const long long n = 2LL * h.X.n[l1] * h.V.n[l2];
-  const int m = std::min(h.cfg.inner_its, W.m);
-  double beta;
-  SG_ST(vnorm<T>(h, b, n, &beta, s));
-  if (beta == 0.0) {
-    SG_CU(vec_fill<T>(x, n, (T)0, s));
-    return {};
+Status gdots(Handle& h, const Active& act, const std::vector<const T*>& V, const std::vector<long long>& ldv,
+             const std::vector<const T*>& w, int k, double* dots, int ld, int off, cudaStream_t s) {
+  Workspace& ws = *h.ws;
+  CtBatch<T>& B = ct_ws<T>(ws);
+  const int ng = (int)act.g.size();
+  GVec<T> p;
+  GVec<double> r;
+  p.ng = r.ng = ng;
+  for (int q = 0; q < ng; ++q) {
+    const int g = act.g[q];
+    p.n[q] = 2LL * h.X.n[ws.cl1[g]] * h.V.n[ws.cl2[g]];
+    p.a[q] = V[q];
+    p.b[q] = const_cast<T*>(w[q]);
+    p.ldv[q] = ldv[q];
+    p.slot[q] = r.slot[q] = g;
   }
-  static thread_local Givens G;
-  G.start(beta);
-  SG_CU(vec_axpby<T>(n, 1.0 / beta, b, 0.0, W.V, s));
-  double hcol[kMaxKrylov + 1];
-  int k = 0;
-  for (int j = 0; j < m; ++j) {
-    T* Vj = W.V + (long long)j * n;
-    T* Vn = W.V + (long long)(j + 1) * n;
-    SG_ST(precond_grid<T>(h, l1, l2, Vj, W.t0, s));
-    const T* uin[1] = {W.t0};
-    T* yout[1] = {Vn};
-    SG_ST(apply_diag_grids<T>(h, 1, &l1, &l2, uin, yout, s));
-    SG_ST(arnoldi<T>(h, W.V, n, j, Vn, hcol, s));
-    double res = G.add(j, hcol);
-    k = j + 1;
-    if (res <= h.cfg.inner_rtol * beta || hcol[j + 1] == 0.0) break;
-  }
-  double y[kMaxKrylov];
-  G.solve(k, y);
-  double* dy = h.ws->dev_dots;
-  SG_CU(cudaMemcpyAsync(dy, y, sizeof(double) * k, cudaMemcpyHostToDevice, s));
-  SG_CU(vec_combine<T>(k, W.V, n, dy, 0.0, W.t1, n, s));
-  SG_ST(precond_grid<T>(h, l1, l2, W.t1, x, s));
-  SG_CU(cudaStreamSynchronize(s));   // dy (pageable source) must stay valid
-  if (its) *its += k;
+  k_gmultidot<T><<<dim3(kGroupBlocks, ng), kThreads, 0, s>>>(p, k, B.part);
+  SG_CU(cudaGetLastError());
+  k_greduce2<<<dim3((k + 63) / 64, ng), 64, 0, s>>>(r, k, B.part, kGroupBlocks, dots, ld, off);
+  SG_CU(cudaGetLastError());
   return {};
 }
 
+// z (+)= CT correction for the residual r: lockstep GMRES(m) on every
+// component system A_{l,l} x_l = r_l (x0 = 0, one restart cycle, right
+// preconditioned), then the combination of Algorithm 1.
 template <typename T>
 Status ct_apply(Handle& h, const T* r, T* z, cudaStream_t s, int* its) {
   Workspace& ws = *h.ws;
+  CtBatch<T>& B = ct_ws<T>(ws);
   const int L = h.L;
+  const int NG = (int)ws.cl1.size();
+  const int m = B.m;
+  constexpr int LD = 3 * kMaxKrylov;   // per-grid stride of the dot arrays
   T* X = (T*)ws.ct_x;
-  T* B = (T*)ws.ct_b;
-  // upper grids (l, L-l)
-  for (int l = 0; l <= L; ++l) SG_ST(component_solve<T>(h, l, L - l, r + h.off[l], X + ws.coff[l], s, its));
-  // lower grids (l, L-1-l): residual restricted in dim 1 from grid (l+1, L-1-l)
-  for (int l = 0; l < L; ++l) {
+  auto gsize = [&](int g) { return 2LL * h.X.n[ws.cl1[g]] * h.V.n[ws.cl2[g]]; };
+  // right-hand sides into V_{g,0}: upper grids (l, L-l) take r_l; lower grids
+  // (l, L-1-l) the residual restricted in dim 1 from grid (l+1, L-1-l)
+  for (int l = 0; l <= L; ++l)
+    SG_CU(cudaMemcpyAsync(B.V[l], r + h.off[l], sizeof(T) * gsize(l), cudaMemcpyDeviceToDevice, s));
+  if (L >= 1) {
     SpmmLaunch<T> a;
-    a.ngrids = 1; a.nterms = 1; a.identity = 1; a.accumulate = 0;
-    SpmmGrid<T>& G = a.g[0];
-    G.in = r + h.off[l + 1]; G.in2 = nullptr; G.out = B;
-    G.n1_in = h.n1[l + 1]; G.n2_in = G.n2_out = h.n2[l + 1]; G.n1_out = h.X.n[l];
-    G.rowptr = h.X.R_rowptr[l]; G.col = h.X.R_col[l]; G.val[0] = h.X.vals<T>().R[l];
+    a.ngrids = L; a.nterms = 1; a.identity = 1; a.accumulate = 0;
+    for (int l = 0; l < L; ++l) {
+      SpmmGrid<T>& G = a.g[l];
+      G.in = r + h.off[l + 1]; G.in2 = nullptr; G.out = B.V[L + 1 + l];
+      G.n1_in = h.n1[l + 1]; G.n2_in = G.n2_out = h.n2[l + 1]; G.n1_out = h.X.n[l];
+      G.rowptr = h.X.R_rowptr[l]; G.col = h.X.R_col[l]; G.val[0] = h.X.vals<T>().R[l];
+    }
     SG_CU(launch_left(a, s));
-    SG_ST(component_solve<T>(h, l, L - 1 - l, B, X + ws.coff[L + 1 + l], s, its));
+  }
+  // beta_g and V_{g,0} = r_g / beta_g
+  Active all;
+  for (int g = 0; g < NG; ++g) all.g.push_back(g);
+  std::vector<const T*> v0(NG), w0(NG);
+  std::vector<long long> ldv(NG);
+  for (int g = 0; g < NG; ++g) { v0[g] = B.V[g]; w0[g] = B.V[g]; ldv[g] = gsize(g); }
+  SG_ST(gdots<T>(h, all, v0, ldv, w0, 1, B.dots, LD, 2 * kMaxKrylov, s));
+  SG_CU(cudaMemcpyAsync(B.host, B.dots, sizeof(double) * NG * LD, cudaMemcpyDeviceToHost, s));
+  SG_CU(cudaStreamSynchronize(s));
+  std::vector<double> beta(NG);
+  std::vector<int> kdone(NG, 0);
+  static thread_local std::vector<Givens> Gv;
+  Gv.resize(NG);
+  Active act;
+  for (int g = 0; g < NG; ++g) {
+    beta[g] = std::sqrt(std::max(0.0, B.host[(long long)g * LD + 2 * kMaxKrylov]));
+    if (!std::isfinite(beta[g])) return {SGDG_ENAN, "NaN/Inf in a component right-hand side"};
+    if (beta[g] > 0.0) {
+      act.g.push_back(g);
+      Gv[g].start(beta[g]);
+    }
+  }
+  {
+    GVec<T> p;
+    p.ng = (int)act.g.size();
+    for (int q = 0; q < p.ng; ++q) {
+      const int g = act.g[q];
+      p.n[q] = gsize(g); p.b[q] = B.V[g]; p.slot[q] = g;
+    }
+    if (p.ng) {
+      k_gnormalize<T><<<ggrid(p.n, p.ng), kThreads, 0, s>>>(p, B.dots, LD, 2 * kMaxKrylov);
+      SG_CU(cudaGetLastError());
+    }
+  }
+  Active live = act;
+  for (int j = 0; j < m && !live.g.empty(); ++j) {
+    const int na = (int)live.g.size();
+    std::vector<const T*> vin(na), Vb(na), wv(na);
+    std::vector<T*> pout(na);
+    std::vector<long long> lv(na);
+    for (int q = 0; q < na; ++q) {
+      const int g = live.g[q];
+      vin[q] = B.V[g] + (long long)j * gsize(g);
+      pout[q] = B.t0[g];
+    }
+    SG_ST(precond_group<T>(h, live, vin, pout, s));
+    for (int q = 0; q < na; ++q) {
+      const int g = live.g[q];
+      const int l1 = ws.cl1[g], l2 = ws.cl2[g];
+      const T* uin[1] = {B.t0[g]};
+      T* yout[1] = {B.V[g] + (long long)(j + 1) * gsize(g)};
+      SG_ST(apply_diag_grids<T>(h, 1, &l1, &l2, uin, yout, s));
+      Vb[q] = B.V[g];
+      wv[q] = yout[0];
+      lv[q] = gsize(g);
+    }
+    // CGS2 against V_{g,0..j}, then the norm; all grids at once
+    SG_ST(gdots<T>(h, live, Vb, lv, wv, j + 1, B.dots, LD, 0, s));
+    GVec<T> ax;
+    ax.ng = na;
+    for (int q = 0; q < na; ++q) {
+      const int g = live.g[q];
+      ax.n[q] = gsize(g); ax.a[q] = B.V[g]; ax.b[q] = const_cast<T*>(wv[q]); ax.ldv[q] = gsize(g); ax.slot[q] = g;
+    }
+    k_gmultiaxpy<T><<<ggrid(ax.n, na), kThreads, 0, s>>>(ax, j + 1, B.dots, LD, 0);
+    SG_CU(cudaGetLastError());
+    SG_ST(gdots<T>(h, live, Vb, lv, wv, j + 1, B.dots, LD, kMaxKrylov, s));
+    k_gmultiaxpy<T><<<ggrid(ax.n, na), kThreads, 0, s>>>(ax, j + 1, B.dots, LD, kMaxKrylov);
+    SG_CU(cudaGetLastError());
+    SG_ST(gdots<T>(h, live, wv, lv, wv, 1, B.dots, LD, 2 * kMaxKrylov, s));
+    k_gnormalize<T><<<ggrid(ax.n, na), kThreads, 0, s>>>(ax, B.dots, LD, 2 * kMaxKrylov);
+    SG_CU(cudaGetLastError());
+    SG_CU(cudaMemcpyAsync(B.host, B.dots, sizeof(double) * NG * LD, cudaMemcpyDeviceToHost, s));
+    SG_CU(cudaStreamSynchronize(s));
+    Active next;
+    for (int q = 0; q < na; ++q) {
+      const int g = live.g[q];
+      const double* hd = B.host + (long long)g * LD;
+      double hcol[kMaxKrylov + 1];
+      for (int i = 0; i <= j; ++i) hcol[i] = hd[i] + hd[kMaxKrylov + i];
+      const double nrm = std::sqrt(std::max(0.0, hd[2 * kMaxKrylov]));
+      if (!std::isfinite(nrm)) return {SGDG_ENAN, "NaN/Inf in a component Krylov vector"};
+      hcol[j + 1] = nrm;
+      const double res = Gv[g].add(j, hcol);
+      kdone[g] = j + 1;
+      if (!(res <= h.cfg.inner_rtol * beta[g] || nrm == 0.0)) next.g.push_back(g);
+    }
+    live = next;
+  }
+  // x_g = P^{-1} sum_i y_i V_{g,i};  grids with beta = 0 get x = 0
+  for (int g = 0; g < NG; ++g)
+    if (beta[g] == 0.0) SG_CU(vec_fill<T>(X + ws.coff[g], gsize(g), (T)0, s));
+  if (!act.g.empty()) {
+    for (int g : act.g) {
+      double y[kMaxKrylov];
+      Gv[g].solve(kdone[g], y);
+      for (int i = 0; i < kdone[g]; ++i) B.yh[(long long)g * kMaxKrylov + i] = y[i];
+      if (its) *its += kdone[g];
+    }
+    SG_CU(cudaMemcpyAsync(B.y, B.yh, sizeof(double) * NG * kMaxKrylov, cudaMemcpyHostToDevice, s));
+    GVec<T> cb;
+    cb.ng = (int)act.g.size();
+    std::vector<const T*> cin(cb.ng);
+    std::vector<T*> xout(cb.ng);
+    for (int q = 0; q < cb.ng; ++q) {
+      const int g = act.g[q];
+      cb.n[q] = gsize(g); cb.n2[q] = kdone[g]; cb.a[q] = B.V[g]; cb.c[q] = B.t1[g]; cb.ldv[q] = gsize(g);
+      cb.slot[q] = g;
+      cin[q] = B.t1[g];
+      xout[q] = X + ws.coff[g];
+    }
+    k_gcombine<T><<<ggrid(cb.n, cb.ng), kThreads, 0, s>>>(cb, B.y, kMaxKrylov);
+    SG_CU(cudaGetLastError());
+    SG_ST(precond_group<T>(h, act, cin, xout, s));
+    SG_CU(cudaStreamSynchronize(s));   // B.yh is reused by the next call
   }
   // combination: z_l = dhat_l - (E^(1) (x) Id) dhat_(l-1, L-l)
   SG_CU(cudaMemcpyAsync(z, X, sizeof(T) * h.n_coeffs, cudaMemcpyDeviceToDevice, s));
-  for (int l = 1; l <= L; ++l) {
+  if (L >= 1) {
     SpmmLaunch<T> a;
-    a.ngrids = 1; a.nterms = 1; a.identity = 0; a.accumulate = 1;
+    a.ngrids = L; a.nterms = 1; a.identity = 0; a.accumulate = 1;
     a.tau[0][0] = (T)-1; a.tau[0][1] = 0; a.tau[0][2] = 0; a.tau[0][3] = (T)-1;
-    SpmmGrid<T>& G = a.g[0];
-    G.in = X + ws.coff[L + 1 + (l - 1)]; G.in2 = nullptr; G.out = z + h.off[l];
-    G.n1_in = h.X.n[l - 1]; G.n2_in = G.n2_out = h.n2[l]; G.n1_out = h.n1[l];
-    G.rowptr = h.X.E_rowptr[l - 1]; G.col = h.X.E_col[l - 1]; G.val[0] = h.X.vals<T>().E[l - 1];
+    for (int l = 1; l <= L; ++l) {
+      SpmmGrid<T>& G = a.g[l - 1];
+      G.in = X + ws.coff[L + 1 + (l - 1)]; G.in2 = nullptr; G.out = z + h.off[l];
+      G.n1_in = h.X.n[l - 1]; G.n2_in = G.n2_out = h.n2[l]; G.n1_out = h.n1[l];
+      G.rowptr = h.X.E_rowptr[l - 1]; G.col = h.X.E_col[l - 1]; G.val[0] = h.X.vals<T>().E[l - 1];
+    }
     SG_CU(launch_left(a, s));
   }
   return {};
@@ -334,6 +662,35 @@ Status alloc_krylov(Handle& h, KrylovWs<T>& W, int m, long long n, bool flexible
   if (cheb)
     for (int i = 0; i < 4; ++i)
       if (dev_alloc(h, (void**)&W.ch[i], sizeof(T) * n) != cudaSuccess) return {SGDG_ENOMEM, "Chebyshev temporaries"};
+  return {};
+}
+
+template <typename T>
+Status alloc_ct(Handle& h, CtBatch<T>& B, int m, long long tot) {
+  Workspace& ws = *h.ws;
+  const int NG = (int)ws.cl1.size();
+  B.m = m;
+  const long long per = (long long)(m + 1) + 6;   // basis + t0, t1, cx, cr, cd, cm
+  if (dev_alloc(h, (void**)&B.arena, sizeof(T) * (size_t)(per * tot)) != cudaSuccess)
+    return {SGDG_ENOMEM, "component-solve workspace"};
+  T* p = B.arena;
+  for (int g = 0; g < NG; ++g) {
+    const long long n = 2LL * h.X.n[ws.cl1[g]] * h.V.n[ws.cl2[g]];
+    B.V.push_back(p); p += (m + 1) * n;
+    B.t0.push_back(p); p += n;
+    B.t1.push_back(p); p += n;
+    B.cx.push_back(p); p += n;
+    B.cr.push_back(p); p += n;
+    B.cd.push_back(p); p += n;
+    B.cm.push_back(p); p += n;
+  }
+  if (dev_alloc(h, (void**)&B.part, sizeof(double) * (size_t)NG * (kMaxKrylov + 2) * kGroupBlocks) != cudaSuccess ||
+      dev_alloc(h, (void**)&B.dots, sizeof(double) * (size_t)NG * 3 * kMaxKrylov) != cudaSuccess ||
+      dev_alloc(h, (void**)&B.y, sizeof(double) * (size_t)NG * kMaxKrylov) != cudaSuccess)
+    return {SGDG_ENOMEM, "component-solve scalars"};
+  if (cudaMallocHost((void**)&B.host, sizeof(double) * (size_t)NG * 3 * kMaxKrylov) != cudaSuccess ||
+      cudaMallocHost((void**)&B.yh, sizeof(double) * (size_t)NG * kMaxKrylov) != cudaSuccess)
+    return {SGDG_ENOMEM, "pinned component-solve scalars"};
   return {};
 }
 
@@ -366,13 +723,14 @@ Status solver_init(Handle& h) {
       dev_alloc(h, &ws.ct_b, esz * (size_t)ws.nmax_grid) != cudaSuccess)
     return {SGDG_ENOMEM, "CT buffers"};
   const int mi = std::max(1, std::min(h.cfg.inner_its, kMaxKrylov - 1));
+  if ((int)ws.cl1.size() > kMaxGrids) return {SGDG_EINVAL, "more CT grids than one grouped launch holds"};
   if (mixed) {
-    SG_ST(alloc_krylov<float>(h, ws.in32, mi, ws.nmax_grid, false, true));
+    SG_ST(alloc_ct<float>(h, ws.ct32, mi, tot));
     if (dev_alloc(h, (void**)&ws.r32, sizeof(float) * h.n_coeffs) != cudaSuccess ||
         dev_alloc(h, (void**)&ws.z32, sizeof(float) * h.n_coeffs) != cudaSuccess)
       return {SGDG_ENOMEM, "mixed-precision buffers"};
   } else {
-    SG_ST(alloc_krylov<double>(h, ws.in64, mi, ws.nmax_grid, false, true));
+    SG_ST(alloc_ct<double>(h, ws.ct64, mi, tot));
   }
   const int mo = std::max(1, std::min(h.cfg.restart, kMaxKrylov - 1));
   SG_ST(alloc_krylov<double>(h, ws.outer, mo, h.n_coeffs, true, false));
@@ -503,6 +861,8 @@ Handle::~Handle() {}
 void solver_free(Handle& h) {
   if (!h.ws) return;
   if (h.ws->host) cudaFreeHost(h.ws->host);
+  for (double* p : {h.ws->ct32.host, h.ws->ct32.yh, h.ws->ct64.host, h.ws->ct64.yh})
+    if (p) cudaFreeHost(p);
   delete h.ws;
   h.ws = nullptr;
 }
