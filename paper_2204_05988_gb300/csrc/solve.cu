@@ -34,6 +34,10 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxKrylov = 64;
 
+template <typename T> struct V2;
+template <> struct V2<double> { using type = double2; };
+template <> struct V2<float> { using type = float2; };
+
 template <typename T>
 __global__ void k_cheb_init(long long npts, int n2, int dim, const T* dinv, const T* f, T* r, T* d, T* x, double c) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
@@ -242,72 +246,101 @@ struct TimeInv {
   double m[4];
 };
 
+// Elementwise grouped kernels compute in the storage type T (FP32 in mixed
+// mode: the component solves are FP32 there); only the dot products below
+// accumulate in FP64.
 template <typename T>
 __global__ void k_gtime2x2(const __grid_constant__ GVec<T> p, TimeInv M) {
+  using T2 = typename V2<T>::type;
   const int g = blockIdx.y;
-  const long long npts = p.n[g] / 2;
-  const T* x = p.a[g];
-  T* y = p.b[g];
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
-    const double x0 = (double)x[2 * i], x1 = (double)x[2 * i + 1];
-    y[2 * i] = (T)(M.m[0] * x0 + M.m[1] * x1);
-    y[2 * i + 1] = (T)(M.m[2] * x0 + M.m[3] * x1);
+  const unsigned npts = (unsigned)(p.n[g] / 2);
+  const T2* x = reinterpret_cast<const T2*>(p.a[g]);
+  T2* y = reinterpret_cast<T2*>(p.b[g]);
+  const T m0 = (T)M.m[0], m1 = (T)M.m[1], m2 = (T)M.m[2], m3 = (T)M.m[3];
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += gridDim.x * blockDim.x) {
+    const T2 v = x[i];
+    T2 r;
+    r.x = m0 * v.x + m1 * v.y;
+    r.y = m2 * v.x + m3 * v.y;
+    y[i] = r;
   }
 }
 
 // Chebyshev start on every grid: r = f, d = x = c D^{-1} f (a = f, b = r, c = d, d = x)
 template <typename T>
 __global__ void k_gcheb_init(const __grid_constant__ GVec<T> p, int dim, double c) {
+  using T2 = typename V2<T>::type;
   const int g = blockIdx.y;
-  const long long npts = p.n[g] / 2;
-  const int n2 = p.n2[g];
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
-    const long long k1 = i / n2, k2 = i - k1 * n2;
-    const double di = (double)p.dinv[g][dim == 1 ? k1 : k2];
-    for (int s = 0; s < 2; ++s) {
-      const double fr = (double)p.a[g][2 * i + s];
-      const double dd = c * di * fr;
-      p.b[g][2 * i + s] = (T)fr;
-      p.c[g][2 * i + s] = (T)dd;
-      p.d[g][2 * i + s] = (T)dd;
-    }
+  const unsigned npts = (unsigned)(p.n[g] / 2);
+  const unsigned n2 = (unsigned)p.n2[g];
+  const T2* f = reinterpret_cast<const T2*>(p.a[g]);
+  T2* r = reinterpret_cast<T2*>(p.b[g]);
+  T2* d = reinterpret_cast<T2*>(p.c[g]);
+  T2* x = reinterpret_cast<T2*>(p.d[g]);
+  const T cc = (T)c;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += gridDim.x * blockDim.x) {
+    const unsigned k1 = i / n2, k2 = i - k1 * n2;
+    const T di = cc * p.dinv[g][dim == 1 ? k1 : k2];
+    const T2 fr = f[i];
+    T2 dd;
+    dd.x = di * fr.x;
+    dd.y = di * fr.y;
+    r[i] = fr;
+    d[i] = dd;
+    x[i] = dd;
   }
 }
 
 // Chebyshev step: r -= Md; d = c1 d + c2 D^{-1} r; x += d  (a = Md, b = r, c = d, d = x)
 template <typename T>
 __global__ void k_gcheb_step(const __grid_constant__ GVec<T> p, int dim, double c1, double c2) {
+  using T2 = typename V2<T>::type;
   const int g = blockIdx.y;
-  const long long npts = p.n[g] / 2;
-  const int n2 = p.n2[g];
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
-    const long long k1 = i / n2, k2 = i - k1 * n2;
-    const double di = (double)p.dinv[g][dim == 1 ? k1 : k2];
-    for (int s = 0; s < 2; ++s) {
-      const double rr = (double)p.b[g][2 * i + s] - (double)p.a[g][2 * i + s];
-      const double dd = c1 * (double)p.c[g][2 * i + s] + c2 * di * rr;
-      p.b[g][2 * i + s] = (T)rr;
-      p.c[g][2 * i + s] = (T)dd;
-      p.d[g][2 * i + s] = (T)((double)p.d[g][2 * i + s] + dd);
-    }
+  const unsigned npts = (unsigned)(p.n[g] / 2);
+  const unsigned n2 = (unsigned)p.n2[g];
+  const T2* Md = reinterpret_cast<const T2*>(p.a[g]);
+  T2* r = reinterpret_cast<T2*>(p.b[g]);
+  T2* d = reinterpret_cast<T2*>(p.c[g]);
+  T2* x = reinterpret_cast<T2*>(p.d[g]);
+  const T a1 = (T)c1, a2 = (T)c2;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += gridDim.x * blockDim.x) {
+    const unsigned k1 = i / n2, k2 = i - k1 * n2;
+    const T di = a2 * p.dinv[g][dim == 1 ? k1 : k2];
+    const T2 m = Md[i];
+    T2 rr = r[i], dd = d[i], xx = x[i];
+    rr.x -= m.x;
+    rr.y -= m.y;
+    dd.x = a1 * dd.x + di * rr.x;
+    dd.y = a1 * dd.y + di * rr.y;
+    xx.x += dd.x;
+    xx.y += dd.y;
+    r[i] = rr;
+    d[i] = dd;
+    x[i] = xx;
   }
 }
 
 // part[(slot * (kMaxKrylov + 2) + i) * kGroupBlocks + block] = partial sum of
 // V_i . w over the block's share (a = V base, b = w), for i < k; fixed order.
+// The two time coefficients of a node are multiplied and added in T, the
+// node sums accumulate in FP64.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_gmultidot(const __grid_constant__ GVec<T> p, int k, double* part) {
+  using T2 = typename V2<T>::type;
   const int g = blockIdx.y;
-  const long long n = p.n[g];
-  const T* V = p.a[g];
-  const T* w = p.b[g];
+  const long long n = p.n[g] / 2;   // nodes (pairs)
+  const T2* V = reinterpret_cast<const T2*>(p.a[g]);
+  const T2* w = reinterpret_cast<const T2*>(p.b[g]);
   __shared__ double red[kThreads / 32];
   const long long per = (n + gridDim.x - 1) / gridDim.x;
   const long long lo = blockIdx.x * per, hi = min(n, lo + per);
   for (int i = 0; i < k; ++i) {
-    const T* Vi = V + (long long)i * p.ldv[g];
+    const T2* Vi = V + (long long)i * (p.ldv[g] / 2);
     double acc = 0.0;
-    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) acc += (double)Vi[t] * (double)w[t];
+    for (long long t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+      const T2 a = Vi[t], b = w[t];
+      acc += (double)(a.x * b.x + a.y * b.y);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -334,16 +367,19 @@ __global__ void k_greduce2(const __grid_constant__ GVec<double> p, int k, const 
   dots[(long long)slot * ld + off + i] = sum;
 }
 
-// w -= sum_i h[slot * ld + off + i] V_i   (a = V base, b = w)
+// w -= sum_i h[slot * ld + off + i] V_i   (a = V base, b = w); coefficients
+// rounded to T, accumulation in T
 template <typename T>
 __global__ void k_gmultiaxpy(const __grid_constant__ GVec<T> p, int k, const double* h, int ld, int off) {
   const int g = blockIdx.y;
   const long long n = p.n[g];
   const double* hg = h + (long long)p.slot[g] * ld + off;
+  const T* V = p.a[g];
+  const long long ldv = p.ldv[g];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    double acc = (double)p.b[g][t];
-    for (int i = 0; i < k; ++i) acc -= hg[i] * (double)p.a[g][(long long)i * p.ldv[g] + t];
-    p.b[g][t] = (T)acc;
+    T acc = p.b[g][t];
+    for (int i = 0; i < k; ++i) acc -= (T)hg[i] * V[(long long)i * ldv + t];
+    p.b[g][t] = acc;
   }
 }
 
@@ -353,10 +389,10 @@ __global__ void k_gnormalize(const __grid_constant__ GVec<T> p, const double* h,
   const int g = blockIdx.y;
   const double nn = h[(long long)p.slot[g] * ld + off];
   if (!(nn > 0.0)) return;
-  const double sc = 1.0 / sqrt(nn);
+  const T sc = (T)(1.0 / sqrt(nn));
   const long long n = p.n[g];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-    p.b[g][t] = (T)((double)p.b[g][t] * sc);
+    p.b[g][t] *= sc;
 }
 
 // c = sum_i y[slot * ld + i] V_i   (a = V base, c = output), i < k[g] (in n2 of the descriptor)
@@ -366,10 +402,12 @@ __global__ void k_gcombine(const __grid_constant__ GVec<T> p, const double* y, i
   const long long n = p.n[g];
   const int k = p.n2[g];
   const double* yg = y + (long long)p.slot[g] * ld;
+  const T* V = p.a[g];
+  const long long ldv = p.ldv[g];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int i = 0; i < k; ++i) acc += yg[i] * (double)p.a[g][(long long)i * p.ldv[g] + t];
-    p.c[g][t] = (T)acc;
+    T acc = 0;
+    for (int i = 0; i < k; ++i) acc += (T)yg[i] * V[(long long)i * ldv + t];
+    p.c[g][t] = acc;
   }
 }
 
