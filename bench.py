@@ -351,22 +351,44 @@ def main():
         B.apply(bus, bys, P.SGDG_MIXED_FP32, stream)          # capture
         bms = timed(lambda: B.apply(bus, bys, P.SGDG_MIXED_FP32, stream), args.steps, 1)
         dof = sum(sv.n_coeffs for sv in solvers)
+        # batched mixed precision with the extrapolated guess (warm start 3):
+        # all members concurrently; strip 3 is timed (the first with two
+        # earlier solutions to extrapolate from)
         for sv in solvers:
+            sv.set_warm_start(3)
             sv.set_initial()
         tstr = []
-        for _ in range(2):
+        for _ in range(3):
             t1 = time.perf_counter()
             st = B.advance()
             tstr.append(time.perf_counter() - t1)
+        B.close()
+        for sv in solvers:
+            sv.close()
+        # the plain FP64 solver on the same instances, one after another,
+        # previous-strip guess; strip 3 of each is timed
+        t64, its64, res64 = 0.0, [], []
+        for pr in probs:
+            sv = P.Solver(pr, precision=P.SGDG_FP64, rtol=1e-8, restart=30, inner_its=12, inner_rtol=1e-2,
+                          device=local)
+            sv.set_warm_start(1)
+            sv.set_initial()
+            for k in range(3):
+                r = sv.advance_strip(check=False)
+            t64 += r.seconds
+            its64.append(r.outer_its)
+            res64.append(r.rel_residual)
+            sv.close()
         batch = {"workload": f"{args.batch} x transport_4d free streaming, L from {sorted(set(p.L for p in probs))}",
                  "levels": [p.L for p in probs], "dof_total": dof, "setup_s": round(bsetup, 2),
                  "apply_graph_ms": bms, "apply_GDoFps": dof / (bms * 1e-3) / 1e9,
                  "s_per_batched_strip": round(tstr[-1], 4),
                  "max_rel_residual": max(x.rel_residual for x in st),
-                 "outer_its": [x.outer_its for x in st]}
-        B.close()
-        for sv in solvers:
-            sv.close()
+                 "outer_its": [x.outer_its for x in st],
+                 "strips_per_s_batched_mixed": len(probs) / tstr[-1],
+                 "plain_fp64": {"s_for_all_members": round(t64, 4), "strips_per_s": len(probs) / t64,
+                                "outer_its": its64, "max_rel_residual": max(res64)},
+                 "strips_per_s_ratio": (len(probs) / tstr[-1]) / (len(probs) / t64)}
 
     if rank == 0:
         cpu = None
