@@ -88,15 +88,37 @@ typedef struct {
   void* uv;
 } sgdg_product;
 
-/* beta_p = beta[p] for p < 2d (x-components first), sigma, and
- * u0 = sum_k u0[k].  Every component of beta is ONE product (the tensor
- * structure of Sect. 4.2); inflow splitting (Sect. 5.2) assumes the sign of
- * each factor changes only on mesh lines. */
+/* Batched time callback: out[i] = g(t[i]), i < npts.  Called on the host
+ * when a strip's right-hand side is formed. */
+typedef void (*sgdg_tfn)(int npts, const double* t, double* out, void* user);
+
+/* One separable term coef * ft(t) * fx(x) * fv(v) of the source f; a NULL
+ * function is the constant 1. */
+typedef struct {
+  double coef;
+  sgdg_fn fx;
+  void* ux;
+  sgdg_fn fv;
+  void* uv;
+  sgdg_tfn ft;
+  void* ut;
+} sgdg_source;
+
+/* beta_p = beta[p] for p < 2d (x-components first), sigma,
+ * u0 = sum_k u0[k] and the source f = sum_k f[k] (n_f may be 0).  Every
+ * component of beta is ONE product (the tensor structure of Sect. 4.2);
+ * inflow splitting (Sect. 5.2) assumes the sign of each factor changes only
+ * on mesh lines.  The strip right-hand side b_j of Sect. 2 pairs f with
+ * w + delta (d_t w + beta . grad w); its time integrals use 3-point
+ * Gauss-Legendre on every strip.  The inflow data g is zero.  Sources are
+ * not combined with vlasov_poisson (EINVAL). */
 typedef struct {
   sgdg_product beta[4];
   sgdg_product sigma;
   int n_u0;
   const sgdg_product* u0;
+  int n_f;
+  const sgdg_source* f;
 } sgdg_coeffs;
 
 typedef struct {

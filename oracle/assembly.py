@@ -179,6 +179,28 @@ class FactorStore:
         return self._proj[key]
 
 
+def assemble_load_grad(lev: Level, fn, axis: int, q: int = QUAD_Q) -> np.ndarray:
+    """F[i] = int fn(y) (d/dy_axis phi_i)(y) dy on one level (fn=None: 1);
+    axis is 0-based.  The gradient of a barycentric function is constant on
+    a cell: grad lam = J^{-T} grad_ref lam."""
+    cc = lev.cell_coords
+    nc, d1, d = cc.shape
+    v0 = cc[:, 0, :]
+    J = np.transpose(cc[:, 1:, :] - v0[:, None, :], (0, 2, 1))     # J[c] columns: edge vectors
+    det = np.abs(np.linalg.det(J))
+    Jinv = np.linalg.inv(J)
+    gref = np.concatenate([-np.ones((1, d)), np.eye(d)], axis=0)    # (d1, d): reference gradients
+    grad = np.einsum("ad,cdk->cak", gref, Jinv)                    # (nc, d1, d) physical gradients
+    rp, rw = simplex_rule(d, q)
+    pts = v0[:, None, :] + np.einsum("cij,qj->cqi", J, rp)
+    vals = fn(pts.reshape(-1, d)).reshape(nc, -1) if fn is not None else np.ones((nc, rp.shape[0]))
+    integ = np.einsum("cq,q,c->c", vals, rw, det)                  # int fn over the cell
+    fe = integ[:, None] * grad[:, :, axis]
+    out = np.zeros(lev.n)
+    np.add.at(out, lev.cells.ravel(), fe.ravel())
+    return out
+
+
 def assemble_load(lev: Level, fn, q: int = QUAD_Q) -> np.ndarray:
     """Load vector F[i] = int fn(y) phi_i(y) dy on one level (fn=None: 1)."""
     cc = lev.cell_coords

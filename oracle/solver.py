@@ -17,7 +17,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   Euclidean norm of the correction.
 * ``StripSolver``: the implicit strip-by-strip scheme (Sect. 2): the right-hand
   side (U^-_{j-1}, w^+_{j-1}) = eta(t_{j-1}^+) (x) M_sg U^-_{j-1} (Eq. 5), with
-  (u0, w^+) from load vectors for the first strip; the end value
+  (u0, w^+) from load vectors for the first strip, plus the source part
+  int_{I_j} (f, w + delta (d_t w + beta . grad w)) dt (``source_rhs``; time
+  integrals by adaptive quadrature, the inflow data g = 0); the end value
   U^-_j = sum_s eta_s(t_j) u_s.
 * ``nodal_values``: the unique representation of a sparse-grid function: its
   values at the nodes of every component grid (prolongation from coarser
@@ -29,8 +31,10 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .assembly import Factor, assemble_load
-from .operator import SparseGridOperator, eta_at, time_matrices
+from scipy import integrate
+
+from .assembly import Factor, assemble_load, assemble_load_grad
+from .operator import SparseGridOperator, eta, eta_at, time_matrices
 
 
 def fgmres(A, b, M=None, x0=None, tol=1e-10, restart=30, maxiter=1000):
@@ -195,8 +199,51 @@ class StripSolver:
         u[:, 0] = U
         return op.apply_mass(u.ravel()).reshape(-1, op.R)[:, 0]
 
-    def rhs(self, MU: np.ndarray) -> np.ndarray:
-        return np.outer(MU, self.e_start).ravel()
+    def source_rhs(self, t0: float) -> np.ndarray:
+        """int_I (f, w + delta (d_t w + beta . grad w)) dt for w = eta_s phi psi on
+        the strip I = (t0, t0 + dt) (Sect. 2, b_j), f = sum_k c_k ft_k fx_k fv_k,
+        beta_c = b_c(x) c_c(v):
+          (f, w)            -> int ft eta_s      (fx, phi)(fv, psi)
+          delta (f, d_t w)  -> delta int ft eta_s' (fx, phi)(fv, psi)
+          delta (f, beta_c d_c w) -> delta int ft eta_s (fx b_c, D phi)(fv c_c, D psi)."""
+        op, prob = self.op, self.prob
+        R, d, dt, dl = op.R, prob.d, prob.dt, prob.delta
+        out = np.zeros(op.size)
+        if not prob.f:
+            return out
+        hx, hv = op.hx.levels[op.L], op.hv.levels[op.L]
+        mul = lambda f, g: (None if f is None and g is None else
+                            (lambda p: (f(p) if f is not None else 1.0) * (g(p) if g is not None else 1.0)))
+        ev = lambda s, t: eta(s, np.array([(t - t0) / dt]), dt)[0][0]     # eta_s(t)
+        ed = lambda s, t: eta(s, np.array([(t - t0) / dt]), dt)[1][0]     # d eta_s / dt
+
+        terms = []   # (time weights [R], x load (finest), v load (finest), x axis or -1, v axis or -1)
+        for src in prob.f:
+            ft = (lambda t: 1.0) if src.ft is None else (lambda t, g=src.ft: float(np.asarray(g(np.array([t])))[0]))
+            w_val = np.array([integrate.quad(lambda t, s=s: ft(t) * ev(s, t), t0, t0 + dt,
+                                             epsabs=1e-15, epsrel=1e-13)[0] for s in range(R)])
+            w_dt = np.array([integrate.quad(lambda t, s=s: ft(t) * ed(s, t), t0, t0 + dt,
+                                            epsabs=1e-15, epsrel=1e-13)[0] for s in range(R)])
+            terms.append((src.coef * (w_val + dl * w_dt), src.fx, src.fv, -1, -1))
+            for c, b in enumerate(prob.beta):
+                if b.coef == 0.0:
+                    continue
+                terms.append((src.coef * b.coef * dl * w_val, mul(src.fx, b.fx), mul(src.fv, b.fv),
+                              c if c < d else -1, c - d if c >= d else -1))
+        off = 0
+        for (l1, l2) in op.grids:
+            n1, n2 = op.grid_shape(l1, l2)
+            blk = np.zeros((n1, n2, R))
+            for (wt, fx, fv, ax, av) in terms:
+                Fx = assemble_load(hx, fx) if ax < 0 else assemble_load_grad(hx, fx, ax)
+                Fv = assemble_load(hv, fv) if av < 0 else assemble_load_grad(hv, fv, av)
+                blk += np.einsum("i,j,s->ijs", op.fx.embed(l1).T @ Fx, op.fv.embed(l2).T @ Fv, wt)
+            out[off:off + blk.size] = blk.ravel()
+            off += blk.size
+        return out
+
+    def rhs(self, MU: np.ndarray, t0: float = 0.0) -> np.ndarray:
+        return np.outer(MU, self.e_start).ravel() + self.source_rhs(t0)
 
     def endpoint(self, u: np.ndarray) -> np.ndarray:
         return u.reshape(-1, self.op.R) @ self.e_end
@@ -215,7 +262,7 @@ class StripSolver:
         MU = self.initial_mass_u0()
         ends = []
         for j in range(n):
-            u, it, res = self.solve_strip(self.rhs(MU))
+            u, it, res = self.solve_strip(self.rhs(MU, j * self.prob.dt))
             U = self.endpoint(u)
             ends.append(U)
             MU = self.mass_spatial(U)

@@ -36,8 +36,17 @@ class Product(C.Structure):
     _fields_ = [("coef", C.c_double), ("fx", FN), ("ux", C.c_void_p), ("fv", FN), ("uv", C.c_void_p)]
 
 
+TFN = C.CFUNCTYPE(None, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
+
+
+class Source(C.Structure):
+    _fields_ = [("coef", C.c_double), ("fx", FN), ("ux", C.c_void_p), ("fv", FN), ("uv", C.c_void_p),
+                ("ft", TFN), ("ut", C.c_void_p)]
+
+
 class Coeffs(C.Structure):
-    _fields_ = [("beta", Product * 4), ("sigma", Product), ("n_u0", C.c_int), ("u0", C.POINTER(Product))]
+    _fields_ = [("beta", Product * 4), ("sigma", Product), ("n_u0", C.c_int), ("u0", C.POINTER(Product)),
+                ("n_f", C.c_int), ("f", C.POINTER(Source))]
 
 
 class Config(C.Structure):
@@ -206,7 +215,14 @@ class Solver:
             u0[k] = self._product(pr, d)
         co.n_u0 = len(problem.u0)
         co.u0 = u0
-        self._keep += [cfg, co, u0]
+        srcs = getattr(problem, "f", None) or []
+        fa = (Source * max(1, len(srcs)))()
+        for k, sr in enumerate(srcs):
+            fa[k] = Source(float(sr.coef), self._fn(sr.fx, d), None, self._fn(sr.fv, d), None, self._tfn(sr.ft),
+                           None)
+        co.n_f = len(srcs)
+        co.f = fa
+        self._keep += [cfg, co, u0, fa]
         h = C.c_void_p()
         st = self.lib.sgdg_create(C.byref(cfg), C.byref(co), C.byref(h))
         if self._cb_error:
@@ -257,6 +273,23 @@ class Solver:
         self._keep.append(c)
         return c
 
+    def _tfn(self, f):
+        if f is None:
+            return TFN()
+        errs = self._cb_error
+
+        def cb(n, ts, out, user):
+            try:
+                t = np.ctypeslib.as_array(ts, shape=(n,))
+                o = np.ctypeslib.as_array(out, shape=(n,))
+                o[:] = np.broadcast_to(np.asarray(f(t.copy()), dtype=np.float64), (n,))
+            except Exception as e:  # reported by the entry point that called it
+                errs.append(repr(e))
+                np.ctypeslib.as_array(out, shape=(n,))[:] = np.nan
+        c = TFN(cb)
+        self._keep.append(c)
+        return c
+
     def _product(self, pr, d) -> Product:
         return Product(float(pr.coef), self._fn(pr.fx, d), None, self._fn(pr.fv, d), None)
 
@@ -293,6 +326,8 @@ class Solver:
     def advance_strip(self, stream=None, check: bool = True) -> StripStats:
         st = StripStats()
         code = self.lib.sgdg_advance_strip(self.h, _stream(stream), C.byref(st))
+        if self._cb_error:
+            raise RuntimeError("source callback failed: " + self._cb_error[0])
         if check:
             self._check(code)
         return st

@@ -292,13 +292,19 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
 }
 
 Status load_vectors(const Hierarchy& h, sgdg_fn fn, void* user, std::vector<std::vector<double>>& out) {
+  return load_vectors_w(h, {{fn, user}}, 0, out);
+}
+
+Status load_vectors_w(const Hierarchy& h, const std::vector<std::pair<sgdg_fn, void*>>& fns, int deriv,
+                      std::vector<std::vector<double>>& out) {
   const int d = h.d, d1 = d + 1, L = h.L;
+  if (deriv < 0 || deriv > d) return {SGDG_EINVAL, "load vector: derivative direction out of range"};
   const MeshLevel& lv = h.lev[L];
   const int nc = lv.ncells(d);
   std::vector<double> rp, rw;
   simplex_rule(d, rp, rw);
   const int nq = (int)rw.size();
-  std::vector<double> pts((size_t)nc * nq * d), val;
+  std::vector<double> pts((size_t)nc * nq * d), val((size_t)nc * nq, 1.0), tmp;
   for (int e = 0; e < nc; ++e) {
     const double* v0 = &lv.cell_coords[(size_t)e * d1 * d];
     for (int q = 0; q < nq; ++q)
@@ -308,27 +314,46 @@ Status load_vectors(const Hierarchy& h, sgdg_fn fn, void* user, std::vector<std:
         pts[((size_t)e * nq + q) * d + k] = x;
       }
   }
-  if (fn) {
+  for (const auto& f : fns) {
+    if (!f.first) continue;
     SideFns t;
-    t.fn.push_back(fn);
-    t.user.push_back(user);
-    eval_fn(t, 0, pts, d, val);
-  } else {
-    val.assign((size_t)nc * nq, 1.0);
+    t.fn.push_back(f.first);
+    t.user.push_back(f.second);
+    eval_fn(t, 0, pts, d, tmp);
+    for (size_t i = 0; i < val.size(); ++i) val[i] *= tmp[i];
   }
   out.assign(L + 1, {});
   out[L].assign(lv.n, 0.0);
   for (int e = 0; e < nc; ++e) {
     const double* v0 = &lv.cell_coords[(size_t)e * d1 * d];
-    double det;
-    if (d == 1) det = v0[1] - v0[0];
-    else det = (v0[2] - v0[0]) * (v0[5] - v0[1]) - (v0[4] - v0[0]) * (v0[3] - v0[1]);
+    double J[2][2] = {{0, 0}, {0, 0}}, Ji[2][2], det;
+    for (int k = 0; k < d; ++k)
+      for (int a = 0; a < d; ++a) J[k][a] = v0[(a + 1) * d + k] - v0[k];
+    if (d == 1) { det = J[0][0]; Ji[0][0] = 1.0 / det; }
+    else {
+      det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det;
+      Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
+    }
+    // physical gradient component of the barycentric functions (constant per cell)
+    double grad[3] = {0.0, 0.0, 0.0};
+    if (deriv > 0)
+      for (int a = 0; a < d1; ++a) {
+        double g = 0.0;
+        for (int m = 0; m < d; ++m) {
+          const double gr = (a == 0) ? -1.0 : (m == a - 1 ? 1.0 : 0.0);
+          g += Ji[m][deriv - 1] * gr;
+        }
+        grad[a] = g;
+      }
     det = std::fabs(det);
     for (int q = 0; q < nq; ++q) {
       double lam[3];
       lam[0] = 1.0;
       for (int a = 1; a < d1; ++a) { lam[a] = rp[q * d + a - 1]; lam[0] -= lam[a]; }
-      for (int a = 0; a < d1; ++a) out[L][lv.cells[(size_t)e * d1 + a]] += rw[q] * det * val[(size_t)e * nq + q] * lam[a];
+      const double wq = rw[q] * det * val[(size_t)e * nq + q];
+      for (int a = 0; a < d1; ++a)
+        out[L][lv.cells[(size_t)e * d1 + a]] += wq * (deriv > 0 ? grad[a] : lam[a]);
     }
   }
   for (int l = L - 1; l >= 0; --l) {

@@ -374,6 +374,47 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
     h.u0v.push_back(lv);
     h.u0coef.push_back(c.u0[k].coef);
   }
+  // source f: the Kronecker terms of int_I (f, w + delta (d_t w + beta . grad w))
+  // (Sect. 2, b_j): (f_k, phi)(g_k, psi) scaled by int ft (eta_s + delta eta_s'),
+  // and per component beta_c = b_c(x) c_c(v) the term
+  // delta (f_k b_c, D phi)(g_k c_c, D psi) scaled by int ft eta_s, D the
+  // derivative along component c on its side
+  if (c.n_f > 0) {
+    if (cfg.vlasov_poisson) return {SGDG_EINVAL, "sources are not combined with vlasov_poisson"};
+    if (!c.f) return {SGDG_EINVAL, "n_f > 0 with a NULL source array"};
+    auto upload_levels = [&](const std::vector<std::vector<double>>& lv, std::vector<double*>& dst) -> Status {
+      dst.assign(lv.size(), nullptr);
+      for (size_t l = 0; l < lv.size(); ++l) SG_ST(upload(h, &dst[l], lv[l].data(), lv[l].size()));
+      return {};
+    };
+    for (int k = 0; k < c.n_f; ++k) {
+      const sgdg_source& f = c.f[k];
+      h.src_t.push_back({f.ft, f.ut});
+      Handle::SourceTerm t;
+      t.src = k;
+      t.kind = 0;
+      t.coef = f.coef;
+      std::vector<std::vector<double>> lx, lv;
+      SG_ST(load_vectors_w(hx, {{f.fx, f.ux}}, 0, lx));
+      SG_ST(load_vectors_w(hv, {{f.fv, f.uv}}, 0, lv));
+      SG_ST(upload_levels(lx, t.lx));
+      SG_ST(upload_levels(lv, t.lv));
+      h.src_terms.push_back(t);
+      for (int comp = 0; comp < 2 * h.d; ++comp) {
+        const sgdg_product& b = c.beta[comp];
+        if (b.coef == 0.0) continue;
+        Handle::SourceTerm tb;
+        tb.src = k;
+        tb.kind = 1;
+        tb.coef = f.coef * b.coef;
+        SG_ST(load_vectors_w(hx, {{f.fx, f.ux}, {b.fx, b.ux}}, comp < h.d ? comp + 1 : 0, lx));
+        SG_ST(load_vectors_w(hv, {{f.fv, f.uv}, {b.fv, b.uv}}, comp >= h.d ? comp - h.d + 1 : 0, lv));
+        SG_ST(upload_levels(lx, tb.lx));
+        SG_ST(upload_levels(lv, tb.lv));
+        h.src_terms.push_back(tb);
+      }
+    }
+  }
   if (dev_alloc(h, (void**)&h.U_end, sizeof(double) * h.n_spatial) != cudaSuccess ||
       dev_alloc(h, (void**)&h.u_sol, sizeof(double) * h.n_coeffs) != cudaSuccess ||
       dev_alloc(h, (void**)&h.rhs, sizeof(double) * h.n_coeffs) != cudaSuccess)
@@ -569,6 +610,7 @@ sgdg_status sgdg_set_initial(void* hp) {
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(h, {SGDG_ECUDA, "set_initial"});
   h->have_initial = true;
   h->first_strip = true;
+  h->t_now = 0.0;
   h->solved = false;
   h->nsolved = 0;
   return SGDG_OK;

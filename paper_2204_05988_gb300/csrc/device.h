@@ -68,6 +68,9 @@ cudaError_t reduce_parts(int k, const double* part, int nb, double* out, cudaStr
 // outer-product block: out[k1][k2][s] = e[s] * sum_p fx_p[k1] fv_p[k2]
 cudaError_t outer_init(double* out, int n1, int n2, int np, const double* fx, const double* fv, double e0,
                        double e1, cudaStream_t s);
+// out[k1][k2][s] += e_s * fx[k1] * fv[k2]   (FP64, R = 2)
+cudaError_t outer_add(double* out, int n1, int n2, const double* fx, const double* fv, double e0, double e1,
+                      cudaStream_t s);
 // nodal injection along one dim: out[k1][k2] = in[idx[k1]][k2] (dim 1) / in[k1][idx[k2]] (dim 2); R = 1
 cudaError_t inject_dim(const double* in, double* out, int n1_out, int n2_out, int n2_in, const int* idx, int dim,
                        int accumulate, cudaStream_t s);

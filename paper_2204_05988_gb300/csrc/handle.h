@@ -91,6 +91,13 @@ struct Handle {
   // host copies of the u0 load vectors per level (for set_initial)
   std::vector<std::vector<std::vector<double>>> u0x, u0v;   // [product][level][n]
   std::vector<double> u0coef;
+  // source terms of the strip right-hand side (Sect. 2, b_j): per term the x
+  // and v load vectors per level (device) and which time weight scales them:
+  // kind 0 - int ft eta_s + delta int ft eta_s',  kind 1 - delta int ft eta_s
+  struct SourceTerm { int src = 0, kind = 0; double coef = 0.0; std::vector<double*> lx, lv; };
+  std::vector<SourceTerm> src_terms;
+  std::vector<std::pair<sgdg_tfn, void*>> src_t;   // time factor per source
+  double t_now = 0.0;                              // start of the next strip
   // strip state
   double* U_end = nullptr;   // spatial, n_spatial
   double* u_sol = nullptr;   // last strip solution, n_coeffs

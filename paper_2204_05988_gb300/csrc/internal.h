@@ -102,5 +102,10 @@ void product_values(const Csr& A, const std::vector<double>& aval, const Csr& B,
 
 // Load vector F[i] = int fn phi_i on the finest level, restricted to all levels.
 Status load_vectors(const Hierarchy& h, sgdg_fn fn, void* user, std::vector<std::vector<double>>& per_level);
+// F[i] = int (prod_k fns[k]) D phi_i, D = identity (deriv 0) or d/dy_p (deriv
+// p + 1), on the finest level and restricted to all levels; NULL functions
+// are the constant 1.
+Status load_vectors_w(const Hierarchy& h, const std::vector<std::pair<sgdg_fn, void*>>& fns, int deriv,
+                      std::vector<std::vector<double>>& per_level);
 
 }  // namespace sgdg

@@ -243,6 +243,25 @@ template cudaError_t launch_right<float>(SpmmLaunch<float>&, cudaStream_t);
 // vector kernels
 // ---------------------------------------------------------------------------
 
+__global__ void k_outer_add(double* out, int n1, int n2, const double* fx, const double* fv, double e0, double e1) {
+  const long long n = (long long)n1 * n2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long k1 = i / n2, k2 = i - k1 * n2;
+    const double p = fx[k1] * fv[k2];
+    out[2 * i] += e0 * p;
+    out[2 * i + 1] += e1 * p;
+  }
+}
+
+cudaError_t outer_add(double* out, int n1, int n2, const double* fx, const double* fv, double e0, double e1,
+                      cudaStream_t s) {
+  const long long n = (long long)n1 * n2;
+  if (n <= 0) return cudaSuccess;
+  const long long b = std::min<long long>((n + 255) / 256, (long long)num_sms() * 8);
+  k_outer_add<<<(unsigned)b, 256, 0, s>>>(out, n1, n2, fx, fv, e0, e1);
+  return cudaGetLastError();
+}
+
 int num_sms() {
   static int n = 0;
   if (!n) {

@@ -787,6 +787,44 @@ Status ct_precondition(Handle& h, const double* r, double* z, cudaStream_t s, in
   return ct_apply<double>(h, r, z, s, its);
 }
 
+// rhs += the source part of b_j (Sect. 2) on the strip [t_now, t_now + dt]:
+// per source k the time weights
+//   e1_s = int_I ft_k eta_s dt,   e0_s = e1_s + delta int_I ft_k eta_s' dt
+// by 3-point Gauss-Legendre (exact for ft of degree <= 4), then every
+// Kronecker term of the source on every grid.
+static Status add_source(Handle& h, cudaStream_t s) {
+  if (h.src_terms.empty()) return {};
+  const double dt = h.cfg.dt, ta = h.t_now, dl = h.cfg.delta;
+  const double z[3] = {-std::sqrt(0.6), 0.0, std::sqrt(0.6)};
+  const double wz[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+  double tq[3];
+  for (int q = 0; q < 3; ++q) tq[q] = ta + 0.5 * dt * (1.0 + z[q]);
+  const size_t ns = h.src_t.size();
+  std::vector<double> e0(2 * ns), e1(2 * ns);
+  for (size_t k = 0; k < ns; ++k) {
+    double fq[3] = {1.0, 1.0, 1.0};
+    if (h.src_t[k].first) h.src_t[k].first(3, tq, fq, h.src_t[k].second);
+    double a0 = 0.0, a1 = 0.0, d1 = 0.0;   // int ft eta_0, int ft eta_1, int ft eta_1'
+    for (int q = 0; q < 3; ++q) {
+      const double w = 0.5 * dt * wz[q] * fq[q];
+      a0 += w;                 // eta_0 = 1
+      a1 += w * z[q];          // eta_1 = 2 (t - t_a) / dt - 1 = z
+      d1 += w * 2.0 / dt;      // eta_1' = 2 / dt  (eta_0' = 0)
+    }
+    e1[2 * k] = a0;
+    e1[2 * k + 1] = a1;
+    e0[2 * k] = a0;
+    e0[2 * k + 1] = a1 + dl * d1;
+  }
+  for (const Handle::SourceTerm& t : h.src_terms) {
+    const double* e = t.kind == 0 ? &e0[2 * t.src] : &e1[2 * t.src];
+    const double sc = t.kind == 0 ? t.coef : t.coef * dl;
+    for (int l = 0; l <= h.L; ++l)
+      SG_CU(outer_add(h.rhs + h.off[l], h.n1[l], h.n2[l], t.lx[l], t.lv[h.L - l], sc * e[0], sc * e[1], s));
+  }
+  return {};
+}
+
 // w = A z in the configured precision (FP64 storage in and out).
 static Status apply_mixed(Handle& h, const double* z, double* w, bool force64, cudaStream_t s) {
   if (force64 || h.cfg.precision == SGDG_FP64) return apply_plan<double>(h, h.op, z, w, s);
@@ -812,6 +850,7 @@ Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resol
     SG_CU(cudaGetLastError());
     SG_ST(apply_plan<double>(h, h.mass, O.t0, h.rhs, s));
   }
+  if (!resolve) SG_ST(add_source(h, s));
   sgdg_strip_stats S{};
   double bnorm;
   SG_ST(vnorm<double>(h, h.rhs, n, &bnorm, s));
@@ -887,7 +926,10 @@ Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resol
   SG_CU(cudaStreamSynchronize(s));
   h.first_strip = false;
   h.solved = true;
-  if (!resolve) h.nsolved++;
+  if (!resolve) {
+    h.nsolved++;
+    h.t_now += h.cfg.dt;
+  }
   S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (st) *st = S;
   if (S.status == SGDG_ENOCONV) return {SGDG_ENOCONV, "outer FGMRES reached max_outer"};

@@ -51,6 +51,16 @@ class Product:
 
 
 @dataclass
+class Source:
+    """coef * ft(t) * fx(x) * fv(v), one term of the source f; ``None``
+    factors are the constant 1 (ft maps an array of times to values)."""
+    coef: float
+    fx: Fn = None
+    fv: Fn = None
+    ft: Optional[Callable[[np.ndarray], np.ndarray]] = None
+
+
+@dataclass
 class Problem:
     """One transport problem on a product phase space (Sect. 1-2)."""
     name: str
@@ -66,6 +76,7 @@ class Problem:
     sigma: Product
     u0: List[Product]           # sum of separable products
     exact: Optional[Callable[[float, np.ndarray, np.ndarray], np.ndarray]] = None
+    f: List[Source] = field(default_factory=list)   # source, sum of separable terms
 
 
 # ----------------------------------------------------------------------------
@@ -197,6 +208,105 @@ def landau_4d(L: int = 8, alpha: float = 0.01, k: float = 0.5, n_strips: int = 2
         beta=[Product(1.0, None, lambda p: p[:, 0]), Product(1.0, None, lambda p: p[:, 1]),
               Product(-1.0, zero, None), Product(-1.0, zero, None)],
         sigma=Product(0.0), u0=[Product(1.0, fx, fv)])
+
+
+def _poly(c):
+    """t -> c[0] + c[1] t + c[2] t^2 and its derivative."""
+    a = lambda t: c[0] + c[1] * np.asarray(t) + c[2] * np.asarray(t) ** 2
+    da = lambda t: c[1] + 2.0 * c[2] * np.asarray(t)
+    return a, da
+
+
+def manufactured_1d(L: int = 4, sigma: float = 0.5, dt: float = 1.0 / 16.0, n_strips: int = 4,
+                    seed: int = 0) -> Problem:
+    """d=1 manufactured solution u*(t, x, v) = a(t) X(x) V(v) on [0,1] x [-1,1]
+    with X = sin^2(pi x), V = cos^2(pi v / 2) (1 + b v), a a seeded quadratic;
+    beta = (v, 0), constant sigma; f = d_t u* + v d_x u* + sigma u* as three
+    separable terms.  u* vanishes on the boundary, so the inflow data g is 0."""
+    rng = np.random.default_rng(seed)
+    c = (1.0, float(rng.uniform(-0.5, 0.5)), float(rng.uniform(-0.5, 0.5)))
+    b = float(rng.uniform(-0.3, 0.3))
+    a, da = _poly(c)
+    X = lambda p: np.sin(np.pi * p[:, 0]) ** 2
+    dX = lambda p: np.pi * np.sin(2 * np.pi * p[:, 0])
+    V = lambda p: np.cos(0.5 * np.pi * p[:, 0]) ** 2 * (1.0 + b * p[:, 0])
+    vV = lambda p: p[:, 0] * V(p)
+
+    def exact(t, x, v):
+        return a(t) * np.sin(np.pi * x) ** 2 * np.cos(0.5 * np.pi * v) ** 2 * (1.0 + b * v)
+
+    f = [Source(1.0, X, V, da), Source(sigma, X, V, a), Source(1.0, dX, vV, a)]
+    h = 1.0 / (4 * 2 ** L)
+    return Problem(name=f"manufactured_1d_L{L}", d=1, mesh_x=interval_mesh(0.0, 1.0, 4),
+                   mesh_v=interval_mesh(-1.0, 1.0, 4), L=L, r=1, dt=dt, delta=h, n_strips=n_strips,
+                   beta=[Product(1.0, None, lambda p: p[:, 0]), Product(0.0)],
+                   sigma=Product(sigma) if sigma != 0.0 else Product(0.0),
+                   u0=[Product(float(a(0.0)), X, V)], exact=exact, f=f)
+
+
+def discrete_manufactured_1d(L: int = 3, sigma: float = 0.5, dt: float = 1.0 / 8.0, n_strips: int = 2,
+                             c0: float = 1.0, c1: float = 0.75) -> Problem:
+    """d=1 solution inside the discrete space: u*(t, x, v) = (c0 + c1 t)
+    phi(x) psi(v) with phi, psi the level-0 hat functions at x = 1/2 and v = 0
+    (supports inside the domain, so the inflow data g = 0), beta = (v, 0),
+    constant sigma; f = d_t u* + v d_x u* + sigma u* as three separable terms
+    (piecewise polynomial, kinks on coarse mesh lines).  A consistent scheme
+    with exact quadrature reproduces u* up to the solver tolerance."""
+    phi = lambda p: np.maximum(0.0, 1.0 - np.abs(p[:, 0] - 0.5) / 0.25)
+    dphi = lambda p: np.where(np.abs(p[:, 0] - 0.5) < 0.25, -np.sign(p[:, 0] - 0.5) / 0.25, 0.0)
+    psi = lambda p: np.maximum(0.0, 1.0 - np.abs(p[:, 0]) / 0.5)
+    vpsi = lambda p: p[:, 0] * psi(p)
+    a = lambda t: c0 + c1 * np.asarray(t)
+    da = lambda t: c1 + 0.0 * np.asarray(t)
+
+    def exact(t, x, v):
+        return (c0 + c1 * t) * np.maximum(0.0, 1.0 - np.abs(x - 0.5) / 0.25) * np.maximum(0.0, 1.0 - np.abs(v) / 0.5)
+
+    f = [Source(1.0, phi, psi, da), Source(sigma, phi, psi, a), Source(1.0, dphi, vpsi, a)]
+    h = 1.0 / (4 * 2 ** L)
+    return Problem(name=f"discrete_manufactured_1d_L{L}", d=1, mesh_x=interval_mesh(0.0, 1.0, 4),
+                   mesh_v=interval_mesh(-1.0, 1.0, 4), L=L, r=1, dt=dt, delta=h, n_strips=n_strips,
+                   beta=[Product(1.0, None, lambda p: p[:, 0]), Product(0.0)],
+                   sigma=Product(sigma) if sigma != 0.0 else Product(0.0),
+                   u0=[Product(c0, phi, psi)], exact=exact, f=f)
+
+
+def manufactured_2d(L: int = 9, sigma: float = 0.1, dt: float = 1.0 / 64.0, n_strips: int = 16,
+                    seed: int = 0) -> Problem:
+    """d=2 manufactured solution on the transport_2d problem (beta = (v1, v2,
+    E1(x), E2(x)), E = 0.5 (sin 2 pi x2, cos 2 pi x1), constant sigma):
+    u* = a(t) X(x) V(v), X = sin^2(pi x1) sin^2(pi x2),
+    V = cos^2(pi v1 / 2) cos^2(pi v2 / 2) (1 + b1 v1 + b2 v2), a a seeded
+    quadratic; f = d_t u* + beta . grad u* + sigma u* as six separable terms.
+    u* vanishes on the boundary, so the inflow data g is 0."""
+    base = transport_2d(L=L, sigma=sigma, dt=dt, n_strips=n_strips)
+    rng = np.random.default_rng(seed)
+    c = (1.0, float(rng.uniform(-0.5, 0.5)), float(rng.uniform(-0.5, 0.5)))
+    b1, b2 = (float(x) for x in rng.uniform(-0.3, 0.3, size=2))
+    a, da = _poly(c)
+    pi = np.pi
+    X = lambda p: np.sin(pi * p[:, 0]) ** 2 * np.sin(pi * p[:, 1]) ** 2
+    d1X = lambda p: pi * np.sin(2 * pi * p[:, 0]) * np.sin(pi * p[:, 1]) ** 2
+    d2X = lambda p: pi * np.sin(pi * p[:, 0]) ** 2 * np.sin(2 * pi * p[:, 1])
+    C = lambda p: np.cos(0.5 * pi * p[:, 0]) ** 2 * np.cos(0.5 * pi * p[:, 1]) ** 2
+    lin = lambda p: 1.0 + b1 * p[:, 0] + b2 * p[:, 1]
+    V = lambda p: C(p) * lin(p)
+    v1V = lambda p: p[:, 0] * V(p)
+    v2V = lambda p: p[:, 1] * V(p)
+    d1V = lambda p: (-0.5 * pi * np.sin(pi * p[:, 0]) * np.cos(0.5 * pi * p[:, 1]) ** 2 * lin(p) + C(p) * b1)
+    d2V = lambda p: (-0.5 * pi * np.cos(0.5 * pi * p[:, 0]) ** 2 * np.sin(pi * p[:, 1]) * lin(p) + C(p) * b2)
+    E1X = lambda p: np.sin(2 * pi * p[:, 1]) * X(p)
+    E2X = lambda p: np.cos(2 * pi * p[:, 0]) * X(p)
+
+    def exact(t, x, v):
+        return a(t) * X(x) * V(v)
+
+    base.name = f"manufactured_2d_L{L}"
+    base.u0 = [Product(float(a(0.0)), X, V)]
+    base.exact = exact
+    base.f = [Source(1.0, X, V, da), Source(sigma, X, V, a), Source(1.0, d1X, v1V, a), Source(1.0, d2X, v2V, a),
+              Source(0.5, E1X, d1V, a), Source(0.5, E2X, d2V, a)]
+    return base
 
 
 def batched_4d(n: int = 48, seed: int = 0, levels=(6, 7, 8, 9), dt: float = 1.0 / 32.0,
