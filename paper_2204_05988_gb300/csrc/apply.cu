@@ -39,74 +39,12 @@ namespace sgdg {
     if (e_ != cudaSuccess) return {SGDG_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)}; \
   } while (0)
 
-template <typename T>
-cudaError_t run_spmm(Handle& h, bool left, SpmmLaunch<T>& a, cudaStream_t s, int kind, double mat_bytes) {
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (h.prof) {
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, s);
-  }
-  cudaError_t e = left ? launch_left(a, s) : launch_right(a, s);
-  h.launches++;
-  if (h.prof) {
-    cudaEventRecord(e1, s);
-    double bytes = mat_bytes;
-    for (int g = 0; g < a.ngrids; ++g) {
-      double in = 2.0 * sizeof(T) * (double)a.g[g].n1_in * a.g[g].n2_in;
-      double out = 2.0 * sizeof(T) * (double)a.g[g].n1_out * a.g[g].n2_out;
-      bytes += in * (a.g[g].in2 ? 2 : 1) + out * (a.accumulate ? 2 : 1);
-    }
-    h.kev.push_back({kind, bytes, e0, e1, -1, 0.0});
-  }
-  return e;
-}
-template cudaError_t run_spmm<double>(Handle&, bool, SpmmLaunch<double>&, cudaStream_t, int, double);
-template cudaError_t run_spmm<float>(Handle&, bool, SpmmLaunch<float>&, cudaStream_t, int, double);
 
 namespace {
 
 // bytes of a level's CSR pattern plus nvals value arrays
-template <typename T>
-double pattern_bytes(const SideDev& sd, int lev, int nvals) {
-  return 4.0 * (sd.n[lev] + 1) + (4.0 + nvals * (double)sizeof(T)) * sd.nnz[lev];
-}
 
-template <typename T>
-void set_terms(Handle& h, SpmmLaunch<T>& a, const std::vector<Term>& terms, const std::vector<int>& idx, int lo,
-               int hi, bool x_side, int level_of_grid[], int ngrids) {
-  (void)ngrids;
-  a.nterms = hi - lo;
-  a.identity = 0;
-  for (int t = lo; t < hi; ++t) {
-    const Term& tm = terms[idx[t]];
-    for (int s = 0; s < 2; ++s)
-      for (int q = 0; q < 2; ++q) a.tau[t - lo][s * 2 + q] = (T)tm.tau[s][q];
-  }
-  SideDev& sd = x_side ? h.X : h.V;
-  for (int g = 0; g < a.ngrids; ++g) {
-    int lev = level_of_grid[g];
-    a.g[g].rowptr = sd.rowptr[lev];
-    a.g[g].col = sd.col[lev];
-    for (int t = lo; t < hi; ++t) {
-      const Term& tm = terms[idx[t]];
-      a.g[g].val[t - lo] = sd.vals<T>().fac[x_side ? tm.x : tm.v][lev];
-    }
-  }
-}
 
-template <typename T>
-void set_single(Handle& h, SpmmLaunch<T>& a, int factor, bool x_side, int level_of_grid[]) {
-  a.nterms = 1;
-  a.identity = 1;
-  SideDev& sd = x_side ? h.X : h.V;
-  for (int g = 0; g < a.ngrids; ++g) {
-    int lev = level_of_grid[g];
-    a.g[g].rowptr = sd.rowptr[lev];
-    a.g[g].col = sd.col[lev];
-    a.g[g].val[0] = sd.vals<T>().fac[factor][lev];
-  }
-}
 
 template <typename T>
 Handle::Bufs& bufs(Handle& h);
@@ -176,10 +114,6 @@ Status ensure_pool(Handle& h, const Plan& p, Pool<T>& pool) {
   return {};
 }
 
-template <typename T>
-double csr_bytes(int rows, int nnz, int nvals) {
-  return 4.0 * (rows + 1) + (4.0 + (double)nvals * sizeof(T)) * nnz;
-}
 
 // launch site: kind (< 16), chains or terms (< 64), element size, grid shape (< 2^24 each)
 inline long long site_key(int kind, int n1, int n2, int count, int elem) {

@@ -50,9 +50,6 @@ template <typename TI, typename TO>
 cudaError_t vec_convert(const TI* x, TO* y, long long n, cudaStream_t s);
 template <typename T>
 cudaError_t vec_axpby(long long n, double a, const T* x, double b, T* y, cudaStream_t s);   // y = a x + b y
-// out[i] = sum over the time slot pair: y[k][s] = sum_s' M[s][s'] x[k][s'], elementwise 2x2
-template <typename T>
-cudaError_t vec_time2x2(long long npts, const double M[4], const T* x, T* y, cudaStream_t s);
 // partial dot products of w with k vectors V + i*ldv: part[i*nb + b]; nb = gridDim
 template <typename T>
 cudaError_t vec_multidot(int k, const T* V, long long ldv, const T* w, long long n, double* part, int nb,

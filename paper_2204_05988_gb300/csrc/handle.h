@@ -144,11 +144,6 @@ enum {
   KIND_CHAIN_A = 4, KIND_CHAIN_B = 5, KIND_RESERVED = 6, KIND_FINAL_RIGHT = 7, KIND_COUNT = 8
 };
 
-// Launch a grouped SpMM (left or right) with accounting.  mat_bytes: bytes of
-// the CSR pattern and value arrays the launch reads.
-template <typename T>
-cudaError_t run_spmm(Handle& h, bool left, SpmmLaunch<T>& a, cudaStream_t s, int kind, double mat_bytes);
-
 // allocation helper that records bytes and reports ENOMEM
 cudaError_t dev_alloc(Handle& h, void** p, size_t bytes);
 

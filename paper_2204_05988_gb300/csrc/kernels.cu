@@ -319,24 +319,6 @@ cudaError_t vec_axpby(long long n, double a, const T* x, double b, T* y, cudaStr
 template cudaError_t vec_axpby<double>(long long, double, const double*, double, double*, cudaStream_t);
 template cudaError_t vec_axpby<float>(long long, double, const float*, double, float*, cudaStream_t);
 
-struct M22 { double m[4]; };
-template <typename T>
-__global__ void k_time2x2(long long npts, M22 M, const T* x, T* y) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
-    double a = x[2 * i], b = x[2 * i + 1];
-    y[2 * i] = (T)(M.m[0] * a + M.m[1] * b);
-    y[2 * i + 1] = (T)(M.m[2] * a + M.m[3] * b);
-  }
-}
-template <typename T>
-cudaError_t vec_time2x2(long long npts, const double M[4], const T* x, T* y, cudaStream_t s) {
-  M22 m;
-  for (int i = 0; i < 4; ++i) m.m[i] = M[i];
-  k_time2x2<<<grid_for(npts), kThreads, 0, s>>>(npts, m, x, y);
-  return cudaGetLastError();
-}
-template cudaError_t vec_time2x2<double>(long long, const double*, const double*, double*, cudaStream_t);
-template cudaError_t vec_time2x2<float>(long long, const double*, const float*, float*, cudaStream_t);
 
 // Deterministic multi-dot: block b reduces its grid-stride share of all k
 // dots in a fixed order; the host-side or reduce_parts sum runs in block order.
