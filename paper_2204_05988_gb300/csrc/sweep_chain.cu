@@ -15,13 +15,16 @@ namespace {
 
 using namespace sweep;
 
-template <typename T, int ROW>
+// resident blocks per SM the register budget is sized for: rows of up to 8
+// entries keep 4 FP32 blocks; wide rows (restriction-factor products) keep 3
+// in mode B and 2 in mode A, whose 2 x 19 gathered U values would spill at 3
+template <typename T, int ROW, bool MODE_A>
 struct ChainBounds {
-  static constexpr int blocks = ROW > 8 ? 2 : (sizeof(T) == 4 ? 4 : 2);
+  static constexpr int blocks = sizeof(T) == 4 ? (ROW > 8 ? (MODE_A ? 2 : 3) : 4) : 2;
 };
 
 template <typename T, bool MODE_A, int ROW>
-__global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW>::blocks)) k_chain(const __grid_constant__ ChainArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, MODE_A>::blocks)) k_chain(const __grid_constant__ ChainArgs<T> a) {
   using T2 = typename V2<T>::type;
   constexpr int W = Ell<ROW>::W;
   constexpr bool kPrefetch = ROW <= 8;

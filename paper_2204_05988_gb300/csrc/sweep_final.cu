@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kThreads) k_final(const __grid_constant__ Fina
 // 64 consecutive columns, both loads coalesced); right - rows k1 and k1 + 1
 // of one column.
 template <typename T, bool LEFT, int ROW>
-__global__ void __launch_bounds__(kThreads) k_final2(const __grid_constant__ FinalArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_final2(const __grid_constant__ FinalArgs<T> a) {
   using T2 = typename V2<T>::type;
   constexpr int W = Ell<ROW>::W;
   const unsigned n2 = (unsigned)a.n2;
