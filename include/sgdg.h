@@ -315,7 +315,8 @@ sgdg_status sgdg_batch_advance(void* batch, sgdg_strip_stats* per_member);
  * 0 = per-grid states S_b = u V_b^T (+ P1 Z_b) of the sweep's branch A and of
  *     the diagonal blocks, 1 = final updates y (+)= tau X S_b along dim 1,
  * 2 / 3 = restriction of sweep chain states along dim 1 / dim 2,
- * 4 / 5 = sweep chain steps of branch A / B, 6 = reserved (no launches),
+ * 4 / 5 = sweep chain steps of branch A (no launches: branch A restricts the
+ *     states S_b, kind 3) / branch B, 6 = reserved (no launches),
  * 7 = final updates of branch B along dim 2.
  * n_kinds must be >= 8. */
 typedef struct {

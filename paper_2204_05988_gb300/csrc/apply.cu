@@ -11,18 +11,19 @@
 // applied first (P = prolongation E, R = restriction E^T, subscript = the
 // dimension, U_i the input on grid i):
 //   branch A (sources l1' <= l1), chains b by V:
-//     Z_{b,1} = U_0 (R2 V_b)^T,   Z_{b,i+1} = P1 (Z_{b,i} R2^T) + U_i (R2 V_b)^T
-//     S_{b,i} = U_i V_b^T + P1 Z_{b,i},   Y_i = sum_a tau_a X_a S_{b,i}
+//     S_{b,i} = U_i V_b^T + P1 Z_{b,i},   Z_{b,i+1} = S_{b,i} R2^T,   Z_{b,0} = 0
+//     Y_i = sum_a tau_a X_a S_{b,i}
 //   branch B (sources l1' > l1), chains c by X:
 //     Z_{c,L-1} = (R1 X_c) U_L,   Z_{c,i} = (R1 Z_{c,i+1}) P2^T + (R1 X_c) U_{i+1}
 //     Y_i += tau_a Z_{c,i} (V_a P2)^T
 // Z_{b,i} = S_{b,i-1} R2^T and Z_{c,i} = R1 T_{c,i+1} are the chain states of
 // the plain recursions S_i = P1 R2 S_{i-1} + U_i V^T and T'_i = R1 P2 (T'_{i+1}
-// + X U_{i+1}) taken one transfer early: they live on the coarse side of both
-// dimensions (a quarter of a grid for 2-D sides) and are the only states
-// carried from grid to grid; S_{b,i} (which includes the diagonal blocks) is
-// formed on each grid only to feed its final update.  The products R2 V_b,
-// R1 X_c and V_a P2 are formed once per level on the host.  This reaches
+// + X U_{i+1}) taken one transfer early, restriction before prolongation:
+// they live on the coarse side of both dimensions (a quarter of a grid for
+// 2-D sides).  S_{b,i}, which includes the diagonal blocks, is formed on every
+// grid for its final update and restricted once to carry the chains on;
+// branch B never forms T or T' at full size.  The products R1 X_c and V_a P2
+// are formed once per level on the host.  This reaches
 // the blockwise sum of Sect. 4.2 exactly in exact arithmetic with
 // O(#terms * N) work; no intermediate exceeds one component grid, like the
 // ordering rule of Sect. 4.2.
@@ -351,48 +352,24 @@ Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s) {
                        [&](int c) { return i >= 1 ? (const T*)pool.ZA(c, i & 1) : (const T*)nullptr; });
     if (st.code) return st;
     if (i == L) break;
-    // Z_{b,i+1} = P1 (Z_{b,i} R2^T) + U_i (R2 V_b)^T:  (nx[i] x nv[lv-1])
+    // Z_{b,i+1} = S_{b,i} R2^T  (nx[i] x nv[lv-1]): S_{b,i} is already formed
+    // for the final update, so one restriction carries every chain forward
     for (int c0 = 0; c0 < nA; c0 += G) {
       const int nc = std::min(G, nA - c0);
-      double qbytes = 0.0;
-      if (i >= 1) {
-        RestrictArgs<T> r;   // Q_g = Z_{b,i} R2^T: (nx[i-1] x nv[lv-1])
-        r.n1 = X.n[i - 1];
-        r.n2 = V.n[lv - 1];
-        r.n1_in = X.n[i - 1];
-        r.n2_in = V.n[lv];
-        r.nchains = nc;
-        r.row = V.row_regs();
-        r.col = V.R_ell_col[lv - 1];
-        r.val = V.vals<T>().ell_R[lv - 1];
-        for (int g = 0; g < nc; ++g) {
-          r.in[g] = pool.ZA(c0 + g, i & 1);
-          r.out[g] = pool.Q(g);
-        }
-        st = run_restrict(h, r, true, s, ell_bytes<T>(V.n[lv - 1], V.ell_w(), 1));
-        if (st.code) return st;
-        qbytes = nc * grid_bytes<T>(r.n1, r.n2) + ell_bytes<T>(X.n[i], kEllE, 1);
-      }
-      ChainArgs<T> a;
-      a.n1 = X.n[i];
-      a.n2 = V.n[lv - 1];
-      a.nu2 = V.n[lv];
-      a.nchains = nc;
-      a.has_prev = i >= 1;
-      a.row = row_class(V.rf_row);
-      a.U = u + h.off[i];
-      a.f_col = V.RF_ell_col[lv - 1];
+      RestrictArgs<T> r;
+      r.n1 = X.n[i];
+      r.n2 = V.n[lv - 1];
+      r.n1_in = X.n[i];
+      r.n2_in = V.n[lv];
+      r.nchains = nc;
+      r.row = V.row_regs();
+      r.col = V.R_ell_col[lv - 1];
+      r.val = V.vals<T>().ell_R[lv - 1];
       for (int g = 0; g < nc; ++g) {
-        a.f_val[g] = V.vals<T>().ell_RF[p.A[c0 + g].first][lv - 1];
-        a.out[g] = pool.ZA(c0 + g, (i + 1) & 1);
-        a.Z[g] = i >= 1 ? pool.Q(g) : nullptr;
+        r.in[g] = pool.W(c0 + g);
+        r.out[g] = pool.ZA(c0 + g, (i + 1) & 1);
       }
-      if (i >= 1) {
-        a.p_col = X.E_ell_col[i - 1];
-        a.p_val = X.vals<T>().ell_E[i - 1];
-      }
-      st = run_chain(h, a, true, KIND_CHAIN_A, s,
-                     qbytes + grid_bytes<T>(h.n1[i], h.n2[i]) + ell_bytes<T>(V.n[lv - 1], V.rf_w(), nc));
+      st = run_restrict(h, r, true, s, ell_bytes<T>(V.n[lv - 1], V.ell_w(), 1));
       if (st.code) return st;
     }
   }

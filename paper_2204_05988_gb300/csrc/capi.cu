@@ -102,7 +102,7 @@ Status upload_ell_vals(Handle& h, const std::vector<int>& rowptr, const std::vec
 Status upload_factor_products(Handle& h, const Hierarchy& hi, SideDev& sd, int f, const std::vector<Csr>& X) {
   const int L = hi.L;
   std::vector<double> v;
-  for (int l = 0; l < L; ++l) {
+  for (int l = 0; l < L && sd.has_rf; ++l) {
     product_values(hi.Rt[l], hi.Rt[l].val, X[l + 1], X[l + 1].val, sd.RF_pat[l], v);
     SG_ST(upload_ell_vals(h, sd.RF_pat[l].rowptr, v, sd.rf_w(), &sd.v64.ell_RF[f][l], &sd.v32.ell_RF[f][l]));
   }
@@ -116,15 +116,16 @@ Status upload_factor_products(Handle& h, const Hierarchy& hi, SideDev& sd, int f
 
 namespace {
 
-// Patterns of the factor-transfer products R_l F_{l+1} and (with_fp)
-// F_l E_{l-1}, shared by every factor of the side, uploaded in ELL form.
-Status setup_products(Handle& h, const Hierarchy& hi, SideDev& sd, bool with_fp) {
+// Patterns of the factor-transfer products R_l F_{l+1} (with_rf) and
+// F_l E_{l-1} (with_fp), shared by every factor of the side, in ELL form.
+Status setup_products(Handle& h, const Hierarchy& hi, SideDev& sd, bool with_rf, bool with_fp) {
   const int L = hi.L;
+  sd.has_rf = with_rf;
   sd.has_fp = with_fp;
   sd.RF_pat.assign(L, Csr());
   sd.FP_pat.assign(L + 1, Csr());
   sd.rf_row = sd.fp_row = 0;
-  for (int l = 0; l < L; ++l) {
+  for (int l = 0; l < L && with_rf; ++l) {
     sd.RF_pat[l] = product_pattern(hi.Rt[l], hi.lev[l + 1].pattern);
     for (int r = 0; r < sd.RF_pat[l].nrows; ++r)
       sd.rf_row = std::max(sd.rf_row, sd.RF_pat[l].rowptr[r + 1] - sd.RF_pat[l].rowptr[r]);
@@ -140,7 +141,7 @@ Status setup_products(Handle& h, const Hierarchy& hi, SideDev& sd, bool with_fp)
   sd.fp_row = std::max(sd.fp_row, 1);
   sd.RF_ell_col.assign(L, nullptr);
   sd.FP_ell_col.assign(L + 1, nullptr);
-  for (int l = 0; l < L; ++l) {
+  for (int l = 0; l < L && with_rf; ++l) {
     const std::vector<int> c = ell_columns(sd.RF_pat[l].rowptr, sd.RF_pat[l].col, sd.rf_w());
     SG_ST(upload(h, &sd.RF_ell_col[l], c.data(), c.size()));
   }
@@ -294,9 +295,9 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   h.V.maxrow = side_maxrow[1];
   SG_ST(upload_side(h, hx, h.X));
   SG_ST(upload_side(h, hv, h.V));
-  // the sweep uses R X (branch B), R V (branch A) and V E (branch B's final)
-  SG_ST(setup_products(h, hx, h.X, false));
-  SG_ST(setup_products(h, hv, h.V, true));
+  // the sweep uses R X (branch B's chain steps) and V E (branch B's final)
+  SG_ST(setup_products(h, hx, h.X, true, false));
+  SG_ST(setup_products(h, hv, h.V, false, true));
   for (int side = 0; side < 2; ++side) {
     SideDev& sd = side == 0 ? h.X : h.V;
     const Hierarchy& hi = side == 0 ? hx : hv;

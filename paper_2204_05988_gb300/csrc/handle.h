@@ -19,7 +19,8 @@ struct SideValues {
   std::vector<std::vector<T*>> ell_fac;   // [factor][level]
   std::vector<T*> ell_E, ell_R;
   // products with the transfers, ELL: RF[f][l] = R_l F_{l+1} (l < L, width
-  // rf_w), FP[f][l] = F_l E_{l-1} (1 <= l <= L, width fp_w; sides with has_fp)
+  // rf_w; sides with has_rf), FP[f][l] = F_l E_{l-1} (1 <= l <= L, width fp_w;
+  // sides with has_fp)
   std::vector<std::vector<T*>> ell_RF, ell_FP;
 };
 
@@ -40,7 +41,7 @@ struct SideDev {
   // patterns of the factor-transfer products (shared by all factors of the side)
   std::vector<int*> RF_ell_col, FP_ell_col;          // [l] as SideValues::ell_RF / ell_FP
   int rf_row = 0, fp_row = 0;                        // longest product rows
-  bool has_fp = false;                               // F E products formed for this side
+  bool has_rf = false, has_fp = false;               // R F / F E products formed for this side
   static int ell_width(int row) { return (row + 3) / 4 * 4; }
   int rf_w() const { return ell_width(rf_row); }
   int fp_w() const { return ell_width(fp_row); }
