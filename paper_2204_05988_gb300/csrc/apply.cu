@@ -334,7 +334,7 @@ Status diag_block(Handle& h, const Plan& p, const Pool<T>& pool, int lx, int lv,
 }  // namespace
 
 template <typename T>
-Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s) {
+Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s, const ApplyHooks* hooks) {
   Pool<T> pool;
   Status st = ensure_pool<T>(h, p, pool);
   if (st.code) return st;
@@ -347,11 +347,18 @@ Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s) {
   for (int i = 0; i <= L; ++i) {
     const int lv = L - i;
     // S_{b,i} = U_i V_b^T + P1 Z_{b,i};  Y_i = sum_a tau_a X_a S_{b,i}
+    if (hooks && hooks->ready) SG_CU(cudaStreamWaitEvent(s, hooks->ready[i], 0));
     T* yi = y + h.off[i];
     st = diag_block<T>(h, p, pool, i, lv, u + h.off[i], yi, false, s,
                        [&](int c) { return i >= 1 ? (const T*)pool.ZA(c, i & 1) : (const T*)nullptr; });
     if (st.code) return st;
-    if (i == L) break;
+    if (i == L) {
+      if (hooks && hooks->done) {   // grid L gets no branch-B contribution
+        st = hooks->done(hooks->ctx, L);
+        if (st.code) return st;
+      }
+      break;
+    }
     // Z_{b,i+1} = S_{b,i} R2^T  (nx[i] x nv[lv-1]): S_{b,i} is already formed
     // for the final update, so one restriction carries every chain forward
     for (int c0 = 0; c0 < nA; c0 += G) {
@@ -437,12 +444,16 @@ Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s) {
     st = finals_on<T>(h, p, p.B, fs, [&](int c) { return (const T*)pool.ZB(c, i & 1); },
                       [&](const Term& tm) { return (const T*)V.vals<T>().ell_FP[tm.v][lv]; }, true, y + h.off[i], s);
     if (st.code) return st;
+    if (hooks && hooks->done) {
+      st = hooks->done(hooks->ctx, i);
+      if (st.code) return st;
+    }
   }
   return {};
 }
 
-template Status apply_plan<double>(Handle&, const Plan&, const double*, double*, cudaStream_t);
-template Status apply_plan<float>(Handle&, const Plan&, const float*, float*, cudaStream_t);
+template Status apply_plan<double>(Handle&, const Plan&, const double*, double*, cudaStream_t, const ApplyHooks*);
+template Status apply_plan<float>(Handle&, const Plan&, const float*, float*, cudaStream_t, const ApplyHooks*);
 
 // Diagonal blocks A_{l,l} on a list of grids (l1[g], l2[g]): the component
 // systems of the combination-technique preconditioner.  Per grid: one launch

@@ -452,6 +452,10 @@ void sgdg_destroy(void* hp) {
   cudaSetDevice(h->cfg.device);
   cudaDeviceSynchronize();
   solver_free(*h);
+  for (cudaEvent_t e : h->ev_in) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_out) if (e) cudaEventDestroy(e);
+  if (h->host_s) cudaStreamDestroy(h->host_s);
+  if (h->host_c) cudaStreamDestroy(h->host_c);
   {
     std::lock_guard<std::mutex> lk(registry_mutex());
     for (void* p : registry(h)) cudaFree(p);
@@ -520,9 +524,38 @@ sgdg_status sgdg_apply_mass(void* hp, const void* u, void* y, int prec, void* st
   return st.code ? fail(h, st) : SGDG_OK;
 }
 
+namespace {
+
+// The host-buffer apply is pipelined per grid: grid i's input is copied (and
+// rounded to FP32) on a copy stream while earlier grids compute, and Y_i is
+// converted and copied back as soon as the sweep has finished it.
+struct HostApply {
+  Handle* h = nullptr;
+  bool f32 = false;
+  double* y = nullptr;
+};
+
+Status host_apply_done(void* ctx, int i) {
+  HostApply& x = *(HostApply*)ctx;
+  Handle& h = *x.h;
+  const size_t off = (size_t)h.off[i], n = (size_t)(h.off[i + 1] - h.off[i]);
+  double* out64 = (double*)h.b64.cvt_out;
+  if (cudaEventRecord(h.ev_out[i], h.host_s) != cudaSuccess || cudaStreamWaitEvent(h.host_c, h.ev_out[i], 0) != cudaSuccess)
+    return {SGDG_ECUDA, "host apply: event"};
+  if (x.f32 && vec_convert<float, double>((const float*)h.b32.cvt_out + off, out64 + off, (long long)n, h.host_c) !=
+                   cudaSuccess)
+    return {SGDG_ECUDA, "host apply: conversion"};
+  if (cudaMemcpyAsync(x.y + off, out64 + off, 8 * n, cudaMemcpyDeviceToHost, h.host_c) != cudaSuccess)
+    return {SGDG_ECUDA, "host apply: device-to-host copy"};
+  return {};
+}
+
+}  // namespace
+
 sgdg_status sgdg_apply_operator_host(void* hp, const double* u, double* y, int prec) {
   if (!hp || !u || !y) return fail((Handle*)hp, {SGDG_EINVAL, "null argument"});
   Handle* h = (Handle*)hp;
+  if (prec != SGDG_FP64 && prec != SGDG_MIXED_FP32) return fail(h, {SGDG_EINVAL, "unknown precision"});
   Handle::Bufs& b = h->b64;
   size_t n = (size_t)h->n_coeffs;
   if (!b.cvt_in) {
@@ -533,22 +566,45 @@ sgdg_status sgdg_apply_operator_host(void* hp, const double* u, double* y, int p
     if (dev_alloc(*h, &h->b32.cvt_in, 4 * n) != cudaSuccess || dev_alloc(*h, &h->b32.cvt_out, 4 * n) != cudaSuccess)
       return fail(h, {SGDG_ENOMEM, "host-apply buffers"});
   }
-  cudaStream_t s = nullptr;
-  if (cudaMemcpyAsync(b.cvt_in, u, 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return fail(h, {SGDG_ECUDA, "host-to-device copy"});
-  Status st;
-  if (prec == SGDG_FP64) {
-    st = apply_plan<double>(*h, h->op, (const double*)b.cvt_in, (double*)b.cvt_out, s);
-  } else if (prec == SGDG_MIXED_FP32) {
-    vec_convert<double, float>((const double*)b.cvt_in, (float*)h->b32.cvt_in, n, s);
-    st = apply_plan<float>(*h, h->op, (const float*)h->b32.cvt_in, (float*)h->b32.cvt_out, s);
-    vec_convert<float, double>((const float*)h->b32.cvt_out, (double*)b.cvt_out, n, s);
-  } else {
-    st = {SGDG_EINVAL, "unknown precision"};
+  if (!h->host_s) {
+    if (cudaStreamCreateWithFlags(&h->host_s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->host_c, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(h, {SGDG_ECUDA, "host apply: streams"});
+    h->ev_in.assign(h->L + 1, nullptr);
+    h->ev_out.assign(h->L + 1, nullptr);
+    for (int i = 0; i <= h->L; ++i)
+      if (cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming) != cudaSuccess)
+        return fail(h, {SGDG_ECUDA, "host apply: events"});
   }
-  if (st.code) return fail(h, st);
-  if (cudaMemcpyAsync(y, b.cvt_out, 8 * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
+  const bool f32 = prec == SGDG_MIXED_FP32;
+  double* in64 = (double*)b.cvt_in;
+  for (int i = 0; i <= h->L; ++i) {
+    const size_t off = (size_t)h->off[i], m = (size_t)(h->off[i + 1] - h->off[i]);
+    if (cudaMemcpyAsync(in64 + off, u + off, 8 * m, cudaMemcpyHostToDevice, h->host_c) != cudaSuccess)
+      return fail(h, {SGDG_ECUDA, "host-to-device copy"});
+    if (f32 && vec_convert<double, float>(in64 + off, (float*)h->b32.cvt_in + off, (long long)m, h->host_c) !=
+                   cudaSuccess)
+      return fail(h, {SGDG_ECUDA, "host apply: conversion"});
+    if (cudaEventRecord(h->ev_in[i], h->host_c) != cudaSuccess) return fail(h, {SGDG_ECUDA, "host apply: event"});
+  }
+  HostApply ctx;
+  ctx.h = h;
+  ctx.f32 = f32;
+  ctx.y = y;
+  ApplyHooks hooks;
+  hooks.ready = h->ev_in.data();
+  hooks.done = host_apply_done;
+  hooks.ctx = &ctx;
+  Status st = f32 ? apply_plan<float>(*h, h->op, (const float*)h->b32.cvt_in, (float*)h->b32.cvt_out, h->host_s,
+                                      &hooks)
+                  : apply_plan<double>(*h, h->op, (const double*)b.cvt_in, (double*)b.cvt_out, h->host_s, &hooks);
+  if (st.code) {
+    cudaStreamSynchronize(h->host_c);
+    cudaStreamSynchronize(h->host_s);
+    return fail(h, st);
+  }
+  if (cudaStreamSynchronize(h->host_s) != cudaSuccess || cudaStreamSynchronize(h->host_c) != cudaSuccess)
     return fail(h, {SGDG_ECUDA, "device-to-host copy"});
   return SGDG_OK;
 }

@@ -88,6 +88,9 @@ struct Handle {
     void* cvt_in = nullptr; void* cvt_out = nullptr;
     void* pool = nullptr; long long pool_elems = 0;   // sweep chain states
   } b64, b32;
+  // host-buffer apply: compute and copy streams, per-grid events
+  cudaStream_t host_s = nullptr, host_c = nullptr;
+  std::vector<cudaEvent_t> ev_in, ev_out;
   long long tmp_elems = 0;
   // host copies of the u0 load vectors per level (for set_initial)
   std::vector<std::vector<std::vector<double>>> u0x, u0v;   // [product][level][n]
@@ -159,8 +162,17 @@ Status upload_factor_products(Handle& h, const Hierarchy& hi, SideDev& sd, int f
 Status upload_ell_vals(Handle& h, const std::vector<int>& rowptr, const std::vector<double>& val, int w,
                        double** d64, float** d32);
 
+// Optional per-grid synchronisation of an apply: before grid i's input U_i
+// is first read the stream waits for ready[i]; once Y_i is final, done(i)
+// is called (it may enqueue work that reads Y_i on another stream).
+struct ApplyHooks {
+  const cudaEvent_t* ready = nullptr;
+  Status (*done)(void* ctx, int grid) = nullptr;
+  void* ctx = nullptr;
+};
+
 template <typename T>
-Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s);
+Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s, const ApplyHooks* hooks = nullptr);
 template <typename T>
 Status apply_diag_grids(Handle& h, int ng, const int* l1, const int* l2, const T* const* u, T* const* y,
                         cudaStream_t s);
