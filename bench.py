@@ -238,15 +238,15 @@ def main():
     for _ in range(args.warmup):
         s.apply_operator(u32, y32, P.SGDG_MIXED_FP32, stream)
     barrier()
-    l0 = s.launch_count()
+    # clocks are sampled over both timed regions (FP32, then FP64), ~1.5 s of load
     with Clocks(local) as clk:
+        l0 = s.launch_count()
         ms32 = timed(lambda: s.apply_operator(u32, y32, P.SGDG_MIXED_FP32, stream), args.steps, 0)
-    launches = (s.launch_count() - l0) // 1
+        launches = s.launch_count() - l0
+        # ---- FP64 apply
+        ms64 = timed(lambda: s.apply_operator(u64, y64, P.SGDG_FP64, stream), max(2, args.steps // 2), 1)
     clocks = clk.summary()
     value = world * n / (ms32 * 1e-3) / 1e9
-
-    # ---- FP64 apply
-    ms64 = timed(lambda: s.apply_operator(u64, y64, P.SGDG_FP64, stream), max(2, args.steps // 2), 1)
 
     # ---- per-kernel roofline (one profiled apply per precision)
     peak, peak_kind = _peaks()
