@@ -206,6 +206,10 @@ def main():
     s = P.Solver(prob, device=local)
     setup_s = time.perf_counter() - t0
     n = s.n_coeffs
+    # (r+1) dim V_L, the unique count of the paper's convention: the grids
+    # (l, L-l) overlap in the grids (l, L-1-l) of the nested spaces
+    sh = s.shapes
+    unique = 2 * (sum(a * b for a, b in sh) - sum(sh[l][0] * sh[l + 1][1] for l in range(len(sh) - 1)))
     u64 = torch.tensor(W.uniform_vector(n, seed=1 + rank), dtype=torch.float64, device="cuda")
     u32 = u64.float()
     y32 = torch.empty_like(u32)
@@ -398,7 +402,9 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"transport_2d d=2 L={args.L} sigma=0.1 operator apply A^(delta) u",
-                           "dof_per_step": n, "terms": s.info.n_terms, "x_factors": s.info.n_x_factors,
+                           "dof_per_step": n, "unique_dof_per_step": unique,
+                           "unique_GDoFps": unique / (ms32 * 1e-3) / 1e9 * world,
+                           "terms": s.info.n_terms, "x_factors": s.info.n_x_factors,
                            "v_factors": s.info.n_v_factors, "l2": "inputs larger than L2 (493 MB f32)",
                            "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
                            "autotune_s": round(tune_s, 2)},
