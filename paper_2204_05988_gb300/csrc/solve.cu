@@ -291,23 +291,56 @@ __global__ void k_gcheb_init(const __grid_constant__ GVec<T> p, int dim, double 
   }
 }
 
-// Chebyshev step: r -= Md; d = c1 d + c2 D^{-1} r; x += d  (a = Md, b = r, c = d, d = x)
+// Fused Chebyshev step on every grid, the mass apply included:
+//   r -= M d_old;  d_new = c1 d_old + c2 D^{-1} r;  x += d_new
+// with M along dim 1 (rows k1) or dim 2 (rows k2) from its ELL rows (width W,
+// zero padding); d ping-pongs between two buffers because neighbouring
+// elements still read d_old.
 template <typename T>
-__global__ void k_gcheb_step(const __grid_constant__ GVec<T> p, int dim, double c1, double c2) {
+struct GCheb {
+  int ng = 0;
+  int n1[kMaxGrids], n2[kMaxGrids];
+  const int* col[kMaxGrids];
+  const T* val[kMaxGrids];
+  const T* dinv[kMaxGrids];
+  const T* dold[kMaxGrids];
+  T* dnew[kMaxGrids];
+  T* r[kMaxGrids];
+  T* x[kMaxGrids];
+};
+
+template <typename T, bool DIM2, int W>
+__global__ void __launch_bounds__(kThreads) k_gcheb_fused(const __grid_constant__ GCheb<T> p, double c1, double c2) {
   using T2 = typename V2<T>::type;
   const int g = blockIdx.y;
-  const unsigned npts = (unsigned)(p.n[g] / 2);
-  const unsigned n2 = (unsigned)p.n2[g];
-  const T2* Md = reinterpret_cast<const T2*>(p.a[g]);
-  T2* r = reinterpret_cast<T2*>(p.b[g]);
-  T2* d = reinterpret_cast<T2*>(p.c[g]);
-  T2* x = reinterpret_cast<T2*>(p.d[g]);
+  const unsigned n1 = (unsigned)p.n1[g], n2 = (unsigned)p.n2[g];
+  const unsigned npts = n1 * n2;
+  const T2* dold = reinterpret_cast<const T2*>(p.dold[g]);
+  T2* dnew = reinterpret_cast<T2*>(p.dnew[g]);
+  T2* r = reinterpret_cast<T2*>(p.r[g]);
+  T2* x = reinterpret_cast<T2*>(p.x[g]);
   const T a1 = (T)c1, a2 = (T)c2;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += gridDim.x * blockDim.x) {
     const unsigned k1 = i / n2, k2 = i - k1 * n2;
-    const T di = a2 * p.dinv[g][dim == 1 ? k1 : k2];
-    const T2 m = Md[i];
-    T2 rr = r[i], dd = d[i], xx = x[i];
+    const unsigned row = DIM2 ? k2 : k1;
+    const int4* cq = reinterpret_cast<const int4*>(p.col[g] + (size_t)row * W);
+    const T* vq = p.val[g] + (size_t)row * W;
+    T2 m;
+    m.x = m.y = 0;
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) {
+      const int4 c = __ldg(cq + q);
+      const int cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const T v = __ldg(vq + 4 * q + e);
+        const T2 dv = DIM2 ? dold[k1 * n2 + (unsigned)cc[e]] : dold[(unsigned)cc[e] * n2 + k2];
+        m.x += v * dv.x;
+        m.y += v * dv.y;
+      }
+    }
+    const T di = a2 * p.dinv[g][row];
+    T2 rr = r[i], dd = dold[i], xx = x[i];
     rr.x -= m.x;
     rr.y -= m.y;
     dd.x = a1 * dd.x + di * rr.x;
@@ -315,7 +348,7 @@ __global__ void k_gcheb_step(const __grid_constant__ GVec<T> p, int dim, double 
     xx.x += dd.x;
     xx.y += dd.y;
     r[i] = rr;
-    d[i] = dd;
+    dnew[i] = dd;
     x[i] = xx;
   }
 }
@@ -451,18 +484,13 @@ Status precond_group(Handle& h, const Active& act, const std::vector<const T*>& 
   }
   k_gtime2x2<T><<<ggrid(t.n, ng), kThreads, 0, s>>>(t, Minv);
   SG_CU(cudaGetLastError());
-  // Chebyshev-Jacobi along dim 1 (f = cx -> x = t0), then along dim 2 (f = t0 -> x = out)
+  // Chebyshev-Jacobi along dim 1 (f = cx -> x = t1), then along dim 2 (f = t1 -> x = out)
   const int K = std::max(1, h.cfg.cheb_steps);
   const double a = 0.5, b = (h.d == 1) ? 1.5 : 2.0;
   const double theta = 0.5 * (a + b), del = 0.5 * (b - a), sigma1 = theta / del;
   for (int dim = 1; dim <= 2; ++dim) {
     GVec<T> c;
     c.ng = ng;
-    SpmmLaunch<T> A;
-    A.ngrids = ng;
-    A.nterms = 1;
-    A.identity = 1;
-    A.accumulate = 0;
     for (int q = 0; q < ng; ++q) {
       const int g = act.g[q];
       const int l1 = ws.cl1[g], l2 = ws.cl2[g];
@@ -475,26 +503,44 @@ Status precond_group(Handle& h, const Active& act, const std::vector<const T*>& 
       c.b[q] = B.cr[g];                            // r
       c.c[q] = B.cd[g];                            // d
       c.d[q] = dim == 1 ? B.t1[g] : out[q];        // x
-      SpmmGrid<T>& G = A.g[q];
-      G.in = B.cd[g];
-      G.in2 = nullptr;
-      G.out = B.cm[g];
-      G.n1_in = G.n1_out = h.X.n[l1];
-      G.n2_in = G.n2_out = h.V.n[l2];
-      G.rowptr = sd.rowptr[lev];
-      G.col = sd.col[lev];
-      G.val[0] = sd.vals<T>().fac[sd.mass][lev];
     }
     k_gcheb_init<T><<<ggrid(c.n, ng), kThreads, 0, s>>>(c, dim, 1.0 / theta);
     SG_CU(cudaGetLastError());
     double rho = 1.0 / sigma1;
-    GVec<T> st = c;
-    for (int q = 0; q < ng; ++q) st.a[q] = B.cm[act.g[q]];   // Md
+    // steps: d ping-pongs between cd and cm
+    GCheb<T> fz;
+    fz.ng = ng;
+    const SideDev& sdd = dim == 1 ? h.X : h.V;
+    const int W = sdd.ell_w();
+    for (int q = 0; q < ng; ++q) {
+      const int g = act.g[q];
+      const int lev = dim == 1 ? ws.cl1[g] : ws.cl2[g];
+      fz.n1[q] = h.X.n[ws.cl1[g]];
+      fz.n2[q] = h.V.n[ws.cl2[g]];
+      fz.col[q] = sdd.ell_col[lev];
+      fz.val[q] = sdd.vals<T>().ell_fac[sdd.mass][lev];
+      fz.dinv[q] = sdd.vals<T>().dinv[lev];
+      fz.dold[q] = B.cd[g];
+      fz.dnew[q] = B.cm[g];
+      fz.r[q] = B.cr[g];
+      fz.x[q] = c.d[q];
+    }
     for (int k = 1; k < K; ++k) {
-      if (dim == 1) SG_CU(launch_left(A, s)); else SG_CU(launch_right(A, s));
       const double rhon = 1.0 / (2.0 * sigma1 - rho);
-      k_gcheb_step<T><<<ggrid(st.n, ng), kThreads, 0, s>>>(st, dim, rhon * rho, 2.0 * rhon / del);
+      const dim3 gg = ggrid(c.n, ng);
+      if (dim == 1) {
+        if (W == 4) k_gcheb_fused<T, false, 4><<<gg, kThreads, 0, s>>>(fz, rhon * rho, 2.0 * rhon / del);
+        else k_gcheb_fused<T, false, 8><<<gg, kThreads, 0, s>>>(fz, rhon * rho, 2.0 * rhon / del);
+      } else {
+        if (W == 4) k_gcheb_fused<T, true, 4><<<gg, kThreads, 0, s>>>(fz, rhon * rho, 2.0 * rhon / del);
+        else k_gcheb_fused<T, true, 8><<<gg, kThreads, 0, s>>>(fz, rhon * rho, 2.0 * rhon / del);
+      }
       SG_CU(cudaGetLastError());
+      for (int q = 0; q < ng; ++q) {
+        T* t = const_cast<T*>(fz.dold[q]);
+        fz.dold[q] = fz.dnew[q];
+        fz.dnew[q] = t;
+      }
       rho = rhon;
     }
   }
