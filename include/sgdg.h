@@ -55,9 +55,16 @@ typedef enum {
 
 typedef enum {
   SGDG_FP64 = 0,        /* every apply, transfer and Krylov vector in FP64 */
-  SGDG_MIXED_FP32 = 1   /* FP32 apply / transfers / component solves, FP64
+  SGDG_MIXED_FP32 = 1,  /* FP32 apply / transfers / component solves, FP64
                            Krylov scalars and FP64 outer residual
                            (iterative refinement) */
+  SGDG_BF16_STORE = 2   /* applies only (operator, mass, diagonal blocks,
+                           autotune, batch): every grid array - input,
+                           chain states, output - stored in bfloat16
+                           (round to nearest even), FP32 matrix values and
+                           FP32 arithmetic.  Half the bytes per element of
+                           FP32; about 2^-8 relative rounding per stored
+                           intermediate.  Not a solver precision. */
 } sgdg_precision;
 
 /* A coarse simplicial mesh of an axis-aligned box (one of Omega_x, Omega_v).
@@ -178,8 +185,9 @@ sgdg_status sgdg_grid_shape(const void* h, int l, int* n1, int* n2, long long* o
 /* y = A^(delta) u: the strip operator of Eq. 5 on the sparse grid,
  * [A u]_l = sum_l' A_{l,l'} u_l' (Sect. 4.2), evaluated by a linear-cost
  * sweep over the grids.  u, y: device arrays of n_coeffs elements of type
- * double (SGDG_FP64) or float (SGDG_MIXED_FP32); y is overwritten; u and y
- * must not overlap. */
+ * double (SGDG_FP64), float (SGDG_MIXED_FP32) or bfloat16 (SGDG_BF16_STORE);
+ * y is overwritten; u and y must not overlap.  Any other precision:
+ * SGDG_EINVAL. */
 sgdg_status sgdg_apply_operator(void* h, const void* u, void* y, int precision, void* stream);
 /* Same operator with host arrays (double): copies u to the device, applies
  * in the given precision, copies y back.  Synchronous. */
@@ -258,7 +266,7 @@ sgdg_status sgdg_finest_x(const void* h, int* n_vertices, int* n_cells);
  * (lexicographic order), host arrays of n_vertices doubles. */
 sgdg_status sgdg_get_density_potential(const void* h, double* rho, double* phi);
 
-/* Learned warm start (no counterpart in the paper; the task's extension).
+/* Learned warm start (no counterpart in the paper: an extension of the solver).
  *
  * sgdg_coarse_values: the values of a sparse-grid function at the nodes of
  * the full grid (lx, lv): u is a strip vector (R = 2) or a spatial vector

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libsgdg.so")
 
 SGDG_FP64 = 0
 SGDG_MIXED_FP32 = 1
+SGDG_BF16_STORE = 2   # applies only: grid arrays in bfloat16, FP32 arithmetic
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENAN", 6: "ETIMEOUT", 7: "EIO"}
 
 FN = C.CFUNCTYPE(None, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)

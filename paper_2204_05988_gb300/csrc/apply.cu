@@ -51,13 +51,14 @@ template <typename T>
 Handle::Bufs& bufs(Handle& h);
 template <> Handle::Bufs& bufs<double>(Handle& h) { return h.b64; }
 template <> Handle::Bufs& bufs<float>(Handle& h) { return h.b32; }
+template <> Handle::Bufs& bufs<Bf16>(Handle& h) { return h.b16; }
 
 template <typename T>
 Status ensure_bufs(Handle& h) {
   Handle::Bufs& b = bufs<T>(h);
   if (b.S) return {};
-  size_t full = sizeof(T) * (size_t)h.n_coeffs;
-  size_t tmp = sizeof(T) * (size_t)h.tmp_elems;
+  size_t full = sizeof(Store<T>) * (size_t)h.n_coeffs;
+  size_t tmp = sizeof(Store<T>) * (size_t)h.tmp_elems;
   if (dev_alloc(h, &b.S, full) != cudaSuccess || dev_alloc(h, &b.Z, full) != cudaSuccess ||
       dev_alloc(h, &b.TP, full) != cudaSuccess || dev_alloc(h, &b.tmp, tmp) != cudaSuccess ||
       dev_alloc(h, &b.W, full) != cudaSuccess)
@@ -89,13 +90,13 @@ inline PoolShape pool_shape(const Handle& h) {
 
 template <typename T>
 struct Pool {
-  T* base = nullptr;
+  Store<T>* base = nullptr;
   PoolShape ps;
   size_t nA = 0, nB = 0;
-  T* W(int b) const { return base + (size_t)b * ps.mg; }
-  T* ZA(int b, int par) const { return base + nA * ps.mg + (size_t)(2 * b + par) * ps.mz; }
-  T* ZB(int c, int par) const { return base + nA * ps.mg + 2 * nA * ps.mz + (size_t)(2 * c + par) * ps.mz; }
-  T* Q(int g) const { return base + nA * ps.mg + 2 * (nA + nB) * ps.mz + (size_t)g * ps.mq; }
+  Store<T>* W(int b) const { return base + (size_t)b * ps.mg; }
+  Store<T>* ZA(int b, int par) const { return base + nA * ps.mg + (size_t)(2 * b + par) * ps.mz; }
+  Store<T>* ZB(int c, int par) const { return base + nA * ps.mg + 2 * nA * ps.mz + (size_t)(2 * c + par) * ps.mz; }
+  Store<T>* Q(int g) const { return base + nA * ps.mg + 2 * (nA + nB) * ps.mz + (size_t)g * ps.mq; }
 };
 
 template <typename T>
@@ -107,11 +108,11 @@ Status ensure_pool(Handle& h, const Plan& p, Pool<T>& pool) {
   const long long need = std::max(pool.ps.elems(h.op), pool.ps.elems(p));
   Handle::Bufs& b = bufs<T>(h);
   if (!b.pool) {
-    if (dev_alloc(h, &b.pool, sizeof(T) * (size_t)need) != cudaSuccess) return {SGDG_ENOMEM, "sweep chain pool"};
+    if (dev_alloc(h, &b.pool, sizeof(Store<T>) * (size_t)need) != cudaSuccess) return {SGDG_ENOMEM, "sweep chain pool"};
     b.pool_elems = need;
   }
   if (b.pool_elems < pool.ps.elems(p)) return {SGDG_EINVAL, "sweep chain pool too small for this plan"};
-  pool.base = (T*)b.pool;
+  pool.base = (Store<T>*)b.pool;
   return {};
 }
 
@@ -172,13 +173,13 @@ struct ProfScope {
 
 template <typename T>
 double grid_bytes(long long n1, long long n2) {
-  return 2.0 * sizeof(T) * (double)n1 * (double)n2;
+  return 2.0 * sizeof(Store<T>) * (double)n1 * (double)n2;
 }
 
 template <typename T>
 Status run_restrict(Handle& h, RestrictArgs<T>& a, bool dim2, cudaStream_t s, double mat_bytes) {
   const int kind = dim2 ? KIND_XFER_RIGHT : KIND_XFER_LEFT;
-  const long long site = site_key(kind, a.n1, a.n2, a.nchains, sizeof(T));
+  const long long site = site_key(kind, a.n1, a.n2, a.nchains, sizeof(Store<T>));
   const Shape sh = pick_shape<T>(h, site, !dim2, a.n1, a.n2);
   a.ch = sh.ch;
   a.tiled = sh.tiled;
@@ -192,7 +193,7 @@ Status run_restrict(Handle& h, RestrictArgs<T>& a, bool dim2, cudaStream_t s, do
 // in_bytes: the matrices, U and the Q inputs the launch reads
 template <typename T>
 Status run_chain(Handle& h, ChainArgs<T>& a, bool mode_a, int kind, cudaStream_t s, double in_bytes) {
-  const long long site = site_key(kind, a.n1, a.n2, a.nchains, sizeof(T));
+  const long long site = site_key(kind, a.n1, a.n2, a.nchains, sizeof(Store<T>));
   const Shape sh = pick_shape<T>(h, site, !mode_a, a.n1, a.n2);
   a.ch = sh.ch;
   a.tiled = sh.tiled;
@@ -207,7 +208,7 @@ Status run_chain(Handle& h, ChainArgs<T>& a, bool mode_a, int kind, cudaStream_t
 // mat_bytes: pattern and value rows the launch reads; in_bytes: one input
 template <typename T>
 Status run_final(Handle& h, FinalArgs<T>& f, bool left, int kind, cudaStream_t s, double mat_bytes, double in_bytes) {
-  const long long site = site_key(kind, f.n1, f.n2, f.nin, sizeof(T));
+  const long long site = site_key(kind, f.n1, f.n2, f.nin, sizeof(Store<T>));
   const Shape sh = pick_shape<T>(h, site, left, f.n1, f.n2);
   f.ch = sh.ch;
   f.tiled = sh.tiled;
@@ -223,7 +224,7 @@ Status run_final(Handle& h, FinalArgs<T>& f, bool left, int kind, cudaStream_t s
 // ELL bytes of `rows` rows of width w: the columns plus nvals value arrays
 template <typename T>
 double ell_bytes(long long rows, int w, int nvals) {
-  return (double)rows * w * (4.0 + (double)nvals * sizeof(T));
+  return (double)rows * w * (4.0 + (double)nvals * sizeof(Comp<T>));
 }
 
 // One final launch family: y (+)= sum over the chains' terms of tau_a F_a in_c
@@ -240,7 +241,7 @@ struct FinalSpec {
 
 template <typename T, typename InOf, typename ValOf>
 Status finals_on(Handle& h, const Plan& p, const std::vector<Chain>& chains, const FinalSpec& fs, InOf in_of,
-                 ValOf val_of, bool accumulate_first, T* ygrid, cudaStream_t s) {
+                 ValOf val_of, bool accumulate_first, Store<T>* ygrid, cudaStream_t s) {
   FinalArgs<T> f;
   f.n1 = fs.n1;
   f.n2 = fs.n2;
@@ -275,7 +276,7 @@ Status finals_on(Handle& h, const Plan& p, const std::vector<Chain>& chains, con
       const Term& tm = p.terms[t];
       f.val[f.nterms] = val_of(tm);
       for (int a = 0; a < 2; ++a)
-        for (int q = 0; q < 2; ++q) f.tau[f.nterms][a * 2 + q] = (T)tm.tau[a][q];
+        for (int q = 0; q < 2; ++q) f.tau[f.nterms][a * 2 + q] = (Comp<T>)tm.tau[a][q];
       f.nterms++;
     }
   }
@@ -286,7 +287,7 @@ Status finals_on(Handle& h, const Plan& p, const std::vector<Chain>& chains, con
 //   S_b = u V_b^T (+ P1 Z_b when zin is given: the chain states of branch A)
 //   for the chains b (by v factor), then y (+)= sum tau_a X_a S_b
 template <typename T, typename ZOf>
-Status diag_block(Handle& h, const Plan& p, const Pool<T>& pool, int lx, int lv, const T* u, T* y,
+Status diag_block(Handle& h, const Plan& p, const Pool<T>& pool, int lx, int lv, const Store<T>* u, Store<T>* y,
                   bool accumulate, cudaStream_t s, ZOf zin) {
   const int n1 = h.X.n[lx], n2 = h.V.n[lv];
   const int nc = (int)p.A.size();
@@ -304,14 +305,14 @@ Status diag_block(Handle& h, const Plan& p, const Pool<T>& pool, int lx, int lv,
     a.U = u;
     a.f_col = h.V.ell_col[lv];
     for (int c = 0; c < a.nchains; ++c) {
-      a.f_val[c] = h.V.vals<T>().ell_fac[p.A[c0 + c].first][lv];
+      a.f_val[c] = h.V.vals<Comp<T>>().ell_fac[p.A[c0 + c].first][lv];
       a.out[c] = pool.W(c0 + c);
       a.Z[c] = zin(c0 + c);
     }
     double in = g + ell_bytes<T>(n2, h.V.ell_w(), a.nchains);
     if (prev) {
       a.p_col = h.X.E_ell_col[lx - 1];
-      a.p_val = h.X.vals<T>().ell_E[lx - 1];
+      a.p_val = h.X.vals<Comp<T>>().ell_E[lx - 1];
       in += a.nchains * grid_bytes<T>(h.X.n[lx - 1], n2) + ell_bytes<T>(n1, kEllE, 1);
     }
     Status st = run_chain(h, a, true, KIND_S_CHAIN, s, in);
@@ -327,14 +328,14 @@ Status diag_block(Handle& h, const Plan& p, const Pool<T>& pool, int lx, int lv,
   fs.w = h.X.ell_w();
   fs.mat_rows = n1;
   fs.in_bytes = g;
-  return finals_on<T>(h, p, p.A, fs, [&](int c) { return (const T*)pool.W(c); },
-                      [&](const Term& tm) { return (const T*)h.X.vals<T>().ell_fac[tm.x][lx]; }, accumulate, y, s);
+  return finals_on<T>(h, p, p.A, fs, [&](int c) { return (const Store<T>*)pool.W(c); },
+                      [&](const Term& tm) { return (const Comp<T>*)h.X.vals<Comp<T>>().ell_fac[tm.x][lx]; }, accumulate, y, s);
 }
 
 }  // namespace
 
 template <typename T>
-Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s, const ApplyHooks* hooks) {
+Status apply_plan(Handle& h, const Plan& p, const Store<T>* u, Store<T>* y, cudaStream_t s, const ApplyHooks* hooks) {
   Pool<T> pool;
   Status st = ensure_pool<T>(h, p, pool);
   if (st.code) return st;
@@ -348,9 +349,9 @@ Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s, co
     const int lv = L - i;
     // S_{b,i} = U_i V_b^T + P1 Z_{b,i};  Y_i = sum_a tau_a X_a S_{b,i}
     if (hooks && hooks->ready) SG_CU(cudaStreamWaitEvent(s, hooks->ready[i], 0));
-    T* yi = y + h.off[i];
+    Store<T>* yi = y + h.off[i];
     st = diag_block<T>(h, p, pool, i, lv, u + h.off[i], yi, false, s,
-                       [&](int c) { return i >= 1 ? (const T*)pool.ZA(c, i & 1) : (const T*)nullptr; });
+                       [&](int c) { return i >= 1 ? (const Store<T>*)pool.ZA(c, i & 1) : (const Store<T>*)nullptr; });
     if (st.code) return st;
     if (i == L) {
       if (hooks && hooks->done) {   // grid L gets no branch-B contribution
@@ -371,7 +372,7 @@ Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s, co
       r.nchains = nc;
       r.row = V.row_regs();
       r.col = V.R_ell_col[lv - 1];
-      r.val = V.vals<T>().ell_R[lv - 1];
+      r.val = V.vals<Comp<T>>().ell_R[lv - 1];
       for (int g = 0; g < nc; ++g) {
         r.in[g] = pool.W(c0 + g);
         r.out[g] = pool.ZA(c0 + g, (i + 1) & 1);
@@ -396,7 +397,7 @@ Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s, co
         r.nchains = nc;
         r.row = X.row_regs();
         r.col = X.R_ell_col[i];
-        r.val = X.vals<T>().ell_R[i];
+        r.val = X.vals<Comp<T>>().ell_R[i];
         for (int g = 0; g < nc; ++g) {
           r.in[g] = pool.ZB(c0 + g, (i + 1) & 1);
           r.out[g] = pool.Q(g);
@@ -417,13 +418,13 @@ Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s, co
       a.U = u + h.off[i + 1];
       a.f_col = X.RF_ell_col[i];
       for (int g = 0; g < nc; ++g) {
-        a.f_val[g] = X.vals<T>().ell_RF[p.B[c0 + g].first][i];
+        a.f_val[g] = X.vals<Comp<T>>().ell_RF[p.B[c0 + g].first][i];
         a.out[g] = pool.ZB(c0 + g, i & 1);
         a.Z[g] = prev ? pool.Q(g) : nullptr;
       }
       if (prev) {
         a.p_col = V.E_ell_col[lv - 2];
-        a.p_val = V.vals<T>().ell_E[lv - 2];
+        a.p_val = V.vals<Comp<T>>().ell_E[lv - 2];
       }
       st = run_chain(h, a, false, KIND_CHAIN_B, s,
                      qbytes + grid_bytes<T>(h.n1[i + 1], h.n2[i + 1]) + ell_bytes<T>(X.n[i], X.rf_w(), nc));
@@ -441,8 +442,8 @@ Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s, co
     fs.w = V.fp_w();
     fs.mat_rows = V.n[lv];
     fs.in_bytes = grid_bytes<T>(X.n[i], V.n[lv - 1]);
-    st = finals_on<T>(h, p, p.B, fs, [&](int c) { return (const T*)pool.ZB(c, i & 1); },
-                      [&](const Term& tm) { return (const T*)V.vals<T>().ell_FP[tm.v][lv]; }, true, y + h.off[i], s);
+    st = finals_on<T>(h, p, p.B, fs, [&](int c) { return (const Store<T>*)pool.ZB(c, i & 1); },
+                      [&](const Term& tm) { return (const Comp<T>*)V.vals<Comp<T>>().ell_FP[tm.v][lv]; }, true, y + h.off[i], s);
     if (st.code) return st;
     if (hooks && hooks->done) {
       st = hooks->done(hooks->ctx, i);
@@ -454,19 +455,21 @@ Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s, co
 
 template Status apply_plan<double>(Handle&, const Plan&, const double*, double*, cudaStream_t, const ApplyHooks*);
 template Status apply_plan<float>(Handle&, const Plan&, const float*, float*, cudaStream_t, const ApplyHooks*);
+template Status apply_plan<Bf16>(Handle&, const Plan&, const __nv_bfloat16*, __nv_bfloat16*, cudaStream_t,
+                                 const ApplyHooks*);
 
 // Diagonal blocks A_{l,l} on a list of grids (l1[g], l2[g]): the component
 // systems of the combination-technique preconditioner.  Per grid: one launch
 // forms W_b = u V_b^T for every distinct v factor (the chain-step kernel
 // without a transfer), then fused final launches fold all terms into y.
 template <typename T>
-Status apply_diag_grids(Handle& h, int ng, const int* l1, const int* l2, const T* const* u, T* const* y,
-                        cudaStream_t s) {
+Status apply_diag_grids(Handle& h, int ng, const int* l1, const int* l2, const Store<T>* const* u,
+                        Store<T>* const* y, cudaStream_t s) {
   Pool<T> pool;
   Status st = ensure_pool<T>(h, h.op, pool);
   if (st.code) return st;
   for (int g = 0; g < ng; ++g) {
-    st = diag_block<T>(h, h.op, pool, l1[g], l2[g], u[g], y[g], false, s, [](int) { return (const T*)nullptr; });
+    st = diag_block<T>(h, h.op, pool, l1[g], l2[g], u[g], y[g], false, s, [](int) { return (const Store<T>*)nullptr; });
     if (st.code) return st;
   }
   return {};
@@ -476,6 +479,8 @@ template Status apply_diag_grids<double>(Handle&, int, const int*, const int*, c
                                          double* const*, cudaStream_t);
 template Status apply_diag_grids<float>(Handle&, int, const int*, const int*, const float* const*, float* const*,
                                         cudaStream_t);
+template Status apply_diag_grids<Bf16>(Handle&, int, const int*, const int*, const __nv_bfloat16* const*,
+                                       __nv_bfloat16* const*, cudaStream_t);
 
 // Values of a spatial sparse-grid function at the nodes of every grid:
 //   out_i = sum_{j<=i} P1 I2 u_j + sum_{j>i} I1 P2 u_j  (P: prolongation, I: injection)
@@ -512,7 +517,7 @@ Status nodal_eval(Handle& h, const double* u, double* out, cudaStream_t s) {
 }
 
 template <typename T>
-Status autotune(Handle& h, const T* u, T* y, cudaStream_t s) {
+Status autotune(Handle& h, const Store<T>* u, Store<T>* y, cudaStream_t s) {
   // rows per thread x block order x paired outputs, encoded as ch | tiled << 4 | pair << 5
   std::vector<int> cand;
   for (int pair = 0; pair < 2; ++pair)
@@ -551,5 +556,6 @@ Status autotune(Handle& h, const T* u, T* y, cudaStream_t s) {
 
 template Status autotune<double>(Handle&, const double*, double*, cudaStream_t);
 template Status autotune<float>(Handle&, const float*, float*, cudaStream_t);
+template Status autotune<Bf16>(Handle&, const __nv_bfloat16*, __nv_bfloat16*, cudaStream_t);
 
 }  // namespace sgdg

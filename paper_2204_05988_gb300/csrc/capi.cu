@@ -245,6 +245,8 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   if (2 * cfg.level_L + 2 > kMaxGrids) return {SGDG_EINVAL, "too many grids"};
   if (cfg.time_degree != 1) return {SGDG_EINVAL, "only time_degree 1 is supported"};
   if (!(cfg.dt > 0.0) || !(cfg.delta >= 0.0)) return {SGDG_EINVAL, "dt must be > 0 and delta >= 0"};
+  if (cfg.precision == SGDG_BF16_STORE)
+    return {SGDG_EINVAL, "BF16 storage is an apply precision, not a solver precision"};
   if (cfg.precision != SGDG_FP64 && cfg.precision != SGDG_MIXED_FP32) return {SGDG_EINVAL, "unknown precision"};
   if (cfg.restart < 1 || cfg.restart > 63 || cfg.inner_its < 1 || cfg.inner_its > 63)
     return {SGDG_EINVAL, "restart and inner_its must be in 1..63"};
@@ -509,6 +511,7 @@ sgdg_status sgdg_apply_operator(void* hp, const void* u, void* y, int prec, void
   Status st;
   if (prec == SGDG_FP64) st = apply_plan<double>(*h, h->op, (const double*)u, (double*)y, s);
   else if (prec == SGDG_MIXED_FP32) st = apply_plan<float>(*h, h->op, (const float*)u, (float*)y, s);
+  else if (prec == SGDG_BF16_STORE) st = apply_plan<Bf16>(*h, h->op, (const __nv_bfloat16*)u, (__nv_bfloat16*)y, s);
   else st = {SGDG_EINVAL, "unknown precision"};
   return st.code ? fail(h, st) : SGDG_OK;
 }
@@ -520,6 +523,8 @@ sgdg_status sgdg_apply_mass(void* hp, const void* u, void* y, int prec, void* st
   Status st;
   if (prec == SGDG_FP64) st = apply_plan<double>(*h, h->mass, (const double*)u, (double*)y, s);
   else if (prec == SGDG_MIXED_FP32) st = apply_plan<float>(*h, h->mass, (const float*)u, (float*)y, s);
+  else if (prec == SGDG_BF16_STORE)
+    st = apply_plan<Bf16>(*h, h->mass, (const __nv_bfloat16*)u, (__nv_bfloat16*)y, s);
   else st = {SGDG_EINVAL, "unknown precision"};
   return st.code ? fail(h, st) : SGDG_OK;
 }
@@ -527,11 +532,12 @@ sgdg_status sgdg_apply_mass(void* hp, const void* u, void* y, int prec, void* st
 namespace {
 
 // The host-buffer apply is pipelined per grid: grid i's input is copied (and
-// rounded to FP32) on a copy stream while earlier grids compute, and Y_i is
-// converted and copied back as soon as the sweep has finished it.
+// rounded to the precision's storage type) on a copy stream while earlier
+// grids compute, and Y_i is converted and copied back as soon as the sweep
+// has finished it.
 struct HostApply {
   Handle* h = nullptr;
-  bool f32 = false;
+  int prec = SGDG_FP64;
   double* y = nullptr;
 };
 
@@ -542,9 +548,13 @@ Status host_apply_done(void* ctx, int i) {
   double* out64 = (double*)h.b64.cvt_out;
   if (cudaEventRecord(h.ev_out[i], h.host_s) != cudaSuccess || cudaStreamWaitEvent(h.host_c, h.ev_out[i], 0) != cudaSuccess)
     return {SGDG_ECUDA, "host apply: event"};
-  if (x.f32 && vec_convert<float, double>((const float*)h.b32.cvt_out + off, out64 + off, (long long)n, h.host_c) !=
-                   cudaSuccess)
-    return {SGDG_ECUDA, "host apply: conversion"};
+  cudaError_t e = cudaSuccess;
+  if (x.prec == SGDG_MIXED_FP32)
+    e = vec_convert<float, double>((const float*)h.b32.cvt_out + off, out64 + off, (long long)n, h.host_c);
+  else if (x.prec == SGDG_BF16_STORE)
+    e = vec_convert<__nv_bfloat16, double>((const __nv_bfloat16*)h.b16.cvt_out + off, out64 + off, (long long)n,
+                                           h.host_c);
+  if (e != cudaSuccess) return {SGDG_ECUDA, "host apply: conversion"};
   if (cudaMemcpyAsync(x.y + off, out64 + off, 8 * n, cudaMemcpyDeviceToHost, h.host_c) != cudaSuccess)
     return {SGDG_ECUDA, "host apply: device-to-host copy"};
   return {};
@@ -555,15 +565,19 @@ Status host_apply_done(void* ctx, int i) {
 sgdg_status sgdg_apply_operator_host(void* hp, const double* u, double* y, int prec) {
   if (!hp || !u || !y) return fail((Handle*)hp, {SGDG_EINVAL, "null argument"});
   Handle* h = (Handle*)hp;
-  if (prec != SGDG_FP64 && prec != SGDG_MIXED_FP32) return fail(h, {SGDG_EINVAL, "unknown precision"});
+  if (prec != SGDG_FP64 && prec != SGDG_MIXED_FP32 && prec != SGDG_BF16_STORE)
+    return fail(h, {SGDG_EINVAL, "unknown precision"});
   Handle::Bufs& b = h->b64;
   size_t n = (size_t)h->n_coeffs;
   if (!b.cvt_in) {
     if (dev_alloc(*h, &b.cvt_in, 8 * n) != cudaSuccess || dev_alloc(*h, &b.cvt_out, 8 * n) != cudaSuccess)
       return fail(h, {SGDG_ENOMEM, "host-apply buffers"});
   }
-  if (prec == SGDG_MIXED_FP32 && !h->b32.cvt_in) {
-    if (dev_alloc(*h, &h->b32.cvt_in, 4 * n) != cudaSuccess || dev_alloc(*h, &h->b32.cvt_out, 4 * n) != cudaSuccess)
+  if (prec != SGDG_FP64) {
+    Handle::Bufs& bs = prec == SGDG_MIXED_FP32 ? h->b32 : h->b16;
+    const size_t esz = prec == SGDG_MIXED_FP32 ? 4 : 2;
+    if (!bs.cvt_in &&
+        (dev_alloc(*h, &bs.cvt_in, esz * n) != cudaSuccess || dev_alloc(*h, &bs.cvt_out, esz * n) != cudaSuccess))
       return fail(h, {SGDG_ENOMEM, "host-apply buffers"});
   }
   if (!h->host_s) {
@@ -577,28 +591,36 @@ sgdg_status sgdg_apply_operator_host(void* hp, const double* u, double* y, int p
           cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming) != cudaSuccess)
         return fail(h, {SGDG_ECUDA, "host apply: events"});
   }
-  const bool f32 = prec == SGDG_MIXED_FP32;
   double* in64 = (double*)b.cvt_in;
   for (int i = 0; i <= h->L; ++i) {
     const size_t off = (size_t)h->off[i], m = (size_t)(h->off[i + 1] - h->off[i]);
     if (cudaMemcpyAsync(in64 + off, u + off, 8 * m, cudaMemcpyHostToDevice, h->host_c) != cudaSuccess)
       return fail(h, {SGDG_ECUDA, "host-to-device copy"});
-    if (f32 && vec_convert<double, float>(in64 + off, (float*)h->b32.cvt_in + off, (long long)m, h->host_c) !=
-                   cudaSuccess)
-      return fail(h, {SGDG_ECUDA, "host apply: conversion"});
+    cudaError_t e = cudaSuccess;
+    if (prec == SGDG_MIXED_FP32)
+      e = vec_convert<double, float>(in64 + off, (float*)h->b32.cvt_in + off, (long long)m, h->host_c);
+    else if (prec == SGDG_BF16_STORE)
+      e = vec_convert<double, __nv_bfloat16>(in64 + off, (__nv_bfloat16*)h->b16.cvt_in + off, (long long)m,
+                                             h->host_c);
+    if (e != cudaSuccess) return fail(h, {SGDG_ECUDA, "host apply: conversion"});
     if (cudaEventRecord(h->ev_in[i], h->host_c) != cudaSuccess) return fail(h, {SGDG_ECUDA, "host apply: event"});
   }
   HostApply ctx;
   ctx.h = h;
-  ctx.f32 = f32;
+  ctx.prec = prec;
   ctx.y = y;
   ApplyHooks hooks;
   hooks.ready = h->ev_in.data();
   hooks.done = host_apply_done;
   hooks.ctx = &ctx;
-  Status st = f32 ? apply_plan<float>(*h, h->op, (const float*)h->b32.cvt_in, (float*)h->b32.cvt_out, h->host_s,
-                                      &hooks)
-                  : apply_plan<double>(*h, h->op, (const double*)b.cvt_in, (double*)b.cvt_out, h->host_s, &hooks);
+  Status st;
+  if (prec == SGDG_MIXED_FP32)
+    st = apply_plan<float>(*h, h->op, (const float*)h->b32.cvt_in, (float*)h->b32.cvt_out, h->host_s, &hooks);
+  else if (prec == SGDG_BF16_STORE)
+    st = apply_plan<Bf16>(*h, h->op, (const __nv_bfloat16*)h->b16.cvt_in, (__nv_bfloat16*)h->b16.cvt_out,
+                          h->host_s, &hooks);
+  else
+    st = apply_plan<double>(*h, h->op, (const double*)b.cvt_in, (double*)b.cvt_out, h->host_s, &hooks);
   if (st.code) {
     cudaStreamSynchronize(h->host_c);
     cudaStreamSynchronize(h->host_s);
@@ -624,6 +646,10 @@ sgdg_status sgdg_apply_diag(void* hp, int l1, int l2, const void* u, void* y, in
     const float* ui[1] = {(const float*)u};
     float* yo[1] = {(float*)y};
     st = apply_diag_grids<float>(*h, 1, &l1, &l2, ui, yo, s);
+  } else if (prec == SGDG_BF16_STORE) {
+    const __nv_bfloat16* ui[1] = {(const __nv_bfloat16*)u};
+    __nv_bfloat16* yo[1] = {(__nv_bfloat16*)y};
+    st = apply_diag_grids<Bf16>(*h, 1, &l1, &l2, ui, yo, s);
   } else {
     st = {SGDG_EINVAL, "unknown precision"};
   }
@@ -702,6 +728,8 @@ sgdg_status sgdg_autotune(void* hp, const void* u, void* y, int prec, void* stre
   Status st;
   if (prec == SGDG_FP64) st = autotune<double>(*h, (const double*)u, (double*)y, (cudaStream_t)stream);
   else if (prec == SGDG_MIXED_FP32) st = autotune<float>(*h, (const float*)u, (float*)y, (cudaStream_t)stream);
+  else if (prec == SGDG_BF16_STORE)
+    st = autotune<Bf16>(*h, (const __nv_bfloat16*)u, (__nv_bfloat16*)y, (cudaStream_t)stream);
   else st = {SGDG_EINVAL, "unknown precision"};
   return st.code ? fail(h, st) : SGDG_OK;
 }
@@ -748,7 +776,8 @@ void sgdg_batch_destroy(void* bp) {
 
 sgdg_status sgdg_batch_apply(void* bp, const void* const* u, void* const* y, int prec, void* stream) {
   if (!bp || !u || !y) return fail(nullptr, {SGDG_EINVAL, "null argument"});
-  if (prec != SGDG_FP64 && prec != SGDG_MIXED_FP32) return fail(nullptr, {SGDG_EINVAL, "unknown precision"});
+  if (prec != SGDG_FP64 && prec != SGDG_MIXED_FP32 && prec != SGDG_BF16_STORE)
+    return fail(nullptr, {SGDG_EINVAL, "unknown precision"});
   Batch* b = (Batch*)bp;
   const size_t n = b->m.size();
   for (auto& g : b->graphs) {
@@ -763,9 +792,11 @@ sgdg_status sgdg_batch_apply(void* bp, const void* const* u, void* const* y, int
   // eager pass: allocates every lazily created buffer before the capture
   auto run_all = [&](cudaStream_t s) -> Status {
     for (size_t k = 0; k < n; ++k) {
-      Status st = prec == SGDG_FP64
-                      ? apply_plan<double>(*b->m[k], b->m[k]->op, (const double*)u[k], (double*)y[k], s)
-                      : apply_plan<float>(*b->m[k], b->m[k]->op, (const float*)u[k], (float*)y[k], s);
+      Handle& m = *b->m[k];
+      Status st =
+          prec == SGDG_FP64        ? apply_plan<double>(m, m.op, (const double*)u[k], (double*)y[k], s)
+          : prec == SGDG_BF16_STORE ? apply_plan<Bf16>(m, m.op, (const __nv_bfloat16*)u[k], (__nv_bfloat16*)y[k], s)
+                                    : apply_plan<float>(m, m.op, (const float*)u[k], (float*)y[k], s);
       if (st.code) return st;
     }
     return {};

@@ -1,6 +1,7 @@
 // Device-side data structures and kernel launchers of the sgdg library.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <string>

@@ -5,6 +5,7 @@
 #include <memory>
 
 #include "device.h"
+#include "sweep.h"
 
 namespace sgdg {
 
@@ -82,12 +83,12 @@ struct Handle {
   std::vector<long long> soff;       // spatial offsets
   long long n_coeffs = 0, n_spatial = 0;
   Plan op, mass;
-  // sweep buffers (both precisions allocated lazily)
+  // sweep buffers per precision (FP64, FP32, BF16 storage), allocated lazily
   struct Bufs {
     void* S = nullptr; void* Z = nullptr; void* TP = nullptr; void* tmp = nullptr; void* W = nullptr;
     void* cvt_in = nullptr; void* cvt_out = nullptr;
     void* pool = nullptr; long long pool_elems = 0;   // sweep chain states
-  } b64, b32;
+  } b64, b32, b16;
   // host-buffer apply: compute and copy streams, per-grid events
   cudaStream_t host_s = nullptr, host_c = nullptr;
   std::vector<cudaEvent_t> ev_in, ev_out;
@@ -172,16 +173,17 @@ struct ApplyHooks {
 };
 
 template <typename T>
-Status apply_plan(Handle& h, const Plan& p, const T* u, T* y, cudaStream_t s, const ApplyHooks* hooks = nullptr);
+Status apply_plan(Handle& h, const Plan& p, const Store<T>* u, Store<T>* y, cudaStream_t s,
+                  const ApplyHooks* hooks = nullptr);
 template <typename T>
-Status apply_diag_grids(Handle& h, int ng, const int* l1, const int* l2, const T* const* u, T* const* y,
-                        cudaStream_t s);
+Status apply_diag_grids(Handle& h, int ng, const int* l1, const int* l2, const Store<T>* const* u,
+                        Store<T>* const* y, cudaStream_t s);
 Status nodal_eval(Handle& h, const double* u, double* out, cudaStream_t s);
 
 // Time candidate rows-per-thread settings of every sweep launch site on live
 // applies of u and keep the fastest per site.
 template <typename T>
-Status autotune(Handle& h, const T* u, T* y, cudaStream_t s);
+Status autotune(Handle& h, const Store<T>* u, Store<T>* y, cudaStream_t s);
 
 // Vlasov-Poisson coupling (field.cu)
 Status field_setup(Handle& h, const sgdg_coeffs& c, const Hierarchy& hx, const Hierarchy& hv, const SideFns& fx);

@@ -292,10 +292,19 @@ cudaError_t vec_fill(T* x, long long n, T v, cudaStream_t s) {
 template cudaError_t vec_fill<double>(double*, long long, double, cudaStream_t);
 template cudaError_t vec_fill<float>(float*, long long, float, cudaStream_t);
 
+template <typename TO, typename TI>
+__device__ __forceinline__ TO convert_to(TI x) { return (TO)x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 convert_to<__nv_bfloat16, double>(double x) { return __double2bfloat16(x); }
+template <>
+__device__ __forceinline__ double convert_to<double, __nv_bfloat16>(__nv_bfloat16 x) {
+  return (double)__bfloat162float(x);   // exact: every bfloat16 is a float
+}
+
 template <typename TI, typename TO>
 __global__ void k_convert(const TI* x, TO* y, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = (TO)x[i];
+    y[i] = convert_to<TO>(x[i]);
 }
 template <typename TI, typename TO>
 cudaError_t vec_convert(const TI* x, TO* y, long long n, cudaStream_t s) {
@@ -305,6 +314,8 @@ cudaError_t vec_convert(const TI* x, TO* y, long long n, cudaStream_t s) {
 template cudaError_t vec_convert<double, float>(const double*, float*, long long, cudaStream_t);
 template cudaError_t vec_convert<float, double>(const float*, double*, long long, cudaStream_t);
 template cudaError_t vec_convert<double, double>(const double*, double*, long long, cudaStream_t);
+template cudaError_t vec_convert<double, __nv_bfloat16>(const double*, __nv_bfloat16*, long long, cudaStream_t);
+template cudaError_t vec_convert<__nv_bfloat16, double>(const __nv_bfloat16*, double*, long long, cudaStream_t);
 
 template <typename T>
 __global__ void k_axpby(long long n, double a, const T* x, double b, T* y) {

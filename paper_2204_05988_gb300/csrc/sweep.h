@@ -2,9 +2,20 @@
 // sweep_final.cu).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace sgdg {
+
+// Precision of a sweep, named by a type: double and float store every grid
+// array (inputs, chain states, outputs) and compute in that type; Bf16
+// stores the grid arrays in bfloat16 and computes in FP32, with FP32 matrix
+// values (the BF16-storage variant: half the bytes per grid element).
+struct Bf16 {};
+template <typename T> struct Prec { using S = T; using C = T; };
+template <> struct Prec<Bf16> { using S = __nv_bfloat16; using C = float; };
+template <typename T> using Store = typename Prec<T>::S;   // grid element
+template <typename T> using Comp = typename Prec<T>::C;    // arithmetic and matrix values
 
 template <typename T>
 constexpr int kChainMax() { return 32; }   // chains per chain-step launch
@@ -55,9 +66,9 @@ struct RestrictArgs {
   int nchains = 0, ch = 0, row = 8;   // ch: rows per thread (0: heuristic)
   int tiled = 0;                      // block order: 0 row-major, 1 column tiles (see kTileW)
   const int* col = nullptr;           // R, ELL
-  const T* val = nullptr;
-  const T* in[kChainSlots] = {};
-  T* out[kChainSlots] = {};
+  const Comp<T>* val = nullptr;
+  const Store<T>* in[kChainSlots] = {};
+  Store<T>* out[kChainSlots] = {};
 };
 
 // One chain step producing (n1 x n2) outputs for up to kChainSlots chains,
@@ -73,13 +84,13 @@ struct ChainArgs {
   int nchains = 0, has_prev = 0, ch = 0, row = 8;
   int tiled = 0;
   int pair = 0;   // mode A, rows of at most 8: two rows per thread
-  const T* U = nullptr;
+  const Store<T>* U = nullptr;
   const int* f_col = nullptr;    // ELL
-  const T* f_val[kChainSlots] = {};
+  const Comp<T>* f_val[kChainSlots] = {};
   const int* p_col = nullptr;    // ELL, width 2
-  const T* p_val = nullptr;
-  const T* Z[kChainSlots] = {};  // the Q inputs
-  T* out[kChainSlots] = {};
+  const Comp<T>* p_val = nullptr;
+  const Store<T>* Z[kChainSlots] = {};  // the Q inputs
+  Store<T>* out[kChainSlots] = {};
 };
 
 // y (+)= sum_c sum_{t in c} tau_t (x) F_t in_c on one (n1 x n2) grid, all F_t
@@ -92,12 +103,12 @@ struct FinalArgs {
   int n1 = 0, n2 = 0, nin2 = 0, ch = 0, row = 8, accumulate = 0, tiled = 0;
   int pair = 0;   // two outputs per thread: left - columns k2, k2 + 32; right - rows k1, k1 + 1
   int nin = 0, nterms = 0;
-  const T* in[kFinalIn] = {};
+  const Store<T>* in[kFinalIn] = {};
   int tbeg[kFinalIn + 1] = {};
-  const T* val[kFinalTerms] = {};   // ELL
-  T tau[kFinalTerms][4] = {};
-  const int* col = nullptr;         // ELL
-  T* y = nullptr;
+  const Comp<T>* val[kFinalTerms] = {};   // ELL
+  Comp<T> tau[kFinalTerms][4] = {};
+  const int* col = nullptr;               // ELL
+  Store<T>* y = nullptr;
 };
 
 template <typename T>

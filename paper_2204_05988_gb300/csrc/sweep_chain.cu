@@ -20,12 +20,13 @@ using namespace sweep;
 // in mode B and 2 in mode A, whose 2 x 19 gathered U values would spill at 3
 template <typename T, int ROW, bool MODE_A>
 struct ChainBounds {
-  static constexpr int blocks = sizeof(T) == 4 ? (ROW > 8 ? (MODE_A ? 2 : 3) : 4) : 2;
+  static constexpr int blocks = sizeof(Comp<T>) == 4 ? (ROW > 8 ? (MODE_A ? 2 : 3) : 4) : 2;
 };
 
 template <typename T, bool MODE_A, int ROW>
 __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, MODE_A>::blocks)) k_chain(const __grid_constant__ ChainArgs<T> a) {
-  using T2 = typename V2<T>::type;
+  using C = Comp<T>;
+  using CP = C2<T>;
   constexpr int W = Ell<ROW>::W;
   constexpr bool kPrefetch = ROW <= 8;
   const unsigned n2 = (unsigned)a.n2;
@@ -34,19 +35,18 @@ __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, MODE_A>::blocks
   if (!thread_rows(a.n1, a.n2, a.ch, a.tiled, k2, r0, r1)) return;
   unsigned fc[ROW];
   unsigned pc[kProlongRow] = {0, 0};
-  T pv[kProlongRow] = {0, 0};
+  C pv[kProlongRow] = {0, 0};
   if (MODE_A) ell_cols<ROW>(a.f_col + (size_t)k2 * W, fc);          // F row k2
   else if (a.has_prev) prolong_row(a.p_col, a.p_val, k2, pc, pv);   // P row k2
-  const T2* U = reinterpret_cast<const T2*>(a.U);
   for (int k1 = r0; k1 < r1; ++k1) {
     // the shared operand of the chains: U gathered along the first factor's row
-    T2 u[ROW];
+    CP u[ROW];
     unsigned zo[kProlongRow];
     if (MODE_A) {
       unsigned off[ROW];
 #pragma unroll
       for (int j = 0; j < ROW; ++j) off[j] = (unsigned)k1 * (unsigned)a.nu2 + fc[j];
-      gather(U, off, u);
+      gather<T>(a.U, off, u);
       if (a.has_prev) prolong_row(a.p_col, a.p_val, (unsigned)k1, pc, pv);   // P row k1
 #pragma unroll
       for (int q = 0; q < kProlongRow; ++q) zo[q] = pc[q] * n2 + k2;
@@ -55,21 +55,21 @@ __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, MODE_A>::blocks
       unsigned off[ROW];
 #pragma unroll
       for (int j = 0; j < ROW; ++j) off[j] = fc[j] * n2 + k2;
-      gather(U, off, u);
+      gather<T>(a.U, off, u);
 #pragma unroll
       for (int q = 0; q < kProlongRow; ++q) zo[q] = (unsigned)k1 * (unsigned)a.nz2 + pc[q];
     }
     const size_t o = (size_t)k1 * n2 + k2;
     const size_t frow = (size_t)(MODE_A ? k2 : (unsigned)k1) * W;
-    T fv[ROW];
-    T2 z[kProlongRow];
+    C fv[ROW];
+    CP z[kProlongRow];
 #pragma unroll
     for (int q = 0; q < kProlongRow; ++q) z[q].x = z[q].y = 0;
     if (kPrefetch) ell_vals<ROW>(a.f_val[0] + frow, fv);
-    if (a.has_prev) gather(reinterpret_cast<const T2*>(a.Z[0]), zo, z);
+    if (a.has_prev) gather<T>(a.Z[0], zo, z);
     for (int g = 0; g < a.nchains; ++g) {
-      T cv[ROW];
-      T2 cz[kProlongRow];
+      C cv[ROW];
+      CP cz[kProlongRow];
       if (kPrefetch) {
 #pragma unroll
         for (int j = 0; j < ROW; ++j) cv[j] = fv[j];
@@ -78,10 +78,10 @@ __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, MODE_A>::blocks
       for (int q = 0; q < kProlongRow; ++q) cz[q] = z[q];
       if (g + 1 < a.nchains) {
         if (kPrefetch) ell_vals<ROW>(a.f_val[g + 1] + frow, fv);
-        if (a.has_prev) gather(reinterpret_cast<const T2*>(a.Z[g + 1]), zo, z);
+        if (a.has_prev) gather<T>(a.Z[g + 1], zo, z);
       }
       if (!kPrefetch) ell_vals<ROW>(a.f_val[g] + frow, cv);
-      T zx = 0, zy = 0;
+      C zx = 0, zy = 0;
       if (a.has_prev) {
 #pragma unroll
         for (int q = 0; q < kProlongRow; ++q) {
@@ -94,10 +94,7 @@ __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, MODE_A>::blocks
         zx += cv[j] * u[j].x;
         zy += cv[j] * u[j].y;
       }
-      T2 r;
-      r.x = zx;
-      r.y = zy;
-      reinterpret_cast<T2*>(a.out[g])[o] = r;
+      put2(a.out[g], o, zx, zy);
     }
   }
 }
@@ -107,9 +104,10 @@ __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, MODE_A>::blocks
 // diagonal-block products W_b = U V_b^T, and S_b = W_b + P1 Q_b); the next
 // chain's Q values are loaded before the current chain is combined.
 template <typename T, bool MODE_A, int ROW>
-__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 ? 3 : 2)) k_chain_pair(const __grid_constant__ ChainArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, (sizeof(Comp<T>) == 4 ? 3 : 2)) k_chain_pair(const __grid_constant__ ChainArgs<T> a) {
   static_assert(MODE_A && ROW <= 8, "row pairs: mode A, short rows");
-  using T2 = typename V2<T>::type;
+  using C = Comp<T>;
+  using CP = C2<T>;
   constexpr int W = Ell<ROW>::W;
   const unsigned n2 = (unsigned)a.n2;
   unsigned k2;
@@ -117,21 +115,21 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 ? 3 : 2)) k_chain_pa
   if (!thread_rows(a.n1, a.n2, a.ch, a.tiled, k2, r0, r1)) return;
   unsigned fc[ROW];
   ell_cols<ROW>(a.f_col + (size_t)k2 * W, fc);
-  const T2* U = reinterpret_cast<const T2*>(a.U);
+  const S2<T>* U = reinterpret_cast<const S2<T>*>(a.U);
   const size_t frow = (size_t)k2 * W;
   for (int k1 = r0; k1 < r1; k1 += 2) {
     const bool b_ok = k1 + 1 < r1;
-    T2 ua[ROW], ub[ROW];
+    CP ua[ROW], ub[ROW];
 #pragma unroll
     for (int j = 0; j < ROW; ++j) {
       const unsigned off = (unsigned)k1 * (unsigned)a.nu2 + fc[j];
-      ua[j] = U[off];
-      if (b_ok) ub[j] = U[off + (unsigned)a.nu2];
+      ua[j] = widen(U[off]);
+      if (b_ok) ub[j] = widen(U[off + (unsigned)a.nu2]);
       else ub[j].x = ub[j].y = 0;
     }
     // prolongation rows k1, k1 + 1 and their Q offsets
     unsigned pca[kProlongRow] = {0, 0}, pcb[kProlongRow] = {0, 0};
-    T pva[kProlongRow] = {0, 0}, pvb[kProlongRow] = {0, 0};
+    C pva[kProlongRow] = {0, 0}, pvb[kProlongRow] = {0, 0};
     unsigned zoa[kProlongRow] = {0, 0}, zob[kProlongRow] = {0, 0};
     if (a.has_prev) {
       prolong_row(a.p_col, a.p_val, (unsigned)k1, pca, pva);
@@ -144,16 +142,16 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 ? 3 : 2)) k_chain_pa
       }
     }
     const size_t o = (size_t)k1 * n2 + k2;
-    T2 za[kProlongRow], zb[kProlongRow];
+    CP za[kProlongRow], zb[kProlongRow];
 #pragma unroll
     for (int q = 0; q < kProlongRow; ++q) za[q].x = za[q].y = zb[q].x = zb[q].y = 0;
     if (a.has_prev) {
-      gather(reinterpret_cast<const T2*>(a.Z[0]), zoa, za);
-      gather(reinterpret_cast<const T2*>(a.Z[0]), zob, zb);
+      gather<T>(a.Z[0], zoa, za);
+      gather<T>(a.Z[0], zob, zb);
     }
     for (int g = 0; g < a.nchains; ++g) {
-      T cv[ROW];
-      T2 cza[kProlongRow], czb[kProlongRow];
+      C cv[ROW];
+      CP cza[kProlongRow], czb[kProlongRow];
       ell_vals<ROW>(a.f_val[g] + frow, cv);
 #pragma unroll
       for (int q = 0; q < kProlongRow; ++q) {
@@ -162,11 +160,11 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 ? 3 : 2)) k_chain_pa
       }
       if (g + 1 < a.nchains) {
         if (a.has_prev) {
-          gather(reinterpret_cast<const T2*>(a.Z[g + 1]), zoa, za);
-          gather(reinterpret_cast<const T2*>(a.Z[g + 1]), zob, zb);
+          gather<T>(a.Z[g + 1], zoa, za);
+          gather<T>(a.Z[g + 1], zob, zb);
         }
       }
-      T ax = 0, ay = 0, bx = 0, by = 0;
+      C ax = 0, ay = 0, bx = 0, by = 0;
       if (a.has_prev) {
 #pragma unroll
         for (int q = 0; q < kProlongRow; ++q) {
@@ -183,16 +181,8 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 ? 3 : 2)) k_chain_pa
         bx += cv[j] * ub[j].x;
         by += cv[j] * ub[j].y;
       }
-      T2* out = reinterpret_cast<T2*>(a.out[g]) + o;
-      T2 r;
-      r.x = ax;
-      r.y = ay;
-      out[0] = r;
-      if (b_ok) {
-        r.x = bx;
-        r.y = by;
-        out[n2] = r;
-      }
+      put2(a.out[g], o, ax, ay);
+      if (b_ok) put2(a.out[g], o + n2, bx, by);
     }
   }
 }
@@ -220,5 +210,6 @@ cudaError_t launch_chain(ChainArgs<T>& a, bool mode_a, cudaStream_t s) {
 
 template cudaError_t launch_chain<double>(ChainArgs<double>&, bool, cudaStream_t);
 template cudaError_t launch_chain<float>(ChainArgs<float>&, bool, cudaStream_t);
+template cudaError_t launch_chain<Bf16>(ChainArgs<Bf16>&, bool, cudaStream_t);
 
 }  // namespace sgdg

@@ -12,6 +12,32 @@ namespace sweep {
 template <typename T> struct V2;
 template <> struct V2<double> { using type = double2; };
 template <> struct V2<float> { using type = float2; };
+template <> struct V2<__nv_bfloat16> { using type = __nv_bfloat162; };
+
+// the (time slot 0, time slot 1) pair of one grid element: storage and
+// arithmetic forms of precision T
+template <typename T> using S2 = typename V2<Store<T>>::type;
+template <typename T> using C2 = typename V2<Comp<T>>::type;
+
+__device__ __forceinline__ double2 widen(double2 v) { return v; }
+__device__ __forceinline__ float2 widen(float2 v) { return v; }
+__device__ __forceinline__ float2 widen(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+
+// pair p of a grid array in arithmetic form
+template <typename T>
+__device__ __forceinline__ C2<T> load2(const Store<T>* g, size_t p) {
+  return widen(reinterpret_cast<const S2<T>*>(g)[p]);
+}
+// store (x, y) as pair p (rounded to nearest for BF16 storage)
+__device__ __forceinline__ void put2(double* g, size_t p, double x, double y) {
+  reinterpret_cast<double2*>(g)[p] = make_double2(x, y);
+}
+__device__ __forceinline__ void put2(float* g, size_t p, float x, float y) {
+  reinterpret_cast<float2*>(g)[p] = make_float2(x, y);
+}
+__device__ __forceinline__ void put2(__nv_bfloat16* g, size_t p, float x, float y) {
+  reinterpret_cast<__nv_bfloat162*>(g)[p] = __floats2bfloat162_rn(x, y);
+}
 
 constexpr int kThreads = 256;
 constexpr int kChunksPerBlock = kThreads / kTileW;
@@ -121,10 +147,12 @@ __device__ __forceinline__ void prolong_row(const int* col, const T* val, unsign
   v[1] = __ldg(val + 2 * (size_t)r + 1);
 }
 
-template <typename T2, int N>
-__device__ __forceinline__ void gather(const T2* base, const unsigned (&off)[N], T2 (&w)[N]) {
+// pairs off[j] of a grid array, widened to the arithmetic type
+template <typename T, int N>
+__device__ __forceinline__ void gather(const Store<T>* base, const unsigned (&off)[N], C2<T> (&w)[N]) {
+  const S2<T>* b = reinterpret_cast<const S2<T>*>(base);
 #pragma unroll
-  for (int j = 0; j < N; ++j) w[j] = base[off[j]];
+  for (int j = 0; j < N; ++j) w[j] = widen(b[off[j]]);
 }
 
 }  // namespace sweep

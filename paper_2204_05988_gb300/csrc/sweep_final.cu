@@ -14,7 +14,8 @@ using namespace sweep;
 
 template <typename T, bool LEFT, int ROW>
 __global__ void __launch_bounds__(kThreads) k_final(const __grid_constant__ FinalArgs<T> a) {
-  using T2 = typename V2<T>::type;
+  using C = Comp<T>;
+  using CP = C2<T>;
   constexpr int W = Ell<ROW>::W;
   const unsigned n2 = (unsigned)a.n2;
   unsigned k2;
@@ -29,18 +30,18 @@ __global__ void __launch_bounds__(kThreads) k_final(const __grid_constant__ Fina
     for (int j = 0; j < ROW; ++j) off[j] = LEFT ? fc[j] * n2 + k2 : (unsigned)k1 * (unsigned)a.nin2 + fc[j];
     const size_t frow = (size_t)(LEFT ? (unsigned)k1 : k2) * W;
     const size_t o = (size_t)k1 * n2 + k2;
-    T yx = 0, yy = 0;
-    T2 w[ROW];
-    gather(reinterpret_cast<const T2*>(a.in[0]), off, w);
+    C yx = 0, yy = 0;
+    CP w[ROW];
+    gather<T>(a.in[0], off, w);
     for (int ci = 0; ci < a.nin; ++ci) {
-      T2 cw[ROW];
+      CP cw[ROW];
 #pragma unroll
       for (int j = 0; j < ROW; ++j) cw[j] = w[j];
-      if (ci + 1 < a.nin) gather(reinterpret_cast<const T2*>(a.in[ci + 1]), off, w);
+      if (ci + 1 < a.nin) gather<T>(a.in[ci + 1], off, w);
       for (int t = a.tbeg[ci]; t < a.tbeg[ci + 1]; ++t) {
-        T ev[ROW];
+        C ev[ROW];
         ell_vals<ROW>(a.val[t] + frow, ev);
-        T sx = 0, sy = 0;
+        C sx = 0, sy = 0;
 #pragma unroll
         for (int j = 0; j < ROW; ++j) {
           sx += ev[j] * cw[j].x;
@@ -50,17 +51,12 @@ __global__ void __launch_bounds__(kThreads) k_final(const __grid_constant__ Fina
         yy += a.tau[t][2] * sx + a.tau[t][3] * sy;
       }
     }
-    T2* y = reinterpret_cast<T2*>(a.y) + o;
-    T2 r;
     if (a.accumulate) {
-      r = *y;
-      r.x += yx;
-      r.y += yy;
+      const CP r = load2<T>(a.y, o);
+      put2(a.y, o, r.x + yx, r.y + yy);
     } else {
-      r.x = yx;
-      r.y = yy;
+      put2(a.y, o, yx, yy);
     }
-    *y = r;
   }
 }
 
@@ -69,8 +65,9 @@ __global__ void __launch_bounds__(kThreads) k_final(const __grid_constant__ Fina
 // 64 consecutive columns, both loads coalesced); right - rows k1 and k1 + 1
 // of one column.
 template <typename T, bool LEFT, int ROW>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_final2(const __grid_constant__ FinalArgs<T> a) {
-  using T2 = typename V2<T>::type;
+__global__ void __launch_bounds__(kThreads, sizeof(Comp<T>) == 4 ? 4 : 2) k_final2(const __grid_constant__ FinalArgs<T> a) {
+  using C = Comp<T>;
+  using CP = C2<T>;
   constexpr int W = Ell<ROW>::W;
   const unsigned n2 = (unsigned)a.n2;
   // left: the thread grid runs over column pairs, 32 pairs per 64 columns
@@ -91,20 +88,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_final2(con
     for (int j = 0; j < ROW; ++j) off[j] = LEFT ? fc[j] * n2 + k2 : (unsigned)k1 * (unsigned)a.nin2 + fc[j];
     const unsigned step_b = LEFT ? 32u : (unsigned)a.nin2;   // second output's gather offset
     const size_t frow = (size_t)(LEFT ? (unsigned)k1 : k2) * W;
-    T ax = 0, ay = 0, bx = 0, by = 0;
+    C ax = 0, ay = 0, bx = 0, by = 0;
     for (int ci = 0; ci < a.nin; ++ci) {
-      const T2* in = reinterpret_cast<const T2*>(a.in[ci]);
-      T2 wa[ROW], wb[ROW];
+      const S2<T>* in = reinterpret_cast<const S2<T>*>(a.in[ci]);
+      CP wa[ROW], wb[ROW];
 #pragma unroll
       for (int j = 0; j < ROW; ++j) {
-        wa[j] = in[off[j]];
-        if (b_ok) wb[j] = in[off[j] + step_b];
+        wa[j] = widen(in[off[j]]);
+        if (b_ok) wb[j] = widen(in[off[j] + step_b]);
         else wb[j].x = wb[j].y = 0;
       }
       for (int t = a.tbeg[ci]; t < a.tbeg[ci + 1]; ++t) {
-        T ev[ROW];
+        C ev[ROW];
         ell_vals<ROW>(a.val[t] + frow, ev);
-        T sax = 0, say = 0, sbx = 0, sby = 0;
+        C sax = 0, say = 0, sbx = 0, sby = 0;
 #pragma unroll
         for (int j = 0; j < ROW; ++j) {
           sax += ev[j] * wa[j].x;
@@ -112,35 +109,28 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_final2(con
           sbx += ev[j] * wb[j].x;
           sby += ev[j] * wb[j].y;
         }
-        const T t0 = a.tau[t][0], t1 = a.tau[t][1], t2 = a.tau[t][2], t3 = a.tau[t][3];
+        const C t0 = a.tau[t][0], t1 = a.tau[t][1], t2 = a.tau[t][2], t3 = a.tau[t][3];
         ax += t0 * sax + t1 * say;
         ay += t2 * sax + t3 * say;
         bx += t0 * sbx + t1 * sby;
         by += t2 * sbx + t3 * sby;
       }
     }
-    T2* ya = reinterpret_cast<T2*>(a.y) + (size_t)k1 * n2 + k2;
-    T2* yb = LEFT ? ya + 32 : ya + n2;
-    T2 r;
+    const size_t oa = (size_t)k1 * n2 + k2;
+    const size_t ob = LEFT ? oa + 32 : oa + n2;
     if (a.accumulate) {
-      r = *ya;
-      r.x += ax;
-      r.y += ay;
+      const CP r = load2<T>(a.y, oa);
+      put2(a.y, oa, r.x + ax, r.y + ay);
     } else {
-      r.x = ax;
-      r.y = ay;
+      put2(a.y, oa, ax, ay);
     }
-    *ya = r;
     if (b_ok) {
       if (a.accumulate) {
-        r = *yb;
-        r.x += bx;
-        r.y += by;
+        const CP r = load2<T>(a.y, ob);
+        put2(a.y, ob, r.x + bx, r.y + by);
       } else {
-        r.x = bx;
-        r.y = by;
+        put2(a.y, ob, bx, by);
       }
-      *yb = r;
     }
   }
 }
@@ -173,5 +163,6 @@ cudaError_t launch_final(FinalArgs<T>& a, bool left, cudaStream_t s) {
 
 template cudaError_t launch_final<double>(FinalArgs<double>&, bool, cudaStream_t);
 template cudaError_t launch_final<float>(FinalArgs<float>&, bool, cudaStream_t);
+template cudaError_t launch_final<Bf16>(FinalArgs<Bf16>&, bool, cudaStream_t);
 
 }  // namespace sgdg

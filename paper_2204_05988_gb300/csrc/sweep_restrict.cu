@@ -13,14 +13,14 @@ using namespace sweep;
 
 template <typename T, bool DIM2, int ROW>
 __global__ void __launch_bounds__(kThreads) k_restrict(const __grid_constant__ RestrictArgs<T> a) {
-  using T2 = typename V2<T>::type;
+  using C = Comp<T>;
   constexpr int W = Ell<ROW>::W;
   const unsigned n2 = (unsigned)a.n2;
   unsigned k2;
   int r0, r1;
   if (!thread_rows(a.n1, a.n2, a.ch, a.tiled, k2, r0, r1)) return;
   unsigned rc[ROW];
-  T rv[ROW];
+  C rv[ROW];
   if (DIM2) {
     // Q[k1][k2] = sum_j R[k2][j] in[k1][col_j]: row k2 of R, reused over the rows
     ell_cols<ROW>(a.col + (size_t)k2 * W, rc);
@@ -37,18 +37,15 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const __grid_constant__ R
     for (int j = 0; j < ROW; ++j) off[j] = DIM2 ? (unsigned)k1 * (unsigned)a.n2_in + rc[j] : rc[j] * n2 + k2;
     const size_t o = (size_t)k1 * n2 + k2;
     for (int g = 0; g < a.nchains; ++g) {
-      T2 w[ROW];
-      gather(reinterpret_cast<const T2*>(a.in[g]), off, w);
-      T sx = 0, sy = 0;
+      C2<T> w[ROW];
+      gather<T>(a.in[g], off, w);
+      C sx = 0, sy = 0;
 #pragma unroll
       for (int j = 0; j < ROW; ++j) {
         sx += rv[j] * w[j].x;
         sy += rv[j] * w[j].y;
       }
-      T2 r;
-      r.x = sx;
-      r.y = sy;
-      reinterpret_cast<T2*>(a.out[g])[o] = r;
+      put2(a.out[g], o, sx, sy);
     }
   }
 }
@@ -69,5 +66,6 @@ cudaError_t launch_restrict(RestrictArgs<T>& a, bool dim2, cudaStream_t s) {
 
 template cudaError_t launch_restrict<double>(RestrictArgs<double>&, bool, cudaStream_t);
 template cudaError_t launch_restrict<float>(RestrictArgs<float>&, bool, cudaStream_t);
+template cudaError_t launch_restrict<Bf16>(RestrictArgs<Bf16>&, bool, cudaStream_t);
 
 }  // namespace sgdg
