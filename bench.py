@@ -212,12 +212,15 @@ def main():
     unique = 2 * (sum(a * b for a, b in sh) - sum(sh[l][0] * sh[l + 1][1] for l in range(len(sh) - 1)))
     u64 = torch.tensor(W.uniform_vector(n, seed=1 + rank), dtype=torch.float64, device="cuda")
     u32 = u64.float()
+    u16 = u64.to(torch.bfloat16)
     y32 = torch.empty_like(u32)
     y64 = torch.empty_like(u64)
+    y16 = torch.empty_like(u16)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     s.autotune(u32, y32, P.SGDG_MIXED_FP32, stream)
     s.autotune(u64, y64, P.SGDG_FP64, stream)
+    s.autotune(u16, y16, P.SGDG_BF16_STORE, stream)
     torch.cuda.synchronize()
     tune_s = time.perf_counter() - t0
 
@@ -242,20 +245,34 @@ def main():
     for _ in range(args.warmup):
         s.apply_operator(u32, y32, P.SGDG_MIXED_FP32, stream)
     barrier()
-    # clocks are sampled over both timed regions (FP32, then FP64), ~1.5 s of load
+    # clocks are sampled over the timed regions (FP32, FP64, BF16 storage), ~2 s of load
     with Clocks(local) as clk:
         l0 = s.launch_count()
         ms32 = timed(lambda: s.apply_operator(u32, y32, P.SGDG_MIXED_FP32, stream), args.steps, 0)
         launches = s.launch_count() - l0
         # ---- FP64 apply
         ms64 = timed(lambda: s.apply_operator(u64, y64, P.SGDG_FP64, stream), max(2, args.steps // 2), 1)
+        # ---- BF16-storage apply
+        ms16 = timed(lambda: s.apply_operator(u16, y16, P.SGDG_BF16_STORE, stream), args.steps, 1)
     clocks = clk.summary()
     value = world * n / (ms32 * 1e-3) / 1e9
+
+    # errors of the reduced precisions against the FP64 apply of the same input
+    # (the FP64 path matches the oracle to 1e-12)
+    def rel(a, b):
+        return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    s.apply_operator(u64, y64, P.SGDG_FP64, stream)
+    s.apply_operator(u32, y32, P.SGDG_MIXED_FP32, stream)
+    err32 = rel(y32.double(), y64)
+    s.apply_operator(u16.double(), y64, P.SGDG_FP64, stream)
+    s.apply_operator(u16, y16, P.SGDG_BF16_STORE, stream)
+    err16 = rel(y16.double(), y64)
 
     # ---- per-kernel roofline (one profiled apply per precision)
     peak, peak_kind = _peaks()
     roof = {}
-    for name, (u_, y_, pr) in {"f32": (u32, y32, P.SGDG_MIXED_FP32), "f64": (u64, y64, P.SGDG_FP64)}.items():
+    for name, (u_, y_, pr) in {"f32": (u32, y32, P.SGDG_MIXED_FP32), "f64": (u64, y64, P.SGDG_FP64),
+                               "bf16": (u16, y16, P.SGDG_BF16_STORE)}.items():
         s.profile(True)
         s.apply_operator(u_, y_, pr, stream)
         st = s.kernel_stats()
@@ -300,6 +317,19 @@ def main():
                                      "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None,
                                      "GFLOPs": (v["flops"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                                  for k, v in roof["f64"].items() if v["launches"]}}
+    st16 = roof["bf16"]
+    dom16 = max(st16, key=lambda k: st16[k]["ms"])
+    bf16_apply = {"value": world * n / (ms16 * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms16,
+                  "storage": "bfloat16 grid arrays, FP32 arithmetic and matrix values",
+                  "rel_err_vs_fp64": err16,
+                  "roofline": {"bound": "hbm", "kernel": dom16,
+                               "achieved": st16[dom16]["bytes"] / (st16[dom16]["ms"] * 1e-3) / 1e9,
+                               "peak": peak, "unit": "GB/s",
+                               "frac": st16[dom16]["bytes"] / (st16[dom16]["ms"] * 1e-3) / 1e9 / peak,
+                               "share_of_apply": st16[dom16]["ms"] / sum(v["ms"] for v in st16.values())},
+                  "per_kind": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                                   "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                               for k, v in st16.items() if v["launches"]}}
 
     # ---- end to end through the C ABI with pinned host buffers (FP64 in/out, FP32 apply)
     hu = torch.empty(n, dtype=torch.float64, pin_memory=True)
@@ -317,7 +347,7 @@ def main():
     e2e = {"value": world * n / e2e_s / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * n,
            "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_s * 1e3}
     s.close()
-    del u64, u32, y32, y64
+    del u64, u32, y32, y64, u16, y16
     torch.cuda.empty_cache()
 
     # ---- strip solves at 1e-8 (mixed vs FP64)
@@ -410,6 +440,8 @@ def main():
                            "autotune_s": round(tune_s, 2)},
                 "fp64_apply": {"value": world * n / (ms64 * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms64,
                                "roofline": fp64_roof},
+                "bf16_apply": bf16_apply,
+                "rel_err_vs_fp64_apply": {"f32": err32, "bf16_storage": err16},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
                 "strip": strip, "batch": batch, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -178,6 +178,17 @@ class FactorStore:
             self._proj[key] = (self.embed(l).T @ self.fine(f) @ self.embed(lp)).tocsr()
         return self._proj[key]
 
+    def test_row(self, f: Factor, l: int, k: int) -> sp.csr_matrix:
+        """Row k of E_{L<-l}^T X_L (1 x n_L): the factor's bilinear form with
+        the level-l test function k written in the finest basis."""
+        if ("csc", l) not in self._emb:
+            self._emb[("csc", l)] = self.embed(l).tocsc()
+        return (self._emb[("csc", l)][:, [k]].T @ self.fine(f)).tocsr()
+
+    def proj_row(self, row: sp.csr_matrix, lp: int) -> sp.csr_matrix:
+        """Row k of X_{l,l'} from test_row(f, l, k): times E_{L<-l'}."""
+        return (row @ self.embed(lp)).tocsr()
+
 
 def assemble_load_grad(lev: Level, fn, axis: int, q: int = QUAD_Q) -> np.ndarray:
     """F[i] = int fn(y) (d/dy_axis phi_i)(y) dy on one level (fn=None: 1);

@@ -221,6 +221,38 @@ class SparseGridOperator:
             y[self.offsets[i]:self.offsets[i + 1]] = acc.ravel()
         return y
 
+    def apply_rows(self, us, rows, terms=None) -> np.ndarray:
+        """Selected outputs of the blockwise apply, each from the definition
+        (Sect. 4.2):
+            [A u]_l[k1, k2, :] = sum_{l'} sum_t tau_t (X_{l1,l1'}[k1, :] U_l' V_{l2,l2'}[k2, :]^T)
+        with only row k1 of X_{l1,l1'} and row k2 of V_{l2,l2'} formed, from
+        the finest-level factor and the embeddings.  For sizes where the
+        whole apply is out of reach.  us: list of coefficient vectors;
+        rows: (grid i, k1, k2) triples.  Returns [len(us)][len(rows)][R]."""
+        terms = self.terms if terms is None else terms
+        out = np.zeros((len(us), len(rows), self.R))
+        for n, (i, k1, k2) in enumerate(rows):
+            l1, l2 = self.grids[i]
+            xrow, vrow = {}, {}
+            for _, X, V in terms:
+                if X not in xrow:
+                    xrow[X] = self.fx.test_row(X, l1, k1)
+                if V not in vrow:
+                    vrow[V] = self.fv.test_row(V, l2, k2)
+            for j, (m1, m2) in enumerate(self.grids):
+                xr = {X: self.fx.proj_row(r, m1) for X, r in xrow.items()}
+                vr = {V: self.fv.proj_row(r, m2) for V, r in vrow.items()}
+                blocks = [self.block(u, j) for u in us]
+                for tau, X, V in terms:
+                    x, v = xr[X], vr[V]
+                    if x.nnz == 0 or v.nnz == 0:
+                        continue
+                    for q, U in enumerate(blocks):
+                        sub = U[np.ix_(x.indices, v.indices)]          # (nx, nv, R)
+                        w = np.einsum("a,abt,b->t", x.data, sub, v.data)
+                        out[q, n] += tau @ w
+        return out
+
     def apply_diag(self, l1: int, l2: int, u: np.ndarray, terms=None) -> np.ndarray:
         """A_{l,l} on one anisotropic full grid (used by the component solves)."""
         terms = self.terms if terms is None else terms

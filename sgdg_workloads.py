@@ -343,6 +343,28 @@ def uniform_vector(n: int, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).uniform(-1.0, 1.0, size=n)
 
 
+def round_to_bf16(x: np.ndarray) -> np.ndarray:
+    """The nearest bfloat16 values of x (rounded to float32, then to 8
+    significant bits, ties to even), returned as float64: inputs that a
+    bfloat16-storage apply and an FP64 reference read identically."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
+    return (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def grid_samples(shapes, per_grid: int, seed: int):
+    """(grid, k1, k2) output positions, per_grid >= 2 on every grid: the
+    last row and column (the ragged edges of any tiling), then seeded
+    interior positions."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, (n1, n2) in enumerate(shapes):
+        out.append((i, n1 - 1, n2 - 1))
+        for _ in range(per_grid - 1):
+            out.append((i, int(rng.integers(0, n1)), int(rng.integers(0, n2))))
+    return out
+
+
 def sample_indices(n: int, k: int, seed: int) -> np.ndarray:
     """k distinct sorted indices in [0, n), seeded."""
     rng = np.random.default_rng(seed)

@@ -134,3 +134,21 @@ def test_blockwise_apply_matches_dense_and_ordering_rule():
                 acc = acc + op.time(tau, w)
         y2[op.offsets[i]:op.offsets[i + 1]] = acc.ravel()
     assert np.abs(y - y2).max() < 1e-12 * np.abs(y).max()
+
+
+@pytest.mark.parametrize("prob", [W.transport_2d(L=3, sigma=0.1), W.free_streaming_1d(L=4)],
+                         ids=["d2_L3", "d1_L4"])
+def test_sampled_outputs_match_blockwise_apply(prob):
+    """apply_rows (rows of the projected factors from the finest-level matrix,
+    used where the whole apply is out of reach) returns the blockwise apply's
+    outputs: first and last rows and columns and interior ones, every grid,
+    two input vectors at once."""
+    op = SparseGridOperator(prob)
+    us = [W.uniform_vector(op.size, seed=3), W.uniform_vector(op.size, seed=4)]
+    rows = [(i, k1, k2) for i, (n1, n2) in enumerate(op.shape)
+            for k1 in sorted({0, n1 - 1, n1 // 2}) for k2 in sorted({0, n2 - 1, n2 // 3})]
+    out = op.apply_rows(us, rows)
+    for q, u in enumerate(us):
+        y = op.apply(u)
+        ref = np.array([op.block(y, i)[k1, k2] for (i, k1, k2) in rows])
+        assert np.abs(out[q] - ref).max() < 1e-13 * np.abs(ref).max()
