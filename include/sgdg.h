@@ -303,6 +303,13 @@ sgdg_status sgdg_mlp_set_params(void* mlp, const float* params);
  * sgdg_apply_operator, overwritten) and keeps the fastest per site for all
  * later applies of this handle. */
 sgdg_status sgdg_autotune(void* h, const void* u, void* y, int precision, void* stream);
+/* Pins every sweep launch site of later applies to one launch shape,
+ * code = rows per thread (1..15) | block order << 4 (0 row-major, 1 column
+ * tiles) | two outputs per thread in the final kernels << 5 | input-outer
+ * final kernels << 6 (rows per thread capped at 8); code 0 returns to the
+ * tuned or default shapes.  For tests and measurements: a shape changes the
+ * thread mapping, never the values.  code < 0 or > 127: SGDG_EINVAL. */
+sgdg_status sgdg_set_launch_shape(void* h, int code);
 
 /* Batches of independent problems (many instances of uneven L, Sect. 5's
  * experiments run one after another; here they share the GPU).  A batch

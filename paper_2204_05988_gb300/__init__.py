@@ -95,6 +95,7 @@ EXPORTS = {
     "sgdg_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "sgdg_launch_count": (C.c_longlong, [C.c_void_p]),
     "sgdg_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "sgdg_set_launch_shape": (C.c_int, [C.c_void_p, C.c_int]),
     "sgdg_field_update": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "sgdg_resolve_strip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_set_warm_start": (C.c_int, [C.c_void_p, C.c_int]),
@@ -390,6 +391,10 @@ class Solver:
 
     def autotune(self, u, y, precision: int = SGDG_MIXED_FP32, stream=None):
         self._check(self.lib.sgdg_autotune(self.h, _ptr(u), _ptr(y), precision, _stream(stream)))
+
+    def set_launch_shape(self, code: int):
+        """Pin every sweep launch site to one shape (0: tuned or default)."""
+        self._check(self.lib.sgdg_set_launch_shape(self.h, code))
 
     def launch_count(self) -> int:
         return int(self.lib.sgdg_launch_count(self.h))

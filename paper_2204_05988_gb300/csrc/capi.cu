@@ -722,6 +722,15 @@ sgdg_status sgdg_get_end_value(const void* hp, double* dst, int on_device) {
   return e == cudaSuccess ? SGDG_OK : SGDG_ECUDA;
 }
 
+sgdg_status sgdg_set_launch_shape(void* hp, int code) {
+  if (!hp) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  if (code < 0 || code > 127 || (code > 0 && (code & 15) == 0))
+    return fail(h, {SGDG_EINVAL, "launch shape code: rows per thread 1..15, flags in bits 4..6"});
+  h->force_ch = code;
+  return SGDG_OK;
+}
+
 sgdg_status sgdg_autotune(void* hp, const void* u, void* y, int prec, void* stream) {
   if (!hp || !u || !y) return fail((Handle*)hp, {SGDG_EINVAL, "null argument"});
   Handle* h = (Handle*)hp;

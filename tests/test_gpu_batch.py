@@ -92,3 +92,41 @@ def test_autotune_keeps_results(P, prec):
     ref = SparseGridOperator(prob).apply(u.double().cpu().numpy())
     err = np.linalg.norm(y1.double().cpu().numpy() - ref) / np.linalg.norm(ref)
     assert err < (1e-12 if prec == "fp64" else 1e-5)
+
+
+_SHAPES = ([ch | tiled << 4 | pair << 5 for pair in (0, 1) for tiled in (0, 1) for ch in (1, 2, 4, 8)]
+           + [ch | tiled << 4 | 1 << 6 for tiled in (0, 1) for ch in (2, 3, 8)])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("case", ["d2_L4", "d1_L6"])
+def test_every_launch_shape_gives_the_same_values(P, prec, case):
+    """Every launch shape the autotuner can pick (rows per thread, block
+    order, paired outputs, input-outer finals) pinned on all sites at once:
+    the values are those of the default shapes, bit for bit, and match the
+    oracle."""
+    from oracle.operator import SparseGridOperator
+    prob = W.transport_2d(L=4, sigma=0.1) if case == "d2_L4" else W.free_streaming_1d(L=6)
+    s = P.Solver(prob)
+    u = W.uniform_vector(s.n_coeffs, seed=6)
+    if prec == "bf16":
+        u = W.round_to_bf16(u)
+    dt = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.bfloat16}[prec]
+    pc = {"fp64": P.SGDG_FP64, "fp32": P.SGDG_MIXED_FP32, "bf16": P.SGDG_BF16_STORE}[prec]
+    ud = torch.tensor(u, dtype=torch.float64, device="cuda").to(dt)
+    y0 = torch.empty_like(ud)
+    s.apply_operator(ud, y0, pc)
+    ref = SparseGridOperator(prob).apply(u)
+    tol = {"fp64": 1e-12, "fp32": 1e-5, "bf16": (2 * prob.L + 3) * 2.0 ** -8}[prec]
+    for code in _SHAPES:
+        s.set_launch_shape(code)
+        y = torch.full_like(ud, float("nan"))
+        s.apply_operator(ud, y, pc)
+        torch.cuda.synchronize()
+        assert torch.equal(y, y0), code
+        err = np.linalg.norm(y.double().cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err < tol, (code, err)
+    s.set_launch_shape(0)
+    with pytest.raises(P.SgdgError):
+        s.set_launch_shape(16)
+    s.close()
