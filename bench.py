@@ -41,7 +41,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
 FP64_PEAK_GFLOPS = 1250.0
 
 
-def _traffic(kind: str, L: int):
+def _traffic(kind: str, L: int, key: str = "dram_bytes_per_launch"):
     """DRAM bytes per launch of a sweep kernel kind from the committed ncu
     launch-list summary, when it was taken on this workload and on the kernel
     sources as they are now (None otherwise)."""
@@ -57,7 +57,7 @@ def _traffic(kind: str, L: int):
             h.update(f.read())
     if h.hexdigest() != d["kernel_sources_sha256"]:
         return None
-    return d["dram_bytes_per_launch"].get(kind)
+    return d.get(key, {}).get(kind)
 
 
 def _peaks():
@@ -326,6 +326,8 @@ def main():
                                "achieved": st16[dom16]["bytes"] / (st16[dom16]["ms"] * 1e-3) / 1e9,
                                "peak": peak, "unit": "GB/s",
                                "frac": st16[dom16]["bytes"] / (st16[dom16]["ms"] * 1e-3) / 1e9 / peak,
+                               "traffic": _traffic(dom16, args.L, "dram_bytes_per_launch_bf16"),
+                               "alg_bytes_per_launch": st16[dom16]["bytes"] / max(1, st16[dom16]["launches"]),
                                "share_of_apply": st16[dom16]["ms"] / sum(v["ms"] for v in st16.values())},
                   "per_kind": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                                    "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}

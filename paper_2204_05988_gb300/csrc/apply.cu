@@ -124,13 +124,12 @@ inline long long site_key(int kind, int n1, int n2, int count, int elem) {
 }
 
 // Launch shape of a site: rows per thread (ch, 0 = heuristic), block order
-// (tiled) and, for the final kernels, two outputs per thread (pair) or the
-// input-outer order (io).  Tuned choices are stored as
-// ch | tiled << 4 | pair << 5 | io << 6.  Untuned sites take the column tiles
-// when the launch's stencil runs along dim 1 and rows are long enough to fill
-// a tile.
+// (tiled) and, for the final kernels, two outputs per thread (pair).  Tuned
+// choices are stored as ch | tiled << 4 | pair << 5.  Untuned sites take the
+// column tiles when the launch's stencil runs along dim 1 and rows are long
+// enough to fill a tile.
 struct Shape {
-  int ch = 0, tiled = 0, pair = 0, io = 0;
+  int ch = 0, tiled = 0, pair = 0;
 };
 
 template <typename T>
@@ -145,7 +144,6 @@ Shape pick_shape(Handle& h, long long site, bool dim1_stencil, int n1, int n2) {
     sh.ch = std::min(code & 15, n1);
     sh.tiled = (code >> 4) & 1;
     sh.pair = (code >> 5) & 1;
-    sh.io = (code >> 6) & 1;
   } else {
     sh.tiled = dim1_stencil && n2 >= kTileW ? 1 : 0;
   }
@@ -215,7 +213,6 @@ Status run_final(Handle& h, FinalArgs<T>& f, bool left, int kind, cudaStream_t s
   f.ch = sh.ch;
   f.tiled = sh.tiled;
   f.pair = sh.pair;
-  f.io = sh.io;
   ProfScope ps(h, s);
   SG_CU(launch_final(f, left, s));
   const double g = grid_bytes<T>(f.n1, f.n2);
@@ -521,14 +518,11 @@ Status nodal_eval(Handle& h, const double* u, double* out, cudaStream_t s) {
 
 template <typename T>
 Status autotune(Handle& h, const Store<T>* u, Store<T>* y, cudaStream_t s) {
-  // rows per thread x block order x (paired outputs | input-outer finals),
-  // encoded as ch | tiled << 4 | pair << 5 | io << 6
+  // rows per thread x block order x paired outputs, encoded as ch | tiled << 4 | pair << 5
   std::vector<int> cand;
   for (int pair = 0; pair < 2; ++pair)
     for (int tiled = 0; tiled < 2; ++tiled)
       for (int ch : {1, 2, 4, 8}) cand.push_back(ch | tiled << 4 | pair << 5);
-  for (int tiled = 0; tiled < 2; ++tiled)
-    for (int ch : {2, 4, 8}) cand.push_back(ch | tiled << 4 | 1 << 6);
   std::map<long long, std::pair<float, int>> best;
   const bool prof_was = h.prof;
   for (int c : cand) {

@@ -33,7 +33,6 @@ constexpr int kProlongRow = 2;    // entries of a prolongation row (nested P1 re
 //             row chunks - the rows a dim-1 stencil reaches (one mesh row
 //             away) are read by blocks that run at the same time.
 constexpr int kTileW = 64;
-constexpr int kIoRows = 8;   // rows per thread of the input-outer final kernel
 
 // Matrices reach the sweep kernels in ELL form: row r's entries at
 // [r w, r w + w) of a column and a value array, w = the longest row rounded
@@ -103,7 +102,6 @@ template <typename T>
 struct FinalArgs {
   int n1 = 0, n2 = 0, nin2 = 0, ch = 0, row = 8, accumulate = 0, tiled = 0;
   int pair = 0;   // two outputs per thread: left - columns k2, k2 + 32; right - rows k1, k1 + 1
-  int io = 0;     // input-outer order: a chunk's (<= kIoRows) partial sums held over one pass of the inputs
   int nin = 0, nterms = 0;
   const Store<T>* in[kFinalIn] = {};
   int tbeg[kFinalIn + 1] = {};

@@ -135,69 +135,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(Comp<T>) == 4 ? 4 : 2) k_fina
   }
 }
 
-// Input-outer order: a thread holds the partial sums of its whole chunk of
-// rows (at most kIoRows) and passes over the inputs once.  Right: a term's
-// factor row k2 is loaded once per input and serves every row of the chunk
-// (the row-outer order reloads it per row); left: the input rows a chunk's
-// stencils reach are gathered for consecutive rows back to back, while they
-// are still in L1.  Per output the sums run in the same order as in k_final.
-template <typename T, bool LEFT, int ROW>
-__global__ void __launch_bounds__(kThreads, sizeof(Comp<T>) == 4 ? 4 : 2) k_final_io(const __grid_constant__ FinalArgs<T> a) {
-  using C = Comp<T>;
-  using CP = C2<T>;
-  constexpr int W = Ell<ROW>::W;
-  const unsigned n2 = (unsigned)a.n2;
-  unsigned k2;
-  int r0, r1;
-  if (!thread_rows(a.n1, a.n2, a.ch, a.tiled, k2, r0, r1)) return;
-  const int nr = r1 - r0;   // <= kIoRows: the launcher caps ch
-  C ax[kIoRows], ay[kIoRows];
-#pragma unroll
-  for (int r = 0; r < kIoRows; ++r) ax[r] = ay[r] = 0;
-  unsigned fr[ROW];
-  if (!LEFT) ell_cols<ROW>(a.col + (size_t)k2 * W, fr);
-  for (int ci = 0; ci < a.nin; ++ci) {
-    const S2<T>* in = reinterpret_cast<const S2<T>*>(a.in[ci]);
-    for (int t = a.tbeg[ci]; t < a.tbeg[ci + 1]; ++t) {
-      const C t0 = a.tau[t][0], t1 = a.tau[t][1], t2 = a.tau[t][2], t3 = a.tau[t][3];
-      C ev[ROW];
-      if (!LEFT) ell_vals<ROW>(a.val[t] + (size_t)k2 * W, ev);
-#pragma unroll
-      for (int r = 0; r < kIoRows; ++r) {
-        if (r < nr) {
-          const unsigned k1 = (unsigned)(r0 + r);
-          unsigned fc[ROW];
-          if (LEFT) {
-            ell_cols<ROW>(a.col + (size_t)k1 * W, fc);
-            ell_vals<ROW>(a.val[t] + (size_t)k1 * W, ev);
-          }
-          C sx = 0, sy = 0;
-#pragma unroll
-          for (int j = 0; j < ROW; ++j) {
-            const CP w = widen(in[LEFT ? fc[j] * n2 + k2 : k1 * (unsigned)a.nin2 + fr[j]]);
-            sx += ev[j] * w.x;
-            sy += ev[j] * w.y;
-          }
-          ax[r] += t0 * sx + t1 * sy;
-          ay[r] += t2 * sx + t3 * sy;
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < kIoRows; ++r) {
-    if (r < nr) {
-      const size_t o = (size_t)(r0 + r) * n2 + k2;
-      if (a.accumulate) {
-        const CP y = load2<T>(a.y, o);
-        put2(a.y, o, y.x + ax[r], y.y + ay[r]);
-      } else {
-        put2(a.y, o, ax[r], ay[r]);
-      }
-    }
-  }
-}
-
 }  // namespace
 
 template <typename T>
@@ -209,13 +146,6 @@ cudaError_t launch_final(FinalArgs<T>& a, bool left, cudaStream_t s) {
   if (a.n1 <= 0 || a.n2 <= 0) return cudaSuccess;
   if (a.nin2 <= 0) a.nin2 = a.n2;
   unsigned b = 0;
-  if (a.io) {
-    a.ch = a.ch <= 0 ? kIoRows : (a.ch > kIoRows ? kIoRows : a.ch);
-    if (!launch_shape(a.n1, a.n2, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
-    if (left) { SG_SWEEP_DISPATCH(k_final_io, T, true, a.row, kMaxFinalRow, b, kThreads, 0, s) }
-    else { SG_SWEEP_DISPATCH(k_final_io, T, false, a.row, kMaxFinalRow, b, kThreads, 0, s) }
-    return cudaGetLastError();
-  }
   if (a.pair) {
     // left: column pairs (32 per 64 columns); right: row pairs (ch even)
     if (!left && (a.ch <= 0 || a.ch % 2)) a.ch = a.ch <= 0 ? 2 : a.ch + 1;
