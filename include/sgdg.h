@@ -305,11 +305,10 @@ sgdg_status sgdg_mlp_set_params(void* mlp, const float* params);
 sgdg_status sgdg_autotune(void* h, const void* u, void* y, int precision, void* stream);
 /* Pins every sweep launch site of later applies to one launch shape,
  * code = rows per thread (1..15) | block order << 4 (0 row-major, 1 column
- * tiles) | two outputs per thread (final kernels, short-row chain steps)
- * << 5 | the next chain's factor row loaded ahead in paired chain steps
- * << 6; code 0 returns to the tuned or default shapes (sgdg_autotune also
- * clears the pin).  For tests and measurements: a shape changes the thread
- * mapping, never the values.  Other codes: SGDG_EINVAL. */
+ * tiles) | two outputs per thread in the final kernels << 5; code 0 returns
+ * to the tuned or default shapes (sgdg_autotune also clears the pin).  For
+ * tests and measurements: a shape changes the thread mapping, never the
+ * values.  Other codes: SGDG_EINVAL. */
 sgdg_status sgdg_set_launch_shape(void* h, int code);
 
 /* Batches of independent problems (many instances of uneven L, Sect. 5's

@@ -124,14 +124,12 @@ inline long long site_key(int kind, int n1, int n2, int count, int elem) {
 }
 
 // Launch shape of a site: rows per thread (ch, 0 = heuristic), block order
-// (tiled), two outputs per thread (pair; final kernels and short-row mode-A
-// chain steps) and, for paired chain steps, the next chain's factor row
-// loaded ahead (deep).  Tuned choices are stored as
-// ch | tiled << 4 | pair << 5 | deep << 6.  Untuned sites take the column
-// tiles when the launch's stencil runs along dim 1 and rows are long enough
-// to fill a tile.
+// (tiled) and, for the final kernels, two outputs per thread (pair).  Tuned
+// choices are stored as ch | tiled << 4 | pair << 5.  Untuned sites take the
+// column tiles when the launch's stencil runs along dim 1 and rows are long
+// enough to fill a tile.
 struct Shape {
-  int ch = 0, tiled = 0, pair = 0, deep = 0;
+  int ch = 0, tiled = 0, pair = 0;
 };
 
 template <typename T>
@@ -146,7 +144,6 @@ Shape pick_shape(Handle& h, long long site, bool dim1_stencil, int n1, int n2) {
     sh.ch = std::min(code & 15, n1);
     sh.tiled = (code >> 4) & 1;
     sh.pair = (code >> 5) & 1;
-    sh.deep = (code >> 6) & 1;
   } else {
     sh.tiled = dim1_stencil && n2 >= kTileW ? 1 : 0;
   }
@@ -201,7 +198,6 @@ Status run_chain(Handle& h, ChainArgs<T>& a, bool mode_a, int kind, cudaStream_t
   a.ch = sh.ch;
   a.tiled = sh.tiled;
   a.pair = sh.pair;
-  a.deep = sh.deep;
   ProfScope ps(h, s);
   SG_CU(launch_chain(a, mode_a, s));
   ps.done(kind, in_bytes + a.nchains * grid_bytes<T>(a.n1, a.n2), site,
@@ -522,14 +518,11 @@ Status nodal_eval(Handle& h, const double* u, double* out, cudaStream_t s) {
 
 template <typename T>
 Status autotune(Handle& h, const Store<T>* u, Store<T>* y, cudaStream_t s) {
-  // rows per thread x block order x paired outputs (x factor rows loaded
-  // ahead in paired chain steps), encoded as ch | tiled << 4 | pair << 5 | deep << 6
+  // rows per thread x block order x paired outputs, encoded as ch | tiled << 4 | pair << 5
   std::vector<int> cand;
   for (int pair = 0; pair < 2; ++pair)
     for (int tiled = 0; tiled < 2; ++tiled)
       for (int ch : {1, 2, 4, 8}) cand.push_back(ch | tiled << 4 | pair << 5);
-  for (int tiled = 0; tiled < 2; ++tiled)
-    for (int ch : {2, 4, 8}) cand.push_back(ch | tiled << 4 | 1 << 5 | 1 << 6);
   std::map<long long, std::pair<float, int>> best;
   const bool prof_was = h.prof;
   for (int c : cand) {

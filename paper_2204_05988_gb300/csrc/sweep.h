@@ -84,7 +84,6 @@ struct ChainArgs {
   int nchains = 0, has_prev = 0, ch = 0, row = 8;
   int tiled = 0;
   int pair = 0;   // mode A, rows of at most 8: two rows per thread
-  int deep = 0;   // with pair: the next chain's factor row loaded ahead
   const Store<T>* U = nullptr;
   const int* f_col = nullptr;    // ELL
   const Comp<T>* f_val[kChainSlots] = {};

@@ -102,12 +102,10 @@ __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, MODE_A>::blocks
 // Mode A with rows of at most 8 entries, two rows (k1, k1 + 1) per thread:
 // the factor row k2 is loaded once per chain for both rows (the
 // diagonal-block products W_b = U V_b^T, and S_b = W_b + P1 Q_b); the next
-// chain's Q values are loaded before the current chain is combined.  DEEP
-// also loads the next chain's factor row ahead (more loads in flight per
-// thread, fewer resident blocks: 2 per SM).
-template <typename T, bool DEEP, int ROW>
-__global__ void __launch_bounds__(kThreads, (DEEP || sizeof(Comp<T>) != 4 ? 2 : 3)) k_chain_pair(const __grid_constant__ ChainArgs<T> a) {
-  static_assert(ROW <= 8, "row pairs: mode A, short rows");
+// chain's Q values are loaded before the current chain is combined.
+template <typename T, bool MODE_A, int ROW>
+__global__ void __launch_bounds__(kThreads, (sizeof(Comp<T>) == 4 ? 3 : 2)) k_chain_pair(const __grid_constant__ ChainArgs<T> a) {
+  static_assert(MODE_A && ROW <= 8, "row pairs: mode A, short rows");
   using C = Comp<T>;
   using CP = C2<T>;
   constexpr int W = Ell<ROW>::W;
@@ -151,24 +149,16 @@ __global__ void __launch_bounds__(kThreads, (DEEP || sizeof(Comp<T>) != 4 ? 2 : 
       gather<T>(a.Z[0], zoa, za);
       gather<T>(a.Z[0], zob, zb);
     }
-    C nv[ROW];
-    if (DEEP) ell_vals<ROW>(a.f_val[0] + frow, nv);
     for (int g = 0; g < a.nchains; ++g) {
       C cv[ROW];
       CP cza[kProlongRow], czb[kProlongRow];
-      if (DEEP) {
-#pragma unroll
-        for (int j = 0; j < ROW; ++j) cv[j] = nv[j];
-      } else {
-        ell_vals<ROW>(a.f_val[g] + frow, cv);
-      }
+      ell_vals<ROW>(a.f_val[g] + frow, cv);
 #pragma unroll
       for (int q = 0; q < kProlongRow; ++q) {
         cza[q] = za[q];
         czb[q] = zb[q];
       }
       if (g + 1 < a.nchains) {
-        if (DEEP) ell_vals<ROW>(a.f_val[g + 1] + frow, nv);
         if (a.has_prev) {
           gather<T>(a.Z[g + 1], zoa, za);
           gather<T>(a.Z[g + 1], zob, zb);
@@ -209,8 +199,7 @@ cudaError_t launch_chain(ChainArgs<T>& a, bool mode_a, cudaStream_t s) {
   if (a.pair && mode_a && a.row <= 8) {
     if (a.ch <= 0 || a.ch % 2) a.ch = a.ch <= 0 ? 2 : a.ch + 1;
     if (!launch_shape(a.n1, a.n2, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
-    if (a.deep) { SG_SWEEP_DISPATCH(k_chain_pair, T, true, a.row, 8, b, kThreads, 0, s) }
-    else { SG_SWEEP_DISPATCH(k_chain_pair, T, false, a.row, 8, b, kThreads, 0, s) }
+    SG_SWEEP_DISPATCH(k_chain_pair, T, true, a.row, 8, b, kThreads, 0, s)
     return cudaGetLastError();
   }
   if (!launch_shape(a.n1, a.n2, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
