@@ -123,7 +123,8 @@ struct Handle {
   struct KEvent { int kind; double bytes; cudaEvent_t e0, e1; long long site; double flops = 0.0; };
   std::vector<KEvent> kev;
   // autotuner: launch shape per launch site (kind and grid shape), stored as
-  // rows per thread | block order << 4 | paired outputs << 5; force_ch > 0
+  // rows per thread | block order << 4 | paired outputs << 5 | L2 prefetch
+  // hints << 6; force_ch > 0
   // overrides every site while tuning
   std::map<long long, int> tuned_ch;
   int force_ch = 0;

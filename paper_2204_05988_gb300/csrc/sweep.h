@@ -84,6 +84,7 @@ struct ChainArgs {
   int nchains = 0, has_prev = 0, ch = 0, row = 8;
   int tiled = 0;
   int pair = 0;   // mode A, rows of at most 8: two rows per thread
+  int pf = 0;     // L2 prefetch hints for the operands of the chain after next
   const Store<T>* U = nullptr;
   const int* f_col = nullptr;    // ELL
   const Comp<T>* f_val[kChainSlots] = {};
@@ -102,6 +103,7 @@ template <typename T>
 struct FinalArgs {
   int n1 = 0, n2 = 0, nin2 = 0, ch = 0, row = 8, accumulate = 0, tiled = 0;
   int pair = 0;   // two outputs per thread: left - columns k2, k2 + 32; right - rows k1, k1 + 1
+  int pf = 0;     // L2 prefetch hints for the gathers of an input ahead of its loads
   int nin = 0, nterms = 0;
   const Store<T>* in[kFinalIn] = {};
   int tbeg[kFinalIn + 1] = {};

@@ -23,8 +23,11 @@ struct ChainBounds {
   static constexpr int blocks = sizeof(Comp<T>) == 4 ? (ROW > 8 ? (MODE_A ? 2 : 3) : 4) : 2;
 };
 
-template <typename T, bool MODE_A, int ROW>
-__global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, MODE_A>::blocks)) k_chain(const __grid_constant__ ChainArgs<T> a) {
+// MODE: bit 0 - mode A (else B); bit 1 - L2 prefetch hints for the factor
+// row and Q values of the chain after next
+template <typename T, int MODE, int ROW>
+__global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, (MODE & 1) != 0>::blocks)) k_chain(const __grid_constant__ ChainArgs<T> a) {
+  constexpr bool MODE_A = MODE & 1, PF = (MODE & 2) != 0;
   using C = Comp<T>;
   using CP = C2<T>;
   constexpr int W = Ell<ROW>::W;
@@ -80,6 +83,13 @@ __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, MODE_A>::blocks
         if (kPrefetch) ell_vals<ROW>(a.f_val[g + 1] + frow, fv);
         if (a.has_prev) gather<T>(a.Z[g + 1], zo, z);
       }
+      if (PF && g + 2 < a.nchains) {
+        prefetch_l2(a.f_val[g + 2] + frow);
+        if (a.has_prev) {
+#pragma unroll
+          for (int q = 0; q < kProlongRow; ++q) prefetch_l2(reinterpret_cast<const S2<T>*>(a.Z[g + 2]) + zo[q]);
+        }
+      }
       if (!kPrefetch) ell_vals<ROW>(a.f_val[g] + frow, cv);
       C zx = 0, zy = 0;
       if (a.has_prev) {
@@ -103,9 +113,12 @@ __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, MODE_A>::blocks
 // the factor row k2 is loaded once per chain for both rows (the
 // diagonal-block products W_b = U V_b^T, and S_b = W_b + P1 Q_b); the next
 // chain's Q values are loaded before the current chain is combined.
-template <typename T, bool MODE_A, int ROW>
+// MODE: bit 0 set (mode A); bit 1 - L2 prefetch hints for the factor row
+// of the next chain and the Q values of the chain after next
+template <typename T, int MODE, int ROW>
 __global__ void __launch_bounds__(kThreads, (sizeof(Comp<T>) == 4 ? 3 : 2)) k_chain_pair(const __grid_constant__ ChainArgs<T> a) {
-  static_assert(MODE_A && ROW <= 8, "row pairs: mode A, short rows");
+  static_assert((MODE & 1) && ROW <= 8, "row pairs: mode A, short rows");
+  constexpr bool PF = (MODE & 2) != 0;
   using C = Comp<T>;
   using CP = C2<T>;
   constexpr int W = Ell<ROW>::W;
@@ -159,9 +172,18 @@ __global__ void __launch_bounds__(kThreads, (sizeof(Comp<T>) == 4 ? 3 : 2)) k_ch
         czb[q] = zb[q];
       }
       if (g + 1 < a.nchains) {
+        if (PF) prefetch_l2(a.f_val[g + 1] + frow);
         if (a.has_prev) {
           gather<T>(a.Z[g + 1], zoa, za);
           gather<T>(a.Z[g + 1], zob, zb);
+        }
+      }
+      if (PF && a.has_prev && g + 2 < a.nchains) {
+        const S2<T>* zn = reinterpret_cast<const S2<T>*>(a.Z[g + 2]);
+#pragma unroll
+        for (int q = 0; q < kProlongRow; ++q) {
+          prefetch_l2(zn + zoa[q]);
+          prefetch_l2(zn + zob[q]);
         }
       }
       C ax = 0, ay = 0, bx = 0, by = 0;
@@ -199,12 +221,17 @@ cudaError_t launch_chain(ChainArgs<T>& a, bool mode_a, cudaStream_t s) {
   if (a.pair && mode_a && a.row <= 8) {
     if (a.ch <= 0 || a.ch % 2) a.ch = a.ch <= 0 ? 2 : a.ch + 1;
     if (!launch_shape(a.n1, a.n2, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
-    SG_SWEEP_DISPATCH(k_chain_pair, T, true, a.row, 8, b, kThreads, 0, s)
+    if (a.pf) { SG_SWEEP_DISPATCH(k_chain_pair, T, 3, a.row, 8, b, kThreads, 0, s) }
+    else { SG_SWEEP_DISPATCH(k_chain_pair, T, 1, a.row, 8, b, kThreads, 0, s) }
     return cudaGetLastError();
   }
   if (!launch_shape(a.n1, a.n2, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
-  if (mode_a) { SG_SWEEP_DISPATCH(k_chain, T, true, a.row, kMaxChainRow, b, kThreads, 0, s) }
-  else { SG_SWEEP_DISPATCH(k_chain, T, false, a.row, kMaxChainRow, b, kThreads, 0, s) }
+  switch ((mode_a ? 1 : 0) | (a.pf ? 2 : 0)) {
+    case 0: SG_SWEEP_DISPATCH(k_chain, T, 0, a.row, kMaxChainRow, b, kThreads, 0, s) break;
+    case 1: SG_SWEEP_DISPATCH(k_chain, T, 1, a.row, kMaxChainRow, b, kThreads, 0, s) break;
+    case 2: SG_SWEEP_DISPATCH(k_chain, T, 2, a.row, kMaxChainRow, b, kThreads, 0, s) break;
+    default: SG_SWEEP_DISPATCH(k_chain, T, 3, a.row, kMaxChainRow, b, kThreads, 0, s) break;
+  }
   return cudaGetLastError();
 }
 

@@ -147,6 +147,10 @@ __device__ __forceinline__ void prolong_row(const int* col, const T* val, unsign
   v[1] = __ldg(val + 2 * (size_t)r + 1);
 }
 
+// Hint: bring the L2 line holding p on chip ahead of its load (holds no
+// register, never waits; the address is one the thread loads later).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // pairs off[j] of a grid array, widened to the arithmetic type
 template <typename T, int N>
 __device__ __forceinline__ void gather(const Store<T>* base, const unsigned (&off)[N], C2<T> (&w)[N]) {

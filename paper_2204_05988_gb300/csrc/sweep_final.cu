@@ -12,8 +12,10 @@ namespace {
 
 using namespace sweep;
 
-template <typename T, bool LEFT, int ROW>
+// MODE: bit 0 - left (dim 1) or right (dim 2); bit 1 - L2 prefetch hints
+template <typename T, int MODE, int ROW>
 __global__ void __launch_bounds__(kThreads) k_final(const __grid_constant__ FinalArgs<T> a) {
+  constexpr bool LEFT = MODE & 1, PF = (MODE & 2) != 0;
   using C = Comp<T>;
   using CP = C2<T>;
   constexpr int W = Ell<ROW>::W;
@@ -38,6 +40,10 @@ __global__ void __launch_bounds__(kThreads) k_final(const __grid_constant__ Fina
 #pragma unroll
       for (int j = 0; j < ROW; ++j) cw[j] = w[j];
       if (ci + 1 < a.nin) gather<T>(a.in[ci + 1], off, w);
+      if (PF && ci + 2 < a.nin) {
+#pragma unroll
+        for (int j = 0; j < ROW; ++j) prefetch_l2(reinterpret_cast<const S2<T>*>(a.in[ci + 2]) + off[j]);
+      }
       for (int t = a.tbeg[ci]; t < a.tbeg[ci + 1]; ++t) {
         C ev[ROW];
         ell_vals<ROW>(a.val[t] + frow, ev);
@@ -64,8 +70,9 @@ __global__ void __launch_bounds__(kThreads) k_final(const __grid_constant__ Fina
 // time coupling: left - columns k2 and k2 + 32 of one row (the warp covers
 // 64 consecutive columns, both loads coalesced); right - rows k1 and k1 + 1
 // of one column.
-template <typename T, bool LEFT, int ROW>
+template <typename T, int MODE, int ROW>
 __global__ void __launch_bounds__(kThreads, sizeof(Comp<T>) == 4 ? 4 : 2) k_final2(const __grid_constant__ FinalArgs<T> a) {
+  constexpr bool LEFT = MODE & 1, PF = (MODE & 2) != 0;
   using C = Comp<T>;
   using CP = C2<T>;
   constexpr int W = Ell<ROW>::W;
@@ -91,6 +98,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(Comp<T>) == 4 ? 4 : 2) k_fina
     C ax = 0, ay = 0, bx = 0, by = 0;
     for (int ci = 0; ci < a.nin; ++ci) {
       const S2<T>* in = reinterpret_cast<const S2<T>*>(a.in[ci]);
+      if (PF && ci + 1 < a.nin) {
+        const S2<T>* nx = reinterpret_cast<const S2<T>*>(a.in[ci + 1]);
+#pragma unroll
+        for (int j = 0; j < ROW; ++j) {
+          prefetch_l2(nx + off[j]);
+          if (b_ok) prefetch_l2(nx + off[j] + step_b);
+        }
+      }
       CP wa[ROW], wb[ROW];
 #pragma unroll
       for (int j = 0; j < ROW; ++j) {
@@ -151,13 +166,21 @@ cudaError_t launch_final(FinalArgs<T>& a, bool left, cudaStream_t s) {
     if (!left && (a.ch <= 0 || a.ch % 2)) a.ch = a.ch <= 0 ? 2 : a.ch + 1;
     const int ncol = left ? (a.n2 + 63) / 64 * 32 : a.n2;
     if (!launch_shape(a.n1, ncol, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
-    if (left) { SG_SWEEP_DISPATCH(k_final2, T, true, a.row, kMaxFinalRow, b, kThreads, 0, s) }
-    else { SG_SWEEP_DISPATCH(k_final2, T, false, a.row, kMaxFinalRow, b, kThreads, 0, s) }
+    switch ((left ? 1 : 0) | (a.pf ? 2 : 0)) {
+      case 0: SG_SWEEP_DISPATCH(k_final2, T, 0, a.row, kMaxFinalRow, b, kThreads, 0, s) break;
+      case 1: SG_SWEEP_DISPATCH(k_final2, T, 1, a.row, kMaxFinalRow, b, kThreads, 0, s) break;
+      case 2: SG_SWEEP_DISPATCH(k_final2, T, 2, a.row, kMaxFinalRow, b, kThreads, 0, s) break;
+      default: SG_SWEEP_DISPATCH(k_final2, T, 3, a.row, kMaxFinalRow, b, kThreads, 0, s) break;
+    }
     return cudaGetLastError();
   }
   if (!launch_shape(a.n1, a.n2, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
-  if (left) { SG_SWEEP_DISPATCH(k_final, T, true, a.row, kMaxFinalRow, b, kThreads, 0, s) }
-  else { SG_SWEEP_DISPATCH(k_final, T, false, a.row, kMaxFinalRow, b, kThreads, 0, s) }
+  switch ((left ? 1 : 0) | (a.pf ? 2 : 0)) {
+    case 0: SG_SWEEP_DISPATCH(k_final, T, 0, a.row, kMaxFinalRow, b, kThreads, 0, s) break;
+    case 1: SG_SWEEP_DISPATCH(k_final, T, 1, a.row, kMaxFinalRow, b, kThreads, 0, s) break;
+    case 2: SG_SWEEP_DISPATCH(k_final, T, 2, a.row, kMaxFinalRow, b, kThreads, 0, s) break;
+    default: SG_SWEEP_DISPATCH(k_final, T, 3, a.row, kMaxFinalRow, b, kThreads, 0, s) break;
+  }
   return cudaGetLastError();
 }
 
