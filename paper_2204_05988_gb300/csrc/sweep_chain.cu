@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, (MODE & 1) != 0
 // diagonal-block products W_b = U V_b^T, and S_b = W_b + P1 Q_b); the next
 // chain's Q values are loaded before the current chain is combined.
 // MODE: bit 0 set (mode A); bit 1 - L2 prefetch hints for the factor row
-// and the Q values of the chain after next
+// of the next chain and the Q values of the chain after next
 template <typename T, int MODE, int ROW>
 __global__ void __launch_bounds__(kThreads, (sizeof(Comp<T>) == 4 ? 3 : 2)) k_chain_pair(const __grid_constant__ ChainArgs<T> a) {
   static_assert((MODE & 1) && ROW <= 8, "row pairs: mode A, short rows");
@@ -172,20 +172,18 @@ __global__ void __launch_bounds__(kThreads, (sizeof(Comp<T>) == 4 ? 3 : 2)) k_ch
         czb[q] = zb[q];
       }
       if (g + 1 < a.nchains) {
+        if (PF) prefetch_l2(a.f_val[g + 1] + frow);
         if (a.has_prev) {
           gather<T>(a.Z[g + 1], zoa, za);
           gather<T>(a.Z[g + 1], zob, zb);
         }
       }
-      if (PF && g + 2 < a.nchains) {
-        prefetch_l2(a.f_val[g + 2] + frow);
-        if (a.has_prev) {
-          const S2<T>* zn = reinterpret_cast<const S2<T>*>(a.Z[g + 2]);
+      if (PF && a.has_prev && g + 2 < a.nchains) {
+        const S2<T>* zn = reinterpret_cast<const S2<T>*>(a.Z[g + 2]);
 #pragma unroll
-          for (int q = 0; q < kProlongRow; ++q) {
-            prefetch_l2(zn + zoa[q]);
-            prefetch_l2(zn + zob[q]);
-          }
+        for (int q = 0; q < kProlongRow; ++q) {
+          prefetch_l2(zn + zoa[q]);
+          prefetch_l2(zn + zob[q]);
         }
       }
       C ax = 0, ay = 0, bx = 0, by = 0;
