@@ -124,6 +124,38 @@ class Clocks:
                 "samples": len(sm)}
 
 
+class Ranks:
+    """The replicas of a multi-GPU run: one process per GPU under torchrun,
+    each with its own problem instance and no data-path collective.  Barrier
+    and max-over-ranks reductions of timings on `device` (NCCL on the GPUs;
+    gloo on the host cores in the tests).  dist None: a single process."""
+
+    def __init__(self, dist=None, device="cpu"):
+        self.dist = dist
+        self.device = device
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+        if str(self.device).startswith("cuda"):
+            import torch
+            torch.cuda.synchronize()
+
+    def max(self, x: float) -> float:
+        if not self.dist:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def whole_job(world: int, units_per_rank: float, seconds: float) -> float:
+    """Weak scaling: every rank processes units_per_rank; `seconds` is the
+    slowest rank's time, so the job's rate is world x units / seconds."""
+    return world * units_per_rank / seconds
+
+
 def cpu_baseline(steps: int = 4, L: int = 5):
     """The oracle's blockwise apply (Sect. 4.2) on the host cores, as it stands,
     on a bounded sample of the same workload family (d = 2, level L)."""
@@ -196,10 +228,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    def barrier():
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
+    ranks = Ranks(dist, "cuda")
+    barrier = ranks.barrier
 
     prob = W.transport_2d(L=args.L, sigma=0.1)
     t0 = time.perf_counter()
@@ -234,12 +264,7 @@ def main():
             fn()
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1) / K
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return ranks.max(e0.elapsed_time(e1) / K)
 
     # ---- FP32 apply (headline), clocks sampled during the timed region
     for _ in range(args.warmup):
@@ -255,7 +280,7 @@ def main():
         # ---- BF16-storage apply
         ms16 = timed(lambda: s.apply_operator(u16, y16, P.SGDG_BF16_STORE, stream), args.steps, 1)
     clocks = clk.summary()
-    value = world * n / (ms32 * 1e-3) / 1e9
+    value = whole_job(world, n, ms32 * 1e-3) / 1e9
 
     # errors of the reduced precisions against the FP64 apply of the same input
     # (the FP64 path matches the oracle to 1e-12)
@@ -319,7 +344,7 @@ def main():
                                  for k, v in roof["f64"].items() if v["launches"]}}
     st16 = roof["bf16"]
     dom16 = max(st16, key=lambda k: st16[k]["ms"])
-    bf16_apply = {"value": world * n / (ms16 * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms16,
+    bf16_apply = {"value": whole_job(world, n, ms16 * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms16,
                   "storage": "bfloat16 grid arrays, FP32 arithmetic and matrix values",
                   "rel_err_vs_fp64": err16,
                   "roofline": {"bound": "hbm", "kernel": dom16,
@@ -348,12 +373,8 @@ def main():
         s.apply_operator_host(hu, hy, P.SGDG_MIXED_FP32)
         per.append(time.perf_counter() - te)
     barrier()
-    e2e_s = float(np.median(per))
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * n / e2e_s / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * n,
+    e2e_s = ranks.max(float(np.median(per)))
+    e2e = {"value": whole_job(world, n, e2e_s) / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * n,
            "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_s * 1e3, "statistic": f"median of {ke} calls",
            "ms_per_call": [round(x * 1e3, 2) for x in per]}
     s.close()
@@ -448,7 +469,7 @@ def main():
                            "v_factors": s.info.n_v_factors, "l2": "inputs larger than L2 (493 MB f32)",
                            "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
                            "autotune_s": round(tune_s, 2)},
-                "fp64_apply": {"value": world * n / (ms64 * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms64,
+                "fp64_apply": {"value": whole_job(world, n, ms64 * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms64,
                                "roofline": fp64_roof},
                 "bf16_apply": bf16_apply,
                 "rel_err_vs_fp64_apply": {"f32": err32, "bf16_storage": err16},
