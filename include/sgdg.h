@@ -298,8 +298,7 @@ sgdg_status sgdg_mlp_set_params(void* mlp, const float* params);
 
 /* Autotuner (no counterpart in the paper): times candidate launch shapes
  * (rows per thread in {1,2,4,8} x row-major or column-tiled block order x one
- * or two outputs per thread x with or without L2 prefetch hints, and with the
- * hints also streaming chain stores) of
+ * or two outputs per thread x with or without L2 prefetch hints) of
  * every sweep launch site on live applies y = A u (device arrays as for
  * sgdg_apply_operator, overwritten) and keeps the fastest per site for all
  * later applies of this handle. */
@@ -308,8 +307,8 @@ sgdg_status sgdg_autotune(void* h, const void* u, void* y, int precision, void* 
  * code = rows per thread (1..15) | block order << 4 (0 row-major, 1 column
  * tiles) | two outputs per thread (final kernels, short-row chain steps) << 5
  * | L2 prefetch hints for operands a step ahead (final and chain kernels)
- * << 6 | streaming (evict-first) stores of the chain outputs << 7; code 0
- * returns to the tuned or default shapes (sgdg_autotune also clears the pin).  For tests and measurements: a shape changes the thread
+ * << 6; code 0 returns to the tuned or default shapes (sgdg_autotune also
+ * clears the pin).  For tests and measurements: a shape changes the thread
  * mapping and the prefetching, never the values.  Other codes: SGDG_EINVAL. */
 sgdg_status sgdg_set_launch_shape(void* h, int code);
 

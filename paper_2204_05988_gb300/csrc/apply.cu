@@ -125,13 +125,13 @@ inline long long site_key(int kind, int n1, int n2, int count, int elem) {
 
 // Launch shape of a site: rows per thread (ch, 0 = heuristic), block order
 // (tiled), two outputs per thread (pair: final kernels and short-row mode-A
-// chain steps), L2 prefetch hints for operands a step ahead (pf: final and
-// chain kernels) and streaming stores of the chain outputs (cs).  Tuned
-// choices are stored as ch | tiled << 4 | pair << 5 | pf << 6 | cs << 7.
-// Untuned sites take the column tiles when the launch's stencil runs along
-// dim 1 and rows are long enough to fill a tile.
+// chain steps) and L2 prefetch hints for operands a step ahead (pf: final
+// and chain kernels).  Tuned choices are stored as
+// ch | tiled << 4 | pair << 5 | pf << 6.  Untuned sites take the column tiles
+// when the launch's stencil runs along dim 1 and rows are long enough to fill
+// a tile.
 struct Shape {
-  int ch = 0, tiled = 0, pair = 0, pf = 0, cs = 0;
+  int ch = 0, tiled = 0, pair = 0, pf = 0;
 };
 
 template <typename T>
@@ -147,7 +147,6 @@ Shape pick_shape(Handle& h, long long site, bool dim1_stencil, int n1, int n2) {
     sh.tiled = (code >> 4) & 1;
     sh.pair = (code >> 5) & 1;
     sh.pf = (code >> 6) & 1;
-    sh.cs = (code >> 7) & 1;
   } else {
     sh.tiled = dim1_stencil && n2 >= kTileW ? 1 : 0;
   }
@@ -203,7 +202,6 @@ Status run_chain(Handle& h, ChainArgs<T>& a, bool mode_a, int kind, cudaStream_t
   a.tiled = sh.tiled;
   a.pair = sh.pair;
   a.pf = sh.pf;
-  a.cs = sh.cs;
   ProfScope ps(h, s);
   SG_CU(launch_chain(a, mode_a, s));
   ps.done(kind, in_bytes + a.nchains * grid_bytes<T>(a.n1, a.n2), site,
@@ -525,17 +523,13 @@ Status nodal_eval(Handle& h, const double* u, double* out, cudaStream_t s) {
 
 template <typename T>
 Status autotune(Handle& h, const Store<T>* u, Store<T>* y, cudaStream_t s) {
-  // rows per thread x block order x paired outputs x L2 prefetch hints
-  // (x streaming chain stores, with the hints), encoded as
-  // ch | tiled << 4 | pair << 5 | pf << 6 | cs << 7
+  // rows per thread x block order x paired outputs x L2 prefetch hints,
+  // encoded as ch | tiled << 4 | pair << 5 | pf << 6
   std::vector<int> cand;
   for (int pf = 0; pf < 2; ++pf)
     for (int pair = 0; pair < 2; ++pair)
       for (int tiled = 0; tiled < 2; ++tiled)
         for (int ch : {1, 2, 4, 8}) cand.push_back(ch | tiled << 4 | pair << 5 | pf << 6);
-  for (int pair = 0; pair < 2; ++pair)
-    for (int tiled = 0; tiled < 2; ++tiled)
-      for (int ch : {1, 2, 4, 8}) cand.push_back(ch | tiled << 4 | pair << 5 | 1 << 6 | 1 << 7);
   std::map<long long, std::pair<float, int>> best;
   const bool prof_was = h.prof;
   for (int c : cand) {

@@ -725,8 +725,8 @@ sgdg_status sgdg_get_end_value(const void* hp, double* dst, int on_device) {
 sgdg_status sgdg_set_launch_shape(void* hp, int code) {
   if (!hp) return SGDG_EINVAL;
   Handle* h = (Handle*)hp;
-  if (code < 0 || code > 255 || (code > 0 && (code & 15) == 0))
-    return fail(h, {SGDG_EINVAL, "launch shape code: rows per thread 1..15, flags in bits 4..7"});
+  if (code < 0 || code > 127 || (code > 0 && (code & 15) == 0))
+    return fail(h, {SGDG_EINVAL, "launch shape code: rows per thread 1..15, flags in bits 4..6"});
   h->force_ch = code;
   return SGDG_OK;
 }

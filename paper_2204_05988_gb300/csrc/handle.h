@@ -124,7 +124,7 @@ struct Handle {
   std::vector<KEvent> kev;
   // autotuner: launch shape per launch site (kind and grid shape), stored as
   // rows per thread | block order << 4 | paired outputs << 5 | L2 prefetch
-  // hints << 6 | streaming chain stores << 7; force_ch > 0
+  // hints << 6; force_ch > 0
   // overrides every site while tuning
   std::map<long long, int> tuned_ch;
   int force_ch = 0;

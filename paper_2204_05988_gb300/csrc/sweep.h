@@ -85,7 +85,6 @@ struct ChainArgs {
   int tiled = 0;
   int pair = 0;   // mode A, rows of at most 8: two rows per thread
   int pf = 0;     // L2 prefetch hints for the operands of the chain after next
-  int cs = 0;     // streaming (evict-first) stores of the chain outputs
   const Store<T>* U = nullptr;
   const int* f_col = nullptr;    // ELL
   const Comp<T>* f_val[kChainSlots] = {};

@@ -24,10 +24,10 @@ struct ChainBounds {
 };
 
 // MODE: bit 0 - mode A (else B); bit 1 - L2 prefetch hints for the factor
-// row and Q values of the chain after next; bit 2 - streaming stores
+// row and Q values of the chain after next
 template <typename T, int MODE, int ROW>
 __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, (MODE & 1) != 0>::blocks)) k_chain(const __grid_constant__ ChainArgs<T> a) {
-  constexpr bool MODE_A = MODE & 1, PF = (MODE & 2) != 0, CS = (MODE & 4) != 0;
+  constexpr bool MODE_A = MODE & 1, PF = (MODE & 2) != 0;
   using C = Comp<T>;
   using CP = C2<T>;
   constexpr int W = Ell<ROW>::W;
@@ -104,8 +104,7 @@ __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, (MODE & 1) != 0
         zx += cv[j] * u[j].x;
         zy += cv[j] * u[j].y;
       }
-      if (CS) put2_cs(a.out[g], o, zx, zy);
-      else put2(a.out[g], o, zx, zy);
+      put2(a.out[g], o, zx, zy);
     }
   }
 }
@@ -115,12 +114,11 @@ __global__ void __launch_bounds__(kThreads, (ChainBounds<T, ROW, (MODE & 1) != 0
 // diagonal-block products W_b = U V_b^T, and S_b = W_b + P1 Q_b); the next
 // chain's Q values are loaded before the current chain is combined.
 // MODE: bit 0 set (mode A); bit 1 - L2 prefetch hints for the factor row
-// of the next chain and the Q values of the chain after next; bit 2 -
-// streaming stores
+// of the next chain and the Q values of the chain after next
 template <typename T, int MODE, int ROW>
 __global__ void __launch_bounds__(kThreads, (sizeof(Comp<T>) == 4 ? 3 : 2)) k_chain_pair(const __grid_constant__ ChainArgs<T> a) {
   static_assert((MODE & 1) && ROW <= 8, "row pairs: mode A, short rows");
-  constexpr bool PF = (MODE & 2) != 0, CS = (MODE & 4) != 0;
+  constexpr bool PF = (MODE & 2) != 0;
   using C = Comp<T>;
   using CP = C2<T>;
   constexpr int W = Ell<ROW>::W;
@@ -205,13 +203,8 @@ __global__ void __launch_bounds__(kThreads, (sizeof(Comp<T>) == 4 ? 3 : 2)) k_ch
         bx += cv[j] * ub[j].x;
         by += cv[j] * ub[j].y;
       }
-      if (CS) {
-        put2_cs(a.out[g], o, ax, ay);
-        if (b_ok) put2_cs(a.out[g], o + n2, bx, by);
-      } else {
-        put2(a.out[g], o, ax, ay);
-        if (b_ok) put2(a.out[g], o + n2, bx, by);
-      }
+      put2(a.out[g], o, ax, ay);
+      if (b_ok) put2(a.out[g], o + n2, bx, by);
     }
   }
 }
@@ -228,24 +221,16 @@ cudaError_t launch_chain(ChainArgs<T>& a, bool mode_a, cudaStream_t s) {
   if (a.pair && mode_a && a.row <= 8) {
     if (a.ch <= 0 || a.ch % 2) a.ch = a.ch <= 0 ? 2 : a.ch + 1;
     if (!launch_shape(a.n1, a.n2, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
-    switch ((a.pf ? 2 : 0) | (a.cs ? 4 : 0)) {
-      case 0: SG_SWEEP_DISPATCH(k_chain_pair, T, 1, a.row, 8, b, kThreads, 0, s) break;
-      case 2: SG_SWEEP_DISPATCH(k_chain_pair, T, 3, a.row, 8, b, kThreads, 0, s) break;
-      case 4: SG_SWEEP_DISPATCH(k_chain_pair, T, 5, a.row, 8, b, kThreads, 0, s) break;
-      default: SG_SWEEP_DISPATCH(k_chain_pair, T, 7, a.row, 8, b, kThreads, 0, s) break;
-    }
+    if (a.pf) { SG_SWEEP_DISPATCH(k_chain_pair, T, 3, a.row, 8, b, kThreads, 0, s) }
+    else { SG_SWEEP_DISPATCH(k_chain_pair, T, 1, a.row, 8, b, kThreads, 0, s) }
     return cudaGetLastError();
   }
   if (!launch_shape(a.n1, a.n2, a.ch, a.tiled, b)) return cudaErrorInvalidValue;
-  switch ((mode_a ? 1 : 0) | (a.pf ? 2 : 0) | (a.cs ? 4 : 0)) {
+  switch ((mode_a ? 1 : 0) | (a.pf ? 2 : 0)) {
     case 0: SG_SWEEP_DISPATCH(k_chain, T, 0, a.row, kMaxChainRow, b, kThreads, 0, s) break;
     case 1: SG_SWEEP_DISPATCH(k_chain, T, 1, a.row, kMaxChainRow, b, kThreads, 0, s) break;
     case 2: SG_SWEEP_DISPATCH(k_chain, T, 2, a.row, kMaxChainRow, b, kThreads, 0, s) break;
-    case 3: SG_SWEEP_DISPATCH(k_chain, T, 3, a.row, kMaxChainRow, b, kThreads, 0, s) break;
-    case 4: SG_SWEEP_DISPATCH(k_chain, T, 4, a.row, kMaxChainRow, b, kThreads, 0, s) break;
-    case 5: SG_SWEEP_DISPATCH(k_chain, T, 5, a.row, kMaxChainRow, b, kThreads, 0, s) break;
-    case 6: SG_SWEEP_DISPATCH(k_chain, T, 6, a.row, kMaxChainRow, b, kThreads, 0, s) break;
-    default: SG_SWEEP_DISPATCH(k_chain, T, 7, a.row, kMaxChainRow, b, kThreads, 0, s) break;
+    default: SG_SWEEP_DISPATCH(k_chain, T, 3, a.row, kMaxChainRow, b, kThreads, 0, s) break;
   }
   return cudaGetLastError();
 }

@@ -147,20 +147,6 @@ __device__ __forceinline__ void prolong_row(const int* col, const T* val, unsign
   v[1] = __ldg(val + 2 * (size_t)r + 1);
 }
 
-// store (x, y) as pair p with the evict-first (streaming) cache policy: for
-// outputs written once and read only after the launch, so that they do not
-// push the launch's re-read operands out of L2
-__device__ __forceinline__ void put2_cs(double* g, size_t p, double x, double y) {
-  asm volatile("st.global.cs.v2.f64 [%0], {%1, %2};" ::"l"(g + 2 * p), "d"(x), "d"(y) : "memory");
-}
-__device__ __forceinline__ void put2_cs(float* g, size_t p, float x, float y) {
-  asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(g + 2 * p), "f"(x), "f"(y) : "memory");
-}
-__device__ __forceinline__ void put2_cs(__nv_bfloat16* g, size_t p, float x, float y) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(x, y);
-  asm volatile("st.global.cs.b32 [%0], %1;" ::"l"(g + 2 * p), "r"(*reinterpret_cast<const unsigned*>(&v)) : "memory");
-}
-
 // Hint: bring the L2 line holding p on chip ahead of its load (holds no
 // register, never waits; the address is one the thread loads later).
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }

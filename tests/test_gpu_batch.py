@@ -94,17 +94,16 @@ def test_autotune_keeps_results(P, prec):
     assert err < (1e-12 if prec == "fp64" else 1e-5)
 
 
-_SHAPES = ([ch | tiled << 4 | pair << 5 | pf << 6
-            for pf in (0, 1) for pair in (0, 1) for tiled in (0, 1) for ch in (1, 2, 3, 4, 8)]
-           + [ch | tiled << 4 | pair << 5 | 3 << 6 for pair in (0, 1) for tiled in (0, 1) for ch in (1, 3)])
+_SHAPES = [ch | tiled << 4 | pair << 5 | pf << 6
+           for pf in (0, 1) for pair in (0, 1) for tiled in (0, 1) for ch in (1, 2, 3, 4, 8)]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 @pytest.mark.parametrize("case", ["d2_L4", "d1_L6"])
 def test_every_launch_shape_gives_the_same_values(P, prec, case):
     """Every launch shape the autotuner can pick (rows per thread, block
-    order, paired outputs, L2 prefetch hints, streaming chain stores), and a
-    ragged rows-per-thread, pinned on all sites at once:
+    order, paired outputs, L2 prefetch hints), and a ragged rows-per-thread,
+    pinned on all sites at once:
     the values are those of the default shapes, bit for bit, and match the
     oracle."""
     from oracle.operator import SparseGridOperator
@@ -132,5 +131,5 @@ def test_every_launch_shape_gives_the_same_values(P, prec, case):
     with pytest.raises(P.SgdgError):
         s.set_launch_shape(16)
     with pytest.raises(P.SgdgError):
-        s.set_launch_shape(256)
+        s.set_launch_shape(128)
     s.close()
