@@ -178,8 +178,8 @@ sgdg_status sgdg_create(const sgdg_config* cfg, const sgdg_coeffs* coeffs, void*
 void sgdg_destroy(void* h);
 const char* sgdg_last_error(const void* h);
 sgdg_status sgdg_get_info(const void* h, sgdg_info* out);
-/* Shape and element offset (in doubles/floats of a strip vector, i.e. with
- * the time index) of grid l = (l, L-l). */
+/* Shape and element offset (in elements of a strip vector of any precision,
+ * i.e. with the time index) of grid l = (l, L-l). */
 sgdg_status sgdg_grid_shape(const void* h, int l, int* n1, int* n2, long long* offset);
 
 /* y = A^(delta) u: the strip operator of Eq. 5 on the sparse grid,
@@ -189,13 +189,16 @@ sgdg_status sgdg_grid_shape(const void* h, int l, int* n1, int* n2, long long* o
  * y is overwritten; u and y must not overlap.  Any other precision:
  * SGDG_EINVAL. */
 sgdg_status sgdg_apply_operator(void* h, const void* u, void* y, int precision, void* stream);
-/* Same operator with host arrays (double): copies u to the device, applies
- * in the given precision, copies y back.  Synchronous. */
+/* Same operator with host arrays (double): copies u to the device, rounds
+ * it to the precision's element type there, applies, and copies y back as
+ * double.  Synchronous; pinned host memory gives the full copy rate. */
 sgdg_status sgdg_apply_operator_host(void* h, const double* u, double* y, int precision);
-/* y = (Id_t (x) M_sg) u, the sparse-grid mass matrix on both time slots. */
+/* y = (Id_t (x) M_sg) u, the sparse-grid mass matrix on both time slots;
+ * u, y as for sgdg_apply_operator. */
 sgdg_status sgdg_apply_mass(void* h, const void* u, void* y, int precision, void* stream);
 /* y = A_{l,l} u on one anisotropic full grid (l1, l2) with l1 + l2 in {L-1, L}
- * (the component systems of Eq. 22); arrays [n1][n2][2] on the device. */
+ * (the component systems of Eq. 22); arrays [n1][n2][2] of the precision's
+ * element type on the device. */
 sgdg_status sgdg_apply_diag(void* h, int l1, int l2, const void* u, void* y, int precision, void* stream);
 
 /* The same y = A_{l,l} u as sgdg_apply_diag, from an entry point that
@@ -210,7 +213,8 @@ sgdg_status sgdg_apply_diag(void* h, int l1, int l2, const void* u, void* y, int
  * SGDG_EINVAL and a message naming the size and the limit.  The first call on
  * a device looks up the array's device address; make that first call before
  * any stream capture.  All calls share the array: calls that overlap on the
- * GPU race.  u, y as for sgdg_apply_diag. */
+ * GPU race.  u, y as for sgdg_apply_diag; precision SGDG_FP64 or
+ * SGDG_MIXED_FP32 (others: SGDG_EINVAL). */
 #define SGDG_NOALLOC_SCRATCH_BYTES (64u << 20)
 sgdg_status sgdg_apply_diag_noalloc(void* h, int l1, int l2, const void* u, void* y, int precision,
                                     void* stream);
