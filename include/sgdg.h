@@ -67,6 +67,16 @@ typedef enum {
                            intermediate.  Not a solver precision. */
 } sgdg_precision;
 
+/* Outer iteration of a strip solve; both stop on the FP64 true residual
+ * ||b - A u||_2 <= rtol ||b||_2. */
+typedef enum {
+  SGDG_OUTER_FGMRES = 0,      /* right-preconditioned FGMRES with the CT
+                                 preconditioner (restart, max_outer) */
+  SGDG_OUTER_RICHARDSON = 1   /* Algorithm 1 (Sect. 4.3): u <- u + P_CT(b - A u),
+                                 one CT preconditioner step and one FP64
+                                 apply per iteration, up to max_outer */
+} sgdg_outer;
+
 /* A coarse simplicial mesh of an axis-aligned box (one of Omega_x, Omega_v).
  * coords: [n_vertices][dim]; cells: [n_cells][dim+1] vertex indices.
  * lo/hi: box bounds per axis; periodic: per-axis flag (0/1).  Uniform
@@ -136,7 +146,7 @@ typedef struct {
   double delta;         /* streamline-diffusion parameter (> 0) */
   sgdg_precision precision;
   double rtol;          /* outer stop: ||b - A u||_2 <= rtol ||b||_2 */
-  int max_outer;        /* outer FGMRES iteration cap */
+  int max_outer;        /* outer iteration cap (FGMRES or Richardson steps) */
   int restart;          /* outer FGMRES restart length (<= 64) */
   int inner_its;        /* GMRES iterations per component solve (<= 64) */
   double inner_rtol;    /* early stop of a component solve */
@@ -145,6 +155,7 @@ typedef struct {
   int vlasov_poisson;   /* 1: beta_v = -E(x) with E from a Poisson solve of the
                            density (Sect. 5.3); needs a periodic Omega_x and
                            beta[d+i] = {coef -1, fx = initial E_i, fv = NULL} */
+  int outer_method;     /* sgdg_outer; 0 (zero-initialised): FGMRES */
 } sgdg_config;
 
 typedef struct {

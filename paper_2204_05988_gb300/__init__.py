@@ -22,6 +22,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libsgdg.so")
 SGDG_FP64 = 0
 SGDG_MIXED_FP32 = 1
 SGDG_BF16_STORE = 2   # applies only: grid arrays in bfloat16, FP32 arithmetic
+SGDG_OUTER_FGMRES = 0
+SGDG_OUTER_RICHARDSON = 1   # Algorithm 1: u <- u + P_CT(b - A u)
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENAN", 6: "ETIMEOUT", 7: "EIO"}
 
 FN = C.CFUNCTYPE(None, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
@@ -55,7 +57,7 @@ class Config(C.Structure):
                 ("dt", C.c_double), ("delta", C.c_double), ("precision", C.c_int), ("rtol", C.c_double),
                 ("max_outer", C.c_int), ("restart", C.c_int), ("inner_its", C.c_int),
                 ("inner_rtol", C.c_double), ("cheb_steps", C.c_int), ("device", C.c_int),
-                ("vlasov_poisson", C.c_int)]
+                ("vlasov_poisson", C.c_int), ("outer_method", C.c_int)]
 
 
 class Info(C.Structure):
@@ -183,7 +185,7 @@ class Solver:
 
     def __init__(self, problem, precision: int = SGDG_FP64, rtol: float = 1e-10, max_outer: int = 200,
                  restart: int = 30, inner_its: int = 20, inner_rtol: float = 1e-3, cheb_steps: int = 6,
-                 device: int = 0, vlasov_poisson: bool = False):
+                 device: int = 0, vlasov_poisson: bool = False, outer_method: int = SGDG_OUTER_FGMRES):
         self.lib = load_library()
         self.problem = problem
         self._keep: List = []
@@ -204,6 +206,7 @@ class Solver:
         cfg.cheb_steps = cheb_steps
         cfg.device = device
         cfg.vlasov_poisson = int(vlasov_poisson)
+        cfg.outer_method = int(outer_method)
         co = Coeffs()
         d = problem.d
         for p in range(4):

@@ -250,6 +250,8 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   if (cfg.precision != SGDG_FP64 && cfg.precision != SGDG_MIXED_FP32) return {SGDG_EINVAL, "unknown precision"};
   if (cfg.restart < 1 || cfg.restart > 63 || cfg.inner_its < 1 || cfg.inner_its > 63)
     return {SGDG_EINVAL, "restart and inner_its must be in 1..63"};
+  if (cfg.outer_method != SGDG_OUTER_FGMRES && cfg.outer_method != SGDG_OUTER_RICHARDSON)
+    return {SGDG_EINVAL, "unknown outer_method"};
   if (c.n_u0 < 0 || (c.n_u0 > 0 && !c.u0)) return {SGDG_EINVAL, "bad u0 list"};
   h.cfg = cfg;
   h.d = cfg.mesh_x.dim;

@@ -936,7 +936,18 @@ Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resol
   // what one cycle can resolve), then the FP64 residual restarts it
   const bool mixed = h.cfg.precision == SGDG_MIXED_FP32;
   const double kRefineGain = 1e-4;
-  while (beta > tol && total < h.cfg.max_outer && bnorm > 0.0) {
+  // Algorithm 1 (Sect. 4.3): Richardson on the CT-preconditioned system,
+  // u <- u + P_CT(b - A u), with the true residual in FP64 after every step
+  while (h.cfg.outer_method == SGDG_OUTER_RICHARDSON && beta > tol && total < h.cfg.max_outer && bnorm > 0.0) {
+    SG_ST(ct_precondition(h, r, O.Z, s, &S.inner_its_total));
+    SG_CU(vec_axpby<double>(n, 1.0, O.Z, 1.0, x, s));
+    SG_ST(apply_plan<double>(h, h.op, x, r, s));
+    S.applies++;
+    SG_CU(vec_axpby<double>(n, 1.0, h.rhs, -1.0, r, s));
+    SG_ST(vnorm<double>(h, r, n, &beta, s));
+    total++;
+  }
+  while (h.cfg.outer_method == SGDG_OUTER_FGMRES && beta > tol && total < h.cfg.max_outer && bnorm > 0.0) {
     G.start(beta);
     SG_CU(vec_axpby<double>(n, 1.0 / beta, r, 0.0, O.V, s));
     const double cycle_tol = mixed ? std::max(tol, kRefineGain * beta) : tol;
@@ -978,7 +989,7 @@ Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resol
   }
   S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (st) *st = S;
-  if (S.status == SGDG_ENOCONV) return {SGDG_ENOCONV, "outer FGMRES reached max_outer"};
+  if (S.status == SGDG_ENOCONV) return {SGDG_ENOCONV, "outer iteration reached max_outer"};
   return res;
 }
 

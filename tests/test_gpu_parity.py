@@ -182,6 +182,31 @@ def test_strip_solution_parity_free_streaming(P, prec):
         assert _rel(a, b) < 1e-8, j
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_richardson_outer_iteration(P, prec):
+    """Algorithm 1's outer iteration, u <- u + P_CT(b - A u), on the GPU:
+    it reaches the true-residual tolerance and the oracle's strip solution
+    (1e-8 on the nodal values), and takes at least as many outer steps as
+    FGMRES with the same preconditioner."""
+    from oracle.solver import StripSolver, nodal_values
+    prob = W.free_streaming_1d(L=3, n_strips=1)
+    ref = StripSolver(prob, tol=1e-12)
+    end_ref = ref.run()[0]
+    its = {}
+    for method in (P.SGDG_OUTER_RICHARDSON, P.SGDG_OUTER_FGMRES):
+        s = P.Solver(prob, precision=P.SGDG_FP64 if prec == "fp64" else P.SGDG_MIXED_FP32, rtol=1e-11,
+                     max_outer=300, inner_its=60, inner_rtol=1e-12, cheb_steps=12, outer_method=method)
+        s.set_initial()
+        st = s.advance_strip()
+        assert st.status == 0 and st.rel_residual <= 1e-11, (method, st.rel_residual)
+        U = np.empty(s.n_spatial)
+        s.get_end_value(U, on_device=False)
+        assert _rel(nodal_values(ref.op, U, R=1), nodal_values(ref.op, end_ref, R=1)) < 1e-8, method
+        its[method] = st.outer_its
+        s.close()
+    assert its[P.SGDG_OUTER_RICHARDSON] >= its[P.SGDG_OUTER_FGMRES], its
+
+
 def test_strip_d2_converges_to_tolerance(P):
     prob = W.transport_2d(L=3, sigma=0.1, n_strips=2)
     s = P.Solver(prob, rtol=1e-8, precision=P.SGDG_MIXED_FP32)
