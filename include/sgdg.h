@@ -266,6 +266,17 @@ sgdg_status sgdg_field_update(void* h, int source, double* field_energy);
  * side), starting from its last solution; replaces the solution and the end
  * value.  One step of the per-strip fixed point of Sect. 5.3. */
 sgdg_status sgdg_resolve_strip(void* h, void* stream, sgdg_strip_stats* stats);
+/* One strip of the Vlasov-Poisson system with the field iterated to
+ * consistency (Sect. 5.3 iterates E and f within a strip): the field from
+ * U^-_{j-1} (sgdg_field_update source 0), a strip solve, then up to max_fp
+ * times: the field from the strip solution at the midpoint (source 1) and,
+ * while the potential changed by more than tol (relative l2 against the
+ * previous field), a re-solve of the strip with it.  stats: the last solve;
+ * fp_steps: the re-solves made; phi_change: the last relative change (may be
+ * NULL).  Handles without vlasov_poisson, tol < 0 or max_fp < 0: SGDG_EINVAL;
+ * SGDG_ENOCONV when a solve hits max_outer. */
+sgdg_status sgdg_advance_strip_vp(void* h, void* stream, double tol, int max_fp, sgdg_strip_stats* stats,
+                                  int* fp_steps, double* phi_change);
 /* Initial guess of the next sgdg_advance_strip: 0 zero (default), 1 the
  * previous strip's solution, 2 the array last given to sgdg_set_guess, 3 the
  * linear extrapolation 2 u_{j-1} - u_{j-2} of the last two strip solutions

@@ -100,6 +100,8 @@ EXPORTS = {
     "sgdg_set_launch_shape": (C.c_int, [C.c_void_p, C.c_int]),
     "sgdg_field_update": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "sgdg_resolve_strip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sgdg_advance_strip_vp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p,
+                                        C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "sgdg_set_warm_start": (C.c_int, [C.c_void_p, C.c_int]),
     "sgdg_set_guess": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sgdg_extrapolated_guess": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -369,6 +371,19 @@ class Solver:
         if check:
             self._check(code)
         return st
+
+    def advance_strip_vp(self, tol: float = 1e-8, max_fp: int = 10, stream=None, check: bool = True):
+        """One Vlasov-Poisson strip with the field iterated to consistency
+        (sgdg_advance_strip_vp): returns (stats of the last solve, re-solves,
+        last relative change of the potential)."""
+        st = StripStats()
+        steps = C.c_int()
+        change = C.c_double()
+        code = self.lib.sgdg_advance_strip_vp(self.h, _stream(stream), tol, max_fp, C.byref(st), C.byref(steps),
+                                              C.byref(change))
+        if check:
+            self._check(code)
+        return st, steps.value, change.value
 
     def coarse_values(self, u, R: int, lx: int, lv: int, out, stream=None):
         self._check(self.lib.sgdg_coarse_values(self.h, _ptr(u), R, lx, lv, _ptr(out), _stream(stream)))

@@ -1,5 +1,6 @@
 // C ABI of the sgdg library: set-up (hierarchies, FP64 assembly, term table,
 // device upload) and the entry points declared in include/sgdg.h.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -934,6 +935,39 @@ sgdg_status sgdg_resolve_strip(void* hp, void* stream, sgdg_strip_stats* stats) 
   if (!hp) return SGDG_EINVAL;
   Handle* h = (Handle*)hp;
   Status st = advance_strip(*h, (cudaStream_t)stream, stats, true);
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+sgdg_status sgdg_advance_strip_vp(void* hp, void* stream, double tol, int max_fp, sgdg_strip_stats* stats,
+                                  int* fp_steps, double* phi_change) {
+  if (!hp) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  if (!h->field) return fail(h, {SGDG_EINVAL, "the handle was not created with vlasov_poisson = 1"});
+  if (!(tol >= 0.0) || max_fp < 0) return fail(h, {SGDG_EINVAL, "tol and max_fp must be >= 0"});
+  cudaStream_t s = (cudaStream_t)stream;
+  double energy = 0.0;
+  Status st = field_update(*h, 0, &energy);
+  if (!st.code) st = advance_strip(*h, s, stats, false);
+  int k = 0;
+  double change = 0.0;
+  std::vector<double> prev = h->field->phi;
+  while (!st.code && k < max_fp) {
+    st = field_update(*h, 1, &energy);
+    if (st.code) break;
+    const std::vector<double>& phi = h->field->phi;
+    double dn = 0.0, pn = 0.0;
+    for (size_t i = 0; i < phi.size(); ++i) {
+      dn += (phi[i] - prev[i]) * (phi[i] - prev[i]);
+      pn += phi[i] * phi[i];
+    }
+    change = pn > 0.0 ? std::sqrt(dn / pn) : std::sqrt(dn);
+    if (change <= tol) break;
+    prev = phi;
+    st = advance_strip(*h, s, stats, true);
+    ++k;
+  }
+  if (fp_steps) *fp_steps = k;
+  if (phi_change) *phi_change = change;
   return st.code ? fail(h, st) : SGDG_OK;
 }
 

@@ -78,3 +78,39 @@ def test_landau_damping_rate():
     slope = np.polyfit(t[peaks], np.log(en[peaks]), 1)[0]
     gamma = -slope / 2.0
     assert 0.13 < gamma < 0.19, (gamma, t[peaks], en[peaks])
+
+
+def test_field_fixed_point_iterated_to_consistency():
+    """sgdg_advance_strip_vp iterates field and transport within each strip
+    (Sect. 5.3) until the potential changes by less than tol: it ends below
+    tol within the step cap, and one fixed-point step through it equals the
+    manual sequence (field from U^-, solve, field from the midpoint,
+    re-solve) bit for bit."""
+    import paper_2204_05988_gb300 as P
+    prob = W.landau_4d(L=3)
+    kw = dict(vlasov_poisson=True, rtol=1e-10, inner_its=30, inner_rtol=1e-4)
+    s = P.Solver(prob, **kw)
+    s.set_initial()
+    for j in range(3):
+        # tol well above the floor that rtol 1e-10 puts on the potential's
+        # relative change (the potential is O(alpha) = 1e-2 of the density)
+        st, steps, change = s.advance_strip_vp(tol=1e-6, max_fp=12)
+        assert st.rel_residual <= 1e-10 and steps < 12 and change <= 1e-6, (j, steps, change)
+    # one fixed-point step (tol 0, max_fp 1) against the manual calls
+    a, b = P.Solver(prob, **kw), P.Solver(prob, **kw)
+    a.set_initial()
+    b.set_initial()
+    st, steps, change = a.advance_strip_vp(tol=0.0, max_fp=1)
+    assert steps == 1 and change > 0.0
+    b.field_update(0)
+    b.advance_strip()
+    b.field_update(1)
+    b.resolve_strip()
+    ua, ub = np.empty(a.n_spatial), np.empty(b.n_spatial)
+    a.get_end_value(ua, on_device=False)
+    b.get_end_value(ub, on_device=False)
+    assert np.array_equal(ua, ub)
+    with pytest.raises(P.SgdgError):
+        a.advance_strip_vp(tol=-1.0)
+    for x in (s, a, b):
+        x.close()
