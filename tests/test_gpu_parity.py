@@ -214,3 +214,38 @@ def test_strip_d2_converges_to_tolerance(P):
     for _ in range(2):
         st = s.advance_strip()
         assert st.rel_residual <= 1e-8 and st.outer_its < 60
+
+
+def test_config1_run_to_end_time(P):
+    """The d = 1 free-streaming configuration (L = 6, dt = 1/32) run through
+    all 16 strips to T = 0.5 in FP64: the unique nodal values of U^-(T)
+    match the oracle's end state (tests/golden/config1_end_L6.txt, written
+    by make_config1_end.py from the oracle's strip solver) within 1e-8 at
+    the sampled nodes and in the l2 norm over all nodes.  The oracle's error
+    against the exact solution u0(x - v t, v), recorded beside it, is the
+    discretisation error both share (3.0e-3 at L = 6)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config1_end_L6.txt")
+    head, idx, val = {}, [], []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("# ") and len(line.split()) == 3:
+                head[line.split()[1]] = float(line.split()[2])
+            elif not line.startswith("#"):
+                i, v = line.split()
+                idx.append(int(i))
+                val.append(float(v))
+    prob = W.free_streaming_1d(L=6)
+    s = P.Solver(prob, rtol=1e-11, restart=30, inner_its=30, inner_rtol=1e-4)
+    s.set_initial()
+    for j in range(prob.n_strips):
+        st = s.advance_strip()
+        assert st.rel_residual <= 1e-11, j
+    U = np.empty(s.n_spatial)
+    s.get_end_value(U, on_device=False)
+    nod = _nodal(P, s, U)
+    assert nod.size == int(head["n_nodal"])
+    assert _rel(nod[idx], np.array(val)) < 1e-8
+    assert abs(np.linalg.norm(nod) - head["nodal_l2"]) < 1e-8 * head["nodal_l2"]
+    assert 1e-3 < head["exact_rel_l2_error_finest_grid"] < 1e-2
+    s.close()
