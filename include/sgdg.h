@@ -375,6 +375,11 @@ typedef struct {
 sgdg_status sgdg_profile(void* h, int enable);
 /* Synchronise the device, fill out[0..7] (one per kind) and clear the records. */
 sgdg_status sgdg_kernel_stats(void* h, sgdg_kernel_stat* out, int n_kinds);
+/* Sizes in bytes of the ABI structs, for bindings to check their layouts
+ * (host only; no device is touched): out[0..7] = sgdg_mesh, sgdg_product,
+ * sgdg_source, sgdg_coeffs, sgdg_config, sgdg_info, sgdg_strip_stats,
+ * sgdg_kernel_stat.  Writes min(n, 8) entries and returns 8. */
+int sgdg_struct_sizes(int* out, int n);
 /* Number of SpMM kernels this handle has launched so far. */
 long long sgdg_launch_count(const void* h);
 

@@ -98,6 +98,7 @@ EXPORTS = {
     "sgdg_launch_count": (C.c_longlong, [C.c_void_p]),
     "sgdg_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "sgdg_set_launch_shape": (C.c_int, [C.c_void_p, C.c_int]),
+    "sgdg_struct_sizes": (C.c_int, [C.POINTER(C.c_int), C.c_int]),
     "sgdg_field_update": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "sgdg_resolve_strip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_advance_strip_vp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p,

@@ -725,6 +725,14 @@ sgdg_status sgdg_get_end_value(const void* hp, double* dst, int on_device) {
   return e == cudaSuccess ? SGDG_OK : SGDG_ECUDA;
 }
 
+int sgdg_struct_sizes(int* out, int n) {
+  const int sz[8] = {(int)sizeof(sgdg_mesh),   (int)sizeof(sgdg_product), (int)sizeof(sgdg_source),
+                     (int)sizeof(sgdg_coeffs), (int)sizeof(sgdg_config),  (int)sizeof(sgdg_info),
+                     (int)sizeof(sgdg_strip_stats), (int)sizeof(sgdg_kernel_stat)};
+  for (int i = 0; out && i < n && i < 8; ++i) out[i] = sz[i];
+  return 8;
+}
+
 sgdg_status sgdg_set_launch_shape(void* hp, int code) {
   if (!hp) return SGDG_EINVAL;
   Handle* h = (Handle*)hp;

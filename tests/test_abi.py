@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     with open(os.path.join(ROOT, "include", "sgdg.h")) as f:
         src = f.read()
-    return sorted(set(re.findall(r"^\s*(?:sgdg_status|void|const char\*|long long)\s+(sgdg_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:sgdg_status|void|const char\*|long long|int)\s+(sgdg_\w+)\s*\(", src, re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -47,3 +47,15 @@ def test_binding_fails_loudly_without_library(tmp_path):
             P.load_library(str(tmp_path / "missing.so"))
     finally:
         P._lib = saved
+
+
+def test_binding_structs_match_the_library_layouts(lib):
+    """ctypes structures of the binding have the sizes the library compiled
+    (a field missing on either side changes them)."""
+    import ctypes as C
+    import paper_2204_05988_gb300 as P
+    out = (C.c_int * 8)()
+    assert lib.sgdg_struct_sizes(out, 8) == 8
+    mine = [C.sizeof(t) for t in (P.Mesh, P.Product, P.Source, P.Coeffs, P.Config, P.Info, P.StripStats,
+                                  P.KernelStat)]
+    assert list(out) == mine
