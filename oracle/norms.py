@@ -1,0 +1,180 @@
+"""Norms of sparse-grid functions: the streamline-diffusion norm of an error
+over all strips (Sect. 3, Eq. 11) and the H^1(J x Omega) norm of one strip
+function (the stop test of Algorithm 1, Sect. 4.3).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+For a discrete solution U (one strip vector per strip) and an exact solution
+u, e = U - u and
+
+  |||e|||_delta^2 = sum_j int_{I_j} sigma ||e||^2 + delta ||d_t e + d_beta e||^2
+                    + |e|^2_{dOmega} dt
+                  + sum_{j<N} ||[e]_j||^2 + ||e_0^+||^2 + ||e_N^-||^2,
+
+with the jump [e]_j = e_j^+ - e_j^-.  The exact solution solves the
+homogeneous equation (f = 0), is continuous in time, so
+
+  d_t e + d_beta e = (d_t U + d_beta U) + sigma u  and  [e]_j = [U]_j.
+
+Only domains without a boundary part (every axis periodic) are handled here:
+the |e|^2_{dOmega} term is then absent.
+
+Quadrature: the sparse-grid function is represented exactly on the finest
+full grid (L, L) (``full_grid_values``); on every pair of finest cells the
+collapsed Gauss rule of ``assembly.simplex_rule`` with q points per
+direction integrates the squared errors (polynomial parts exactly for q >= 2;
+the exact solution's contribution to the error to the rule's accuracy), and
+Gauss-Legendre with three points per strip integrates in time (the
+integrand d_t U + d_beta U is linear in t for r = 1).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .assembly import Factor, gauss01
+from .brute import _cell_data
+from .operator import eta
+from .solver import full_grid_values
+
+
+def _products(prob, X, V, p):
+    """beta_p on all (x point, v point) pairs."""
+    b = prob.beta[p]
+    fx = b.fx(X) if b.fx is not None else np.ones(X.shape[0])
+    fv = b.fv(V) if b.fv is not None else np.ones(V.shape[0])
+    return b.coef * np.outer(fx, fv)
+
+
+class _FullGrid:
+    """Point values and gradients of finest-full-grid P1 (x) P1 functions on
+    every (x cell, v cell) pair's quadrature points."""
+
+    def __init__(self, op, q):
+        L = op.L
+        self.op = op
+        self.lx, self.lv = op.hx.levels[L], op.hv.levels[L]
+        if any(len(lev.bfaces) for lev in (self.lx, self.lv)):
+            raise NotImplementedError("SD-norm errors only on domains without boundary (periodic)")
+        self.px, self.wx, self.lamx, self.gx = _cell_data(self.lx, q)
+        self.pv, self.wv, self.lamv, self.gv = _cell_data(self.lv, q)
+        nx, nv = self.px.shape[0], self.pv.shape[0]
+        q1, q2 = self.px.shape[1], self.pv.shape[1]
+        self.shape = (nx, q1, nv, q2)
+        # point coordinates broadcast over pairs
+        self.Xp = self.px.reshape(-1, self.px.shape[2])      # (nx q1, d)
+        self.Vp = self.pv.reshape(-1, self.pv.shape[2])      # (nv q2, d)
+        self.W = np.einsum("ai,bj->aibj", self.wx, self.wv)  # (nx, q1, nv, q2)
+
+    def nodal(self, U):
+        """Nodal values on the finest full grid of a spatial sparse-grid vector."""
+        return full_grid_values(self.op, U)
+
+    def value(self, F):
+        Fc = F[self.lx.cells][:, :, self.lv.cells]           # (nx, d+1, nv, d+1)
+        return np.einsum("ia,xayb,jb->xiyj", self.lamx, Fc, self.lamv)
+
+    def grad_x(self, F, axis):
+        Fc = F[self.lx.cells][:, :, self.lv.cells]
+        gx = self.gx[:, :, axis]                              # (nx, d+1)
+        q1 = self.px.shape[1]
+        v = np.einsum("xa,xayb,jb->xyj", gx, Fc, self.lamv)
+        return np.broadcast_to(v[:, None, :, :], (v.shape[0], q1) + v.shape[1:])
+
+    def grad_v(self, F, axis):
+        Fc = F[self.lx.cells][:, :, self.lv.cells]
+        gv = self.gv[:, :, axis]
+        q2 = self.pv.shape[1]
+        v = np.einsum("ia,xayb,yb->xiy", self.lamx, Fc, gv)
+        return np.broadcast_to(v[:, :, :, None], v.shape + (q2,))
+
+    def exact(self, fn, t):
+        """fn(t, x, v) on every quadrature point pair (d = 1: scalar coordinates)."""
+        d = self.Xp.shape[1]
+        if d == 1:
+            val = fn(t, self.Xp[:, 0][:, None], self.Vp[:, 0][None, :])
+        else:
+            val = fn(t, self.Xp[:, None, :], self.Vp[None, :, :])
+        return np.asarray(val).reshape(self.shape)
+
+    def l2sq(self, vals):
+        return float(np.sum(self.W * vals * vals))
+
+
+def sd_norm_error(prob, op, strips, exact, q: int = 5):
+    """|||U - u|||_delta over the strips (Eq. 11).
+
+    strips: the strip solutions u_j (strip vectors, [coefficient][s], s
+    fastest), j = 1..N, on strips I_j = ((j-1) dt, j dt); exact(t, x, v):
+    the exact solution of the homogeneous problem.  Returns (norm, parts),
+    parts = dict of the squared contributions."""
+    if prob.r != 1:
+        raise NotImplementedError("time degree 1 only")
+    fg = _FullGrid(op, q)
+    d, dt, dl, R = prob.d, prob.dt, prob.delta, op.R
+    sig = prob.sigma
+    sigma_pts = None
+    if sig.coef != 0.0:
+        fx = sig.fx(fg.Xp) if sig.fx is not None else np.ones(fg.Xp.shape[0])
+        fv = sig.fv(fg.Vp) if sig.fv is not None else np.ones(fg.Vp.shape[0])
+        sigma_pts = (sig.coef * np.outer(fx, fv)).reshape(fg.shape)
+    beta_pts = [_products(prob, fg.Xp, fg.Vp, p).reshape(fg.shape) for p in range(2 * d)]
+    tq, tw = gauss01(3)
+    parts = {"sigma": 0.0, "streamline": 0.0, "jumps": 0.0, "initial": 0.0, "final": 0.0}
+    prev_end = None
+    N = len(strips)
+    for j, u in enumerate(strips):
+        t0 = j * dt
+        us = u.reshape(-1, R)
+        F = [fg.nodal(us[:, s]) for s in range(R)]
+        val = [fg.value(Fs) for Fs in F]
+        dbeta = []
+        for s in range(R):
+            acc = np.zeros(fg.shape)
+            for p in range(2 * d):
+                g = fg.grad_x(F[s], p) if p < d else fg.grad_v(F[s], p - d)
+                acc = acc + beta_pts[p] * g
+            dbeta.append(acc)
+        for tau, w in zip(tq, tw):
+            e_s = [eta(s, np.array([tau]), dt) for s in range(R)]
+            Ut = sum(e_s[s][0][0] * val[s] for s in range(R))
+            DU = sum(e_s[s][1][0] * val[s] + e_s[s][0][0] * dbeta[s] for s in range(R))
+            ex = fg.exact(exact, t0 + tau * dt)
+            if sigma_pts is not None:
+                parts["sigma"] += w * dt * float(np.sum(fg.W * sigma_pts * (Ut - ex) ** 2))
+                DU = DU + sigma_pts * ex
+            parts["streamline"] += w * dt * dl * fg.l2sq(DU)
+        e0 = [eta(s, np.array([0.0]), dt)[0][0] for s in range(R)]
+        e1 = [eta(s, np.array([1.0]), dt)[0][0] for s in range(R)]
+        start = sum(e0[s] * val[s] for s in range(R))
+        end = sum(e1[s] * val[s] for s in range(R))
+        if j == 0:
+            parts["initial"] = fg.l2sq(start - fg.exact(exact, 0.0))
+        else:
+            parts["jumps"] += fg.l2sq(start - prev_end)
+        if j == N - 1:
+            parts["final"] = fg.l2sq(end - fg.exact(exact, N * dt))
+        prev_end = end
+    return float(np.sqrt(sum(parts.values()))), parts
+
+
+def h1_terms(op):
+    """Kronecker terms of the H^1(J x Omega) Gram form on one strip:
+    int_J (v, w) + (d_t v, d_t w) + sum_p (d_p v, d_p w) dt, p over the d
+    axes of Omega_x and of Omega_v."""
+    from .operator import time_matrices
+    Mt, Tt, Ct, Gt = time_matrices(op.prob.dt, op.prob.r)
+    d = op.prob.d
+    vol = Factor("vol")
+    terms = [(Mt + Ct, vol, vol)]
+    for p in range(1, d + 1):
+        terms.append((Mt, Factor("vol", 1.0, (), p, p), vol))
+        terms.append((Mt, vol, Factor("vol", 1.0, (), p, p)))
+    return terms
+
+
+def h1_norm(op, u):
+    """||U||_{H^1(J x Omega)} of the strip function with coefficients u: the
+    Gram form applied blockwise (rows are test functions, so u . (G u) is
+    the form of U with itself)."""
+    g = op.apply(u, h1_terms(op))
+    return float(np.sqrt(max(float(u @ g), 0.0)))

@@ -13,8 +13,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   solves on the grids (l, L-l), l = 0..L and (l, L-1-l), l = 0..L-1 (residual
   restricted in dim 1 from grid (l+1, L-1-l)), then the combination
   du_l = dhat_l - (E^(1) (x) Id) dhat_(l-1, L-l).
-* ``richardson``: Algorithm 1 itself (u <- u - P(A u - b)), stop on the
-  Euclidean norm of the correction.
+* ``richardson``: Algorithm 1 itself (u <- u - P(A u - b)), stopped by the
+  paper's test on the H^1(J x Omega) norm of the correction (or, as an
+  option, on its Euclidean norm).
 * ``StripSolver``: the implicit strip-by-strip scheme (Sect. 2): the right-hand
   side (U^-_{j-1}, w^+_{j-1}) = eta(t_{j-1}^+) (x) M_sg U^-_{j-1} (Eq. 5), with
   (u0, w^+) from load vectors for the first strip, plus the source part
@@ -151,14 +152,20 @@ def ct_precondition(op: SparseGridOperator, comp: ComponentSolver, r: np.ndarray
     return out
 
 
-def richardson(op, comp, b, tol=1e-10, maxiter=200):
-    """Algorithm 1: u <- u - P(A u - b) until ||du||_2 < tol * ||b||_2."""
+def richardson(op, comp, b, tol=1e-10, maxiter=200, norm="h1"):
+    """Algorithm 1: u <- u - P(A u - b) until the correction is small.
+
+    norm="h1": the paper's stop, ||du||_{H^1(J x Omega)} < tol (the H^1 norm
+    of the correction function over the strip, ``norms.h1_norm``);
+    norm="l2": ||du||_2 < tol * ||b||_2 on the spanning-set coefficients."""
+    from .norms import h1_norm
     u = np.zeros_like(b)
     bn = np.linalg.norm(b)
     for k in range(maxiter):
         du = ct_precondition(op, comp, op.apply(u) - b)
         u = u - du
-        if np.linalg.norm(du) < tol * bn:
+        small = h1_norm(op, du) < tol if norm == "h1" else np.linalg.norm(du) < tol * bn
+        if small:
             return u, k + 1
     return u, maxiter
 
@@ -256,13 +263,16 @@ class StripSolver:
         self.outer_its.append(it)
         return x, it, res
 
-    def run(self, n_strips=None):
-        """Returns the list of end values U^-_j (spatial sparse-grid vectors)."""
+    def run(self, n_strips=None, solutions=None):
+        """Returns the list of end values U^-_j (spatial sparse-grid vectors);
+        appends every strip solution u_j to ``solutions`` when given."""
         n = self.prob.n_strips if n_strips is None else n_strips
         MU = self.initial_mass_u0()
         ends = []
         for j in range(n):
             u, it, res = self.solve_strip(self.rhs(MU, j * self.prob.dt))
+            if solutions is not None:
+                solutions.append(u)
             U = self.endpoint(u)
             ends.append(U)
             MU = self.mass_spatial(U)

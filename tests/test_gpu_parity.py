@@ -2,7 +2,11 @@
 
 Tolerances (relative l2 over the output vector):
   * operator, mass and diagonal-block applies: 1e-12 in FP64, 1e-5 in FP32
-    (apply outputs are unique - rows are test functions);
+    (apply outputs are unique - rows are test functions); the operator and
+    mass applies are also checked grid by grid at the same tolerances, as
+    max |y_l - ref_l| / max |ref_l| on every component grid l, so that a
+    wrong boundary row or ragged tile edge on one grid is not diluted by the
+    other grids' correct entries;
   * strip solutions: 1e-8 on the canonical nodal values (the spanning-set
     coefficients are not unique, Sect. 4.1), both sides solved tightly.
 Inputs are seeded U[-1, 1] vectors from sgdg_workloads.
@@ -18,6 +22,15 @@ pytestmark = pytest.mark.gpu
 
 def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _per_grid(op, y, ref, tol):
+    """max-abs error over each component grid, scaled by that grid's largest
+    reference value; every grid within tol."""
+    for i in range(len(op.grids)):
+        a, b = y[op.offsets[i]:op.offsets[i + 1]], ref[op.offsets[i]:op.offsets[i + 1]]
+        err = np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+        assert err < tol, (op.grids[i], err)
 
 
 @pytest.fixture(scope="module")
@@ -70,6 +83,7 @@ def test_apply_operator_parity(P, setups, name, prec):
     y = yd.double().cpu().numpy()
     tol = 1e-12 if prec == "fp64" else 1e-5
     assert _rel(y, ref) < tol
+    _per_grid(op, y, ref, tol)
 
 
 @pytest.mark.parametrize("name", ["d1_L6", "d2_L3_sigma", "d1_L0"])
@@ -104,6 +118,7 @@ def test_apply_mass_parity(P, setups, name):
     s.apply_mass(ud, yd, P.SGDG_FP64)
     torch.cuda.synchronize()
     assert _rel(yd.cpu().numpy(), ref) < 1e-12
+    _per_grid(op, yd.cpu().numpy(), ref, 1e-12)
 
 
 @pytest.mark.parametrize("name", ["d1_L6", "d2_L3_sigma"])

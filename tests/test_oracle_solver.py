@@ -132,3 +132,53 @@ def test_richardson_and_fgmres_agree():
     n2 = nodal_values(s.op, x2, R=2)
     assert np.abs(n1 - n2).max() < 1e-9 * np.abs(n1).max()
     assert its < 60
+
+
+def _hat_values(lev, pts):
+    """H[a, k] = phi_k(pts[a]) for the P1 basis of one mesh level, from the
+    cells' geometry (barycentric coordinates), independent of the embeddings."""
+    cc, cells = lev.cell_coords, lev.cells
+    d = pts.shape[1]
+    H = np.zeros((pts.shape[0], lev.n))
+    for a, p in enumerate(pts):
+        for c in range(cells.shape[0]):
+            v0 = cc[c, 0]
+            J = (cc[c, 1:] - v0).T
+            lam_r = np.linalg.solve(J, p - v0)
+            lam = np.concatenate([[1.0 - lam_r.sum()], lam_r])
+            if lam.min() >= -1e-12:
+                for k, l in zip(cells[c], lam):
+                    H[a, k] += l
+                break
+        else:
+            raise AssertionError("point outside the mesh")
+    return H
+
+
+@pytest.mark.parametrize("make,targets", [
+    (lambda: W.free_streaming_1d(L=3, n_strips=1), [(0, 0), (1, 2), (2, 2), (3, 1)]),
+    (lambda: W.transport_2d(L=2, sigma=0.0), [(0, 0), (1, 1), (2, 0)]),
+], ids=["d1", "d2"])
+def test_coarse_values_are_point_values(make, targets):
+    """coarse_values (the warm start's coarse view) against the sparse-grid
+    function evaluated at the coarse grid's node coordinates by summing every
+    component grid's P1 (x) P1 basis functions there."""
+    from oracle.solver import coarse_values
+    prob = make()
+    op = SparseGridOperator(prob)
+    rng = np.random.default_rng(5)
+    for R in (1, 2):
+        U = rng.uniform(-1, 1, op.size // op.R * R)
+        for lx, lv in targets:
+            X = op.hx.levels[lx].coords
+            V = op.hv.levels[lv].coords
+            ref = np.zeros((X.shape[0], V.shape[0], R))
+            off = 0
+            for (l1, l2) in op.grids:
+                n1, n2 = op.grid_shape(l1, l2)
+                u = U[off:off + n1 * n2 * R].reshape(n1, n2, R)
+                off += n1 * n2 * R
+                ref += np.einsum("ai,ijs,bj->abs", _hat_values(op.hx.levels[l1], X), u,
+                                 _hat_values(op.hv.levels[l2], V))
+            got = coarse_values(op, U, R, lx, lv)
+            assert np.abs(got - ref.ravel()).max() < 1e-12 * max(1.0, np.abs(ref).max())
