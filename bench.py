@@ -7,9 +7,13 @@ coefficients, 123,180,372 DoF per strip vector (FP32: 493 MB, FP64: 985 MB,
 both larger than L2).  A step is one application of the strip operator
 A^(delta) to a seeded U[-1,1] vector, resident in HBM.
 
-Reported: value = GDoF/s of the mixed-precision (FP32) apply; the FP64 apply,
-the end-to-end apply through the C ABI with host buffers, per-kernel roofline,
-strip solves at 1e-8 (mixed vs FP64), the oracle timed on the host cores.
+Reported: value = GDoF/s of the mixed-precision (FP32) apply; the FP64 and
+BF16-storage applies; the end-to-end apply through the C ABI with host
+buffers; the roofline of the whole apply (algorithmic bytes over HBM, executed
+FLOPs over the measured FP32 peak) and of its dominant kernel; strip solves
+at 1e-8 on the same workload (mixed vs FP64); the batched apply of 48
+instances of uneven L (one CUDA graph); batched strips against the plain
+FP64 solver; the oracle timed on one host core and on all of them.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -34,9 +38,10 @@ import sgdg_workloads as W  # noqa: E402
 METRIC = "operator-apply GDoF/s; s/time-strip at 1e-8 rel. residual, mixed vs FP64"
 
 
-# ALU peaks derived from the unit counts and the maximum SM clock (2,070 MHz):
-# FP32 - 152 SMs x 128 FP32 lanes x 2 flops per multiply-add; FP64 - the
-# nominal GB300 non-tensor FP64 rate (1.25 TFLOP/s), far below FP32.
+# ALU peaks from the unit counts and the maximum SM clock (2,070 MHz), used
+# only when the measured ones (sgdg_alu_peak, timed at the start of the run)
+# are unavailable: FP32 - 152 SMs x 128 FP32 lanes x 2 flops per multiply-add;
+# FP64 - the nominal GB300 non-tensor FP64 rate (1.25 TFLOP/s).
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
 FP64_PEAK_GFLOPS = 1250.0
 
@@ -150,16 +155,77 @@ class Ranks:
         return float(t.item())
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg: str):
+    """Progress of the run on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
 def whole_job(world: int, units_per_rank: float, seconds: float) -> float:
     """Weak scaling: every rank processes units_per_rank; `seconds` is the
     slowest rank's time, so the job's rate is world x units / seconds."""
     return world * units_per_rank / seconds
 
 
-def cpu_baseline(steps: int = 4, L: int = 5):
-    """The oracle's blockwise apply (Sect. 4.2) on the host cores, as it stands,
-    on a bounded sample of the same workload family (d = 2, level L)."""
+def cpu_info():
+    """Host CPU model and logical core count (for the baseline's record)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+_POOL_OP = None
+
+
+def _pool_init(L):
+    global _POOL_OP
+    os.environ["OMP_NUM_THREADS"] = "1"
     from oracle.operator import SparseGridOperator
+    _POOL_OP = SparseGridOperator(W.transport_2d(L=L, sigma=0.1))
+    u = W.uniform_vector(_POOL_OP.size, seed=7)
+    _POOL_OP.apply(u)                               # builds the projected factors
+
+
+def _pool_blocks(args):
+    """Blocks (i, j) of the oracle's blockwise apply: A_ij u_j for target grid i."""
+    pairs, u = args
+    op = _POOL_OP
+    return [(i, op.apply_block(op.terms, op.grids[i], op.grids[j], op.block(u, j))) for i, j in pairs]
+
+
+def _pool_apply(pool, nw, op, u):
+    """y = A u with the (target, source) blocks spread over the pool's workers."""
+    pairs = [(i, j) for i in range(len(op.grids)) for j in range(len(op.grids))]
+    chunks = [pairs[k::nw] for k in range(nw)]
+    y = [np.zeros(op.shape[i] + (op.R,)) for i in range(len(op.grids))]
+    for part in pool.map(_pool_blocks, [(c, u) for c in chunks]):
+        for i, blk in part:
+            y[i] += blk
+    return np.concatenate([b.ravel() for b in y])
+
+
+def cpu_baseline(steps: int = 4, L: int = 5, all_cores: bool = True):
+    """The oracle's blockwise apply (Sect. 4.2) on the host cores, as it stands,
+    on a bounded sample of the same workload family (d = 2, level L): on one
+    core, and on all cores with the target grids spread over a process pool
+    (spawned, so that no worker inherits the CUDA context)."""
+    from oracle.operator import SparseGridOperator
+    info = cpu_info()
     prob = W.transport_2d(L=L, sigma=0.1)
     op = SparseGridOperator(prob)
     u = W.uniform_vector(op.size, seed=7)
@@ -168,9 +234,24 @@ def cpu_baseline(steps: int = 4, L: int = 5):
     for _ in range(steps):
         op.apply(u)
     dt = (time.perf_counter() - t) / steps
-    return {"value": op.size / dt / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-            "sample": f"blockwise FP64 apply, d=2 L={L} ({op.size} DoF), {steps} applies after 1 warm-up; "
-                      f"numpy/scipy single thread"}, dt, op.size
+    res = {"value": op.size / dt / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+           "sample": f"blockwise FP64 apply, d=2 L={L} ({op.size} DoF), {steps} applies after 1 warm-up; "
+                     f"numpy/scipy, one process", "nproc": info["nproc"], "cpu_model": info["model"]}
+    if all_cores and (info["nproc"] or 1) > 1:
+        import multiprocessing as mp
+        nw = min(info["nproc"], len(op.grids) ** 2)
+        with mp.get_context("spawn").Pool(nw, initializer=_pool_init, initargs=(L,)) as pool:
+            y = _pool_apply(pool, nw, op, u)                          # warm-up
+            t = time.perf_counter()
+            for _ in range(steps):
+                _pool_apply(pool, nw, op, u)
+            dtp = (time.perf_counter() - t) / steps
+        ref = op.apply(u)
+        res["all_cores"] = {"value": op.size / dtp / 1e9, "unit": "GDoF/s", "cores": nw,
+                            "sample": f"same apply, its {len(op.grids) ** 2} (target, source) grid blocks "
+                                      f"spread over {nw} spawned worker processes (one core each)",
+                            "max_abs_diff_vs_one_core": float(np.abs(y - ref).max())}
+    return res, dt, op.size
 
 
 def run_reference(args, rank, world):
@@ -208,10 +289,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--L", type=int, default=9)
     ap.add_argument("--ref-L", type=int, default=5)
-    ap.add_argument("--strip-L", type=int, default=7, help="level of the strip-solve timing (-1: skip)")
+    ap.add_argument("--strip-L", type=int, default=9, help="level of the strip-solve timing (-1: skip)")
+    ap.add_argument("--strips-mixed", type=int, default=3, help="mixed-precision strips solved")
+    ap.add_argument("--strips-fp64", type=int, default=2, help="plain FP64 strips solved")
+    ap.add_argument("--inner-its", type=int, default=48, help="GMRES steps per component solve (strips)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--batch", type=int, default=8, help="instances in the batch measurement (0: skip)")
+    ap.add_argument("--batch", type=int, default=8, help="instances in the batched strip measurement (0: skip)")
     ap.add_argument("--batch-levels", type=int, nargs="+", default=[5, 6, 7])
+    ap.add_argument("--batch-apply", type=int, default=48,
+                    help="instances in the full-size batched apply (L from {6,7,8,9}, seed 0; 0: skip)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -230,7 +316,16 @@ def main():
 
     ranks = Ranks(dist, "cuda")
     barrier = ranks.barrier
+    # measured ALU peaks (register-only multiply-add kernels), the roofline
+    # denominators of the FP32 sweep and of the FP64 apply
+    try:
+        fp32_peak, fp32_peak_src = P.alu_peak(P.SGDG_MIXED_FP32, local, 1 << 18)[0], "measured (sgdg_alu_peak FFMA)"
+        fp64_peak, fp64_peak_src = P.alu_peak(P.SGDG_FP64, local, 1 << 13)[0], "measured (sgdg_alu_peak DFMA)"
+    except P.SgdgError:
+        fp32_peak, fp32_peak_src = FP32_PEAK_GFLOPS, "derived: 152 SMs x 128 lanes x 2 x 2.07 GHz"
+        fp64_peak, fp64_peak_src = FP64_PEAK_GFLOPS, "nominal GB300 FP64 rate"
 
+    log(f"peaks: FP32 {fp32_peak:.0f} GFLOP/s, FP64 {fp64_peak:.0f} GFLOP/s")
     prob = W.transport_2d(L=args.L, sigma=0.1)
     t0 = time.perf_counter()
     s = P.Solver(prob, device=local)
@@ -266,6 +361,7 @@ def main():
         barrier()
         return ranks.max(e0.elapsed_time(e1) / K)
 
+    log(f"set-up {setup_s:.1f} s, autotune {tune_s:.1f} s")
     # ---- FP32 apply (headline), clocks sampled during the timed region
     for _ in range(args.warmup):
         s.apply_operator(u32, y32, P.SGDG_MIXED_FP32, stream)
@@ -293,6 +389,7 @@ def main():
     s.apply_operator(u16, y16, P.SGDG_BF16_STORE, stream)
     err16 = rel(y16.double(), y64)
 
+    log(f"applies: FP32 {ms32:.2f} ms, FP64 {ms64:.2f} ms, BF16 storage {ms16:.2f} ms")
     # ---- per-kernel roofline (one profiled apply per precision)
     peak, peak_kind = _peaks()
     roof = {}
@@ -312,10 +409,10 @@ def main():
     tot64 = sum(v["ms"] for v in st64.values())
     fl64 = sum(v["flops"] for v in st64.values())
     fp64_roof = {"bound": "alu", "kernel": dom64,
-                 "achieved": st64[dom64]["flops"] / (st64[dom64]["ms"] * 1e-3) / 1e9, "peak": FP64_PEAK_GFLOPS,
-                 "unit": "GFLOP/s", "peak_source": "nominal GB300 FP64 rate",
-                 "frac": st64[dom64]["flops"] / (st64[dom64]["ms"] * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
-                 "apply_GFLOPs": fl64 / (tot64 * 1e-3) / 1e9, "apply_frac": fl64 / (tot64 * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
+                 "achieved": st64[dom64]["flops"] / (st64[dom64]["ms"] * 1e-3) / 1e9, "peak": fp64_peak,
+                 "unit": "GFLOP/s", "peak_source": fp64_peak_src,
+                 "frac": st64[dom64]["flops"] / (st64[dom64]["ms"] * 1e-3) / 1e9 / fp64_peak,
+                 "apply_GFLOPs": fl64 / (tot64 * 1e-3) / 1e9, "apply_frac": fl64 / (tot64 * 1e-3) / 1e9 / fp64_peak,
                  "share_of_apply": st64[dom64]["ms"] / tot64}
     # whole-apply effective bandwidth: the bytes the method must move per apply
     # (read u, write y, every pattern once, every factor value array once),
@@ -323,25 +420,31 @@ def main():
     inf = s.info
     b_alg = (n * (4 + 4) + 4 * (inf.rows_x + inf.rows_v + 2 * (inf.L + 1))
              + 4 * inf.nnz_x * (1 + inf.n_x_factors) + 4 * inf.nnz_v * (1 + inf.n_v_factors))
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs", "traffic": _traffic(dom, args.L),
-                "alg_bytes_per_launch": st[dom]["bytes"] / max(1, st[dom]["launches"]),
-                "share_of_apply": st[dom]["ms"] / tot_ms,
-                "apply_effective": {"b_alg_bytes": b_alg, "GBps": b_alg / (ms32 * 1e-3) / 1e9,
-                                    "frac": b_alg / (ms32 * 1e-3) / 1e9 / peak,
-                                    "sweep_bytes": sum(v["bytes"] for v in st.values()),
-                                    "sweep_GBps": sum(v["bytes"] for v in st.values()) / (tot_ms * 1e-3) / 1e9},
-                "fp32_alu": {"achieved": st[dom]["flops"] / (st[dom]["ms"] * 1e-3) / 1e9, "peak": FP32_PEAK_GFLOPS,
-                             "unit": "GFLOP/s",
-                             "frac": st[dom]["flops"] / (st[dom]["ms"] * 1e-3) / 1e9 / FP32_PEAK_GFLOPS},
-                "per_kind": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
-                                 "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None,
-                                 "GFLOPs": (v["flops"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
-                             for k, v in st.items() if v["launches"]},
-                "f64_per_kind": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
-                                     "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None,
-                                     "GFLOPs": (v["flops"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
-                                 for k, v in roof["f64"].items() if v["launches"]}}
+    fl32 = sum(v["flops"] for v in st.values())
+    per_kind = lambda stats: {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                                  "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None,
+                                  "GFLOPs": (v["flops"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                              for k, v in stats.items() if v["launches"]}
+    # headline roofline: the whole apply, B_alg (what the method must move:
+    # u read, y written, every pattern and factor value array once) over the
+    # apply's time; the dominant kernel's own figure is kept beside it
+    roofline = {"bound": "hbm", "kernel": "operator apply (all sweep launches)",
+                "achieved": b_alg / (ms32 * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": b_alg / (ms32 * 1e-3) / 1e9 / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": _traffic("apply", args.L, "dram_bytes_per_apply"),
+                "alg_bytes_per_launch": b_alg, "b_alg_definition": "8 B x DoF (u in, y out, FP32) + int32 patterns "
+                "+ FP32 value arrays of every factor, once",
+                "dominant_kernel": {"kernel": dom, "achieved": ach, "unit": "GB/s", "frac": ach / peak,
+                                    "traffic": _traffic(dom, args.L),
+                                    "alg_bytes_per_launch": st[dom]["bytes"] / max(1, st[dom]["launches"]),
+                                    "share_of_apply": st[dom]["ms"] / tot_ms},
+                "sweep_bytes": sum(v["bytes"] for v in st.values()),
+                "sweep_GBps": sum(v["bytes"] for v in st.values()) / (tot_ms * 1e-3) / 1e9,
+                "fp32_alu": {"achieved": fl32 / (tot_ms * 1e-3) / 1e9, "peak": fp32_peak, "unit": "GFLOP/s",
+                             "frac": fl32 / (tot_ms * 1e-3) / 1e9 / fp32_peak, "peak_source": fp32_peak_src,
+                             "flops_per_apply": fl32,
+                             "dominant_kernel_frac": st[dom]["flops"] / (st[dom]["ms"] * 1e-3) / 1e9 / fp32_peak},
+                "per_kind": per_kind(st), "f64_per_kind": per_kind(roof["f64"])}
     st16 = roof["bf16"]
     dom16 = max(st16, key=lambda k: st16[k]["ms"])
     bf16_apply = {"value": whole_job(world, n, ms16 * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms16,
@@ -358,6 +461,7 @@ def main():
                                    "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                                for k, v in st16.items() if v["launches"]}}
 
+    log("profiled applies done")
     # ---- end to end through the C ABI with pinned host buffers (FP64 in/out, FP32 apply)
     hu = torch.empty(n, dtype=torch.float64, pin_memory=True)
     hu.copy_(u64.cpu())
@@ -381,25 +485,95 @@ def main():
     del u64, u32, y32, y64, u16, y16
     torch.cuda.empty_cache()
 
-    # ---- strip solves at 1e-8 (mixed vs FP64)
+    # ---- strip solves at 1e-8 (mixed vs FP64), the d = 2 transport workload at
+    # level strip_L, dt = 1/64: both arms start each strip from the linear
+    # extrapolation of the last two solutions (warm start 3; the previous
+    # solution on strip 2), so the ratio compares precisions only
     strip = None
     if args.strip_L >= 0:
-        strip = {"workload": f"transport_2d d=2 L={args.strip_L} sigma=0.1 dt=1/64, strips 1-2, rtol 1e-8"}
-        for nm, pr in (("mixed", P.SGDG_MIXED_FP32), ("fp64", P.SGDG_FP64)):
+        strip = {"workload": f"transport_2d d=2 L={args.strip_L} sigma=0.1 dt=1/64, rtol 1e-8, component solves "
+                             f"GMRES({args.inner_its}) to 1e-3, outer FGMRES(30); warm start: the previous solution "
+                             f"(strip 2), then the extrapolation of the last two (both arms)"}
+        for nm, pr, ns in (("mixed", P.SGDG_MIXED_FP32, args.strips_mixed), ("fp64", P.SGDG_FP64, args.strips_fp64)):
+            if ns <= 0:
+                continue
             ps = W.transport_2d(L=args.strip_L, sigma=0.1)
-            sv = P.Solver(ps, precision=pr, rtol=1e-8, restart=30, inner_its=12, inner_rtol=1e-2, device=local)
+            t0 = time.perf_counter()
+            sv = P.Solver(ps, precision=pr, rtol=1e-8, restart=30, inner_its=args.inner_its, inner_rtol=1e-3,
+                          device=local)
+            setup = time.perf_counter() - t0
+            if pr == P.SGDG_MIXED_FP32:      # launch shapes of the FP32 applies the solve makes
+                tu = torch.rand(sv.n_coeffs, dtype=torch.float32, device="cuda")
+                sv.autotune(tu, torch.empty_like(tu), P.SGDG_MIXED_FP32, stream)
+                del tu
+            sv.set_warm_start(3)
             sv.set_initial()
             sts = []
-            for _ in range(2):
+            log(f"strip solver {nm}: set-up {setup:.1f} s")
+            for _ in range(ns):
                 r = sv.advance_strip(check=False)
+                log(f"  strip {len(sts) + 1} {nm}: {r.seconds:.2f} s, outer {r.outer_its}, rel {r.rel_residual:.2e}")
                 sts.append({"s": round(r.seconds, 4), "outer": r.outer_its, "inner": r.inner_its_total,
                             "applies": r.applies, "rel_res": r.rel_residual, "status": r.status})
-            strip[nm] = {"s_per_strip": sts[-1]["s"], "strips": sts, "dof": sv.n_coeffs}
+            # strip 2 of both arms starts from the previous strip's solution (the
+            # extrapolation needs two), strip 3 on from the extrapolation
+            strip[nm] = {"s_per_strip": sts[1]["s"] if len(sts) > 1 else sts[0]["s"],
+                         "statistic": "strip 2 (both arms: previous-solution start)",
+                         "s_per_strip_extrapolated": (float(np.median([x["s"] for x in sts[2:]]))
+                                                      if len(sts) > 2 else None),
+                         "strips_timed": ns, "total_s": round(sum(x["s"] for x in sts), 3),
+                         "max_rel_residual": max(x["rel_res"] for x in sts), "strips": sts,
+                         "dof": sv.n_coeffs, "setup_s": round(setup, 2)}
             sv.close()
-        strip["speedup_mixed_vs_fp64"] = strip["fp64"]["s_per_strip"] / strip["mixed"]["s_per_strip"]
+            torch.cuda.empty_cache()
+        if "mixed" in strip and "fp64" in strip:
+            strip["speedup_mixed_vs_fp64"] = strip["fp64"]["s_per_strip"] / strip["mixed"]["s_per_strip"]
 
-    # ---- batch of independent instances of uneven L: one CUDA graph per apply,
-    # concurrent strip solves
+    # ---- the batched apply at full size: 48 independent instances, L drawn
+    # from {6, 7, 8, 9} (seed 0), every member's sweep captured into one CUDA
+    # graph and replayed; FP32 and BF16 storage
+    batch_apply = None
+    if args.batch_apply > 0:
+        probs = W.batched_4d(n=args.batch_apply, seed=0, levels=(6, 7, 8, 9))
+        tb = time.perf_counter()
+        solvers = [P.Solver(pr, precision=P.SGDG_MIXED_FP32, device=local) for pr in probs]
+        bsetup = time.perf_counter() - tb
+        dof = sum(sv.n_coeffs for sv in solvers)
+        log(f"batched apply: {len(solvers)} handles set up in {bsetup:.1f} s")
+        batch_apply = {"workload": f"{len(probs)} x transport_4d free streaming (beta = (v, 0)), "
+                                   f"L drawn from {{6,7,8,9}} (seed 0)",
+                       "levels": [p.L for p in probs], "dof_total": dof, "setup_s": round(bsetup, 2)}
+        for nm, dt_, pr in (("f32", torch.float32, P.SGDG_MIXED_FP32), ("bf16", torch.bfloat16, P.SGDG_BF16_STORE)):
+            bus = [torch.tensor(W.uniform_vector(sv.n_coeffs, seed=100 + k), device="cuda").to(dt_)
+                   for k, sv in enumerate(solvers)]
+            bys = [torch.empty_like(x) for x in bus]
+            ta = time.perf_counter()
+            tuned = {}                      # one autotuned handle per level; the others copy its shapes
+            for sv, x, y, pb in zip(solvers, bus, bys, probs):
+                if pb.L in tuned:
+                    sv.copy_tuning(tuned[pb.L])
+                else:
+                    sv.autotune(x, y, pr, stream)
+                    tuned[pb.L] = sv
+            tune = time.perf_counter() - ta
+            B = P.Batch(solvers)
+            B.apply(bus, bys, pr, stream)          # capture
+            l0 = sum(sv.launch_count() for sv in solvers)
+            bms = timed(lambda: B.apply(bus, bys, pr, stream), args.steps, 2)
+            batch_apply[nm] = {"apply_graph_ms": bms, "GDoFps": dof / (bms * 1e-3) / 1e9, "autotune_s": round(tune, 2)}
+            log(f"batched apply {nm}: {bms:.2f} ms")
+            B.close()
+            del bus, bys
+            torch.cuda.empty_cache()
+        for sv in solvers:
+            sv.close()
+        torch.cuda.empty_cache()
+
+    # ---- batched strips against the plain FP64 solver, on a reduced batch
+    # (the Krylov bases of config 3's 48 instances at L 6-9 do not fit in HBM):
+    # `batch` instances of uneven L, members concurrently; both arms start from
+    # the extrapolated guess (warm start 3); strip 3 is timed (the first with
+    # two earlier solutions to extrapolate from)
     batch = None
     if args.batch > 0:
         probs = W.batched_4d(n=args.batch, seed=0, levels=tuple(args.batch_levels))
@@ -407,18 +581,13 @@ def main():
         solvers = [P.Solver(pr, precision=P.SGDG_MIXED_FP32, rtol=1e-8, restart=30, inner_its=12,
                             inner_rtol=1e-2, device=local) for pr in probs]
         bsetup = time.perf_counter() - tb
+        bdof = sum(sv.n_coeffs for sv in solvers)
         bus = [torch.tensor(W.uniform_vector(sv.n_coeffs, seed=100 + k), dtype=torch.float32, device="cuda")
                for k, sv in enumerate(solvers)]
         bys = [torch.empty_like(x) for x in bus]
         for sv, x, y in zip(solvers, bus, bys):
             sv.autotune(x, y, P.SGDG_MIXED_FP32, stream)
         B = P.Batch(solvers)
-        B.apply(bus, bys, P.SGDG_MIXED_FP32, stream)          # capture
-        bms = timed(lambda: B.apply(bus, bys, P.SGDG_MIXED_FP32, stream), args.steps, 1)
-        dof = sum(sv.n_coeffs for sv in solvers)
-        # batched mixed precision with the extrapolated guess (warm start 3):
-        # all members concurrently; strip 3 is timed (the first with two
-        # earlier solutions to extrapolate from)
         for sv in solvers:
             sv.set_warm_start(3)
             sv.set_initial()
@@ -427,16 +596,15 @@ def main():
             t1 = time.perf_counter()
             st = B.advance()
             tstr.append(time.perf_counter() - t1)
+            log(f"batched strip {len(tstr)}: {tstr[-1]:.2f} s")
         B.close()
         for sv in solvers:
             sv.close()
-        # the plain FP64 solver on the same instances, one after another,
-        # previous-strip guess; strip 3 of each is timed
         t64, its64, res64 = 0.0, [], []
         for pr in probs:
             sv = P.Solver(pr, precision=P.SGDG_FP64, rtol=1e-8, restart=30, inner_its=12, inner_rtol=1e-2,
                           device=local)
-            sv.set_warm_start(1)
+            sv.set_warm_start(3)
             sv.set_initial()
             for k in range(3):
                 r = sv.advance_strip(check=False)
@@ -444,9 +612,11 @@ def main():
             its64.append(r.outer_its)
             res64.append(r.rel_residual)
             sv.close()
-        batch = {"workload": f"{args.batch} x transport_4d free streaming, L from {sorted(set(p.L for p in probs))}",
-                 "levels": [p.L for p in probs], "dof_total": dof, "setup_s": round(bsetup, 2),
-                 "apply_graph_ms": bms, "apply_GDoFps": dof / (bms * 1e-3) / 1e9,
+        batch = {"workload": f"{args.batch} x transport_4d free streaming, L from {sorted(set(p.L for p in probs))} "
+                             f"(reduced from config 3's 48 at L 6-9: Krylov bases)",
+                 "warm_start": "extrapolation of the last two strip solutions, both arms",
+                 "levels": [p.L for p in probs], "dof_total": bdof,
+                 "setup_s": round(bsetup, 2),
                  "s_per_batched_strip": round(tstr[-1], 4),
                  "max_rel_residual": max(x.rel_residual for x in st),
                  "outer_its": [x.outer_its for x in st],
@@ -458,7 +628,9 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu:
+            log("cpu baseline")
             cpu, _, _ = cpu_baseline()
+            log("cpu baseline done")
         line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -474,7 +646,10 @@ def main():
                 "bf16_apply": bf16_apply,
                 "rel_err_vs_fp64_apply": {"f32": err32, "bf16_storage": err16},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
-                "strip": strip, "batch": batch, "cpu_baseline": cpu}
+                "strip": strip, "batch_apply": batch_apply, "batch": batch, "cpu_baseline": cpu,
+                "peaks": {"fp32_alu_gflops": fp32_peak, "fp32_source": fp32_peak_src,
+                          "fp64_alu_gflops": fp64_peak, "fp64_source": fp64_peak_src,
+                          "hbm_gbs": peak, "hbm_source": peak_kind}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -156,6 +156,10 @@ typedef struct {
                            density (Sect. 5.3); needs a periodic Omega_x and
                            beta[d+i] = {coef -1, fx = initial E_i, fv = NULL} */
   int outer_method;     /* sgdg_outer; 0 (zero-initialised): FGMRES */
+  size_t hbm_budget_bytes; /* device memory the handle may hold (factors, state,
+                              sweep and solver buffers); 0: no limit.  An
+                              allocation that would pass it fails with
+                              SGDG_ENOMEM (at create or on first use). */
 } sgdg_config;
 
 typedef struct {
@@ -221,10 +225,11 @@ sgdg_status sgdg_apply_diag(void* h, int l1, int l2, const void* u, void* y, int
  * device array of SGDG_NOALLOC_SCRATCH_BYTES held by every GPU that loads the
  * library until the process exits; grids whose intermediates
  * (distinct v factors x n1 x n2 x 2 elements) do not fit are rejected with
- * SGDG_EINVAL and a message naming the size and the limit.  The first call on
- * a device looks up the array's device address; make that first call before
- * any stream capture.  All calls share the array: calls that overlap on the
- * GPU race.  u, y as for sgdg_apply_diag; precision SGDG_FP64 or
+ * SGDG_EINVAL and a message naming the size and the limit.  Every call looks
+ * up the array's device address (a host query, so a device reset cannot leave
+ * a stale address); the first call on a device also loads the library's
+ * device code there, so make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU race.  u, y as for sgdg_apply_diag; precision SGDG_FP64 or
  * SGDG_MIXED_FP32 (others: SGDG_EINVAL). */
 #define SGDG_NOALLOC_SCRATCH_BYTES (64u << 20)
 sgdg_status sgdg_apply_diag_noalloc(void* h, int l1, int l2, const void* u, void* y, int precision,
@@ -233,6 +238,24 @@ sgdg_status sgdg_apply_diag_noalloc(void* h, int l1, int l2, const void* u, void
  * configured inner iterations, restriction of the residual, combination).
  * r, z: device arrays of n_coeffs doubles. */
 sgdg_status sgdg_ct_precondition(void* h, const double* r, double* z, void* stream);
+
+/* Checkpoint and restore at a strip boundary (the strip scheme of Sect. 2
+ * carries only U^-_j from strip to strip; the file also holds what the
+ * library's warm starts and the Vlasov-Poisson field need to continue
+ * bit for bit).  sgdg_checkpoint writes, to the file at `path`: the strip
+ * count j and start time t_j, U^-_j, the last strip solution u_j, the one
+ * before it (extrapolated warm start), the next right-hand side, the
+ * warm-start mode and guess, and for vlasov_poisson handles the field E per
+ * finest cell with the density and potential; plus a 64-bit hash of the
+ * discrete problem (meshes, levels, dt, delta, term table, finest-level
+ * factor values at creation).  sgdg_restore reads such a file into a handle
+ * created with the same problem (hash mismatch: SGDG_EINVAL) and replaces
+ * its strip state; later sgdg_advance_strip calls then give the results an
+ * uninterrupted run gives, bit for bit (the solver's reductions are
+ * deterministic).  Both synchronise the device.  File errors: SGDG_EIO.
+ * sgdg_checkpoint needs sgdg_set_initial first (else SGDG_EINVAL). */
+sgdg_status sgdg_checkpoint(void* h, const char* path);
+sgdg_status sgdg_restore(void* h, const char* path);
 
 /* U^-_0 := u0 (the first right-hand side uses (u0, w^+) directly). */
 sgdg_status sgdg_set_initial(void* h);
@@ -329,6 +352,11 @@ sgdg_status sgdg_mlp_set_params(void* mlp, const float* params);
  * sgdg_apply_operator, overwritten) and keeps the fastest per site for all
  * later applies of this handle. */
 sgdg_status sgdg_autotune(void* h, const void* u, void* y, int precision, void* stream);
+/* Copies the autotuner's per-site choices of `src` into `dst` (sites are keyed
+ * by kernel kind, grid shape, chain count and element size, so handles of the
+ * same problem size share them; sites `dst` never meets are ignored) and
+ * clears any pinned shape of `dst`.  Host only. */
+sgdg_status sgdg_copy_tuning(void* dst, const void* src);
 /* Pins every sweep launch site of later applies to one launch shape,
  * code = rows per thread (1..15) | block order << 4 (0 row-major, 1 column
  * tiles) | two outputs per thread (final kernels, short-row chain steps) << 5
@@ -382,6 +410,14 @@ sgdg_status sgdg_kernel_stats(void* h, sgdg_kernel_stat* out, int n_kinds);
 int sgdg_struct_sizes(int* out, int n);
 /* Number of SpMM kernels this handle has launched so far. */
 long long sgdg_launch_count(const void* h);
+/* Measured multiply-add peak of device `device` (measurement; no counterpart
+ * in the paper): a register-only kernel runs 8 independent multiply-add
+ * chains per thread, `iters` steps each, on every SM (as many 256-thread
+ * blocks as fit), timed with CUDA events, best of 3 after a warm-up.
+ * precision SGDG_MIXED_FP32 (FP32 FFMA) or SGDG_FP64 (DFMA); others EINVAL.
+ * gflops: 2 flops per multiply-add / the best time; ms (may be NULL): that
+ * time.  Allocates one small device buffer and frees it. */
+sgdg_status sgdg_alu_peak(int device, int precision, int iters, double* gflops, double* ms);
 
 #ifdef __cplusplus
 }

@@ -57,7 +57,7 @@ class Config(C.Structure):
                 ("dt", C.c_double), ("delta", C.c_double), ("precision", C.c_int), ("rtol", C.c_double),
                 ("max_outer", C.c_int), ("restart", C.c_int), ("inner_its", C.c_int),
                 ("inner_rtol", C.c_double), ("cheb_steps", C.c_int), ("device", C.c_int),
-                ("vlasov_poisson", C.c_int), ("outer_method", C.c_int)]
+                ("vlasov_poisson", C.c_int), ("outer_method", C.c_int), ("hbm_budget_bytes", C.c_size_t)]
 
 
 class Info(C.Structure):
@@ -126,6 +126,10 @@ EXPORTS = {
     "sgdg_batch_apply": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
                                    C.c_void_p]),
     "sgdg_batch_advance": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sgdg_alu_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "sgdg_checkpoint": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "sgdg_copy_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sgdg_restore": (C.c_int, [C.c_void_p, C.c_char_p]),
 }
 
 KERNEL_KINDS = ("s_chain", "final_left", "restrict_dim1", "restrict_dim2", "chain_a", "chain_b", "reserved",
@@ -188,7 +192,8 @@ class Solver:
 
     def __init__(self, problem, precision: int = SGDG_FP64, rtol: float = 1e-10, max_outer: int = 200,
                  restart: int = 30, inner_its: int = 20, inner_rtol: float = 1e-3, cheb_steps: int = 6,
-                 device: int = 0, vlasov_poisson: bool = False, outer_method: int = SGDG_OUTER_FGMRES):
+                 device: int = 0, vlasov_poisson: bool = False, outer_method: int = SGDG_OUTER_FGMRES,
+                 hbm_budget_bytes: int = 0):
         self.lib = load_library()
         self.problem = problem
         self._keep: List = []
@@ -210,6 +215,7 @@ class Solver:
         cfg.device = device
         cfg.vlasov_poisson = int(vlasov_poisson)
         cfg.outer_method = int(outer_method)
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
         co = Coeffs()
         d = problem.d
         for p in range(4):
@@ -340,6 +346,12 @@ class Solver:
             self._check(code)
         return st
 
+    def checkpoint(self, path: str):
+        self._check(self.lib.sgdg_checkpoint(self.h, os.fsencode(path)))
+
+    def restore(self, path: str):
+        self._check(self.lib.sgdg_restore(self.h, os.fsencode(path)))
+
     def get_solution(self, dst, on_device: bool = True):
         self._check(self.lib.sgdg_get_solution(self.h, _ptr(dst), int(on_device)))
 
@@ -411,6 +423,10 @@ class Solver:
     def autotune(self, u, y, precision: int = SGDG_MIXED_FP32, stream=None):
         self._check(self.lib.sgdg_autotune(self.h, _ptr(u), _ptr(y), precision, _stream(stream)))
 
+    def copy_tuning(self, other: "Solver"):
+        """Take over another handle's autotuned launch shapes (same problem sizes)."""
+        self._check(self.lib.sgdg_copy_tuning(self.h, other.h))
+
     def set_launch_shape(self, code: int):
         """Pin every sweep launch site to one shape (0: tuned or default)."""
         self._check(self.lib.sgdg_set_launch_shape(self.h, code))
@@ -428,6 +444,17 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def alu_peak(precision: int, device: int = 0, iters: int = 1 << 16):
+    """Measured multiply-add peak of the device in GFLOP/s (sgdg_alu_peak):
+    precision SGDG_MIXED_FP32 (FFMA) or SGDG_FP64 (DFMA).  Returns (GFLOP/s, ms)."""
+    lib = load_library()
+    g, ms = C.c_double(), C.c_double()
+    st = lib.sgdg_alu_peak(device, precision, iters, C.byref(g), C.byref(ms))
+    if st != 0:
+        raise SgdgError(st, "sgdg_alu_peak")
+    return g.value, ms.value
 
 
 class Batch:

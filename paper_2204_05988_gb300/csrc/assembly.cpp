@@ -118,7 +118,39 @@ static void project_down(const Hierarchy& h, std::vector<Csr>& X) {
   }
 }
 
-Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec& f, std::vector<Csr>& X) {
+Status prefill_cache(const Hierarchy& h, const SideFns& fns, const std::vector<FactorSpec>& specs, QuadCache& cache) {
+  // one serial assembly of a plain volume factor fills the points and positions
+  FactorSpec plain;
+  std::vector<Csr> X;
+  Status st = assemble_factor(h, fns, plain, X, &cache);
+  if (st.code) return st;
+  const int d = h.d, d1 = d + 1;
+  const MeshLevel& lv = h.lev[h.L];
+  const int nc = lv.ncells(d);
+  std::vector<double> cen;
+  for (const FactorSpec& f : specs) {
+    if (f.kind != 0) continue;
+    for (int id : f.wfn) {
+      if (fns.cell_field(id) || cache.fn_vals.count(id)) continue;
+      if (!fns.fn[id]) return {SGDG_EINVAL, "factor needs a coefficient function that is no longer available"};
+      eval_fn(fns, id, cache.pts, d, cache.fn_vals[id]);
+    }
+    for (auto& rs : f.restrict_) {
+      if (fns.cell_field(rs.first) || cache.cen_vals.count(rs.first)) continue;
+      if (cen.empty()) {
+        cen.assign((size_t)nc * d, 0.0);
+        for (int e = 0; e < nc; ++e)
+          for (int a = 0; a < d1; ++a)
+            for (int k = 0; k < d; ++k) cen[(size_t)e * d + k] += lv.cell_coords[((size_t)e * d1 + a) * d + k] / d1;
+      }
+      eval_fn(fns, rs.first, cen, d, cache.cen_vals[rs.first]);
+    }
+  }
+  return {};
+}
+
+Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec& f, std::vector<Csr>& X,
+                       QuadCache* cache) {
   const int d = h.d, d1 = d + 1, L = h.L;
   const MeshLevel& lv = h.lev[L];
   const Csr& P = lv.pattern;
@@ -145,23 +177,31 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
         if (const std::vector<double>* cf = fns.cell_field(rs.first)) {
           if ((int)cf->size() != nc) return {SGDG_EINVAL, "cell field size differs from the finest cell count"};
           val = *cf;
+        } else if (cache && cache->cen_vals.count(rs.first)) {
+          val = cache->cen_vals.at(rs.first);
         } else {
           eval_fn(fns, rs.first, cen, d, val);
+          if (cache) cache->cen_vals[rs.first] = val;
         }
         for (int e = 0; e < nc; ++e)
           if (!(rs.second * val[e] > 0.0)) keep[e] = 0;
       }
     }
     // quadrature points of all cells and the weight product there
-    std::vector<double> pts((size_t)nc * nq * d);
-    for (int e = 0; e < nc; ++e) {
-      const double* v0 = &lv.cell_coords[(size_t)e * d1 * d];
-      for (int q = 0; q < nq; ++q)
-        for (int k = 0; k < d; ++k) {
-          double x = v0[k];
-          for (int a = 1; a < d1; ++a) x += (v0[a * d + k] - v0[k]) * rp[q * d + (a - 1)];
-          pts[((size_t)e * nq + q) * d + k] = x;
-        }
+    std::vector<double> own_pts;
+    std::vector<double>& pts = cache ? cache->pts : own_pts;
+    if (pts.size() != (size_t)nc * nq * d) {
+      pts.assign((size_t)nc * nq * d, 0.0);
+#pragma omp parallel for schedule(static)
+      for (int e = 0; e < nc; ++e) {
+        const double* v0 = &lv.cell_coords[(size_t)e * d1 * d];
+        for (int q = 0; q < nq; ++q)
+          for (int k = 0; k < d; ++k) {
+            double x = v0[k];
+            for (int a = 1; a < d1; ++a) x += (v0[a * d + k] - v0[k]) * rp[q * d + (a - 1)];
+            pts[((size_t)e * nq + q) * d + k] = x;
+          }
+      }
     }
     std::vector<double> wprod((size_t)nc * nq, 1.0), tmp;
     for (int id : f.wfn) {
@@ -172,8 +212,19 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
         continue;
       }
       if (!fns.fn[id]) return {SGDG_EINVAL, "factor needs a coefficient function that is no longer available"};
-      eval_fn(fns, id, pts, d, tmp);
-      for (size_t i = 0; i < wprod.size(); ++i) wprod[i] *= tmp[i];
+      const std::vector<double>* vals = nullptr;
+      if (cache) {
+        auto it = cache->fn_vals.find(id);
+        if (it == cache->fn_vals.end()) {
+          eval_fn(fns, id, pts, d, tmp);
+          it = cache->fn_vals.emplace(id, std::move(tmp)).first;
+        }
+        vals = &it->second;
+      } else {
+        eval_fn(fns, id, pts, d, tmp);
+        vals = &tmp;
+      }
+      for (size_t i = 0; i < wprod.size(); ++i) wprod[i] *= (*vals)[i];
     }
     // element matrices in parallel, then one ordered scatter: the assembled
     // values do not depend on the thread count (bit-reproducible set-up)
@@ -219,11 +270,21 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
       for (int i = 0; i < d1; ++i)
         for (int j = 0; j < d1; ++j) Kall[((size_t)e * d1 + i) * d1 + j] = Ke[i][j];
     }
+    std::vector<int> own_pos;
+    std::vector<int>& pos = cache ? cache->pos : own_pos;
+    if (pos.size() != (size_t)nc * d1 * d1) {
+      pos.assign((size_t)nc * d1 * d1, 0);
+#pragma omp parallel for schedule(static)
+      for (int e = 0; e < nc; ++e) {
+        const int* cv = &lv.cells[(size_t)e * d1];
+        for (int i = 0; i < d1; ++i)
+          for (int j = 0; j < d1; ++j) pos[((size_t)e * d1 + i) * d1 + j] = find_pos(P, cv[i], cv[j]);
+      }
+    }
     for (int e = 0; e < nc; ++e) {
       if (!keep[e]) continue;
-      const int* cv = &lv.cells[(size_t)e * d1];
       for (int i = 0; i < d1; ++i)
-        for (int j = 0; j < d1; ++j) A.val[find_pos(P, cv[i], cv[j])] += Kall[((size_t)e * d1 + i) * d1 + j];
+        for (int j = 0; j < d1; ++j) A.val[pos[((size_t)e * d1 + i) * d1 + j]] += Kall[((size_t)e * d1 + i) * d1 + j];
     }
   } else {
     // boundary faces on one side

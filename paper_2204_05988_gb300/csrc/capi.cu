@@ -28,6 +28,10 @@ static std::vector<void*>& registry(Handle* h) {
 cudaError_t dev_alloc(Handle& h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
+  {
+    std::lock_guard<std::mutex> lk(registry_mutex());
+    if (h.budget && h.device_bytes + bytes > h.budget) return cudaErrorMemoryAllocation;   // over hbm_budget_bytes
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e == cudaSuccess) {
     std::lock_guard<std::mutex> lk(registry_mutex());
@@ -100,19 +104,28 @@ Status upload_ell_vals(Handle& h, const std::vector<int>& rowptr, const std::vec
   return {};
 }
 
-Status upload_factor_products(Handle& h, const Hierarchy& hi, SideDev& sd, int f, const std::vector<Csr>& X) {
+void factor_products(const Hierarchy& hi, const SideDev& sd, const std::vector<Csr>& X, FactorProducts& out) {
   const int L = hi.L;
-  std::vector<double> v;
-  for (int l = 0; l < L && sd.has_rf; ++l) {
-    product_values(hi.Rt[l], hi.Rt[l].val, X[l + 1], X[l + 1].val, sd.RF_pat[l], v);
-    SG_ST(upload_ell_vals(h, sd.RF_pat[l].rowptr, v, sd.rf_w(), &sd.v64.ell_RF[f][l], &sd.v32.ell_RF[f][l]));
-  }
-  if (!sd.has_fp) return {};
-  for (int l = 1; l <= L; ++l) {
-    product_values(X[l], X[l].val, hi.E[l - 1], hi.E[l - 1].val, sd.FP_pat[l], v);
-    SG_ST(upload_ell_vals(h, sd.FP_pat[l].rowptr, v, sd.fp_w(), &sd.v64.ell_FP[f][l], &sd.v32.ell_FP[f][l]));
-  }
+  out.rf.assign(L, {});
+  out.fp.assign(L + 1, {});
+  for (int l = 0; l < L && sd.has_rf; ++l)
+    product_values(hi.Rt[l], hi.Rt[l].val, X[l + 1], X[l + 1].val, sd.RF_pat[l], out.rf[l]);
+  for (int l = 1; l <= L && sd.has_fp; ++l)
+    product_values(X[l], X[l].val, hi.E[l - 1], hi.E[l - 1].val, sd.FP_pat[l], out.fp[l]);
+}
+
+Status upload_products(Handle& h, SideDev& sd, int f, const FactorProducts& pr) {
+  for (int l = 0; l < (int)pr.rf.size() && sd.has_rf; ++l)
+    SG_ST(upload_ell_vals(h, sd.RF_pat[l].rowptr, pr.rf[l], sd.rf_w(), &sd.v64.ell_RF[f][l], &sd.v32.ell_RF[f][l]));
+  for (int l = 1; l < (int)pr.fp.size() && sd.has_fp; ++l)
+    SG_ST(upload_ell_vals(h, sd.FP_pat[l].rowptr, pr.fp[l], sd.fp_w(), &sd.v64.ell_FP[f][l], &sd.v32.ell_FP[f][l]));
   return {};
+}
+
+Status upload_factor_products(Handle& h, const Hierarchy& hi, SideDev& sd, int f, const std::vector<Csr>& X) {
+  FactorProducts pr;
+  factor_products(hi, sd, X, pr);
+  return upload_products(h, sd, f, pr);
 }
 
 namespace {
@@ -225,6 +238,15 @@ void make_plan(Plan& p, const std::vector<Term>& terms) {
   p.D = cv.size() <= cx.size() ? cv : cx;
 }
 
+// FNV-1a, 64 bit, over raw bytes (the problem identity of checkpoints)
+void fnv(unsigned long long& hsh, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) {
+    hsh ^= b[i];
+    hsh *= 1099511628211ULL;
+  }
+}
+
 struct ErrStore {
   std::string msg;
 };
@@ -257,10 +279,22 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   h.cfg = cfg;
   h.d = cfg.mesh_x.dim;
   h.L = cfg.level_L;
+  h.budget = cfg.hbm_budget_bytes;
+  h.problem_hash = 1469598103934665603ULL;
+  fnv(h.problem_hash, &h.d, sizeof(h.d));
+  fnv(h.problem_hash, &h.L, sizeof(h.L));
+  fnv(h.problem_hash, &cfg.dt, sizeof(cfg.dt));
+  fnv(h.problem_hash, &cfg.delta, sizeof(cfg.delta));
   SG_CU(cudaSetDevice(cfg.device));
   Hierarchy hx, hv;
-  SG_ST(build_hierarchy(cfg.mesh_x, h.L, hx));
-  SG_ST(build_hierarchy(cfg.mesh_v, h.L, hv));
+  {
+    Status sv;   // the two level hierarchies are independent: build them side by side
+    std::thread tv([&] { sv = build_hierarchy(cfg.mesh_v, h.L, hv); });
+    Status sx = build_hierarchy(cfg.mesh_x, h.L, hx);
+    tv.join();
+    SG_ST(sx);
+    SG_ST(sv);
+  }
   SG_ST(build_terms(c, h.d, cfg.mesh_x, cfg.mesh_v, cfg.dt, cfg.delta, h.tt));
   // callback tables: ids 0..3 beta components, 4 sigma
   SideFns fx, fv;
@@ -316,17 +350,39 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
     sd.v32.ell_RF.assign(fs.size(), std::vector<float*>(h.L + 1, nullptr));
     sd.v64.ell_FP.assign(fs.size(), std::vector<double*>(h.L + 1, nullptr));
     sd.v32.ell_FP.assign(fs.size(), std::vector<float*>(h.L + 1, nullptr));
-    for (size_t f = 0; f < fs.size(); ++f) {
+    for (size_t f = 0; f < fs.size(); ++f)
       for (int id : fs[f].wfn)
         if (!fns.fn[id]) return {SGDG_EINVAL, "factor references a missing coefficient function"};
-      std::vector<Csr> X;
-      SG_ST(assemble_factor(hi, fns, fs[f], X));
+    // FP64 assembly of every factor of the side on the host: the coefficient
+    // callbacks run first, serially (quadrature points and centroids of the
+    // volume factors, cached; the boundary-face factors); then the volume
+    // factors and all products with the transfers are formed concurrently,
+    // one factor per thread - each factor's values do not depend on the
+    // thread count
+    QuadCache qc;
+    SG_ST(prefill_cache(hi, fns, fs, qc));
+    const int nf = (int)fs.size();
+    std::vector<std::vector<Csr>> Xs(nf);
+    std::vector<FactorProducts> Ps(nf);
+    std::vector<Status> sts(nf);
+    for (int f = 0; f < nf; ++f)
+      if (fs[f].kind != 0) sts[f] = assemble_factor(hi, fns, fs[f], Xs[f], &qc);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int f = 0; f < nf; ++f) {
+      if (fs[f].kind == 0) sts[f] = assemble_factor(hi, fns, fs[f], Xs[f], &qc);
+      if (!sts[f].code) factor_products(hi, sd, Xs[f], Ps[f]);
+    }
+    for (int f = 0; f < nf; ++f) SG_ST(sts[f]);
+    for (size_t f = 0; f < fs.size(); ++f) {
+      std::vector<Csr>& X = Xs[f];
+      fnv(h.problem_hash, X[h.L].val.data(), sizeof(double) * X[h.L].val.size());
+      fnv(h.problem_hash, X[h.L].col.data(), sizeof(int) * X[h.L].col.size());
       for (int l = 0; l <= h.L; ++l) {
         SG_ST(upload_vals(h, X[l].val, &sd.v64.fac[f][l], &sd.v32.fac[f][l]));
         SG_ST(upload_ell_vals(h, hi.lev[l].pattern.rowptr, X[l].val, sd.ell_w(), &sd.v64.ell_fac[f][l],
                               &sd.v32.ell_fac[f][l]));
       }
-      SG_ST(upload_factor_products(h, hi, sd, (int)f, X));
+      SG_ST(upload_products(h, sd, (int)f, Ps[f]));
       if ((int)f == sd.mass) {
         sd.v64.dinv.resize(h.L + 1);
         sd.v32.dinv.resize(h.L + 1);
@@ -342,6 +398,8 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
           SG_ST(upload_vals(h, di, &sd.v64.dinv[l], &sd.v32.dinv[l]));
         }
       }
+      std::vector<Csr>().swap(Xs[f]);
+      Ps[f] = FactorProducts();
     }
   }
   // grids, offsets
@@ -365,6 +423,11 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   for (int i = 1; i <= L; ++i) tmp = std::max(tmp, 2LL * h.X.n[i - 1] * h.V.n[L - i]);
   for (int i = 0; i < L; ++i) tmp = std::max(tmp, 2LL * h.X.n[i + 1] * h.V.n[L - i]);
   h.tmp_elems = tmp;
+  for (const Term& t : h.tt.terms) {
+    fnv(h.problem_hash, t.tau, sizeof(t.tau));
+    fnv(h.problem_hash, &t.x, sizeof(t.x));
+    fnv(h.problem_hash, &t.v, sizeof(t.v));
+  }
   make_plan(h.op, h.tt.terms);
   Term mt;
   mt.tau[0][0] = 1.0; mt.tau[0][1] = 0.0; mt.tau[1][0] = 0.0; mt.tau[1][1] = 1.0;
@@ -673,7 +736,8 @@ sgdg_status sgdg_set_initial(void* hp) {
   // b_1 = eta(t_0^+) (x) (u0, phi_{l,k}) = (1, -1) (x) sum_p fx_p (x) fv_p per grid
   const int np = (int)h->u0x.size();
   if (np == 0) {
-    cudaMemset(h->rhs, 0, sizeof(double) * h->n_coeffs);
+    if (cudaMemset(h->rhs, 0, sizeof(double) * h->n_coeffs) != cudaSuccess)
+      return fail(h, {SGDG_ECUDA, "set_initial: clearing the right-hand side"});
   } else {
     for (int l = 0; l <= h->L; ++l) {
       const int n1 = h->n1[l], n2 = h->n2[l];
@@ -682,15 +746,19 @@ sgdg_status sgdg_set_initial(void* hp) {
         for (int i = 0; i < n1; ++i) fx[(size_t)p * n1 + i] = h->u0coef[p] * h->u0x[p][l][i];
         for (int i = 0; i < n2; ++i) fv[(size_t)p * n2 + i] = h->u0v[p][h->L - l][i];
       }
-      double *dfx, *dfv;
+      double *dfx = nullptr, *dfv = nullptr;
+      Status st;
       if (cudaMalloc(&dfx, 8 * fx.size()) != cudaSuccess || cudaMalloc(&dfv, 8 * fv.size()) != cudaSuccess)
-        return fail(h, {SGDG_ENOMEM, "initial load vectors"});
-      cudaMemcpy(dfx, fx.data(), 8 * fx.size(), cudaMemcpyHostToDevice);
-      cudaMemcpy(dfv, fv.data(), 8 * fv.size(), cudaMemcpyHostToDevice);
-      outer_init(h->rhs + h->off[l], n1, n2, np, dfx, dfv, 1.0, -1.0, nullptr);
-      cudaDeviceSynchronize();
-      cudaFree(dfx);
-      cudaFree(dfv);
+        st = {SGDG_ENOMEM, "initial load vectors"};
+      else if (cudaMemcpy(dfx, fx.data(), 8 * fx.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+               cudaMemcpy(dfv, fv.data(), 8 * fv.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        st = {SGDG_ECUDA, "set_initial: uploading the initial load vectors"};
+      else if (outer_init(h->rhs + h->off[l], n1, n2, np, dfx, dfv, 1.0, -1.0, nullptr) != cudaSuccess ||
+               cudaDeviceSynchronize() != cudaSuccess)
+        st = {SGDG_ECUDA, "set_initial: forming the first right-hand side"};
+      if (dfx) cudaFree(dfx);
+      if (dfv) cudaFree(dfv);
+      if (st.code) return fail(h, st);
     }
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(h, {SGDG_ECUDA, "set_initial"});
@@ -752,6 +820,15 @@ sgdg_status sgdg_autotune(void* hp, const void* u, void* y, int prec, void* stre
     st = autotune<Bf16>(*h, (const __nv_bfloat16*)u, (__nv_bfloat16*)y, (cudaStream_t)stream);
   else st = {SGDG_EINVAL, "unknown precision"};
   return st.code ? fail(h, st) : SGDG_OK;
+}
+
+sgdg_status sgdg_copy_tuning(void* dst, const void* src) {
+  if (!dst || !src) return SGDG_EINVAL;
+  Handle* d = (Handle*)dst;
+  const Handle* sh = (const Handle*)src;
+  for (const auto& kv : sh->tuned_ch) d->tuned_ch[kv.first] = kv.second;
+  d->force_ch = 0;
+  return SGDG_OK;
 }
 
 namespace {

@@ -230,7 +230,17 @@ Status field_update(Handle& h, int source, double* energy) {
     en += 0.5 * e2 * area;
   }
   if (energy) *energy = en;
-  // re-assemble and upload every x factor that uses E
+  F.updated = true;
+  return field_reassemble(h);
+}
+
+// Re-assemble and upload every x factor whose weight or inflow split uses E,
+// from the current cell field F.E.
+Status field_reassemble(Handle& h) {
+  if (!h.field) return {SGDG_EINVAL, "the handle was not created with vlasov_poisson = 1"};
+  Handle::Field& F = *h.field;
+  const int d = h.d, L = h.L;
+  Status st;
   for (size_t f = 0; f < h.tt.xf.size(); ++f) {
     const FactorSpec& fs = h.tt.xf[f];
     bool uses = false;

@@ -139,8 +139,13 @@ struct Handle {
     std::vector<double> rho, phi;              // last density and potential
     Csr K, M;                                  // finest-level stiffness and mass (FP64)
     double* d_rowsum = nullptr;                // per-grid int U dv (device, sum of n1)
+    bool updated = false;                      // E comes from a field update (not the create-time callback)
   };
   std::unique_ptr<Field> field;
+  // identity of the discrete problem (meshes, levels, dt, delta, term table,
+  // finest-level factor values at creation), checked by sgdg_restore
+  unsigned long long problem_hash = 0;
+  size_t budget = 0;   // device-memory budget of the handle (0: none), checked by dev_alloc
   ~Handle();
 };
 
@@ -160,6 +165,11 @@ std::vector<double> ell_values(const std::vector<int>& rowptr, const std::vector
 // Values of factor f's products with the transfers (R_l F_{l+1}, F_l E_{l-1})
 // from its per-level matrices X, uploaded in ELL form (allocated on first use).
 Status upload_factor_products(Handle& h, const Hierarchy& hi, SideDev& sd, int f, const std::vector<Csr>& X);
+// The same in two steps: host values of the products (no device work; safe
+// to run concurrently for different factors), then their upload.
+struct FactorProducts { std::vector<std::vector<double>> rf, fp; };
+void factor_products(const Hierarchy& hi, const SideDev& sd, const std::vector<Csr>& X, FactorProducts& out);
+Status upload_products(Handle& h, SideDev& sd, int f, const FactorProducts& pr);
 // Uploads the FP64 and FP32 ELL values; allocates when *d64 is null, else overwrites.
 Status upload_ell_vals(Handle& h, const std::vector<int>& rowptr, const std::vector<double>& val, int w,
                        double** d64, float** d32);
@@ -189,6 +199,7 @@ Status autotune(Handle& h, const Store<T>* u, Store<T>* y, cudaStream_t s);
 // Vlasov-Poisson coupling (field.cu)
 Status field_setup(Handle& h, const sgdg_coeffs& c, const Hierarchy& hx, const Hierarchy& hv, const SideFns& fx);
 Status field_update(Handle& h, int source, double* energy);
+Status field_reassemble(Handle& h);
 
 // coarse full-grid views (coarse.cu)
 Status coarse_values(Handle& h, const double* u, int R, int lx, int lv, double* out, cudaStream_t s);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -78,8 +79,28 @@ struct FactorSpec {
   bool operator==(const FactorSpec& o) const;
 };
 
+// Quadrature data shared by the volume factors of one hierarchy and one
+// function table: the finest level's quadrature points, the coefficient
+// functions evaluated there (per function id) and the CSR position of every
+// element-matrix entry.  Filled on first use; valid only for the hierarchy
+// and table it was first used with.
+struct QuadCache {
+  std::vector<double> pts;
+  std::map<int, std::vector<double>> fn_vals;
+  std::map<int, std::vector<double>> cen_vals;   // functions at the finest cell centroids
+  std::vector<int> pos;
+};
+
+// Fills `cache` with everything the volume factors in `specs` read through it
+// (quadrature points, element scatter positions, every coefficient function
+// at the quadrature points and at the cell centroids), so that later
+// assemble_factor calls with this cache only read it (and may run
+// concurrently) and call no coefficient callback for volume factors.
+Status prefill_cache(const Hierarchy& h, const SideFns& fns, const std::vector<FactorSpec>& specs, QuadCache& cache);
+
 Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec& f,
-                       std::vector<Csr>& per_level);   // per_level[l] on lev[l].pattern
+                       std::vector<Csr>& per_level,    // per_level[l] on lev[l].pattern
+                       QuadCache* cache = nullptr);
 
 struct Term {
   double tau[kR][kR];  // time coupling [s][s']

@@ -16,8 +16,6 @@
 // scratch element is written before it is read, so nothing needs clearing.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "handle.h"
 #include "sweep.h"
 
@@ -27,25 +25,18 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SGDG_NOALLOC_SC
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-
-// Device address of g_noalloc_scratch on the current device, looked up once per
-// device (host code only holds a stand-in for the array, not its address).
+// Device address of g_noalloc_scratch on the current device (host code only
+// holds a stand-in for the array, not its address).  It is looked up on every
+// call: cudaGetSymbolAddress is a cheap host query, and a cached address
+// would go stale when the device is reset (cudaDeviceReset reloads the
+// module).  The first call on a device also loads the module there, so make
+// it before any stream capture.
 Status scratch_address(void** out) {
-  static std::mutex mu;
-  static void* addr[kMaxDevices] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return {SGDG_ECUDA, "no-alloc apply: cannot determine the current device"};
-  std::lock_guard<std::mutex> lk(mu);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return {SGDG_ECUDA, std::string("no-alloc apply: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e)};
-    addr[dev] = p;
-  }
-  *out = addr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return {SGDG_ECUDA, std::string("no-alloc apply: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e)};
+  *out = p;
   return {};
 }
 
@@ -132,8 +123,12 @@ using namespace sgdg;
 
 extern "C" sgdg_status sgdg_apply_diag_noalloc(void* hp, int l1, int l2, const void* u, void* y, int prec,
                                                void* stream) {
-  if (!hp || !u || !y) return SGDG_EINVAL;
+  if (!hp) return SGDG_EINVAL;
   Handle* h = (Handle*)hp;
+  if (!u || !y) {
+    h->err = "no-alloc apply: null input or output";
+    return SGDG_EINVAL;
+  }
   if (l1 < 0 || l2 < 0 || l1 > h->L || l2 > h->L || (l1 + l2 != h->L && l1 + l2 != h->L - 1)) {
     h->err = "no-alloc apply: grid levels must satisfy l1 + l2 in {L-1, L}";
     return SGDG_EINVAL;

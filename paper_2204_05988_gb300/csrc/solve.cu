@@ -151,6 +151,10 @@ Status mdot(Handle& h, int k, const T* V, long long ldv, const T* w, long long n
 
 // Arnoldi step: orthogonalise w against V_0..V_j (CGS2), normalise into V_{j+1}.
 // Returns the new Hessenberg column hcol[0..j+1] on the host.
+// sqrt of a reduced squared norm; NaN stays NaN (std::max(0.0, NaN) would
+// return 0.0 and hide it from the finiteness checks)
+inline double norm_of(double sq) { return std::isnan(sq) ? sq : std::sqrt(std::max(0.0, sq)); }
+
 template <typename T>
 Status arnoldi(Handle& h, T* V, long long n, int j, T* w, double* hcol, cudaStream_t s) {
   Workspace& ws = *h.ws;
@@ -163,7 +167,7 @@ Status arnoldi(Handle& h, T* V, long long n, int j, T* w, double* hcol, cudaStre
   SG_CU(cudaMemcpyAsync(ws.host, d, sizeof(double) * 3 * kMaxKrylov, cudaMemcpyDeviceToHost, s));
   SG_CU(cudaStreamSynchronize(s));
   for (int i = 0; i <= j; ++i) hcol[i] = ws.host[i] + ws.host[kMaxKrylov + i];
-  double nrm = std::sqrt(std::max(0.0, ws.host[2 * kMaxKrylov]));
+  double nrm = norm_of(ws.host[2 * kMaxKrylov]);
   hcol[j + 1] = nrm;
   if (!std::isfinite(nrm)) return {SGDG_ENAN, "NaN/Inf in Krylov vector"};
   if (nrm > 0.0) SG_CU(vec_axpby<T>(n, 1.0 / nrm, w, 0.0, w, s));
@@ -176,7 +180,7 @@ Status vnorm(Handle& h, const T* x, long long n, double* out, cudaStream_t s) {
   SG_ST(mdot<T>(h, 1, x, n, x, n, ws.dev_dots, s));
   SG_CU(cudaMemcpyAsync(ws.host, ws.dev_dots, sizeof(double), cudaMemcpyDeviceToHost, s));
   SG_CU(cudaStreamSynchronize(s));
-  *out = std::sqrt(std::max(0.0, ws.host[0]));
+  *out = norm_of(ws.host[0]);
   if (!std::isfinite(*out)) return {SGDG_ENAN, "NaN/Inf in a residual"};
   return {};
 }
@@ -615,7 +619,7 @@ Status ct_apply(Handle& h, const T* r, T* z, cudaStream_t s, int* its) {
   Gv.resize(NG);
   Active act;
   for (int g = 0; g < NG; ++g) {
-    beta[g] = std::sqrt(std::max(0.0, B.host[(long long)g * LD + 2 * kMaxKrylov]));
+    beta[g] = norm_of(B.host[(long long)g * LD + 2 * kMaxKrylov]);
     if (!std::isfinite(beta[g])) return {SGDG_ENAN, "NaN/Inf in a component right-hand side"};
     if (beta[g] > 0.0) {
       act.g.push_back(g);
@@ -680,7 +684,7 @@ Status ct_apply(Handle& h, const T* r, T* z, cudaStream_t s, int* its) {
       const double* hd = B.host + (long long)g * LD;
       double hcol[kMaxKrylov + 1];
       for (int i = 0; i <= j; ++i) hcol[i] = hd[i] + hd[kMaxKrylov + i];
-      const double nrm = std::sqrt(std::max(0.0, hd[2 * kMaxKrylov]));
+      const double nrm = norm_of(hd[2 * kMaxKrylov]);
       if (!std::isfinite(nrm)) return {SGDG_ENAN, "NaN/Inf in a component Krylov vector"};
       hcol[j + 1] = nrm;
       const double res = Gv[g].add(j, hcol);
