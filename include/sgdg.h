@@ -300,6 +300,19 @@ sgdg_status sgdg_resolve_strip(void* h, void* stream, sgdg_strip_stats* stats);
  * SGDG_ENOCONV when a solve hits max_outer. */
 sgdg_status sgdg_advance_strip_vp(void* h, void* stream, double tol, int max_fp, sgdg_strip_stats* stats,
                                   int* fp_steps, double* phi_change);
+/* Stop test of sgdg_advance_strip_vp's fixed point: 0 (default) the relative
+ * l2 change of the potential phi between field updates; 1 the test of
+ * Sect. 5.3, ||E^(k+1) - E^(k)||_{L^inf(I_j x Omega_x)} +
+ * ||f^(k+1) - f^(k)||_{H^1(I_j x Omega)}, with f^(0) = U^-_{j-1} constant in
+ * time on the strip and E constant in time on the strip (midpoint rule);
+ * phi_change then reports that sum.  Other values: SGDG_EINVAL. */
+sgdg_status sgdg_set_vp_stop(void* h, int criterion);
+/* *out = ||U||_{H^1(I_j x Omega)}, the norm of Algorithm 1's stop test
+ * (Sect. 4.3): int_{I_j} ||U||^2 + ||d_t U||^2 + ||grad_x U||^2 +
+ * ||grad_v U||^2 dt for the strip function with coefficients u (device
+ * array of n_coeffs doubles), from the Gram form applied blockwise in FP64.
+ * Synchronises `stream`. */
+sgdg_status sgdg_h1_norm(void* h, const double* u, double* out, void* stream);
 /* Initial guess of the next sgdg_advance_strip: 0 zero (default), 1 the
  * previous strip's solution, 2 the array last given to sgdg_set_guess, 3 the
  * linear extrapolation 2 u_{j-1} - u_{j-2} of the last two strip solutions
@@ -352,6 +365,14 @@ sgdg_status sgdg_mlp_set_params(void* mlp, const float* params);
  * sgdg_apply_operator, overwritten) and keeps the fastest per site for all
  * later applies of this handle. */
 sgdg_status sgdg_autotune(void* h, const void* u, void* y, int precision, void* stream);
+/* Which kernels run the sweep's branch A (no counterpart in the paper; both
+ * compute the same operator, up to rounding order):
+ * 0 (default): one fused launch per grid where a tile plan fits - the states
+ *   S_b = U V_b^T + P1 Z_b are formed per tile in shared memory, folded into
+ *   y and restricted there, and never written to device memory;
+ * 1: the unfused kernels (S_b written per grid, then final update and
+ *   restriction).  Other values: SGDG_EINVAL. */
+sgdg_status sgdg_set_sweep_variant(void* h, int variant);
 /* Copies the autotuner's per-site choices of `src` into `dst` (sites are keyed
  * by kernel kind, grid shape, chain count and element size, so handles of the
  * same problem size share them; sites `dst` never meets are ignored) and
@@ -385,8 +406,9 @@ sgdg_status sgdg_batch_advance(void* batch, sgdg_strip_stats* per_member);
  * 0 = per-grid states S_b = u V_b^T (+ P1 Z_b) of the sweep's branch A and of
  *     the diagonal blocks, 1 = final updates y (+)= tau X S_b along dim 1,
  * 2 / 3 = restriction of sweep chain states along dim 1 / dim 2,
- * 4 / 5 = sweep chain steps of branch A (no launches: branch A restricts the
- *     states S_b, kind 3) / branch B, 6 = reserved (no launches),
+ * 4 = fused branch-A launches (S_b per tile in shared memory, final update
+ *     and restriction in one kernel), 5 = sweep chain steps of branch B,
+ * 6 = reserved (no launches),
  * 7 = final updates of branch B along dim 2.
  * n_kinds must be >= 8. */
 typedef struct {

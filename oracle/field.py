@@ -12,9 +12,22 @@ Per strip, from the end value U^-_{j-1} (u0 before the first strip):
   E = -grad phi on every finest cell; beta = (v, -E) is installed in the
            problem as cell-constant factors.
 
+``vp_strip``: the fixed point of Sect. 5.3 on one strip.  Starting from
+f^(0) = U^-_{j-1} (constant in time on the strip) and its field E^(0), it
+alternates a strip solve with the field frozen, f^(k+1) from E^(k), and the
+field of the new solution at the strip midpoint (the midpoint rule),
+E^(k+1) from f^(k+1), until
+    ||E^(k+1) - E^(k)||_{L^inf(I_j x Omega_x)} + ||f^(k+1) - f^(k)||_{H^1(I_j x Omega)} < eps
+(E is constant in time on the strip, so the first norm is the largest cell
+value of any component; the second is ``norms.h1_norm_nodal`` of the
+difference of the strip functions).  The returned solution is f^(k+1) of the last
+solve, the field the one it was solved with.
+
 Pinned by tests/test_oracle_field.py: the Poisson solution of a cosine
 density against the exact potential (second-order convergence), the density
-of u0, and Landau-type energy of a single mode.
+of u0, Landau-type energy of a single mode, and the fixed point's
+consistency (at convergence the returned strip solution solves the strip
+with the field of its own midpoint density, to the tolerance).
 """
 from __future__ import annotations
 
@@ -82,3 +95,39 @@ def install_field(op: SparseGridOperator, prob, E: np.ndarray) -> None:
     for i in range(d):
         prob.beta[d + i] = W.Product(prob.beta[d + i].coef, CellField(E[i]), None)
     op.terms = kron_terms(prob)
+
+
+def constant_in_time(U: np.ndarray, R: int) -> np.ndarray:
+    """The strip vector of a spatial function constant on the strip
+    (coefficient of eta_0 = 1; higher Legendre coefficients zero)."""
+    u = np.zeros((U.size, R))
+    u[:, 0] = U
+    return u.ravel()
+
+
+def vp_strip(solver, prob, U_prev: np.ndarray, rho_prev: np.ndarray, MU: np.ndarray, t0: float,
+             eps: float, max_fp: int = 50):
+    """One strip of the Vlasov-Poisson fixed point (Sect. 5.3).
+
+    solver: an oracle StripSolver of the problem (its operator's field is
+    replaced); U_prev: U^-_{j-1}; rho_prev: its density (the caller passes
+    the interpolant of int u0 dv before the first strip); MU: M_sg U^-_{j-1}
+    (or (u0, phi) for the first strip).  Returns (u, E, iterations, last
+    criterion value); iterations counts the strip solves."""
+    from .norms import h1_norm_nodal
+    op = solver.op
+    R = op.R
+    b = solver.rhs(MU, t0)
+    _, E, _ = poisson(op, rho_prev)
+    f_prev = constant_in_time(U_prev, R)
+    crit = np.inf
+    for k in range(1, max_fp + 1):
+        install_field(op, prob, E)
+        u, _, _ = solver.solve_strip(b)
+        rho = density(op, u.reshape(-1, R)[:, 0])          # midpoint: eta_0 = 1, eta_1(1/2) = 0
+        _, E_new, _ = poisson(op, rho)
+        crit = float(np.abs(E_new - E).max()) + h1_norm_nodal(op, u - f_prev)
+        if crit < eps:
+            return u, E, k, crit
+        E, f_prev = E_new, u
+    return u, E, max_fp, crit

@@ -129,10 +129,13 @@ EXPORTS = {
     "sgdg_alu_peak": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "sgdg_checkpoint": (C.c_int, [C.c_void_p, C.c_char_p]),
     "sgdg_copy_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sgdg_set_sweep_variant": (C.c_int, [C.c_void_p, C.c_int]),
+    "sgdg_set_vp_stop": (C.c_int, [C.c_void_p, C.c_int]),
+    "sgdg_h1_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "sgdg_restore": (C.c_int, [C.c_void_p, C.c_char_p]),
 }
 
-KERNEL_KINDS = ("s_chain", "final_left", "restrict_dim1", "restrict_dim2", "chain_a", "chain_b", "reserved",
+KERNEL_KINDS = ("s_chain", "final_left", "restrict_dim1", "restrict_dim2", "fused_a", "chain_b", "reserved",
                 "final_right")
 
 
@@ -404,6 +407,15 @@ class Solver:
     def add_coarse(self, c, lx: int, lv: int, u, stream=None):
         self._check(self.lib.sgdg_add_coarse(self.h, _ptr(c), lx, lv, _ptr(u), _stream(stream)))
 
+    def set_vp_stop(self, criterion: int):
+        """Fixed-point stop of advance_strip_vp: 0 relative change of phi, 1 the norms of Sect. 5.3."""
+        self._check(self.lib.sgdg_set_vp_stop(self.h, criterion))
+
+    def h1_norm(self, u, stream=None) -> float:
+        out = C.c_double()
+        self._check(self.lib.sgdg_h1_norm(self.h, _ptr(u), C.byref(out), _stream(stream)))
+        return out.value
+
     def set_warm_start(self, mode: int):
         self._check(self.lib.sgdg_set_warm_start(self.h, mode))
 
@@ -422,6 +434,10 @@ class Solver:
 
     def autotune(self, u, y, precision: int = SGDG_MIXED_FP32, stream=None):
         self._check(self.lib.sgdg_autotune(self.h, _ptr(u), _ptr(y), precision, _stream(stream)))
+
+    def set_sweep_variant(self, variant: int):
+        """0: fused branch A where a tile plan fits (default); 1: unfused kernels."""
+        self._check(self.lib.sgdg_set_sweep_variant(self.h, variant))
 
     def copy_tuning(self, other: "Solver"):
         """Take over another handle's autotuned launch shapes (same problem sizes)."""

@@ -337,6 +337,78 @@ Status diag_block(Handle& h, const Plan& p, const Pool<T>& pool, int lx, int lv,
                       [&](const Term& tm) { return (const Comp<T>*)h.X.vals<Comp<T>>().ell_fac[tm.x][lx]; }, accumulate, y, s);
 }
 
+// Branch A on grid i in one fused launch (sweep_fused.cu): S_b formed per
+// tile in shared memory, Y_i = sum_a tau_a X_a S_b written, and the
+// restricted states Z_{b,i+1} passed on.  False in *done when no plan fits
+// (the caller then runs the unfused kernels).
+template <typename T>
+Status fused_branch_a(Handle& h, const Plan& p, const Pool<T>& pool, int i, const Store<T>* u, Store<T>* y,
+                      cudaStream_t s, bool* done) {
+  *done = false;
+  const int L = h.L, lx = i, lv = L - i;
+  const int nA = (int)p.A.size();
+  int nterms = 0;
+  for (const Chain& c : p.A) nterms += (int)c.terms.size();
+  const Handle::FusedGrid* fg = nullptr;
+  Status st = fused_plan(h, i, (int)(2 * sizeof(Comp<T>)), nA, nterms, &fg);
+  if (st.code || !fg) return st;
+  SideDev& X = h.X;
+  SideDev& V = h.V;
+  FusedArgs<T> a;
+  a.tiles = fg->tiles;
+  a.xrows = fg->xrows;
+  a.vcols = fg->vcols;
+  a.xnbr = fg->xnbr;
+  a.qcols = fg->qcols;
+  a.qloc = fg->qloc;
+  a.ntiles = fg->ntiles;
+  a.W = fg->W;
+  a.n2 = V.n[lv];
+  a.n2c = lv >= 1 ? V.n[lv - 1] : 0;
+  a.has_prev = i >= 1;
+  a.restrict_out = i < L;
+  a.nchains = nA;
+  a.G = fg->G;
+  a.U = u;
+  a.Y = y;
+  a.vcol = V.ell_col[lv];
+  int nt = 0;
+  for (int c = 0; c < nA; ++c) {
+    a.vval[c] = V.vals<Comp<T>>().ell_fac[p.A[c].first][lv];
+    a.zin[c] = i >= 1 ? pool.ZA(c, i & 1) : nullptr;
+    a.zout[c] = i < L ? pool.ZA(c, (i + 1) & 1) : nullptr;
+    a.tbeg[c] = nt;
+    for (int t : p.A[c].terms) {
+      const Term& tm = p.terms[t];
+      a.xval[nt] = X.vals<Comp<T>>().ell_fac[tm.x][lx];
+      for (int q = 0; q < 2; ++q)
+        for (int r = 0; r < 2; ++r) a.tau[nt][q * 2 + r] = (Comp<T>)tm.tau[q][r];
+      nt++;
+    }
+  }
+  a.tbeg[nA] = nt;
+  if (a.has_prev) {
+    a.pcol = X.E_ell_col[lx - 1];
+    a.pval = X.vals<Comp<T>>().ell_E[lx - 1];
+  }
+  if (a.restrict_out) {
+    a.rcol = V.R_ell_col[lv - 1];
+    a.rval = V.vals<Comp<T>>().ell_R[lv - 1];
+  }
+  ProfScope ps(h, s);
+  SG_CU(launch_fused_a(a, fg->smem, s));
+  const int n1 = X.n[lx], n2 = V.n[lv], W = fg->W;
+  const double g = grid_bytes<T>(n1, n2);
+  double bytes = 2.0 * g + ell_bytes<T>(n1, W, nt) + ell_bytes<T>(n2, W, nA);
+  if (a.has_prev) bytes += nA * grid_bytes<T>(X.n[lx - 1], n2) + ell_bytes<T>(n1, kEllE, 1);
+  if (a.restrict_out) bytes += nA * grid_bytes<T>(n1, a.n2c) + ell_bytes<T>(a.n2c, W, 1);
+  const double flops = 2.0 * (fg->s_points * nA * (2.0 * W + (a.has_prev ? 4.0 : 0.0)) +
+                              (double)n1 * n2 * nt * (2.0 * W + 4.0) + fg->q_points * nA * 2.0 * W);
+  ps.done(KIND_FUSED_A, bytes, -1, flops);
+  *done = true;
+  return {};
+}
+
 }  // namespace
 
 template <typename T>
@@ -355,6 +427,19 @@ Status apply_plan(Handle& h, const Plan& p, const Store<T>* u, Store<T>* y, cuda
     // S_{b,i} = U_i V_b^T + P1 Z_{b,i};  Y_i = sum_a tau_a X_a S_{b,i}
     if (hooks && hooks->ready) SG_CU(cudaStreamWaitEvent(s, hooks->ready[i], 0));
     Store<T>* yi = y + h.off[i];
+    bool fused = false;
+    if (h.sweep_variant == 0) {
+      st = fused_branch_a<T>(h, p, pool, i, u + h.off[i], yi, s, &fused);
+      if (st.code) return st;
+    }
+    if (fused) {
+      if (i == L && hooks && hooks->done) {
+        st = hooks->done(hooks->ctx, L);
+        if (st.code) return st;
+      }
+      if (i == L) break;
+      continue;
+    }
     st = diag_block<T>(h, p, pool, i, lv, u + h.off[i], yi, false, s,
                        [&](int c) { return i >= 1 ? (const Store<T>*)pool.ZA(c, i & 1) : (const Store<T>*)nullptr; });
     if (st.code) return st;

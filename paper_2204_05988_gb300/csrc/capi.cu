@@ -314,6 +314,14 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   };
   h.X.mass = find_or_add(h.tt.xf);
   h.V.mass = find_or_add(h.tt.vf);
+  // stiffness factors (d/dy_p, d/dy_p) of both sides for the H^1 Gram plan
+  int kx[3] = {0, 0, 0}, kv[3] = {0, 0, 0};
+  for (int p = 1; p <= h.d; ++p) {
+    mass.test = mass.trial = p;
+    kx[p - 1] = find_or_add(h.tt.xf);
+    kv[p - 1] = find_or_add(h.tt.vf);
+  }
+  mass.test = mass.trial = 0;
   // the sweep kernels keep one matrix row of at most 8 entries (prolongation:
   // kProlongRow) in registers
   int side_maxrow[2] = {0, 0};
@@ -434,6 +442,26 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   mt.x = h.X.mass;
   mt.v = h.V.mass;
   make_plan(h.mass, std::vector<Term>{mt});
+  {
+    // H^1(I_j x Omega) Gram form in the Legendre time basis: M_t = dt diag(1, 1/3),
+    // C_t = int eta_s' eta_s'' = diag(0, 4 / dt)
+    const double dt = cfg.dt;
+    std::vector<Term> g;
+    Term t0 = mt;
+    t0.tau[0][0] = dt;
+    t0.tau[1][1] = dt / 3.0 + 4.0 / dt;
+    g.push_back(t0);
+    for (int p = 0; p < h.d; ++p) {
+      Term a = mt, b = mt;
+      a.tau[0][0] = b.tau[0][0] = dt;
+      a.tau[1][1] = b.tau[1][1] = dt / 3.0;
+      a.x = kx[p];
+      b.v = kv[p];
+      g.push_back(a);
+      g.push_back(b);
+    }
+    make_plan(h.h1, g);
+  }
   // u0 load vectors
   for (int k = 0; k < c.n_u0; ++k) {
     std::vector<std::vector<double>> lx, lv;
@@ -491,6 +519,8 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   SG_CU(cudaMemset(h.u_sol, 0, sizeof(double) * h.n_coeffs));
   SG_CU(cudaMemset(h.U_end, 0, sizeof(double) * h.n_spatial));
   SG_CU(cudaDeviceSynchronize());
+  h.hx_host = std::make_shared<Hierarchy>(std::move(hx));
+  h.hv_host = std::make_shared<Hierarchy>(std::move(hv));
   return {};
 }
 
@@ -822,6 +852,14 @@ sgdg_status sgdg_autotune(void* hp, const void* u, void* y, int prec, void* stre
   return st.code ? fail(h, st) : SGDG_OK;
 }
 
+sgdg_status sgdg_set_sweep_variant(void* hp, int variant) {
+  if (!hp) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  if (variant != 0 && variant != 1) return fail(h, {SGDG_EINVAL, "sweep variant must be 0 or 1"});
+  h->sweep_variant = variant;
+  return SGDG_OK;
+}
+
 sgdg_status sgdg_copy_tuning(void* dst, const void* src) {
   if (!dst || !src) return SGDG_EINVAL;
   Handle* d = (Handle*)dst;
@@ -1031,28 +1069,76 @@ sgdg_status sgdg_advance_strip_vp(void* hp, void* stream, double tol, int max_fp
   if (!(tol >= 0.0) || max_fp < 0) return fail(h, {SGDG_EINVAL, "tol and max_fp must be >= 0"});
   cudaStream_t s = (cudaStream_t)stream;
   double energy = 0.0;
+  const bool paper = h->vp_stop == 1;
+  if (paper && !h->vp_prev &&
+      (dev_alloc(*h, (void**)&h->vp_prev, sizeof(double) * h->n_coeffs) != cudaSuccess ||
+       dev_alloc(*h, (void**)&h->vp_tmp, sizeof(double) * h->n_coeffs) != cudaSuccess))
+    return fail(h, {SGDG_ENOMEM, "fixed-point buffers"});
   Status st = field_update(*h, 0, &energy);
+  // f^(0) = U^-_{j-1}, constant in time on the strip
+  if (!st.code && paper) st = constant_in_time(*h, h->U_end, h->vp_prev, s);
   if (!st.code) st = advance_strip(*h, s, stats, false);
   int k = 0;
   double change = 0.0;
   std::vector<double> prev = h->field->phi;
+  std::vector<std::vector<double>> E_prev = h->field->E;
   while (!st.code && k < max_fp) {
     st = field_update(*h, 1, &energy);
     if (st.code) break;
-    const std::vector<double>& phi = h->field->phi;
-    double dn = 0.0, pn = 0.0;
-    for (size_t i = 0; i < phi.size(); ++i) {
-      dn += (phi[i] - prev[i]) * (phi[i] - prev[i]);
-      pn += phi[i] * phi[i];
+    if (paper) {
+      // Sect. 5.3: ||E^(k+1) - E^(k)||_inf (E is constant in time on the strip)
+      // + ||f^(k+1) - f^(k)||_{H^1(I_j x Omega)}
+      double einf = 0.0;
+      for (size_t c = 0; c < E_prev.size(); ++c)
+        for (size_t e = 0; e < E_prev[c].size(); ++e)
+          einf = std::max(einf, std::fabs(h->field->E[c][e] - E_prev[c][e]));
+      if (vec_axpby<double>(h->n_coeffs, 1.0, h->u_sol, -1.0, h->vp_prev, s) != cudaSuccess) {
+        st = {SGDG_ECUDA, "fixed-point difference"};
+        break;
+      }
+      double fn = 0.0;
+      st = h1_norm(*h, h->vp_prev, h->vp_tmp, &fn, s);
+      if (st.code) break;
+      change = einf + fn;
+    } else {
+      const std::vector<double>& phi = h->field->phi;
+      double dn = 0.0, pn = 0.0;
+      for (size_t i = 0; i < phi.size(); ++i) {
+        dn += (phi[i] - prev[i]) * (phi[i] - prev[i]);
+        pn += phi[i] * phi[i];
+      }
+      change = pn > 0.0 ? std::sqrt(dn / pn) : std::sqrt(dn);
     }
-    change = pn > 0.0 ? std::sqrt(dn / pn) : std::sqrt(dn);
     if (change <= tol) break;
-    prev = phi;
+    prev = h->field->phi;
+    E_prev = h->field->E;
+    if (paper && cudaMemcpyAsync(h->vp_prev, h->u_sol, sizeof(double) * h->n_coeffs, cudaMemcpyDeviceToDevice, s) !=
+                     cudaSuccess) {
+      st = {SGDG_ECUDA, "fixed-point copy"};
+      break;
+    }
     st = advance_strip(*h, s, stats, true);
     ++k;
   }
   if (fp_steps) *fp_steps = k;
   if (phi_change) *phi_change = change;
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+sgdg_status sgdg_set_vp_stop(void* hp, int criterion) {
+  if (!hp) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  if (criterion != 0 && criterion != 1) return fail(h, {SGDG_EINVAL, "fixed-point stop must be 0 or 1"});
+  h->vp_stop = criterion;
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_h1_norm(void* hp, const double* u, double* out, void* stream) {
+  if (!hp || !u || !out) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  if (!h->vp_tmp && dev_alloc(*h, (void**)&h->vp_tmp, sizeof(double) * h->n_coeffs) != cudaSuccess)
+    return fail(h, {SGDG_ENOMEM, "H1 norm buffer"});
+  Status st = h1_norm(*h, u, h->vp_tmp, out, (cudaStream_t)stream);
   return st.code ? fail(h, st) : SGDG_OK;
 }
 

@@ -83,6 +83,7 @@ struct Handle {
   std::vector<long long> soff;       // spatial offsets
   long long n_coeffs = 0, n_spatial = 0;
   Plan op, mass;
+  Plan h1;   // H^1(I_j x Omega) Gram form: (M_t + C_t) (x) M (x) M + M_t (x) (K_p (x) M + M (x) K_p)
   // sweep buffers per precision (FP64, FP32, BF16 storage), allocated lazily
   struct Bufs {
     void* S = nullptr; void* Z = nullptr; void* TP = nullptr; void* tmp = nullptr; void* W = nullptr;
@@ -142,6 +143,29 @@ struct Handle {
     bool updated = false;                      // E comes from a field update (not the create-time callback)
   };
   std::unique_ptr<Field> field;
+  int vp_stop = 0;                 // fixed-point stop: 0 relative change of phi, 1 Sect. 5.3's norms
+  double* vp_prev = nullptr;       // previous iterate f^(k) (n_coeffs), allocated on first use
+  double* vp_tmp = nullptr;
+  // host level hierarchies (patterns, transfers, coordinates), kept for the
+  // fused sweep's tile planner
+  std::shared_ptr<Hierarchy> hx_host, hv_host;
+  // fused branch-A launch plans per (grid, bytes of an S pair), built on first use
+  struct FusedGrid {
+    bool tried = false, ok = false;
+    int G = 0, ntiles = 0, W = 0;
+    size_t smem = 0;
+    double s_points = 0.0;        // S_b entries formed per chain (interior and halo)
+    double q_points = 0.0;        // restricted outputs per chain
+    std::string why;              // reason when no plan fits
+    FusedTile* tiles = nullptr;
+    int* xrows = nullptr;
+    int* vcols = nullptr;
+    unsigned short* xnbr = nullptr;
+    int* qcols = nullptr;
+    unsigned short* qloc = nullptr;
+  };
+  std::map<long long, FusedGrid> fused;
+  int sweep_variant = 0;          // 0: fused branch A where a plan fits; 1: unfused kernels only
   // identity of the discrete problem (meshes, levels, dt, delta, term table,
   // finest-level factor values at creation), checked by sgdg_restore
   unsigned long long problem_hash = 0;
@@ -152,7 +176,7 @@ struct Handle {
 // kinds of SpMM launches for the per-kernel statistics
 enum {
   KIND_S_CHAIN = 0, KIND_FINAL_LEFT = 1, KIND_XFER_LEFT = 2, KIND_XFER_RIGHT = 3,
-  KIND_CHAIN_A = 4, KIND_CHAIN_B = 5, KIND_RESERVED = 6, KIND_FINAL_RIGHT = 7, KIND_COUNT = 8
+  KIND_FUSED_A = 4, KIND_CHAIN_B = 5, KIND_RESERVED = 6, KIND_FINAL_RIGHT = 7, KIND_COUNT = 8
 };
 
 // allocation helper that records bytes and reports ENOMEM
@@ -198,6 +222,9 @@ Status autotune(Handle& h, const Store<T>* u, Store<T>* y, cudaStream_t s);
 
 // Vlasov-Poisson coupling (field.cu)
 Status field_setup(Handle& h, const sgdg_coeffs& c, const Hierarchy& hx, const Hierarchy& hv, const SideFns& fx);
+// Fused branch-A plan of grid i for S pairs of pair_bytes bytes and nchains
+// chains (sweep_fused_plan.cu); *out is null when no tile shape fits.
+Status fused_plan(Handle& h, int i, int pair_bytes, int nchains, int nterms, const Handle::FusedGrid** out);
 Status field_update(Handle& h, int source, double* energy);
 Status field_reassemble(Handle& h);
 
@@ -206,6 +233,11 @@ Status coarse_values(Handle& h, const double* u, int R, int lx, int lv, double* 
 Status add_coarse(Handle& h, const double* c, int lx, int lv, double* u, cudaStream_t s);
 
 Status solver_init(Handle& h);
+// ||u||_{H^1(I_j x Omega)} of a strip vector (FP64, device): u . (G u) with
+// the Gram plan h.h1 (deterministic reduction); tmp: n_coeffs doubles.
+Status h1_norm(Handle& h, const double* u, double* tmp, double* out, cudaStream_t s);
+// dst = (U, 0): a spatial vector as the strip function constant in time
+Status constant_in_time(Handle& h, const double* U, double* dst, cudaStream_t s);
 Status ct_precondition(Handle& h, const double* r, double* z, cudaStream_t s, int* inner_its);
 Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resolve = false);
 void solver_free(Handle& h);

@@ -997,6 +997,24 @@ Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resol
   return res;
 }
 
+Status h1_norm(Handle& h, const double* u, double* tmp, double* out, cudaStream_t s) {
+  SG_ST(solver_init(h));
+  SG_ST(apply_plan<double>(h, h.h1, u, tmp, s));
+  Workspace& ws = *h.ws;
+  SG_ST(mdot<double>(h, 1, u, h.n_coeffs, tmp, h.n_coeffs, ws.dev_dots, s));
+  SG_CU(cudaMemcpyAsync(ws.host, ws.dev_dots, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SG_CU(cudaStreamSynchronize(s));
+  *out = norm_of(ws.host[0]);
+  if (!std::isfinite(*out)) return {SGDG_ENAN, "NaN/Inf in an H1 norm"};
+  return {};
+}
+
+Status constant_in_time(Handle& h, const double* U, double* dst, cudaStream_t s) {
+  k_expand<<<gridsz(h.n_spatial), kThreads, 0, s>>>(h.n_spatial, U, dst, 1.0, 0.0);
+  SG_CU(cudaGetLastError());
+  return {};
+}
+
 Handle::~Handle() {}
 
 void solver_free(Handle& h) {

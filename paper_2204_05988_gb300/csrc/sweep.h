@@ -113,6 +113,56 @@ struct FinalArgs {
   Store<T>* y = nullptr;
 };
 
+// Fused branch-A step on one grid (sweep_fused.cu).  The grid's (k1, k2)
+// index set is cut into tiles: an x patch of rows (interior rows first, then
+// the rows the dim-1 stencils of the interior reach) times a v patch of
+// columns (interior columns first, then the fine columns the restriction rows
+// of the coarse columns it owns reach).  Per tile and per group of G chains
+// the kernel forms S_b = U V_b^T + P1 Z_b on the whole tile in shared memory,
+// folds y += sum_a tau_a X_a S_b into registers on the interior, and writes
+// the restricted states Z'_b = S_b R2^T of the owned coarse columns; S_b never
+// leaves the SM.
+constexpr int kFusedChains = 32;
+constexpr int kFusedTerms = 64;
+constexpr int kFusedThreads = 512;
+constexpr int kFusedOut = 4;   // interior outputs per thread (<= kFusedThreads * kFusedOut per tile)
+
+struct FusedTile {
+  int xs0, nxi, nxt, xn0;   // rows: xrows[xs0 ..), interior / total; neighbour table xnbr[xn0 ..)
+  int vs0, nvi, nvt;        // columns: vcols[vs0 ..)
+  int q0, nq;               // owned coarse columns qcols[q0 ..), their positions qloc[q0 * W ..)
+};
+
+template <typename T>
+struct FusedArgs {
+  const FusedTile* tiles = nullptr;
+  const int* xrows = nullptr;
+  const int* vcols = nullptr;
+  const unsigned short* xnbr = nullptr;   // [interior row][W]: local row of each X pattern entry
+  const int* qcols = nullptr;
+  const unsigned short* qloc = nullptr;   // [owned coarse column][W]: local column of each R2 entry
+  int ntiles = 0, W = 8;
+  int n2 = 0, n2c = 0;                    // row lengths of the grid and of the restricted states
+  int has_prev = 0, restrict_out = 0;
+  int nchains = 0, G = 1;
+  const Store<T>* U = nullptr;
+  Store<T>* Y = nullptr;
+  const int* vcol = nullptr;              // V pattern, ELL (level lv)
+  const Comp<T>* vval[kFusedChains] = {};
+  const Store<T>* zin[kFusedChains] = {};   // Z_{b,i}: [nx(lx - 1)][n2]
+  Store<T>* zout[kFusedChains] = {};        // Z_{b,i+1}: [n1][n2c]
+  const int* pcol = nullptr;              // prolongation E_{lx <- lx-1}, ELL width 2
+  const Comp<T>* pval = nullptr;
+  const int* rcol = nullptr;              // restriction R_{lv-1 <- lv}, ELL width W
+  const Comp<T>* rval = nullptr;
+  int tbeg[kFusedChains + 1] = {};
+  const Comp<T>* xval[kFusedTerms] = {};  // X_a, ELL width W (level lx)
+  Comp<T> tau[kFusedTerms][4] = {};
+};
+
+template <typename T>
+cudaError_t launch_fused_a(const FusedArgs<T>& a, size_t smem, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_restrict(RestrictArgs<T>& a, bool dim2, cudaStream_t s);
 template <typename T>

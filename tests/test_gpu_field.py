@@ -114,3 +114,56 @@ def test_field_fixed_point_iterated_to_consistency():
         a.advance_strip_vp(tol=-1.0)
     for x in (s, a, b):
         x.close()
+
+
+def test_vp_fixed_point_matches_oracle():
+    """The per-strip fixed point with the stop test of Sect. 5.3
+    (sgdg_set_vp_stop 1: ||E^(k+1) - E^(k)||_inf + ||f^(k+1) - f^(k)||_H1)
+    against the oracle's ``vp_strip`` on two strips of the L = 2 Landau
+    problem: the same number of strip solves per strip and the same end
+    values (nodal values within 1e-8; both sides solve every strip to 1e-12)."""
+    import paper_2204_05988_gb300 as P
+    from oracle.field import density, density_u0, vp_strip
+    from oracle.solver import StripSolver, nodal_values
+    eps = 1e-6
+    prob_o = W.landau_4d(L=2, n_strips=2, dt=0.25)
+    so = StripSolver(prob_o, tol=1e-12)
+    op = so.op
+    MU = so.initial_mass_u0()
+    U = np.linalg.lstsq(op.dense(op.mass_terms())[::2, ::2], MU, rcond=None)[0]
+    rho = density_u0(op, prob_o)
+    ends, its = [], []
+    for j in range(2):
+        u, E, k, crit = vp_strip(so, prob_o, U, rho, MU, j * prob_o.dt, eps)
+        U = so.endpoint(u)
+        ends.append(U)
+        its.append(k)
+        rho = density(op, U)
+        MU = so.mass_spatial(U)
+    s = P.Solver(W.landau_4d(L=2, n_strips=2, dt=0.25), vlasov_poisson=True, rtol=1e-12, inner_its=40,
+                 inner_rtol=1e-6)
+    s.set_vp_stop(1)
+    s.set_initial()
+    for j in range(2):
+        st, steps, crit = s.advance_strip_vp(tol=eps, max_fp=20)
+        assert steps + 1 == its[j] and crit <= eps, (j, steps, its[j], crit)
+        Ug = np.empty(s.n_spatial)
+        s.get_end_value(Ug, on_device=False)
+        assert _rel(nodal_values(op, Ug), nodal_values(op, ends[j])) < 1e-8, j
+    s.close()
+
+
+def test_h1_norm_matches_oracle():
+    """sgdg_h1_norm (the Gram form of Algorithm 1's stop norm, FP64 on the
+    device) against the oracle's Gram form on a random strip vector."""
+    import paper_2204_05988_gb300 as P
+    from oracle.norms import h1_norm
+    from oracle.operator import SparseGridOperator
+    for prob in (W.transport_2d(L=3, sigma=0.1), W.landau_4d(L=3)):
+        op = SparseGridOperator(prob)
+        s = P.Solver(prob)
+        u = W.uniform_vector(op.size, seed=8)
+        got = s.h1_norm(torch.tensor(u, device="cuda"))
+        ref = h1_norm(op, u)
+        assert abs(got - ref) < 1e-12 * ref, (got, ref)
+        s.close()

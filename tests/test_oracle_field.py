@@ -53,3 +53,44 @@ def test_density_of_u0():
     rho = density_u0(op, prob)
     g = 1.0   # int exp(-|v|^2/2)/(2 pi) over [-6,6]^2 = erf(6/sqrt 2)^2 = 1 - 4e-9
     assert np.allclose(rho, (1.0 + ALPHA * np.cos(K * x[:, 0])) * g, rtol=2e-3, atol=0)
+
+
+def _vp_first_strip(alpha, L=2, eps=1e-8):
+    from oracle.field import density_u0, vp_strip
+    from oracle.solver import StripSolver
+    prob = W.landau_4d(L=L, alpha=alpha, k=K, n_strips=1, dt=0.25)
+    s = StripSolver(prob, tol=1e-12)
+    op = s.op
+    MU = s.initial_mass_u0()
+    # U^-_0: the spanning-set vector of the projection of u0 is not needed as
+    # such; f^(0) only enters through its H1 distance, taken from the
+    # oracle's own solve of the first strip's mass problem M_sg U = (u0, phi)
+    U0 = np.linalg.lstsq(op.dense(op.mass_terms())[::2, ::2], MU, rcond=None)[0]
+    return prob, s, vp_strip(s, prob, U0, density_u0(op, prob), MU, 0.0, eps)
+
+
+def test_vp_fixed_point_uniform_density_is_immediate():
+    """alpha = 0: the density is uniform, the field vanishes, the strip
+    solution of an x-independent state is constant in time - the fixed point
+    of Sect. 5.3 stops after its first solve with a zero field."""
+    prob, s, (u, E, its, crit) = _vp_first_strip(0.0)
+    assert its == 1 and np.abs(E).max() < 1e-12 and crit < 1e-8
+
+
+def test_vp_fixed_point_converges_and_is_consistent():
+    """alpha = 0.01: a few alternations reach the tolerance; the returned
+    solution solves the strip with the field it returns, and that field is
+    the midpoint field of the solution to within the tolerance."""
+    from oracle.field import density, install_field, poisson
+    from oracle.norms import h1_norm
+    prob, s, (u, E, its, crit) = _vp_first_strip(0.01)
+    assert 2 <= its <= 10 and crit < 1e-8
+    op = s.op
+    rho = density(op, u.reshape(-1, op.R)[:, 0])
+    _, E_mid, _ = poisson(op, rho)
+    assert np.abs(E_mid - E).max() < 1e-8
+    install_field(op, prob, E)
+    b = s.rhs(s.initial_mass_u0(), 0.0)
+    r = op.apply(u) - b
+    assert np.linalg.norm(r) < 1e-10 * np.linalg.norm(b)
+    assert h1_norm(op, u) > 0

@@ -12,7 +12,9 @@
   parameter off by a factor 2, moves the error by about 40% and fails the band.
 * The H^1(J x Omega) norm of Algorithm 1's stop test: closed forms for a
   function constant in space (constant and linear in time) and for a
-  function linear in x.
+  function linear in x; the Gram-form evaluation against the independent
+  evaluation from finest-full-grid values and cell quadrature on random
+  spanning-set vectors.
 """
 import os
 
@@ -20,7 +22,7 @@ import numpy as np
 import pytest
 
 import sgdg_workloads as W
-from oracle.norms import h1_norm, sd_norm_error
+from oracle.norms import h1_norm, h1_norm_nodal, sd_norm_error
 from oracle.operator import SparseGridOperator
 from oracle.solver import StripSolver
 
@@ -95,3 +97,14 @@ def test_h1_norm_closed_forms(make):
     blk[:, :, 0] = x1[:, None]
     mean_x1sq = (hi_x[0] ** 3 - lo_x[0] ** 3) / (3 * (hi_x[0] - lo_x[0]))
     assert h1_norm(op, u) ** 2 == pytest.approx(dt * vol * (mean_x1sq + 1.0), rel=1e-12)
+
+
+@pytest.mark.parametrize("make", [lambda: W.free_streaming_1d(L=3, n_strips=1),
+                                  lambda: W.transport_2d(L=2, sigma=0.1)], ids=["d1", "d2"])
+def test_h1_gram_equals_nodal_quadrature(make):
+    prob = make()
+    op = SparseGridOperator(prob)
+    for seed in (1, 2):
+        u = W.uniform_vector(op.size, seed=seed)
+        a, b = h1_norm(op, u), h1_norm_nodal(op, u)
+        assert abs(a - b) < 1e-10 * b, (a, b)
