@@ -366,13 +366,23 @@ sgdg_status sgdg_mlp_set_params(void* mlp, const float* params);
  * later applies of this handle. */
 sgdg_status sgdg_autotune(void* h, const void* u, void* y, int precision, void* stream);
 /* Which kernels run the sweep's branch A (no counterpart in the paper; both
- * compute the same operator, up to rounding order):
- * 0 (default): one fused launch per grid where a tile plan fits - the states
+ * compute the same operator with the same FP32/FP64 sums, bit for bit; in BF16
+ * storage the fused kernel keeps S_b in FP32):
+ * 0: one fused launch per grid where a tile plan fits - the states
  *   S_b = U V_b^T + P1 Z_b are formed per tile in shared memory, folded into
- *   y and restricted there, and never written to device memory;
- * 1: the unfused kernels (S_b written per grid, then final update and
- *   restriction).  Other values: SGDG_EINVAL. */
+ *   y and restricted there, and never written to device memory (about a
+ *   tenth of the unfused DRAM traffic, but slower on GB300: the kernels are
+ *   bound by L1/shared-memory throughput and latency, and the tiles cost
+ *   occupancy, barriers and halo recomputation);
+ * 1 (default): the unfused kernels (S_b written per grid, then final update
+ *   and restriction).  Other values: SGDG_EINVAL. */
 sgdg_status sgdg_set_sweep_variant(void* h, int variant);
+/* The fused branch-A plan of grid l for S pairs of pair_bytes bytes in shared
+ * memory (FP32 and BF16 storage: 8; FP64: 16), built if needed (measurement; no counterpart in the paper): iout[0..3] = tiles,
+ * chains per group, ELL width, shared-memory bytes per block; dout[0..1] =
+ * S_b entries formed per chain (interior and halo), restricted outputs per
+ * chain.  All zero when no tile shape fits (the unfused kernels run). */
+sgdg_status sgdg_fused_plan_info(void* h, int l, int pair_bytes, int* iout, double* dout);
 /* Copies the autotuner's per-site choices of `src` into `dst` (sites are keyed
  * by kernel kind, grid shape, chain count and element size, so handles of the
  * same problem size share them; sites `dst` never meets are ignored) and

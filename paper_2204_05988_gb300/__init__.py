@@ -130,6 +130,7 @@ EXPORTS = {
     "sgdg_checkpoint": (C.c_int, [C.c_void_p, C.c_char_p]),
     "sgdg_copy_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sgdg_set_sweep_variant": (C.c_int, [C.c_void_p, C.c_int]),
+    "sgdg_fused_plan_info": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "sgdg_set_vp_stop": (C.c_int, [C.c_void_p, C.c_int]),
     "sgdg_h1_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "sgdg_restore": (C.c_int, [C.c_void_p, C.c_char_p]),
@@ -436,8 +437,15 @@ class Solver:
         self._check(self.lib.sgdg_autotune(self.h, _ptr(u), _ptr(y), precision, _stream(stream)))
 
     def set_sweep_variant(self, variant: int):
-        """0: fused branch A where a tile plan fits (default); 1: unfused kernels."""
+        """0: fused branch A where a tile plan fits; 1: unfused kernels (default)."""
         self._check(self.lib.sgdg_set_sweep_variant(self.h, variant))
+
+    def fused_plan_info(self, grid: int, pair_bytes: int = 8):
+        """(tiles, chains per group, ELL width, shared bytes, S entries per chain, restricted outputs per chain)."""
+        io = (C.c_int * 4)()
+        do = (C.c_double * 2)()
+        self._check(self.lib.sgdg_fused_plan_info(self.h, grid, pair_bytes, io, do))
+        return tuple(io) + tuple(do)
 
     def copy_tuning(self, other: "Solver"):
         """Take over another handle's autotuned launch shapes (same problem sizes)."""

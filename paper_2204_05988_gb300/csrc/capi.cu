@@ -852,6 +852,28 @@ sgdg_status sgdg_autotune(void* hp, const void* u, void* y, int prec, void* stre
   return st.code ? fail(h, st) : SGDG_OK;
 }
 
+sgdg_status sgdg_fused_plan_info(void* hp, int grid, int pair_bytes, int* iout, double* dout) {
+  if (!hp || !iout || !dout) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  if (grid < 0 || grid > h->L || (pair_bytes != 4 && pair_bytes != 8 && pair_bytes != 16))
+    return fail(h, {SGDG_EINVAL, "fused plan info: grid or pair size out of range"});
+  int nterms = 0;
+  for (const Chain& c : h->op.A) nterms += (int)c.terms.size();
+  const Handle::FusedGrid* fg = nullptr;
+  Status st = fused_plan(*h, grid, pair_bytes, (int)h->op.A.size(), nterms, &fg);
+  if (st.code) return fail(h, st);
+  for (int k = 0; k < 4; ++k) iout[k] = 0;
+  dout[0] = dout[1] = 0.0;
+  if (!fg) return SGDG_OK;
+  iout[0] = fg->ntiles;
+  iout[1] = fg->G;
+  iout[2] = fg->W;
+  iout[3] = (int)fg->smem;
+  dout[0] = fg->s_points;
+  dout[1] = fg->q_points;
+  return SGDG_OK;
+}
+
 sgdg_status sgdg_set_sweep_variant(void* hp, int variant) {
   if (!hp) return SGDG_EINVAL;
   Handle* h = (Handle*)hp;

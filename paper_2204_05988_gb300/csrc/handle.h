@@ -165,7 +165,7 @@ struct Handle {
     unsigned short* qloc = nullptr;
   };
   std::map<long long, FusedGrid> fused;
-  int sweep_variant = 0;          // 0: fused branch A where a plan fits; 1: unfused kernels only
+  int sweep_variant = 1;          // 0: fused branch A where a plan fits; 1 (default): unfused kernels
   // identity of the discrete problem (meshes, levels, dt, delta, term table,
   // finest-level factor values at creation), checked by sgdg_restore
   unsigned long long problem_hash = 0;

@@ -1,10 +1,10 @@
 """The fused branch-A sweep (GPU): per tile, S_b in shared memory, folded into
-y and restricted there (sgdg_set_sweep_variant 0, the default) against the
-unfused kernels (variant 1) and the oracle.
+y and restricted there (sgdg_set_sweep_variant 0) against the unfused
+kernels (variant 1, the default) and the oracle.
 
-Both variants compute the same operator; only the order of the floating-point
-sums differs.  Tolerances: FP64 1e-12 relative against the oracle and 1e-13
-between the variants (max-abs per grid over the grid's largest value); FP32
+Both variants compute the same operator with the same sums in FP32 and FP64.
+Tolerances: FP64 1e-12 relative against the oracle and 1e-13 between the
+variants (max-abs per grid over the grid's largest value); FP32
 1e-5 against the oracle; BF16 storage as in test_gpu_bf16 (the fused kernel
 keeps S_b in FP32 in shared memory, one rounding fewer per step).  Cases span
 1-D, 2-D and periodic meshes, and a d = 2, L = 6 problem whose grids are cut
