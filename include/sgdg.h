@@ -4,8 +4,8 @@
  *
  * Problem (Sect. 1, Eqs. 1-2): d_t u + beta . grad u + sigma u = f on
  * (0,T) x Omega, Omega = Omega_x x Omega_v (both d-dimensional, d = 1, 2),
- * u(0) = u0, inflow u = g on Gamma^- = {beta . n < 0}.  This library solves
- * f = 0, g = 0.
+ * u(0) = u0, inflow u = g on Gamma^- = {beta . n < 0}, with f and g sums of
+ * separable terms.
  *
  * Discretisation (Sect. 2): sparse grid V_L = sum_{l=0..L} V^(1)_l (x) V^(2)_{L-l}
  * of nested P1 spaces (levels 0-based: the paper's level is L+1), time-DG of
@@ -122,13 +122,15 @@ typedef struct {
 } sgdg_source;
 
 /* beta_p = beta[p] for p < 2d (x-components first), sigma,
- * u0 = sum_k u0[k] and the source f = sum_k f[k] (n_f may be 0).  Every
- * component of beta is ONE product (the tensor structure of Sect. 4.2);
- * inflow splitting (Sect. 5.2) assumes the sign of each factor changes only
- * on mesh lines.  The strip right-hand side b_j of Sect. 2 pairs f with
- * w + delta (d_t w + beta . grad w); its time integrals use 3-point
- * Gauss-Legendre on every strip.  The inflow data g is zero.  Sources are
- * not combined with vlasov_poisson (EINVAL). */
+ * u0 = sum_k u0[k], the source f = sum_k f[k] (n_f may be 0) and the inflow
+ * data g = sum_k g[k] on Gamma^- (n_g may be 0: g = 0).  Every component of
+ * beta is ONE product (the tensor structure of Sect. 4.2); inflow splitting
+ * (Sect. 5.2) assumes the sign of each factor changes only on mesh lines.
+ * The strip right-hand side b_j of Sect. 2 pairs f with
+ * w + delta (d_t w + beta . grad w) and takes -int_{I_j} <g, w>_{Gamma^-} dt,
+ * <u, w>_Gamma = int_Gamma (beta . n) u w, split like the inflow term of the
+ * operator; its time integrals use 3-point Gauss-Legendre on every strip.
+ * Sources and inflow data are not combined with vlasov_poisson (EINVAL). */
 typedef struct {
   sgdg_product beta[4];
   sgdg_product sigma;
@@ -136,6 +138,8 @@ typedef struct {
   const sgdg_product* u0;
   int n_f;
   const sgdg_source* f;
+  int n_g;
+  const sgdg_source* g;
 } sgdg_coeffs;
 
 typedef struct {

@@ -19,9 +19,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 * ``StripSolver``: the implicit strip-by-strip scheme (Sect. 2): the right-hand
   side (U^-_{j-1}, w^+_{j-1}) = eta(t_{j-1}^+) (x) M_sg U^-_{j-1} (Eq. 5), with
   (u0, w^+) from load vectors for the first strip, plus the source part
-  int_{I_j} (f, w + delta (d_t w + beta . grad w)) dt (``source_rhs``; time
-  integrals by adaptive quadrature, the inflow data g = 0); the end value
-  U^-_j = sum_s eta_s(t_j) u_s.
+  int_{I_j} (f, w + delta (d_t w + beta . grad w)) dt (``source_rhs``) and the
+  inflow part -int_{I_j} <g, w>_{Gamma^-} dt (``inflow_rhs``), time integrals
+  by adaptive quadrature; the end value U^-_j = sum_s eta_s(t_j) u_s.
 * ``nodal_values``: the unique representation of a sparse-grid function: its
   values at the nodes of every component grid (prolongation from coarser
   levels, injection from finer ones).
@@ -249,8 +249,62 @@ class StripSolver:
             off += blk.size
         return out
 
+    def inflow_rhs(self, t0: float) -> np.ndarray:
+        """-int_I <g, w>_{Gamma^-} dt for w = eta_s phi psi on the strip
+        I = (t0, t0 + dt) (Sect. 2, b_j), g = sum_k c_k gt_k gx_k gv_k and
+        <u, w>_{Gamma^-} = int_{Gamma^-} (beta . n) u w: per beta component
+        p = b_p(x) c_p(v) the inflow part of the faces x_p = side (p < d) or
+        v_{p-d} = side is split by the signs of the two factors exactly like
+        the inflow term of the operator (Sect. 5.2); its x and v factors
+        carry the extra weights gx and gv.  Load vectors follow from the
+        factor matrices and the partition of unity: int w phi_i = sum_j
+        int w phi_i phi_j."""
+        op, prob = self.op, self.prob
+        R, d, dt = op.R, prob.d, prob.dt
+        out = np.zeros(op.size)
+        if not prob.g:
+            return out
+        w = lambda f: (f,) if f is not None else ()
+        fn = lambda f: f if f is not None else (lambda p: np.ones(p.shape[0]))
+        ev = lambda s, t: eta(s, np.array([(t - t0) / dt]), dt)[0][0]
+        terms = []   # (time weights [R], x factor, v factor)
+        for src in prob.g:
+            gt = (lambda t: 1.0) if src.ft is None else (lambda t, g=src.ft: float(np.asarray(g(np.array([t])))[0]))
+            wt = -src.coef * np.array([integrate.quad(lambda t, s=s: gt(t) * ev(s, t), t0, t0 + dt,
+                                                      epsabs=1e-15, epsrel=1e-13)[0] for s in range(R)])
+            for p, b in enumerate(prob.beta):
+                if b.coef == 0.0:
+                    continue
+                for side in (-1, +1):
+                    for s1 in (+1, -1):
+                        s2 = -side * s1
+                        rx = ((fn(b.fx), b.coef, s1),)
+                        rv = ((fn(b.fv), 1.0, s2),)
+                        if p < d:
+                            if prob.mesh_x.periodic[p]:
+                                continue
+                            X = Factor("face", side * b.coef, w(b.fx) + w(src.fx), restrict=rx, face=(p, side))
+                            V = Factor("vol", 1.0, w(b.fv) + w(src.fv), restrict=rv)
+                        else:
+                            if prob.mesh_v.periodic[p - d]:
+                                continue
+                            X = Factor("vol", side * b.coef, w(b.fx) + w(src.fx), restrict=rx)
+                            V = Factor("face", 1.0, w(b.fv) + w(src.fv), restrict=rv, face=(p - d, side))
+                        terms.append((wt, X, V))
+        loads = [(wt, op.fx.fine(X) @ np.ones(op.fx.fine(X).shape[1]), op.fv.fine(V) @ np.ones(op.fv.fine(V).shape[1]))
+                 for wt, X, V in terms]
+        off = 0
+        for (l1, l2) in op.grids:
+            n1, n2 = op.grid_shape(l1, l2)
+            blk = np.zeros((n1, n2, R))
+            for wt, Fx, Fv in loads:
+                blk += np.einsum("i,j,s->ijs", op.fx.embed(l1).T @ Fx, op.fv.embed(l2).T @ Fv, wt)
+            out[off:off + blk.size] = blk.ravel()
+            off += blk.size
+        return out
+
     def rhs(self, MU: np.ndarray, t0: float = 0.0) -> np.ndarray:
-        return np.outer(MU, self.e_start).ravel() + self.source_rhs(t0)
+        return np.outer(MU, self.e_start).ravel() + self.source_rhs(t0) + self.inflow_rhs(t0)
 
     def endpoint(self, u: np.ndarray) -> np.ndarray:
         return u.reshape(-1, self.op.R) @ self.e_end

@@ -49,7 +49,7 @@ class Source(C.Structure):
 
 class Coeffs(C.Structure):
     _fields_ = [("beta", Product * 4), ("sigma", Product), ("n_u0", C.c_int), ("u0", C.POINTER(Product)),
-                ("n_f", C.c_int), ("f", C.POINTER(Source))]
+                ("n_f", C.c_int), ("f", C.POINTER(Source)), ("n_g", C.c_int), ("g", C.POINTER(Source))]
 
 
 class Config(C.Structure):
@@ -240,7 +240,14 @@ class Solver:
                            None)
         co.n_f = len(srcs)
         co.f = fa
-        self._keep += [cfg, co, u0, fa]
+        gs = getattr(problem, "g", None) or []
+        ga = (Source * max(1, len(gs)))()
+        for k, sr in enumerate(gs):
+            ga[k] = Source(float(sr.coef), self._fn(sr.fx, d), None, self._fn(sr.fv, d), None, self._tfn(sr.ft),
+                           None)
+        co.n_g = len(gs)
+        co.g = ga
+        self._keep += [cfg, co, u0, fa, ga]
         h = C.c_void_p()
         st = self.lib.sgdg_create(C.byref(cfg), C.byref(co), C.byref(h))
         if self._cb_error:

@@ -1,5 +1,6 @@
 // C ABI of the sgdg library: set-up (hierarchies, FP64 assembly, term table,
 // device upload) and the entry points declared in include/sgdg.h.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -509,6 +510,51 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
         SG_ST(upload_levels(lx, tb.lx));
         SG_ST(upload_levels(lv, tb.lv));
         h.src_terms.push_back(tb);
+      }
+    }
+  }
+  // inflow data g: -int_I <g, w>_{Gamma^-} (Sect. 2, b_j), per g term and
+  // inflow part the load vectors of the part's x and v factors with the
+  // extra weights gx, gv (row sums of the factor matrices: the P1 functions
+  // sum to one), scaled by -int_I gt eta_s at every strip
+  if (c.n_g > 0) {
+    if (cfg.vlasov_poisson) return {SGDG_EINVAL, "inflow data are not combined with vlasov_poisson"};
+    if (!c.g) return {SGDG_EINVAL, "n_g > 0 with a NULL inflow array"};
+    const std::vector<InflowPart> parts = inflow_parts(c, h.d, cfg.mesh_x, cfg.mesh_v);
+    auto row_sums = [](const std::vector<Csr>& X, std::vector<std::vector<double>>& out) {
+      out.assign(X.size(), {});
+      for (size_t l = 0; l < X.size(); ++l) {
+        out[l].assign(X[l].nrows, 0.0);
+        for (int i = 0; i < X[l].nrows; ++i)
+          for (int p = X[l].rowptr[i]; p < X[l].rowptr[i + 1]; ++p) out[l][i] += X[l].val[p];
+      }
+    };
+    for (int k = 0; k < c.n_g; ++k) {
+      const sgdg_source& g = c.g[k];
+      const int src = (int)h.src_t.size();
+      h.src_t.push_back({g.ft, g.ut});
+      SideFns gx = fx, gv = fv;   // id 5: the g factors
+      gx.fn.push_back(g.fx); gx.user.push_back(g.ux);
+      gv.fn.push_back(g.fv); gv.user.push_back(g.uv);
+      for (const InflowPart& ip : parts) {
+        FactorSpec X = ip.x, V = ip.v;
+        if (g.fx) { X.wfn.push_back(5); std::sort(X.wfn.begin(), X.wfn.end()); }
+        if (g.fv) { V.wfn.push_back(5); std::sort(V.wfn.begin(), V.wfn.end()); }
+        std::vector<Csr> AX, AV;
+        SG_ST(assemble_factor(hx, gx, X, AX));
+        SG_ST(assemble_factor(hv, gv, V, AV));
+        std::vector<std::vector<double>> lx, lv;
+        row_sums(AX, lx);
+        row_sums(AV, lv);
+        Handle::SourceTerm t;
+        t.src = src;
+        t.kind = 2;
+        t.coef = g.coef * ip.scale;
+        t.lx.assign(lx.size(), nullptr);
+        t.lv.assign(lv.size(), nullptr);
+        for (size_t l = 0; l < lx.size(); ++l) SG_ST(upload(h, &t.lx[l], lx[l].data(), lx[l].size()));
+        for (size_t l = 0; l < lv.size(); ++l) SG_ST(upload(h, &t.lv[l], lv[l].data(), lv[l].size()));
+        h.src_terms.push_back(t);
       }
     }
   }

@@ -99,7 +99,8 @@ struct Handle {
   std::vector<double> u0coef;
   // source terms of the strip right-hand side (Sect. 2, b_j): per term the x
   // and v load vectors per level (device) and which time weight scales them:
-  // kind 0 - int ft eta_s + delta int ft eta_s',  kind 1 - delta int ft eta_s
+  // kind 0 - int ft eta_s + delta int ft eta_s',  kind 1 - delta int ft eta_s,
+  // kind 2 - minus int gt eta_s (inflow data on Gamma^-)
   struct SourceTerm { int src = 0, kind = 0; double coef = 0.0; std::vector<double*> lx, lv; };
   std::vector<SourceTerm> src_terms;
   std::vector<std::pair<sgdg_tfn, void*>> src_t;   // time factor per source

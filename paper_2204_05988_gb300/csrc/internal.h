@@ -115,6 +115,16 @@ struct TermTable {
 Status build_terms(const sgdg_coeffs& c, int d, const sgdg_mesh& mx, const sgdg_mesh& mv,
                    double dt, double delta, TermTable& out);
 
+// The inflow boundary Gamma^- of Sect. 2 split into Kronecker pairs (Sect.
+// 5.2): <u, w>_{Gamma^-} = sum over parts of scale (x factor) (x) (v factor),
+// one part per beta component, box side and sign pair of its two factors
+// (function ids 0..2d-1 are the beta components).
+struct InflowPart {
+  FactorSpec x, v;
+  double scale = 0.0;
+};
+std::vector<InflowPart> inflow_parts(const sgdg_coeffs& c, int d, const sgdg_mesh& mx, const sgdg_mesh& mv);
+
 // C = A B: the structural pattern (sorted rows, no values) and the values of
 // A B on that pattern (aval, bval: values of A and B on their patterns).
 Csr product_pattern(const Csr& A, const Csr& B);

@@ -837,8 +837,8 @@ Status ct_precondition(Handle& h, const double* r, double* z, cudaStream_t s, in
   return ct_apply<double>(h, r, z, s, its);
 }
 
-// rhs += the source part of b_j (Sect. 2) on the strip [t_now, t_now + dt]:
-// per source k the time weights
+// rhs += the source and inflow parts of b_j (Sect. 2) on the strip
+// [t_now, t_now + dt]: per source (or inflow datum) k the time weights
 //   e1_s = int_I ft_k eta_s dt,   e0_s = e1_s + delta int_I ft_k eta_s' dt
 // by 3-point Gauss-Legendre (exact for ft of degree <= 4), then every
 // Kronecker term of the source on every grid.
@@ -868,7 +868,8 @@ static Status add_source(Handle& h, cudaStream_t s) {
   }
   for (const Handle::SourceTerm& t : h.src_terms) {
     const double* e = t.kind == 0 ? &e0[2 * t.src] : &e1[2 * t.src];
-    const double sc = t.kind == 0 ? t.coef : t.coef * dl;
+    // kind 0: (f, w + delta d_t w); kind 1: delta (f, beta_c d_c w); kind 2: -<g, w>_{Gamma^-}
+    const double sc = t.kind == 0 ? t.coef : (t.kind == 1 ? t.coef * dl : -t.coef);
     for (int l = 0; l <= h.L; ++l)
       SG_CU(outer_add(h.rhs + h.off[l], h.n1[l], h.n2[l], t.lx[l], t.lv[h.L - l], sc * e[0], sc * e[1], s));
   }

@@ -28,6 +28,41 @@
 
 namespace sgdg {
 
+std::vector<InflowPart> inflow_parts(const sgdg_coeffs& c, int d, const sgdg_mesh& mx, const sgdg_mesh& mv) {
+  // beta_p = cp b_p(x) c_p(v); on the face y_ax = side of Omega_x (p < d) or
+  // Omega_v (p >= d), beta . n = side cp b_p c_p < 0 where the signs s1 of
+  // cp b_p and s2 of c_p satisfy side s1 s2 < 0; each sign pair is one
+  // Kronecker pair with the sign restricted at cell or face centroids
+  std::vector<InflowPart> out;
+  for (int p = 0; p < 2 * d; ++p) {
+    if (c.beta[p].coef == 0.0) continue;
+    const bool xface = p < d;
+    const int ax = xface ? p : p - d;
+    const sgdg_mesh& m = xface ? mx : mv;
+    if (m.periodic && m.periodic[ax]) continue;
+    const double cp = c.beta[p].coef;
+    const int sc = cp > 0 ? 1 : -1;
+    const bool hx = c.beta[p].fx != nullptr, hv = c.beta[p].fv != nullptr;
+    for (int side = -1; side <= 1; side += 2)
+      for (int s1 = 1; s1 >= -1; s1 -= 2) {
+        const int s2 = -side * s1;
+        InflowPart ip;
+        ip.x.kind = xface ? 1 : 0;
+        ip.v.kind = xface ? 0 : 1;
+        if (hx) { ip.x.wfn = {p}; ip.x.restrict_ = {{p, s1 * sc}}; }
+        else if (s1 != sc) continue;
+        if (hv) { ip.v.wfn = {p}; ip.v.restrict_ = {{p, s2}}; }
+        else if (s2 != 1) continue;
+        FactorSpec& F = xface ? ip.x : ip.v;
+        F.face_axis = ax;
+        F.face_side = side;
+        ip.scale = side * cp;
+        out.push_back(ip);
+      }
+  }
+  return out;
+}
+
 Status build_terms(const sgdg_coeffs& c, int d, const sgdg_mesh& mx, const sgdg_mesh& mv,
                    double dt, double delta, TermTable& out) {
   const double Mt[2][2] = {{dt, 0.0}, {0.0, dt / 3.0}};
@@ -103,29 +138,7 @@ Status build_terms(const sgdg_coeffs& c, int d, const sgdg_mesh& mx, const sgdg_
   double mMt[2][2];
   for (int s = 0; s < 2; ++s)
     for (int q = 0; q < 2; ++q) mMt[s][q] = -Mt[s][q];
-  for (int p : act) {
-    const bool xface = p < d;
-    const int ax = xface ? p : p - d;
-    const sgdg_mesh& m = xface ? mx : mv;
-    if (m.periodic && m.periodic[ax]) continue;
-    const double cp = c.beta[p].coef;
-    const int sc = cp > 0 ? 1 : -1;
-    for (int side = -1; side <= 1; side += 2)
-      for (int s1 = 1; s1 >= -1; s1 -= 2) {
-        const int s2 = -side * s1;
-        FactorSpec X, V;
-        X.kind = xface ? 1 : 0;
-        V.kind = xface ? 0 : 1;
-        if (has_x(p)) { X.wfn = {p}; X.restrict_ = {{p, s1 * sc}}; }
-        else if (s1 != sc) continue;
-        if (has_v(p)) { V.wfn = {p}; V.restrict_ = {{p, s2}}; }
-        else if (s2 != 1) continue;
-        FactorSpec& F = xface ? X : V;
-        F.face_axis = ax;
-        F.face_side = side;
-        add(mMt, side * cp, X, V);
-      }
-  }
+  for (const InflowPart& ip : inflow_parts(c, d, mx, mv)) add(mMt, ip.scale, ip.x, ip.v);
   // merge equal factor pairs; index the distinct factors
   std::map<FactorSpec, int> xid, vid;
   std::map<std::pair<int, int>, int> tid;

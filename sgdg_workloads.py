@@ -77,6 +77,7 @@ class Problem:
     u0: List[Product]           # sum of separable products
     exact: Optional[Callable[[float, np.ndarray, np.ndarray], np.ndarray]] = None
     f: List[Source] = field(default_factory=list)   # source, sum of separable terms
+    g: List[Source] = field(default_factory=list)   # inflow data on Gamma^-, sum of separable terms
 
 
 # ----------------------------------------------------------------------------
@@ -269,6 +270,62 @@ def discrete_manufactured_1d(L: int = 3, sigma: float = 0.5, dt: float = 1.0 / 8
                    beta=[Product(1.0, None, lambda p: p[:, 0]), Product(0.0)],
                    sigma=Product(sigma) if sigma != 0.0 else Product(0.0),
                    u0=[Product(c0, phi, psi)], exact=exact, f=f)
+
+
+def inflow_manufactured_1d(L: int = 3, sigma: float = 0.3, dt: float = 1.0 / 8.0, n_strips: int = 2,
+                           c0: float = 1.0, c1: float = 0.5) -> Problem:
+    """d=1 solution inside the discrete space that does not vanish on the
+    boundary: u*(t, x, v) = (c0 + c1 t)(1 + x)(1 + v/2) on x in [0,1],
+    v in [-1,1] (P1 in x and v, linear in t), beta = (v, x - 1/2) (inflow on
+    all four sides, sign changes on the mesh lines v = 0 and x = 1/2),
+    constant sigma; f = d_t u* + beta . grad u* + sigma u* as four separable
+    terms and the inflow data g = u* on Gamma^-.  Exact quadrature of the
+    polynomial data lets a consistent scheme reproduce u* up to the solver
+    tolerance."""
+    X = lambda p: 1.0 + p[:, 0]
+    V = lambda p: 1.0 + 0.5 * p[:, 0]
+    vV = lambda p: p[:, 0] * V(p)
+    eX = lambda p: (p[:, 0] - 0.5) * X(p)
+    a = lambda t: c0 + c1 * np.asarray(t)
+    da = lambda t: c1 + 0.0 * np.asarray(t)
+
+    def exact(t, x, v):
+        return (c0 + c1 * t) * (1.0 + x) * (1.0 + 0.5 * v)
+
+    f = [Source(1.0, X, V, da), Source(sigma, X, V, a), Source(1.0, None, vV, a), Source(0.5, eX, None, a)]
+    h = 1.0 / (4 * 2 ** L)
+    return Problem(name=f"inflow_manufactured_1d_L{L}", d=1, mesh_x=interval_mesh(0.0, 1.0, 4),
+                   mesh_v=interval_mesh(-1.0, 1.0, 4), L=L, r=1, dt=dt, delta=h, n_strips=n_strips,
+                   beta=[Product(1.0, None, lambda p: p[:, 0]), Product(1.0, lambda p: p[:, 0] - 0.5, None)],
+                   sigma=Product(sigma) if sigma != 0.0 else Product(0.0),
+                   u0=[Product(c0, X, V)], exact=exact, f=f, g=[Source(1.0, X, V, a)])
+
+
+def inflow_manufactured_2d(L: int = 2, sigma: float = 0.2, dt: float = 1.0 / 8.0, n_strips: int = 2,
+                           c0: float = 1.0, c1: float = -0.4) -> Problem:
+    """d=2 analogue on [0,1]^2 x [-1,1]^2: u* = (c0 + c1 t)(1 + x1 + 2 x2)
+    (1 + v1/2 - 0.3 v2), beta = (v1, v2, x2 - 1/2, 1/2 - x1) (inflow on every
+    side of both boxes), f as separable polynomial terms, g = u* on Gamma^-."""
+    X = lambda p: 1.0 + p[:, 0] + 2.0 * p[:, 1]
+    V = lambda p: 1.0 + 0.5 * p[:, 0] - 0.3 * p[:, 1]
+    a = lambda t: c0 + c1 * np.asarray(t)
+    da = lambda t: c1 + 0.0 * np.asarray(t)
+
+    def exact(t, x, v):
+        return (c0 + c1 * t) * (1.0 + x[..., 0] + 2.0 * x[..., 1]) * (1.0 + 0.5 * v[..., 0] - 0.3 * v[..., 1])
+
+    f = [Source(1.0, X, V, da), Source(sigma, X, V, a),
+         Source(1.0, None, lambda p: p[:, 0] * V(p), a),            # v1 d_x1 u*, d_x1 X = 1
+         Source(2.0, None, lambda p: p[:, 1] * V(p), a),            # v2 d_x2 u*, d_x2 X = 2
+         Source(0.5, lambda p: (p[:, 1] - 0.5) * X(p), None, a),     # E1 d_v1 u*, d_v1 V = 1/2
+         Source(-0.3, lambda p: (0.5 - p[:, 0]) * X(p), None, a)]    # E2 d_v2 u*, d_v2 V = -0.3
+    hx = 1.0 / 2 ** (L + 1)
+    return Problem(name=f"inflow_manufactured_2d_L{L}", d=2, mesh_x=square_mesh(0.0, 1.0, 2),
+                   mesh_v=square_mesh(-1.0, 1.0, 2), L=L, r=1, dt=dt, delta=hx, n_strips=n_strips,
+                   beta=[Product(1.0, None, lambda p: p[:, 0]), Product(1.0, None, lambda p: p[:, 1]),
+                         Product(1.0, lambda p: p[:, 1] - 0.5, None), Product(1.0, lambda p: 0.5 - p[:, 0], None)],
+                   sigma=Product(sigma) if sigma != 0.0 else Product(0.0),
+                   u0=[Product(c0, X, V)], exact=exact, f=f, g=[Source(1.0, X, V, a)])
 
 
 def manufactured_2d(L: int = 9, sigma: float = 0.1, dt: float = 1.0 / 64.0, n_strips: int = 16,
