@@ -56,6 +56,11 @@ def simplex_rule(d: int, q: int = QUAD_Q):
         wa, wb = np.meshgrid(w, w, indexing="ij")
         pts = np.stack([a.ravel(), (b * (1 - a)).ravel()], axis=1)
         return pts, (wa * wb * (1 - a)).ravel()
+    if d == 3:
+        a, b, c = np.meshgrid(g, g, g, indexing="ij")
+        wa, wb, wc = np.meshgrid(w, w, w, indexing="ij")
+        pts = np.stack([a.ravel(), (b * (1 - a)).ravel(), (c * (1 - a) * (1 - b)).ravel()], axis=1)
+        return pts, (wa * wb * wc * (1 - a) ** 2 * (1 - b)).ravel()
     raise NotImplementedError
 
 

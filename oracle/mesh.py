@@ -9,7 +9,11 @@ function at the fine vertices: a fine vertex that is a coarse vertex copies it,
 an edge midpoint averages the two edge end points.
 
 Refinement: 1D bisection, 2D red refinement (4 children through the edge
-midpoints).  Vertex order on every level is canonical: vertices sorted
+midpoints), 3D regular refinement after Bey (8 children: the four corner
+tetrahedra and the inner octahedron cut along the diagonal between the
+midpoints of edges 02 and 13), which maps a Kuhn (Freudenthal) tetrahedron
+with its vertices in path order onto the Kuhn tetrahedra of the refined
+lattice.  Vertex order on every level is canonical: vertices sorted
 lexicographically by coordinates, last axis slowest.  Periodic axes identify
 the vertex at the upper bound with the one at the lower bound.
 
@@ -68,8 +72,14 @@ def _refine_raw(coords: np.ndarray, cells: np.ndarray):
             a, b, cc = c
             mab, mbc, mca = m(a, b), m(b, cc), m(cc, a)
             out += [[a, mab, mca], [mab, b, mbc], [mca, mbc, cc], [mab, mbc, mca]]
+        elif d == 3:
+            x0, x1, x2, x3 = c
+            m01, m02, m03 = m(x0, x1), m(x0, x2), m(x0, x3)
+            m12, m13, m23 = m(x1, x2), m(x1, x3), m(x2, x3)
+            out += [[x0, m01, m02, m03], [m01, x1, m12, m13], [m02, m12, x2, m23], [m03, m13, m23, x3],
+                    [m01, m02, m03, m13], [m01, m02, m12, m13], [m02, m03, m13, m23], [m02, m12, m13, m23]]
         else:
-            raise NotImplementedError("oracle refinement supports d = 1, 2")
+            raise NotImplementedError("oracle refinement supports d = 1, 2, 3")
     return np.array(new_coords), np.array(out, dtype=np.int64), parents
 
 

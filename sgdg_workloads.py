@@ -106,6 +106,30 @@ def square_mesh(a: float, b: float, n_sq: int = 2, periodic: bool = False) -> Co
     return CoarseMesh(coords, np.array(cells, dtype=np.int32), (a, a), (b, b), (periodic, periodic))
 
 
+def cube_mesh(a: float, b: float, n_cb: int = 1, periodic: bool = False) -> CoarseMesh:
+    """n_cb^3 cubes, each cut into the 6 Kuhn (Freudenthal) tetrahedra that
+    share its main diagonal; every tetrahedron lists its vertices along a
+    monotone lattice path (corner, + e_i, + e_i + e_j, opposite corner).
+    n_cb = 1 gives the 6-tetrahedron coarse mesh."""
+    t = np.linspace(a, b, n_cb + 1)
+    Z, Y, X = np.meshgrid(t, t, t, indexing="ij")
+    coords = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    vid = lambda i, j, k: (k * (n_cb + 1) + j) * (n_cb + 1) + i
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    cells = []
+    for k in range(n_cb):
+        for j in range(n_cb):
+            for i in range(n_cb):
+                for pm in perms:
+                    p = [i, j, k]
+                    path = [vid(*p)]
+                    for ax in pm:
+                        p[ax] += 1
+                        path.append(vid(*p))
+                    cells.append(path)
+    return CoarseMesh(coords, np.array(cells, dtype=np.int32), (a, a, a), (b, b, b), (periodic,) * 3)
+
+
 # ----------------------------------------------------------------------------
 # problems
 # ----------------------------------------------------------------------------
@@ -183,6 +207,26 @@ def periodic_advection_1d(L: int, r: int = 1) -> Problem:
     return Problem(name=f"periodic_advection_1d_L{L}", d=1, mesh_x=mx, mesh_v=mv, L=L, r=r,
                    dt=T / n_strips, delta=h, n_strips=n_strips,
                    beta=[Product(1.0), Product(1.0)], sigma=Product(0.0), u0=u0, exact=exact)
+
+
+def transport_3d(L: int = 7, dt: float = 1.0 / 32.0, n_strips: int = 8) -> Problem:
+    """d=3 (6-D phase space): Omega_x = [0,1]^3, Omega_v = [-1,1]^3, 6-tetrahedron
+    Kuhn coarse meshes refined uniformly ((2^l + 1)^3 vertices on level l),
+    beta = (v, E(x)) with E = 0.5 (sin 2 pi x2, sin 2 pi x3, sin 2 pi x1),
+    sigma = 0, u0 = exp(-|x - 1/2|^2 / 0.01) exp(-|v|^2 / 0.1), delta = the
+    shortest finest edge (the x mesh's, 2^-L)."""
+    mx = cube_mesh(0.0, 1.0, 1)
+    mv = cube_mesh(-1.0, 1.0, 1)
+    hx = 1.0 / 2 ** L
+    beta = [Product(1.0, None, lambda p: p[:, 0]), Product(1.0, None, lambda p: p[:, 1]),
+            Product(1.0, None, lambda p: p[:, 2]),
+            Product(0.5, lambda p: np.sin(2 * np.pi * p[:, 1]), None),
+            Product(0.5, lambda p: np.sin(2 * np.pi * p[:, 2]), None),
+            Product(0.5, lambda p: np.sin(2 * np.pi * p[:, 0]), None)]
+    ux = lambda p: np.exp(-((p[:, 0] - 0.5) ** 2 + (p[:, 1] - 0.5) ** 2 + (p[:, 2] - 0.5) ** 2) / 0.01)
+    uv = lambda p: np.exp(-(p[:, 0] ** 2 + p[:, 1] ** 2 + p[:, 2] ** 2) / 0.1)
+    return Problem(name=f"transport_3d_L{L}", d=3, mesh_x=mx, mesh_v=mv, L=L, r=1, dt=dt, delta=hx,
+                   n_strips=n_strips, beta=beta, sigma=Product(0.0), u0=[Product(1.0, ux, uv)])
 
 
 def landau_4d(L: int = 8, alpha: float = 0.01, k: float = 0.5, n_strips: int = 200, dt: float = None,
