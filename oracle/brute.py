@@ -53,24 +53,33 @@ def _face_data(lev, q):
     return pts, rw[None, :] * meas[:, None], lam
 
 
-def _beta(prob, X, V):
-    """beta_p(x, v) on all point pairs: (2d, nx, nv)."""
+def _tf(pr, t):
+    """The time factor of a coefficient product at time t (1 without one)."""
+    ft = getattr(pr, "ft", None)
+    return 1.0 if ft is None else float(np.asarray(ft(np.array([t])))[0])
+
+
+def _beta(prob, X, V, t=0.0):
+    """beta_p(t, x, v) on all point pairs: (2d, nx, nv)."""
     out = []
     for b in prob.beta:
         fx = b.fx(X) if b.fx is not None else np.ones(X.shape[0])
         fv = b.fv(V) if b.fv is not None else np.ones(V.shape[0])
-        out.append(b.coef * np.outer(fx, fv))
+        out.append(b.coef * _tf(b, t) * np.outer(fx, fv))
     return np.array(out)
 
 
-def _sigma(prob, X, V):
+def _sigma(prob, X, V, t=0.0):
     s = prob.sigma
     fx = s.fx(X) if s.fx is not None else np.ones(X.shape[0])
     fv = s.fv(V) if s.fv is not None else np.ones(V.shape[0])
-    return s.coef * np.outer(fx, fv)
+    return s.coef * _tf(s, t) * np.outer(fx, fv)
 
 
-def full_matrix(prob, Lx: int, Lv: int, q: int = 4) -> np.ndarray:
+def full_matrix(prob, Lx: int, Lv: int, q: int = 4, t0: float = 0.0) -> np.ndarray:
+    """The strip (t0, t0 + dt); beta and sigma evaluated at every time
+    quadrature point (3-point Gauss-Legendre for r = 1), pointwise in
+    (t, x, v), Gamma^- included."""
     d, R, dt, dl = prob.d, prob.r + 1, prob.dt, prob.delta
     hx, hv = Hierarchy(prob.mesh_x, Lx), Hierarchy(prob.mesh_v, Lv)
     lx, lv = hx.levels[Lx], hv.levels[Lv]
@@ -92,21 +101,22 @@ def full_matrix(prob, Lx: int, Lv: int, q: int = 4) -> np.ndarray:
         s = np.arange(R)[None, None, :]
         return ((i * n2 + j) * R + s).ravel()
 
+    tabs = t0 + tq * dt                                  # absolute time points
     for cx in range(ncx):
         for cv in range(ncv):
-            B = _beta(prob, px[cx], pv[cv])            # (2d, qx, qv)
-            S = _sigma(prob, px[cx], pv[cv])           # (qx, qv)
+            B = np.array([_beta(prob, px[cx], pv[cv], t) for t in tabs])    # (nt, 2d, qx, qv)
+            S = np.array([_sigma(prob, px[cx], pv[cv], t) for t in tabs])   # (nt, qx, qv)
             W = np.outer(wx[cx], wv[cv])               # (qx, qv)
             # basis product values phi = lamx[qx,a] lamv[qv,b]; shape (qx,qv,a,b)
             phi = np.einsum("xa,vb->xvab", lamx, lamv)
-            # beta . grad of the spatial basis functions
-            bg = np.einsum("pxv,ap->xva", B[:d], gx[cx])[:, :, :, None] * lamv[None, :, None, :]
-            bg = bg + lamx[:, None, :, None] * np.einsum("pxv,bp->xvb", B[d:], gv[cv])[:, :, None, :]
+            # beta . grad of the spatial basis functions at every time point: (nt, qx, qv, a, b)
+            bg = np.einsum("tpxv,ap->txva", B[:, :d], gx[cx])[..., None] * lamv[None, None, :, None, :]
+            bg = bg + lamx[None, :, None, :, None] * np.einsum("tpxv,bp->txvb", B[:, d:], gv[cv])[:, :, :, None, :]
             # time: L(Phi') = eta' phi + eta (bg + sigma phi);  W(Phi) = eta phi + dl (eta' phi + eta bg)
             Lop = (np.einsum("st,xvab->txvsab", ed, phi)
-                   + np.einsum("st,xvab->txvsab", et, bg + S[:, :, None, None] * phi))
+                   + np.einsum("st,txvab->txvsab", et, bg + S[..., None, None] * phi))
             Wop = (np.einsum("st,xvab->txvsab", et, phi)
-                   + dl * (np.einsum("st,xvab->txvsab", ed, phi) + np.einsum("st,xvab->txvsab", et, bg)))
+                   + dl * (np.einsum("st,xvab->txvsab", ed, phi) + np.einsum("st,txvab->txvsab", et, bg)))
             wts = tw[:, None, None] * W[None]
             loc = np.einsum("txv,txvsab,txvSAB->abSABs", wts, Wop, Lop)
             # loc[a, b, S, A, B, s]: test (a, b, s) x trial (A, B, S) -> reorder to (a,b,s),(A,B,S)
@@ -135,25 +145,24 @@ def full_matrix(prob, Lx: int, Lv: int, q: int = 4) -> np.ndarray:
             ax, sd = lev_b.bface_axis[f], lev_b.bface_side[f]
             for co in range(lev_o.cells.shape[0]):
                 if is_x:
-                    B = _beta(prob, pf[f], pts_o[co])                   # (2d, qf, qo)
-                    bn = sd * B[ax]
+                    B = np.array([_beta(prob, pf[f], pts_o[co], t) for t in tabs])   # (nt, 2d, qf, qo)
+                    bn = sd * B[:, ax]
                     phi = np.einsum("fa,ob->foab", lamf, lam_o)
                     W = np.outer(wf[f], w_o[co])
                     di = lev_b.bfaces[f][:, None, None]
                     dj = lev_o.cells[co][None, :, None]
                 else:
-                    B = _beta(prob, pts_o[co], pf[f])                   # (2d, qo, qf)
-                    bn = sd * B[d + ax].T                               # (qf, qo)
+                    B = np.array([_beta(prob, pts_o[co], pf[f], t) for t in tabs])   # (nt, 2d, qo, qf)
+                    bn = sd * np.transpose(B[:, d + ax], (0, 2, 1))                  # (nt, qf, qo)
                     phi = np.einsum("fb,oa->foab", lamf, lam_o)
                     W = np.outer(wf[f], w_o[co])
                     di = lev_o.cells[co][:, None, None]
                     dj = lev_b.bfaces[f][None, :, None]
-                inflow = (bn < 0.0).astype(float)
-                g = W * bn * inflow                                     # (qf, qo)
-                m = np.einsum("fo,foab,foAB->abAB", g, phi, phi)
-                tm = np.einsum("q,sq,Sq->sS", tw, et, et)               # time mass
-                loc = -np.einsum("abAB,sS->absABS", m, tm)
-                a_n, b_n = m.shape[0], m.shape[1]
+                inflow = (bn < 0.0).astype(float)                       # Gamma^- at every time point
+                g = W[None] * bn * inflow                               # (nt, qf, qo)
+                m = np.einsum("tfo,foab,foAB->tabAB", g, phi, phi)
+                loc = -np.einsum("tabAB,t,st,St->absABS", m, tw, et, et)
+                a_n, b_n = m.shape[1], m.shape[2]
                 loc = loc.reshape(a_n * b_n * R, a_n * b_n * R)
                 idx = ((di * n2 + dj) * R + np.arange(R)[None, None, :]).ravel()
                 A[np.ix_(idx, idx)] += loc

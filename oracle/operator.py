@@ -7,7 +7,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 * Time matrices M^(t), T^(t), C^(t), G^(t) (Sect. 4.2, Eq. 10) from their
   definitions by Gauss quadrature in time (exact: the integrands are
   polynomials).
-* The Kronecker block formula (Sect. 4.2) with time-constant coefficients:
+* The Kronecker block formula (Sect. 4.2) with time-constant coefficients
+  (coefficients with a time factor: the quadrature sum over the strip's
+  Gauss points, ``time_dependent_terms``):
       A = (T_t + d C_t) (x) M  +  d T_t (x) T^T  +  d T_t^T (x) (T + K)
           + M_t (x) (T + d C + K + d K~ - G)  +  G_t (x) M
   where the factor d on K~ is taken from the weak form of Sect. 2 (the printed
@@ -133,8 +135,14 @@ def spatial_operators(prob):
     return ops
 
 
-def kron_terms(prob):
-    """List of (tau (R x R), X, V): the block formula of Sect. 4.2."""
+def kron_terms(prob, t0: float = 0.0, m: int = 3):
+    """List of (tau (R x R), X, V): the block formula of Sect. 4.2 for the
+    strip (t0, t0 + dt).  Time-constant coefficients: the exact time
+    matrices.  Coefficients with a time factor (Product.ft): the paper's
+    quadrature in time, m-point Gauss-Legendre on the strip, with the spatial
+    operators frozen at every point tau_mu (``time_dependent_terms``)."""
+    if is_time_dependent(prob):
+        return time_dependent_terms(prob, t0, m)
     Mt, Tt, Ct, Gt = time_matrices(prob.dt, prob.r)
     dl = prob.delta
     ops = spatial_operators(prob)
@@ -148,6 +156,59 @@ def kron_terms(prob):
     for tau, name in plan:
         for X, V in ops[name]:
             out.append((tau, X, V))
+    return out
+
+
+def is_time_dependent(prob) -> bool:
+    return any(getattr(b, "ft", None) is not None for b in prob.beta) or getattr(prob.sigma, "ft", None) is not None
+
+
+def _frozen(prob, t: float):
+    """The problem with its coefficients frozen at time t: every time factor
+    folded into the product's scalar coefficient."""
+    import copy
+    from dataclasses import replace
+
+    def fz(pr):
+        if getattr(pr, "ft", None) is None:
+            return pr
+        return replace(pr, coef=pr.coef * float(np.asarray(pr.ft(np.array([t])))[0]), ft=None)
+    q = copy.copy(prob)
+    q.beta = [fz(b) for b in prob.beta]
+    q.sigma = fz(prob.sigma)
+    return q
+
+
+def time_dependent_terms(prob, t0: float, m: int = 3):
+    """Sect. 4.2 with time-dependent beta, sigma: per Gauss point tau_mu of the
+    strip (weight w_mu, sum w_mu = dt) the point matrices
+        M_mu = [eta_s' eta_s], T_mu = [eta'_s' eta_s], C_mu = [eta'_s' eta'_s]
+    at tau_mu and the spatial operators T, C, K, K~, G of the coefficients
+    at tau_mu (the inflow boundary Gamma^-(tau_mu) included), summed as
+        sum_mu w_mu [ (T_mu + d C_mu) (x) M + d T_mu (x) T_mu^T
+                      + d T_mu^T (x) (T_mu + K_mu)
+                      + M_mu (x) (T_mu + d C_mu + K_mu + d K~_mu - G_mu) ]
+        + G^(t) (x) M,
+    with the factor d on K~ as in the time-constant case."""
+    R, dt, dl = prob.r + 1, prob.dt, prob.delta
+    tq, wq = gauss01(m)
+    _, _, _, Gt = time_matrices(dt, prob.r)
+    out = []
+    ops0 = spatial_operators(prob)
+    out += [(Gt, X, V) for X, V in ops0["M"]]
+    for q in range(m):
+        ev = np.array([eta(s, tq[q:q + 1], dt)[0][0] for s in range(R)])
+        ed = np.array([eta(s, tq[q:q + 1], dt)[1][0] for s in range(R)])
+        w = wq[q] * dt
+        Mm = w * np.outer(ev, ev)
+        Tm = w * np.outer(ev, ed)          # [s, s'] = eta'_s' eta_s
+        Cm = w * np.outer(ed, ed)
+        ops = spatial_operators(_frozen(prob, t0 + tq[q] * dt))
+        plan = [(Tm + dl * Cm, "M"), (dl * Tm, "Tt"), (dl * Tm.T, "T"), (dl * Tm.T, "K"),
+                (Mm, "T"), (dl * Mm, "C"), (Mm, "K"), (dl * Mm, "Kt"), (-Mm, "G")]
+        for tau, name in plan:
+            for X, V in ops[name]:
+                out.append((tau, X, V))
     return out
 
 
@@ -165,11 +226,19 @@ class SparseGridOperator:
         self.fx = FactorStore(self.hx)
         self.fv = FactorStore(self.hv)
         self.terms = kron_terms(prob)
+        self.t0 = 0.0
         self.grids = [(l, self.L - l) for l in range(self.L + 1)]
         self.shape = [(self.hx.levels[a].n, self.hv.levels[b].n) for a, b in self.grids]
         sizes = [a * b * self.R for a, b in self.shape]
         self.offsets = np.concatenate([[0], np.cumsum(sizes)])
         self.size = int(self.offsets[-1])
+
+    def set_time(self, t0: float):
+        """The operator of the strip (t0, t0 + dt): only coefficients with a
+        time factor make it depend on t0."""
+        if is_time_dependent(self.prob) and t0 != self.t0:
+            self.terms = kron_terms(self.prob, t0)
+        self.t0 = t0
 
     # --- layout helpers
     def block(self, u: np.ndarray, i: int) -> np.ndarray:

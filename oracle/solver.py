@@ -35,7 +35,7 @@ import scipy.sparse.linalg as spla
 from scipy import integrate
 
 from .assembly import Factor, assemble_load, assemble_load_grad
-from .operator import SparseGridOperator, eta, eta_at, time_matrices
+from .operator import SparseGridOperator, eta, eta_at, is_time_dependent, time_matrices
 
 
 def fgmres(A, b, M=None, x0=None, tol=1e-10, restart=30, maxiter=1000):
@@ -304,6 +304,8 @@ class StripSolver:
         return out
 
     def rhs(self, MU: np.ndarray, t0: float = 0.0) -> np.ndarray:
+        if is_time_dependent(self.prob) and (self.prob.f or self.prob.g):
+            raise NotImplementedError("sources and inflow data with time-dependent beta or sigma")
         return np.outer(MU, self.e_start).ravel() + self.source_rhs(t0) + self.inflow_rhs(t0)
 
     def endpoint(self, u: np.ndarray) -> np.ndarray:
@@ -324,6 +326,7 @@ class StripSolver:
         MU = self.initial_mass_u0()
         ends = []
         for j in range(n):
+            self.op.set_time(j * self.prob.dt)
             u, it, res = self.solve_strip(self.rhs(MU, j * self.prob.dt))
             if solutions is not None:
                 solutions.append(u)

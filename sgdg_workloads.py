@@ -44,10 +44,13 @@ class CoarseMesh:
 
 @dataclass
 class Product:
-    """coef * fx(x) * fv(v); ``None`` factors are the constant 1."""
+    """coef * ft(t) * fx(x) * fv(v); ``None`` factors are the constant 1.
+    ft (time-dependent beta and sigma, Sect. 4.2) maps an array of times to
+    values; u0 products leave it None."""
     coef: float
     fx: Fn = None
     fv: Fn = None
+    ft: Optional[Callable[[np.ndarray], np.ndarray]] = None
 
 
 @dataclass
@@ -227,6 +230,40 @@ def transport_3d(L: int = 7, dt: float = 1.0 / 32.0, n_strips: int = 8) -> Probl
     uv = lambda p: np.exp(-(p[:, 0] ** 2 + p[:, 1] ** 2 + p[:, 2] ** 2) / 0.1)
     return Problem(name=f"transport_3d_L{L}", d=3, mesh_x=mx, mesh_v=mv, L=L, r=1, dt=dt, delta=hx,
                    n_strips=n_strips, beta=beta, sigma=Product(0.0), u0=[Product(1.0, ux, uv)])
+
+
+def time_dependent_1d(L: int = 3, dt: float = 1.0 / 8.0, n_strips: int = 4, omega: float = 3.0,
+                      sigma0: float = 0.4) -> Problem:
+    """d=1 transport with coefficients that vary in time (Sect. 4.2 allows
+    beta(t, x, v) and sigma(t, x, v) in tensor form): x in [0,1], v in [-1,1],
+    beta = (v (1 + t/2), cos(omega t) (x - 1/2)), sigma = sigma0 (1 + sin(omega t)/2).
+    The v-component changes sign in time (at t = pi / (2 omega) = 0.52 for
+    omega = 3) and in space on the mesh line x = 1/2, so the inflow part of
+    the v-boundary switches sides within the run.  u0 = config-1 Gaussian."""
+    mx = interval_mesh(0.0, 1.0, 4)
+    mv = interval_mesh(-1.0, 1.0, 4)
+    h = 1.0 / (4 * 2 ** L)
+    ux = _gauss(0.5, 0.01)
+    uv = lambda p: np.exp(-(p[:, 0] ** 2) / 0.1)
+    return Problem(
+        name=f"time_dependent_1d_L{L}", d=1, mesh_x=mx, mesh_v=mv, L=L, r=1, dt=dt, delta=h, n_strips=n_strips,
+        beta=[Product(1.0, None, lambda p: p[:, 0], lambda t: 1.0 + 0.5 * np.asarray(t)),
+              Product(1.0, lambda p: p[:, 0] - 0.5, None, lambda t: np.cos(omega * np.asarray(t)))],
+        sigma=Product(sigma0, None, None, lambda t: 1.0 + 0.5 * np.sin(omega * np.asarray(t))),
+        u0=[Product(1.0, ux, uv)])
+
+
+def time_dependent_2d(L: int = 3, dt: float = 1.0 / 16.0, n_strips: int = 4, omega: float = 6.0) -> Problem:
+    """The transport_2d problem with a field that rotates its sign in time:
+    E(t, x) = cos(omega t) 0.5 (sin 2 pi x2, cos 2 pi x1) and
+    sigma = 0.1 (1 + t); beta = (v, E(t, x))."""
+    p = transport_2d(L=L, sigma=0.1, dt=dt, n_strips=n_strips)
+    c = lambda t: np.cos(omega * np.asarray(t))
+    p.beta[2] = Product(0.5, lambda q: np.sin(2 * np.pi * q[:, 1]), None, c)
+    p.beta[3] = Product(0.5, lambda q: np.cos(2 * np.pi * q[:, 0]), None, c)
+    p.sigma = Product(0.1, None, None, lambda t: 1.0 + np.asarray(t))
+    p.name = f"time_dependent_2d_L{L}"
+    return p
 
 
 def landau_4d(L: int = 8, alpha: float = 0.01, k: float = 0.5, n_strips: int = 200, dt: float = None,
