@@ -296,6 +296,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=8, help="instances in the batched strip measurement (0: skip)")
     ap.add_argument("--batch-levels", type=int, nargs="+", default=[5, 6, 7])
+    ap.add_argument("--d3-L", type=int, default=7,
+                    help="level of the d = 3 (6-D) apply measurement (transport_3d; -1: skip)")
     ap.add_argument("--batch-apply", type=int, default=48,
                     help="instances in the full-size batched apply (L from {6,7,8,9}, seed 0; 0: skip)")
     args = ap.parse_args()
@@ -485,6 +487,53 @@ def main():
     del u64, u32, y32, y64, u16, y16
     torch.cuda.empty_cache()
 
+    # ---- d = 3 (6-D phase space): the transport_3d workload (Kuhn cube meshes,
+    # beta = (v, E(x)), sigma = 0) at level d3_L; FP32 and FP64 applies, the
+    # handle's HBM footprint and the whole-apply algorithmic bandwidth
+    d3 = None
+    if args.d3_L >= 0:
+        t0 = time.perf_counter()
+        s3 = P.Solver(W.transport_3d(L=args.d3_L), device=local)
+        setup3 = time.perf_counter() - t0
+        n3 = s3.n_coeffs
+        v64 = torch.tensor(W.uniform_vector(n3, seed=3 + rank), dtype=torch.float64, device="cuda")
+        v32 = v64.float()
+        w32, w64 = torch.empty_like(v32), torch.empty_like(v64)
+        t0 = time.perf_counter()
+        s3.autotune(v32, w32, P.SGDG_MIXED_FP32, stream)
+        tune3 = time.perf_counter() - t0
+        l0 = s3.launch_count()
+        ms3 = timed(lambda: s3.apply_operator(v32, w32, P.SGDG_MIXED_FP32, stream), max(2, args.steps // 2), 2)
+        launches3 = (s3.launch_count() - l0) // (max(2, args.steps // 2) + 2)
+        ms3_64 = timed(lambda: s3.apply_operator(v64, w64, P.SGDG_FP64, stream), 2, 1)
+        s3.apply_operator(v64, w64, P.SGDG_FP64, stream)
+        s3.apply_operator(v32, w32, P.SGDG_MIXED_FP32, stream)
+        err3 = float(torch.linalg.vector_norm(w32.double() - w64) / torch.linalg.vector_norm(w64))
+        i3 = s3.info
+        b3 = (n3 * (4 + 4) + 4 * (i3.rows_x + i3.rows_v + 2 * (i3.L + 1))
+              + 4 * i3.nnz_x * (1 + i3.n_x_factors) + 4 * i3.nnz_v * (1 + i3.n_v_factors))
+        s3.profile(True)
+        s3.apply_operator(v32, w32, P.SGDG_MIXED_FP32, stream)
+        st3 = s3.kernel_stats()
+        s3.profile(False)
+        tot3 = sum(v["ms"] for v in st3.values())
+        d3 = {"workload": f"transport_3d d=3 L={args.d3_L} (6-D), Kuhn cube meshes, beta = (v, E(x)), sigma = 0, "
+                          f"operator apply A^(delta) u",
+              "dof_per_step": n3, "terms": i3.n_terms, "x_factors": i3.n_x_factors, "v_factors": i3.n_v_factors,
+              "f32": {"value": whole_job(world, n3, ms3 * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms3},
+              "f64": {"value": whole_job(world, n3, ms3_64 * 1e-3) / 1e9, "unit": "GDoF/s", "ms_per_step": ms3_64},
+              "rel_err_f32_vs_fp64": err3,
+              "hbm_footprint_bytes": i3.device_bytes,
+              "roofline": {"bound": "hbm", "achieved": b3 / (ms3 * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                           "frac": b3 / (ms3 * 1e-3) / 1e9 / peak, "alg_bytes_per_launch": b3,
+                           "sweep_GBps": sum(v["bytes"] for v in st3.values()) / (tot3 * 1e-3) / 1e9},
+              "launches_per_apply": launches3,
+              "per_kind": per_kind(st3), "setup_s": round(setup3, 2), "autotune_s": round(tune3, 2)}
+        log(f"d=3 L={args.d3_L}: FP32 {ms3:.2f} ms, FP64 {ms3_64:.2f} ms, {i3.device_bytes / 1e9:.1f} GB")
+        s3.close()
+        del v64, v32, w32, w64
+        torch.cuda.empty_cache()
+
     # ---- strip solves at 1e-8 (mixed vs FP64), the d = 2 transport workload at
     # level strip_L, dt = 1/64: both arms start each strip from the linear
     # extrapolation of the last two solutions (warm start 3; the previous
@@ -646,7 +695,7 @@ def main():
                 "bf16_apply": bf16_apply,
                 "rel_err_vs_fp64_apply": {"f32": err32, "bf16_storage": err16},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
-                "strip": strip, "batch_apply": batch_apply, "batch": batch, "cpu_baseline": cpu,
+                "strip": strip, "d3_apply": d3, "batch_apply": batch_apply, "batch": batch, "cpu_baseline": cpu,
                 "peaks": {"fp32_alu_gflops": fp32_peak, "fp32_source": fp32_peak_src,
                           "fp64_alu_gflops": fp64_peak, "fp64_source": fp64_peak_src,
                           "hbm_gbs": peak, "hbm_source": peak_kind}}

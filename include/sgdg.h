@@ -3,7 +3,7 @@
  * transport library (sm_103a CUDA + C++).
  *
  * Problem (Sect. 1, Eqs. 1-2): d_t u + beta . grad u + sigma u = f on
- * (0,T) x Omega, Omega = Omega_x x Omega_v (both d-dimensional, d = 1, 2),
+ * (0,T) x Omega, Omega = Omega_x x Omega_v (both d-dimensional, d = 1, 2, 3),
  * u(0) = u0, inflow u = g on Gamma^- = {beta . n < 0}, with f and g sums of
  * separable terms.
  *
@@ -80,7 +80,9 @@ typedef enum {
 /* A coarse simplicial mesh of an axis-aligned box (one of Omega_x, Omega_v).
  * coords: [n_vertices][dim]; cells: [n_cells][dim+1] vertex indices.
  * lo/hi: box bounds per axis; periodic: per-axis flag (0/1).  Uniform
- * refinement (1D bisection, 2D red refinement) builds the levels. */
+ * refinement (1D bisection, 2D red refinement, 3D regular refinement after
+ * Bey, which keeps a Kuhn mesh whose tetrahedra list their vertices along a
+ * monotone lattice path a Kuhn lattice) builds the levels (Sect. 2). */
 typedef struct {
   int dim;
   int n_vertices;
@@ -132,7 +134,7 @@ typedef struct {
  * operator; its time integrals use 3-point Gauss-Legendre on every strip.
  * Sources and inflow data are not combined with vlasov_poisson (EINVAL). */
 typedef struct {
-  sgdg_product beta[4];
+  sgdg_product beta[6];   /* 2d used; the rest are ignored */
   sgdg_product sigma;
   int n_u0;
   const sgdg_product* u0;

@@ -48,7 +48,7 @@ class Source(C.Structure):
 
 
 class Coeffs(C.Structure):
-    _fields_ = [("beta", Product * 4), ("sigma", Product), ("n_u0", C.c_int), ("u0", C.POINTER(Product)),
+    _fields_ = [("beta", Product * 6), ("sigma", Product), ("n_u0", C.c_int), ("u0", C.POINTER(Product)),
                 ("n_f", C.c_int), ("f", C.POINTER(Source)), ("n_g", C.c_int), ("g", C.POINTER(Source))]
 
 
@@ -222,7 +222,7 @@ class Solver:
         cfg.hbm_budget_bytes = int(hbm_budget_bytes)
         co = Coeffs()
         d = problem.d
-        for p in range(4):
+        for p in range(6):
             if p < 2 * d:
                 co.beta[p] = self._product(problem.beta[p], d)
             else:

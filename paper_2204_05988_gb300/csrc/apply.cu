@@ -23,7 +23,9 @@
 // 2-D sides).  S_{b,i}, which includes the diagonal blocks, is formed on every
 // grid for its final update and restricted once to carry the chains on;
 // branch B never forms T or T' at full size.  The products R1 X_c and V_a P2
-// are formed once per level on the host.  This reaches
+// are formed once per level on the host.  On 3D Kuhn lattices R1 X_c has rows
+// of 65 entries; there branch B forms T_c = X_c U_{i+1} + Z_{c,i+1} P2^T on
+// grid i + 1 and restricts it (Z_{c,i} = R1 T_c), one launch group at a time.  This reaches
 // the blockwise sum of Sect. 4.2 exactly in exact arithmetic with
 // O(#terms * N) work; no intermediate exceeds one component grid, like the
 // ordering rule of Sect. 4.2.
@@ -66,20 +68,27 @@ Status ensure_bufs(Handle& h) {
   return {};
 }
 
-// Sweep pool: the diagonal-block products W_b (one grid each, all A chains),
-// a ring of two chain states Z per chain of both branches, and the
-// restricted states Q of one launch group.
+// Sweep pool: the diagonal-block products W_b (one grid each, all A chains;
+// on sides without R X products also the full-size branch-B states T_c of
+// one launch group), a ring of two chain states Z per chain of both branches,
+// and the restricted states Q of one launch group.
 struct PoolShape {
   long long mg = 2, mz = 2, mq = 2;   // elements per W, Z and Q slot
+  bool wide_b = false;                // branch B through full-size states (no R X products)
+  long long nw(const Plan& p) const {
+    return std::max<long long>((long long)p.A.size(),
+                               wide_b ? std::min<long long>(kChainSlots, (long long)p.B.size()) : 0);
+  }
   long long elems(const Plan& p) const {
     const long long a = (long long)p.A.size(), b = (long long)p.B.size();
-    return a * mg + 2 * (a + b) * mz + std::min<long long>(kChainSlots, std::max(a, b)) * mq;
+    return nw(p) * mg + 2 * (a + b) * mz + std::min<long long>(kChainSlots, std::max(a, b)) * mq;
   }
 };
 
 inline PoolShape pool_shape(const Handle& h) {
   PoolShape ps;
   const int L = h.L;
+  ps.wide_b = !h.X.has_rf;
   for (int l = 0; l <= L; ++l) ps.mg = std::max(ps.mg, 2LL * h.n1[l] * h.n2[l]);
   for (int i = 1; i <= L; ++i) ps.mz = std::max(ps.mz, 2LL * h.X.n[i - 1] * h.V.n[L - i]);
   for (int i = 0; i < L; ++i) ps.mz = std::max(ps.mz, 2LL * h.X.n[i] * h.V.n[L - i - 1]);
@@ -92,11 +101,11 @@ template <typename T>
 struct Pool {
   Store<T>* base = nullptr;
   PoolShape ps;
-  size_t nA = 0, nB = 0;
+  size_t nA = 0, nB = 0, nW = 0;
   Store<T>* W(int b) const { return base + (size_t)b * ps.mg; }
-  Store<T>* ZA(int b, int par) const { return base + nA * ps.mg + (size_t)(2 * b + par) * ps.mz; }
-  Store<T>* ZB(int c, int par) const { return base + nA * ps.mg + 2 * nA * ps.mz + (size_t)(2 * c + par) * ps.mz; }
-  Store<T>* Q(int g) const { return base + nA * ps.mg + 2 * (nA + nB) * ps.mz + (size_t)g * ps.mq; }
+  Store<T>* ZA(int b, int par) const { return base + nW * ps.mg + (size_t)(2 * b + par) * ps.mz; }
+  Store<T>* ZB(int c, int par) const { return base + nW * ps.mg + 2 * nA * ps.mz + (size_t)(2 * c + par) * ps.mz; }
+  Store<T>* Q(int g) const { return base + nW * ps.mg + 2 * (nA + nB) * ps.mz + (size_t)g * ps.mq; }
 };
 
 template <typename T>
@@ -104,6 +113,7 @@ Status ensure_pool(Handle& h, const Plan& p, Pool<T>& pool) {
   pool.ps = pool_shape(h);
   pool.nA = p.A.size();
   pool.nB = p.B.size();
+  pool.nW = (size_t)pool.ps.nw(p);
   // sized once for the largest plan of the handle (the operator's)
   const long long need = std::max(pool.ps.elems(h.op), pool.ps.elems(p));
   Handle::Bufs& b = bufs<T>(h);
@@ -476,8 +486,51 @@ Status apply_plan(Handle& h, const Plan& p, const Store<T>* u, Store<T>* y, cuda
     const int lv = L - i;   // output v level; Z_{c,i}: (nx[i] x nv[lv-1])
     for (int c0 = 0; c0 < nB; c0 += G) {
       const int nc = std::min(G, nB - c0);
-      double qbytes = 0.0;
       const bool prev = i < L - 1;
+      if (!X.has_rf) {
+        // no R X products (3D): T_c = X_c U_{i+1} + Z_{c,i+1} P2^T on grid
+        // i + 1 (nx[i+1] x nv[lv-1]), then Z_{c,i} = R1 T_c
+        ChainArgs<T> a;
+        a.n1 = X.n[i + 1];
+        a.n2 = V.n[lv - 1];
+        a.nu2 = V.n[lv - 1];
+        a.nz2 = prev ? V.n[lv - 2] : 0;
+        a.nchains = nc;
+        a.has_prev = prev;
+        a.row = X.row_regs();
+        a.U = u + h.off[i + 1];
+        a.f_col = X.ell_col[i + 1];
+        for (int g = 0; g < nc; ++g) {
+          a.f_val[g] = X.vals<Comp<T>>().ell_fac[p.B[c0 + g].first][i + 1];
+          a.out[g] = pool.W(g);
+          a.Z[g] = prev ? pool.ZB(c0 + g, (i + 1) & 1) : nullptr;
+        }
+        double in = grid_bytes<T>(h.n1[i + 1], h.n2[i + 1]) + ell_bytes<T>(X.n[i + 1], X.ell_w(), nc);
+        if (prev) {
+          a.p_col = V.E_ell_col[lv - 2];
+          a.p_val = V.vals<Comp<T>>().ell_E[lv - 2];
+          in += nc * grid_bytes<T>(X.n[i + 1], V.n[lv - 2]) + ell_bytes<T>(V.n[lv - 1], kEllE, 1);
+        }
+        st = run_chain(h, a, false, KIND_CHAIN_B, s, in);
+        if (st.code) return st;
+        RestrictArgs<T> r;
+        r.n1 = X.n[i];
+        r.n2 = V.n[lv - 1];
+        r.n1_in = X.n[i + 1];
+        r.n2_in = V.n[lv - 1];
+        r.nchains = nc;
+        r.row = X.row_regs();
+        r.col = X.R_ell_col[i];
+        r.val = X.vals<Comp<T>>().ell_R[i];
+        for (int g = 0; g < nc; ++g) {
+          r.in[g] = pool.W(g);
+          r.out[g] = pool.ZB(c0 + g, i & 1);
+        }
+        st = run_restrict(h, r, false, s, ell_bytes<T>(X.n[i], X.ell_w(), 1));
+        if (st.code) return st;
+        continue;
+      }
+      double qbytes = 0.0;
       if (prev) {
         RestrictArgs<T> r;   // Q_g = R1 Z_{c,i+1}: (nx[i] x nv[lv-2])
         r.n1 = X.n[i];

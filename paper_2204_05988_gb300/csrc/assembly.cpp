@@ -4,7 +4,8 @@
 //
 // Quadrature: q = 4 Gauss-Legendre points per direction on [0,1] (nodes by
 // Newton's method on P_q), collapsed onto the triangle (Duffy map
-// (a, b) -> (a, b (1 - a)), Jacobian 1 - a).  Sign restrictions (inflow
+// (a, b) -> (a, b (1 - a)), Jacobian 1 - a) and the tetrahedron
+// ((a, b, c) -> (a, b (1 - a), c (1 - a)(1 - b)), Jacobian (1 - a)^2 (1 - b)).  Sign restrictions (inflow
 // splitting, Sect. 5.2) test the sign of one coefficient function at the cell
 // or face centroid.
 #include <algorithm>
@@ -50,12 +51,24 @@ void simplex_rule(int k, std::vector<double>& pts, std::vector<double>& wts) {
   wts.clear();
   if (k == 0) { wts.push_back(1.0); return; }
   if (k == 1) { pts = g; wts = w; return; }
+  if (k == 2) {
+    for (int a = 0; a < kQ; ++a)
+      for (int b = 0; b < kQ; ++b) {
+        pts.push_back(g[a]);
+        pts.push_back(g[b] * (1.0 - g[a]));
+        wts.push_back(w[a] * w[b] * (1.0 - g[a]));
+      }
+    return;
+  }
+  // tetrahedron: (a, b, c) -> (a, b (1 - a), c (1 - a)(1 - b)), Jacobian (1 - a)^2 (1 - b)
   for (int a = 0; a < kQ; ++a)
-    for (int b = 0; b < kQ; ++b) {
-      pts.push_back(g[a]);
-      pts.push_back(g[b] * (1.0 - g[a]));
-      wts.push_back(w[a] * w[b] * (1.0 - g[a]));
-    }
+    for (int b = 0; b < kQ; ++b)
+      for (int c = 0; c < kQ; ++c) {
+        pts.push_back(g[a]);
+        pts.push_back(g[b] * (1.0 - g[a]));
+        pts.push_back(g[c] * (1.0 - g[a]) * (1.0 - g[b]));
+        wts.push_back(w[a] * w[b] * w[c] * (1.0 - g[a]) * (1.0 - g[a]) * (1.0 - g[b]));
+      }
 }
 
 int find_pos(const Csr& P, int i, int j) {
@@ -118,175 +131,197 @@ static void project_down(const Hierarchy& h, std::vector<Csr>& X) {
   }
 }
 
-Status prefill_cache(const Hierarchy& h, const SideFns& fns, const std::vector<FactorSpec>& specs, QuadCache& cache) {
-  // one serial assembly of a plain volume factor fills the points and positions
-  FactorSpec plain;
-  std::vector<Csr> X;
-  Status st = assemble_factor(h, fns, plain, X, &cache);
-  if (st.code) return st;
-  const int d = h.d, d1 = d + 1;
-  const MeshLevel& lv = h.lev[h.L];
-  const int nc = lv.ncells(d);
-  std::vector<double> cen;
-  for (const FactorSpec& f : specs) {
-    if (f.kind != 0) continue;
-    for (int id : f.wfn) {
-      if (fns.cell_field(id) || cache.fn_vals.count(id)) continue;
-      if (!fns.fn[id]) return {SGDG_EINVAL, "factor needs a coefficient function that is no longer available"};
-      eval_fn(fns, id, cache.pts, d, cache.fn_vals[id]);
-    }
-    for (auto& rs : f.restrict_) {
-      if (fns.cell_field(rs.first) || cache.cen_vals.count(rs.first)) continue;
-      if (cen.empty()) {
-        cen.assign((size_t)nc * d, 0.0);
-        for (int e = 0; e < nc; ++e)
-          for (int a = 0; a < d1; ++a)
-            for (int k = 0; k < d; ++k) cen[(size_t)e * d + k] += lv.cell_coords[((size_t)e * d1 + a) * d + k] / d1;
-      }
-      eval_fn(fns, rs.first, cen, d, cache.cen_vals[rs.first]);
-    }
+namespace {
+
+// Affine map of a simplex (vertices v0 .. vd): the inverse Jacobian Ji and
+// det J, for d = 1, 2, 3.
+void simplex_jacobian(int d, const double* v0, double (&Ji)[3][3], double& det) {
+  double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int k = 0; k < d; ++k)
+    for (int a = 0; a < d; ++a) J[k][a] = v0[(a + 1) * d + k] - v0[k];
+  if (d == 1) {
+    det = J[0][0];
+    Ji[0][0] = 1.0 / det;
+  } else if (d == 2) {
+    det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det;
+    Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
+  } else {
+    // cofactors: Ji = adj(J) / det
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    Ji[0][0] = c00 / det;
+    Ji[1][0] = c01 / det;
+    Ji[2][0] = c02 / det;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
   }
-  return {};
 }
 
-Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec& f, std::vector<Csr>& X,
-                       QuadCache* cache) {
+// physical gradients of the barycentric functions: grad lam_a = Ji^T gref_a
+void barycentric_gradients(int d, const double (&Ji)[3][3], double (&grad)[4][3]) {
+  for (int a = 0; a <= d; ++a)
+    for (int k = 0; k < d; ++k) {
+      double g = 0.0;
+      for (int m = 0; m < d; ++m) {
+        const double gr = (a == 0) ? -1.0 : (m == a - 1 ? 1.0 : 0.0);
+        g += Ji[m][k] * gr;
+      }
+      grad[a][k] = g;
+    }
+}
+
+constexpr int kCellChunk = 1 << 15;   // cells per pass of the volume assembly
+
+}  // namespace
+
+Status assemble_volume(const Hierarchy& h, const SideFns& fns, const std::vector<FactorSpec>& specs,
+                       std::vector<std::vector<Csr>>& X) {
   const int d = h.d, d1 = d + 1, L = h.L;
   const MeshLevel& lv = h.lev[L];
   const Csr& P = lv.pattern;
+  const int nc = lv.ncells(d);
+  const int nf = (int)specs.size();
+  X.assign(nf, std::vector<Csr>());
+  // the functions the factors read (weights at the quadrature points, signs
+  // at the cell centroids); cell fields are read per cell
+  std::vector<int> wids, rids;
+  for (const FactorSpec& f : specs) {
+    if (f.kind != 0) return {SGDG_EINVAL, "assemble_volume: boundary-face factor"};
+    for (int id : f.wfn) {
+      if (const std::vector<double>* cf = fns.cell_field(id)) {
+        if ((int)cf->size() != nc) return {SGDG_EINVAL, "cell field size differs from the finest cell count"};
+      } else if (id < 0 || id >= (int)fns.fn.size() || !fns.fn[id]) {
+        return {SGDG_EINVAL, "factor needs a coefficient function that is no longer available"};
+      } else if (std::find(wids.begin(), wids.end(), id) == wids.end()) {
+        wids.push_back(id);
+      }
+    }
+    for (auto& rs : f.restrict_) {
+      if (const std::vector<double>* cf = fns.cell_field(rs.first)) {
+        if ((int)cf->size() != nc) return {SGDG_EINVAL, "cell field size differs from the finest cell count"};
+      } else if (rs.first < 0 || rs.first >= (int)fns.fn.size() || !fns.fn[rs.first]) {
+        return {SGDG_EINVAL, "factor needs a coefficient function that is no longer available"};
+      } else if (std::find(rids.begin(), rids.end(), rs.first) == rids.end()) {
+        rids.push_back(rs.first);
+      }
+    }
+  }
+  for (int f = 0; f < nf; ++f) {
+    X[f].assign(L + 1, Csr());
+    Csr& A = X[f][L];
+    A.nrows = A.ncols = lv.n;
+    A.rowptr = P.rowptr;
+    A.col = P.col;
+    A.val.assign(P.col.size(), 0.0);
+  }
+  std::vector<double> rp, rw;
+  simplex_rule(d, rp, rw);
+  const int nq = (int)rw.size();
+  // per chunk: quadrature points, centroids, function values, element scatter
+  // positions; then every factor's element matrices, scattered in cell order
+  // (the values do not depend on the chunk size or the thread count)
+  std::vector<double> pts, cen;
+  std::map<int, std::vector<double>> wv, rv;
+  std::vector<int> pos;
+  for (int e0 = 0; e0 < nc; e0 += kCellChunk) {
+    const int ne = std::min(kCellChunk, nc - e0);
+    pts.assign((size_t)ne * nq * d, 0.0);
+    cen.assign((size_t)ne * d, 0.0);
+    pos.assign((size_t)ne * d1 * d1, 0);
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < ne; ++c) {
+      const size_t e = (size_t)e0 + c;
+      const double* v0 = &lv.cell_coords[e * d1 * d];
+      for (int q = 0; q < nq; ++q)
+        for (int k = 0; k < d; ++k) {
+          double x = v0[k];
+          for (int a = 1; a < d1; ++a) x += (v0[a * d + k] - v0[k]) * rp[q * d + (a - 1)];
+          pts[((size_t)c * nq + q) * d + k] = x;
+        }
+      for (int a = 0; a < d1; ++a)
+        for (int k = 0; k < d; ++k) cen[(size_t)c * d + k] += v0[a * d + k] / d1;
+      const int* cv = &lv.cells[e * d1];
+      for (int i = 0; i < d1; ++i)
+        for (int j = 0; j < d1; ++j) pos[((size_t)c * d1 + i) * d1 + j] = find_pos(P, cv[i], cv[j]);
+    }
+    for (int id : wids) eval_fn(fns, id, pts, d, wv[id]);
+    for (int id : rids) eval_fn(fns, id, cen, d, rv[id]);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int fi = 0; fi < nf; ++fi) {
+      const FactorSpec& f = specs[fi];
+      std::vector<double>& val = X[fi][L].val;
+      std::vector<double> wq((size_t)nq);
+      for (int c = 0; c < ne; ++c) {
+        const size_t e = (size_t)e0 + c;
+        bool keep = true;
+        for (auto& rs : f.restrict_) {
+          const std::vector<double>* cf = fns.cell_field(rs.first);
+          const double sv = cf ? (*cf)[e] : rv.at(rs.first)[c];
+          if (!(rs.second * sv > 0.0)) keep = false;
+        }
+        if (!keep) continue;
+        const double* v0 = &lv.cell_coords[e * d1 * d];
+        double Ji[3][3], det, grad[4][3];
+        simplex_jacobian(d, v0, Ji, det);
+        barycentric_gradients(d, Ji, grad);
+        for (int q = 0; q < nq; ++q) wq[q] = 1.0;
+        for (int id : f.wfn) {
+          if (const std::vector<double>* cf = fns.cell_field(id)) {
+            for (int q = 0; q < nq; ++q) wq[q] *= (*cf)[e];
+          } else {
+            const double* fv = &wv.at(id)[(size_t)c * nq];
+            for (int q = 0; q < nq; ++q) wq[q] *= fv[q];
+          }
+        }
+        double Ke[4][4] = {{0}};
+        for (int q = 0; q < nq; ++q) {
+          double lam[4];
+          lam[0] = 1.0;
+          for (int a = 1; a < d1; ++a) { lam[a] = rp[q * d + a - 1]; lam[0] -= lam[a]; }
+          const double w = rw[q] * std::fabs(det) * wq[q];
+          for (int i = 0; i < d1; ++i) {
+            const double ti = f.test == 0 ? lam[i] : grad[i][f.test - 1];
+            for (int j = 0; j < d1; ++j) {
+              const double tj = f.trial == 0 ? lam[j] : grad[j][f.trial - 1];
+              Ke[i][j] += w * ti * tj;
+            }
+          }
+        }
+        for (int i = 0; i < d1; ++i)
+          for (int j = 0; j < d1; ++j) val[pos[((size_t)c * d1 + i) * d1 + j]] += Ke[i][j];
+      }
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int fi = 0; fi < nf; ++fi) project_down(h, X[fi]);
+  return {};
+}
+
+Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec& f, std::vector<Csr>& X) {
+  const int d = h.d, L = h.L;
+  const MeshLevel& lv = h.lev[L];
+  const Csr& P = lv.pattern;
+  if (f.kind == 0) {
+    std::vector<std::vector<Csr>> one;
+    Status st = assemble_volume(h, fns, {f}, one);
+    if (st.code) return st;
+    X = std::move(one[0]);
+    return {};
+  }
   X.assign(L + 1, Csr());
   Csr& A = X[L];
   A.nrows = A.ncols = lv.n;
   A.rowptr = P.rowptr;
   A.col = P.col;
   A.val.assign(P.col.size(), 0.0);
-
-  if (f.kind == 0) {
-    const int nc = lv.ncells(d);
-    std::vector<double> rp, rw;
-    simplex_rule(d, rp, rw);
-    const int nq = (int)rw.size();
-    // centroids for the sign restriction
-    std::vector<char> keep(nc, 1);
-    if (!f.restrict_.empty()) {
-      std::vector<double> cen((size_t)nc * d, 0.0), val;
-      for (int e = 0; e < nc; ++e)
-        for (int a = 0; a < d1; ++a)
-          for (int k = 0; k < d; ++k) cen[(size_t)e * d + k] += lv.cell_coords[((size_t)e * d1 + a) * d + k] / d1;
-      for (auto& rs : f.restrict_) {
-        if (const std::vector<double>* cf = fns.cell_field(rs.first)) {
-          if ((int)cf->size() != nc) return {SGDG_EINVAL, "cell field size differs from the finest cell count"};
-          val = *cf;
-        } else if (cache && cache->cen_vals.count(rs.first)) {
-          val = cache->cen_vals.at(rs.first);
-        } else {
-          eval_fn(fns, rs.first, cen, d, val);
-          if (cache) cache->cen_vals[rs.first] = val;
-        }
-        for (int e = 0; e < nc; ++e)
-          if (!(rs.second * val[e] > 0.0)) keep[e] = 0;
-      }
-    }
-    // quadrature points of all cells and the weight product there
-    std::vector<double> own_pts;
-    std::vector<double>& pts = cache ? cache->pts : own_pts;
-    if (pts.size() != (size_t)nc * nq * d) {
-      pts.assign((size_t)nc * nq * d, 0.0);
-#pragma omp parallel for schedule(static)
-      for (int e = 0; e < nc; ++e) {
-        const double* v0 = &lv.cell_coords[(size_t)e * d1 * d];
-        for (int q = 0; q < nq; ++q)
-          for (int k = 0; k < d; ++k) {
-            double x = v0[k];
-            for (int a = 1; a < d1; ++a) x += (v0[a * d + k] - v0[k]) * rp[q * d + (a - 1)];
-            pts[((size_t)e * nq + q) * d + k] = x;
-          }
-      }
-    }
-    std::vector<double> wprod((size_t)nc * nq, 1.0), tmp;
-    for (int id : f.wfn) {
-      if (const std::vector<double>* cf = fns.cell_field(id)) {
-        if ((int)cf->size() != nc) return {SGDG_EINVAL, "cell field size differs from the finest cell count"};
-        for (int e = 0; e < nc; ++e)
-          for (int q = 0; q < nq; ++q) wprod[(size_t)e * nq + q] *= (*cf)[e];
-        continue;
-      }
-      if (!fns.fn[id]) return {SGDG_EINVAL, "factor needs a coefficient function that is no longer available"};
-      const std::vector<double>* vals = nullptr;
-      if (cache) {
-        auto it = cache->fn_vals.find(id);
-        if (it == cache->fn_vals.end()) {
-          eval_fn(fns, id, pts, d, tmp);
-          it = cache->fn_vals.emplace(id, std::move(tmp)).first;
-        }
-        vals = &it->second;
-      } else {
-        eval_fn(fns, id, pts, d, tmp);
-        vals = &tmp;
-      }
-      for (size_t i = 0; i < wprod.size(); ++i) wprod[i] *= (*vals)[i];
-    }
-    // element matrices in parallel, then one ordered scatter: the assembled
-    // values do not depend on the thread count (bit-reproducible set-up)
-    std::vector<double> Kall((size_t)nc * d1 * d1, 0.0);
-#pragma omp parallel for schedule(static)
-    for (int e = 0; e < nc; ++e) {
-      if (!keep[e]) continue;
-      const double* v0 = &lv.cell_coords[(size_t)e * d1 * d];
-      double J[2][2] = {{0, 0}, {0, 0}}, Ji[2][2], det;
-      for (int k = 0; k < d; ++k)
-        for (int a = 0; a < d; ++a) J[k][a] = v0[(a + 1) * d + k] - v0[k];
-      if (d == 1) { det = J[0][0]; Ji[0][0] = 1.0 / det; }
-      else {
-        det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-        Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det;
-        Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
-      }
-      // physical gradients of the barycentric functions: grad lam_a = Ji^T gref_a
-      double grad[3][2];
-      for (int a = 0; a < d1; ++a)
-        for (int k = 0; k < d; ++k) {
-          double g = 0.0;
-          for (int m = 0; m < d; ++m) {
-            double gr = (a == 0) ? -1.0 : (m == a - 1 ? 1.0 : 0.0);
-            g += Ji[m][k] * gr;
-          }
-          grad[a][k] = g;
-        }
-      double Ke[3][3] = {{0}};
-      for (int q = 0; q < nq; ++q) {
-        double lam[3];
-        lam[0] = 1.0;
-        for (int a = 1; a < d1; ++a) { lam[a] = rp[q * d + a - 1]; lam[0] -= lam[a]; }
-        double wq = rw[q] * std::fabs(det) * wprod[(size_t)e * nq + q];
-        for (int i = 0; i < d1; ++i) {
-          double ti = f.test == 0 ? lam[i] : grad[i][f.test - 1];
-          for (int j = 0; j < d1; ++j) {
-            double tj = f.trial == 0 ? lam[j] : grad[j][f.trial - 1];
-            Ke[i][j] += wq * ti * tj;
-          }
-        }
-      }
-      for (int i = 0; i < d1; ++i)
-        for (int j = 0; j < d1; ++j) Kall[((size_t)e * d1 + i) * d1 + j] = Ke[i][j];
-    }
-    std::vector<int> own_pos;
-    std::vector<int>& pos = cache ? cache->pos : own_pos;
-    if (pos.size() != (size_t)nc * d1 * d1) {
-      pos.assign((size_t)nc * d1 * d1, 0);
-#pragma omp parallel for schedule(static)
-      for (int e = 0; e < nc; ++e) {
-        const int* cv = &lv.cells[(size_t)e * d1];
-        for (int i = 0; i < d1; ++i)
-          for (int j = 0; j < d1; ++j) pos[((size_t)e * d1 + i) * d1 + j] = find_pos(P, cv[i], cv[j]);
-      }
-    }
-    for (int e = 0; e < nc; ++e) {
-      if (!keep[e]) continue;
-      for (int i = 0; i < d1; ++i)
-        for (int j = 0; j < d1; ++j) A.val[pos[((size_t)e * d1 + i) * d1 + j]] += Kall[((size_t)e * d1 + i) * d1 + j];
-    }
-  } else {
+  {
     // boundary faces on one side
     std::vector<int> sel;
     const int nf = lv.nbfaces(d);
@@ -297,10 +332,16 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
     simplex_rule(dv - 1, rp, rw);
     const int nq = (int)rw.size();
     std::vector<char> keep(sel.size(), 1);
-    for (auto& rs : f.restrict_)
+    for (auto& rs : f.restrict_) {
       if (fns.cell_field(rs.first)) return {SGDG_EINVAL, "cell fields are not supported on boundary faces"};
-    for (int id : f.wfn)
+      if (rs.first < 0 || rs.first >= (int)fns.fn.size() || !fns.fn[rs.first])
+        return {SGDG_EINVAL, "boundary-face factor restricted by a missing coefficient function"};
+    }
+    for (int id : f.wfn) {
       if (fns.cell_field(id)) return {SGDG_EINVAL, "cell fields are not supported on boundary faces"};
+      if (id < 0 || id >= (int)fns.fn.size() || !fns.fn[id])
+        return {SGDG_EINVAL, "boundary-face factor needs a missing coefficient function"};
+    }
     if (!f.restrict_.empty() && !sel.empty()) {
       std::vector<double> cen(sel.size() * d, 0.0), val;
       for (size_t s = 0; s < sel.size(); ++s)
@@ -316,11 +357,18 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
     std::vector<double> meas(sel.size());
     for (size_t s = 0; s < sel.size(); ++s) {
       const double* f0 = &lv.bface_coords[(size_t)sel[s] * dv * d];
+      // |det| of the map from the reference face: 1 (a point), the edge
+      // length, or twice the triangle area |(f1 - f0) x (f2 - f0)|
       if (dv == 1) meas[s] = 1.0;
-      else {
+      else if (dv == 2) {
         double l2 = 0.0;
         for (int k = 0; k < d; ++k) l2 += (f0[d + k] - f0[k]) * (f0[d + k] - f0[k]);
         meas[s] = std::sqrt(l2);
+      } else {
+        double a[3], b[3];
+        for (int k = 0; k < 3; ++k) { a[k] = f0[3 + k] - f0[k]; b[k] = f0[6 + k] - f0[k]; }
+        const double cx = a[1] * b[2] - a[2] * b[1], cy = a[2] * b[0] - a[0] * b[2], cz = a[0] * b[1] - a[1] * b[0];
+        meas[s] = std::sqrt(cx * cx + cy * cy + cz * cz);
       }
       for (int q = 0; q < nq; ++q)
         for (int k = 0; k < d; ++k) {
@@ -339,7 +387,7 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
       if (!keep[s]) continue;
       const int* fv = &lv.bfaces[(size_t)sel[s] * dv];
       for (int q = 0; q < nq; ++q) {
-        double lam[2];
+        double lam[3];
         lam[0] = 1.0;
         for (int a = 1; a < dv; ++a) { lam[a] = rp[q * (dv - 1) + a - 1]; lam[0] -= lam[a]; }
         double wq = rw[q] * meas[s] * wprod[s * nq + q];
@@ -365,56 +413,48 @@ Status load_vectors_w(const Hierarchy& h, const std::vector<std::pair<sgdg_fn, v
   std::vector<double> rp, rw;
   simplex_rule(d, rp, rw);
   const int nq = (int)rw.size();
-  std::vector<double> pts((size_t)nc * nq * d), val((size_t)nc * nq, 1.0), tmp;
-  for (int e = 0; e < nc; ++e) {
-    const double* v0 = &lv.cell_coords[(size_t)e * d1 * d];
-    for (int q = 0; q < nq; ++q)
-      for (int k = 0; k < d; ++k) {
-        double x = v0[k];
-        for (int a = 1; a < d1; ++a) x += (v0[a * d + k] - v0[k]) * rp[q * d + (a - 1)];
-        pts[((size_t)e * nq + q) * d + k] = x;
-      }
-  }
-  for (const auto& f : fns) {
-    if (!f.first) continue;
-    SideFns t;
-    t.fn.push_back(f.first);
-    t.user.push_back(f.second);
-    eval_fn(t, 0, pts, d, tmp);
-    for (size_t i = 0; i < val.size(); ++i) val[i] *= tmp[i];
-  }
   out.assign(L + 1, {});
   out[L].assign(lv.n, 0.0);
-  for (int e = 0; e < nc; ++e) {
-    const double* v0 = &lv.cell_coords[(size_t)e * d1 * d];
-    double J[2][2] = {{0, 0}, {0, 0}}, Ji[2][2], det;
-    for (int k = 0; k < d; ++k)
-      for (int a = 0; a < d; ++a) J[k][a] = v0[(a + 1) * d + k] - v0[k];
-    if (d == 1) { det = J[0][0]; Ji[0][0] = 1.0 / det; }
-    else {
-      det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-      Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det;
-      Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
-    }
-    // physical gradient component of the barycentric functions (constant per cell)
-    double grad[3] = {0.0, 0.0, 0.0};
-    if (deriv > 0)
-      for (int a = 0; a < d1; ++a) {
-        double g = 0.0;
-        for (int m = 0; m < d; ++m) {
-          const double gr = (a == 0) ? -1.0 : (m == a - 1 ? 1.0 : 0.0);
-          g += Ji[m][deriv - 1] * gr;
+  // cells in chunks (points, function values), accumulated in cell order
+  std::vector<double> pts, val, tmp;
+  for (int e0 = 0; e0 < nc; e0 += kCellChunk) {
+    const int ne = std::min(kCellChunk, nc - e0);
+    pts.assign((size_t)ne * nq * d, 0.0);
+    val.assign((size_t)ne * nq, 1.0);
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < ne; ++c) {
+      const double* v0 = &lv.cell_coords[((size_t)e0 + c) * d1 * d];
+      for (int q = 0; q < nq; ++q)
+        for (int k = 0; k < d; ++k) {
+          double x = v0[k];
+          for (int a = 1; a < d1; ++a) x += (v0[a * d + k] - v0[k]) * rp[q * d + (a - 1)];
+          pts[((size_t)c * nq + q) * d + k] = x;
         }
-        grad[a] = g;
+    }
+    for (const auto& f : fns) {
+      if (!f.first) continue;
+      SideFns t;
+      t.fn.push_back(f.first);
+      t.user.push_back(f.second);
+      eval_fn(t, 0, pts, d, tmp);
+      for (size_t i = 0; i < val.size(); ++i) val[i] *= tmp[i];
+    }
+    for (int c = 0; c < ne; ++c) {
+      const size_t e = (size_t)e0 + c;
+      const double* v0 = &lv.cell_coords[e * d1 * d];
+      double Ji[3][3], det, grad[4][3];
+      simplex_jacobian(d, v0, Ji, det);
+      // physical gradient component of the barycentric functions (constant per cell)
+      if (deriv > 0) barycentric_gradients(d, Ji, grad);
+      det = std::fabs(det);
+      for (int q = 0; q < nq; ++q) {
+        double lam[4];
+        lam[0] = 1.0;
+        for (int a = 1; a < d1; ++a) { lam[a] = rp[q * d + a - 1]; lam[0] -= lam[a]; }
+        const double wq = rw[q] * det * val[(size_t)c * nq + q];
+        for (int a = 0; a < d1; ++a)
+          out[L][lv.cells[e * d1 + a]] += wq * (deriv > 0 ? grad[a][deriv - 1] : lam[a]);
       }
-    det = std::fabs(det);
-    for (int q = 0; q < nq; ++q) {
-      double lam[3];
-      lam[0] = 1.0;
-      for (int a = 1; a < d1; ++a) { lam[a] = rp[q * d + a - 1]; lam[0] -= lam[a]; }
-      const double wq = rw[q] * det * val[(size_t)e * nq + q];
-      for (int a = 0; a < d1; ++a)
-        out[L][lv.cells[(size_t)e * d1 + a]] += wq * (deriv > 0 ? grad[a] : lam[a]);
     }
   }
   for (int l = L - 1; l >= 0; --l) {

@@ -264,7 +264,7 @@ sgdg_status fail(Handle* h, const Status& st) {
 
 Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   if (cfg.mesh_x.dim != cfg.mesh_v.dim) return {SGDG_EINVAL, "mesh_x and mesh_v must have the same dimension"};
-  if (cfg.mesh_x.dim < 1 || cfg.mesh_x.dim > 2) return {SGDG_EINVAL, "dimension must be 1 or 2"};
+  if (cfg.mesh_x.dim < 1 || cfg.mesh_x.dim > kMaxDim) return {SGDG_EINVAL, "dimension must be 1, 2 or 3"};
   if (cfg.level_L < 0 || cfg.level_L >= kMaxLevels) return {SGDG_EINVAL, "level_L out of range 0..11"};
   if (2 * cfg.level_L + 2 > kMaxGrids) return {SGDG_EINVAL, "too many grids"};
   if (cfg.time_degree != 1) return {SGDG_EINVAL, "only time_degree 1 is supported"};
@@ -297,9 +297,9 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
     SG_ST(sv);
   }
   SG_ST(build_terms(c, h.d, cfg.mesh_x, cfg.mesh_v, cfg.dt, cfg.delta, h.tt));
-  // callback tables: ids 0..3 beta components, 4 sigma
+  // callback tables: ids 0 .. 2 kMaxDim - 1 beta components, then sigma
   SideFns fx, fv;
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < 2 * kMaxDim; ++p) {
     fx.fn.push_back(p < 2 * h.d ? c.beta[p].fx : nullptr); fx.user.push_back(c.beta[p].ux);
     fv.fn.push_back(p < 2 * h.d ? c.beta[p].fv : nullptr); fv.user.push_back(c.beta[p].uv);
   }
@@ -323,7 +323,7 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
     kv[p - 1] = find_or_add(h.tt.vf);
   }
   mass.test = mass.trial = 0;
-  // the sweep kernels keep one matrix row of at most 8 entries (prolongation:
+  // the sweep kernels keep one matrix row of at most 16 entries (prolongation:
   // kProlongRow) in registers
   int side_maxrow[2] = {0, 0};
   for (int side = 0; side < 2; ++side) {
@@ -335,7 +335,7 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
     };
     for (const MeshLevel& lv : hi->lev) side_maxrow[side] = std::max(side_maxrow[side], maxrow(lv.pattern));
     for (const Csr& R : hi->Rt) side_maxrow[side] = std::max(side_maxrow[side], maxrow(R));
-    if (side_maxrow[side] > 8) return {SGDG_EINVAL, "P1 pattern or restriction rows longer than 8 entries"};
+    if (side_maxrow[side] > 16) return {SGDG_EINVAL, "P1 pattern or restriction rows longer than 16 entries"};
     for (const Csr& E : hi->E)
       if (maxrow(E) > kProlongRow) return {SGDG_EINVAL, "prolongation rows with more than 2 entries"};
   }
@@ -343,16 +343,16 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   h.V.maxrow = side_maxrow[1];
   SG_ST(upload_side(h, hx, h.X));
   SG_ST(upload_side(h, hv, h.V));
-  // the sweep uses R X (branch B's chain steps) and V E (branch B's final)
-  SG_ST(setup_products(h, hx, h.X, true, false));
+  // the sweep uses R X (branch B's chain steps) and V E (branch B's final).
+  // On 3D Kuhn lattices R X has rows of 65 entries: branch B then applies X
+  // and R one after the other (apply.cu)
+  SG_ST(setup_products(h, hx, h.X, h.d < 3, false));
   SG_ST(setup_products(h, hv, h.V, false, true));
   for (int side = 0; side < 2; ++side) {
     SideDev& sd = side == 0 ? h.X : h.V;
     const Hierarchy& hi = side == 0 ? hx : hv;
     const std::vector<FactorSpec>& fs = side == 0 ? h.tt.xf : h.tt.vf;
     const SideFns& fns = side == 0 ? fx : fv;
-    sd.v64.fac.assign(fs.size(), std::vector<double*>(h.L + 1, nullptr));
-    sd.v32.fac.assign(fs.size(), std::vector<float*>(h.L + 1, nullptr));
     sd.v64.ell_fac.assign(fs.size(), std::vector<double*>(h.L + 1, nullptr));
     sd.v32.ell_fac.assign(fs.size(), std::vector<float*>(h.L + 1, nullptr));
     sd.v64.ell_RF.assign(fs.size(), std::vector<double*>(h.L + 1, nullptr));
@@ -362,32 +362,35 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
     for (size_t f = 0; f < fs.size(); ++f)
       for (int id : fs[f].wfn)
         if (!fns.fn[id]) return {SGDG_EINVAL, "factor references a missing coefficient function"};
-    // FP64 assembly of every factor of the side on the host: the coefficient
-    // callbacks run first, serially (quadrature points and centroids of the
-    // volume factors, cached; the boundary-face factors); then the volume
-    // factors and all products with the transfers are formed concurrently,
-    // one factor per thread - each factor's values do not depend on the
-    // thread count
-    QuadCache qc;
-    SG_ST(prefill_cache(hi, fns, fs, qc));
+    // FP64 assembly of every factor of the side on the host: the boundary-face
+    // factors one by one, the volume factors together in one pass over the
+    // finest cells (each coefficient callback once per quadrature point),
+    // then all products with the transfers concurrently, one factor per
+    // thread - the values do not depend on the thread count
     const int nf = (int)fs.size();
     std::vector<std::vector<Csr>> Xs(nf);
     std::vector<FactorProducts> Ps(nf);
     std::vector<Status> sts(nf);
-    for (int f = 0; f < nf; ++f)
-      if (fs[f].kind != 0) sts[f] = assemble_factor(hi, fns, fs[f], Xs[f], &qc);
-#pragma omp parallel for schedule(dynamic, 1)
+    std::vector<FactorSpec> vspec;
+    std::vector<int> vidx;
     for (int f = 0; f < nf; ++f) {
-      if (fs[f].kind == 0) sts[f] = assemble_factor(hi, fns, fs[f], Xs[f], &qc);
-      if (!sts[f].code) factor_products(hi, sd, Xs[f], Ps[f]);
+      if (fs[f].kind != 0) sts[f] = assemble_factor(hi, fns, fs[f], Xs[f]);
+      else { vspec.push_back(fs[f]); vidx.push_back(f); }
     }
+    {
+      std::vector<std::vector<Csr>> Xv;
+      SG_ST(assemble_volume(hi, fns, vspec, Xv));
+      for (size_t k = 0; k < vidx.size(); ++k) Xs[vidx[k]] = std::move(Xv[k]);
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int f = 0; f < nf; ++f)
+      if (!sts[f].code) factor_products(hi, sd, Xs[f], Ps[f]);
     for (int f = 0; f < nf; ++f) SG_ST(sts[f]);
     for (size_t f = 0; f < fs.size(); ++f) {
       std::vector<Csr>& X = Xs[f];
       fnv(h.problem_hash, X[h.L].val.data(), sizeof(double) * X[h.L].val.size());
       fnv(h.problem_hash, X[h.L].col.data(), sizeof(int) * X[h.L].col.size());
       for (int l = 0; l <= h.L; ++l) {
-        SG_ST(upload_vals(h, X[l].val, &sd.v64.fac[f][l], &sd.v32.fac[f][l]));
         SG_ST(upload_ell_vals(h, hi.lev[l].pattern.rowptr, X[l].val, sd.ell_w(), &sd.v64.ell_fac[f][l],
                               &sd.v32.ell_fac[f][l]));
       }
@@ -533,13 +536,14 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
       const sgdg_source& g = c.g[k];
       const int src = (int)h.src_t.size();
       h.src_t.push_back({g.ft, g.ut});
-      SideFns gx = fx, gv = fv;   // id 5: the g factors
+      SideFns gx = fx, gv = fv;   // id gid (after sigma): the g factors
+      const int gid = (int)gx.fn.size();
       gx.fn.push_back(g.fx); gx.user.push_back(g.ux);
       gv.fn.push_back(g.fv); gv.user.push_back(g.uv);
       for (const InflowPart& ip : parts) {
         FactorSpec X = ip.x, V = ip.v;
-        if (g.fx) { X.wfn.push_back(5); std::sort(X.wfn.begin(), X.wfn.end()); }
-        if (g.fv) { V.wfn.push_back(5); std::sort(V.wfn.begin(), V.wfn.end()); }
+        if (g.fx) { X.wfn.push_back(gid); std::sort(X.wfn.begin(), X.wfn.end()); }
+        if (g.fv) { V.wfn.push_back(gid); std::sort(V.wfn.begin(), V.wfn.end()); }
         std::vector<Csr> AX, AV;
         SG_ST(assemble_factor(hx, gx, X, AX));
         SG_ST(assemble_factor(hv, gv, V, AV));

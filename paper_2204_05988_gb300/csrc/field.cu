@@ -251,10 +251,6 @@ Status field_reassemble(Handle& h) {
     st = assemble_factor(F.hx, F.fx, fs, X);
     if (st.code) return st;
     for (int l = 0; l <= L; ++l) {
-      SG_CU(cudaMemcpy(h.X.v64.fac[f][l], X[l].val.data(), sizeof(double) * X[l].val.size(),
-                       cudaMemcpyHostToDevice));
-      std::vector<float> v32(X[l].val.begin(), X[l].val.end());
-      SG_CU(cudaMemcpy(h.X.v32.fac[f][l], v32.data(), sizeof(float) * v32.size(), cudaMemcpyHostToDevice));
       st = upload_ell_vals(h, F.hx.lev[l].pattern.rowptr, X[l].val, h.X.ell_w(), &h.X.v64.ell_fac[f][l],
                            &h.X.v32.ell_fac[f][l]);
       if (st.code) return st;

@@ -12,7 +12,6 @@ namespace sgdg {
 // Device copies of one side's (Omega_x or Omega_v) level data.
 template <typename T>
 struct SideValues {
-  std::vector<std::vector<T*>> fac;   // [factor][level] values on the level pattern
   std::vector<T*> E, R;               // E[l]: level l -> l+1 values;  R[l] = E[l]^T values
   std::vector<T*> dinv;               // inverse diagonal of the mass matrix per level
   // ELL copies read by the sweep kernels: row r's entries at [r w, r w + len),
@@ -34,10 +33,11 @@ struct SideDev {
   std::vector<int*> inj;                          // level l vertex -> index on level l+1
   int mass = -1;                                  // factor id of the plain mass matrix
   int maxrow = 8;                                 // longest pattern or restriction row
-  // row length the sweep kernels keep in registers (3, 4, 7 or 8) and the ELL
-  // width of the patterns and restrictions (4 or 8, 16-byte rows for vector loads)
-  int row_regs() const { return maxrow <= 3 ? 3 : maxrow <= 4 ? 4 : maxrow <= 7 ? 7 : 8; }
-  int ell_w() const { return maxrow <= 4 ? 4 : 8; }
+  // row length the sweep kernels keep in registers (3, 4, 7, 8 or 16: P1
+  // rows of 3 in 1D, 7 in 2D, 15 on 3D Kuhn lattices) and the ELL width of
+  // the patterns and restrictions (4, 8 or 16, 16-byte rows for vector loads)
+  int row_regs() const { return maxrow <= 3 ? 3 : maxrow <= 4 ? 4 : maxrow <= 7 ? 7 : maxrow <= 8 ? 8 : 16; }
+  int ell_w() const { return maxrow <= 4 ? 4 : maxrow <= 8 ? 8 : 16; }
   std::vector<int*> ell_col, R_ell_col, E_ell_col;   // ELL column indices (padding repeats the first column)
   // patterns of the factor-transfer products (shared by all factors of the side)
   std::vector<int*> RF_ell_col, FP_ell_col;          // [l] as SideValues::ell_RF / ell_FP

@@ -12,6 +12,9 @@ namespace sgdg {
 
 constexpr int kMaxLevels = 12;   // 0..11
 constexpr int kR = 2;            // time-DG degree 1: two Legendre coefficients
+constexpr int kMaxDim = 3;       // d = 1, 2, 3 (phase space of dimension 2d)
+// coefficient function ids of a side: beta components 0 .. 2 kMaxDim - 1, then sigma
+constexpr int kSigmaFn = 2 * kMaxDim;
 
 struct Status {
   sgdg_status code = SGDG_OK;
@@ -79,28 +82,17 @@ struct FactorSpec {
   bool operator==(const FactorSpec& o) const;
 };
 
-// Quadrature data shared by the volume factors of one hierarchy and one
-// function table: the finest level's quadrature points, the coefficient
-// functions evaluated there (per function id) and the CSR position of every
-// element-matrix entry.  Filled on first use; valid only for the hierarchy
-// and table it was first used with.
-struct QuadCache {
-  std::vector<double> pts;
-  std::map<int, std::vector<double>> fn_vals;
-  std::map<int, std::vector<double>> cen_vals;   // functions at the finest cell centroids
-  std::vector<int> pos;
-};
-
-// Fills `cache` with everything the volume factors in `specs` read through it
-// (quadrature points, element scatter positions, every coefficient function
-// at the quadrature points and at the cell centroids), so that later
-// assemble_factor calls with this cache only read it (and may run
-// concurrently) and call no coefficient callback for volume factors.
-Status prefill_cache(const Hierarchy& h, const SideFns& fns, const std::vector<FactorSpec>& specs, QuadCache& cache);
+// Volume factors (kind 0) of one hierarchy assembled together on the finest
+// level and projected to every coarser level: one pass over the cells in
+// chunks evaluates each coefficient function once per quadrature point and
+// forms every factor's element matrices, scattered in cell order (values
+// independent of the chunking and the thread count).  X[f][l] on
+// lev[l].pattern.
+Status assemble_volume(const Hierarchy& h, const SideFns& fns, const std::vector<FactorSpec>& specs,
+                       std::vector<std::vector<Csr>>& X);
 
 Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec& f,
-                       std::vector<Csr>& per_level,    // per_level[l] on lev[l].pattern
-                       QuadCache* cache = nullptr);
+                       std::vector<Csr>& per_level);   // per_level[l] on lev[l].pattern
 
 struct Term {
   double tau[kR][kR];  // time coupling [s][s']

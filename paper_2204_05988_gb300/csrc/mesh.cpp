@@ -2,10 +2,14 @@
 // (Sect. 2: V_1 subset V_2 subset ... by uniform refinement; Sect. 4.2: the
 // embedding E of a coarse level into the next finer one).
 //
-// Refinement: 1D bisection, 2D red refinement through the edge midpoints.
-// Vertex order on every level: lexicographic by coordinates, last axis
-// slowest.  Periodic axes identify the upper-bound vertex with the
-// lower-bound one.  E_{l+1<-l} evaluates a level-l P1 function at the level
+// Refinement: 1D bisection, 2D red refinement through the edge midpoints,
+// 3D regular refinement after Bey (eight children: four corner tetrahedra and
+// the inner octahedron split along the diagonal between the midpoints of
+// edges 02 and 13; a Kuhn tetrahedron with its vertices in lattice-path order
+// gives the Kuhn tetrahedra of the halved lattice, so a Kuhn coarse mesh stays
+// a Kuhn lattice on every level).  Vertex order on every level:
+// lexicographic by coordinates, last axis slowest.  Periodic axes identify
+// the upper-bound vertex with the lower-bound one.  E_{l+1<-l} evaluates a level-l P1 function at the level
 // l+1 vertices: 1 at a kept vertex, 1/2 + 1/2 at an edge midpoint.
 #include <algorithm>
 #include <array>
@@ -50,18 +54,26 @@ RawMesh refine(const RawMesh& c) {
     return id;
   };
   const int d1 = c.d + 1;
-  f.cells.reserve((size_t)c.nc() * d1 * (c.d == 1 ? 2 : 4));
+  f.cells.reserve((size_t)c.nc() * d1 * (c.d == 1 ? 2 : c.d == 2 ? 4 : 8));
   for (int e = 0; e < c.nc(); ++e) {
     const int* v = &c.cells[(size_t)e * d1];
     if (c.d == 1) {
       int m = midpoint(v[0], v[1]);
       int ch[4] = {v[0], m, m, v[1]};
       f.cells.insert(f.cells.end(), ch, ch + 4);
-    } else {
+    } else if (c.d == 2) {
       int a = v[0], b = v[1], cc = v[2];
       int mab = midpoint(a, b), mbc = midpoint(b, cc), mca = midpoint(cc, a);
       int ch[12] = {a, mab, mca, mab, b, mbc, mca, mbc, cc, mab, mbc, mca};
       f.cells.insert(f.cells.end(), ch, ch + 12);
+    } else {
+      // children in Bey's order, vertices of each child in its own path order
+      const int x0 = v[0], x1 = v[1], x2 = v[2], x3 = v[3];
+      const int m01 = midpoint(x0, x1), m02 = midpoint(x0, x2), m03 = midpoint(x0, x3);
+      const int m12 = midpoint(x1, x2), m13 = midpoint(x1, x3), m23 = midpoint(x2, x3);
+      const int ch[32] = {x0,  m01, m02, m03,  m01, x1,  m12, m13,  m02, m12, x2,  m23,  m03, m13, m23, x3,
+                          m01, m02, m03, m13,  m01, m02, m12, m13,  m02, m03, m13, m23,  m02, m12, m13, m23};
+      f.cells.insert(f.cells.end(), ch, ch + 32);
     }
   }
   return f;
@@ -117,40 +129,57 @@ void canonical(const RawMesh& r, const sgdg_mesh& m, MeshLevel& lv, std::vector<
       lv.cells[(size_t)e * d1 + a] = raw2can[rv];
       for (int k = 0; k < d; ++k) lv.cell_coords[((size_t)e * d1 + a) * d + k] = r.coords[(size_t)rv * d + k];
     }
-  // boundary faces: faces of exactly one cell, not on a periodic side
-  // faces have d <= 2 vertices: pack the sorted ids into one 64-bit key
-  std::unordered_map<uint64_t, int> count;
-  count.reserve((size_t)nc * d1);
-  auto face_key = [&](int e, int drop) {
-    int f[2] = {0, 0}, k = 0;
-    for (int a = 0; a < d1; ++a)
-      if (a != drop) f[k++] = r.cells[(size_t)e * d1 + a];
-    if (k == 2 && f[0] > f[1]) std::swap(f[0], f[1]);
-    return k == 1 ? (uint64_t)(uint32_t)f[0] : (((uint64_t)(uint32_t)f[0] << 32) | (uint32_t)f[1]);
-  };
-  for (int e = 0; e < nc; ++e)
-    for (int drop = 0; drop < d1; ++drop) count[face_key(e, drop)]++;
-  std::vector<uint64_t> once;
-  for (auto& kv : count)
-    if (kv.second == 1) once.push_back(kv.first);
-  std::sort(once.begin(), once.end());
-  for (uint64_t key : once) {
-    std::vector<int> f;
-    if (d == 1) f = {(int)key};
-    else f = {(int)(key >> 32), (int)(key & 0xffffffffu)};
+  // boundary faces, not on a periodic side.  d <= 2: faces of exactly one
+  // cell (sorted vertex ids packed into one 64-bit key).  d = 3: the faces
+  // whose vertices all lie on one side of the box - on a box domain exactly
+  // the faces of one cell, found without a face table (a Kuhn mesh at level 7
+  // has 5 10^7 cell faces)
+  auto add_face = [&](const int* f) {
     for (int ax = 0; ax < d; ++ax)
       for (int side = -1; side <= 1; side += 2) {
         double bound = side < 0 ? m.lo[ax] : m.hi[ax];
         bool on = true;
-        for (int v : f) on = on && (r.coords[(size_t)v * d + ax] == bound);
+        for (int a = 0; a < d; ++a) on = on && (r.coords[(size_t)f[a] * d + ax] == bound);
         if (!on || (m.periodic && m.periodic[ax])) continue;
-        for (int v : f) {
-          lv.bfaces.push_back(raw2can[v]);
-          for (int k = 0; k < d; ++k) lv.bface_coords.push_back(r.coords[(size_t)v * d + k]);
+        for (int a = 0; a < d; ++a) {
+          lv.bfaces.push_back(raw2can[f[a]]);
+          for (int k = 0; k < d; ++k) lv.bface_coords.push_back(r.coords[(size_t)f[a] * d + k]);
         }
         lv.bface_axis.push_back(ax);
         lv.bface_side.push_back(side);
       }
+  };
+  if (d == 3) {
+    for (int e = 0; e < nc; ++e)
+      for (int drop = 0; drop < d1; ++drop) {
+        int f[3], k = 0;
+        for (int a = 0; a < d1; ++a)
+          if (a != drop) f[k++] = r.cells[(size_t)e * d1 + a];
+        std::sort(f, f + 3);
+        add_face(f);
+      }
+  } else {
+    std::unordered_map<uint64_t, int> count;
+    count.reserve((size_t)nc * d1);
+    auto face_key = [&](int e, int drop) {
+      int f[2] = {0, 0}, k = 0;
+      for (int a = 0; a < d1; ++a)
+        if (a != drop) f[k++] = r.cells[(size_t)e * d1 + a];
+      if (k == 2 && f[0] > f[1]) std::swap(f[0], f[1]);
+      return k == 1 ? (uint64_t)(uint32_t)f[0] : (((uint64_t)(uint32_t)f[0] << 32) | (uint32_t)f[1]);
+    };
+    for (int e = 0; e < nc; ++e)
+      for (int drop = 0; drop < d1; ++drop) count[face_key(e, drop)]++;
+    std::vector<uint64_t> once;
+    for (auto& kv : count)
+      if (kv.second == 1) once.push_back(kv.first);
+    std::sort(once.begin(), once.end());
+    for (uint64_t key : once) {
+      int f[2];
+      if (d == 1) f[0] = (int)key;
+      else { f[0] = (int)(key >> 32); f[1] = (int)(key & 0xffffffffu); }
+      add_face(f);
+    }
   }
   // P1 adjacency pattern
   std::vector<std::vector<int>> adj(lv.n);
@@ -192,7 +221,7 @@ Csr transpose(const Csr& A) {
 
 Status build_hierarchy(const sgdg_mesh& m, int L, Hierarchy& h) {
   Status st;
-  if (m.dim < 1 || m.dim > 2) return {SGDG_EINVAL, "mesh dim must be 1 or 2"};
+  if (m.dim < 1 || m.dim > 3) return {SGDG_EINVAL, "mesh dim must be 1, 2 or 3"};
   if (m.n_vertices <= 0 || m.n_cells <= 0 || !m.coords || !m.cells || !m.lo || !m.hi)
     return {SGDG_EINVAL, "empty or incomplete mesh"};
   h.d = m.dim;

@@ -490,7 +490,7 @@ Status precond_group(Handle& h, const Active& act, const std::vector<const T*>& 
   SG_CU(cudaGetLastError());
   // Chebyshev-Jacobi along dim 1 (f = cx -> x = t1), then along dim 2 (f = t1 -> x = out)
   const int K = std::max(1, h.cfg.cheb_steps);
-  const double a = 0.5, b = (h.d == 1) ? 1.5 : 2.0;
+  const double a = 0.5, b = (h.d == 1) ? 1.5 : (h.d == 2 ? 2.0 : 2.5);
   const double theta = 0.5 * (a + b), del = 0.5 * (b - a), sigma1 = theta / del;
   for (int dim = 1; dim <= 2; ++dim) {
     GVec<T> c;
@@ -534,10 +534,12 @@ Status precond_group(Handle& h, const Active& act, const std::vector<const T*>& 
       const dim3 gg = ggrid(c.n, ng);
       if (dim == 1) {
         if (W == 4) k_gcheb_fused<T, false, 4><<<gg, kThreads, 0, s>>>(fz, rhon * rho, 2.0 * rhon / del);
-        else k_gcheb_fused<T, false, 8><<<gg, kThreads, 0, s>>>(fz, rhon * rho, 2.0 * rhon / del);
+        else if (W == 8) k_gcheb_fused<T, false, 8><<<gg, kThreads, 0, s>>>(fz, rhon * rho, 2.0 * rhon / del);
+        else k_gcheb_fused<T, false, 16><<<gg, kThreads, 0, s>>>(fz, rhon * rho, 2.0 * rhon / del);
       } else {
         if (W == 4) k_gcheb_fused<T, true, 4><<<gg, kThreads, 0, s>>>(fz, rhon * rho, 2.0 * rhon / del);
-        else k_gcheb_fused<T, true, 8><<<gg, kThreads, 0, s>>>(fz, rhon * rho, 2.0 * rhon / del);
+        else if (W == 8) k_gcheb_fused<T, true, 8><<<gg, kThreads, 0, s>>>(fz, rhon * rho, 2.0 * rhon / del);
+        else k_gcheb_fused<T, true, 16><<<gg, kThreads, 0, s>>>(fz, rhon * rho, 2.0 * rhon / del);
       }
       SG_CU(cudaGetLastError());
       for (int q = 0; q < ng; ++q) {

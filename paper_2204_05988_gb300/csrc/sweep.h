@@ -52,7 +52,7 @@ inline int row_class(int r) {
   if (r <= 24) return 24;
   return -1;
 }
-constexpr int kMaxRestrictRow = 8;   // restriction rows (P1 nested meshes)
+constexpr int kMaxRestrictRow = 16;  // restriction rows (P1 nested meshes: 15 on 3D Kuhn lattices)
 constexpr int kMaxFinalRow = 16;     // factor and factor-prolongation rows
 constexpr int kMaxChainRow = 24;     // restriction-factor product rows
 

@@ -69,8 +69,8 @@ Status build_terms(const sgdg_coeffs& c, int d, const sgdg_mesh& mx, const sgdg_
   const double Tt[2][2] = {{0.0, 2.0}, {0.0, 0.0}};
   const double Ct[2][2] = {{0.0, 0.0}, {0.0, 4.0 / dt}};
   const double Gt[2][2] = {{1.0, -1.0}, {-1.0, 1.0}};
-  // function ids: beta components 0..2d-1, sigma factor 4
-  const int SIG = 4;
+  // function ids: beta components 0..2d-1, sigma kSigmaFn
+  const int SIG = kSigmaFn;
   auto has_x = [&](int p) { return (p == SIG ? c.sigma.fx : c.beta[p].fx) != nullptr; };
   auto has_v = [&](int p) { return (p == SIG ? c.sigma.fv : c.beta[p].fv) != nullptr; };
   auto Dx = [&](int p) { return p < d ? p + 1 : 0; };

@@ -143,3 +143,36 @@ def test_table1_dof_d3():
     G = op.dense(op.mass_terms())
     ev = np.linalg.eigvalsh(0.5 * (G + G.T))
     assert int(np.sum(ev > 1e-10 * ev.max())) == rows[0][1] == 4096
+
+
+def kuhn_hat_integrals(l: int, edge: float) -> np.ndarray:
+    """int phi_k over the level-l Kuhn lattice of a cube of edge `edge` (the
+    6-tetrahedron coarse mesh refined l times) for every vertex k in
+    lexicographic order, last axis slowest.  Each of the cubes of side
+    h = edge / 2^l holds 6 tetrahedra of volume h^3 / 6 around its main
+    diagonal: its two diagonal corners touch all 6, the other corners 2; a
+    hat function integrates to a quarter of the volume of every tetrahedron
+    it lives on, so int phi_k = h^3 n_k / 24 with n_k the tetrahedra around k."""
+    m = 2 ** l
+    h = edge / m
+    i = np.arange(m + 1)
+    K, J, I = np.meshgrid(i, i, i, indexing="ij")
+    n = np.zeros(K.shape)
+    for o in [(a, b, c) for a in (0, 1) for b in (0, 1) for c in (0, 1)]:
+        ci, cj, ck = I - o[0], J - o[1], K - o[2]
+        ok = (ci >= 0) & (ci < m) & (cj >= 0) & (cj < m) & (ck >= 0) & (ck < m)
+        n += ok * (6 if o in ((0, 0, 0), (1, 1, 1)) else 2)
+    return (h ** 3 * n / 24.0).ravel()
+
+
+def test_kuhn_hat_integrals():
+    """The closed form above against the oracle's projected mass rows (every
+    level of an L = 3 hierarchy, both boxes of the d = 3 workload); the GPU
+    tests use it at L = 7, where the oracle cannot assemble."""
+    for lo, hi in ((0.0, 1.0), (-1.0, 1.0)):
+        H = Hierarchy(W.cube_mesh(lo, hi, 1), 3)
+        M = assemble_level(H.levels[3], Factor("vol"))
+        for l in range(4):
+            E = H.embed(3, l)
+            ref = np.asarray((E.T @ M @ E).sum(axis=1)).ravel()
+            assert np.allclose(kuhn_hat_integrals(l, hi - lo), ref, rtol=1e-13, atol=0), l
