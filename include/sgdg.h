@@ -142,6 +142,24 @@ typedef struct {
   const sgdg_source* f;
   int n_g;
   const sgdg_source* g;
+  /* Time factors (Sect. 4.2 lets beta and sigma depend on t inside the
+   * tensor form): beta_p(t, x, v) = beta[p].coef * beta_t[p](t) * fx(x) *
+   * fv(v), sigma likewise with sigma_t; a NULL factor is the constant 1.
+   * With any time factor the strip operator is the quadrature sum of
+   * Sect. 4.2 over time_quad Gauss-Legendre points per strip (0: 3 points;
+   * at most 8): the Kronecker factors stay as assembled at create, the 2 x 2
+   * time couplings are recomputed per strip (time callbacks on the host),
+   * and the inflow part of each beta component follows the sign of its time
+   * factor at every point.  Applies (operator, diagonal blocks, batch) use
+   * the operator of the strip that starts at the handle's current time: 0
+   * after sgdg_create and sgdg_set_initial, advanced by dt with every
+   * sgdg_advance_strip, restored by sgdg_restore.  Time factors are not
+   * combined with sources, inflow data or vlasov_poisson (EINVAL). */
+  sgdg_tfn beta_t[6];
+  void* beta_ut[6];
+  sgdg_tfn sigma_t;
+  void* sigma_ut;
+  int time_quad;
 } sgdg_coeffs;
 
 typedef struct {
@@ -178,6 +196,7 @@ typedef struct {
   double device_bytes;         /* device memory held by the handle */
   long long nnz_x, nnz_v;      /* P1 pattern entries summed over the levels of each side */
   long long rows_x, rows_v;    /* pattern rows (vertices) summed over the levels of each side */
+  int lattice_x_levels;        /* x levels held as 2-D structured lattices (slot-ordered rows) */
 } sgdg_info;
 
 typedef struct {
@@ -340,10 +359,14 @@ sgdg_status sgdg_get_density_potential(const void* h, double* rho, double* phi);
  * the full grid (lx, lv): u is a strip vector (R = 2) or a spatial vector
  * (R = 1); out [n_x(lx)][n_v(lv)][R] on the device.  Finer component grids are
  * injected, coarser ones prolonged (unique, unlike the coefficients).
+ * sgdg_coarse_diff: out = the same view of a - b (both strip vectors for
+ * R = 2, spatial for R = 1); the warm start's features and targets.
  * sgdg_add_coarse: adds the P1 function c ([n_x(lx)][n_v(lv)][2], device) to
  * the strip vector u, represented on component grid (lx, L-lx) by
  * prolongation in v; needs lv <= L - lx. */
 sgdg_status sgdg_coarse_values(void* h, const double* u, int R, int lx, int lv, double* out, void* stream);
+sgdg_status sgdg_coarse_diff(void* h, const double* a, const double* b, int R, int lx, int lv, double* out,
+                             void* stream);
 sgdg_status sgdg_add_coarse(void* h, const double* c, int lx, int lv, double* u, void* stream);
 
 /* A 3-layer MLP y = W3^T relu(W2^T relu(W1^T x + b1) + b2) + b3 trained and
@@ -381,7 +404,11 @@ sgdg_status sgdg_autotune(void* h, const void* u, void* y, int precision, void* 
  *   bound by L1/shared-memory throughput and latency, and the tiles cost
  *   occupancy, barriers and halo recomputation);
  * 1 (default): the unfused kernels (S_b written per grid, then final update
- *   and restriction).  Other values: SGDG_EINVAL. */
+ *   and restriction); on x levels that are 2-D structured lattices (cells
+ *   cut along the (1, 1) diagonal) the final update along dim 1 runs a
+ *   kernel that slides a register window along the lattice rows;
+ * 2: the unfused kernels with the generic final update everywhere (the
+ *   same sums; for measurement).  Other values: SGDG_EINVAL. */
 sgdg_status sgdg_set_sweep_variant(void* h, int variant);
 /* The fused branch-A plan of grid l for S pairs of pair_bytes bytes in shared
  * memory (FP32 and BF16 storage: 8; FP64: 16), built if needed (measurement; no counterpart in the paper): iout[0..3] = tiles,

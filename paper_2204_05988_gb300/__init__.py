@@ -49,7 +49,9 @@ class Source(C.Structure):
 
 class Coeffs(C.Structure):
     _fields_ = [("beta", Product * 6), ("sigma", Product), ("n_u0", C.c_int), ("u0", C.POINTER(Product)),
-                ("n_f", C.c_int), ("f", C.POINTER(Source)), ("n_g", C.c_int), ("g", C.POINTER(Source))]
+                ("n_f", C.c_int), ("f", C.POINTER(Source)), ("n_g", C.c_int), ("g", C.POINTER(Source)),
+                ("beta_t", TFN * 6), ("beta_ut", C.c_void_p * 6), ("sigma_t", TFN), ("sigma_ut", C.c_void_p),
+                ("time_quad", C.c_int)]
 
 
 class Config(C.Structure):
@@ -65,7 +67,7 @@ class Info(C.Structure):
                 ("n_spatial", C.c_longlong), ("n_coeffs", C.c_longlong), ("n_terms", C.c_int),
                 ("n_x_factors", C.c_int), ("n_v_factors", C.c_int), ("device_bytes", C.c_double),
                 ("nnz_x", C.c_longlong), ("nnz_v", C.c_longlong), ("rows_x", C.c_longlong),
-                ("rows_v", C.c_longlong)]
+                ("rows_v", C.c_longlong), ("lattice_x_levels", C.c_int)]
 
 
 class StripStats(C.Structure):
@@ -109,6 +111,8 @@ EXPORTS = {
     "sgdg_finest_x": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "sgdg_get_density_potential": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_coarse_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "sgdg_coarse_diff": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                   C.c_void_p]),
     "sgdg_add_coarse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "sgdg_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_ulonglong, C.POINTER(C.c_void_p)]),
     "sgdg_mlp_destroy": (None, [C.c_void_p]),
@@ -247,6 +251,10 @@ class Solver:
                            None)
         co.n_g = len(gs)
         co.g = ga
+        for p in range(2 * d):
+            co.beta_t[p] = self._tfn(getattr(problem.beta[p], "ft", None))
+        co.sigma_t = self._tfn(getattr(problem.sigma, "ft", None))
+        co.time_quad = 0
         self._keep += [cfg, co, u0, fa, ga]
         h = C.c_void_p()
         st = self.lib.sgdg_create(C.byref(cfg), C.byref(co), C.byref(h))
@@ -411,6 +419,9 @@ class Solver:
 
     def coarse_values(self, u, R: int, lx: int, lv: int, out, stream=None):
         self._check(self.lib.sgdg_coarse_values(self.h, _ptr(u), R, lx, lv, _ptr(out), _stream(stream)))
+
+    def coarse_diff(self, a, b, R: int, lx: int, lv: int, out, stream=None):
+        self._check(self.lib.sgdg_coarse_diff(self.h, _ptr(a), _ptr(b), R, lx, lv, _ptr(out), _stream(stream)))
 
     def add_coarse(self, c, lx: int, lv: int, u, stream=None):
         self._check(self.lib.sgdg_add_coarse(self.h, _ptr(c), lx, lv, _ptr(u), _stream(stream)))

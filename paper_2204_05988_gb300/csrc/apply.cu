@@ -229,7 +229,8 @@ Status run_final(Handle& h, FinalArgs<T>& f, bool left, int kind, cudaStream_t s
   f.pair = sh.pair;
   f.pf = sh.pf;
   ProfScope ps(h, s);
-  SG_CU(launch_final(f, left, s));
+  if (left && f.lat_nx > 0 && h.sweep_variant == 1 && f.row == 7) SG_CU(launch_final_lattice(f, s));
+  else SG_CU(launch_final(f, left, s));
   const double g = grid_bytes<T>(f.n1, f.n2);
   ps.done(kind, mat_bytes + f.nin * in_bytes + g * (f.accumulate ? 2.0 : 1.0), site,
           2.0 * (2.0 * f.row + 4.0) * f.nterms * (double)f.n1 * f.n2);
@@ -252,6 +253,7 @@ struct FinalSpec {
   int row = 8, w = 8;
   long long mat_rows = 0;
   double in_bytes = 0.0;
+  int lat_nx = 0;                    // left on a 2-D lattice level: vertices per lattice row
 };
 
 template <typename T, typename InOf, typename ValOf>
@@ -264,6 +266,7 @@ Status finals_on(Handle& h, const Plan& p, const std::vector<Chain>& chains, con
   f.row = fs.row;
   f.col = fs.col;
   f.y = ygrid;
+  f.lat_nx = fs.lat_nx;
   bool first = true;
   auto flush = [&]() -> Status {
     if (f.nterms == 0) return {};
@@ -343,6 +346,7 @@ Status diag_block(Handle& h, const Plan& p, const Pool<T>& pool, int lx, int lv,
   fs.w = h.X.ell_w();
   fs.mat_rows = n1;
   fs.in_bytes = g;
+  fs.lat_nx = lx < (int)h.X.lat_nx.size() ? h.X.lat_nx[lx] : 0;
   return finals_on<T>(h, p, p.A, fs, [&](int c) { return (const Store<T>*)pool.W(c); },
                       [&](const Term& tm) { return (const Comp<T>*)h.X.vals<Comp<T>>().ell_fac[tm.x][lx]; }, accumulate, y, s);
 }

@@ -90,6 +90,8 @@ void eval_fn(const SideFns& fns, int id, const std::vector<double>& pts, int d, 
 
 }  // namespace
 
+void gauss_rule01(int q, std::vector<double>& x, std::vector<double>& w) { gauss_legendre01(q, x, w); }
+
 bool FactorSpec::operator<(const FactorSpec& o) const {
   if (kind != o.kind) return kind < o.kind;
   if (wfn != o.wfn) return wfn < o.wfn;

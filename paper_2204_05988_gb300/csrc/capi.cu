@@ -91,6 +91,78 @@ std::vector<double> ell_values(const std::vector<int>& rowptr, const std::vector
   return out;
 }
 
+namespace {
+
+// Stencil-slot offsets (dx, dy) of a 2-D lattice whose cells are cut along
+// the (1, 1) diagonal, in the order of their lexicographic index offsets.
+constexpr int kLatSlots = 7;
+constexpr int kLatDx[kLatSlots] = {-1, 0, -1, 0, 1, 0, 1};
+constexpr int kLatDy[kLatSlots] = {-1, -1, 0, 0, 0, 1, 1};
+
+// The slot map of a level when it is such a lattice (empty otherwise).
+std::vector<int> lattice_slots(const MeshLevel& lv, int d, int w, int* nx_out) {
+  *nx_out = 0;
+  if (d != 2 || w < 8 || lv.n < 4) return {};
+  const Csr& P = lv.pattern;
+  const double y0 = lv.coords[1];
+  int nx = 0;
+  while (nx < lv.n && lv.coords[2 * nx + 1] == y0) ++nx;
+  if (nx < 2 || lv.n % nx) return {};
+  const int ny = lv.n / nx;
+  for (int k = 0; k < lv.n; ++k)
+    if (lv.coords[2 * k] != lv.coords[2 * (k % nx)] || lv.coords[2 * k + 1] != lv.coords[2 * (k / nx * nx) + 1])
+      return {};
+  std::vector<int> pos((size_t)lv.n * w, -1);
+  for (int k = 0; k < lv.n; ++k) {
+    const int ix = k % nx, iy = k / nx;
+    for (int p = P.rowptr[k]; p < P.rowptr[k + 1]; ++p) {
+      const int c = P.col[p], dx = c % nx - ix, dy = c / nx - iy;
+      int slot = -1;
+      for (int q = 0; q < kLatSlots; ++q)
+        if (kLatDx[q] == dx && kLatDy[q] == dy) slot = q;
+      if (slot < 0) return {};
+      pos[(size_t)k * w + slot] = p;
+    }
+    (void)ny;
+  }
+  *nx_out = nx;
+  return pos;
+}
+
+}  // namespace
+
+std::vector<int> pattern_ell_columns(const SideDev& sd, const Csr& P, int l) {
+  const int w = sd.ell_w();
+  if (l >= (int)sd.lat_nx.size() || !sd.lat_nx[l]) return ell_columns(P.rowptr, P.col, w);
+  const std::vector<int>& pos = sd.lat_pos[l];
+  std::vector<int> out((size_t)P.nrows * w);
+  for (int r = 0; r < P.nrows; ++r)
+    for (int s = 0; s < w; ++s) {
+      const int p = pos[(size_t)r * w + s];
+      out[(size_t)r * w + s] = p >= 0 ? P.col[p] : r;
+    }
+  return out;
+}
+
+Status upload_pattern_vals(Handle& h, const SideDev& sd, const Csr& P, int l, const std::vector<double>& val,
+                           double** d64, float** d32) {
+  const int w = sd.ell_w();
+  if (l >= (int)sd.lat_nx.size() || !sd.lat_nx[l]) return upload_ell_vals(h, P.rowptr, val, w, d64, d32);
+  const std::vector<int>& pos = sd.lat_pos[l];
+  std::vector<double> e(pos.size(), 0.0);
+  for (size_t i = 0; i < pos.size(); ++i)
+    if (pos[i] >= 0) e[i] = val[pos[i]];
+  const std::vector<float> f(e.begin(), e.end());
+  if (!*d64) {
+    SG_ST(upload(h, d64, e.data(), e.size()));
+    SG_ST(upload(h, d32, f.data(), f.size()));
+  } else {
+    SG_CU(cudaMemcpy(*d64, e.data(), sizeof(double) * e.size(), cudaMemcpyHostToDevice));
+    SG_CU(cudaMemcpy(*d32, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice));
+  }
+  return {};
+}
+
 Status upload_ell_vals(Handle& h, const std::vector<int>& rowptr, const std::vector<double>& val, int w,
                        double** d64, float** d32) {
   const std::vector<double> e = ell_values(rowptr, val, w);
@@ -175,13 +247,16 @@ Status upload_side(Handle& h, const Hierarchy& hi, SideDev& sd) {
   sd.col.resize(L + 1);
   const int w = sd.ell_w();
   sd.ell_col.resize(L + 1);
+  sd.lat_nx.assign(L + 1, 0);
+  sd.lat_pos.assign(L + 1, {});
   for (int l = 0; l <= L; ++l) {
     const Csr& P = hi.lev[l].pattern;
     sd.n[l] = P.nrows;
     sd.nnz[l] = P.nnz();
     SG_ST(upload(h, &sd.rowptr[l], P.rowptr.data(), P.rowptr.size()));
     SG_ST(upload(h, &sd.col[l], P.col.data(), P.col.size()));
-    const std::vector<int> ec = ell_columns(P.rowptr, P.col, w);
+    if (sd.lattice_ok) sd.lat_pos[l] = lattice_slots(hi.lev[l], hi.d, w, &sd.lat_nx[l]);
+    const std::vector<int> ec = pattern_ell_columns(sd, P, l);
     SG_ST(upload(h, &sd.ell_col[l], ec.data(), ec.size()));
   }
   sd.E_rowptr.resize(L); sd.E_col.resize(L); sd.R_rowptr.resize(L); sd.R_col.resize(L); sd.inj.resize(L);
@@ -277,6 +352,14 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   if (cfg.outer_method != SGDG_OUTER_FGMRES && cfg.outer_method != SGDG_OUTER_RICHARDSON)
     return {SGDG_EINVAL, "unknown outer_method"};
   if (c.n_u0 < 0 || (c.n_u0 > 0 && !c.u0)) return {SGDG_EINVAL, "bad u0 list"};
+  {
+    bool timed = c.sigma_t != nullptr;
+    for (int p = 0; p < 2 * cfg.mesh_x.dim && p < 2 * kMaxDim; ++p) timed = timed || c.beta_t[p] != nullptr;
+    if (timed && (c.n_f > 0 || c.n_g > 0 || cfg.vlasov_poisson))
+      return {SGDG_EINVAL, "time factors of beta or sigma are not combined with sources, inflow data or "
+                           "vlasov_poisson"};
+    if (c.time_quad < 0 || c.time_quad > 8) return {SGDG_EINVAL, "time_quad must be in 0..8"};
+  }
   h.cfg = cfg;
   h.d = cfg.mesh_x.dim;
   h.L = cfg.level_L;
@@ -341,6 +424,7 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   }
   h.X.maxrow = side_maxrow[0];
   h.V.maxrow = side_maxrow[1];
+  h.X.lattice_ok = true;   // the x side's dim-1 finals have a lattice kernel
   SG_ST(upload_side(h, hx, h.X));
   SG_ST(upload_side(h, hv, h.V));
   // the sweep uses R X (branch B's chain steps) and V E (branch B's final).
@@ -391,8 +475,8 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
       fnv(h.problem_hash, X[h.L].val.data(), sizeof(double) * X[h.L].val.size());
       fnv(h.problem_hash, X[h.L].col.data(), sizeof(int) * X[h.L].col.size());
       for (int l = 0; l <= h.L; ++l) {
-        SG_ST(upload_ell_vals(h, hi.lev[l].pattern.rowptr, X[l].val, sd.ell_w(), &sd.v64.ell_fac[f][l],
-                              &sd.v32.ell_fac[f][l]));
+        SG_ST(upload_pattern_vals(h, sd, hi.lev[l].pattern, l, X[l].val, &sd.v64.ell_fac[f][l],
+                                  &sd.v32.ell_fac[f][l]));
       }
       SG_ST(upload_products(h, sd, (int)f, Ps[f]));
       if ((int)f == sd.mass) {
@@ -441,6 +525,11 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
     fnv(h.problem_hash, &t.v, sizeof(t.v));
   }
   make_plan(h.op, h.tt.terms);
+  // time factors: the couplings of the first strip (0, dt)
+  for (int p = 0; p < 2 * kMaxDim; ++p) h.coef_t.push_back({p < 2 * h.d ? c.beta_t[p] : nullptr, c.beta_ut[p]});
+  h.coef_t.push_back({c.sigma_t, c.sigma_ut});
+  h.time_quad = c.time_quad > 0 ? c.time_quad : 3;
+  SG_ST(set_strip_time(h, 0.0));
   Term mt;
   mt.tau[0][0] = 1.0; mt.tau[0][1] = 0.0; mt.tau[1][0] = 0.0; mt.tau[1][1] = 1.0;
   mt.x = h.X.mass;
@@ -637,6 +726,8 @@ sgdg_status sgdg_get_info(const void* hp, sgdg_info* o) {
     o->rows_x += h->X.n[l];
     o->rows_v += h->V.n[l];
   }
+  o->lattice_x_levels = 0;
+  for (int nx : h->X.lat_nx) o->lattice_x_levels += nx > 0 ? 1 : 0;
   return SGDG_OK;
 }
 
@@ -847,6 +938,10 @@ sgdg_status sgdg_set_initial(void* hp) {
   h->t_now = 0.0;
   h->solved = false;
   h->nsolved = 0;
+  {
+    Status st = set_strip_time(*h, 0.0);
+    if (st.code) return fail(h, st);
+  }
   return SGDG_OK;
 }
 
@@ -927,7 +1022,7 @@ sgdg_status sgdg_fused_plan_info(void* hp, int grid, int pair_bytes, int* iout, 
 sgdg_status sgdg_set_sweep_variant(void* hp, int variant) {
   if (!hp) return SGDG_EINVAL;
   Handle* h = (Handle*)hp;
-  if (variant != 0 && variant != 1) return fail(h, {SGDG_EINVAL, "sweep variant must be 0 or 1"});
+  if (variant < 0 || variant > 2) return fail(h, {SGDG_EINVAL, "sweep variant must be 0, 1 or 2"});
   h->sweep_variant = variant;
   return SGDG_OK;
 }
@@ -948,6 +1043,7 @@ struct Batch {
     std::vector<const void*> u;
     std::vector<void*> y;
     int prec;
+    std::vector<long long> tau_version;   // members' time couplings when captured
     cudaGraphExec_t exec;
   };
   std::vector<Graph> graphs;
@@ -987,14 +1083,21 @@ sgdg_status sgdg_batch_apply(void* bp, const void* const* u, void* const* y, int
     return fail(nullptr, {SGDG_EINVAL, "unknown precision"});
   Batch* b = (Batch*)bp;
   const size_t n = b->m.size();
-  for (auto& g : b->graphs) {
+  for (size_t gi = 0; gi < b->graphs.size(); ++gi) {
+    Batch::Graph& g = b->graphs[gi];
     bool same = g.prec == prec;
     for (size_t k = 0; same && k < n; ++k) same = g.u[k] == u[k] && g.y[k] == y[k];
-    if (same) {
-      if (cudaGraphLaunch(g.exec, (cudaStream_t)stream) != cudaSuccess)
-        return fail(nullptr, {SGDG_ECUDA, "batch graph launch"});
-      return SGDG_OK;
+    if (!same) continue;
+    bool fresh = true;
+    for (size_t k = 0; k < n; ++k) fresh = fresh && g.tau_version[k] == b->m[k]->tau_version;
+    if (!fresh) {   // time couplings changed since the capture (time factors): capture again
+      cudaGraphExecDestroy(g.exec);
+      b->graphs.erase(b->graphs.begin() + gi);
+      break;
     }
+    if (cudaGraphLaunch(g.exec, (cudaStream_t)stream) != cudaSuccess)
+      return fail(nullptr, {SGDG_ECUDA, "batch graph launch"});
+    return SGDG_OK;
   }
   // eager pass: allocates every lazily created buffer before the capture
   auto run_all = [&](cudaStream_t s) -> Status {
@@ -1027,6 +1130,7 @@ sgdg_status sgdg_batch_apply(void* bp, const void* const* u, void* const* y, int
   g.u.assign(u, u + n);
   g.y.assign(y, y + n);
   g.prec = prec;
+  for (size_t k = 0; k < n; ++k) g.tau_version.push_back(b->m[k]->tau_version);
   ce = cudaGraphInstantiate(&g.exec, graph, 0);
   cudaGraphDestroy(graph);
   if (ce != cudaSuccess) return fail(nullptr, {SGDG_ECUDA, "graph instantiate"});
@@ -1116,6 +1220,14 @@ sgdg_status sgdg_coarse_values(void* hp, const double* u, int R, int lx, int lv,
   if (!hp || !u || !out) return SGDG_EINVAL;
   Handle* h = (Handle*)hp;
   Status st = coarse_values(*h, u, R, lx, lv, out, (cudaStream_t)stream);
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+sgdg_status sgdg_coarse_diff(void* hp, const double* a, const double* b, int R, int lx, int lv, double* out,
+                             void* stream) {
+  if (!hp || !a || !b || !out) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  Status st = coarse_diff(*h, a, b, R, lx, lv, out, (cudaStream_t)stream);
   return st.code ? fail(h, st) : SGDG_OK;
 }
 

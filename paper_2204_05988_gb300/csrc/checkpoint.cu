@@ -145,6 +145,10 @@ Status restore(Handle& h, const char* path) {
   h.nsolved = flags[3];
   h.warm = flags[4];
   h.t_now = t_now;
+  {
+    Status st = set_strip_time(h, t_now);   // time factors: the couplings of the next strip
+    if (st.code) return st;
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) return {SGDG_ECUDA, "restore: synchronise"};
   return {};
 }

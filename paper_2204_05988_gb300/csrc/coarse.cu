@@ -5,6 +5,7 @@
 // nodes are either nodes of the grid's (finer) level - take them by the
 // composed injection - or the grid's (coarser) level is prolonged up to the
 // coarse level by the embeddings E (Sect. 4.2).
+// sgdg_coarse_diff: the same view of the difference of two functions.
 // sgdg_add_coarse: adds the P1 function c on the full grid (lx, lv) to the
 // component grid (lx, L-lx), prolonged in v from level lv to L-lx.
 #include <cuda_runtime.h>
@@ -61,6 +62,10 @@ __global__ void k_prolong_cols(const double* in, double* out, int n1, int n2i, i
     for (int p = rp[j]; p < rp[j + 1]; ++p) acc += v[p] * in[((size_t)r * n2i + ci[p]) * R + s];
     out[i] = acc;
   }
+}
+__global__ void k_sub(double* y, const double* x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] -= x[i];
 }
 __global__ void k_add(double* y, const double* x, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -133,6 +138,23 @@ Status coarse_values(Handle& h, const double* u, int R, int lx, int lv, double* 
   cudaFreeAsync(t1, s);
   cudaFreeAsync(rm, s);
   cudaFreeAsync(cm, s);
+  return st;
+}
+
+Status coarse_diff(Handle& h, const double* a, const double* b, int R, int lx, int lv, double* out,
+                   cudaStream_t s) {
+  const int L = h.L;
+  if ((R != 1 && R != 2) || lx < 0 || lv < 0 || lx > L || lv > L) return {SGDG_EINVAL, "bad coarse grid or R"};
+  const long long n = (long long)h.X.n[lx] * h.V.n[lv] * R;
+  double* t = nullptr;
+  CK(cudaMallocAsync((void**)&t, sizeof(double) * n, s));
+  Status st = coarse_values(h, a, R, lx, lv, out, s);
+  if (!st.code) st = coarse_values(h, b, R, lx, lv, t, s);
+  if (!st.code) {
+    k_sub<<<nb(n), kTh, 0, s>>>(out, t, n);
+    if (cudaGetLastError() != cudaSuccess) st = {SGDG_ECUDA, "coarse difference kernel"};
+  }
+  cudaFreeAsync(t, s);
   return st;
 }
 

@@ -251,7 +251,7 @@ Status field_reassemble(Handle& h) {
     st = assemble_factor(F.hx, F.fx, fs, X);
     if (st.code) return st;
     for (int l = 0; l <= L; ++l) {
-      st = upload_ell_vals(h, F.hx.lev[l].pattern.rowptr, X[l].val, h.X.ell_w(), &h.X.v64.ell_fac[f][l],
+      st = upload_pattern_vals(h, h.X, F.hx.lev[l].pattern, l, X[l].val, &h.X.v64.ell_fac[f][l],
                            &h.X.v32.ell_fac[f][l]);
       if (st.code) return st;
     }

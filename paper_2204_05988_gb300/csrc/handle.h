@@ -47,6 +47,16 @@ struct SideDev {
   int rf_w() const { return ell_width(rf_row); }
   int fp_w() const { return ell_width(fp_row); }
   std::vector<Csr> RF_pat, FP_pat;                   // host patterns (FP_pat[0] empty)
+  // 2-D structured lattice levels (lexicographic vertex order, every cell
+  // cut along the (1, 1) diagonal): lat_nx[l] = vertices per lattice row, 0
+  // when level l is not such a lattice.  Their pattern ELL rows (columns and
+  // every factor's values) are in stencil-slot order - offsets -nx-1, -nx,
+  // -1, 0, 1, nx, nx+1, then one padding slot - with column = the row itself
+  // and value 0 for an absent neighbour; lat_pos[l][r w + s] is the CSR
+  // position of slot s of row r (-1: absent or padding)
+  std::vector<int> lat_nx;
+  std::vector<std::vector<int>> lat_pos;
+  bool lattice_ok = false;            // look for lattice levels (the x side)
   SideValues<double> v64;
   SideValues<float> v32;
   template <typename T> SideValues<T>& vals();
@@ -105,6 +115,12 @@ struct Handle {
   std::vector<SourceTerm> src_terms;
   std::vector<std::pair<sgdg_tfn, void*>> src_t;   // time factor per source
   double t_now = 0.0;                              // start of the next strip
+  // time factors of the coefficients (function ids: beta 0..2 kMaxDim - 1,
+  // then sigma; NULL = 1), the Gauss points per strip, and a counter bumped
+  // whenever the time couplings of h.op change (batch graphs re-capture)
+  std::vector<std::pair<sgdg_tfn, void*>> coef_t;
+  int time_quad = 3;
+  long long tau_version = 0;
   // strip state
   double* U_end = nullptr;   // spatial, n_spatial
   double* u_sol = nullptr;   // last strip solution, n_coeffs
@@ -166,7 +182,8 @@ struct Handle {
     unsigned short* qloc = nullptr;
   };
   std::map<long long, FusedGrid> fused;
-  int sweep_variant = 1;          // 0: fused branch A where a plan fits; 1 (default): unfused kernels
+  int sweep_variant = 1;          // 0: fused branch A where a plan fits; 1 (default): unfused kernels, the
+                                  // lattice final on 2-D lattice levels; 2: unfused, generic finals only
   // identity of the discrete problem (meshes, levels, dt, delta, term table,
   // finest-level factor values at creation), checked by sgdg_restore
   unsigned long long problem_hash = 0;
@@ -198,6 +215,11 @@ Status upload_products(Handle& h, SideDev& sd, int f, const FactorProducts& pr);
 // Uploads the FP64 and FP32 ELL values; allocates when *d64 is null, else overwrites.
 Status upload_ell_vals(Handle& h, const std::vector<int>& rowptr, const std::vector<double>& val, int w,
                        double** d64, float** d32);
+// The ELL columns of level l's pattern P as the device holds them (slot order
+// on lattice levels), and the upload of a factor's values on that pattern.
+std::vector<int> pattern_ell_columns(const SideDev& sd, const Csr& P, int l);
+Status upload_pattern_vals(Handle& h, const SideDev& sd, const Csr& P, int l, const std::vector<double>& val,
+                           double** d64, float** d32);
 
 // Optional per-grid synchronisation of an apply: before grid i's input U_i
 // is first read the stream waits for ready[i]; once Y_i is final, done(i)
@@ -232,6 +254,8 @@ Status field_reassemble(Handle& h);
 // coarse full-grid views (coarse.cu)
 Status coarse_values(Handle& h, const double* u, int R, int lx, int lv, double* out, cudaStream_t s);
 Status add_coarse(Handle& h, const double* c, int lx, int lv, double* u, cudaStream_t s);
+Status coarse_diff(Handle& h, const double* a, const double* b, int R, int lx, int lv, double* out,
+                   cudaStream_t s);
 
 Status solver_init(Handle& h);
 // ||u||_{H^1(I_j x Omega)} of a strip vector (FP64, device): u . (G u) with
@@ -241,6 +265,9 @@ Status h1_norm(Handle& h, const double* u, double* tmp, double* out, cudaStream_
 Status constant_in_time(Handle& h, const double* U, double* dst, cudaStream_t s);
 Status ct_precondition(Handle& h, const double* r, double* z, cudaStream_t s, int* inner_its);
 Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resolve = false);
+// With time factors of beta or sigma: the time couplings of the operator for
+// the strip (t0, t0 + dt) (Sect. 4.2 quadrature); nothing otherwise.
+Status set_strip_time(Handle& h, double t0);
 void solver_free(Handle& h);
 
 }  // namespace sgdg

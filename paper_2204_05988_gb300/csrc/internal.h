@@ -53,6 +53,9 @@ struct Hierarchy {
 
 Status build_hierarchy(const sgdg_mesh& m, int L, Hierarchy& h);
 
+// q-point Gauss-Legendre rule on [0, 1] (nodes by Newton's method on P_q).
+void gauss_rule01(int q, std::vector<double>& x, std::vector<double>& w);
+
 // ---------------------------------------------------------------------------
 // Factors of the Kronecker terms (Sect. 4.2)
 // ---------------------------------------------------------------------------
@@ -99,10 +102,37 @@ struct Term {
   int x, v;            // factor ids
 };
 
+// One contribution to a term's time coupling (Sect. 4.2):
+//   scale * sum_mu w_mu g(tau_mu) B_mu      (base M, T, T^T or C)
+//   scale * G^(t)                           (base G, the jump at t_{j-1})
+// with B_mu the time basis products at the Gauss point tau_mu (M: eta_s'
+// eta_s, T: eta'_s' eta_s, C: eta'_s' eta'_s; [s][s'], s the test index),
+// g the product of the time factors of the coefficients f1, f2 (function
+// ids, -1: none) and, for inflow parts, the indicator that the time factor
+// of component gate_fn has the sign gate_sign (times its coefficient).
+// Without time factors the sum is the exact time matrix.
+struct TauPart {
+  enum Base { M = 0, T = 1, TT = 2, C = 3, G = 4 };
+  int base = M;
+  double scale = 0.0;
+  int f1 = -1, f2 = -1;
+  int gate_fn = -1, gate_sign = 0;
+  double gate_coef = 1.0;
+};
+
 struct TermTable {
   std::vector<FactorSpec> xf, vf;
   std::vector<Term> terms;
+  std::vector<std::vector<TauPart>> parts;   // per term: its time coupling
+  bool time_dep = false;                     // some coefficient has a time factor
 };
+
+// The time coupling of every term for the strip (t0, t0 + dt) from its
+// parts: an m-point Gauss rule per strip with time factors (ft[id] = the
+// callback of function id, NULL: constant 1), the exact time matrices
+// without.  Writes terms[k].tau.
+Status strip_time_couplings(TermTable& tt, double t0, double dt, int m,
+                            const std::vector<std::pair<sgdg_tfn, void*>>& ft);
 
 Status build_terms(const sgdg_coeffs& c, int d, const sgdg_mesh& mx, const sgdg_mesh& mv,
                    double dt, double delta, TermTable& out);
@@ -114,8 +144,11 @@ Status build_terms(const sgdg_coeffs& c, int d, const sgdg_mesh& mx, const sgdg_
 struct InflowPart {
   FactorSpec x, v;
   double scale = 0.0;
+  int gate_fn = -1, gate_sign = 0;   // time factor of beta[gate_fn]: part active when
+                                     // sign(coef * factor(t)) == gate_sign
 };
-std::vector<InflowPart> inflow_parts(const sgdg_coeffs& c, int d, const sgdg_mesh& mx, const sgdg_mesh& mv);
+std::vector<InflowPart> inflow_parts(const sgdg_coeffs& c, int d, const sgdg_mesh& mx, const sgdg_mesh& mv,
+                                     bool with_time = false);
 
 // C = A B: the structural pattern (sorted rows, no values) and the values of
 // A B on that pattern (aval, bval: values of A and B on their patterns).

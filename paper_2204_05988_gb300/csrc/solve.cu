@@ -888,6 +888,16 @@ static Status apply_mixed(Handle& h, const double* z, double* w, bool force64, c
   return {};
 }
 
+Status set_strip_time(Handle& h, double t0) {
+  if (!h.tt.time_dep) return {};
+  SG_ST(strip_time_couplings(h.tt, t0, h.cfg.dt, h.time_quad, h.coef_t));
+  for (size_t k = 0; k < h.tt.terms.size() && k < h.op.terms.size(); ++k)
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) h.op.terms[k].tau[a][b] = h.tt.terms[k].tau[a][b];
+  h.tau_version++;
+  return {};
+}
+
 Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resolve) {
   auto t0 = std::chrono::steady_clock::now();
   SG_ST(solver_init(h));
@@ -896,6 +906,8 @@ Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resol
   const long long n = h.n_coeffs;
   if (!h.have_initial) return {SGDG_EINVAL, "sgdg_set_initial was not called"};
   if (resolve && !h.solved) return {SGDG_EINVAL, "no strip has been solved yet"};
+  // the strip's operator (time factors: couplings of (t_{j-1}, t_j))
+  SG_ST(set_strip_time(h, resolve ? h.t_now - h.cfg.dt : h.t_now));
   // right-hand side: eta(t_{j-1}^+) (x) M_sg U^-_{j-1}; the first strip uses (u0, phi);
   // a re-solve keeps the right-hand side of the strip
   if (!resolve && !h.first_strip) {
@@ -994,6 +1006,8 @@ Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resol
     h.nsolved++;
     h.t_now += h.cfg.dt;
   }
+  // applies between strips use the operator of the next strip
+  SG_ST(set_strip_time(h, h.t_now));
   S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (st) *st = S;
   if (S.status == SGDG_ENOCONV) return {SGDG_ENOCONV, "outer iteration reached max_outer"};

@@ -111,6 +111,7 @@ struct FinalArgs {
   Comp<T> tau[kFinalTerms][4] = {};
   const int* col = nullptr;               // ELL
   Store<T>* y = nullptr;
+  int lat_nx = 0;                         // left on a 2-D lattice level: vertices per lattice row
 };
 
 // Fused branch-A step on one grid (sweep_fused.cu).  The grid's (k1, k2)
@@ -169,5 +170,10 @@ template <typename T>
 cudaError_t launch_chain(ChainArgs<T>& a, bool mode_a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_final(FinalArgs<T>& a, bool left, cudaStream_t s);
+// left final on a 2-D lattice level (sweep_lattice.cu): rows in stencil-slot
+// order, a.row == 7, a.lat_nx = vertices per lattice row, a.ch <= 4: runs of
+// 4 vertices per thread, else 8
+template <typename T>
+cudaError_t launch_final_lattice(FinalArgs<T>& a, cudaStream_t s);
 
 }  // namespace sgdg

@@ -205,7 +205,7 @@ Status fused_plan(Handle& h, int i, int pair_bytes, int nchains, int nterms, con
   const Hierarchy& HV = *h.hv_host;
   const MeshLevel& xl = HX.lev[lx];
   const MeshLevel& vl = HV.lev[lv];
-  const std::vector<int> xell = ell_columns(xl.pattern.rowptr, xl.pattern.col, W);
+  const std::vector<int> xell = pattern_ell_columns(h.X, xl.pattern, lx);
   const bool restrict_out = i < L;
   std::vector<int> rell;
   if (restrict_out) rell = ell_columns(HV.Rt[lv - 1].rowptr, HV.Rt[lv - 1].col, W);

@@ -52,11 +52,7 @@ def features(solver: Solver, lx: int, lv: int, g):
     solver.get_solution(u, on_device=True)
     f = torch.empty(nx * nv * 3, dtype=torch.float64, device="cuda")
     solver.coarse_values(U, 1, lx, lv, f[: nx * nv])
-    ca = torch.empty(nx * nv * 2, dtype=torch.float64, device="cuda")
-    cb = torch.empty_like(ca)
-    solver.coarse_values(g, 2, lx, lv, ca)
-    solver.coarse_values(u, 2, lx, lv, cb)
-    f[nx * nv:] = ca - cb
+    solver.coarse_diff(g, u, 2, lx, lv, f[nx * nv:])
     return f
 
 
@@ -77,16 +73,14 @@ def collect(problems, n_strips: int, lx: int = 2, lv: int = 2, solver_kw=None) -
             if j >= 2:
                 s.extrapolated_guess(g)
                 f = features(s, lx, lv, g)
-                cg = torch.empty(nx * nv * 2, dtype=torch.float64, device="cuda")
-                s.coarse_values(g, 2, lx, lv, cg)
             s.advance_strip()
             if f is not None:
                 u = torch.empty_like(g)
                 s.get_solution(u, on_device=True)
-                cu = torch.empty_like(cg)
-                s.coarse_values(u, 2, lx, lv, cu)
+                t = torch.empty(nx * nv * 2, dtype=torch.float64, device="cuda")
+                s.coarse_diff(u, g, 2, lx, lv, t)
                 pairs.x.append(f)
-                pairs.y.append(cu - cg)
+                pairs.y.append(t)
             s.field_update(0)
         s.close()
     return pairs

@@ -7,7 +7,9 @@
 * training on strip pairs from the plain solver lowers the loss; the trained
   network's guess (extrapolation + learned coarse correction, warm start 2)
   starts closer than the previous-solution guess and the solver still reaches
-  the tolerance from every guess - the converged residual decides.
+  the tolerance from every guess - the converged residual decides; the
+  comparison with the extrapolation (the method without the network) is
+  reported per strip.
 """
 import numpy as np
 import pytest
@@ -45,6 +47,13 @@ def test_coarse_values_parity_and_roundtrip(P):
         s.coarse_values(torch.tensor(U, device="cuda"), 1, lx, lv, out1)
         torch.cuda.synchronize()
         assert np.abs(out1.cpu().numpy() - ref1).max() < 1e-12 * np.abs(ref1).max(), (lx, lv)
+    # the view of a difference (the warm start's features and targets)
+    a, b = W.uniform_vector(op.size, seed=10), W.uniform_vector(op.size, seed=11)
+    ref = coarse_values(op, a - b, 2, 2, 2)
+    out = torch.empty(ref.size, dtype=torch.float64, device="cuda")
+    s.coarse_diff(torch.tensor(a, device="cuda"), torch.tensor(b, device="cuda"), 2, 2, 2, out)
+    torch.cuda.synchronize()
+    assert np.abs(out.cpu().numpy() - ref).max() < 1e-12 * np.abs(ref).max()
     # round trip: a coarse function added to zero evaluates back to itself
     lx, lv = 2, 2
     nx, nv = op.hx.levels[lx].n, op.hv.levels[lv].n
@@ -80,7 +89,18 @@ def test_mlp_gradients_match_oracle(P):
     assert np.linalg.norm(g - g_ref) < 3e-2 * np.linalg.norm(g_ref)
 
 
-def test_training_and_learned_guess(P):
+def test_training_and_learned_guess(P, record_property):
+    """Train on strip pairs of the plain solver, then solve a held-out problem
+    from three guesses: the previous solution, the extrapolation 2 u_{j-1} -
+    u_{j-2} (the method without the network) and the learned guess
+    (extrapolation + the network's coarse correction).  Asserted: training
+    lowers the loss, every guess reaches the tolerance (the converged residual
+    decides), and the learned guess starts closer than the previous solution.
+    Reported against the extrapolation, per strip: the initial residual, the
+    outer iterations and the time.  So far the network lowers the initial
+    residual below the extrapolation's but does not lower the iteration count
+    (at L = 6 on the Landau problem: 118 outer iterations against 83 for 16
+    strips) - the gain over the method without it is not shown."""
     from paper_2204_05988_gb300 import warmstart as WS
     probs = [W.landau_4d(L=3, alpha=a, phase=ph, dt=0.25) for a, ph in [(0.01, 0.0), (0.02, 1.0), (0.015, 2.0)]]
     pairs = WS.collect(probs, n_strips=6, lx=2, lv=1)
@@ -95,3 +115,11 @@ def test_training_and_learned_guess(P):
     r_prev = np.mean([r[1] for r in res["previous"][2:]])
     r_learn = np.mean([r[1] for r in res["learned"][2:]])
     assert r_learn < r_prev, (r_learn, r_prev)
+    # against the method without the network (extrapolation): reported
+    for k in ("extrapolated", "learned"):
+        record_property(f"{k}_initial_residual", [r[1] for r in res[k][2:]])
+        record_property(f"{k}_outer_its", [r[0] for r in res[k][2:]])
+        record_property(f"{k}_seconds", [round(r[2], 4) for r in res[k][2:]])
+    print("learned vs extrapolated, strips 3-5: initial residual",
+          [f"{a[1]:.2e}/{b[1]:.2e}" for a, b in zip(res["learned"][2:], res["extrapolated"][2:])],
+          "outer its", [(a[0], b[0]) for a, b in zip(res["learned"][2:], res["extrapolated"][2:])])
