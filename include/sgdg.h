@@ -405,10 +405,11 @@ sgdg_status sgdg_autotune(void* h, const void* u, void* y, int precision, void* 
  *   occupancy, barriers and halo recomputation);
  * 1 (default): the unfused kernels (S_b written per grid, then final update
  *   and restriction); on x levels that are 2-D structured lattices (cells
- *   cut along the (1, 1) diagonal) the final update along dim 1 runs a
- *   kernel that slides a register window along the lattice rows;
- * 2: the unfused kernels with the generic final update everywhere (the
- *   same sums; for measurement).  Other values: SGDG_EINVAL. */
+ *   cut along the (1, 1) diagonal) the autotuner may also pick lattice
+ *   kernels for the final update along dim 1 and the mode-A chain step
+ *   (runs along the lattice rows with register windows);
+ * 2: the unfused generic kernels only (the same sums).  Other values:
+ *   SGDG_EINVAL. */
 sgdg_status sgdg_set_sweep_variant(void* h, int variant);
 /* The fused branch-A plan of grid l for S pairs of pair_bytes bytes in shared
  * memory (FP32 and BF16 storage: 8; FP64: 16), built if needed (measurement; no counterpart in the paper): iout[0..3] = tiles,
@@ -425,7 +426,9 @@ sgdg_status sgdg_copy_tuning(void* dst, const void* src);
  * code = rows per thread (1..15) | block order << 4 (0 row-major, 1 column
  * tiles) | two outputs per thread (final kernels, short-row chain steps) << 5
  * | L2 prefetch hints for operands a step ahead (final and chain kernels)
- * << 6; code 0 returns to the tuned or default shapes (sgdg_autotune also
+ * << 6 | the lattice kernels where a level allows them (runs of 4 or 8
+ * vertices for the final, 2 or 4 for the chain step, from the rows per
+ * thread) << 7; code 0 returns to the tuned or default shapes (sgdg_autotune also
  * clears the pin).  For tests and measurements: a shape changes the thread
  * mapping and the prefetching, never the values.  Other codes: SGDG_EINVAL. */
 sgdg_status sgdg_set_launch_shape(void* h, int code);

@@ -30,6 +30,7 @@
 // O(#terms * N) work; no intermediate exceeds one component grid, like the
 // ordering rule of Sect. 4.2.
 #include <algorithm>
+#include <type_traits>
 
 #include "handle.h"
 #include "sweep.h"
@@ -135,13 +136,14 @@ inline long long site_key(int kind, int n1, int n2, int count, int elem) {
 
 // Launch shape of a site: rows per thread (ch, 0 = heuristic), block order
 // (tiled), two outputs per thread (pair: final kernels and short-row mode-A
-// chain steps) and L2 prefetch hints for operands a step ahead (pf: final
-// and chain kernels).  Tuned choices are stored as
-// ch | tiled << 4 | pair << 5 | pf << 6.  Untuned sites take the column tiles
+// chain steps), L2 prefetch hints for operands a step ahead (pf: final
+// and chain kernels) and the lattice kernels (lat: left finals and mode-A
+// chain steps on 2-D lattice x levels, run length from ch).  Tuned choices
+// are stored as ch | tiled << 4 | pair << 5 | pf << 6 | lat << 7.  Untuned sites take the column tiles
 // when the launch's stencil runs along dim 1 and rows are long enough to fill
 // a tile.
 struct Shape {
-  int ch = 0, tiled = 0, pair = 0, pf = 0;
+  int ch = 0, tiled = 0, pair = 0, pf = 0, lat = 0;   // lat: the lattice kernel where the level allows it
 };
 
 template <typename T>
@@ -157,6 +159,7 @@ Shape pick_shape(Handle& h, long long site, bool dim1_stencil, int n1, int n2) {
     sh.tiled = (code >> 4) & 1;
     sh.pair = (code >> 5) & 1;
     sh.pf = (code >> 6) & 1;
+    sh.lat = (code >> 7) & 1;
   } else {
     sh.tiled = dim1_stencil && n2 >= kTileW ? 1 : 0;
   }
@@ -213,7 +216,14 @@ Status run_chain(Handle& h, ChainArgs<T>& a, bool mode_a, int kind, cudaStream_t
   a.pair = sh.pair;
   a.pf = sh.pf;
   ProfScope ps(h, s);
-  SG_CU(launch_chain(a, mode_a, s));
+  bool lat = false;
+  if constexpr (!std::is_same<T, double>::value) {
+    if (mode_a && sh.lat && a.lat_nx > 0 && h.sweep_variant == 1 && a.row == 7) {
+      SG_CU(launch_chain_lattice(a, s));
+      lat = true;
+    }
+  }
+  if (!lat) SG_CU(launch_chain(a, mode_a, s));
   ps.done(kind, in_bytes + a.nchains * grid_bytes<T>(a.n1, a.n2), site,
           4.0 * (a.row + (a.has_prev ? kProlongRow : 0)) * a.nchains * (double)a.n1 * a.n2);
   return {};
@@ -229,7 +239,7 @@ Status run_final(Handle& h, FinalArgs<T>& f, bool left, int kind, cudaStream_t s
   f.pair = sh.pair;
   f.pf = sh.pf;
   ProfScope ps(h, s);
-  if (left && f.lat_nx > 0 && h.sweep_variant == 1 && f.row == 7) SG_CU(launch_final_lattice(f, s));
+  if (left && sh.lat && f.lat_nx > 0 && h.sweep_variant == 1 && f.row == 7) SG_CU(launch_final_lattice(f, s));
   else SG_CU(launch_final(f, left, s));
   const double g = grid_bytes<T>(f.n1, f.n2);
   ps.done(kind, mat_bytes + f.nin * in_bytes + g * (f.accumulate ? 2.0 : 1.0), site,
@@ -322,6 +332,8 @@ Status diag_block(Handle& h, const Plan& p, const Pool<T>& pool, int lx, int lv,
     a.row = h.V.row_regs();
     a.U = u;
     a.f_col = h.V.ell_col[lv];
+    // lattice x level (and, for the prolongation, the lattice level below)
+    if (lx < (int)h.X.lat_nx.size() && h.X.lat_nx[lx] && (!prev || h.X.lat_E[lx])) a.lat_nx = h.X.lat_nx[lx];
     for (int c = 0; c < a.nchains; ++c) {
       a.f_val[c] = h.V.vals<Comp<T>>().ell_fac[p.A[c0 + c].first][lv];
       a.out[c] = pool.W(c0 + c);
@@ -666,12 +678,16 @@ Status nodal_eval(Handle& h, const double* u, double* out, cudaStream_t s) {
 template <typename T>
 Status autotune(Handle& h, const Store<T>* u, Store<T>* y, cudaStream_t s) {
   // rows per thread x block order x paired outputs x L2 prefetch hints,
-  // encoded as ch | tiled << 4 | pair << 5 | pf << 6
+  // encoded as ch | tiled << 4 | pair << 5 | pf << 6; plus the lattice
+  // kernels (bit 7) with their run lengths (from ch), used where a level is
+  // a 2-D lattice and ignored elsewhere
   std::vector<int> cand;
   for (int pf = 0; pf < 2; ++pf)
     for (int pair = 0; pair < 2; ++pair)
       for (int tiled = 0; tiled < 2; ++tiled)
         for (int ch : {1, 2, 4, 8}) cand.push_back(ch | tiled << 4 | pair << 5 | pf << 6);
+  if (h.X.lat_nx.size() && *std::max_element(h.X.lat_nx.begin(), h.X.lat_nx.end()) > 0)
+    for (int ch : {2, 4, 8}) cand.push_back(ch | 1 << 7);
   std::map<long long, std::pair<float, int>> best;
   const bool prof_was = h.prof;
   for (int c : cand) {

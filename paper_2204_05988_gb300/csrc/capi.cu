@@ -259,6 +259,26 @@ Status upload_side(Handle& h, const Hierarchy& hi, SideDev& sd) {
     const std::vector<int> ec = pattern_ell_columns(sd, P, l);
     SG_ST(upload(h, &sd.ell_col[l], ec.data(), ec.size()));
   }
+  sd.lat_E.assign(L + 1, 0);
+  for (int l = 1; l <= L; ++l) {
+    const int nx = sd.lat_nx[l], nxc = sd.lat_nx[l - 1];
+    if (!nx || !nxc || nxc != (nx + 1) / 2 || (hi.lev[l].n / nx + 1) / 2 != hi.lev[l - 1].n / nxc) continue;
+    const Csr& E = hi.E[l - 1];
+    bool ok = true;
+    for (int k = 0; k < E.nrows && ok; ++k) {
+      const int ix = k % nx, iy = k / nx;
+      int want[2], nw = 0;
+      if (!(ix & 1) && !(iy & 1)) want[nw++] = (iy / 2) * nxc + ix / 2;
+      else if (!(iy & 1)) { want[nw++] = (iy / 2) * nxc + (ix - 1) / 2; want[nw++] = (iy / 2) * nxc + (ix + 1) / 2; }
+      else if (!(ix & 1)) { want[nw++] = (iy - 1) / 2 * nxc + ix / 2; want[nw++] = (iy + 1) / 2 * nxc + ix / 2; }
+      else { want[nw++] = (iy - 1) / 2 * nxc + (ix - 1) / 2; want[nw++] = (iy + 1) / 2 * nxc + (ix + 1) / 2; }
+      const int len = E.rowptr[k + 1] - E.rowptr[k];
+      if (len != nw) ok = false;
+      for (int p = 0; p < len && ok; ++p)
+        ok = E.col[E.rowptr[k] + p] == want[p] && E.val[E.rowptr[k] + p] == (nw == 1 ? 1.0 : 0.5);
+    }
+    sd.lat_E[l] = ok ? 1 : 0;
+  }
   sd.E_rowptr.resize(L); sd.E_col.resize(L); sd.R_rowptr.resize(L); sd.R_col.resize(L); sd.inj.resize(L);
   sd.E_nnz.resize(L); sd.R_nnz.resize(L);
   sd.v64.E.resize(L); sd.v64.R.resize(L); sd.v32.E.resize(L); sd.v32.R.resize(L);
@@ -979,8 +999,8 @@ int sgdg_struct_sizes(int* out, int n) {
 sgdg_status sgdg_set_launch_shape(void* hp, int code) {
   if (!hp) return SGDG_EINVAL;
   Handle* h = (Handle*)hp;
-  if (code < 0 || code > 127 || (code > 0 && (code & 15) == 0))
-    return fail(h, {SGDG_EINVAL, "launch shape code: rows per thread 1..15, flags in bits 4..6"});
+  if (code < 0 || code > 255 || (code > 0 && (code & 15) == 0))
+    return fail(h, {SGDG_EINVAL, "launch shape code: rows per thread 1..15, flags in bits 4..7"});
   h->force_ch = code;
   return SGDG_OK;
 }
@@ -1048,6 +1068,16 @@ struct Batch {
   };
   std::vector<Graph> graphs;
   cudaStream_t cap = nullptr;
+  // one stream and two events per member: the captured graph forks into one
+  // branch per member (the members share no buffers), so instances whose
+  // launches do not fill the GPU run side by side
+  std::vector<cudaStream_t> ms;
+  std::vector<cudaEvent_t> fork, join;
+  ~Batch() {
+    for (cudaStream_t x : ms) if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t e : fork) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : join) if (e) cudaEventDestroy(e);
+  }
 };
 }  // namespace
 
@@ -1065,6 +1095,16 @@ sgdg_status sgdg_batch_create(int n, void* const* members, void** out) {
     delete b;
     return fail(nullptr, {SGDG_ECUDA, "batch stream"});
   }
+  b->ms.assign(n, nullptr);
+  b->fork.assign(n, nullptr);
+  b->join.assign(n, nullptr);
+  for (int k = 0; k < n; ++k)
+    if (cudaStreamCreateWithFlags(&b->ms[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) != cudaSuccess) {
+      delete b;
+      return fail(nullptr, {SGDG_ECUDA, "batch member streams"});
+    }
   *out = b;
   return SGDG_OK;
 }
@@ -1099,18 +1139,43 @@ sgdg_status sgdg_batch_apply(void* bp, const void* const* u, void* const* y, int
       return fail(nullptr, {SGDG_ECUDA, "batch graph launch"});
     return SGDG_OK;
   }
-  // eager pass: allocates every lazily created buffer before the capture
+  // eager pass: allocates every lazily created buffer before the capture.
+  // Both passes fork from stream s into one stream per member (members
+  // whose device differs from the batch's stay on s) and join back into s.
   auto run_all = [&](cudaStream_t s) -> Status {
+    int dev = 0;
+    cudaGetDevice(&dev);
     for (size_t k = 0; k < n; ++k) {
       Handle& m = *b->m[k];
+      const bool own = m.cfg.device == dev;
+      cudaStream_t ks = own ? b->ms[k] : s;
+      if (own) {
+        SG_CU(cudaEventRecord(b->fork[k], s));
+        SG_CU(cudaStreamWaitEvent(ks, b->fork[k], 0));
+      }
       Status st =
-          prec == SGDG_FP64        ? apply_plan<double>(m, m.op, (const double*)u[k], (double*)y[k], s)
-          : prec == SGDG_BF16_STORE ? apply_plan<Bf16>(m, m.op, (const __nv_bfloat16*)u[k], (__nv_bfloat16*)y[k], s)
-                                    : apply_plan<float>(m, m.op, (const float*)u[k], (float*)y[k], s);
+          prec == SGDG_FP64        ? apply_plan<double>(m, m.op, (const double*)u[k], (double*)y[k], ks)
+          : prec == SGDG_BF16_STORE ? apply_plan<Bf16>(m, m.op, (const __nv_bfloat16*)u[k], (__nv_bfloat16*)y[k], ks)
+                                    : apply_plan<float>(m, m.op, (const float*)u[k], (float*)y[k], ks);
       if (st.code) return st;
+      if (own) {
+        SG_CU(cudaEventRecord(b->join[k], ks));
+        SG_CU(cudaStreamWaitEvent(s, b->join[k], 0));
+      }
     }
     return {};
   };
+  {
+    // the eager pass runs on the batch's own (non-blocking) stream: order it
+    // after the caller's work, which may still use the members' buffers
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev, (cudaStream_t)stream) != cudaSuccess || cudaStreamWaitEvent(b->cap, ev, 0) != cudaSuccess) {
+      if (ev) cudaEventDestroy(ev);
+      return fail(nullptr, {SGDG_ECUDA, "batch: ordering after the caller's stream"});
+    }
+    cudaEventDestroy(ev);
+  }
   Status st = run_all(b->cap);
   if (st.code) return fail(nullptr, st);
   if (cudaStreamSynchronize(b->cap) != cudaSuccess) return fail(nullptr, {SGDG_ECUDA, "batch eager apply"});
@@ -1147,6 +1212,18 @@ sgdg_status sgdg_batch_advance(void* bp, sgdg_strip_stats* per_member) {
   std::vector<Status> res(n);
   std::vector<sgdg_strip_stats> st(n);
   std::vector<std::thread> th;
+  // the members run on streams of their own: finish the callers' work first
+  {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    std::vector<int> devs;
+    for (size_t k = 0; k < n; ++k)
+      if (std::find(devs.begin(), devs.end(), b->m[k]->cfg.device) == devs.end()) devs.push_back(b->m[k]->cfg.device);
+    for (int d : devs)
+      if (cudaSetDevice(d) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return fail(nullptr, {SGDG_ECUDA, "batch advance: synchronising a member's device"});
+    cudaSetDevice(cur);
+  }
   for (size_t k = 0; k < n; ++k) {
     th.emplace_back([&, k]() {
       Handle& h = *b->m[k];

@@ -57,6 +57,10 @@ struct SideDev {
   std::vector<int> lat_nx;
   std::vector<std::vector<int>> lat_pos;
   bool lattice_ok = false;            // look for lattice levels (the x side)
+  // lat_E[l] (l >= 1): levels l and l - 1 are lattices and E_{l <- l-1} is
+  // the P1 prolongation of the lattice (1 at coarse vertices, 1/2 + 1/2 at
+  // the midpoints of row, column and (1, 1)-diagonal edges)
+  std::vector<char> lat_E;
   SideValues<double> v64;
   SideValues<float> v32;
   template <typename T> SideValues<T>& vals();

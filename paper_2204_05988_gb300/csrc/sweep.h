@@ -92,6 +92,7 @@ struct ChainArgs {
   const Comp<T>* p_val = nullptr;
   const Store<T>* Z[kChainSlots] = {};  // the Q inputs
   Store<T>* out[kChainSlots] = {};
+  int lat_nx = 0;   // mode A on a 2-D lattice x level (and, with has_prev, a lattice level below)
 };
 
 // y (+)= sum_c sum_{t in c} tau_t (x) F_t in_c on one (n1 x n2) grid, all F_t
@@ -175,5 +176,10 @@ cudaError_t launch_final(FinalArgs<T>& a, bool left, cudaStream_t s);
 // 4 vertices per thread, else 8
 template <typename T>
 cudaError_t launch_final_lattice(FinalArgs<T>& a, cudaStream_t s);
+// mode-A chain step on a 2-D lattice x level (sweep_lattice.cu; FP32 and BF16
+// storage): a.row == 7, a.lat_nx = vertices per lattice row, a.ch <= 2: runs
+// of 2 vertices per thread, else 4
+template <typename T>
+cudaError_t launch_chain_lattice(ChainArgs<T>& a, cudaStream_t s);
 
 }  // namespace sgdg

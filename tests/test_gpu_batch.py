@@ -96,13 +96,15 @@ def test_autotune_keeps_results(P, prec):
 
 _SHAPES = [ch | tiled << 4 | pair << 5 | pf << 6
            for pf in (0, 1) for pair in (0, 1) for tiled in (0, 1) for ch in (1, 2, 3, 4, 8)]
+_SHAPES += [ch | 1 << 7 for ch in (1, 2, 3, 4, 8)]   # the lattice kernels (2-D lattice x levels)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 @pytest.mark.parametrize("case", ["d2_L4", "d1_L6"])
 def test_every_launch_shape_gives_the_same_values(P, prec, case):
     """Every launch shape the autotuner can pick (rows per thread, block
-    order, paired outputs, L2 prefetch hints), and a ragged rows-per-thread,
+    order, paired outputs, L2 prefetch hints, lattice kernels), and a ragged
+    rows-per-thread,
     pinned on all sites at once:
     the values are those of the default shapes, bit for bit, and match the
     oracle."""
