@@ -118,9 +118,13 @@ def full_matrix(prob, Lx: int, Lv: int, q: int = 4, t0: float = 0.0) -> np.ndarr
             Wop = (np.einsum("st,xvab->txvsab", et, phi)
                    + dl * (np.einsum("st,xvab->txvsab", ed, phi) + np.einsum("st,txvab->txvsab", et, bg)))
             wts = tw[:, None, None] * W[None]
-            loc = np.einsum("txv,txvsab,txvSAB->abSABs", wts, Wop, Lop)
-            # loc[a, b, S, A, B, s]: test (a, b, s) x trial (A, B, S) -> reorder to (a,b,s),(A,B,S)
-            loc = np.transpose(loc, (0, 1, 5, 3, 4, 2)).reshape(d1 * d1 * R, d1 * d1 * R)
+            # sum over the quadrature points (t, x, v) of wts * Wop[s, a, b] * Lop[S, A, B]: a
+            # matrix product over the points, rows test (s, a, b), columns trial (S, A, B)
+            npt = wts.size
+            Wm = Wop.reshape(npt, R * d1 * d1) * wts.reshape(npt, 1)
+            loc = Wm.T @ Lop.reshape(npt, R * d1 * d1)
+            # reorder to test (a, b, s) x trial (A, B, S), the dof order
+            loc = loc.reshape(R, d1, d1, R, d1, d1).transpose(1, 2, 0, 4, 5, 3).reshape(d1 * d1 * R, d1 * d1 * R)
             idx = dofs(cx, cv)
             A[np.ix_(idx, idx)] += loc
 
@@ -193,8 +197,8 @@ def energy_terms(prob, Lx: int, Lv: int, u: np.ndarray, q: int = 4) -> float:
             B = _beta(prob, px[cx], pv[cv])
             W = np.outer(wx[cx], wv[cv])
             val = np.einsum("xa,vb,abs->xvs", lamx, lamv, Uc)         # spatial value per time coef
-            dxv = np.einsum("pxv,ap,vb,abs->xvs", B[:d], gx[cx], lamv, Uc)
-            dvv = np.einsum("pxv,bp,xa,abs->xvs", B[d:], gv[cv], lamx, Uc)
+            dxv = np.einsum("pxv,ap,vb,abs->xvs", B[:d], gx[cx], lamv, Uc, optimize=True)
+            dvv = np.einsum("pxv,bp,xa,abs->xvs", B[d:], gv[cv], lamx, Uc, optimize=True)
             bgrad = dxv + dvv
             # d_t v + d_beta v at time points
             res = np.einsum("st,xvs->txv", ed, val) + np.einsum("st,xvs->txv", et, bgrad)
