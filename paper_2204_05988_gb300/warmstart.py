@@ -4,9 +4,9 @@ Non-learned guesses for strip j (kept as the fallback): the previous strip's
 solution u_{j-1} (warm start 1) and its linear extrapolation
 g_j = 2 u_{j-1} - u_{j-2} (warm start 3).  The learned guess adds a coarse
 correction to g_j: a 3-layer MLP (the library's BF16 tensor-core kernels)
-maps coarse features - the values of the end value U^-_{j-1} and of the last
-change u_{j-1} - u_{j-2} at the nodes of the coarse full grid (lx, lv) - to
-the values there of u_j - g_j (both time coefficients); the prediction is
+maps coarse features - the values of the last change u_{j-1} - u_{j-2} at
+the nodes of the coarse full grid (lx, lv), both time coefficients - to the
+values there of u_j - g_j (both time coefficients); the prediction is
 added to g_j as a P1 function on component grid (lx, L-lx).  Every step runs
 in the library: coarse views (sgdg_coarse_values / sgdg_add_coarse), the
 extrapolation (sgdg_extrapolated_guess), the network (sgdg_mlp_*) and the
@@ -42,17 +42,17 @@ def _solver(prob, kw):
 
 
 def features(solver: Solver, lx: int, lv: int, g):
-    """[coarse U^-_{j-1} (nx nv), coarse (g - u_{j-1}) (nx nv 2)] for the next
-    strip, g the extrapolated guess (g - u_{j-1} = u_{j-1} - u_{j-2})."""
+    """coarse (g - u_{j-1}) (nx nv 2) for the next strip, g the extrapolated
+    guess (g - u_{j-1} = u_{j-1} - u_{j-2}, the last change).  The end value
+    U^-_{j-1} itself is left out: it is dominated by the part of the state
+    that does not change (the Maxwellian of the Landau problem), which a
+    single input scale would let swamp the changes."""
     import torch
     nx, nv = coarse_dims(solver, lx, lv)
-    U = torch.empty(solver.n_spatial, dtype=torch.float64, device="cuda")
-    solver.get_end_value(U, on_device=True)
     u = torch.empty(solver.n_coeffs, dtype=torch.float64, device="cuda")
     solver.get_solution(u, on_device=True)
-    f = torch.empty(nx * nv * 3, dtype=torch.float64, device="cuda")
-    solver.coarse_values(U, 1, lx, lv, f[: nx * nv])
-    solver.coarse_diff(g, u, 2, lx, lv, f[nx * nv:])
+    f = torch.empty(nx * nv * 2, dtype=torch.float64, device="cuda")
+    solver.coarse_diff(g, u, 2, lx, lv, f)
     return f
 
 
