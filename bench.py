@@ -294,7 +294,8 @@ def main():
     ap.add_argument("--strip-L", type=int, default=9, help="level of the strip-solve timing (-1: skip)")
     ap.add_argument("--strips-mixed", type=int, default=3, help="mixed-precision strips solved")
     ap.add_argument("--strips-fp64", type=int, default=2, help="plain FP64 strips solved")
-    ap.add_argument("--inner-its", type=int, default=48, help="GMRES steps per component solve (strips)")
+    ap.add_argument("--inner-its", type=int, default=24, help="GMRES steps per component solve (strips)")
+    ap.add_argument("--inner-rtol", type=float, default=1e-2, help="early stop of a component solve (strips)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=8, help="instances in the batched strip measurement (0: skip)")
     ap.add_argument("--batch-levels", type=int, nargs="+", default=[5, 6, 7])
@@ -567,14 +568,14 @@ def main():
     strip = None
     if args.strip_L >= 0:
         strip = {"workload": f"transport_2d d=2 L={args.strip_L} sigma=0.1 dt=1/64, rtol 1e-8, component solves "
-                             f"GMRES({args.inner_its}) to 1e-3, outer FGMRES(30); warm start: the previous solution "
+                             f"GMRES({args.inner_its}) to {args.inner_rtol:g}, outer FGMRES(30); warm start: the previous solution "
                              f"(strip 2), then the extrapolation of the last two (both arms)"}
         for nm, pr, ns in (("mixed", P.SGDG_MIXED_FP32, args.strips_mixed), ("fp64", P.SGDG_FP64, args.strips_fp64)):
             if ns <= 0:
                 continue
             ps = W.transport_2d(L=args.strip_L, sigma=0.1)
             t0 = time.perf_counter()
-            sv = P.Solver(ps, precision=pr, rtol=1e-8, restart=30, inner_its=args.inner_its, inner_rtol=1e-3,
+            sv = P.Solver(ps, precision=pr, rtol=1e-8, restart=30, inner_its=args.inner_its, inner_rtol=args.inner_rtol,
                           device=local)
             setup = time.perf_counter() - t0
             if pr == P.SGDG_MIXED_FP32:      # launch shapes of the FP32 applies the solve makes

@@ -310,6 +310,17 @@ sgdg_status sgdg_eval_nodal(void* h, const double* u, double* out, void* stream)
  * field_energy (may be NULL): 1/2 int |E|^2 dx of the new field.  Only for
  * handles created with vlasov_poisson = 1 (else EINVAL). */
 sgdg_status sgdg_field_update(void* h, int source, double* field_energy);
+/* A field given by the caller instead of the Poisson solve (Sect. 5.3 with
+ * E from elsewhere, e.g. an external field solver): E[k * n_cells + e] is
+ * component k (< d) of E on cell e of the finest level of Omega_x, in the
+ * order of sgdg_get_field, n_cells the count sgdg_finest_x reports (host
+ * array, copied).  Re-assembles every x factor that depends on E, like
+ * sgdg_field_update; later strips use it until the next field update.
+ * sgdg_get_field copies the current field out (host array of d n_cells).
+ * Only for vlasov_poisson handles; a wrong n_cells or a NaN/Inf value:
+ * SGDG_EINVAL. */
+sgdg_status sgdg_set_field(void* h, const double* E, int n_cells);
+sgdg_status sgdg_get_field(const void* h, double* E, int n_cells);
 /* Re-solve the last strip with the current coefficients (same right-hand
  * side), starting from its last solution; replaces the solution and the end
  * value.  One step of the per-strip fixed point of Sect. 5.3. */

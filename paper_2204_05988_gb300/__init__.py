@@ -110,6 +110,8 @@ EXPORTS = {
     "sgdg_extrapolated_guess": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sgdg_finest_x": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "sgdg_get_density_potential": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sgdg_set_field": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "sgdg_get_field": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "sgdg_coarse_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "sgdg_coarse_diff": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                    C.c_void_p]),
@@ -443,6 +445,19 @@ class Solver:
 
     def set_guess(self, u):
         self._check(self.lib.sgdg_set_guess(self.h, _ptr(u)))
+
+    def get_field(self) -> np.ndarray:
+        """E per finest x cell, shape (d, n_cells)."""
+        nv, nc = C.c_int(), C.c_int()
+        self._check(self.lib.sgdg_finest_x(self.h, C.byref(nv), C.byref(nc)))
+        E = np.empty((self.info.d, nc.value))
+        self._check(self.lib.sgdg_get_field(self.h, _ptr(E), nc.value))
+        return E
+
+    def set_field(self, E: np.ndarray):
+        """A caller-supplied field, shape (d, n_cells) per finest x cell."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        self._check(self.lib.sgdg_set_field(self.h, _ptr(E), E.shape[-1]))
 
     def density_potential(self):
         nv, nc = C.c_int(), C.c_int()

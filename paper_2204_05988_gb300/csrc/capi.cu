@@ -1293,6 +1293,20 @@ sgdg_status sgdg_field_update(void* hp, int source, double* energy) {
   return st.code ? fail(h, st) : SGDG_OK;
 }
 
+sgdg_status sgdg_set_field(void* hp, const double* E, int n_cells) {
+  if (!hp) return SGDG_EINVAL;
+  Handle* h = (Handle*)hp;
+  Status st = field_set(*h, E, n_cells);
+  return st.code ? fail(h, st) : SGDG_OK;
+}
+
+sgdg_status sgdg_get_field(const void* hp, double* E, int n_cells) {
+  if (!hp) return SGDG_EINVAL;
+  const Handle* h = (const Handle*)hp;
+  Status st = field_get(*h, E, n_cells);
+  return st.code ? fail(const_cast<Handle*>(h), st) : SGDG_OK;
+}
+
 sgdg_status sgdg_coarse_values(void* hp, const double* u, int R, int lx, int lv, double* out, void* stream) {
   if (!hp || !u || !out) return SGDG_EINVAL;
   Handle* h = (Handle*)hp;

@@ -234,6 +234,28 @@ Status field_update(Handle& h, int source, double* energy) {
   return field_reassemble(h);
 }
 
+Status field_set(Handle& h, const double* E, int n_cells) {
+  if (!h.field) return {SGDG_EINVAL, "the handle was not created with vlasov_poisson = 1"};
+  Handle::Field& F = *h.field;
+  const int d = h.d, nc = F.hx.lev[h.L].ncells(d);
+  if (!E || n_cells != nc) return {SGDG_EINVAL, "set_field: n_cells differs from the finest x cell count"};
+  for (int k = 0; k < d; ++k)
+    for (int e = 0; e < nc; ++e)
+      if (!std::isfinite(E[(size_t)k * nc + e])) return {SGDG_EINVAL, "set_field: NaN or Inf in the field"};
+  for (int k = 0; k < d; ++k) F.E[k].assign(E + (size_t)k * nc, E + (size_t)(k + 1) * nc);
+  F.updated = true;
+  return field_reassemble(h);
+}
+
+Status field_get(const Handle& h, double* E, int n_cells) {
+  if (!h.field) return {SGDG_EINVAL, "the handle was not created with vlasov_poisson = 1"};
+  const Handle::Field& F = *h.field;
+  const int d = h.d, nc = F.hx.lev[h.L].ncells(d);
+  if (!E || n_cells != nc) return {SGDG_EINVAL, "get_field: n_cells differs from the finest x cell count"};
+  for (int k = 0; k < d; ++k) std::copy(F.E[k].begin(), F.E[k].end(), E + (size_t)k * nc);
+  return {};
+}
+
 // Re-assemble and upload every x factor whose weight or inflow split uses E,
 // from the current cell field F.E.
 Status field_reassemble(Handle& h) {

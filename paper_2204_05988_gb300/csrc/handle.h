@@ -254,6 +254,9 @@ Status field_setup(Handle& h, const sgdg_coeffs& c, const Hierarchy& hx, const H
 Status fused_plan(Handle& h, int i, int pair_bytes, int nchains, int nterms, const Handle::FusedGrid** out);
 Status field_update(Handle& h, int source, double* energy);
 Status field_reassemble(Handle& h);
+// caller-supplied field: E[k * n_cells + e] = component k on finest x cell e
+Status field_set(Handle& h, const double* E, int n_cells);
+Status field_get(const Handle& h, double* E, int n_cells);
 
 // coarse full-grid views (coarse.cu)
 Status coarse_values(Handle& h, const double* u, int R, int lx, int lv, double* out, cudaStream_t s);

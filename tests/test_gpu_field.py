@@ -167,3 +167,36 @@ def test_h1_norm_matches_oracle():
         ref = h1_norm(op, u)
         assert abs(got - ref) < 1e-12 * ref, (got, ref)
         s.close()
+
+
+def test_caller_supplied_field():
+    """sgdg_set_field / sgdg_get_field: the field of the first update matches
+    the oracle's E (which also pins the finest cell order); a field given by
+    the caller (seeded values per finest cell) gives the oracle's operator
+    with that field installed, 1e-12 (FP64) relative; a wrong cell count is
+    rejected."""
+    import paper_2204_05988_gb300 as P
+    from oracle.field import density_u0, install_field, poisson
+    from oracle.operator import SparseGridOperator
+
+    prob_o = W.landau_4d(L=2, n_strips=1, dt=0.25)
+    op = SparseGridOperator(prob_o)
+    _, E0, _ = poisson(op, density_u0(op, prob_o))
+    s = P.Solver(W.landau_4d(L=2, n_strips=1, dt=0.25), vlasov_poisson=True)
+    s.set_initial()
+    s.field_update()
+    assert _rel(s.get_field(), E0) < 1e-9
+    E1 = np.random.default_rng(81).uniform(-1.0, 1.0, E0.shape)
+    s.set_field(E1)
+    assert np.array_equal(s.get_field(), E1)
+    install_field(op, prob_o, E1)
+    u = W.uniform_vector(op.size, seed=82)
+    ref = op.apply(u)
+    ud = torch.tensor(u, device="cuda")
+    yd = torch.full_like(ud, float("nan"))
+    s.apply_operator(ud, yd, P.SGDG_FP64)
+    torch.cuda.synchronize()
+    assert _rel(yd.cpu().numpy(), ref) < 1e-12
+    with pytest.raises(P.SgdgError):
+        s.set_field(E1[:, :-1])
+    s.close()
