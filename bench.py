@@ -294,8 +294,8 @@ def main():
     ap.add_argument("--strip-L", type=int, default=9, help="level of the strip-solve timing (-1: skip)")
     ap.add_argument("--strips-mixed", type=int, default=3, help="mixed-precision strips solved")
     ap.add_argument("--strips-fp64", type=int, default=2, help="plain FP64 strips solved")
-    ap.add_argument("--inner-its", type=int, default=24, help="GMRES steps per component solve (strips)")
-    ap.add_argument("--inner-rtol", type=float, default=1e-2, help="early stop of a component solve (strips)")
+    ap.add_argument("--inner-its", type=int, default=48, help="GMRES steps per component solve (strips)")
+    ap.add_argument("--inner-rtol", type=float, default=1e-3, help="early stop of a component solve (strips)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=8, help="instances in the batched strip measurement (0: skip)")
     ap.add_argument("--batch-levels", type=int, nargs="+", default=[5, 6, 7])
