@@ -153,8 +153,11 @@ typedef struct {
    * factor at every point.  Applies (operator, diagonal blocks, batch) use
    * the operator of the strip that starts at the handle's current time: 0
    * after sgdg_create and sgdg_set_initial, advanced by dt with every
-   * sgdg_advance_strip, restored by sgdg_restore.  Time factors are not
-   * combined with sources, inflow data or vlasov_poisson (EINVAL). */
+   * sgdg_advance_strip, restored by sgdg_restore.  In the right-hand side
+   * the streamline-diffusion part of a source and the inflow data carry the
+   * time factor of the beta component they involve (inflow parts gated by
+   * its sign), integrated by the 3-point Gauss rule of the sources.  Time
+   * factors are not combined with vlasov_poisson (EINVAL). */
   sgdg_tfn beta_t[6];
   void* beta_ut[6];
   sgdg_tfn sigma_t;

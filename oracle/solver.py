@@ -34,7 +34,7 @@ import scipy.sparse.linalg as spla
 
 from scipy import integrate
 
-from .assembly import Factor, assemble_load, assemble_load_grad
+from .assembly import Factor, assemble_load, assemble_load_grad, gauss01
 from .operator import SparseGridOperator, eta, eta_at, is_time_dependent, time_matrices
 
 
@@ -235,7 +235,10 @@ class StripSolver:
             for c, b in enumerate(prob.beta):
                 if b.coef == 0.0:
                     continue
-                terms.append((src.coef * b.coef * dl * w_val, mul(src.fx, b.fx), mul(src.fv, b.fv),
+                # a time factor of beta_c enters the integrand: the strip's
+                # 3-point Gauss rule, like the operator's time couplings
+                wb = w_val if getattr(b, "ft", None) is None else self._gauss_weights(t0, ft, b.ft)
+                terms.append((src.coef * b.coef * dl * wb, mul(src.fx, b.fx), mul(src.fv, b.fv),
                               c if c < d else -1, c - d if c >= d else -1))
         off = 0
         for (l1, l2) in op.grids:
@@ -247,6 +250,21 @@ class StripSolver:
                 blk += np.einsum("i,j,s->ijs", op.fx.embed(l1).T @ Fx, op.fv.embed(l2).T @ Fv, wt)
             out[off:off + blk.size] = blk.ravel()
             off += blk.size
+        return out
+
+    def _gauss_weights(self, t0: float, ft, bt, gate=None) -> np.ndarray:
+        """[int_I ft(t) bt(t) [gate(t)] eta_s(t) dt]_s by the 3-point Gauss rule
+        on the strip (t0, t0 + dt); gate(t) in {0, 1} selects the times where an
+        inflow part is active."""
+        R, dt = self.op.R, self.prob.dt
+        tq, wq = gauss01(3)
+        out = np.zeros(R)
+        for q in range(3):
+            t = t0 + tq[q] * dt
+            g = ft(t) * float(np.asarray(bt(np.array([t])))[0])
+            if gate is not None:
+                g *= gate(t)
+            out += wq[q] * dt * g * np.array([eta(s, tq[q:q + 1], dt)[0][0] for s in range(R)])
         return out
 
     def inflow_rhs(self, t0: float) -> np.ndarray:
@@ -275,10 +293,23 @@ class StripSolver:
             for p, b in enumerate(prob.beta):
                 if b.coef == 0.0:
                     continue
-                for side in (-1, +1):
+                bt = getattr(b, "ft", None)
+                # with a time factor tp of beta_p: both signs sc of coef tp(t)
+                # give parts, each active where it holds, weighted by tp (the
+                # strip's 3-point Gauss rule, like the operator's inflow term)
+                for sc in ((+1, -1) if bt is not None else (None,)):
+                  for side in (-1, +1):
                     for s1 in (+1, -1):
                         s2 = -side * s1
-                        rx = ((fn(b.fx), b.coef, s1),)
+                        if sc is None:
+                            wpart = wt
+                            rx = ((fn(b.fx), b.coef, s1),)
+                        else:
+                            gate = (lambda t, sc=sc, bt=bt, c=b.coef:
+                                    1.0 if sc * c * float(np.asarray(bt(np.array([t])))[0]) > 0 else 0.0)
+                            wpart = -src.coef * self._gauss_weights(t0, gt, bt, gate)
+                            # b.coef tp(t) fx(x) has sign s1 where fx has sign s1 sc
+                            rx = ((fn(b.fx), sc, s1),)
                         rv = ((fn(b.fv), 1.0, s2),)
                         if p < d:
                             if prob.mesh_x.periodic[p]:
@@ -290,7 +321,7 @@ class StripSolver:
                                 continue
                             X = Factor("vol", side * b.coef, w(b.fx) + w(src.fx), restrict=rx)
                             V = Factor("face", 1.0, w(b.fv) + w(src.fv), restrict=rv, face=(p - d, side))
-                        terms.append((wt, X, V))
+                        terms.append((wpart, X, V))
         loads = [(wt, op.fx.fine(X) @ np.ones(op.fx.fine(X).shape[1]), op.fv.fine(V) @ np.ones(op.fv.fine(V).shape[1]))
                  for wt, X, V in terms]
         off = 0
@@ -304,8 +335,6 @@ class StripSolver:
         return out
 
     def rhs(self, MU: np.ndarray, t0: float = 0.0) -> np.ndarray:
-        if is_time_dependent(self.prob) and (self.prob.f or self.prob.g):
-            raise NotImplementedError("sources and inflow data with time-dependent beta or sigma")
         return np.outer(MU, self.e_start).ravel() + self.source_rhs(t0) + self.inflow_rhs(t0)
 
     def endpoint(self, u: np.ndarray) -> np.ndarray:

@@ -375,9 +375,8 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   {
     bool timed = c.sigma_t != nullptr;
     for (int p = 0; p < 2 * cfg.mesh_x.dim && p < 2 * kMaxDim; ++p) timed = timed || c.beta_t[p] != nullptr;
-    if (timed && (c.n_f > 0 || c.n_g > 0 || cfg.vlasov_poisson))
-      return {SGDG_EINVAL, "time factors of beta or sigma are not combined with sources, inflow data or "
-                           "vlasov_poisson"};
+    if (timed && cfg.vlasov_poisson)
+      return {SGDG_EINVAL, "time factors of beta or sigma are not combined with vlasov_poisson"};
     if (c.time_quad < 0 || c.time_quad > 8) return {SGDG_EINVAL, "time_quad must be in 0..8"};
   }
   h.cfg = cfg;
@@ -617,6 +616,7 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
         tb.src = k;
         tb.kind = 1;
         tb.coef = f.coef * b.coef;
+        if (c.beta_t[comp]) tb.tfn = comp;
         SG_ST(load_vectors_w(hx, {{f.fx, f.ux}, {b.fx, b.ux}}, comp < h.d ? comp + 1 : 0, lx));
         SG_ST(load_vectors_w(hv, {{f.fv, f.uv}, {b.fv, b.uv}}, comp >= h.d ? comp - h.d + 1 : 0, lv));
         SG_ST(upload_levels(lx, tb.lx));
@@ -632,7 +632,7 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   if (c.n_g > 0) {
     if (cfg.vlasov_poisson) return {SGDG_EINVAL, "inflow data are not combined with vlasov_poisson"};
     if (!c.g) return {SGDG_EINVAL, "n_g > 0 with a NULL inflow array"};
-    const std::vector<InflowPart> parts = inflow_parts(c, h.d, cfg.mesh_x, cfg.mesh_v);
+    const std::vector<InflowPart> parts = inflow_parts(c, h.d, cfg.mesh_x, cfg.mesh_v, true);
     auto row_sums = [](const std::vector<Csr>& X, std::vector<std::vector<double>>& out) {
       out.assign(X.size(), {});
       for (size_t l = 0; l < X.size(); ++l) {
@@ -663,6 +663,11 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
         t.src = src;
         t.kind = 2;
         t.coef = g.coef * ip.scale;
+        if (ip.gate_fn >= 0) {
+          t.tfn = t.gate_fn = ip.gate_fn;
+          t.gate_sign = ip.gate_sign;
+          t.gate_coef = c.beta[ip.gate_fn].coef;
+        }
         t.lx.assign(lx.size(), nullptr);
         t.lv.assign(lv.size(), nullptr);
         for (size_t l = 0; l < lx.size(); ++l) SG_ST(upload(h, &t.lx[l], lx[l].data(), lx[l].size()));

@@ -115,7 +115,16 @@ struct Handle {
   // and v load vectors per level (device) and which time weight scales them:
   // kind 0 - int ft eta_s + delta int ft eta_s',  kind 1 - delta int ft eta_s,
   // kind 2 - minus int gt eta_s (inflow data on Gamma^-)
-  struct SourceTerm { int src = 0, kind = 0; double coef = 0.0; std::vector<double*> lx, lv; };
+  // one Kronecker term of the source or inflow data; tfn: time factor of a
+  // beta component (coef_t id) in the integrand, -1 none; gate_*: an inflow
+  // part active where sign(gate_coef factor(t)) == gate_sign (Sect. 4.2)
+  struct SourceTerm {
+    int src = 0, kind = 0;
+    double coef = 0.0;
+    std::vector<double*> lx, lv;
+    int tfn = -1, gate_fn = -1, gate_sign = 0;
+    double gate_coef = 0.0;
+  };
   std::vector<SourceTerm> src_terms;
   std::vector<std::pair<sgdg_tfn, void*>> src_t;   // time factor per source
   double t_now = 0.0;                              // start of the next strip

@@ -840,10 +840,12 @@ Status ct_precondition(Handle& h, const double* r, double* z, cudaStream_t s, in
 }
 
 // rhs += the source and inflow parts of b_j (Sect. 2) on the strip
-// [t_now, t_now + dt]: per source (or inflow datum) k the time weights
-//   e1_s = int_I ft_k eta_s dt,   e0_s = e1_s + delta int_I ft_k eta_s' dt
-// by 3-point Gauss-Legendre (exact for ft of degree <= 4), then every
-// Kronecker term of the source on every grid.
+// [t_now, t_now + dt]: per Kronecker term the time weights
+//   e1_s = int_I g eta_s dt,   e0_s = e1_s + delta int_I g eta_s' dt
+// by 3-point Gauss-Legendre (exact for g of degree <= 4), g the source's
+// (or inflow datum's) time factor times, for the SD and inflow terms, the
+// time factor of the beta component they carry, with an inflow part's gate
+// (Sect. 4.2); then every term on every grid.
 static Status add_source(Handle& h, cudaStream_t s) {
   if (h.src_terms.empty()) return {};
   const double dt = h.cfg.dt, ta = h.t_now, dl = h.cfg.delta;
@@ -851,29 +853,32 @@ static Status add_source(Handle& h, cudaStream_t s) {
   const double wz[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
   double tq[3];
   for (int q = 0; q < 3; ++q) tq[q] = ta + 0.5 * dt * (1.0 + z[q]);
-  const size_t ns = h.src_t.size();
-  std::vector<double> e0(2 * ns), e1(2 * ns);
-  for (size_t k = 0; k < ns; ++k) {
-    double fq[3] = {1.0, 1.0, 1.0};
-    if (h.src_t[k].first) h.src_t[k].first(3, tq, fq, h.src_t[k].second);
-    double a0 = 0.0, a1 = 0.0, d1 = 0.0;   // int ft eta_0, int ft eta_1, int ft eta_1'
+  const size_t ns = h.src_t.size(), nc = h.coef_t.size();
+  std::vector<double> fq(3 * ns, 1.0), cq(3 * nc, 1.0);
+  for (size_t k = 0; k < ns; ++k)
+    if (h.src_t[k].first) h.src_t[k].first(3, tq, &fq[3 * k], h.src_t[k].second);
+  for (size_t k = 0; k < nc; ++k)
+    if (h.coef_t[k].first) {
+      h.coef_t[k].first(3, tq, &cq[3 * k], h.coef_t[k].second);
+      for (int q = 0; q < 3; ++q)
+        if (!std::isfinite(cq[3 * k + q])) return {SGDG_EINVAL, "a time factor returned NaN or Inf"};
+    }
+  for (const Handle::SourceTerm& t : h.src_terms) {
+    double a0 = 0.0, a1 = 0.0, d1 = 0.0;   // int g eta_0, int g eta_1, int g eta_1'
     for (int q = 0; q < 3; ++q) {
-      const double w = 0.5 * dt * wz[q] * fq[q];
+      double g = fq[3 * t.src + q];
+      if (t.tfn >= 0) g *= cq[3 * t.tfn + q];
+      if (t.gate_fn >= 0 && !(t.gate_sign * t.gate_coef * cq[3 * t.gate_fn + q] > 0.0)) g = 0.0;
+      const double w = 0.5 * dt * wz[q] * g;
       a0 += w;                 // eta_0 = 1
       a1 += w * z[q];          // eta_1 = 2 (t - t_a) / dt - 1 = z
       d1 += w * 2.0 / dt;      // eta_1' = 2 / dt  (eta_0' = 0)
     }
-    e1[2 * k] = a0;
-    e1[2 * k + 1] = a1;
-    e0[2 * k] = a0;
-    e0[2 * k + 1] = a1 + dl * d1;
-  }
-  for (const Handle::SourceTerm& t : h.src_terms) {
-    const double* e = t.kind == 0 ? &e0[2 * t.src] : &e1[2 * t.src];
+    const double e0 = a0, e1 = t.kind == 0 ? a1 + dl * d1 : a1;
     // kind 0: (f, w + delta d_t w); kind 1: delta (f, beta_c d_c w); kind 2: -<g, w>_{Gamma^-}
     const double sc = t.kind == 0 ? t.coef : (t.kind == 1 ? t.coef * dl : -t.coef);
     for (int l = 0; l <= h.L; ++l)
-      SG_CU(outer_add(h.rhs + h.off[l], h.n1[l], h.n2[l], t.lx[l], t.lv[h.L - l], sc * e[0], sc * e[1], s));
+      SG_CU(outer_add(h.rhs + h.off[l], h.n1[l], h.n2[l], t.lx[l], t.lv[h.L - l], sc * e0, sc * e1, s));
   }
   return {};
 }

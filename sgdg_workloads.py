@@ -382,6 +382,35 @@ def inflow_manufactured_1d(L: int = 3, sigma: float = 0.3, dt: float = 1.0 / 8.0
                    u0=[Product(c0, X, V)], exact=exact, f=f, g=[Source(1.0, X, V, a)])
 
 
+def inflow_time_dependent_1d(L: int = 3, sigma: float = 0.3, dt: float = 1.0 / 8.0, n_strips: int = 4,
+                             c0: float = 1.0, c1: float = 0.5) -> Problem:
+    """The inflow_manufactured_1d solution u* = (c0 + c1 t)(1 + x)(1 + v/2)
+    with a field that changes sign in time: beta = (v, (1 - 3t)(x - 1/2))
+    (sign change at t = 1/3, inside the third strip of dt = 1/8), so the
+    inflow part of the v-boundary moves between the two halves of the x
+    range within a strip.  f = d_t u* + beta . grad u* + sigma u* as
+    separable terms with polynomial time factors, g = u* on Gamma^-(t)."""
+    X = lambda p: 1.0 + p[:, 0]
+    V = lambda p: 1.0 + 0.5 * p[:, 0]
+    vV = lambda p: p[:, 0] * V(p)
+    eX = lambda p: (p[:, 0] - 0.5) * X(p)
+    a = lambda t: c0 + c1 * np.asarray(t)
+    da = lambda t: c1 + 0.0 * np.asarray(t)
+    e = lambda t: 1.0 - 3.0 * np.asarray(t)
+
+    def exact(t, x, v):
+        return (c0 + c1 * t) * (1.0 + x) * (1.0 + 0.5 * v)
+
+    f = [Source(1.0, X, V, da), Source(sigma, X, V, a), Source(1.0, None, vV, a),
+         Source(0.5, eX, None, lambda t: e(t) * a(t))]
+    h = 1.0 / (4 * 2 ** L)
+    return Problem(name=f"inflow_time_dependent_1d_L{L}", d=1, mesh_x=interval_mesh(0.0, 1.0, 4),
+                   mesh_v=interval_mesh(-1.0, 1.0, 4), L=L, r=1, dt=dt, delta=h, n_strips=n_strips,
+                   beta=[Product(1.0, None, lambda p: p[:, 0]), Product(1.0, lambda p: p[:, 0] - 0.5, None, e)],
+                   sigma=Product(sigma) if sigma != 0.0 else Product(0.0),
+                   u0=[Product(c0, X, V)], exact=exact, f=f, g=[Source(1.0, X, V, a)])
+
+
 def inflow_manufactured_2d(L: int = 2, sigma: float = 0.2, dt: float = 1.0 / 8.0, n_strips: int = 2,
                            c0: float = 1.0, c1: float = -0.4) -> Problem:
     """d=2 analogue on [0,1]^2 x [-1,1]^2: u* = (c0 + c1 t)(1 + x1 + 2 x2)

@@ -132,8 +132,36 @@ def test_batch_graph_recaptures_when_the_time_moves(P):
     b.close()
 
 
-def test_time_factors_with_sources_are_rejected(P):
-    prob = W.inflow_manufactured_1d(L=2)
-    prob.beta[1] = W.Product(1.0, lambda p: p[:, 0] - 0.5, None, lambda t: np.cos(np.asarray(t)))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_time_dependent_inflow_and_sources(P, prec):
+    """Sources and inflow data with a time factor in beta (beta_v changes sign
+    at t = 1/3, inside the third strip): strip solutions against the oracle
+    at 1e-8, and the manufactured solution reproduced at every node."""
+    from oracle.solver import StripSolver, nodal_values
+    prob = W.inflow_time_dependent_1d(L=3)
+    ref = StripSolver(prob, tol=1e-12)
+    ends = ref.run()
+    s = P.Solver(prob, precision=P.SGDG_FP64 if prec == "fp64" else P.SGDG_MIXED_FP32, rtol=1e-11,
+                 restart=30, inner_its=30, inner_rtol=1e-4)
+    s.set_initial()
+    for j in range(prob.n_strips):
+        st = s.advance_strip()
+        assert st.status == 0 and st.rel_residual <= 1e-11, j
+        U = np.empty(s.n_spatial)
+        s.get_end_value(U, on_device=False)
+        got = nodal_values(ref.op, U, R=1)
+        assert _rel(got, nodal_values(ref.op, ends[j], R=1)) < 1e-8, j
+        exact = []
+        for (l1, l2) in ref.op.grids:
+            x, v = ref.op.hx.levels[l1].coords[:, 0], ref.op.hv.levels[l2].coords[:, 0]
+            exact.append(prob.exact((j + 1) * prob.dt, x[:, None], v[None, :]).ravel())
+        exact = np.concatenate(exact)
+        assert np.abs(got - exact).max() < 1e-8 * np.abs(exact).max(), j
+    s.close()
+
+
+def test_time_factors_with_vlasov_poisson_are_rejected(P):
+    prob = W.landau_4d(L=2)
+    prob.sigma = W.Product(0.1, None, None, lambda t: 1.0 + np.asarray(t))
     with pytest.raises(P.SgdgError):
-        P.Solver(prob)
+        P.Solver(prob, vlasov_poisson=True)
