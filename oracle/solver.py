@@ -95,13 +95,17 @@ def fgmres(A, b, M=None, x0=None, tol=1e-10, restart=30, maxiter=1000):
 
 
 class ComponentSolver:
-    """GMRES on A_{l,l} with the (T_t + d C_t + G_t) (x) M (x) M preconditioner."""
+    """The inverse of one component operator A_{l,l} (Algorithm 1): a sparse
+    LU factorisation of the assembled block sum_k X_k (x) V_k (x) tau_k when it
+    has at most ``direct_max`` unknowns, else GMRES to ``tol`` with the
+    (T_t + d C_t + G_t) (x) M (x) M preconditioner."""
 
-    def __init__(self, op: SparseGridOperator, tol=1e-12, restart=60, maxiter=5000):
+    def __init__(self, op: SparseGridOperator, tol=1e-12, restart=60, maxiter=5000, direct_max=20000):
         self.op = op
         self.tol, self.restart, self.maxiter = tol, restart, maxiter
         Mt, Tt, Ct, Gt = time_matrices(op.prob.dt, op.prob.r)
         self.Pt_inv = np.linalg.inv(Tt + op.prob.delta * Ct + Gt)
+        self.direct_max = direct_max
         self._lu = {}
         self.iterations = []
 
@@ -123,9 +127,23 @@ class ComponentSolver:
         u = lu2.solve(t).reshape(n2, n1, R).transpose(1, 0, 2)
         return np.ascontiguousarray(u).ravel()
 
+    def block_matrix(self, l1, l2) -> sp.csc_matrix:
+        """A_{l,l} in the layout u[k1, k2, s] (row-major), from the operator's
+        current terms."""
+        op = self.op
+        A = None
+        for tau, X, V in op.terms:
+            K = sp.kron(op.fx.proj(X, l1, l1), sp.kron(op.fv.proj(V, l2, l2), sp.csr_matrix(tau)))
+            A = K if A is None else A + K
+        return A.tocsc()
+
     def solve(self, l1, l2, r):
         n1, n2 = self.op.grid_shape(l1, l2)
         R = self.op.R
+        if n1 * n2 * R <= self.direct_max:
+            x = spla.splu(self.block_matrix(l1, l2)).solve(r.ravel())
+            self.iterations.append(1)
+            return x.reshape(n1, n2, R)
         A = lambda x: self.op.apply_diag(l1, l2, x.reshape(n1, n2, R)).ravel()
         x, it, res, _ = fgmres(A, r.ravel(), lambda v: self.precond(l1, l2, v),
                                tol=self.tol, restart=self.restart, maxiter=self.maxiter)

@@ -34,6 +34,25 @@ def test_L0_ct_is_exact_inverse():
     assert s.outer_its == [1, 1]
 
 
+def test_component_direct_solve_equals_gmres():
+    """The assembled component block equals the blockwise apply_diag column
+    by column, and its LU solve equals the GMRES solve on the same block."""
+    prob = W.transport_2d(L=2, sigma=0.1)
+    op = SparseGridOperator(prob)
+    direct = ComponentSolver(op, tol=1e-13)
+    krylov = ComponentSolver(op, tol=1e-13, direct_max=0)
+    rng = np.random.default_rng(5)
+    for (l1, l2) in op.grids:
+        n1, n2 = op.grid_shape(l1, l2)
+        A = direct.block_matrix(l1, l2)
+        u = rng.uniform(-1, 1, (n1, n2, op.R))
+        assert np.abs(A @ u.ravel() - op.apply_diag(l1, l2, u).ravel()).max() < 1e-13 * np.abs(A).max()
+        r = rng.uniform(-1, 1, (n1, n2, op.R))
+        xd, xk = direct.solve(l1, l2, r), krylov.solve(l1, l2, r)
+        assert np.linalg.norm(xd - xk) < 1e-10 * np.linalg.norm(xd)
+    assert krylov.iterations and max(krylov.iterations) > 1
+
+
 def test_ct_restriction_from_either_parent():
     prob = W.transport_2d(L=3, sigma=0.1)
     op = SparseGridOperator(prob)
