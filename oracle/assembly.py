@@ -19,7 +19,9 @@ sign changes on mesh lines.
 
 Quadrature: Gauss-Legendre with q points per direction on [0,1], collapsed
 (Duffy) onto the simplex; exact for polynomial integrands of degree 2q-2 on
-triangles and 2q-1 on intervals.
+triangles and 2q-1 on intervals.  The basis is the Lagrange basis of the
+level's order (P1, or P2 for r = 2); P2 gradients vary inside a cell and are
+formed from the barycentric derivatives by the chain rule.
 
 Pinned by tests/test_oracle_assembly.py: mass row sums = int phi_k, total
 mass = |Omega|, Green's identity D_p + D_p^T = face masses (Sect. 3, proof of
@@ -34,7 +36,7 @@ from typing import Callable, Optional, Tuple
 import numpy as np
 import scipy.sparse as sp
 
-from .mesh import Hierarchy, Level
+from .mesh import Hierarchy, Level, lagrange_basis
 
 QUAD_Q = 4  # Gauss-Legendre points per collapsed direction
 
@@ -118,18 +120,23 @@ def assemble_level(lev: Level, f: Factor, q: int = QUAD_Q) -> sp.csr_matrix:
         pts = v0[:, None, :] + np.einsum("cij,qj->cqi", J, rp)      # (nc, nq, d)
         lam = np.concatenate([1.0 - rp.sum(axis=1, keepdims=True), rp], axis=1)  # (nq, d+1)
         gref = np.vstack([-np.ones((1, d)), np.eye(d)])              # (d+1, d)
-        gphys = np.einsum("cji,kj->cki", Jinv, gref)                 # (nc, d+1, d)
+        gphys = np.einsum("cji,kj->cki", Jinv, gref)                 # (nc, d+1, d): grad lam_k
         wt = _weight(f, pts.reshape(-1, d), rp.shape[0]).reshape(pts.shape[0], -1)
         wq = wt * rw[None, :] * det[:, None]                          # (nc, nq)
+        phi, dphi = lagrange_basis(lev.order, lam)                    # (nq, nloc), (nq, nloc, d+1)
+        nloc = phi.shape[1]
 
         def D(a):
             if a == 0:
-                return np.broadcast_to(lam[None, :, :], (cc.shape[0],) + lam.shape)
-            return np.broadcast_to(gphys[:, None, :, a - 1], (cc.shape[0], rp.shape[0], d1))
+                return np.broadcast_to(phi[None, :, :], (cc.shape[0],) + phi.shape)
+            if lev.order == 1:
+                return np.broadcast_to(gphys[:, None, :, a - 1], (cc.shape[0], rp.shape[0], d1))
+            # grad phi = sum_m (d phi / d lam_m) grad lam_m
+            return np.einsum("qam,cm->cqa", dphi, gphys[:, :, a - 1])
 
         Ke = np.einsum("cq,cqi,cqj->cij", wq, D(f.test), D(f.trial))
-        rows = np.repeat(cells, d1, axis=1).ravel()
-        cols = np.tile(cells, (1, d1)).ravel()
+        rows = np.repeat(cells, nloc, axis=1).ravel()
+        cols = np.tile(cells, (1, nloc)).ravel()
         return sp.coo_matrix((Ke.ravel(), (rows, cols)), shape=(n, n)).tocsr()
 
     # boundary faces on one side
@@ -152,9 +159,10 @@ def assemble_level(lev: Level, f: Factor, q: int = QUAD_Q) -> sp.csr_matrix:
     lam = np.concatenate([1.0 - rp.sum(axis=1, keepdims=True), rp], axis=1)   # (nq, dv)
     wt = _weight(f, pts.reshape(-1, d)).reshape(nf, -1)
     wq = wt * rw[None, :] * meas[:, None]
-    Ke = np.einsum("fq,qi,qj->fij", wq, lam, lam)
-    rows = np.repeat(faces, dv, axis=1).ravel()
-    cols = np.tile(faces, (1, dv)).ravel()
+    phi, _ = lagrange_basis(lev.order, lam)                                  # face basis (nq, nfloc)
+    Ke = np.einsum("fq,qi,qj->fij", wq, phi, phi)
+    rows = np.repeat(faces, phi.shape[1], axis=1).ravel()
+    cols = np.tile(faces, (1, phi.shape[1])).ravel()
     return sp.coo_matrix((Ke.ravel(), (rows, cols)), shape=(n, n)).tocsr()
 
 
@@ -210,8 +218,14 @@ def assemble_load_grad(lev: Level, fn, axis: int, q: int = QUAD_Q) -> np.ndarray
     rp, rw = simplex_rule(d, q)
     pts = v0[:, None, :] + np.einsum("cij,qj->cqi", J, rp)
     vals = fn(pts.reshape(-1, d)).reshape(nc, -1) if fn is not None else np.ones((nc, rp.shape[0]))
-    integ = np.einsum("cq,q,c->c", vals, rw, det)                  # int fn over the cell
-    fe = integ[:, None] * grad[:, :, axis]
+    if lev.order == 1:
+        integ = np.einsum("cq,q,c->c", vals, rw, det)              # int fn over the cell
+        fe = integ[:, None] * grad[:, :, axis]
+    else:
+        lam = np.concatenate([1.0 - rp.sum(axis=1, keepdims=True), rp], axis=1)
+        _, dphi = lagrange_basis(lev.order, lam)
+        G = np.einsum("qam,cm->cqa", dphi, grad[:, :, axis])        # d phi_a / dy_axis at the points
+        fe = np.einsum("cq,q,c,cqa->ca", vals, rw, det, G)
     out = np.zeros(lev.n)
     np.add.at(out, lev.cells.ravel(), fe.ravel())
     return out
@@ -227,8 +241,9 @@ def assemble_load(lev: Level, fn, q: int = QUAD_Q) -> np.ndarray:
     rp, rw = simplex_rule(d, q)
     pts = v0[:, None, :] + np.einsum("cij,qj->cqi", J, rp)
     lam = np.concatenate([1.0 - rp.sum(axis=1, keepdims=True), rp], axis=1)
+    phi, _ = lagrange_basis(lev.order, lam)
     vals = fn(pts.reshape(-1, d)).reshape(nc, -1) if fn is not None else np.ones((nc, rp.shape[0]))
-    fe = np.einsum("cq,q,c,qi->ci", vals, rw, det, lam)
+    fe = np.einsum("cq,q,c,qi->ci", vals, rw, det, phi)
     out = np.zeros(lev.n)
     np.add.at(out, lev.cells.ravel(), fe.ravel())
     return out

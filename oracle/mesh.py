@@ -38,10 +38,42 @@ class Level:
     bface_coords: np.ndarray  # (nf, d, d) geometric coords of the face vertices
     bface_axis: np.ndarray    # (nf,) axis of the outward normal
     bface_side: np.ndarray    # (nf,) -1 (lower bound) or +1 (upper bound)
+    order: int = 1            # polynomial order of the continuous Lagrange space
 
     @property
     def n(self) -> int:
         return self.coords.shape[0]
+
+
+def lagrange_nodes(k: int, order: int) -> np.ndarray:
+    """Barycentric coordinates (nloc, k) of the local nodes of the Lagrange
+    element of order 1 or 2 on a simplex with k vertices: the vertices, then
+    (order 2) the edge midpoints (i, j), i < j, in lexicographic order."""
+    rows = [np.eye(k)[i] for i in range(k)]
+    if order == 2:
+        rows += [0.5 * (np.eye(k)[i] + np.eye(k)[j]) for i in range(k) for j in range(i + 1, k)]
+    return np.array(rows)
+
+
+def lagrange_basis(order: int, lam: np.ndarray):
+    """Values phi (nq, nloc) and barycentric derivatives dphi (nq, nloc, k)
+    (d phi_a / d lam_m) of the Lagrange basis of order 1 or 2 at points with
+    barycentric coordinates lam (nq, k), nodes as in ``lagrange_nodes``.
+    Order 2: lam_i (2 lam_i - 1) at vertex i, 4 lam_i lam_j at edge (i, j)."""
+    nq, k = lam.shape
+    if order == 1:
+        return lam.copy(), np.broadcast_to(np.eye(k), (nq, k, k)).copy()
+    edges = [(i, j) for i in range(k) for j in range(i + 1, k)]
+    phi = np.empty((nq, k + len(edges)))
+    dphi = np.zeros((nq, k + len(edges), k))
+    for i in range(k):
+        phi[:, i] = lam[:, i] * (2.0 * lam[:, i] - 1.0)
+        dphi[:, i, i] = 4.0 * lam[:, i] - 1.0
+    for e, (i, j) in enumerate(edges):
+        phi[:, k + e] = 4.0 * lam[:, i] * lam[:, j]
+        dphi[:, k + e, i] = 4.0 * lam[:, j]
+        dphi[:, k + e, j] = 4.0 * lam[:, i]
+    return phi, dphi
 
 
 def _refine_raw(coords: np.ndarray, cells: np.ndarray):
@@ -199,3 +231,75 @@ class Hierarchy:
         for l in range(lc, lf):
             M = (self.E[l] @ M).tocsr()
         return M
+
+
+class P2Hierarchy(Hierarchy):
+    """Levels 0..L of continuous P2 spaces on the same meshes (Sect. 2 with
+    r = 2).  Uniform refinement puts the new vertices at the edge midpoints,
+    so the P2 nodes of level l are the vertices of level l + 1: a P1
+    hierarchy with L + 1 refinements supplies the node coordinates and their
+    canonical order.  Cells keep the geometry of level l and list their six
+    (d = 2) or three (d = 1) nodes in the order of ``lagrange_nodes``; the
+    embedding evaluates the coarse basis at the fine nodes, which in every
+    coarse cell are the points with barycentric coordinates in (1/4) Z."""
+
+    def __init__(self, mesh, L: int):
+        self.mesh = mesh
+        self.d = mesh.dim
+        self.L = L
+        self.p1 = Hierarchy(mesh, L + 1)
+        self._index = [self._node_index(self.p1.levels[l + 1].coords) for l in range(L + 1)]
+        self.levels: List[Level] = [self._p2_level(l) for l in range(L + 1)]
+        self.E: List[sp.csr_matrix] = [self._p2_embedding(l) for l in range(L)]
+
+    def _key(self, x: np.ndarray) -> tuple:
+        m = self.mesh
+        lo, hi = np.asarray(m.lo, dtype=np.float64), np.asarray(m.hi, dtype=np.float64)
+        y = np.array(x, dtype=np.float64)
+        for ax in range(self.d):
+            if m.periodic[ax] and y[ax] == hi[ax]:
+                y[ax] = lo[ax]
+        # box-relative coordinates on a 2^40 lattice: dyadic node positions
+        # are integers there, rounding absorbs the midpoints' last bits
+        return tuple(np.round((y - lo) / (hi - lo) * 2.0 ** 40).astype(np.int64).tolist())
+
+    def _node_index(self, coords: np.ndarray) -> Dict[tuple, int]:
+        return {self._key(x): i for i, x in enumerate(coords)}
+
+    def _lookup(self, l: int, pts: np.ndarray) -> np.ndarray:
+        idx = self._index[l]
+        flat = pts.reshape(-1, self.d)
+        return np.array([idx[self._key(x)] for x in flat], dtype=np.int64).reshape(pts.shape[:-1])
+
+    def _p2_level(self, l: int) -> Level:
+        geo = self.p1.levels[l]
+        k = self.d + 1
+        bary = lagrange_nodes(k, 2)
+        cells = self._lookup(l, np.einsum("ak,ckd->cad", bary, geo.cell_coords))
+        if geo.bface_coords.shape[0]:
+            fb = lagrange_nodes(self.d, 2)
+            bfaces = self._lookup(l, np.einsum("ak,fkd->fad", fb, geo.bface_coords))
+        else:
+            bfaces = np.zeros((0, lagrange_nodes(self.d, 2).shape[0]), dtype=np.int64)
+        return Level(coords=self.p1.levels[l + 1].coords, cells=cells, cell_coords=geo.cell_coords,
+                     bfaces=bfaces, bface_coords=geo.bface_coords, bface_axis=geo.bface_axis,
+                     bface_side=geo.bface_side, order=2)
+
+    def _p2_embedding(self, l: int) -> sp.csr_matrix:
+        """E_{l+1<-l}: the level-l P2 basis at the level-(l+1) P2 nodes."""
+        k = self.d + 1
+        coarse = self.levels[l]
+        ticks = [np.array(c) / 4.0 for c in np.ndindex(*([5] * k)) if sum(c) == 4]
+        lam = np.array(ticks)                                     # fine nodes of one coarse cell
+        phi, _ = lagrange_basis(2, lam)
+        fine = self._lookup(l + 1, np.einsum("pk,ckd->cpd", lam, coarse.cell_coords))   # (nc, np)
+        entries: Dict[Tuple[int, int], float] = {}
+        for c in range(coarse.cells.shape[0]):
+            for p in range(lam.shape[0]):
+                for a in range(phi.shape[1]):
+                    if phi[p, a] != 0.0:
+                        entries[(int(fine[c, p]), int(coarse.cells[c, a]))] = float(phi[p, a])
+        rows, cols = zip(*entries.keys())
+        E = sp.csr_matrix((list(entries.values()), (rows, cols)),
+                          shape=(self.levels[l + 1].n, coarse.n))
+        return E

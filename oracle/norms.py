@@ -24,8 +24,9 @@ full grid (L, L) (``full_grid_values``); on every pair of finest cells the
 collapsed Gauss rule of ``assembly.simplex_rule`` with q points per
 direction integrates the squared errors (polynomial parts exactly for q >= 2;
 the exact solution's contribution to the error to the rule's accuracy), and
-Gauss-Legendre with three points per strip integrates in time (the
-integrand d_t U + d_beta U is linear in t for r = 1).
+Gauss-Legendre with 2r + 1 points per strip integrates in time (the
+polynomial parts of the integrands have degree <= 2r in t).  The spatial
+basis is the Lagrange basis of the levels' order (P1, or P2 for r = 2).
 """
 from __future__ import annotations
 
@@ -33,6 +34,7 @@ import numpy as np
 
 from .assembly import Factor, gauss01
 from .brute import _cell_data
+from .mesh import lagrange_basis
 from .operator import eta
 from .solver import full_grid_values
 
@@ -45,8 +47,17 @@ def _products(prob, X, V, p):
     return b.coef * np.outer(fx, fv)
 
 
+def _cell_basis(lev, q):
+    """Quadrature points and weights per cell, the level's Lagrange basis at
+    the points (nq, nloc) and its gradients (nc, nq, nloc, d)."""
+    pts, w, lam, glam = _cell_data(lev, q)
+    phi, dphi = lagrange_basis(lev.order, lam)
+    grad = np.einsum("qam,cmd->cqad", dphi, glam)
+    return pts, w, phi, grad
+
+
 class _FullGrid:
-    """Point values and gradients of finest-full-grid P1 (x) P1 functions on
+    """Point values and gradients of finest-full-grid P_r (x) P_r functions on
     every (x cell, v cell) pair's quadrature points."""
 
     def __init__(self, op, q, periodic_only=True):
@@ -55,8 +66,8 @@ class _FullGrid:
         self.lx, self.lv = op.hx.levels[L], op.hv.levels[L]
         if periodic_only and any(len(lev.bfaces) for lev in (self.lx, self.lv)):
             raise NotImplementedError("SD-norm errors only on domains without boundary (periodic)")
-        self.px, self.wx, self.lamx, self.gx = _cell_data(self.lx, q)
-        self.pv, self.wv, self.lamv, self.gv = _cell_data(self.lv, q)
+        self.px, self.wx, self.lamx, self.gx = _cell_basis(self.lx, q)
+        self.pv, self.wv, self.lamv, self.gv = _cell_basis(self.lv, q)
         nx, nv = self.px.shape[0], self.pv.shape[0]
         q1, q2 = self.px.shape[1], self.pv.shape[1]
         self.shape = (nx, q1, nv, q2)
@@ -70,22 +81,16 @@ class _FullGrid:
         return full_grid_values(self.op, U)
 
     def value(self, F):
-        Fc = F[self.lx.cells][:, :, self.lv.cells]           # (nx, d+1, nv, d+1)
+        Fc = F[self.lx.cells][:, :, self.lv.cells]           # (nx, nloc, nv, nloc)
         return np.einsum("ia,xayb,jb->xiyj", self.lamx, Fc, self.lamv)
 
     def grad_x(self, F, axis):
         Fc = F[self.lx.cells][:, :, self.lv.cells]
-        gx = self.gx[:, :, axis]                              # (nx, d+1)
-        q1 = self.px.shape[1]
-        v = np.einsum("xa,xayb,jb->xyj", gx, Fc, self.lamv)
-        return np.broadcast_to(v[:, None, :, :], (v.shape[0], q1) + v.shape[1:])
+        return np.einsum("xia,xayb,jb->xiyj", self.gx[..., axis], Fc, self.lamv)
 
     def grad_v(self, F, axis):
         Fc = F[self.lx.cells][:, :, self.lv.cells]
-        gv = self.gv[:, :, axis]
-        q2 = self.pv.shape[1]
-        v = np.einsum("ia,xayb,yb->xiy", self.lamx, Fc, gv)
-        return np.broadcast_to(v[:, :, :, None], v.shape + (q2,))
+        return np.einsum("ia,xayb,yjb->xiyj", self.lamx, Fc, self.gv[..., axis])
 
     def exact(self, fn, t):
         """fn(t, x, v) on every quadrature point pair (d = 1: scalar coordinates)."""
@@ -107,8 +112,6 @@ def sd_norm_error(prob, op, strips, exact, q: int = 5):
     fastest), j = 1..N, on strips I_j = ((j-1) dt, j dt); exact(t, x, v):
     the exact solution of the homogeneous problem.  Returns (norm, parts),
     parts = dict of the squared contributions."""
-    if prob.r != 1:
-        raise NotImplementedError("time degree 1 only")
     fg = _FullGrid(op, q)
     d, dt, dl, R = prob.d, prob.dt, prob.delta, op.R
     sig = prob.sigma
@@ -118,7 +121,7 @@ def sd_norm_error(prob, op, strips, exact, q: int = 5):
         fv = sig.fv(fg.Vp) if sig.fv is not None else np.ones(fg.Vp.shape[0])
         sigma_pts = (sig.coef * np.outer(fx, fv)).reshape(fg.shape)
     beta_pts = [_products(prob, fg.Xp, fg.Vp, p).reshape(fg.shape) for p in range(2 * d)]
-    tq, tw = gauss01(3)
+    tq, tw = gauss01(2 * prob.r + 1)
     parts = {"sigma": 0.0, "streamline": 0.0, "jumps": 0.0, "initial": 0.0, "final": 0.0}
     prev_end = None
     N = len(strips)

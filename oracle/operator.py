@@ -37,7 +37,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from .assembly import Factor, FactorStore, gauss01
-from .mesh import Hierarchy
+from .mesh import Hierarchy, P2Hierarchy
 
 
 def ONE(p):
@@ -221,8 +221,9 @@ class SparseGridOperator:
         self.prob = prob
         self.L = prob.L
         self.R = prob.r + 1
-        self.hx = Hierarchy(prob.mesh_x, prob.L)
-        self.hv = Hierarchy(prob.mesh_v, prob.L)
+        H = P2Hierarchy if getattr(prob, "order", 1) == 2 else Hierarchy
+        self.hx = H(prob.mesh_x, prob.L)
+        self.hv = H(prob.mesh_v, prob.L)
         self.fx = FactorStore(self.hx)
         self.fv = FactorStore(self.hv)
         self.terms = kron_terms(prob)

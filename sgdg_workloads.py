@@ -81,6 +81,7 @@ class Problem:
     exact: Optional[Callable[[float, np.ndarray, np.ndarray], np.ndarray]] = None
     f: List[Source] = field(default_factory=list)   # source, sum of separable terms
     g: List[Source] = field(default_factory=list)   # inflow data on Gamma^-, sum of separable terms
+    order: int = 1              # polynomial order of the continuous spatial elements (P1, P2)
 
 
 # ----------------------------------------------------------------------------
@@ -193,7 +194,8 @@ def periodic_advection_1d(L: int, r: int = 1) -> Problem:
     """Sect. 5.1 (Eq. 25) with d = 1: beta = (1, 1) on the periodic unit
     square, u0 = sin(2 pi (x + v)); coarse meshes of 4 cells; 2^(L_paper+1)
     strips over one period T = 1/2; delta = finest edge length.  Here L is
-    0-based (L_paper = L + 1)."""
+    0-based (L_paper = L + 1).  r is the order of both the spatial elements
+    (P_r) and the time-DG polynomials, as in Table 1."""
     mx = interval_mesh(0.0, 1.0, 4, periodic=True)
     mv = interval_mesh(0.0, 1.0, 4, periodic=True)
     Lp = L + 1
@@ -207,9 +209,9 @@ def periodic_advection_1d(L: int, r: int = 1) -> Problem:
     def exact(t, x, v):
         return np.sin(2 * np.pi * (x + v - 2 * t))
 
-    return Problem(name=f"periodic_advection_1d_L{L}", d=1, mesh_x=mx, mesh_v=mv, L=L, r=r,
-                   dt=T / n_strips, delta=h, n_strips=n_strips,
-                   beta=[Product(1.0), Product(1.0)], sigma=Product(0.0), u0=u0, exact=exact)
+    return Problem(name=f"periodic_advection_1d_L{L}" + ("" if r == 1 else f"_r{r}"), d=1, mesh_x=mx, mesh_v=mv,
+                   L=L, r=r, dt=T / n_strips, delta=h, n_strips=n_strips,
+                   beta=[Product(1.0), Product(1.0)], sigma=Product(0.0), u0=u0, exact=exact, order=r)
 
 
 def transport_3d(L: int = 7, dt: float = 1.0 / 32.0, n_strips: int = 8) -> Problem:

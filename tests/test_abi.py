@@ -59,3 +59,12 @@ def test_binding_structs_match_the_library_layouts(lib):
     mine = [C.sizeof(t) for t in (P.Mesh, P.Product, P.Source, P.Coeffs, P.Config, P.Info, P.StripStats,
                                   P.KernelStat)]
     assert list(out) == mine
+
+
+def test_binding_rejects_p2_problems():
+    """The library's spaces are continuous P1; a problem asking for P2 (the
+    oracle's r = 2 path) is refused before anything reaches the device."""
+    import paper_2204_05988_gb300 as P
+    import sgdg_workloads as W
+    with pytest.raises(ValueError):
+        P.Solver(W.periodic_advection_1d(L=1, r=2))
