@@ -281,9 +281,27 @@ sgdg_status sgdg_ct_precondition(void* h, const double* r, double* z, void* stre
  * its strip state; later sgdg_advance_strip calls then give the results an
  * uninterrupted run gives, bit for bit (the solver's reductions are
  * deterministic).  Both synchronise the device.  File errors: SGDG_EIO.
- * sgdg_checkpoint needs sgdg_set_initial first (else SGDG_EINVAL). */
+ * sgdg_checkpoint needs sgdg_set_initial first (else SGDG_EINVAL).  The
+ * file ends with an FNV-1a 64 checksum of all bytes before it; sgdg_restore
+ * reads and checks the whole file on the host first (magic, sizes against
+ * the file length, checksum, nothing after it), so a truncated or corrupted
+ * file returns SGDG_EIO and leaves the handle's state unchanged. */
 sgdg_status sgdg_checkpoint(void* h, const char* path);
 sgdg_status sgdg_restore(void* h, const char* path);
+
+/* What a checkpoint file holds, read without a handle or a device. */
+typedef struct {
+  unsigned long long problem_hash;   /* identity of the discrete problem */
+  long long n_coeffs, n_spatial;
+  double t_now;                      /* start time of the next strip */
+  int strips_solved;
+  int has_field;                     /* 1: Vlasov-Poisson state included */
+} sgdg_checkpoint_info;
+/* The checks of sgdg_restore on the file at `path` alone (host only, no
+ * device call): SGDG_OK and *info filled (info may be NULL) when the file
+ * is a complete, uncorrupted checkpoint; SGDG_EIO otherwise; SGDG_EINVAL
+ * for a NULL path. */
+sgdg_status sgdg_checkpoint_verify(const char* path, sgdg_checkpoint_info* info);
 
 /* U^-_0 := u0 (the first right-hand side uses (u0, w^+) directly). */
 sgdg_status sgdg_set_initial(void* h);
@@ -486,9 +504,10 @@ sgdg_status sgdg_profile(void* h, int enable);
 /* Synchronise the device, fill out[0..7] (one per kind) and clear the records. */
 sgdg_status sgdg_kernel_stats(void* h, sgdg_kernel_stat* out, int n_kinds);
 /* Sizes in bytes of the ABI structs, for bindings to check their layouts
- * (host only; no device is touched): out[0..7] = sgdg_mesh, sgdg_product,
+ * (host only; no device is touched): out[0..8] = sgdg_mesh, sgdg_product,
  * sgdg_source, sgdg_coeffs, sgdg_config, sgdg_info, sgdg_strip_stats,
- * sgdg_kernel_stat.  Writes min(n, 8) entries and returns 8. */
+ * sgdg_kernel_stat, sgdg_checkpoint_info.  Writes min(n, 9) entries and
+ * returns 9. */
 int sgdg_struct_sizes(int* out, int n);
 /* Number of SpMM kernels this handle has launched so far. */
 long long sgdg_launch_count(const void* h);

@@ -101,6 +101,7 @@ EXPORTS = {
     "sgdg_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "sgdg_set_launch_shape": (C.c_int, [C.c_void_p, C.c_int]),
     "sgdg_struct_sizes": (C.c_int, [C.POINTER(C.c_int), C.c_int]),
+    "sgdg_checkpoint_verify": (C.c_int, [C.c_char_p, C.c_void_p]),
     "sgdg_field_update": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "sgdg_resolve_strip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_advance_strip_vp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p,
@@ -148,6 +149,11 @@ KERNEL_KINDS = ("s_chain", "final_left", "restrict_dim1", "restrict_dim2", "fuse
 
 class KernelStat(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("ms", C.c_double), ("bytes", C.c_double), ("flops", C.c_double)]
+
+
+class CheckpointInfo(C.Structure):
+    _fields_ = [("problem_hash", C.c_ulonglong), ("n_coeffs", C.c_longlong), ("n_spatial", C.c_longlong),
+                ("t_now", C.c_double), ("strips_solved", C.c_int), ("has_field", C.c_int)]
 
 _lib = None
 
@@ -514,6 +520,18 @@ def alu_peak(precision: int, device: int = 0, iters: int = 1 << 16):
     if st != 0:
         raise SgdgError(st, "sgdg_alu_peak")
     return g.value, ms.value
+
+
+def checkpoint_verify(path: str) -> CheckpointInfo:
+    """sgdg_checkpoint_verify: the restore checks on a checkpoint file alone
+    (host only).  Returns its CheckpointInfo; raises SgdgError (EIO) for a
+    truncated or corrupted file."""
+    lib = load_library()
+    info = CheckpointInfo()
+    st = lib.sgdg_checkpoint_verify(os.fsencode(path), C.byref(info))
+    if st != 0:
+        raise SgdgError(st, f"sgdg_checkpoint_verify({path})")
+    return info
 
 
 class Batch:

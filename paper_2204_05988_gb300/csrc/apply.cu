@@ -439,6 +439,7 @@ Status fused_branch_a(Handle& h, const Plan& p, const Pool<T>& pool, int i, cons
 
 template <typename T>
 Status apply_plan(Handle& h, const Plan& p, const Store<T>* u, Store<T>* y, cudaStream_t s, const ApplyHooks* hooks) {
+  NvtxRange range("sgdg.apply");
   Pool<T> pool;
   Status st = ensure_pool<T>(h, p, pool);
   if (st.code) return st;

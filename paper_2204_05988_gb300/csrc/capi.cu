@@ -334,14 +334,8 @@ void make_plan(Plan& p, const std::vector<Term>& terms) {
   p.D = cv.size() <= cx.size() ? cv : cx;
 }
 
-// FNV-1a, 64 bit, over raw bytes (the problem identity of checkpoints)
-void fnv(unsigned long long& hsh, const void* p, size_t n) {
-  const unsigned char* b = (const unsigned char*)p;
-  for (size_t i = 0; i < n; ++i) {
-    hsh ^= b[i];
-    hsh *= 1099511628211ULL;
-  }
-}
+// the problem identity of checkpoints: FNV-1a 64 over raw bytes
+void fnv(unsigned long long& hsh, const void* p, size_t n) { fnv1a64(hsh, p, n); }
 
 struct ErrStore {
   std::string msg;
@@ -383,7 +377,7 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
   h.d = cfg.mesh_x.dim;
   h.L = cfg.level_L;
   h.budget = cfg.hbm_budget_bytes;
-  h.problem_hash = 1469598103934665603ULL;
+  h.problem_hash = kFnvBasis;
   fnv(h.problem_hash, &h.d, sizeof(h.d));
   fnv(h.problem_hash, &h.L, sizeof(h.L));
   fnv(h.problem_hash, &cfg.dt, sizeof(cfg.dt));
@@ -994,11 +988,12 @@ sgdg_status sgdg_get_end_value(const void* hp, double* dst, int on_device) {
 }
 
 int sgdg_struct_sizes(int* out, int n) {
-  const int sz[8] = {(int)sizeof(sgdg_mesh),   (int)sizeof(sgdg_product), (int)sizeof(sgdg_source),
+  const int sz[9] = {(int)sizeof(sgdg_mesh),   (int)sizeof(sgdg_product), (int)sizeof(sgdg_source),
                      (int)sizeof(sgdg_coeffs), (int)sizeof(sgdg_config),  (int)sizeof(sgdg_info),
-                     (int)sizeof(sgdg_strip_stats), (int)sizeof(sgdg_kernel_stat)};
-  for (int i = 0; out && i < n && i < 8; ++i) out[i] = sz[i];
-  return 8;
+                     (int)sizeof(sgdg_strip_stats), (int)sizeof(sgdg_kernel_stat),
+                     (int)sizeof(sgdg_checkpoint_info)};
+  for (int i = 0; out && i < n && i < 9; ++i) out[i] = sz[i];
+  return 9;
 }
 
 sgdg_status sgdg_set_launch_shape(void* hp, int code) {

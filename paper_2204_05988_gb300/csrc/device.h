@@ -3,6 +3,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <vector>
@@ -10,6 +11,16 @@
 #include "internal.h"
 
 namespace sgdg {
+
+// A named NVTX range over one phase of the strip solve (strip, rhs, apply,
+// ct, inner, orth), closed when the scope ends (early returns included).
+// Without a profiler attached the push and pop are no-ops.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kMaxTerms = 8;    // terms fused into one SpMM launch
 constexpr int kMaxGrids = 24;   // grids fused into one launch

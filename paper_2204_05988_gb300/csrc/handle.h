@@ -9,6 +9,18 @@
 
 namespace sgdg {
 
+// FNV-1a, 64 bit (Fowler, Noll, Vo): h ^= byte, h *= 1099511628211 per
+// byte, starting from the offset basis 14695981039346656037.  The problem
+// identity and the checksum of checkpoint files.
+constexpr unsigned long long kFnvBasis = 14695981039346656037ULL;
+inline void fnv1a64(unsigned long long& hsh, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) {
+    hsh ^= b[i];
+    hsh *= 1099511628211ULL;
+  }
+}
+
 // Device copies of one side's (Omega_x or Omega_v) level data.
 template <typename T>
 struct SideValues {

@@ -157,6 +157,7 @@ inline double norm_of(double sq) { return std::isnan(sq) ? sq : std::sqrt(std::m
 
 template <typename T>
 Status arnoldi(Handle& h, T* V, long long n, int j, T* w, double* hcol, cudaStream_t s) {
+  NvtxRange range("sgdg.orth");
   Workspace& ws = *h.ws;
   double* d = ws.dev_dots;
   SG_ST(mdot<T>(h, j + 1, V, n, w, n, d, s));
@@ -642,6 +643,7 @@ Status ct_apply(Handle& h, const T* r, T* z, cudaStream_t s, int* its) {
   }
   Active live = act;
   for (int j = 0; j < m && !live.g.empty(); ++j) {
+    NvtxRange step("sgdg.inner");
     const int na = (int)live.g.size();
     std::vector<const T*> vin(na), Vb(na), wv(na);
     std::vector<T*> pout(na);
@@ -828,6 +830,7 @@ Status solver_init(Handle& h) {
 }
 
 Status ct_precondition(Handle& h, const double* r, double* z, cudaStream_t s, int* its) {
+  NvtxRange range("sgdg.ct");
   SG_ST(solver_init(h));
   Workspace& ws = *h.ws;
   if (h.cfg.precision == SGDG_MIXED_FP32) {
@@ -848,6 +851,7 @@ Status ct_precondition(Handle& h, const double* r, double* z, cudaStream_t s, in
 // (Sect. 4.2); then every term on every grid.
 static Status add_source(Handle& h, cudaStream_t s) {
   if (h.src_terms.empty()) return {};
+  NvtxRange range("sgdg.rhs");
   const double dt = h.cfg.dt, ta = h.t_now, dl = h.cfg.delta;
   const double z[3] = {-std::sqrt(0.6), 0.0, std::sqrt(0.6)};
   const double wz[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
@@ -904,6 +908,7 @@ Status set_strip_time(Handle& h, double t0) {
 }
 
 Status advance_strip(Handle& h, cudaStream_t s, sgdg_strip_stats* st, bool resolve) {
+  NvtxRange range("sgdg.strip");
   auto t0 = std::chrono::steady_clock::now();
   SG_ST(solver_init(h));
   Workspace& ws = *h.ws;

@@ -8,13 +8,14 @@
 #include "sgdg.h"
 
 int main(void) {
-  const int c_sizes[8] = {(int)sizeof(sgdg_mesh),   (int)sizeof(sgdg_product), (int)sizeof(sgdg_source),
+  const int c_sizes[9] = {(int)sizeof(sgdg_mesh),   (int)sizeof(sgdg_product), (int)sizeof(sgdg_source),
                           (int)sizeof(sgdg_coeffs), (int)sizeof(sgdg_config),  (int)sizeof(sgdg_info),
-                          (int)sizeof(sgdg_strip_stats), (int)sizeof(sgdg_kernel_stat)};
-  int lib_sizes[8] = {0};
-  const int n = sgdg_struct_sizes(lib_sizes, 8);
-  int bad = n != 8;
-  for (int i = 0; i < 8; ++i) {
+                          (int)sizeof(sgdg_strip_stats), (int)sizeof(sgdg_kernel_stat),
+                          (int)sizeof(sgdg_checkpoint_info)};
+  int lib_sizes[9] = {0};
+  const int n = sgdg_struct_sizes(lib_sizes, 9);
+  int bad = n != 9;
+  for (int i = 0; i < 9; ++i) {
     printf("%d %d %d\n", i, c_sizes[i], lib_sizes[i]);
     bad |= c_sizes[i] != lib_sizes[i];
   }

@@ -5,7 +5,8 @@
   gives the strips an uninterrupted run gives, bit for bit - for the plain
   transport solver with the extrapolated warm start and for the
   Vlasov-Poisson solver whose field is iterated within each strip (Sect. 5.3).
-  A checkpoint of another problem is refused.
+  A checkpoint of another problem is refused; a corrupted or truncated one
+  is refused (SGDG_EIO) before the handle's state changes.
 * The device-memory budget: a handle whose set-up needs more than
   hbm_budget_bytes is refused with SGDG_ENOMEM; one that fits creates.
 * Failures injected on the host: NaN initial data gives SGDG_ENAN; an outer
@@ -109,6 +110,42 @@ def test_restore_refuses_another_problem(P, tmp_path):
         b.restore(str(tmp_path / "missing.ckpt"))
     assert e.value.code == 7                      # SGDG_EIO
     b.close()
+
+
+def test_corrupted_checkpoint_leaves_the_handle_unchanged(P, tmp_path):
+    """A checkpoint with one flipped payload byte, or cut short, is refused
+    (SGDG_EIO) by sgdg_restore, and by sgdg_checkpoint_verify without a
+    handle; the handle that refused it continues as if restore had not been
+    called, bit for bit."""
+    prob = W.free_streaming_1d(L=3, n_strips=3)
+    a = P.Solver(prob, rtol=1e-10)
+    a.set_initial()
+    a.advance_strip()
+    path = str(tmp_path / "a.ckpt")
+    a.checkpoint(path)
+    info = P.checkpoint_verify(path)
+    assert info.n_coeffs == a.n_coeffs and info.strips_solved >= 1 and info.has_field == 0
+    a.advance_strip()
+    ref = _end(a)
+    a.close()
+    good = open(path, "rb").read()
+    bad = bytearray(good)
+    bad[len(bad) // 2] ^= 0x01                   # inside a state vector
+    for name, data in (("flip", bytes(bad)), ("short", good[:-9])):
+        p = str(tmp_path / f"{name}.ckpt")
+        open(p, "wb").write(data)
+        with pytest.raises(P.SgdgError) as e:
+            P.checkpoint_verify(p)
+        assert e.value.code == 7
+        b = P.Solver(prob, rtol=1e-10)
+        b.set_initial()
+        b.advance_strip()
+        with pytest.raises(P.SgdgError) as e:
+            b.restore(p)
+        assert e.value.code == 7                  # SGDG_EIO
+        b.advance_strip()
+        assert np.array_equal(_end(b), ref), name
+        b.close()
 
 
 def test_hbm_budget(P):
