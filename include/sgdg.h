@@ -79,10 +79,17 @@ typedef enum {
 
 /* A coarse simplicial mesh of an axis-aligned box (one of Omega_x, Omega_v).
  * coords: [n_vertices][dim]; cells: [n_cells][dim+1] vertex indices.
- * lo/hi: box bounds per axis; periodic: per-axis flag (0/1).  Uniform
- * refinement (1D bisection, 2D red refinement, 3D regular refinement after
- * Bey, which keeps a Kuhn mesh whose tetrahedra list their vertices along a
- * monotone lattice path a Kuhn lattice) builds the levels (Sect. 2). */
+ * lo/hi: box bounds per axis; periodic: per-axis flag (0/1; NULL: none).
+ * Uniform refinement (1D bisection, 2D red refinement, 3D regular
+ * refinement after Bey, which keeps a Kuhn mesh a Kuhn mesh when its
+ * tetrahedra list their vertices along a monotone lattice path) builds the
+ * levels (Sect. 2).  sgdg_create checks each mesh on the host before it
+ * touches a device and returns SGDG_EINVAL when: lo < hi fails on an axis;
+ * a vertex lies outside the box or two share their coordinates; a cell
+ * index is out of range or a cell has zero volume; the cell volumes do not
+ * add up to the box volume; a face lies in more than two cells, or a face of
+ * one cell is not on a side of the box; or the vertices on the two sides of
+ * a periodic axis do not match. */
 typedef struct {
   int dim;
   int n_vertices;
@@ -218,6 +225,10 @@ typedef struct {
  * formula (Sect. 4.2; delta on K~ per the weak form of Sect. 2), upload
  * everything to the device.  EINVAL for unsupported input, ENOMEM, ECUDA. */
 sgdg_status sgdg_create(const sgdg_config* cfg, const sgdg_coeffs* coeffs, void** out_handle);
+/* The mesh checks of sgdg_create on one coarse mesh (host only, no device
+ * call; the list is at sgdg_mesh): SGDG_OK or SGDG_EINVAL, with
+ * sgdg_last_error(NULL) naming the failed check. */
+sgdg_status sgdg_validate_mesh(const sgdg_mesh* mesh);
 void sgdg_destroy(void* h);
 const char* sgdg_last_error(const void* h);
 sgdg_status sgdg_get_info(const void* h, sgdg_info* out);

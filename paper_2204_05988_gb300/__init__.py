@@ -102,6 +102,7 @@ EXPORTS = {
     "sgdg_set_launch_shape": (C.c_int, [C.c_void_p, C.c_int]),
     "sgdg_struct_sizes": (C.c_int, [C.POINTER(C.c_int), C.c_int]),
     "sgdg_checkpoint_verify": (C.c_int, [C.c_char_p, C.c_void_p]),
+    "sgdg_validate_mesh": (C.c_int, [C.c_void_p]),
     "sgdg_field_update": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "sgdg_resolve_strip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_advance_strip_vp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p,
@@ -288,16 +289,7 @@ class Solver:
 
     # -- marshalling helpers
     def _mesh(self, m) -> Mesh:
-        coords = np.ascontiguousarray(m.coords, dtype=np.float64)
-        cells = np.ascontiguousarray(m.cells, dtype=np.int32)
-        lo = np.ascontiguousarray(m.lo, dtype=np.float64)
-        hi = np.ascontiguousarray(m.hi, dtype=np.float64)
-        per = np.ascontiguousarray([int(p) for p in m.periodic], dtype=np.int32)
-        self._keep += [coords, cells, lo, hi, per]
-        dp = C.POINTER(C.c_double)
-        ip = C.POINTER(C.c_int)
-        return Mesh(m.dim, coords.shape[0], coords.ctypes.data_as(dp), cells.shape[0], cells.ctypes.data_as(ip),
-                    lo.ctypes.data_as(dp), hi.ctypes.data_as(dp), per.ctypes.data_as(ip))
+        return _mesh_struct(m, self._keep)
 
     def _fn(self, f, d):
         if f is None:
@@ -520,6 +512,31 @@ def alu_peak(precision: int, device: int = 0, iters: int = 1 << 16):
     if st != 0:
         raise SgdgError(st, "sgdg_alu_peak")
     return g.value, ms.value
+
+
+def _mesh_struct(m, keep: list) -> Mesh:
+    """sgdg_mesh over contiguous copies of a coarse mesh's arrays (kept alive in keep)."""
+    coords = np.ascontiguousarray(m.coords, dtype=np.float64)
+    cells = np.ascontiguousarray(m.cells, dtype=np.int32)
+    lo = np.ascontiguousarray(m.lo, dtype=np.float64)
+    hi = np.ascontiguousarray(m.hi, dtype=np.float64)
+    per = np.ascontiguousarray([int(p) for p in m.periodic], dtype=np.int32)
+    keep += [coords, cells, lo, hi, per]
+    dp = C.POINTER(C.c_double)
+    ip = C.POINTER(C.c_int)
+    return Mesh(m.dim, coords.shape[0], coords.ctypes.data_as(dp), cells.shape[0], cells.ctypes.data_as(ip),
+                lo.ctypes.data_as(dp), hi.ctypes.data_as(dp), per.ctypes.data_as(ip))
+
+
+def validate_mesh(m) -> None:
+    """sgdg_validate_mesh (host only): raises SgdgError (EINVAL) naming the
+    failed check of a coarse mesh."""
+    lib = load_library()
+    keep: list = []
+    ms = _mesh_struct(m, keep)
+    st = lib.sgdg_validate_mesh(C.byref(ms))
+    if st != 0:
+        raise SgdgError(st, lib.sgdg_last_error(None).decode())
 
 
 def checkpoint_verify(path: str) -> CheckpointInfo:

@@ -367,6 +367,12 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
     return {SGDG_EINVAL, "unknown outer_method"};
   if (c.n_u0 < 0 || (c.n_u0 > 0 && !c.u0)) return {SGDG_EINVAL, "bad u0 list"};
   {
+    Status sm = validate_mesh(cfg.mesh_x);
+    if (sm.code) return {sm.code, "mesh_x: " + sm.msg};
+    sm = validate_mesh(cfg.mesh_v);
+    if (sm.code) return {sm.code, "mesh_v: " + sm.msg};
+  }
+  {
     bool timed = c.sigma_t != nullptr;
     for (int p = 0; p < 2 * cfg.mesh_x.dim && p < 2 * kMaxDim; ++p) timed = timed || c.beta_t[p] != nullptr;
     if (timed && cfg.vlasov_poisson)
@@ -718,6 +724,13 @@ void sgdg_destroy(void* hp) {
     registry(h).clear();
   }
   delete h;
+}
+
+sgdg_status sgdg_validate_mesh(const sgdg_mesh* m) {
+  if (!m) return fail(nullptr, {SGDG_EINVAL, "null mesh"});
+  const Status st = validate_mesh(*m);
+  if (st.code) return fail(nullptr, st);
+  return SGDG_OK;
 }
 
 const char* sgdg_last_error(const void* hp) {

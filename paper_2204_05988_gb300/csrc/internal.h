@@ -51,6 +51,10 @@ struct Hierarchy {
   std::vector<std::vector<int>> inj;  // inj[l][k]: level-(l+1) index of level-l vertex k
 };
 
+// Host checks of a coarse mesh: box, vertices inside it and distinct, cells
+// of positive volume tiling the box, conforming faces (at most two cells;
+// one-cell faces on a box side), matching vertices on periodic sides.
+Status validate_mesh(const sgdg_mesh& m);
 Status build_hierarchy(const sgdg_mesh& m, int L, Hierarchy& h);
 
 // q-point Gauss-Legendre rule on [0, 1] (nodes by Newton's method on P_q).

@@ -12,6 +12,7 @@
 // the upper-bound vertex with the lower-bound one.  E_{l+1<-l} evaluates a level-l P1 function at the level
 // l+1 vertices: 1 at a kept vertex, 1/2 + 1/2 at an edge midpoint.
 #include <algorithm>
+#include <cmath>
 #include <array>
 #include <cstring>
 #include <map>
@@ -218,6 +219,93 @@ Csr transpose(const Csr& A) {
 }
 
 }  // namespace
+
+Status validate_mesh(const sgdg_mesh& m) {
+  if (m.dim < 1 || m.dim > 3) return {SGDG_EINVAL, "mesh dim must be 1, 2 or 3"};
+  if (m.n_vertices <= 0 || m.n_cells <= 0 || !m.coords || !m.cells || !m.lo || !m.hi)
+    return {SGDG_EINVAL, "empty or incomplete mesh"};
+  const int d = m.dim, k = d + 1;
+  double box = 1.0, ext = 0.0;
+  for (int a = 0; a < d; ++a) {
+    if (!std::isfinite(m.lo[a]) || !std::isfinite(m.hi[a]) || !(m.lo[a] < m.hi[a]))
+      return {SGDG_EINVAL, "mesh box: lo < hi (finite) on every axis"};
+    box *= m.hi[a] - m.lo[a];
+    ext = std::max(ext, m.hi[a] - m.lo[a]);
+  }
+  const double tol = 1e-12 * ext;
+  auto X = [&](int v, int a) { return m.coords[(size_t)v * d + a]; };
+  for (int v = 0; v < m.n_vertices; ++v)
+    for (int a = 0; a < d; ++a)
+      if (!std::isfinite(X(v, a)) || X(v, a) < m.lo[a] - tol || X(v, a) > m.hi[a] + tol)
+        return {SGDG_EINVAL, "mesh vertex outside its box"};
+  {
+    std::vector<std::vector<double>> pts(m.n_vertices, std::vector<double>(d));
+    for (int v = 0; v < m.n_vertices; ++v)
+      for (int a = 0; a < d; ++a) pts[v][a] = X(v, a);
+    std::sort(pts.begin(), pts.end());
+    for (int v = 1; v < m.n_vertices; ++v)
+      if (pts[v] == pts[v - 1]) return {SGDG_EINVAL, "two mesh vertices share their coordinates"};
+  }
+  // cells: indices in range, positive volume; the volumes tile the box
+  double vol_sum = 0.0, fact = d == 1 ? 1.0 : d == 2 ? 2.0 : 6.0;
+  std::map<std::vector<int>, int> faces;   // sorted face vertices -> cells holding it
+  for (int c = 0; c < m.n_cells; ++c) {
+    const int* cv = m.cells + (size_t)c * k;
+    for (int i = 0; i < k; ++i)
+      if (cv[i] < 0 || cv[i] >= m.n_vertices) return {SGDG_EINVAL, "cell vertex index out of range"};
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int i = 1; i < k; ++i)
+      for (int a = 0; a < d; ++a) J[a][i - 1] = X(cv[i], a) - X(cv[0], a);
+    const double det = d == 1 ? J[0][0]
+                     : d == 2 ? J[0][0] * J[1][1] - J[0][1] * J[1][0]
+                     : J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    const double vol = std::fabs(det) / fact;
+    if (!(vol > 1e-12 * box)) return {SGDG_EINVAL, "degenerate mesh cell (zero volume)"};
+    vol_sum += vol;
+    for (int drop = 0; drop < k; ++drop) {
+      std::vector<int> f;
+      for (int i = 0; i < k; ++i)
+        if (i != drop) f.push_back(cv[i]);
+      std::sort(f.begin(), f.end());
+      faces[f]++;
+    }
+  }
+  if (std::fabs(vol_sum - box) > 1e-10 * box)
+    return {SGDG_EINVAL, "mesh cells do not tile the box (overlap or hole)"};
+  // conformity: a face lies in at most two cells, and a face of one cell lies
+  // on a side of the box
+  for (const auto& fc : faces) {
+    if (fc.second > 2) return {SGDG_EINVAL, "a mesh face is shared by more than two cells"};
+    if (fc.second == 2) continue;
+    bool on_side = false;
+    for (int a = 0; a < d && !on_side; ++a)
+      for (double bound : {m.lo[a], m.hi[a]}) {
+        bool all = true;
+        for (int v : fc.first) all = all && std::fabs(X(v, a) - bound) <= tol;
+        on_side = on_side || all;
+      }
+    if (!on_side) return {SGDG_EINVAL, "a boundary face of the mesh is not on a side of its box"};
+  }
+  // periodic axes: the vertices on the two opposite sides match
+  for (int a = 0; a < d; ++a) {
+    if (!m.periodic || !m.periodic[a]) continue;
+    std::vector<std::vector<double>> side[2];
+    for (int v = 0; v < m.n_vertices; ++v)
+      for (int sd = 0; sd < 2; ++sd)
+        if (std::fabs(X(v, a) - (sd ? m.hi[a] : m.lo[a])) <= tol) {
+          std::vector<double> y;
+          for (int b = 0; b < d; ++b)
+            if (b != a) y.push_back(X(v, b));
+          side[sd].push_back(y);
+        }
+    std::sort(side[0].begin(), side[0].end());
+    std::sort(side[1].begin(), side[1].end());
+    if (side[0] != side[1]) return {SGDG_EINVAL, "periodic axis: the vertices of the two sides do not match"};
+  }
+  return {};
+}
 
 Status build_hierarchy(const sgdg_mesh& m, int L, Hierarchy& h) {
   Status st;
