@@ -214,6 +214,30 @@ def periodic_advection_1d(L: int, r: int = 1) -> Problem:
                    beta=[Product(1.0), Product(1.0)], sigma=Product(0.0), u0=u0, exact=exact, order=r)
 
 
+def periodic_advection_2d(L: int, r: int = 1) -> Problem:
+    """Sect. 5.1 (Eq. 25) with d = 2: beta = (1, 1, 1, 1) on the periodic unit
+    cubes, u0 = sin(2 pi (x1 + x2 + v1 + v2)); coarse meshes of 4 x 4 squares
+    (two triangles each); 2^(L_paper+1) strips over one period T = 1/4;
+    delta = finest edge length along the axes.  L is 0-based; r is the order
+    of the spatial elements and of the time-DG polynomials, as in Table 1."""
+    mx = square_mesh(0.0, 1.0, 4, periodic=True)
+    mv = square_mesh(0.0, 1.0, 4, periodic=True)
+    Lp = L + 1
+    n_strips = 2 ** (Lp + 1)
+    T = 0.25
+    h = 1.0 / (4 * 2 ** L)
+    s2 = lambda p: np.sin(2 * np.pi * (p[:, 0] + p[:, 1]))
+    c2 = lambda p: np.cos(2 * np.pi * (p[:, 0] + p[:, 1]))
+    u0 = [Product(1.0, s2, c2), Product(1.0, c2, s2)]
+
+    def exact(t, x, v):
+        return np.sin(2 * np.pi * (x[..., 0] + x[..., 1] + v[..., 0] + v[..., 1] - 4 * t))
+
+    return Problem(name=f"periodic_advection_2d_L{L}" + ("" if r == 1 else f"_r{r}"), d=2, mesh_x=mx, mesh_v=mv,
+                   L=L, r=r, dt=T / n_strips, delta=h, n_strips=n_strips, beta=[Product(1.0)] * 4,
+                   sigma=Product(0.0), u0=u0, exact=exact, order=r)
+
+
 def transport_3d(L: int = 7, dt: float = 1.0 / 32.0, n_strips: int = 8) -> Problem:
     """d=3 (6-D phase space): Omega_x = [0,1]^3, Omega_v = [-1,1]^3, 6-tetrahedron
     Kuhn coarse meshes refined uniformly ((2^l + 1)^3 vertices on level l),
