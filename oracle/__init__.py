@@ -14,6 +14,7 @@ The oracle follows the paper step by step, slowly and obviously:
                 apply with its ordering rule (Sect. 4.2)
 * ``solver``    GMRES, the combination-technique preconditioner (Algorithm 1),
                 component solves with the (T+dC+G) x M x M preconditioner, strip driver
+* ``tensor``    tensor-product Q_r elements on box meshes of squares (Sect. 5.1, Table 1's d = 2 meshes)
 * ``brute``     literal full-grid 2d-dimensional assembly of the weak form
                 (Sect. 2, Eq. 5) for tiny levels - the pin for the block formula
 

@@ -101,6 +101,8 @@ def _keep(f: Factor, centroids: np.ndarray) -> np.ndarray:
 
 
 def assemble_level(lev: Level, f: Factor, q: int = QUAD_Q) -> sp.csr_matrix:
+    if hasattr(lev, "assemble"):          # tensor-product level (oracle/tensor.py)
+        return lev.assemble(f)
     n = lev.n
     if f.kind == "vol":
         cc = lev.cell_coords
@@ -233,6 +235,8 @@ def assemble_load_grad(lev: Level, fn, axis: int, q: int = QUAD_Q) -> np.ndarray
 
 def assemble_load(lev: Level, fn, q: int = QUAD_Q) -> np.ndarray:
     """Load vector F[i] = int fn(y) phi_i(y) dy on one level (fn=None: 1)."""
+    if hasattr(lev, "load"):              # tensor-product level (oracle/tensor.py)
+        return lev.load(fn, q)
     cc = lev.cell_coords
     nc, d1, d = cc.shape
     v0 = cc[:, 0, :]

@@ -50,6 +50,8 @@ def _products(prob, X, V, p):
 def _cell_basis(lev, q):
     """Quadrature points and weights per cell, the level's Lagrange basis at
     the points (nq, nloc) and its gradients (nc, nq, nloc, d)."""
+    if hasattr(lev, "cell_basis"):        # tensor-product level (oracle/tensor.py)
+        return lev.cell_basis(q)
     pts, w, lam, glam = _cell_data(lev, q)
     phi, dphi = lagrange_basis(lev.order, lam)
     grad = np.einsum("qam,cmd->cqad", dphi, glam)

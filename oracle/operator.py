@@ -221,9 +221,15 @@ class SparseGridOperator:
         self.prob = prob
         self.L = prob.L
         self.R = prob.r + 1
-        H = P2Hierarchy if getattr(prob, "order", 1) == 2 else Hierarchy
-        self.hx = H(prob.mesh_x, prob.L)
-        self.hv = H(prob.mesh_v, prob.L)
+        order = getattr(prob, "order", 1)
+        if getattr(prob, "element", "P") == "Q":
+            from .tensor import TensorHierarchy
+            self.hx = TensorHierarchy(prob.mesh_x, prob.L, order)
+            self.hv = TensorHierarchy(prob.mesh_v, prob.L, order)
+        else:
+            H = P2Hierarchy if order == 2 else Hierarchy
+            self.hx = H(prob.mesh_x, prob.L)
+            self.hv = H(prob.mesh_v, prob.L)
         self.fx = FactorStore(self.hx)
         self.fv = FactorStore(self.hv)
         self.terms = kron_terms(prob)

@@ -82,6 +82,7 @@ class Problem:
     f: List[Source] = field(default_factory=list)   # source, sum of separable terms
     g: List[Source] = field(default_factory=list)   # inflow data on Gamma^-, sum of separable terms
     order: int = 1              # polynomial order of the continuous spatial elements (P1, P2)
+    element: str = "P"          # "P": simplices (P_order); "Q": tensor-product Q_order on the squares
 
 
 # ----------------------------------------------------------------------------
@@ -214,12 +215,14 @@ def periodic_advection_1d(L: int, r: int = 1) -> Problem:
                    beta=[Product(1.0), Product(1.0)], sigma=Product(0.0), u0=u0, exact=exact, order=r)
 
 
-def periodic_advection_2d(L: int, r: int = 1) -> Problem:
+def periodic_advection_2d(L: int, r: int = 1, element: str = "P") -> Problem:
     """Sect. 5.1 (Eq. 25) with d = 2: beta = (1, 1, 1, 1) on the periodic unit
     cubes, u0 = sin(2 pi (x1 + x2 + v1 + v2)); coarse meshes of 4 x 4 squares
     (two triangles each); 2^(L_paper+1) strips over one period T = 1/4;
     delta = finest edge length along the axes.  L is 0-based; r is the order
-    of the spatial elements and of the time-DG polynomials, as in Table 1."""
+    of the spatial elements and of the time-DG polynomials, as in Table 1;
+    element "P" uses the triangles, "Q" tensor-product elements on the
+    squares."""
     mx = square_mesh(0.0, 1.0, 4, periodic=True)
     mv = square_mesh(0.0, 1.0, 4, periodic=True)
     Lp = L + 1
@@ -235,7 +238,7 @@ def periodic_advection_2d(L: int, r: int = 1) -> Problem:
 
     return Problem(name=f"periodic_advection_2d_L{L}" + ("" if r == 1 else f"_r{r}"), d=2, mesh_x=mx, mesh_v=mv,
                    L=L, r=r, dt=T / n_strips, delta=h, n_strips=n_strips, beta=[Product(1.0)] * 4,
-                   sigma=Product(0.0), u0=u0, exact=exact, order=r)
+                   sigma=Product(0.0), u0=u0, exact=exact, order=r, element=element)
 
 
 def transport_3d(L: int = 7, dt: float = 1.0 / 32.0, n_strips: int = 8) -> Problem:
