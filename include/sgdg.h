@@ -8,9 +8,11 @@
  * separable terms.
  *
  * Discretisation (Sect. 2): sparse grid V_L = sum_{l=0..L} V^(1)_l (x) V^(2)_{L-l}
- * of nested P1 spaces (levels 0-based: the paper's level is L+1), time-DG of
- * degree r = 1 on strips, streamline diffusion with parameter delta; the strip
- * problem a_j(U_j, w) = b_j(w) of Eq. 5 is solved strip by strip.
+ * of nested continuous P1 spaces on simplicial meshes (levels 0-based: the
+ * paper's level is L+1), time-DG of degree r = 1 on strips, streamline
+ * diffusion with parameter delta; the strip problem a_j(U_j, w) = b_j(w) of
+ * Eq. 5 is solved strip by strip.  (P2 and tensor-product Q_r elements on
+ * d-cubes, which Sect. 5.1 also uses, are not built.)
  *
  * Storage (Sect. 4.1): a sparse-grid coefficient vector is the concatenation
  * over grids l = 0..L of arrays u_l[k1][k2][s] (row-major, s fastest), k1 over
