@@ -106,6 +106,7 @@ class ComponentSolver:
         Mt, Tt, Ct, Gt = time_matrices(op.prob.dt, op.prob.r)
         self.Pt_inv = np.linalg.inv(Tt + op.prob.delta * Ct + Gt)
         self.direct_max = direct_max
+        self._direct = (None, {})
         self._lu = {}
         self.iterations = []
 
@@ -141,7 +142,14 @@ class ComponentSolver:
         n1, n2 = self.op.grid_shape(l1, l2)
         R = self.op.R
         if n1 * n2 * R <= self.direct_max:
-            x = spla.splu(self.block_matrix(l1, l2)).solve(r.ravel())
+            # one factorisation per grid while the operator's term list is
+            # the same object (the cache holds it, so its id is not reused)
+            if self._direct[0] is not self.op.terms:
+                self._direct = (self.op.terms, {})
+            cache = self._direct[1]
+            if (l1, l2) not in cache:
+                cache[(l1, l2)] = spla.splu(self.block_matrix(l1, l2))
+            x = cache[(l1, l2)].solve(r.ravel())
             self.iterations.append(1)
             return x.reshape(n1, n2, R)
         A = lambda x: self.op.apply_diag(l1, l2, x.reshape(n1, n2, R)).ravel()
