@@ -1,6 +1,8 @@
 """Norms of sparse-grid functions: the streamline-diffusion norm of an error
-over all strips (Sect. 3, Eq. 11) and the H^1(J x Omega) norm of one strip
-function (the stop test of Algorithm 1, Sect. 4.3).
+over all strips (Sect. 3, Eq. 11), against the exact solution or against
+Table 1's reference (the sparse-grid interpolant of level L + 1 and order
+r + 1, Sect. 5.1), and the H^1(J x Omega) norm of one strip function (the
+stop test of Algorithm 1, Sect. 4.3).
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
@@ -62,10 +64,10 @@ class _FullGrid:
     """Point values and gradients of finest-full-grid P_r (x) P_r functions on
     every (x cell, v cell) pair's quadrature points."""
 
-    def __init__(self, op, q, periodic_only=True):
+    def __init__(self, op, q, periodic_only=True, levels=None):
         L = op.L
         self.op = op
-        self.lx, self.lv = op.hx.levels[L], op.hv.levels[L]
+        self.lx, self.lv = (op.hx.levels[L], op.hv.levels[L]) if levels is None else levels
         if periodic_only and any(len(lev.bfaces) for lev in (self.lx, self.lv)):
             raise NotImplementedError("SD-norm errors only on domains without boundary (periodic)")
         self.px, self.wx, self.lamx, self.gx = _cell_basis(self.lx, q)
@@ -158,6 +160,98 @@ def sd_norm_error(prob, op, strips, exact, q: int = 5):
             parts["jumps"] += fg.l2sq(start - prev_end)
         if j == N - 1:
             parts["final"] = fg.l2sq(end - fg.exact(exact, N * dt))
+        prev_end = end
+    return float(np.sqrt(sum(parts.values()))), parts
+
+
+class SparseInterpolant:
+    """The interpolant of a function of (x, v) in the sparse grid space of
+    level L + 1 with P2 elements (d = 1), written on the P2 full grid
+    (L + 1, L + 1): the combination technique, sum over |l| = L + 1 minus sum
+    over |l| = L of the full-grid nodal interpolants (exact for
+    interpolation, Sect. 4.3)."""
+
+    def __init__(self, prob, L: int):
+        from .mesh import P2Hierarchy
+        if prob.d != 1:
+            raise NotImplementedError("d = 1")
+        self.L = L
+        self.Hx, self.Hv = P2Hierarchy(prob.mesh_x, L + 1), P2Hierarchy(prob.mesh_v, L + 1)
+        self.Ex = [self.Hx.embed(L + 1, l) for l in range(L + 2)]
+        self.Ev = [self.Hv.embed(L + 1, l) for l in range(L + 2)]
+        self.combos = [(l, L + 1 - l, 1.0) for l in range(L + 2)] + [(l, L - l, -1.0) for l in range(L + 1)]
+
+    def __call__(self, fn, t) -> np.ndarray:
+        L = self.L
+        acc = np.zeros((self.Hx.levels[L + 1].n, self.Hv.levels[L + 1].n))
+        for l1, l2, c in self.combos:
+            X, V = self.Hx.levels[l1].coords[:, 0], self.Hv.levels[l2].coords[:, 0]
+            acc += c * (self.Ex[l1] @ (self.Ev[l2] @ np.asarray(fn(t, X[:, None], V[None, :])).T).T)
+        return acc
+
+
+def sd_norm_error_interp(prob, op, strips, exact, q: int = 5, dt_fd: float = 1e-6):
+    """|||U - I u|||_delta with Table 1's reference (Sect. 5.1): I u is the
+    interpolant of the exact solution in the sparse grid space of level
+    L + 1 with elements of order r + 1, here in space at every time (d = 1,
+    r = 1: ``SparseInterpolant``).  U (P1, level L) and I u are both written
+    on the P2 full grid (L + 1, L + 1), where the norm's integrals are taken
+    as in ``sd_norm_error``; d_t I u = I d_t u, with d_t u by a central
+    difference of step dt_fd."""
+    if prob.r != 1 or getattr(prob, "order", 1) != 1 or prob.d != 1:
+        raise NotImplementedError("the interpolant reference is built for d = 1, r = 1")
+    L, R, d, dt, dl = op.L, op.R, prob.d, prob.dt, prob.delta
+    interp = SparseInterpolant(prob, L)
+    Hx, Hv = interp.Hx, interp.Hv
+    lx, lv = Hx.levels[L + 1], Hv.levels[L + 1]
+    fg = _FullGrid(op, q, levels=(lx, lv))
+    # a P1 function of level L at the P2 nodes of level L + 1 (the P1
+    # vertices of level L + 2): the P1 embedding, on the same canonical order
+    Px, Pv = Hx.p1.embed(L + 2, L), Hv.p1.embed(L + 2, L)
+    dudt = lambda t, x, v: (exact(t + dt_fd, x, v) - exact(t - dt_fd, x, v)) / (2.0 * dt_fd)
+    beta_pts = [_products(prob, fg.Xp, fg.Vp, p).reshape(fg.shape) for p in range(2 * d)]
+    sig = prob.sigma
+    sigma_pts = None
+    if sig.coef != 0.0:
+        fx = sig.fx(fg.Xp) if sig.fx is not None else np.ones(fg.Xp.shape[0])
+        fv = sig.fv(fg.Vp) if sig.fv is not None else np.ones(fg.Vp.shape[0])
+        sigma_pts = (sig.coef * np.outer(fx, fv)).reshape(fg.shape)
+
+    def dbeta(F):
+        return sum(beta_pts[p] * (fg.grad_x(F, p) if p < d else fg.grad_v(F, p - d)) for p in range(2 * d))
+
+    tq, tw = gauss01(2 * prob.r + 1)
+    parts = {"sigma": 0.0, "streamline": 0.0, "jumps": 0.0, "initial": 0.0, "final": 0.0}
+    prev_end = None
+    N = len(strips)
+    for j, u in enumerate(strips):
+        t0 = j * dt
+        us = u.reshape(-1, R)
+        F = [Px @ full_grid_values(op, us[:, s]) @ Pv.T for s in range(R)]
+        val = [fg.value(Fs) for Fs in F]
+        db = [dbeta(Fs) for Fs in F]
+        for tau, w in zip(tq, tw):
+            t = t0 + tau * dt
+            e_s = [eta(s, np.array([tau]), dt) for s in range(R)]
+            Ut = sum(e_s[s][0][0] * val[s] for s in range(R))
+            DU = sum(e_s[s][1][0] * val[s] + e_s[s][0][0] * db[s] for s in range(R))
+            Iu = interp(exact, t)
+            DI = fg.value(interp(dudt, t)) + dbeta(Iu)
+            if sigma_pts is not None:
+                parts["sigma"] += w * dt * float(np.sum(fg.W * sigma_pts * (Ut - fg.value(Iu)) ** 2))
+                DU = DU + sigma_pts * Ut
+                DI = DI + sigma_pts * fg.value(Iu)
+            parts["streamline"] += w * dt * dl * fg.l2sq(DU - DI)
+        e0 = [eta(s, np.array([0.0]), dt)[0][0] for s in range(R)]
+        e1 = [eta(s, np.array([1.0]), dt)[0][0] for s in range(R)]
+        start = sum(e0[s] * val[s] for s in range(R))
+        end = sum(e1[s] * val[s] for s in range(R))
+        if j == 0:
+            parts["initial"] = fg.l2sq(start - fg.value(interp(exact, 0.0)))
+        else:
+            parts["jumps"] += fg.l2sq(start - prev_end)
+        if j == N - 1:
+            parts["final"] = fg.l2sq(end - fg.value(interp(exact, N * dt)))
         prev_end = end
     return float(np.sqrt(sum(parts.values()))), parts
 
