@@ -31,7 +31,7 @@ against direct assembly on the coarse level.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import Callable, Optional, Tuple
+from typing import Callable, Tuple
 
 import numpy as np
 import scipy.sparse as sp

@@ -31,8 +31,6 @@ dense matrix.
 """
 from __future__ import annotations
 
-from typing import List, Tuple
-
 import numpy as np
 import scipy.sparse as sp
 

@@ -35,7 +35,7 @@ import scipy.sparse.linalg as spla
 from scipy import integrate
 
 from .assembly import Factor, assemble_load, assemble_load_grad, gauss01
-from .operator import SparseGridOperator, eta, eta_at, is_time_dependent, time_matrices
+from .operator import SparseGridOperator, eta, eta_at, time_matrices
 
 
 def fgmres(A, b, M=None, x0=None, tol=1e-10, restart=30, maxiter=1000):

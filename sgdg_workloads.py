@@ -17,7 +17,7 @@ All callables take an array of points of shape (npts, d) and return (npts,).
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import Callable, List, Optional, Sequence, Tuple
+from typing import Callable, List, Optional, Tuple
 
 import numpy as np
 

@@ -6,7 +6,6 @@
 * the density of u0 against the closed form (1 + alpha cos(k x1)) int g dv.
 """
 import numpy as np
-import pytest
 
 import sgdg_workloads as W
 from oracle.field import density_u0, poisson

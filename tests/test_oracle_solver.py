@@ -21,7 +21,7 @@ import sgdg_workloads as W
 from oracle.assembly import assemble_load
 from oracle.brute import _cell_data
 from oracle.operator import SparseGridOperator
-from oracle.solver import (ComponentSolver, StripSolver, ct_precondition, fgmres,
+from oracle.solver import (ComponentSolver, StripSolver,
                            full_grid_values, nodal_values, richardson)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")

@@ -15,8 +15,6 @@
   the estimated order is within 0.05 of the printed 0.45 (observed 0.446; the
   same problem on triangles gives 0.16).
 """
-import os
-
 import numpy as np
 import pytest
 
