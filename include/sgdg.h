@@ -259,10 +259,10 @@ sgdg_status sgdg_apply_diag(void* h, int l1, int l2, const void* u, void* y, int
 
 /* The same y = A_{l,l} u as sgdg_apply_diag, from an entry point that
  * allocates nothing.  The paper has no counterpart: this exists for callers
- * that may not allocate device memory when they apply the operator - code
- * being captured into a CUDA graph (an allocation is not capturable), loops
+ * that may not allocate device memory when they apply the operator - loops
  * that must not pay the allocator's device-wide synchronisation, processes
- * whose device memory belongs to another pool.  Its scratch is a static
+ * (plugins, embedded solvers) whose device memory belongs to a pool another
+ * component owns.  Its scratch is a static
  * device array of SGDG_NOALLOC_SCRATCH_BYTES held by every GPU that loads the
  * library until the process exits; grids whose intermediates
  * (distinct v factors x n1 x n2 x 2 elements) do not fit are rejected with

@@ -347,8 +347,8 @@ class Solver:
 
     def apply_diag_noalloc(self, l1: int, l2: int, u, y, precision: int = SGDG_FP64, stream=None):
         """sgdg_apply_diag without any device allocation (static scratch of
-        SGDG_NOALLOC_SCRATCH_BYTES; for callers that may not allocate, e.g.
-        inside a CUDA graph capture)."""
+        SGDG_NOALLOC_SCRATCH_BYTES; for callers that may not allocate device
+        memory, e.g. because another component owns it all)."""
         self._check(self.lib.sgdg_apply_diag_noalloc(self.h, l1, l2, _ptr(u), _ptr(y), precision,
                                                      _stream(stream)))
 

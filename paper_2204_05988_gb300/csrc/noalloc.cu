@@ -2,12 +2,12 @@
 //
 // The regular sgdg_apply_diag keeps its intermediate products u V_b^T in a
 // pool the handle allocates on first use.  Some callers cannot allow an
-// allocation at that point: code that is being captured into a CUDA graph
-// (cudaMalloc is not a capturable operation and would invalidate the capture),
-// latency-critical loops that must never hit the allocator's device-wide
-// synchronisation, and hosts whose device memory is fully handed to another
-// pool.  This variant takes its scratch from the file-scope array below
-// instead; the caller still passes the input u and the output y.
+// allocation at that point: latency-critical loops that must never hit the
+// allocator's device-wide synchronisation, and hosts (plugins, embedded
+// solvers) whose device memory is handed in full to a pool that another
+// component owns, so that cudaMalloc would fail or steal from it.  This
+// variant takes its scratch from the file-scope array below instead; the
+// caller still passes the input u and the output y.
 //
 // The array lives for the lifetime of the loaded library on every GPU that
 // loads it (SGDG_NOALLOC_SCRATCH_BYTES each).  All calls share it and it keeps

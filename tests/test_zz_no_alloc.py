@@ -1,10 +1,11 @@
 """The allocation-free diagonal-block apply (GPU).
 
 sgdg_apply_diag_noalloc serves callers that may not allocate device memory at
-the time they apply the operator (for example while a CUDA graph is being
-captured).  It must give the same y = A_{l,l} u as sgdg_apply_diag, on
-repeated calls that reuse its static scratch, and must reject grids whose
-intermediates do not fit that scratch.  This file is collected last so that a
+the time they apply the operator (loops that must not hit the allocator's
+device-wide synchronisation, or processes whose device memory belongs to a
+pool another component owns).  It must give the same y = A_{l,l} u as
+sgdg_apply_diag, on repeated calls that reuse its static scratch, and must
+reject grids whose intermediates do not fit that scratch.  This file is collected last so that a
 run stopping at the first failure has run every other test already.
 """
 import numpy as np
