@@ -231,6 +231,49 @@ sgdg_status sgdg_create(const sgdg_config* cfg, const sgdg_coeffs* coeffs, void*
  * call; the list is at sgdg_mesh): SGDG_OK or SGDG_EINVAL, with
  * sgdg_last_error(NULL) naming the failed check. */
 sgdg_status sgdg_validate_mesh(const sgdg_mesh* mesh);
+
+/* Host-only views of what sgdg_create builds from one coarse mesh, with no
+ * handle and no device: the nested levels of Sect. 2 (uniform refinement up
+ * to level L, vertices in the canonical order of the storage layout), the
+ * embedding E_{l+1 <- l} of Sect. 4.2, and one Kronecker factor assembled in
+ * FP64 on level L and carried to level l by the Galerkin projection
+ * X_l = E^T X_{l+1} E (Sect. 4.2).  For checking the library's spaces and
+ * factors against another implementation.  Errors: SGDG_EINVAL (mesh checks
+ * of sgdg_validate_mesh, levels outside 0 <= l <= L < 12, a spec naming
+ * no function of the side), with sgdg_last_error(NULL) saying why.
+ *
+ * A factor is X[i][j] = int w (D_trial phi_j)(D_test phi_i) over the domain
+ * (kind 0) or over the boundary faces on one box side (kind 1: face_axis
+ * 0-based, face_side -1 lower / +1 upper), D_0 = value and D_p = d/dy_p
+ * (1-based axis p); w is the product of n_weight coefficient functions of
+ * the side (ids 0 .. 5: the fx (side 0) or fv (side 1) factor of beta
+ * component id, 6: of sigma, as given in the sgdg_coeffs); n_restrict
+ * restrictions keep the cells (faces) whose centroid has sign(function) ==
+ * sign.  Only the coefficient callbacks of the sgdg_coeffs are read. */
+typedef struct {
+  int kind;
+  int test, trial;
+  int n_weight;
+  int weight[4];
+  int n_restrict;
+  int restrict_fn[2];
+  int restrict_sign[2];
+  int face_axis, face_side;
+} sgdg_factor_spec;
+/* Level `level` of the hierarchy refined to L: its vertex count and (coords
+ * not NULL) its vertex coordinates [n][dim]. */
+sgdg_status sgdg_inspect_level(const sgdg_mesh* mesh, int L, int level, int* n_vertices, double* coords);
+/* E_{level+1 <- level} of the hierarchy refined to L (level < L) as CSR
+ * (rows: level+1 vertices): *nrows and *nnz always; rowptr[nrows+1],
+ * col[nnz], val[nnz] when all three are given (call once for the sizes). */
+sgdg_status sgdg_inspect_embedding(const sgdg_mesh* mesh, int L, int level, int* nrows, int* nnz, int* rowptr,
+                                   int* col, double* val);
+/* The factor `spec` of side 0 (x) or 1 (v), assembled on level L and
+ * projected to `level`, as CSR on that level's P1 pattern (square, rows =
+ * test functions); sizes and arrays as for sgdg_inspect_embedding. */
+sgdg_status sgdg_inspect_factor(const sgdg_mesh* mesh, const sgdg_coeffs* coeffs, int side, int L, int level,
+                                const sgdg_factor_spec* spec, int* nrows, int* nnz, int* rowptr, int* col,
+                                double* val);
 void sgdg_destroy(void* h);
 const char* sgdg_last_error(const void* h);
 sgdg_status sgdg_get_info(const void* h, sgdg_info* out);
@@ -519,8 +562,8 @@ sgdg_status sgdg_kernel_stats(void* h, sgdg_kernel_stat* out, int n_kinds);
 /* Sizes in bytes of the ABI structs, for bindings to check their layouts
  * (host only; no device is touched): out[0..8] = sgdg_mesh, sgdg_product,
  * sgdg_source, sgdg_coeffs, sgdg_config, sgdg_info, sgdg_strip_stats,
- * sgdg_kernel_stat, sgdg_checkpoint_info.  Writes min(n, 9) entries and
- * returns 9. */
+ * sgdg_kernel_stat, sgdg_checkpoint_info, sgdg_factor_spec.  Writes
+ * min(n, 10) entries and returns 10. */
 int sgdg_struct_sizes(int* out, int n);
 /* Number of SpMM kernels this handle has launched so far. */
 long long sgdg_launch_count(const void* h);

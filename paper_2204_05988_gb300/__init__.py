@@ -103,6 +103,11 @@ EXPORTS = {
     "sgdg_struct_sizes": (C.c_int, [C.POINTER(C.c_int), C.c_int]),
     "sgdg_checkpoint_verify": (C.c_int, [C.c_char_p, C.c_void_p]),
     "sgdg_validate_mesh": (C.c_int, [C.c_void_p]),
+    "sgdg_inspect_level": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_void_p]),
+    "sgdg_inspect_embedding": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sgdg_inspect_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                      C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_field_update": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "sgdg_resolve_strip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_advance_strip_vp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p,
@@ -150,6 +155,12 @@ KERNEL_KINDS = ("s_chain", "final_left", "restrict_dim1", "restrict_dim2", "fuse
 
 class KernelStat(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("ms", C.c_double), ("bytes", C.c_double), ("flops", C.c_double)]
+
+
+class FactorSpec(C.Structure):
+    _fields_ = [("kind", C.c_int), ("test", C.c_int), ("trial", C.c_int), ("n_weight", C.c_int),
+                ("weight", C.c_int * 4), ("n_restrict", C.c_int), ("restrict_fn", C.c_int * 2),
+                ("restrict_sign", C.c_int * 2), ("face_axis", C.c_int), ("face_side", C.c_int)]
 
 
 class CheckpointInfo(C.Structure):
@@ -537,6 +548,89 @@ def validate_mesh(m) -> None:
     st = lib.sgdg_validate_mesh(C.byref(ms))
     if st != 0:
         raise SgdgError(st, lib.sgdg_last_error(None).decode())
+
+
+class _Marshal:
+    """Callback and struct marshalling outside a Solver (host-only calls)."""
+
+    def __init__(self):
+        self._keep: list = []
+        self._cb_error: List[str] = []
+
+    _fn = lambda self, f, d: Solver._fn(self, f, d)
+    _product = lambda self, pr, d: Solver._product(self, pr, d)
+
+
+def _csr_out(call):
+    """Run a two-pass CSR query: sizes first, then the arrays."""
+    lib = load_library()
+    nrows, nnz = C.c_int(), C.c_int()
+    st = call(C.byref(nrows), C.byref(nnz), None, None, None)
+    if st != 0:
+        raise SgdgError(st, lib.sgdg_last_error(None).decode())
+    rowptr = np.empty(nrows.value + 1, dtype=np.int32)
+    col = np.empty(nnz.value, dtype=np.int32)
+    val = np.empty(nnz.value, dtype=np.float64)
+    st = call(C.byref(nrows), C.byref(nnz), rowptr.ctypes.data, col.ctypes.data, val.ctypes.data)
+    if st != 0:
+        raise SgdgError(st, lib.sgdg_last_error(None).decode())
+    return rowptr, col, val
+
+
+def inspect_level(mesh, L: int, level: int) -> np.ndarray:
+    """sgdg_inspect_level: the vertex coordinates [n][dim] of one level, in the
+    library's canonical order (host only)."""
+    lib = load_library()
+    keep: list = []
+    ms = _mesh_struct(mesh, keep)
+    n = C.c_int()
+    st = lib.sgdg_inspect_level(C.byref(ms), L, level, C.byref(n), None)
+    if st != 0:
+        raise SgdgError(st, lib.sgdg_last_error(None).decode())
+    coords = np.empty((n.value, mesh.dim), dtype=np.float64)
+    st = lib.sgdg_inspect_level(C.byref(ms), L, level, C.byref(n), coords.ctypes.data)
+    if st != 0:
+        raise SgdgError(st, lib.sgdg_last_error(None).decode())
+    return coords
+
+
+def inspect_embedding(mesh, L: int, level: int):
+    """sgdg_inspect_embedding: E_{level+1 <- level} as CSR arrays (rowptr, col, val)."""
+    lib = load_library()
+    keep: list = []
+    ms = _mesh_struct(mesh, keep)
+    return _csr_out(lambda nr, nz, rp, cl, vl: lib.sgdg_inspect_embedding(C.byref(ms), L, level, nr, nz, rp, cl, vl))
+
+
+def inspect_factor(problem, side: int, L: int, level: int, kind: int = 0, test: int = 0, trial: int = 0,
+                   weight=(), restrict=(), face=(-1, 0)):
+    """sgdg_inspect_factor: one factor of side 0 (x) or 1 (v) of the problem's
+    coefficients, assembled on level L and projected to `level`, as CSR
+    arrays (rowptr, col, val).  weight: function ids (0..5 beta components,
+    6 sigma); restrict: (id, sign) pairs; face: (axis, side) for kind 1."""
+    lib = load_library()
+    m = _Marshal()
+    d = problem.d
+    co = Coeffs()
+    for p in range(6):
+        co.beta[p] = m._product(problem.beta[p], d) if p < 2 * d else Product(0.0, FN(), None, FN(), None)
+    co.sigma = m._product(problem.sigma, d)
+    spec = FactorSpec()
+    spec.kind, spec.test, spec.trial = kind, test, trial
+    spec.n_weight = len(weight)
+    for i, w in enumerate(weight):
+        spec.weight[i] = w
+    spec.n_restrict = len(restrict)
+    for i, (fid, sg) in enumerate(restrict):
+        spec.restrict_fn[i], spec.restrict_sign[i] = fid, sg
+    spec.face_axis, spec.face_side = face
+    mesh = problem.mesh_x if side == 0 else problem.mesh_v
+    ms = _mesh_struct(mesh, m._keep)
+    out = _csr_out(lambda nr, nz, rp, cl, vl: lib.sgdg_inspect_factor(C.byref(ms), C.byref(co), side, L, level,
+                                                                      C.byref(spec), nr, nz, rp, cl, vl))
+    if m._cb_error:
+        raise RuntimeError("coefficient callback failed: " + m._cb_error[0])
+    return out
 
 
 def checkpoint_verify(path: str) -> CheckpointInfo:

@@ -689,6 +689,9 @@ Status create(const sgdg_config& cfg, const sgdg_coeffs& c, Handle& h) {
 }
 
 }  // namespace
+
+void set_last_error(const std::string& msg) { global_err().msg = msg; }
+
 }  // namespace sgdg
 
 using namespace sgdg;
@@ -1001,12 +1004,12 @@ sgdg_status sgdg_get_end_value(const void* hp, double* dst, int on_device) {
 }
 
 int sgdg_struct_sizes(int* out, int n) {
-  const int sz[9] = {(int)sizeof(sgdg_mesh),   (int)sizeof(sgdg_product), (int)sizeof(sgdg_source),
-                     (int)sizeof(sgdg_coeffs), (int)sizeof(sgdg_config),  (int)sizeof(sgdg_info),
-                     (int)sizeof(sgdg_strip_stats), (int)sizeof(sgdg_kernel_stat),
-                     (int)sizeof(sgdg_checkpoint_info)};
-  for (int i = 0; out && i < n && i < 9; ++i) out[i] = sz[i];
-  return 9;
+  const int sz[10] = {(int)sizeof(sgdg_mesh),   (int)sizeof(sgdg_product), (int)sizeof(sgdg_source),
+                      (int)sizeof(sgdg_coeffs), (int)sizeof(sgdg_config),  (int)sizeof(sgdg_info),
+                      (int)sizeof(sgdg_strip_stats), (int)sizeof(sgdg_kernel_stat),
+                      (int)sizeof(sgdg_checkpoint_info), (int)sizeof(sgdg_factor_spec)};
+  for (int i = 0; out && i < n && i < 10; ++i) out[i] = sz[i];
+  return 10;
 }
 
 sgdg_status sgdg_set_launch_shape(void* hp, int code) {

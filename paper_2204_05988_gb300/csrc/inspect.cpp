@@ -1,0 +1,125 @@
+// Host-only views of the discrete spaces and factors the library builds
+// (sgdg_inspect_level, sgdg_inspect_embedding, sgdg_inspect_factor).
+//
+// They run the same host code as sgdg_create - the mesh checks, the
+// refinement into nested levels with their canonical vertex order, the FP64
+// assembly on the finest level and the Galerkin projection of Sect. 4.2 - on
+// one mesh, without a handle or a device, and copy the result out.  They let
+// a caller (or a test on a machine without a GPU) compare what the library
+// assembles with an independent implementation.
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+
+namespace sgdg {
+namespace {
+
+sgdg_status fail_host(const Status& st) {
+  set_last_error(st.msg);
+  return st.code;
+}
+
+Status hierarchy_of(const sgdg_mesh* m, int L, int level, Hierarchy& h) {
+  if (!m) return {SGDG_EINVAL, "null mesh"};
+  if (L < 0 || L >= kMaxLevels) return {SGDG_EINVAL, "L out of range 0..11"};
+  if (level < 0 || level > L) return {SGDG_EINVAL, "level out of range 0..L"};
+  Status st = validate_mesh(*m);
+  if (st.code) return st;
+  return build_hierarchy(*m, L, h);
+}
+
+// CSR out: sizes always; arrays when all three are given
+void copy_csr(const Csr& A, int* nrows, int* nnz, int* rowptr, int* col, double* val) {
+  if (nrows) *nrows = A.nrows;
+  if (nnz) *nnz = A.nnz();
+  if (rowptr && col && val) {
+    std::memcpy(rowptr, A.rowptr.data(), sizeof(int) * A.rowptr.size());
+    std::memcpy(col, A.col.data(), sizeof(int) * A.col.size());
+    std::memcpy(val, A.val.data(), sizeof(double) * A.val.size());
+  }
+}
+
+}  // namespace
+}  // namespace sgdg
+
+using namespace sgdg;
+
+extern "C" {
+
+sgdg_status sgdg_inspect_level(const sgdg_mesh* mesh, int L, int level, int* n_vertices, double* coords) {
+  Hierarchy h;
+  Status st = hierarchy_of(mesh, L, level, h);
+  if (st.code) return fail_host(st);
+  const MeshLevel& lv = h.lev[level];
+  if (n_vertices) *n_vertices = lv.n;
+  if (coords) std::memcpy(coords, lv.coords.data(), sizeof(double) * lv.coords.size());
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_inspect_embedding(const sgdg_mesh* mesh, int L, int level, int* nrows, int* nnz, int* rowptr,
+                                   int* col, double* val) {
+  Hierarchy h;
+  Status st = hierarchy_of(mesh, L, level, h);
+  if (st.code) return fail_host(st);
+  if (level >= L) return fail_host({SGDG_EINVAL, "the embedding of level l needs l < L"});
+  copy_csr(h.E[level], nrows, nnz, rowptr, col, val);
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_inspect_factor(const sgdg_mesh* mesh, const sgdg_coeffs* coeffs, int side, int L, int level,
+                                const sgdg_factor_spec* spec, int* nrows, int* nnz, int* rowptr, int* col,
+                                double* val) {
+  if (!coeffs || !spec) return fail_host({SGDG_EINVAL, "null coefficients or factor spec"});
+  if (side != 0 && side != 1) return fail_host({SGDG_EINVAL, "side must be 0 (x) or 1 (v)"});
+  Hierarchy h;
+  Status st = hierarchy_of(mesh, L, level, h);
+  if (st.code) return fail_host(st);
+  const int d = mesh->dim;
+  // the coefficient functions of this side, numbered as in sgdg_create:
+  // beta components 0 .. 2 kMaxDim - 1, then sigma
+  SideFns fns;
+  for (int p = 0; p < 2 * kMaxDim; ++p) {
+    const sgdg_product& b = coeffs->beta[p];
+    fns.fn.push_back(p < 2 * d ? (side == 0 ? b.fx : b.fv) : nullptr);
+    fns.user.push_back(side == 0 ? b.ux : b.uv);
+  }
+  fns.fn.push_back(side == 0 ? coeffs->sigma.fx : coeffs->sigma.fv);
+  fns.user.push_back(side == 0 ? coeffs->sigma.ux : coeffs->sigma.uv);
+  const int nfn = (int)fns.fn.size();
+  FactorSpec f;
+  f.kind = spec->kind;
+  f.test = spec->test;
+  f.trial = spec->trial;
+  if (f.kind != 0 && f.kind != 1) return fail_host({SGDG_EINVAL, "factor kind must be 0 (volume) or 1 (faces)"});
+  if (f.test < 0 || f.test > d || f.trial < 0 || f.trial > d)
+    return fail_host({SGDG_EINVAL, "derivative index out of range 0..dim"});
+  if (spec->n_weight < 0 || spec->n_weight > 4 || spec->n_restrict < 0 || spec->n_restrict > 2)
+    return fail_host({SGDG_EINVAL, "at most 4 weight functions and 2 restrictions"});
+  for (int i = 0; i < spec->n_weight; ++i) {
+    if (spec->weight[i] < 0 || spec->weight[i] >= nfn || !fns.fn[spec->weight[i]])
+      return fail_host({SGDG_EINVAL, "weight function id names no function of this side"});
+    f.wfn.push_back(spec->weight[i]);
+  }
+  for (int i = 0; i < spec->n_restrict; ++i) {
+    const int id = spec->restrict_fn[i], sg = spec->restrict_sign[i];
+    if (id < 0 || id >= nfn || !fns.fn[id] || (sg != 1 && sg != -1))
+      return fail_host({SGDG_EINVAL, "restriction: a function of this side and a sign of +-1"});
+    f.restrict_.push_back({id, sg});
+  }
+  std::sort(f.wfn.begin(), f.wfn.end());
+  std::sort(f.restrict_.begin(), f.restrict_.end());
+  if (f.kind == 1) {
+    if (spec->face_axis < 0 || spec->face_axis >= d || (spec->face_side != 1 && spec->face_side != -1))
+      return fail_host({SGDG_EINVAL, "face: an axis of the mesh and a side of +-1"});
+    f.face_axis = spec->face_axis;
+    f.face_side = spec->face_side;
+  }
+  std::vector<Csr> per_level;
+  st = assemble_factor(h, fns, f, per_level);
+  if (st.code) return fail_host(st);
+  copy_csr(per_level[level], nrows, nnz, rowptr, col, val);
+  return SGDG_OK;
+}
+
+}  // extern "C"

@@ -21,6 +21,9 @@ struct Status {
   std::string msg;
 };
 
+// The message sgdg_last_error(NULL) returns (calls without a handle).
+void set_last_error(const std::string& msg);
+
 // Host CSR (rows sorted, columns sorted within a row).
 struct Csr {
   int nrows = 0, ncols = 0;

@@ -8,14 +8,14 @@
 #include "sgdg.h"
 
 int main(void) {
-  const int c_sizes[9] = {(int)sizeof(sgdg_mesh),   (int)sizeof(sgdg_product), (int)sizeof(sgdg_source),
-                          (int)sizeof(sgdg_coeffs), (int)sizeof(sgdg_config),  (int)sizeof(sgdg_info),
-                          (int)sizeof(sgdg_strip_stats), (int)sizeof(sgdg_kernel_stat),
-                          (int)sizeof(sgdg_checkpoint_info)};
-  int lib_sizes[9] = {0};
-  const int n = sgdg_struct_sizes(lib_sizes, 9);
-  int bad = n != 9;
-  for (int i = 0; i < 9; ++i) {
+  const int c_sizes[10] = {(int)sizeof(sgdg_mesh),   (int)sizeof(sgdg_product), (int)sizeof(sgdg_source),
+                           (int)sizeof(sgdg_coeffs), (int)sizeof(sgdg_config),  (int)sizeof(sgdg_info),
+                           (int)sizeof(sgdg_strip_stats), (int)sizeof(sgdg_kernel_stat),
+                           (int)sizeof(sgdg_checkpoint_info), (int)sizeof(sgdg_factor_spec)};
+  int lib_sizes[10] = {0};
+  const int n = sgdg_struct_sizes(lib_sizes, 10);
+  int bad = n != 10;
+  for (int i = 0; i < 10; ++i) {
     printf("%d %d %d\n", i, c_sizes[i], lib_sizes[i]);
     bad |= c_sizes[i] != lib_sizes[i];
   }

@@ -54,10 +54,10 @@ def test_binding_structs_match_the_library_layouts(lib):
     (a field missing on either side changes them)."""
     import ctypes as C
     import paper_2204_05988_gb300 as P
-    out = (C.c_int * 9)()
-    assert lib.sgdg_struct_sizes(out, 9) == 9
+    out = (C.c_int * 10)()
+    assert lib.sgdg_struct_sizes(out, 10) == 10
     mine = [C.sizeof(t) for t in (P.Mesh, P.Product, P.Source, P.Coeffs, P.Config, P.Info, P.StripStats,
-                                  P.KernelStat, P.CheckpointInfo)]
+                                  P.KernelStat, P.CheckpointInfo, P.FactorSpec)]
     assert list(out) == mine
 
 

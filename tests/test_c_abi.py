@@ -26,4 +26,4 @@ def test_c99_caller_matches_library_layouts(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, out.stdout + out.stderr
     rows = [l.split() for l in out.stdout.splitlines() if not l.startswith("offset")]
-    assert len(rows) == 9 and all(r[1] == r[2] for r in rows), out.stdout
+    assert len(rows) == 10 and all(r[1] == r[2] for r in rows), out.stdout

@@ -1,0 +1,134 @@
+"""The library's host-side spaces and factors against the oracle, on the CPU
+(sgdg_inspect_level / _embedding / _factor: the code sgdg_create runs,
+without a handle or a device).
+
+* Levels: the vertex coordinates of every level, in the canonical order of
+  the storage layout, equal the oracle's (d = 1, 2, 3; periodic and not).
+* Embeddings E_{l+1 <- l} (Sect. 4.2) equal the oracle's, entry for entry.
+* Kronecker factors (Sect. 4.2): mass, derivative pairings, weights by the
+  coefficient functions of the workloads (linear v, sin/cos of x), products
+  of two weights, sign restrictions (the inflow splitting of Sect. 5.2) and
+  boundary faces on every box side, on both sides of the phase space,
+  assembled on level L and projected to every coarser level, agree with
+  the oracle's independent assembly and projection to 1e-13 of the
+  factor's largest entry.  Both use collapsed Gauss rules with 4 points per
+  direction, written independently.
+* Bad requests give SGDG_EINVAL.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import paper_2204_05988_gb300 as P
+import sgdg_workloads as W
+from oracle.assembly import Factor, FactorStore
+from oracle.mesh import Hierarchy
+
+
+def _csr(t, n):
+    rp, cl, vl = t
+    return sp.csr_matrix((vl, cl, rp), shape=(len(rp) - 1, n))
+
+
+MESHES = [W.interval_mesh(0.0, 1.0, 4), W.interval_mesh(-1.0, 1.0, 4, periodic=True), W.square_mesh(0.0, 1.0, 2),
+          W.square_mesh(-1.0, 1.0, 4, periodic=True), W.cube_mesh(0.0, 1.0, 1)]
+
+
+@pytest.mark.parametrize("mesh", MESHES, ids=lambda m: f"d{m.dim}{'_per' if any(m.periodic) else ''}")
+def test_levels_and_embeddings_equal_the_oracle(mesh):
+    L = 2 if mesh.dim < 3 else 1
+    H = Hierarchy(mesh, L)
+    for l in range(L + 1):
+        c = P.inspect_level(mesh, L, l)
+        assert c.shape == H.levels[l].coords.shape and np.array_equal(c, H.levels[l].coords), l
+    for l in range(L):
+        E = _csr(P.inspect_embedding(mesh, L, l), H.levels[l].n)
+        assert (E != H.E[l]).nnz == 0, l
+
+
+def _oracle_factor(prob, side, spec):
+    d = prob.d
+    fn = lambda i: (prob.sigma if i == 2 * d else prob.beta[i]).__dict__["fx" if side == 0 else "fv"]
+    kind = "face" if spec.get("kind", 0) == 1 else "vol"
+    return Factor(kind, 1.0, tuple(fn(i) for i in spec.get("weight", ())), spec.get("test", 0),
+                  spec.get("trial", 0), tuple((fn(i), 1.0, s) for i, s in spec.get("restrict", ())),
+                  spec.get("face", (-1, 0)))
+
+
+def _specs(prob, side):
+    """Factor specs with weights and restrictions by the functions this side has."""
+    d = prob.d
+    have = [p for p in range(2 * d) if (prob.beta[p].fx if side == 0 else prob.beta[p].fv) is not None]
+    out = [{}]
+    for p in range(1, d + 1):
+        out += [{"test": p, "trial": p}, {"test": 0, "trial": p}, {"test": p, "trial": 0}]
+    if d >= 2:
+        out.append({"test": 1, "trial": 2})
+    for a in have:
+        out += [{"weight": (a,)}, {"weight": (a,), "test": 0, "trial": 1}, {"weight": (a,), "restrict": ((a, 1),)},
+                {"weight": (a,), "restrict": ((a, -1),)}]
+        for b in have:
+            if b >= a:
+                out.append({"weight": (a, b), "test": 1, "trial": d})
+        for ax in range(d):
+            for sd in (-1, 1):
+                out.append({"kind": 1, "weight": (a,), "restrict": ((a, -sd),), "face": (ax, sd)})
+    for ax in range(d):
+        for sd in (-1, 1):
+            out.append({"kind": 1, "face": (ax, sd)})
+    return out
+
+
+def _map_ids(prob, spec):
+    """Oracle function index 2d (sigma) is id 6 in the C ABI."""
+    d = prob.d
+    m = lambda i: 6 if i == 2 * d else i
+    out = dict(spec)
+    if "weight" in spec:
+        out["weight"] = tuple(m(i) for i in spec["weight"])
+    if "restrict" in spec:
+        out["restrict"] = tuple((m(i), s) for i, s in spec["restrict"])
+    return out
+
+
+@pytest.mark.parametrize("case", ["d1_inflow", "d2_transport", "d3_transport"])
+def test_factors_equal_the_oracle(case):
+    prob = {"d1_inflow": lambda: W.inflow_manufactured_1d(L=3), "d2_transport": lambda: W.transport_2d(L=2),
+            "d3_transport": lambda: W.transport_3d(L=1)}[case]()
+    L = prob.L
+    for side, mesh in ((0, prob.mesh_x), (1, prob.mesh_v)):
+        H = Hierarchy(mesh, L)
+        fs = FactorStore(H)
+        specs = _specs(prob, side)
+        if prob.sigma.coef != 0.0 and (prob.sigma.fx if side == 0 else prob.sigma.fv) is not None:
+            specs.append({"weight": (2 * prob.d,)})
+        for spec in specs:
+            f = _oracle_factor(prob, side, spec)
+            cs = _map_ids(prob, spec)
+            for level in range(L, -1, -1):
+                A = _csr(P.inspect_factor(prob, side, L, level, kind=cs.get("kind", 0), test=cs.get("test", 0),
+                                          trial=cs.get("trial", 0), weight=cs.get("weight", ()),
+                                          restrict=cs.get("restrict", ()), face=cs.get("face", (-1, 0))),
+                         H.levels[level].n)
+                B = fs.proj(f, level, level)
+                scale = max(abs(B).max(), 1e-300)
+                assert abs(A - B).max() <= 1e-13 * scale, (case, side, spec, level, abs(A - B).max(), scale)
+
+
+def test_bad_requests_are_refused():
+    prob = W.transport_2d(L=1)
+    with pytest.raises(P.SgdgError) as e:
+        P.inspect_level(prob.mesh_x, 2, 3)
+    assert e.value.code == 1
+    with pytest.raises(P.SgdgError):
+        P.inspect_embedding(prob.mesh_x, 2, 2)                 # no E out of the finest level
+    with pytest.raises(P.SgdgError):
+        P.inspect_factor(prob, 0, 1, 1, weight=(0,))           # beta_0 = v1 has no x function
+    with pytest.raises(P.SgdgError):
+        P.inspect_factor(prob, 1, 1, 1, kind=1, face=(2, 1))   # axis 2 on a 2-D mesh
+    with pytest.raises(P.SgdgError):
+        P.inspect_factor(prob, 0, 1, 1, test=3)
+    bad = W.CoarseMesh(coords=np.array([[0.0], [0.5], [0.5], [1.0]]), cells=np.array([[0, 1], [2, 3]], dtype=np.int32),
+                       lo=(0.0,), hi=(1.0,), periodic=(False,))
+    with pytest.raises(P.SgdgError):
+        P.inspect_level(bad, 1, 0)
