@@ -274,6 +274,19 @@ sgdg_status sgdg_inspect_embedding(const sgdg_mesh* mesh, int L, int level, int*
 sgdg_status sgdg_inspect_factor(const sgdg_mesh* mesh, const sgdg_coeffs* coeffs, int side, int L, int level,
                                 const sgdg_factor_spec* spec, int* nrows, int* nnz, int* rowptr, int* col,
                                 double* val);
+/* The Kronecker terms of A^(delta) (Sect. 4.2, the block formula) that
+ * sgdg_create forms for these meshes and coefficients, with the time
+ * couplings of the strip (t0, t0 + dt) (with time factors: the Gauss sum of
+ * Sect. 4.2 over time_quad points; without: the exact time matrices, and t0
+ * is ignored): *n_terms always; when tau, xspec and vspec are given and
+ * capacity >= *n_terms, term k's coupling tau[4k + 2s + s'] (s the test
+ * index, as in the block formula) and its x and v factors.  The operator's
+ * full-grid form is sum_k tau_k (x) X_k (x) V_k with X_k, V_k from
+ * sgdg_inspect_factor.  Only coefficient callbacks and time factors of the
+ * sgdg_coeffs are read (u0, f, g are not). */
+sgdg_status sgdg_inspect_terms(const sgdg_mesh* mesh_x, const sgdg_mesh* mesh_v, const sgdg_coeffs* coeffs,
+                               double dt, double delta, double t0, int capacity, int* n_terms, double* tau,
+                               sgdg_factor_spec* xspec, sgdg_factor_spec* vspec);
 void sgdg_destroy(void* h);
 const char* sgdg_last_error(const void* h);
 sgdg_status sgdg_get_info(const void* h, sgdg_info* out);

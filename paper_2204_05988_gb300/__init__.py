@@ -108,6 +108,8 @@ EXPORTS = {
                                          C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_inspect_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                       C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sgdg_inspect_terms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                     C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_field_update": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "sgdg_resolve_strip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_advance_strip_vp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p,
@@ -558,7 +560,22 @@ class _Marshal:
         self._cb_error: List[str] = []
 
     _fn = lambda self, f, d: Solver._fn(self, f, d)
+    _tfn = lambda self, f: Solver._tfn(self, f)
     _product = lambda self, pr, d: Solver._product(self, pr, d)
+
+    def coeffs(self, problem) -> "Coeffs":
+        """beta and sigma with their time factors (u0, f, g left empty)."""
+        d = problem.d
+        co = Coeffs()
+        for p in range(6):
+            co.beta[p] = self._product(problem.beta[p], d) if p < 2 * d else Product(0.0, FN(), None, FN(), None)
+        co.sigma = self._product(problem.sigma, d)
+        for p in range(2 * d):
+            co.beta_t[p] = self._tfn(getattr(problem.beta[p], "ft", None))
+        co.sigma_t = self._tfn(getattr(problem.sigma, "ft", None))
+        co.time_quad = 0
+        self._keep.append(co)
+        return co
 
 
 def _csr_out(call):
@@ -610,11 +627,7 @@ def inspect_factor(problem, side: int, L: int, level: int, kind: int = 0, test: 
     6 sigma); restrict: (id, sign) pairs; face: (axis, side) for kind 1."""
     lib = load_library()
     m = _Marshal()
-    d = problem.d
-    co = Coeffs()
-    for p in range(6):
-        co.beta[p] = m._product(problem.beta[p], d) if p < 2 * d else Product(0.0, FN(), None, FN(), None)
-    co.sigma = m._product(problem.sigma, d)
+    co = m.coeffs(problem)
     spec = FactorSpec()
     spec.kind, spec.test, spec.trial = kind, test, trial
     spec.n_weight = len(weight)
@@ -631,6 +644,37 @@ def inspect_factor(problem, side: int, L: int, level: int, kind: int = 0, test: 
     if m._cb_error:
         raise RuntimeError("coefficient callback failed: " + m._cb_error[0])
     return out
+
+
+def _spec_dict(f: FactorSpec) -> dict:
+    return {"kind": f.kind, "test": f.test, "trial": f.trial, "weight": tuple(f.weight[:f.n_weight]),
+            "restrict": tuple((f.restrict_fn[i], f.restrict_sign[i]) for i in range(f.n_restrict)),
+            "face": (f.face_axis, f.face_side)}
+
+
+def inspect_terms(problem, t0: float = 0.0):
+    """sgdg_inspect_terms: the Kronecker terms of the problem's operator with
+    the time couplings of the strip (t0, t0 + dt): a list of (tau (2 x 2),
+    x factor spec, v factor spec), specs as dicts of sgdg_factor_spec's
+    fields (keywords of ``inspect_factor``)."""
+    lib = load_library()
+    m = _Marshal()
+    co = m.coeffs(problem)
+    mx, mv = _mesh_struct(problem.mesh_x, m._keep), _mesh_struct(problem.mesh_v, m._keep)
+    n = C.c_int()
+    args = (C.byref(mx), C.byref(mv), C.byref(co), float(problem.dt), float(problem.delta), float(t0))
+    st = lib.sgdg_inspect_terms(*args, 0, C.byref(n), None, None, None)
+    if st != 0:
+        raise SgdgError(st, lib.sgdg_last_error(None).decode())
+    tau = np.zeros((n.value, 2, 2))
+    xs, vs = (FactorSpec * max(1, n.value))(), (FactorSpec * max(1, n.value))()
+    st = lib.sgdg_inspect_terms(*args, n.value, C.byref(n), tau.ctypes.data, C.cast(xs, C.c_void_p),
+                                C.cast(vs, C.c_void_p))
+    if st != 0:
+        raise SgdgError(st, lib.sgdg_last_error(None).decode())
+    if m._cb_error:
+        raise RuntimeError("coefficient callback failed: " + m._cb_error[0])
+    return [(tau[k], _spec_dict(xs[k]), _spec_dict(vs[k])) for k in range(n.value)]
 
 
 def checkpoint_verify(path: str) -> CheckpointInfo:

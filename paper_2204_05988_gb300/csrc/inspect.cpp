@@ -1,5 +1,6 @@
-// Host-only views of the discrete spaces and factors the library builds
-// (sgdg_inspect_level, sgdg_inspect_embedding, sgdg_inspect_factor).
+// Host-only views of the discrete spaces, factors and Kronecker terms the
+// library builds (sgdg_inspect_level, sgdg_inspect_embedding,
+// sgdg_inspect_factor, sgdg_inspect_terms).
 //
 // They run the same host code as sgdg_create - the mesh checks, the
 // refinement into nested levels with their canonical vertex order, the FP64
@@ -38,6 +39,24 @@ void copy_csr(const Csr& A, int* nrows, int* nnz, int* rowptr, int* col, double*
     std::memcpy(col, A.col.data(), sizeof(int) * A.col.size());
     std::memcpy(val, A.val.data(), sizeof(double) * A.val.size());
   }
+}
+
+Status spec_out(const FactorSpec& f, sgdg_factor_spec& o) {
+  if (f.wfn.size() > 4 || f.restrict_.size() > 2) return {SGDG_EINVAL, "a factor spec does not fit sgdg_factor_spec"};
+  std::memset(&o, 0, sizeof(o));
+  o.kind = f.kind;
+  o.test = f.test;
+  o.trial = f.trial;
+  o.n_weight = (int)f.wfn.size();
+  for (size_t i = 0; i < f.wfn.size(); ++i) o.weight[i] = f.wfn[i];
+  o.n_restrict = (int)f.restrict_.size();
+  for (size_t i = 0; i < f.restrict_.size(); ++i) {
+    o.restrict_fn[i] = f.restrict_[i].first;
+    o.restrict_sign[i] = f.restrict_[i].second;
+  }
+  o.face_axis = f.face_axis;
+  o.face_side = f.face_side;
+  return {};
 }
 
 }  // namespace
@@ -119,6 +138,44 @@ sgdg_status sgdg_inspect_factor(const sgdg_mesh* mesh, const sgdg_coeffs* coeffs
   st = assemble_factor(h, fns, f, per_level);
   if (st.code) return fail_host(st);
   copy_csr(per_level[level], nrows, nnz, rowptr, col, val);
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_inspect_terms(const sgdg_mesh* mesh_x, const sgdg_mesh* mesh_v, const sgdg_coeffs* coeffs,
+                               double dt, double delta, double t0, int capacity, int* n_terms, double* tau,
+                               sgdg_factor_spec* xspec, sgdg_factor_spec* vspec) {
+  if (!mesh_x || !mesh_v || !coeffs || !n_terms) return fail_host({SGDG_EINVAL, "null argument"});
+  if (mesh_x->dim != mesh_v->dim) return fail_host({SGDG_EINVAL, "mesh_x and mesh_v must have the same dimension"});
+  if (!(dt > 0.0) || !(delta >= 0.0)) return fail_host({SGDG_EINVAL, "dt must be > 0 and delta >= 0"});
+  if (coeffs->time_quad < 0 || coeffs->time_quad > 8) return fail_host({SGDG_EINVAL, "time_quad must be in 0..8"});
+  Status st = validate_mesh(*mesh_x);
+  if (!st.code) st = validate_mesh(*mesh_v);
+  if (st.code) return fail_host(st);
+  const int d = mesh_x->dim;
+  TermTable tt;
+  st = build_terms(*coeffs, d, *mesh_x, *mesh_v, dt, delta, tt);
+  if (st.code) return fail_host(st);
+  if (tt.time_dep) {
+    // the couplings of the strip (t0, t0 + dt), as sgdg_create and every
+    // strip compute them
+    std::vector<std::pair<sgdg_tfn, void*>> ft;
+    for (int p = 0; p < 2 * kMaxDim; ++p) ft.push_back({p < 2 * d ? coeffs->beta_t[p] : nullptr, coeffs->beta_ut[p]});
+    ft.push_back({coeffs->sigma_t, coeffs->sigma_ut});
+    st = strip_time_couplings(tt, t0, dt, coeffs->time_quad > 0 ? coeffs->time_quad : 3, ft);
+    if (st.code) return fail_host(st);
+  }
+  const int n = (int)tt.terms.size();
+  *n_terms = n;
+  if (!tau && !xspec && !vspec) return SGDG_OK;
+  if (!tau || !xspec || !vspec || capacity < n) return fail_host({SGDG_EINVAL, "output arrays missing or too short"});
+  for (int k = 0; k < n; ++k) {
+    const Term& t = tt.terms[k];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) tau[4 * k + 2 * a + b] = t.tau[a][b];
+    st = spec_out(tt.xf[t.x], xspec[k]);
+    if (!st.code) st = spec_out(tt.vf[t.v], vspec[k]);
+    if (st.code) return fail_host(st);
+  }
   return SGDG_OK;
 }
 
