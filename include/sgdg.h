@@ -274,6 +274,14 @@ sgdg_status sgdg_inspect_embedding(const sgdg_mesh* mesh, int L, int level, int*
 sgdg_status sgdg_inspect_factor(const sgdg_mesh* mesh, const sgdg_coeffs* coeffs, int side, int L, int level,
                                 const sgdg_factor_spec* spec, int* nrows, int* nnz, int* rowptr, int* col,
                                 double* val);
+/* The load vector F[i] = int (f_1 ... f_n)(y) D phi_i(y) dy of the n_fn
+ * (0..4) functions fns (users: their user pointers, may be NULL; no
+ * functions: f = 1), D = the value (deriv 0) or d/dy_deriv (1-based axis),
+ * assembled on level L and restricted to `level` (E^T, Sect. 4.2) - the
+ * spatial factors of the source terms of b_j (Sect. 2) as sgdg_create forms
+ * them; out[n_vertices of level]. */
+sgdg_status sgdg_inspect_load(const sgdg_mesh* mesh, int L, int level, int n_fn, const sgdg_fn* fns,
+                              void* const* users, int deriv, double* out);
 /* The Kronecker terms of A^(delta) (Sect. 4.2, the block formula) that
  * sgdg_create forms for these meshes and coefficients, with the time
  * couplings of the strip (t0, t0 + dt) (with time factors: the Gauss sum of

@@ -108,6 +108,8 @@ EXPORTS = {
                                          C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_inspect_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                       C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sgdg_inspect_load": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                    C.c_void_p]),
     "sgdg_inspect_terms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                      C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_field_update": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
@@ -641,6 +643,24 @@ def inspect_factor(problem, side: int, L: int, level: int, kind: int = 0, test: 
     ms = _mesh_struct(mesh, m._keep)
     out = _csr_out(lambda nr, nz, rp, cl, vl: lib.sgdg_inspect_factor(C.byref(ms), C.byref(co), side, L, level,
                                                                       C.byref(spec), nr, nz, rp, cl, vl))
+    if m._cb_error:
+        raise RuntimeError("coefficient callback failed: " + m._cb_error[0])
+    return out
+
+
+def inspect_load(mesh, L: int, level: int, fns=(), deriv: int = 0) -> np.ndarray:
+    """sgdg_inspect_load: int (prod fns) D phi_i on level L restricted to
+    `level` (D: value, or d/dy_deriv for deriv >= 1)."""
+    lib = load_library()
+    m = _Marshal()
+    ms = _mesh_struct(mesh, m._keep)
+    arr = (FN * max(1, len(fns)))(*[m._fn(f, mesh.dim) for f in fns])
+    n = inspect_level(mesh, L, level).shape[0]
+    out = np.empty(n)
+    st = lib.sgdg_inspect_load(C.byref(ms), L, level, len(fns), C.cast(arr, C.c_void_p), None, deriv,
+                               out.ctypes.data)
+    if st != 0:
+        raise SgdgError(st, lib.sgdg_last_error(None).decode())
     if m._cb_error:
         raise RuntimeError("coefficient callback failed: " + m._cb_error[0])
     return out

@@ -1,6 +1,6 @@
 // Host-only views of the discrete spaces, factors and Kronecker terms the
 // library builds (sgdg_inspect_level, sgdg_inspect_embedding,
-// sgdg_inspect_factor, sgdg_inspect_terms).
+// sgdg_inspect_factor, sgdg_inspect_load, sgdg_inspect_terms).
 //
 // They run the same host code as sgdg_create - the mesh checks, the
 // refinement into nested levels with their canonical vertex order, the FP64
@@ -138,6 +138,21 @@ sgdg_status sgdg_inspect_factor(const sgdg_mesh* mesh, const sgdg_coeffs* coeffs
   st = assemble_factor(h, fns, f, per_level);
   if (st.code) return fail_host(st);
   copy_csr(per_level[level], nrows, nnz, rowptr, col, val);
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_inspect_load(const sgdg_mesh* mesh, int L, int level, int n_fn, const sgdg_fn* fns,
+                              void* const* users, int deriv, double* out) {
+  if (n_fn < 0 || n_fn > 4 || (n_fn > 0 && !fns)) return fail_host({SGDG_EINVAL, "0..4 weight functions"});
+  Hierarchy h;
+  Status st = hierarchy_of(mesh, L, level, h);
+  if (st.code) return fail_host(st);
+  std::vector<std::pair<sgdg_fn, void*>> w;
+  for (int i = 0; i < n_fn; ++i) w.push_back({fns[i], users ? users[i] : nullptr});
+  std::vector<std::vector<double>> per_level;
+  st = load_vectors_w(h, w, deriv, per_level);
+  if (st.code) return fail_host(st);
+  if (out) std::memcpy(out, per_level[level].data(), sizeof(double) * per_level[level].size());
   return SGDG_OK;
 }
 

@@ -13,6 +13,8 @@ without a handle or a device).
   the oracle's independent assembly and projection to 1e-13 of the
   factor's largest entry.  Both use collapsed Gauss rules with 4 points per
   direction, written independently.
+* Load vectors of the source terms (sgdg_inspect_load; a product of two
+  functions, its value and derivative pairings) on every level, d = 1, 2, 3.
 * The Kronecker term table (sgdg_inspect_terms: time couplings of the
   strip, δ placement, inflow splitting, time-factor gates) with the factors
   forms the same finest full-grid operator sum_k X_k (x) V_k (x) tau_k as the
@@ -197,3 +199,27 @@ def test_term_table_comparison_sees_the_strip_time():
     prob = W.time_dependent_1d(L=2)
     A, B = _library_operator(prob, 0.5 + prob.dt), _oracle_operator(prob, 0.5)
     assert abs(A - B).max() > 1e-6 * abs(B).max()
+
+
+@pytest.mark.parametrize("mesh", [W.interval_mesh(0.0, 1.0, 4), W.square_mesh(-1.0, 1.0, 2), W.cube_mesh(0.0, 1.0, 1)],
+                         ids=["d1", "d2", "d3"])
+def test_load_vectors_equal_the_oracle(mesh):
+    """The spatial factors of the source terms (Sect. 2, b_j): loads of a
+    product of functions and of its derivative pairing, on every level."""
+    from oracle.assembly import assemble_load, assemble_load_grad
+    L = 2 if mesh.dim < 3 else 1
+    H = Hierarchy(mesh, L)
+    f1 = lambda p: np.cos(np.pi * p[:, 0]) + 0.5
+    f2 = lambda p: 1.0 + p[:, -1] ** 2
+    prod = lambda p: f1(p) * f2(p)
+    for level in range(L + 1):
+        E = H.embed(L, level)
+        ref0 = E.T @ assemble_load(H.levels[L], prod)
+        got0 = P.inspect_load(mesh, L, level, (f1, f2), 0)
+        assert np.abs(got0 - ref0).max() <= 1e-13 * np.abs(ref0).max(), level
+        one = P.inspect_load(mesh, L, level, (), 0)
+        assert abs(one.sum() - np.prod(np.array(mesh.hi) - np.array(mesh.lo))) < 1e-12
+        for ax in range(mesh.dim):
+            ref = E.T @ assemble_load_grad(H.levels[L], prod, ax)
+            got = P.inspect_load(mesh, L, level, (f1, f2), ax + 1)
+            assert np.abs(got - ref).max() <= 1e-13 * max(np.abs(ref).max(), 1e-300), (level, ax)
