@@ -274,6 +274,14 @@ sgdg_status sgdg_inspect_embedding(const sgdg_mesh* mesh, int L, int level, int*
 sgdg_status sgdg_inspect_factor(const sgdg_mesh* mesh, const sgdg_coeffs* coeffs, int side, int L, int level,
                                 const sgdg_factor_spec* spec, int* nrows, int* nnz, int* rowptr, int* col,
                                 double* val);
+/* The products of a factor with the transfers that the sweep applies
+ * (Sect. 4.2, X_{l,l'} through E): which 0, R_level X_{level+1} = E^T X
+ * (rows: level, columns: level + 1; level < L); which 1, X_level E_{level-1}
+ * (rows: level, columns: level - 1; level >= 1).  Factor, sizes and arrays
+ * as for sgdg_inspect_factor. */
+sgdg_status sgdg_inspect_product(const sgdg_mesh* mesh, const sgdg_coeffs* coeffs, int side, int L, int level,
+                                 const sgdg_factor_spec* spec, int which, int* nrows, int* nnz, int* rowptr,
+                                 int* col, double* val);
 /* The load vector F[i] = int (f_1 ... f_n)(y) D phi_i(y) dy of the n_fn
  * (0..4) functions fns (users: their user pointers, may be NULL; no
  * functions: f = 1), D = the value (deriv 0) or d/dy_deriv (1-based axis),

@@ -108,6 +108,8 @@ EXPORTS = {
                                          C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_inspect_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                       C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sgdg_inspect_product": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                       C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p]),
     "sgdg_inspect_load": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                     C.c_void_p]),
     "sgdg_inspect_terms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
@@ -622,7 +624,7 @@ def inspect_embedding(mesh, L: int, level: int):
 
 
 def inspect_factor(problem, side: int, L: int, level: int, kind: int = 0, test: int = 0, trial: int = 0,
-                   weight=(), restrict=(), face=(-1, 0)):
+                   weight=(), restrict=(), face=(-1, 0), product: int = -1):
     """sgdg_inspect_factor: one factor of side 0 (x) or 1 (v) of the problem's
     coefficients, assembled on level L and projected to `level`, as CSR
     arrays (rowptr, col, val).  weight: function ids (0..5 beta components,
@@ -641,8 +643,12 @@ def inspect_factor(problem, side: int, L: int, level: int, kind: int = 0, test: 
     spec.face_axis, spec.face_side = face
     mesh = problem.mesh_x if side == 0 else problem.mesh_v
     ms = _mesh_struct(mesh, m._keep)
-    out = _csr_out(lambda nr, nz, rp, cl, vl: lib.sgdg_inspect_factor(C.byref(ms), C.byref(co), side, L, level,
-                                                                      C.byref(spec), nr, nz, rp, cl, vl))
+    if product < 0:
+        out = _csr_out(lambda nr, nz, rp, cl, vl: lib.sgdg_inspect_factor(C.byref(ms), C.byref(co), side, L, level,
+                                                                          C.byref(spec), nr, nz, rp, cl, vl))
+    else:   # sgdg_inspect_product: 0 = R_level X_{level+1}, 1 = X_level E_{level-1}
+        out = _csr_out(lambda nr, nz, rp, cl, vl: lib.sgdg_inspect_product(
+            C.byref(ms), C.byref(co), side, L, level, C.byref(spec), product, nr, nz, rp, cl, vl))
     if m._cb_error:
         raise RuntimeError("coefficient callback failed: " + m._cb_error[0])
     return out

@@ -1,6 +1,7 @@
 // Host-only views of the discrete spaces, factors and Kronecker terms the
 // library builds (sgdg_inspect_level, sgdg_inspect_embedding,
-// sgdg_inspect_factor, sgdg_inspect_load, sgdg_inspect_terms).
+// sgdg_inspect_factor, sgdg_inspect_product, sgdg_inspect_load,
+// sgdg_inspect_terms).
 //
 // They run the same host code as sgdg_create - the mesh checks, the
 // refinement into nested levels with their canonical vertex order, the FP64
@@ -59,6 +60,56 @@ Status spec_out(const FactorSpec& f, sgdg_factor_spec& o) {
   return {};
 }
 
+// one factor on every level of the hierarchy refined to L (the code of
+// sgdg_create: the side's coefficient functions numbered as there, beta
+// components 0 .. 2 kMaxDim - 1, then sigma)
+Status factor_levels(const sgdg_mesh* mesh, const sgdg_coeffs* coeffs, int side, int L, int level,
+                     const sgdg_factor_spec* spec, Hierarchy& h, std::vector<Csr>& per_level) {
+  if (!coeffs || !spec) return {SGDG_EINVAL, "null coefficients or factor spec"};
+  if (side != 0 && side != 1) return {SGDG_EINVAL, "side must be 0 (x) or 1 (v)"};
+  Status st = hierarchy_of(mesh, L, level, h);
+  if (st.code) return st;
+  const int d = mesh->dim;
+  SideFns fns;
+  for (int p = 0; p < 2 * kMaxDim; ++p) {
+    const sgdg_product& b = coeffs->beta[p];
+    fns.fn.push_back(p < 2 * d ? (side == 0 ? b.fx : b.fv) : nullptr);
+    fns.user.push_back(side == 0 ? b.ux : b.uv);
+  }
+  fns.fn.push_back(side == 0 ? coeffs->sigma.fx : coeffs->sigma.fv);
+  fns.user.push_back(side == 0 ? coeffs->sigma.ux : coeffs->sigma.uv);
+  const int nfn = (int)fns.fn.size();
+  FactorSpec f;
+  f.kind = spec->kind;
+  f.test = spec->test;
+  f.trial = spec->trial;
+  if (f.kind != 0 && f.kind != 1) return {SGDG_EINVAL, "factor kind must be 0 (volume) or 1 (faces)"};
+  if (f.test < 0 || f.test > d || f.trial < 0 || f.trial > d)
+    return {SGDG_EINVAL, "derivative index out of range 0..dim"};
+  if (spec->n_weight < 0 || spec->n_weight > 4 || spec->n_restrict < 0 || spec->n_restrict > 2)
+    return {SGDG_EINVAL, "at most 4 weight functions and 2 restrictions"};
+  for (int i = 0; i < spec->n_weight; ++i) {
+    if (spec->weight[i] < 0 || spec->weight[i] >= nfn || !fns.fn[spec->weight[i]])
+      return {SGDG_EINVAL, "weight function id names no function of this side"};
+    f.wfn.push_back(spec->weight[i]);
+  }
+  for (int i = 0; i < spec->n_restrict; ++i) {
+    const int id = spec->restrict_fn[i], sg = spec->restrict_sign[i];
+    if (id < 0 || id >= nfn || !fns.fn[id] || (sg != 1 && sg != -1))
+      return {SGDG_EINVAL, "restriction: a function of this side and a sign of +-1"};
+    f.restrict_.push_back({id, sg});
+  }
+  std::sort(f.wfn.begin(), f.wfn.end());
+  std::sort(f.restrict_.begin(), f.restrict_.end());
+  if (f.kind == 1) {
+    if (spec->face_axis < 0 || spec->face_axis >= d || (spec->face_side != 1 && spec->face_side != -1))
+      return {SGDG_EINVAL, "face: an axis of the mesh and a side of +-1"};
+    f.face_axis = spec->face_axis;
+    f.face_side = spec->face_side;
+  }
+  return assemble_factor(h, fns, f, per_level);
+}
+
 }  // namespace
 }  // namespace sgdg
 
@@ -89,55 +140,34 @@ sgdg_status sgdg_inspect_embedding(const sgdg_mesh* mesh, int L, int level, int*
 sgdg_status sgdg_inspect_factor(const sgdg_mesh* mesh, const sgdg_coeffs* coeffs, int side, int L, int level,
                                 const sgdg_factor_spec* spec, int* nrows, int* nnz, int* rowptr, int* col,
                                 double* val) {
-  if (!coeffs || !spec) return fail_host({SGDG_EINVAL, "null coefficients or factor spec"});
-  if (side != 0 && side != 1) return fail_host({SGDG_EINVAL, "side must be 0 (x) or 1 (v)"});
   Hierarchy h;
-  Status st = hierarchy_of(mesh, L, level, h);
-  if (st.code) return fail_host(st);
-  const int d = mesh->dim;
-  // the coefficient functions of this side, numbered as in sgdg_create:
-  // beta components 0 .. 2 kMaxDim - 1, then sigma
-  SideFns fns;
-  for (int p = 0; p < 2 * kMaxDim; ++p) {
-    const sgdg_product& b = coeffs->beta[p];
-    fns.fn.push_back(p < 2 * d ? (side == 0 ? b.fx : b.fv) : nullptr);
-    fns.user.push_back(side == 0 ? b.ux : b.uv);
-  }
-  fns.fn.push_back(side == 0 ? coeffs->sigma.fx : coeffs->sigma.fv);
-  fns.user.push_back(side == 0 ? coeffs->sigma.ux : coeffs->sigma.uv);
-  const int nfn = (int)fns.fn.size();
-  FactorSpec f;
-  f.kind = spec->kind;
-  f.test = spec->test;
-  f.trial = spec->trial;
-  if (f.kind != 0 && f.kind != 1) return fail_host({SGDG_EINVAL, "factor kind must be 0 (volume) or 1 (faces)"});
-  if (f.test < 0 || f.test > d || f.trial < 0 || f.trial > d)
-    return fail_host({SGDG_EINVAL, "derivative index out of range 0..dim"});
-  if (spec->n_weight < 0 || spec->n_weight > 4 || spec->n_restrict < 0 || spec->n_restrict > 2)
-    return fail_host({SGDG_EINVAL, "at most 4 weight functions and 2 restrictions"});
-  for (int i = 0; i < spec->n_weight; ++i) {
-    if (spec->weight[i] < 0 || spec->weight[i] >= nfn || !fns.fn[spec->weight[i]])
-      return fail_host({SGDG_EINVAL, "weight function id names no function of this side"});
-    f.wfn.push_back(spec->weight[i]);
-  }
-  for (int i = 0; i < spec->n_restrict; ++i) {
-    const int id = spec->restrict_fn[i], sg = spec->restrict_sign[i];
-    if (id < 0 || id >= nfn || !fns.fn[id] || (sg != 1 && sg != -1))
-      return fail_host({SGDG_EINVAL, "restriction: a function of this side and a sign of +-1"});
-    f.restrict_.push_back({id, sg});
-  }
-  std::sort(f.wfn.begin(), f.wfn.end());
-  std::sort(f.restrict_.begin(), f.restrict_.end());
-  if (f.kind == 1) {
-    if (spec->face_axis < 0 || spec->face_axis >= d || (spec->face_side != 1 && spec->face_side != -1))
-      return fail_host({SGDG_EINVAL, "face: an axis of the mesh and a side of +-1"});
-    f.face_axis = spec->face_axis;
-    f.face_side = spec->face_side;
-  }
   std::vector<Csr> per_level;
-  st = assemble_factor(h, fns, f, per_level);
+  Status st = factor_levels(mesh, coeffs, side, L, level, spec, h, per_level);
   if (st.code) return fail_host(st);
   copy_csr(per_level[level], nrows, nnz, rowptr, col, val);
+  return SGDG_OK;
+}
+
+sgdg_status sgdg_inspect_product(const sgdg_mesh* mesh, const sgdg_coeffs* coeffs, int side, int L, int level,
+                                 const sgdg_factor_spec* spec, int which, int* nrows, int* nnz, int* rowptr,
+                                 int* col, double* val) {
+  if (which == 0 ? level >= L : (which == 1 ? level < 1 : true))
+    return fail_host({SGDG_EINVAL, "which 0 needs level < L, which 1 needs level >= 1"});
+  Hierarchy h;
+  std::vector<Csr> X;
+  Status st = factor_levels(mesh, coeffs, side, L, level, spec, h, X);
+  if (st.code) return fail_host(st);
+  // the products as sgdg_create forms them for the sweep (Sect. 4.2: the
+  // restriction of a factor and a factor with the prolongation)
+  Csr C;
+  if (which == 0) {
+    C = product_pattern(h.Rt[level], h.lev[level + 1].pattern);
+    product_values(h.Rt[level], h.Rt[level].val, X[level + 1], X[level + 1].val, C, C.val);
+  } else {
+    C = product_pattern(h.lev[level].pattern, h.E[level - 1]);
+    product_values(X[level], X[level].val, h.E[level - 1], h.E[level - 1].val, C, C.val);
+  }
+  copy_csr(C, nrows, nnz, rowptr, col, val);
   return SGDG_OK;
 }
 

@@ -13,6 +13,9 @@ without a handle or a device).
   the oracle's independent assembly and projection to 1e-13 of the
   factor's largest entry.  Both use collapsed Gauss rules with 4 points per
   direction, written independently.
+* The factor-transfer products of the sweep (sgdg_inspect_product:
+  R_l X_{l+1} and X_l E_{l-1}) equal the oracle's projected factors times
+  its embeddings, to 1e-13.
 * Load vectors of the source terms (sgdg_inspect_load; a product of two
   functions, its value and derivative pairings) on every level, d = 1, 2, 3.
 * The Kronecker term table (sgdg_inspect_terms: time couplings of the
@@ -223,3 +226,30 @@ def test_load_vectors_equal_the_oracle(mesh):
             ref = E.T @ assemble_load_grad(H.levels[L], prod, ax)
             got = P.inspect_load(mesh, L, level, (f1, f2), ax + 1)
             assert np.abs(got - ref).max() <= 1e-13 * max(np.abs(ref).max(), 1e-300), (level, ax)
+
+
+@pytest.mark.parametrize("case", ["d1_inflow", "d2_transport", "d3_transport"])
+def test_transfer_products_equal_the_oracle(case):
+    """The factor-transfer products the sweep applies (sgdg_inspect_product):
+    R_l X_{l+1} = E_l^T X_{l+1} and X_l E_{l-1}, for the mass, a derivative
+    pairing and a weighted factor, against the oracle's projected factors
+    times its embeddings."""
+    prob = {"d1_inflow": lambda: W.inflow_manufactured_1d(L=3), "d2_transport": lambda: W.transport_2d(L=2),
+            "d3_transport": lambda: W.transport_3d(L=1)}[case]()
+    L = prob.L
+    for side, mesh in ((0, prob.mesh_x), (1, prob.mesh_v)):
+        H = Hierarchy(mesh, L)
+        fs = FactorStore(H)
+        have = [p for p in range(2 * prob.d) if (prob.beta[p].fx if side == 0 else prob.beta[p].fv) is not None]
+        specs = [{}, {"test": 0, "trial": 1}] + [{"weight": (have[0],), "test": 1, "trial": 0}]
+        for spec in specs:
+            f = _oracle_factor(prob, side, spec)
+            for level in range(L + 1):
+                if level < L:
+                    A = _csr(P.inspect_factor(prob, side, L, level, product=0, **spec), H.levels[level + 1].n)
+                    B = (H.E[level].T @ fs.proj(f, level + 1, level + 1)).tocsr()
+                    assert abs(A - B).max() <= 1e-13 * abs(B).max(), (case, side, spec, level, "RX")
+                if level >= 1:
+                    A = _csr(P.inspect_factor(prob, side, L, level, product=1, **spec), H.levels[level - 1].n)
+                    B = (fs.proj(f, level, level) @ H.E[level - 1]).tocsr()
+                    assert abs(A - B).max() <= 1e-13 * abs(B).max(), (case, side, spec, level, "XE")
