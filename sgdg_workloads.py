@@ -467,6 +467,37 @@ def inflow_manufactured_2d(L: int = 2, sigma: float = 0.2, dt: float = 1.0 / 8.0
                    u0=[Product(c0, X, V)], exact=exact, f=f, g=[Source(1.0, X, V, a)])
 
 
+def inflow_time_dependent_2d(L: int = 1, sigma: float = 0.2, dt: float = 1.0 / 8.0, n_strips: int = 3,
+                             c0: float = 1.0, c1: float = -0.4) -> Problem:
+    """inflow_manufactured_2d with time factors on the v-components of beta:
+    E1 = (1 - 3t)(x2 - 1/2) changes sign at t = 1/3 (inside the third strip
+    of dt = 1/8) and E2 = (1 + t)(1/2 - x1); the sources carry the same time
+    factors, g = u* on Gamma^-(t)."""
+    X = lambda p: 1.0 + p[:, 0] + 2.0 * p[:, 1]
+    V = lambda p: 1.0 + 0.5 * p[:, 0] - 0.3 * p[:, 1]
+    a = lambda t: c0 + c1 * np.asarray(t)
+    da = lambda t: c1 + 0.0 * np.asarray(t)
+    e1 = lambda t: 1.0 - 3.0 * np.asarray(t)
+    e2 = lambda t: 1.0 + np.asarray(t)
+
+    def exact(t, x, v):
+        return (c0 + c1 * t) * (1.0 + x[..., 0] + 2.0 * x[..., 1]) * (1.0 + 0.5 * v[..., 0] - 0.3 * v[..., 1])
+
+    f = [Source(1.0, X, V, da), Source(sigma, X, V, a),
+         Source(1.0, None, lambda p: p[:, 0] * V(p), a),
+         Source(2.0, None, lambda p: p[:, 1] * V(p), a),
+         Source(0.5, lambda p: (p[:, 1] - 0.5) * X(p), None, lambda t: e1(t) * a(t)),
+         Source(-0.3, lambda p: (0.5 - p[:, 0]) * X(p), None, lambda t: e2(t) * a(t))]
+    hx = 1.0 / 2 ** (L + 1)
+    return Problem(name=f"inflow_time_dependent_2d_L{L}", d=2, mesh_x=square_mesh(0.0, 1.0, 2),
+                   mesh_v=square_mesh(-1.0, 1.0, 2), L=L, r=1, dt=dt, delta=hx, n_strips=n_strips,
+                   beta=[Product(1.0, None, lambda p: p[:, 0]), Product(1.0, None, lambda p: p[:, 1]),
+                         Product(1.0, lambda p: p[:, 1] - 0.5, None, e1),
+                         Product(1.0, lambda p: 0.5 - p[:, 0], None, e2)],
+                   sigma=Product(sigma) if sigma != 0.0 else Product(0.0),
+                   u0=[Product(c0, X, V)], exact=exact, f=f, g=[Source(1.0, X, V, a)])
+
+
 def manufactured_2d(L: int = 9, sigma: float = 0.1, dt: float = 1.0 / 64.0, n_strips: int = 16,
                     seed: int = 0) -> Problem:
     """d=2 manufactured solution on the transport_2d problem (beta = (v1, v2,

@@ -178,7 +178,8 @@ def _oracle_operator(prob, t0):
 
 @pytest.mark.parametrize("case,t0", [
     ("transport_2d", 0.0), ("free_streaming_1d", 0.0), ("inflow_manufactured_1d", 0.0), ("transport_3d", 0.0),
-    ("time_dependent_1d", 0.5), ("time_dependent_2d", 0.25), ("inflow_time_dependent_1d", 0.25)])
+    ("time_dependent_1d", 0.5), ("time_dependent_2d", 0.25), ("inflow_time_dependent_1d", 0.25),
+    ("inflow_time_dependent_2d", 0.25)])
 def test_term_table_gives_the_oracle_operator(case, t0):
     """The library's Kronecker terms (time couplings of the strip at t0,
     inflow splitting, time-factor gates) with its factors form the same
@@ -188,7 +189,8 @@ def test_term_table_gives_the_oracle_operator(case, t0):
             "inflow_manufactured_1d": lambda: W.inflow_manufactured_1d(L=2),
             "transport_3d": lambda: W.transport_3d(L=0), "time_dependent_1d": lambda: W.time_dependent_1d(L=2),
             "time_dependent_2d": lambda: W.time_dependent_2d(L=1),
-            "inflow_time_dependent_1d": lambda: W.inflow_time_dependent_1d(L=2)}
+            "inflow_time_dependent_1d": lambda: W.inflow_time_dependent_1d(L=2),
+            "inflow_time_dependent_2d": lambda: W.inflow_time_dependent_2d(L=1)}
     prob = make[case]()
     A, B = _library_operator(prob, t0), _oracle_operator(prob, t0)
     assert A.shape == B.shape

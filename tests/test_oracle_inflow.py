@@ -71,6 +71,18 @@ def test_time_dependent_inflow_solution_is_reproduced():
         assert np.abs(got - ref).max() < 1e-8 * np.abs(ref).max(), j
 
 
+def test_time_dependent_inflow_solution_is_reproduced_2d():
+    """d = 2: E1 = (1 - 3t)(x2 - 1/2) changes sign inside the third strip,
+    E2 = (1 + t)(1/2 - x1) keeps its sign; u* is reproduced at every node."""
+    prob = W.inflow_time_dependent_2d(L=1)
+    s = StripSolver(prob, tol=1e-12)
+    ends = s.run()
+    for j, U in enumerate(ends):
+        got = nodal_values(s.op, U)
+        ref = _nodal_exact(s.op, prob.exact, (j + 1) * prob.dt)
+        assert np.abs(got - ref).max() < 1e-8 * np.abs(ref).max(), j
+
+
 def test_planted_mistake_ungated_time_dependent_inflow_fails(monkeypatch):
     """Dropping the gate (both inflow parts active on the whole strip, each
     weighted by the time factor) misses u* in the strip with the sign change."""
