@@ -228,8 +228,8 @@ class Solver:
                  restart: int = 30, inner_its: int = 20, inner_rtol: float = 1e-3, cheb_steps: int = 6,
                  device: int = 0, vlasov_poisson: bool = False, outer_method: int = SGDG_OUTER_FGMRES,
                  hbm_budget_bytes: int = 0):
-        if getattr(problem, "order", 1) != 1:
-            raise ValueError("the library builds continuous P1 spaces only (spatial order 1)")
+        if getattr(problem, "order", 1) != 1 or getattr(problem, "element", "P") != "P":
+            raise ValueError("the library builds continuous P1 spaces on simplices only (order 1, element 'P')")
         self.lib = load_library()
         self.problem = problem
         self._keep: List = []

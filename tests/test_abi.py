@@ -62,9 +62,12 @@ def test_binding_structs_match_the_library_layouts(lib):
 
 
 def test_binding_rejects_p2_problems():
-    """The library's spaces are continuous P1; a problem asking for P2 (the
-    oracle's r = 2 path) is refused before anything reaches the device."""
+    """The library's spaces are continuous P1 on simplices; a problem asking
+    for P2 or for tensor-product Q elements (the oracle's r = 2 and Q_r paths)
+    is refused before anything reaches the device."""
     import paper_2204_05988_gb300 as P
     import sgdg_workloads as W
     with pytest.raises(ValueError):
         P.Solver(W.periodic_advection_1d(L=1, r=2))
+    with pytest.raises(ValueError):
+        P.Solver(W.periodic_advection_2d(L=1, element="Q"))
