@@ -567,7 +567,7 @@ class _Marshal:
     _tfn = lambda self, f: Solver._tfn(self, f)
     _product = lambda self, pr, d: Solver._product(self, pr, d)
 
-    def coeffs(self, problem) -> "Coeffs":
+    def coeffs(self, problem, time_quad: int = 0) -> "Coeffs":
         """beta and sigma with their time factors (u0, f, g left empty)."""
         d = problem.d
         co = Coeffs()
@@ -577,7 +577,7 @@ class _Marshal:
         for p in range(2 * d):
             co.beta_t[p] = self._tfn(getattr(problem.beta[p], "ft", None))
         co.sigma_t = self._tfn(getattr(problem.sigma, "ft", None))
-        co.time_quad = 0
+        co.time_quad = int(time_quad)
         self._keep.append(co)
         return co
 
@@ -678,14 +678,15 @@ def _spec_dict(f: FactorSpec) -> dict:
             "face": (f.face_axis, f.face_side)}
 
 
-def inspect_terms(problem, t0: float = 0.0):
+def inspect_terms(problem, t0: float = 0.0, time_quad: int = 0):
     """sgdg_inspect_terms: the Kronecker terms of the problem's operator with
     the time couplings of the strip (t0, t0 + dt): a list of (tau (2 x 2),
     x factor spec, v factor spec), specs as dicts of sgdg_factor_spec's
-    fields (keywords of ``inspect_factor``)."""
+    fields (keywords of ``inspect_factor``); time_quad: Gauss points per
+    strip with time factors (0: 3)."""
     lib = load_library()
     m = _Marshal()
-    co = m.coeffs(problem)
+    co = m.coeffs(problem, time_quad)
     mx, mv = _mesh_struct(problem.mesh_x, m._keep), _mesh_struct(problem.mesh_v, m._keep)
     n = C.c_int()
     args = (C.byref(mx), C.byref(mv), C.byref(co), float(problem.dt), float(problem.delta), float(t0))

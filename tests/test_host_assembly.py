@@ -22,7 +22,8 @@ without a handle or a device).
   strip, δ placement, inflow splitting, time-factor gates) with the factors
   forms the same finest full-grid operator sum_k X_k (x) V_k (x) tau_k as the
   oracle's block formula, to 1e-13 (d = 1, 2, 3; with and without inflow
-  boundaries; time-dependent strips across sign changes).
+  boundaries; time-dependent strips across sign changes; time rules of 1 to
+  8 Gauss points per strip).
 * Bad requests give SGDG_EINVAL.
 """
 import numpy as np
@@ -144,7 +145,7 @@ def test_bad_requests_are_refused():
         P.inspect_level(bad, 1, 0)
 
 
-def _library_operator(prob, t0):
+def _library_operator(prob, t0, time_quad=0):
     """sum_k X_k (x) V_k (x) tau_k on the finest full grid (L, L), from the
     library's term table and factors."""
     L = prob.L
@@ -158,19 +159,18 @@ def _library_operator(prob, t0):
         return cache[key]
 
     A = None
-    for tau, xs, vs in P.inspect_terms(prob, t0):
+    for tau, xs, vs in P.inspect_terms(prob, t0, time_quad):
         K = sp.kron(fac(0, xs), sp.kron(fac(1, vs), sp.csr_matrix(tau)))
         A = K if A is None else A + K
     return A.tocsr()
 
 
-def _oracle_operator(prob, t0):
-    from oracle.operator import SparseGridOperator, is_time_dependent
+def _oracle_operator(prob, t0, m=3):
+    from oracle.operator import SparseGridOperator, is_time_dependent, kron_terms
     op = SparseGridOperator(prob)
-    if is_time_dependent(prob):
-        op.set_time(t0)
+    terms = kron_terms(prob, t0, m) if is_time_dependent(prob) else op.terms
     A = None
-    for tau, X, V in op.terms:
+    for tau, X, V in terms:
         K = sp.kron(op.fx.fine(X), sp.kron(op.fv.fine(V), sp.csr_matrix(tau)))
         A = K if A is None else A + K
     return A.tocsr()
@@ -255,3 +255,16 @@ def test_transfer_products_equal_the_oracle(case):
                     A = _csr(P.inspect_factor(prob, side, L, level, product=1, **spec), H.levels[level - 1].n)
                     B = (fs.proj(f, level, level) @ H.E[level - 1]).tocsr()
                     assert abs(A - B).max() <= 1e-13 * abs(B).max(), (case, side, spec, level, "XE")
+
+
+@pytest.mark.parametrize("m", [1, 2, 5, 8])
+def test_time_quadrature_rules_equal_the_oracle(m):
+    """Strips with time factors under m-point rules (the library's nodes by
+    Newton's method on P_m, the oracle's from numpy's leggauss): the same
+    operator, on a strip across a sign change of the field."""
+    prob = W.time_dependent_1d(L=2)
+    A, B = _library_operator(prob, 0.5, m), _oracle_operator(prob, 0.5, m)
+    assert abs(A - B).max() <= 1e-13 * abs(B).max(), (m, abs(A - B).max())
+    if m == 1:
+        C = _oracle_operator(prob, 0.5, 3)
+        assert abs(A - C).max() > 1e-6 * abs(C).max()     # the rule matters on this strip
