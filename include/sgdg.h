@@ -225,7 +225,10 @@ typedef struct {
  * FP64 (Sect. 4.2), project them to every level with the embeddings
  * (X_l = E^T X_{l+1} E), compile the Kronecker term table of the block
  * formula (Sect. 4.2; delta on K~ per the weak form of Sect. 2), upload
- * everything to the device.  EINVAL for unsupported input, ENOMEM, ECUDA. */
+ * everything to the device.  EINVAL for unsupported input (including a
+ * coefficient function of beta, sigma or g that returns NaN or Inf at a
+ * quadrature point or centroid; NaN in u0 or f is left to the solver's
+ * SGDG_ENAN), ENOMEM, ECUDA. */
 sgdg_status sgdg_create(const sgdg_config* cfg, const sgdg_coeffs* coeffs, void** out_handle);
 /* The mesh checks of sgdg_create on one coarse mesh (host only, no device
  * call; the list is at sgdg_mesh): SGDG_OK or SGDG_EINVAL, with

@@ -78,7 +78,13 @@ int find_pos(const Csr& P, int i, int j) {
   return (int)(it - P.col.begin());
 }
 
-void eval_fn(const SideFns& fns, int id, const std::vector<double>& pts, int d, std::vector<double>& out) {
+// The coefficient function id at every point.  With `finite` a NaN or Inf
+// value (a bad coefficient of a factor - beta, sigma, the inflow data g -
+// or a callback that failed and reported NaN) is refused; the load vectors
+// of u0 and the sources pass it on, so that NaN data reach the solver and
+// its NaN check (SGDG_ENAN).
+Status eval_fn(const SideFns& fns, int id, const std::vector<double>& pts, int d, std::vector<double>& out,
+               bool finite = true) {
   int n = (int)(pts.size() / d);
   out.assign(n, 0.0);
   const int chunk = 1 << 22;
@@ -86,6 +92,10 @@ void eval_fn(const SideFns& fns, int id, const std::vector<double>& pts, int d, 
     int m = std::min(chunk, n - s);
     fns.fn[id](m, pts.data() + (size_t)s * d, out.data() + s, fns.user[id]);
   }
+  if (finite)
+    for (double v : out)
+      if (!std::isfinite(v)) return {SGDG_EINVAL, "a coefficient function returned NaN or Inf"};
+  return {};
 }
 
 }  // namespace
@@ -253,8 +263,14 @@ Status assemble_volume(const Hierarchy& h, const SideFns& fns, const std::vector
       for (int i = 0; i < d1; ++i)
         for (int j = 0; j < d1; ++j) pos[((size_t)c * d1 + i) * d1 + j] = find_pos(P, cv[i], cv[j]);
     }
-    for (int id : wids) eval_fn(fns, id, pts, d, wv[id]);
-    for (int id : rids) eval_fn(fns, id, cen, d, rv[id]);
+    for (int id : wids) {
+      Status se = eval_fn(fns, id, pts, d, wv[id]);
+      if (se.code) return se;
+    }
+    for (int id : rids) {
+      Status se = eval_fn(fns, id, cen, d, rv[id]);
+      if (se.code) return se;
+    }
 #pragma omp parallel for schedule(dynamic, 1)
     for (int fi = 0; fi < nf; ++fi) {
       const FactorSpec& f = specs[fi];
@@ -350,7 +366,8 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
         for (int a = 0; a < dv; ++a)
           for (int k = 0; k < d; ++k) cen[s * d + k] += lv.bface_coords[((size_t)sel[s] * dv + a) * d + k] / dv;
       for (auto& rs : f.restrict_) {
-        eval_fn(fns, rs.first, cen, d, val);
+        Status se = eval_fn(fns, rs.first, cen, d, val);
+        if (se.code) return se;
         for (size_t s = 0; s < sel.size(); ++s)
           if (!(rs.second * val[s] > 0.0)) keep[s] = 0;
       }
@@ -382,7 +399,8 @@ Status assemble_factor(const Hierarchy& h, const SideFns& fns, const FactorSpec&
     std::vector<double> wprod(sel.size() * nq, 1.0), tmp;
     for (int id : f.wfn) {
       if (sel.empty()) break;
-      eval_fn(fns, id, pts, d, tmp);
+      Status se = eval_fn(fns, id, pts, d, tmp);
+      if (se.code) return se;
       for (size_t i = 0; i < wprod.size(); ++i) wprod[i] *= tmp[i];
     }
     for (size_t s = 0; s < sel.size(); ++s) {
@@ -438,7 +456,7 @@ Status load_vectors_w(const Hierarchy& h, const std::vector<std::pair<sgdg_fn, v
       SideFns t;
       t.fn.push_back(f.first);
       t.user.push_back(f.second);
-      eval_fn(t, 0, pts, d, tmp);
+      eval_fn(t, 0, pts, d, tmp, false);   // data: NaN is the solver's to report
       for (size_t i = 0; i < val.size(); ++i) val[i] *= tmp[i];
     }
     for (int c = 0; c < ne; ++c) {

@@ -268,3 +268,23 @@ def test_time_quadrature_rules_equal_the_oracle(m):
     if m == 1:
         C = _oracle_operator(prob, 0.5, 3)
         assert abs(A - C).max() > 1e-6 * abs(C).max()     # the rule matters on this strip
+
+
+def test_non_finite_coefficient_values_are_refused():
+    """A coefficient function of the operator that returns NaN or Inf
+    anywhere (a weight at a quadrature point, a restriction at a centroid, a
+    face weight) makes the assembly fail with SGDG_EINVAL instead of filling
+    the factors with NaN; sgdg_create runs the same code.  Data loads (u0,
+    sources) pass NaN on: the solver's NaN check reports them (SGDG_ENAN)."""
+    prob = W.transport_2d(L=1)
+    bad = lambda p: np.where(p[:, 0] > 0.7, np.nan, p[:, 0])
+    inf = lambda p: np.where(p[:, 1] < -0.7, np.inf, 1.0 + p[:, 1])
+    prob.beta[0] = W.Product(1.0, None, bad)
+    prob.beta[1] = W.Product(1.0, None, inf)
+    for kw in ({"weight": (0,)}, {"weight": (1,), "test": 1, "trial": 0}, {"restrict": ((0, 1),)},
+               {"kind": 1, "weight": (1,), "face": (1, -1)}):
+        with pytest.raises(P.SgdgError) as e:
+            P.inspect_factor(prob, 1, 1, 1, **kw)
+        assert e.value.code == 1 and "NaN or Inf" in str(e.value), kw
+    assert np.isnan(P.inspect_load(prob.mesh_v, 1, 0, (bad,), 0)).any()
+    P.inspect_factor(W.transport_2d(L=1), 1, 1, 1, weight=(0,))   # the finite original passes
