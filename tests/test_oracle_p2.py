@@ -14,8 +14,7 @@ r = 2 column).
   spanning set (paper levels 1-3), and the streamline-diffusion error of the
   periodic advection problem after one period lies within 5% of the printed
   error with the estimated order within 0.05 of the printed one (paper levels
-  1-3; levels 4 and 5 give 1.001 and 1.003 times the printed errors and
-  orders 2.494 and 2.499, too slow for this suite).  Planted mistake: P2 in
+  1-4; level 5 gives 1.003 times the printed error and order 2.499).  Planted mistake: P2 in
   space with time-DG degree 1 misses the printed errors.
 """
 import os
@@ -115,10 +114,10 @@ def _sd_error(Lp, time_degree=2):
 
 def test_table1_error_and_order_d1_r2():
     ref = _table()
-    errs = {Lp: _sd_error(Lp) for Lp in (1, 2, 3)}
+    errs = {Lp: _sd_error(Lp) for Lp in (1, 2, 3, 4)}
     for Lp, e in errs.items():
         assert 0.95 <= e / ref[Lp][1] <= 1.05, (Lp, e, ref[Lp][1])
-    for Lp in (2, 3):
+    for Lp in (2, 3, 4):
         order = np.log2(errs[Lp - 1] / errs[Lp])
         assert abs(order - ref[Lp][2]) <= 0.05, (Lp, order, ref[Lp][2])
 
