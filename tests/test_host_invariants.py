@@ -12,7 +12,8 @@ only), independent of the oracle:
   the face masses on the two sides of axis p (non-periodic box).
 * Time couplings (Eq. 10 with the Legendre basis): for beta = 0 the single
   term has tau = T_t + G_t + sigma M_t with M_t = dt diag(1, 1/3),
-  T_t = [[0, 2], [0, 0]], G_t = [[1, -1], [-1, 1]] in closed form.
+  T_t = [[0, 2], [0, 0]], G_t = [[1, -1], [-1, 1]] in closed form, and one
+  strip of a mode then advances by the Radau IIA stability function.
 """
 import numpy as np
 import pytest
@@ -99,3 +100,22 @@ def test_time_couplings_closed_forms():
     tau, xs, vs = terms[0]
     assert xs["test"] == xs["trial"] == vs["test"] == vs["trial"] == 0 and not xs["weight"] and not vs["weight"]
     assert np.abs(tau - (Tt + Gt + sigma * Mt)).max() < 1e-15
+
+
+@pytest.mark.parametrize("sigma_dt", [0.01, 0.5, 2.0, 40.0])
+def test_dg1_strip_is_radau_iia(sigma_dt):
+    """With beta = 0 and delta = 0 the spatial factor is the mass matrix, so
+    every mode follows the 2 x 2 strip system tau c = eta(t_{j-1}^+) U^-:
+    the end value c_0 + c_1 over U^- is the stability function of DG(1) in
+    time, the (1, 2) Pade approximant of exp(z) that 2-stage Radau IIA also
+    has, R(z) = (1 + z/3) / (1 - 2z/3 + z^2/6), z = -sigma dt."""
+    dt = 0.1
+    prob = W.free_streaming_1d(L=1, n_strips=1)
+    prob.beta = [W.Product(0.0), W.Product(0.0)]
+    prob.dt, prob.delta = dt, 0.0
+    prob.sigma = W.Product(sigma_dt / dt)
+    (tau, _, _), = P.inspect_terms(prob)
+    c = np.linalg.solve(tau, np.array([1.0, -1.0]))     # eta_s(t_{j-1}^+) = (1, -1)
+    z = -sigma_dt
+    R = (1.0 + z / 3.0) / (1.0 - 2.0 * z / 3.0 + z * z / 6.0)
+    assert abs((c[0] + c[1]) - R) < 1e-14 * max(1.0, abs(R)), (sigma_dt, c[0] + c[1], R)
