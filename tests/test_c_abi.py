@@ -2,7 +2,9 @@
 `tests/c/abi_check.c` compiles with gcc against include/sgdg.h alone, links
 the built libsgdg.so, and its struct sizes equal the library's
 (sgdg_struct_sizes) - header/ABI drift that the Python binding's own layout
-checks would not see fails here."""
+checks would not see fails here.  It also calls the host-only entry points
+from C (mesh check, levels, embedding, a factor with a C callback) and
+checks their results."""
 import os
 import shutil
 import subprocess
@@ -22,8 +24,9 @@ def test_c99_caller_matches_library_layouts(tmp_path):
     libdir = os.path.dirname(LIB_PATH)
     subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
                     os.path.join(ROOT, "tests", "c", "abi_check.c"), "-o", str(exe), "-L", libdir,
-                    "-Wl,-rpath," + libdir, "-l:" + os.path.basename(LIB_PATH)], check=True)
+                    "-Wl,-rpath," + libdir, "-l:" + os.path.basename(LIB_PATH), "-lm"], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, out.stdout + out.stderr
-    rows = [l.split() for l in out.stdout.splitlines() if not l.startswith("offset")]
+    rows = [l.split() for l in out.stdout.splitlines() if not l.startswith(("offset", "host calls"))]
     assert len(rows) == 10 and all(r[1] == r[2] for r in rows), out.stdout
+    assert "host calls ok" in out.stdout, out.stdout
